@@ -1,0 +1,200 @@
+/*
+ * lapeig -- the k smallest eigenpairs of a sparse graph Laplacian on one
+ * NVIDIA GB300 (sm_103a).  C ABI of liblapeig.so.
+ *
+ * Method: Bergamaschi, Bozzo, Franceschet, "Computing the smallest eigenpairs
+ * of the graph Laplacian" (arXiv 1311.1695).  The graph is simple, undirected,
+ * with positive weights (Section 2); L = D - A with D the generalised degrees
+ * (Section 2).  Three solvers are compared in the paper: Jacobi-Davidson
+ * (Algorithm 2, Section 3.2), DACG (Algorithm 3, Section 3.3) and implicitly
+ * restarted Lanczos on the inverse (Algorithm 1, Section 3.1).
+ *
+ * Conventions for every entry point
+ *  - Input graphs are given by the CSR of the adjacency matrix A with both
+ *    triangles stored: rowptr int64 [n+1] (rowptr[0] = 0), colidx int32 [nnz]
+ *    strictly increasing within each row, weights double [nnz] or NULL for
+ *    unit weights.  Required: symmetric pattern and values, no diagonal
+ *    entries, weights finite and > 0, nnz < 2^31.
+ *  - "Host" pointers are ordinary CPU memory owned by the caller; the library
+ *    copies what it needs and keeps no pointer after the call returns.
+ *    "Device" pointers are CUDA global memory of the current device, owned by
+ *    the caller, and must stay valid until the work on `stream` completes.
+ *  - Dense blocks on the device are row-major: entry (row r, column c) of a
+ *    block with leading dimension ld is at X[r*ld + c].  Dense results copied
+ *    to the host by lap_eigs are column-major (eigenvector j is
+ *    evecs[j*n .. j*n + n-1]).
+ *  - Return values: 0 = LAP_OK; LAP_ENOCONV (> 0) = partial result (the first
+ *    info->n_converged pairs are valid); negative = error, nothing valid.
+ *    lap_strerror() describes a code; lap_last_error() gives detail of the
+ *    last failure on the calling thread.  No entry point aborts or throws.
+ *  - All device work is issued on `stream` (NULL = the legacy default
+ *    stream).  Entry points that return results to the host synchronise it.
+ */
+#ifndef LAPEIG_H
+#define LAPEIG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LAP_OK = 0,
+  LAP_ENOCONV = 1,       /* iteration cap reached; partial result */
+  LAP_EINVAL = -1,       /* bad argument (n < 2, k < 1, k too large, NULL, ...) */
+  LAP_ENOTSYM = -2,      /* adjacency pattern or values not symmetric */
+  LAP_EWEIGHT = -3,      /* weight <= 0, NaN or Inf */
+  LAP_ESELFLOOP = -4,    /* diagonal entry in the adjacency */
+  LAP_ENUMERIC = -5,     /* NaN/Inf appeared during the iteration */
+  LAP_ENOMEM = -6,       /* device allocation failed */
+  LAP_ETIMEOUT = -7,     /* opts.max_seconds exceeded; partial result in outputs */
+  LAP_ECUDA = -8,        /* CUDA runtime error (see lap_last_error) */
+  LAP_EUNSORTED = -9     /* column indices not strictly increasing in a row */
+};
+
+typedef enum { LAP_JD = 0, LAP_DACG = 1, LAP_IRLM = 2 } lap_method;
+typedef enum { LAP_PREC_FP64 = 0, LAP_PREC_MIXED = 1 } lap_precision;
+typedef enum { LAP_F64 = 0, LAP_F32 = 1 } lap_dtype;
+
+/* Options.  Zero-initialise and set struct_size = sizeof(lap_opts) (or call
+ * lap_opts_default); a zero field means "default". */
+typedef struct {
+  uint32_t struct_size;
+  int block;          /* JD block width b (default k, at most 32) */
+  int m_keep;         /* JD: Ritz vectors kept at each restart (default b + 2);
+                         the paper's m_min (Section 3.2, Section 4) */
+  int inner_maxit;    /* correction-solve PCG steps, ITMAX (default 20, Section 4) */
+  double inner_tol;   /* relative PCG residual drop delta_PCG (default 1e-2, Section 4) */
+  int max_outer;      /* outer-iteration cap (default 1000); exceeded -> LAP_ENOCONV */
+  int ncv;            /* IRLM Krylov dimension (default: 15/30/60/120 for
+                         1/5/20/50 pairs, interpolated; Section 4) */
+  int precision;      /* lap_precision (default LAP_PREC_FP64) */
+  int include_null;   /* 1: pair 1 is (0, e/sqrt(n)) and k-1 more follow */
+  uint64_t seed;      /* start-block seed (SplitMix64 counter generator) */
+  const double* x0;   /* optional host warm start, n x k0 column-major */
+  int k0;
+  void* stream;       /* cudaStream_t for all device work (NULL = default) */
+  double max_seconds; /* wall-clock cap (0 = none) -> LAP_ETIMEOUT */
+  int team;           /* SpMM lanes per row: 4, 8, 16, 32 (0 = autotuned) */
+  int verbose;        /* 1: per-iteration log on stderr */
+} lap_opts;
+
+typedef struct {
+  int status;
+  int n_converged;
+  int outer_its;          /* outer iterations (linear-system solutions for JD/IRLM) */
+  int inner_its;          /* PCG iterations (summed over block columns for JD) */
+  int64_t n_matvec;       /* single-vector products with L (the paper's MVP count) */
+  double norm_L;          /* ||L||_1 = 2 max_i d_i, the residual normaliser */
+  double max_rel_residual;/* max_j ||L v_j - lambda_j v_j||_2 / ||L||_1, FP64, explicit */
+  double elapsed_ms;      /* wall time inside the call */
+  int phase1_outer;       /* mixed precision: outer iterations done in FP32 */
+  int spmm_team;          /* SpMM lanes per row used */
+} lap_info;
+
+void lap_opts_default(lap_opts* opts);
+const char* lap_strerror(int status);
+const char* lap_last_error(void);
+
+/* ---------------------------------------------------------------- solvers
+ * lap_eigs: the k smallest eigenvalues of L restricted to the complement of
+ * the constant vector e (lambda_2..lambda_{k+1} for a connected graph; the
+ * paper's "smallest strictly positive" eigenvalues, Section 4), with
+ * orthonormal eigenvectors, each orthogonal to e, sign fixed so that the
+ * entry of largest magnitude is positive.  Converged means
+ * ||L v - lambda v||_2 <= tol * ||L||_1 for every pair (checked in FP64).
+ *   method = LAP_JD   : block Jacobi-Davidson (Algorithm 2 with the deflated
+ *                       correction equation Eq. 5, projected Jacobi-
+ *                       preconditioned CG, Section 3.2.1)
+ *            LAP_DACG : deflation-accelerated CG (Algorithm 3)
+ *            LAP_IRLM : Lanczos on L^+ with implicit restarts (Algorithm 1 right)
+ * Host pointers: rowptr, colidx, weights (nullable), evals [k] (ascending),
+ * evecs [n*k] column-major (nullable), info (nullable).  k <= 32 for JD,
+ * k <= n - 1 - include_null always.
+ */
+int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights, int k,
+             double tol, int method, const lap_opts* opts, double* evals, double* evecs, lap_info* info);
+
+/* Many independent graphs in one lock-step solve: every kernel launch covers
+ * all graphs (one block-diagonal SpMM, per-graph reductions, one eigensolver
+ * CTA per graph).  Same k for all graphs.  Arrays of nb host pointers; evecs
+ * and infos may be NULL. JD only. */
+int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
+                     const double* const* weights, int k, double tol, const lap_opts* opts,
+                     double* const* evals, double* const* evecs, lap_info* infos);
+
+/* ---------------------------------------------------------------- graph handle
+ * A validated graph (or batch of graphs) resident on the device, with the
+ * SpMM schedule (hub rows, lanes per row) and scratch for the step-level
+ * entry points below.  Host CSR input; copies are made. */
+typedef struct lap_graph lap_graph;
+int lap_graph_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights,
+                     lap_graph** out);
+int lap_graph_create_batched(int nb, const int64_t* n, const int64_t* const* rowptr,
+                             const int32_t* const* colidx, const double* const* weights, lap_graph** out);
+void lap_graph_destroy(lap_graph* g);
+/* n_total rows, number of graphs, ||L||_1 per graph (host [nseg] or NULL),
+ * SpMM lanes per row, number of hub rows. */
+int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm1, int* team, int* nlong);
+/* Override the SpMM schedule: lanes per row (4, 8, 16, 32) and the degree
+ * above which a row gets a whole CTA (0 keeps the current value). */
+int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
+
+/* ---------------------------------------------------------------- step-level entry points
+ * The steps of the Jacobi-Davidson outer loop on device blocks (row-major,
+ * rows = all rows of the handle, segments concatenated).  dtype selects FP64
+ * or FP32 data; small outputs are FP64 device arrays laid out per graph. */
+
+/* Matrix-vector product (Section 3 item 1; Algorithm 2 step 3), b columns:
+ * Y = L X with the degree diagonal fused.  Device X [n_total x ldx], Y [n_total x ldy]. */
+int lap_spmm(lap_graph* g, int dtype, const void* X, int ldx, void* Y, int ldy, int b, void* stream);
+
+/* Gram product [1 | A]^T B per graph (Algorithm 2 step 4: V^T w):
+ * G (device, FP64) [nseg][(p + ones) x q] row-major.  With ones = 1 the first
+ * row holds the column means of B (the e/sqrt(n) deflation coefficient / sqrt(n)). */
+int lap_gram(lap_graph* g, int dtype, const void* A, int lda, int p, const void* B, int ldb, int q, int ones,
+             double* G, void* stream);
+
+/* Deflation (Eq. 5): X <- X - e e^T X / n - Q Q^T X per graph, with Q
+ * (device, nq orthonormal columns orthogonal to e; nq may be 0). */
+int lap_project(lap_graph* g, int dtype, const void* Q, int ldq, int nq, void* X, int ldx, int b, void* stream);
+
+/* Block Gram-Schmidt (Algorithm 2 step 2 on a block; classical Gram-Schmidt
+ * applied twice, each pass followed by a Cholesky-QR of the block): T becomes
+ * an orthonormal basis of the part of span(T) orthogonal to [e, V].  Columns
+ * that are (numerically) in span[e, V, earlier columns] are set to zero and
+ * reported in kept (host int [nseg*b], nullable). */
+int lap_cgs2(lap_graph* g, int dtype, const void* V, int ldv, int m, void* T, int ldt, int b, int* kept,
+             void* stream);
+
+/* Small dense symmetric eigensolver (Algorithm 2 step 5), nmat matrices of
+ * order m <= 64 (device FP64, H [nmat][m x ldh]); evals ascending [nmat][m],
+ * Y [nmat][m x ldy] with eigenvectors in columns.  Parallel cyclic Jacobi,
+ * one CTA per matrix. */
+int lap_syev_batched(int nmat, int m, const double* H, int ldh, double* evals, double* Y, int ldy, void* stream);
+
+/* Rayleigh-Ritz on an orthonormal basis V (m columns, orthogonal to e):
+ * H = V^T L V, its eigenpairs, and V <- V Y in place (Algorithm 2 steps 4-6).
+ * theta (device FP64) [nseg][m] ascending. */
+int lap_rayleigh_ritz(lap_graph* g, int dtype, void* V, int ldv, int m, double* theta, void* stream);
+
+/* Residual norms (Algorithm 2 steps 6-7): norms[s][c] = ||L x_c - theta_c x_c||_2
+ * (device FP64 [nseg][b]) for X (device) and theta (device FP64 [nseg][b]). */
+int lap_residual_norms(lap_graph* g, int dtype, const void* X, int ldx, const double* theta, int b,
+                       double* norms, void* stream);
+
+/* Correction solve (Algorithm 2 step 8, Eq. 5, Section 3.2.1): `iters` steps
+ * of projected CG on (I - QQ^T)(L - theta_c I)(I - QQ^T) t_c = -r_c with
+ * Q = [e/sqrt(n), X] and preconditioner (I - QQ^T) D^{-1} (I - QQ^T),
+ * starting from t = 0; a column stops early when its residual has dropped by
+ * delta (delta = 0: never).  X (device, b orthonormal columns orthogonal to
+ * e), theta (device FP64 [nseg][b]), R (device; must be orthogonal to
+ * [e, X], as residuals of Ritz pairs of X are), T (device output, ldt = b). */
+int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const double* theta, const void* R,
+                       int ldr, void* T, int ldt, int b, int iters, double delta, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAPEIG_H */

@@ -1,0 +1,407 @@
+// C ABI of liblapeig (declared in include/lapeig.h).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "small.cuh"
+
+namespace lapeig {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void set_last_error(const char* file, int line, const char* msg) {
+  g_last_error = std::string(file) + ":" + std::to_string(line) + ": " + msg;
+}
+const char* last_error() { return g_last_error.c_str(); }
+
+namespace {
+
+lap_opts merged(const lap_opts* o) {
+  lap_opts d;
+  lap_opts_default(&d);
+  if (!o || o->struct_size == 0) return d;
+  lap_opts r = d;
+  const size_t sz = o->struct_size < sizeof(lap_opts) ? o->struct_size : sizeof(lap_opts);
+  std::memcpy(&r, o, sz);
+  r.struct_size = sizeof(lap_opts);
+  return r;
+}
+
+int check_cuda(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return LAP_ECUDA;
+  }
+  return LAP_OK;
+}
+
+int solve(lap_graph* g, int k, double tol, int method, const lap_opts& o, bool want_vecs, SolveOut& out) {
+  switch (method) {
+    case LAP_JD: return solve_jd(g, k, tol, o, want_vecs, out);
+    case LAP_DACG: return solve_dacg(g, k, tol, o, want_vecs, out);
+    case LAP_IRLM: return solve_irlm(g, k, tol, o, want_vecs, out);
+    default: set_error("unknown method"); return LAP_EINVAL;
+  }
+}
+
+// Prepend the null pair (0, e/sqrt(n)) when requested.
+void add_null(SolveOut& out, const std::vector<int>& nrows, int kk) {
+  for (size_t s = 0; s < out.evals.size(); ++s) {
+    out.evals[s].insert(out.evals[s].begin(), 0.0);
+    if (!out.evecs.empty()) {
+      const int n = nrows[s];
+      std::vector<double> v((size_t)n * (kk + 1));
+      const double c = 1.0 / std::sqrt((double)n);
+      for (int i = 0; i < n; ++i) v[i] = c;
+      std::memcpy(v.data() + n, out.evecs[s].data(), sizeof(double) * (size_t)n * kk);
+      out.evecs[s].swap(v);
+    }
+    out.info[s].n_converged += 1;
+  }
+}
+
+}  // namespace
+}  // namespace lapeig
+
+using namespace lapeig;
+
+extern "C" {
+
+void lap_opts_default(lap_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->struct_size = sizeof(lap_opts);
+  o->inner_maxit = 20;
+  o->inner_tol = 1e-2;
+  o->max_outer = 1000;
+  o->precision = LAP_PREC_FP64;
+  o->seed = 0x5EEDull;
+}
+
+const char* lap_strerror(int s) {
+  switch (s) {
+    case LAP_OK: return "ok";
+    case LAP_ENOCONV: return "iteration cap reached; partial result";
+    case LAP_EINVAL: return "invalid argument";
+    case LAP_ENOTSYM: return "adjacency not symmetric";
+    case LAP_EWEIGHT: return "weight not finite and positive";
+    case LAP_ESELFLOOP: return "self-loop in adjacency";
+    case LAP_ENUMERIC: return "NaN or Inf during the iteration";
+    case LAP_ENOMEM: return "device allocation failed";
+    case LAP_ETIMEOUT: return "time limit reached; partial result";
+    case LAP_ECUDA: return "CUDA runtime error";
+    case LAP_EUNSORTED: return "column indices not strictly increasing";
+    default: return "unknown status";
+  }
+}
+
+const char* lap_last_error(void) { return lapeig::last_error(); }
+
+int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
+                     const double* const* weights, int k, double tol, const lap_opts* opts, double* const* evals,
+                     double* const* evecs, lap_info* infos) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nb < 1 || !n || !rowptr || !colidx || !evals || k < 1 || !(tol > 0.0)) {
+    set_error("bad arguments to lap_eigs_batched");
+    return LAP_EINVAL;
+  }
+  lap_opts o = merged(opts);
+  const int kk = o.include_null ? k - 1 : k;
+  std::vector<int> nrows(nb);
+  for (int s = 0; s < nb; ++s) {
+    if (n[s] < 2 || kk < 1 || kk > n[s] - 1 || !evals[s]) { set_error("k out of range for a graph"); return LAP_EINVAL; }
+    nrows[s] = (int)n[s];
+  }
+  lap_graph* g = nullptr;
+  int rc = graph_build(nb, n, rowptr, colidx, weights, &g);
+  if (rc) return rc;
+  if (o.team) {
+    rc = graph_set_schedule(g, o.team, 0);
+    if (rc) { graph_free(g); return rc; }
+  }
+  SolveOut out;
+  const bool want = evecs != nullptr;
+  rc = solve_jd(g, kk, tol, o, want, out);
+  graph_free(g);
+  if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+  if (o.include_null) add_null(out, nrows, kk);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int s = 0; s < nb; ++s) {
+    std::memcpy(evals[s], out.evals[s].data(), sizeof(double) * k);
+    if (want && evecs[s]) std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k);
+    if (infos) {
+      infos[s] = out.info[s];
+      infos[s].elapsed_ms = ms;
+    }
+  }
+  return rc;
+}
+
+int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights, int k, double tol,
+             int method, const lap_opts* opts, double* evals, double* evecs, lap_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (n < 2 || !rowptr || !colidx || !evals || k < 1 || !(tol > 0.0) || method < LAP_JD || method > LAP_IRLM) {
+    set_error("bad arguments to lap_eigs");
+    return LAP_EINVAL;
+  }
+  lap_opts o = merged(opts);
+  const int kk = o.include_null ? k - 1 : k;
+  if (kk < 1 || kk > n - 1) { set_error("k out of range"); return LAP_EINVAL; }
+  lap_graph* g = nullptr;
+  const double* w[1] = {weights};
+  const int64_t* rp[1] = {rowptr};
+  const int32_t* ci[1] = {colidx};
+  int rc = graph_build(1, &n, rp, ci, w, &g);
+  if (rc) return rc;
+  if (o.team) {
+    rc = graph_set_schedule(g, o.team, 0);
+    if (rc) { graph_free(g); return rc; }
+  }
+  SolveOut out;
+  rc = solve(g, kk, tol, method, o, evecs != nullptr, out);
+  graph_free(g);
+  if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+  if (o.include_null) add_null(out, std::vector<int>{(int)n}, kk);
+  std::memcpy(evals, out.evals[0].data(), sizeof(double) * k);
+  if (evecs) std::memcpy(evecs, out.evecs[0].data(), sizeof(double) * (size_t)n * k);
+  if (info) {
+    *info = out.info[0];
+    info->elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rc;
+}
+
+int lap_graph_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights, lap_graph** out) {
+  if (!out) { set_error("NULL output handle"); return LAP_EINVAL; }
+  const double* w[1] = {weights};
+  const int64_t* rp[1] = {rowptr};
+  const int32_t* ci[1] = {colidx};
+  return graph_build(1, &n, rp, ci, w, out);
+}
+
+int lap_graph_create_batched(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
+                             const double* const* weights, lap_graph** out) {
+  if (!out) { set_error("NULL output handle"); return LAP_EINVAL; }
+  return graph_build(nb, n, rowptr, colidx, weights, out);
+}
+
+void lap_graph_destroy(lap_graph* g) { graph_free(g); }
+
+int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm1, int* team, int* nlong) {
+  if (!g) { set_error("NULL handle"); return LAP_EINVAL; }
+  if (n_total) *n_total = g->hg.n;
+  if (nseg) *nseg = g->hg.nseg;
+  if (norm1) std::memcpy(norm1, g->norm1.data(), sizeof(double) * g->norm1.size());
+  if (team) *team = g->dg.team;
+  if (nlong) *nlong = g->dg.nlong;
+  return LAP_OK;
+}
+
+int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh) {
+  if (!g) { set_error("NULL handle"); return LAP_EINVAL; }
+  return graph_set_schedule(g, team, long_thresh);
+}
+
+#define LAP_DTYPE_SWITCH(dtype, ...)                            \
+  do {                                                          \
+    if ((dtype) == LAP_F64) { using T = double; __VA_ARGS__; }  \
+    else if ((dtype) == LAP_F32) { using T = float; __VA_ARGS__; } \
+    else { set_error("dtype must be LAP_F64 or LAP_F32"); return LAP_EINVAL; } \
+  } while (0)
+
+int lap_spmm(lap_graph* g, int dtype, const void* X, int ldx, void* Y, int ldy, int b, void* stream) {
+  if (!g || !X || !Y || b < 1 || ldx < b || ldy < b) { set_error("bad arguments to lap_spmm"); return LAP_EINVAL; }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, spmm<T>(g->dg, (const T*)X, ldx, (T*)Y, ldy, b, s));
+  return check_cuda("lap_spmm");
+}
+
+int lap_gram(lap_graph* g, int dtype, const void* A, int lda, int p, const void* B, int ldb, int q, int ones, double* G,
+             void* stream) {
+  if (!g || !B || !G || p < 0 || q < 1 || p > kMaxCols || q > kMaxCols || (p > 0 && (!A || lda < p)) || ldb < q ||
+      (ones != 0 && ones != 1) || p + ones < 1) {
+    set_error("bad arguments to lap_gram");
+    return LAP_EINVAL;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, gram<T>(g->dg, g->red, (const T*)A, lda, p, (const T*)B, ldb, q, ones, ones, G, q,
+                                  (int64_t)(p + ones) * q, nullptr, s));
+  return check_cuda("lap_gram");
+}
+
+int lap_project(lap_graph* g, int dtype, const void* Q, int ldq, int nq, void* X, int ldx, int b, void* stream) {
+  if (!g || !X || b < 1 || b > kMaxCols || ldx < b || nq < 0 || nq > kMaxCols || (nq > 0 && (!Q || ldq < nq))) {
+    set_error("bad arguments to lap_project");
+    return LAP_EINVAL;
+  }
+  const size_t sm = sizeof(double) * (size_t)g->hg.nseg * (nq + 1) * b;
+  int rc = graph_scratch(g, 0, sm);
+  if (rc) return rc;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, {
+    gram<T>(g->dg, g->red, (const T*)Q, ldq, nq, (const T*)X, ldx, b, 1, 1, g->small, b, (int64_t)(nq + 1) * b,
+            nullptr, s);
+    update<T>(g->dg, (T*)X, ldx, b, 1.0, -1.0, (const T*)Q, ldq, nq, 1, g->small, b, (int64_t)(nq + 1) * b, nullptr,
+              s);
+  });
+  return check_cuda("lap_project");
+}
+
+int lap_cgs2(lap_graph* g, int dtype, const void* V, int ldv, int m, void* Tblk, int ldt, int b, int* kept, void* stream) {
+  if (!g || !Tblk || b < 1 || b > kMaxCols || ldt < b || m < 0 || m > kMaxCols || (m > 0 && (!V || ldv < m))) {
+    set_error("bad arguments to lap_cgs2");
+    return LAP_EINVAL;
+  }
+  const int S = g->hg.nseg;
+  const size_t per = (size_t)65 * 64 + 64 * 64 * 2 + 64 * 3;
+  int rc = graph_scratch(g, 0, sizeof(double) * S * per + sizeof(int) * S * 64 * 2 + 1024);
+  if (rc) return rc;
+  double* Gm = g->small;
+  double* Sm = Gm + (size_t)S * 65 * 64;
+  double* Rinv = Sm + (size_t)S * 64 * 64;
+  double* tmp = Rinv + (size_t)S * 64 * 64;
+  double* scale = tmp + (size_t)S * 64;
+  int* keep1 = reinterpret_cast<int*>(scale + (size_t)S * 64 * 2);
+  int* keep2 = keep1 + (size_t)S * 64;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, {
+    T* Tb = (T*)Tblk;
+    const T* Vb = (const T*)V;
+    const double drop1 = dtype == LAP_F32 ? 1e-10 : 1e-20;
+    coldots<T>(g->dg, g->red, Tb, ldt, Tb, ldt, b, tmp, 64, nullptr, s);
+    inv_sqrt(S * 64, tmp, scale, 0.0, s);
+    colscale<T>(g->dg, Tb, ldt, b, scale, 64, nullptr, s);
+    for (int pass = 0; pass < 2; ++pass) {
+      gram<T>(g->dg, g->red, Vb, ldv, m, Tb, ldt, b, 1, 1, Gm, b, 65 * 64, nullptr, s);
+      update<T>(g->dg, Tb, ldt, b, 1.0, -1.0, Vb, ldv, m, 1, Gm, b, 65 * 64, nullptr, s);
+      gram<T>(g->dg, g->red, Tb, ldt, b, Tb, ldt, b, 0, 0, Sm, b, 64 * 64, nullptr, s);
+      chol_inv(S, b, Sm, 64 * 64, pass == 0 ? drop1 : 0.25, 1, Rinv, 64 * 64, pass == 0 ? keep1 : keep2, nullptr, s);
+      update<T>(g->dg, Tb, ldt, b, 0.0, 1.0, Tb, ldt, b, 0, Rinv, b, 64 * 64, nullptr, s);
+    }
+  });
+  and_flags(S * 64, keep1, keep2, s);
+  if (kept) {
+    std::vector<int> kh((size_t)S * 64);
+    if (cudaMemcpyAsync(kh.data(), keep1, sizeof(int) * S * 64, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return check_cuda("lap_cgs2");
+    for (int q = 0; q < S; ++q)
+      for (int c = 0; c < b; ++c) kept[(size_t)q * b + c] = kh[(size_t)q * 64 + c];
+  }
+  return check_cuda("lap_cgs2");
+}
+
+int lap_syev_batched(int nmat, int m, const double* H, int ldh, double* evals, double* Y, int ldy, void* stream) {
+  if (nmat < 1 || m < 1 || m > 64 || !H || !evals || !Y || ldh < m || ldy < m) {
+    set_error("bad arguments to lap_syev_batched");
+    return LAP_EINVAL;
+  }
+  syev(nmat, m, H, ldh, (int64_t)m * ldh, evals, m, Y, ldy, (int64_t)m * ldy, nullptr, nullptr,
+       reinterpret_cast<cudaStream_t>(stream));
+  return check_cuda("lap_syev_batched");
+}
+
+int lap_rayleigh_ritz(lap_graph* g, int dtype, void* V, int ldv, int m, double* theta, void* stream) {
+  if (!g || !V || !theta || m < 1 || m > 64 || ldv < m) { set_error("bad arguments to lap_rayleigh_ritz"); return LAP_EINVAL; }
+  const int S = g->hg.nseg;
+  const size_t es = dtype == LAP_F32 ? 4 : 8;
+  int rc = graph_scratch(g, (size_t)g->hg.n * m * es, sizeof(double) * S * 2 * 64 * 64);
+  if (rc) return rc;
+  double* Hm = g->small;
+  double* Ym = Hm + (size_t)S * 64 * 64;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, {
+    T* W = (T*)g->scratch;
+    spmm<T>(g->dg, (const T*)V, ldv, W, m, m, s);
+    gram<T>(g->dg, g->red, (const T*)V, ldv, m, W, m, m, 0, 0, Hm, m, 64 * 64, nullptr, s);
+    syev(S, m, Hm, m, 64 * 64, theta, m, Ym, m, 64 * 64, nullptr, nullptr, s);
+    update<T>(g->dg, (T*)V, ldv, m, 0.0, 1.0, (const T*)V, ldv, m, 0, Ym, m, 64 * 64, nullptr, s);
+  });
+  return check_cuda("lap_rayleigh_ritz");
+}
+
+int lap_residual_norms(lap_graph* g, int dtype, const void* X, int ldx, const double* theta, int b, double* norms,
+                       void* stream) {
+  if (!g || !X || !theta || !norms || b < 1 || b > kMaxCols || ldx < b) {
+    set_error("bad arguments to lap_residual_norms");
+    return LAP_EINVAL;
+  }
+  const int S = g->hg.nseg;
+  const size_t es = dtype == LAP_F32 ? 4 : 8;
+  int rc = graph_scratch(g, (size_t)g->hg.n * b * es, sizeof(double) * S * 64 * 2);
+  if (rc) return rc;
+  double* n2 = g->small;
+  double* th = n2 + (size_t)S * 64;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  LAP_DTYPE_SWITCH(dtype, {
+    T* LX = (T*)g->scratch;
+    spmm<T>(g->dg, (const T*)X, ldx, LX, b, b, s);
+    cudaMemcpy2DAsync(th, 64 * sizeof(double), theta, b * sizeof(double), b * sizeof(double), S,
+                      cudaMemcpyDeviceToDevice, s);
+    residual<T>(g->dg, g->red, (const T*)X, ldx, LX, b, th, 64, (T*)nullptr, 0, b, n2, 64, nullptr, s);
+  });
+  // norms = sqrt(n2) copied into [S][b]
+  {
+    std::vector<double> h((size_t)S * 64);
+    if (cudaMemcpyAsync(h.data(), n2, sizeof(double) * S * 64, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return check_cuda("lap_residual_norms");
+    std::vector<double> o((size_t)S * b);
+    for (int q = 0; q < S; ++q)
+      for (int c = 0; c < b; ++c) o[(size_t)q * b + c] = std::sqrt(std::max(0.0, h[(size_t)q * 64 + c]));
+    if (cudaMemcpy(norms, o.data(), sizeof(double) * S * b, cudaMemcpyHostToDevice) != cudaSuccess)
+      return check_cuda("lap_residual_norms");
+  }
+  return check_cuda("lap_residual_norms");
+}
+
+int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const double* theta, const void* R, int ldr,
+                       void* Tout, int ldt, int b, int iters, double delta, void* stream) {
+  if (!g || !X || !theta || !R || !Tout || b < 1 || b > 32 || ldx < b || ldr < b || ldt != b || iters < 0 ||
+      delta < 0.0) {
+    set_error("bad arguments to lap_pcg_correction");
+    return LAP_EINVAL;
+  }
+  const int S = g->hg.nseg;
+  const size_t es = dtype == LAP_F32 ? 4 : 8;
+  const size_t n = (size_t)g->hg.n;
+  int rc = graph_scratch(g, 4 * n * b * es + 256, sizeof(double) * S * (64 * 6 + 33 * 32 * 2) + sizeof(int) * S * 64 + 1024);
+  if (rc) return rc;
+  PcgState ps;
+  double* base = g->small;
+  ps.rho = base;
+  ps.alpha = base + (size_t)S * 64;
+  ps.beta = base + (size_t)S * 128;
+  ps.res0 = base + (size_t)S * 192;
+  ps.resn = base + (size_t)S * 256;
+  double* th = base + (size_t)S * 320;
+  ps.G1 = base + (size_t)S * 384;
+  ps.G2 = ps.G1 + (size_t)S * 33 * 32;
+  ps.done = reinterpret_cast<int*>(ps.G2 + (size_t)S * 33 * 32);
+  ps.bstride = 64;
+  ps.gstride = 33 * 32;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaMemcpy2DAsync(th, 64 * sizeof(double), theta, b * sizeof(double), b * sizeof(double), S, cudaMemcpyDeviceToDevice,
+                    s);
+  LAP_DTYPE_SWITCH(dtype, {
+    T* RES = (T*)g->scratch;
+    T* Z = RES + n * b;
+    T* P = Z + n * b;
+    T* AP = P + n * b;
+    pcg_init<T>(g->dg, g->red, ps, (const T*)X, ldx, (const T*)R, ldr, (T*)Tout, RES, Z, P, b, b, nullptr, nullptr, s);
+    for (int it = 0; it < iters; ++it) {
+      spmm<T>(g->dg, P, b, AP, b, b, s);
+      pcg_step_b<T>(g->dg, g->red, ps, (const T*)X, ldx, P, AP, b, b, th, 64, nullptr, s);
+      pcg_step_c<T>(g->dg, g->red, ps, (const T*)X, ldx, P, AP, (T*)Tout, RES, Z, b, b, th, 64, delta, nullptr, s);
+      pcg_step_d<T>(g->dg, ps, (const T*)X, ldx, Z, P, b, b, nullptr, s);
+    }
+  });
+  return check_cuda("lap_pcg_correction");
+}
+
+}  // extern "C"

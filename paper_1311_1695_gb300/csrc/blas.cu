@@ -1,0 +1,801 @@
+// Tall-skinny block kernels of the Jacobi-Davidson loop (Algorithm 2):
+//  * Gram products [1 | A]^T B          -- the V^T w column of H (step 4),
+//                                          the coefficients of Gram-Schmidt
+//                                          (step 2) and of the deflation (Eq. 5)
+//  * block updates Y = beta Y + [1|A] S  -- Gram-Schmidt subtraction, Ritz
+//                                          vectors u = V y (step 6), restart
+//  * column dots, scaling, residuals     -- norms and the stop test (step 7)
+//  * the projected preconditioned CG passes (step 8)
+//
+// Every kernel walks a tile of rows of one segment in chunks of 32 rows staged
+// in shared memory.  Per-tile partial sums are added into per-segment FP64
+// accumulators with atomics; the last tile of a segment to arrive reads the
+// totals, derives what the next pass needs, and zeroes the accumulators
+// (they are zero at rest).  FP32 data is summed in FP32 within a 32-row chunk
+// and in FP64 across chunks and tiles.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lapeig {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 32;
+
+__device__ __forceinline__ int seg_rows(const DevGraph& g, int s) { return g.row0[s + 1] - g.row0[s]; }
+__device__ __forceinline__ int seg_tiles(const DevGraph& g, int s) { return g.tile_ptr[s + 1] - g.tile_ptr[s]; }
+
+// Add this CTA's partials (acc64[u] for output o = tid + 256 u < nout, plus
+// `extra` values held by threads < nextra at offset nout) and report whether
+// this CTA is the segment's last arrival.
+template <int NO>
+__device__ bool commit(const Reduce& red, int seg, int ntiles_seg, const double (&acc)[NO], int nout,
+                       const double* extra, int nextra) {
+  double* a = red.acc + (size_t)seg * red.stride;
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int o = threadIdx.x + kThreads * u;
+    if (o < nout && acc[u] != 0.0) atomicAdd(a + o, acc[u]);
+  }
+  for (int e = threadIdx.x; e < nextra; e += kThreads)
+    if (extra[e] != 0.0) atomicAdd(a + nout + e, extra[e]);
+  __threadfence();
+  __syncthreads();
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_last = (atomicAdd(red.counter + seg, 1) == ntiles_seg - 1);
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+__device__ void release(const Reduce& red, int seg, int n) {
+  __syncthreads();
+  double* a = red.acc + (size_t)seg * red.stride;
+  for (int o = threadIdx.x; o < n; o += kThreads) a[o] = 0.0;
+  if (threadIdx.x == 0) red.counter[seg] = 0;
+}
+
+__device__ __forceinline__ double total(const Reduce& red, int seg, int o) {
+  return __ldcg(red.acc + (size_t)seg * red.stride + o);
+}
+
+// Stage rows [c0, c0+nr) x cols [0, w) of a row-major block into smem (row stride w).
+template <typename T>
+__device__ __forceinline__ void stage(T* dst, const T* __restrict__ src, int ld, int c0, int nr, int w) {
+  const int n = nr * w;
+  for (int e = threadIdx.x; e < n; e += kThreads) {
+    const int r = e / w, c = e - r * w;
+    dst[e] = src[(size_t)(c0 + r) * ld + c];
+  }
+}
+
+// acc[u] += sum_r [1|As][r, i] * Bs[r, j] for output o = i*q + j.
+template <typename T, int NO>
+__device__ __forceinline__ void gram_chunk(const T* As, int p, int ones, const T* Bs, int q, int nr,
+                                           double (&acc)[NO]) {
+  const int nout = (p + ones) * q;
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int o = threadIdx.x + kThreads * u;
+    if (o < nout) {
+      const int i = o / q, j = o - (o / q) * q;
+      T s = T(0);
+      if (i < ones) {
+        for (int r = 0; r < nr; ++r) s += Bs[r * q + j];
+      } else {
+        const T* a = As + (i - ones);
+        for (int r = 0; r < nr; ++r) s += a[r * p] * Bs[r * q + j];
+      }
+      acc[u] += (double)s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ Gram
+template <typename T, int NO>
+__global__ void __launch_bounds__(kThreads) k_gram(DevGraph g, Reduce red, const T* __restrict__ A, int lda,
+                                                   int p, const T* __restrict__ B, int ldb, int q, int ones,
+                                                   int ones_mean, double* __restrict__ G, int ldg, int64_t sg,
+                                                   const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  __shared__ T As[kChunk * kMaxCols];
+  __shared__ T Bs[kChunk * kMaxCols];
+  double acc[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) acc[u] = 0.0;
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    if (p > 0) stage(As, A, lda, c0, nr, p);
+    stage(Bs, B, ldb, c0, nr, q);
+    __syncthreads();
+    gram_chunk<T, NO>(As, p, ones, Bs, q, nr, acc);
+    __syncthreads();
+  }
+  const int nout = (p + ones) * q;
+  if (commit<NO>(red, t.seg, seg_tiles(g, t.seg), acc, nout, nullptr, 0)) {
+    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
+    for (int o = threadIdx.x; o < nout; o += kThreads) {
+      const int i = o / q, j = o - i * q;
+      double v = total(red, t.seg, o);
+      if (i < ones && ones_mean) v *= inv_n;
+      G[(size_t)t.seg * sg + (size_t)i * ldg + j] = v;
+    }
+    release(red, t.seg, nout);
+  }
+}
+
+// ------------------------------------------------------------------ update
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_update(DevGraph g, T* Y, int ldy, int q, double beta, double alpha,
+                                                     const T* A, int lda, int p, int ones,
+                                                     const double* __restrict__ S, int lds, int64_t ss,
+                                                     const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  constexpr int CH = 16;
+  __shared__ T Ss[(kMaxCols + 1) * kMaxCols];
+  __shared__ T As[CH * kMaxCols];
+  const int p1 = p + ones;
+  const double* Sg = S + (size_t)t.seg * ss;
+  for (int e = threadIdx.x; e < p1 * q; e += kThreads) {
+    const int i = e / q, j = e - i * q;
+    Ss[e] = (T)(alpha * Sg[(size_t)i * lds + j]);
+  }
+  const T tb = (T)beta;
+  for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
+    const int nr = min(CH, t.r1 - c0);
+    __syncthreads();
+    if (p > 0) stage(As, A, lda, c0, nr, p);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * q; e += kThreads) {
+      const int r = e / q, c = e - r * q;
+      T s = ones ? Ss[c] : T(0);
+      const T* a = As + r * p;
+      for (int i = 0; i < p; ++i) s += a[i] * Ss[(i + ones) * q + c];
+      T* y = Y + (size_t)(c0 + r) * ldy + c;
+      *y = (beta == 0.0) ? s : tb * (*y) + s;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dots / scale / residual
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_coldots(DevGraph g, Reduce red, const T* __restrict__ A, int lda,
+                                                      const T* __restrict__ B, int ldb, int q, double* out,
+                                                      int64_t so, const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc[2] = {0.0, 0.0};
+  for (int r = t.r0 + warp; r < t.r1; r += kThreads / 32) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      if (c < q) acc[h] += (double)(A[(size_t)r * lda + c] * B[(size_t)r * ldb + c]);
+    }
+  }
+  __shared__ double red_s[kThreads / 32][kMaxCols];
+  red_s[warp][lane] = acc[0];
+  red_s[warp][lane + 32] = acc[1];
+  __syncthreads();
+  __shared__ double colsum[kMaxCols];
+  if (threadIdx.x < kMaxCols) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red_s[w][threadIdx.x];
+    colsum[threadIdx.x] = s;
+  }
+  __syncthreads();
+  double none[1] = {0.0};
+  if (commit<1>(red, t.seg, seg_tiles(g, t.seg), none, 0, colsum, q)) {
+    for (int c = threadIdx.x; c < q; c += kThreads) out[(size_t)t.seg * so + c] = total(red, t.seg, c);
+    release(red, t.seg, q);
+  }
+}
+
+template <typename T>
+__global__ void k_colscale(DevGraph g, T* X, int ldx, int q, const double* __restrict__ scale, int64_t ss,
+                           const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = t.r0 + warp; r < t.r1; r += kThreads / 32)
+    for (int c = lane; c < q; c += 32) X[(size_t)r * ldx + c] *= (T)scale[(size_t)t.seg * ss + c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_residual(DevGraph g, Reduce red, const T* __restrict__ X, int ldx,
+                                                       const T* __restrict__ LX, int ldlx,
+                                                       const double* __restrict__ theta, int64_t sth, T* R, int ldr,
+                                                       int q, double* norms2, int64_t so,
+                                                       const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc[2] = {0.0, 0.0};
+  T th[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = lane + 32 * h;
+    th[h] = c < q ? (T)theta[(size_t)t.seg * sth + c] : T(0);
+  }
+  for (int r = t.r0 + warp; r < t.r1; r += kThreads / 32) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      if (c < q) {
+        const T v = LX[(size_t)r * ldlx + c] - th[h] * X[(size_t)r * ldx + c];
+        if (R) R[(size_t)r * ldr + c] = v;
+        acc[h] += (double)v * (double)v;
+      }
+    }
+  }
+  __shared__ double red_s[kThreads / 32][kMaxCols];
+  red_s[warp][lane] = acc[0];
+  red_s[warp][lane + 32] = acc[1];
+  __syncthreads();
+  __shared__ double colsum[kMaxCols];
+  if (threadIdx.x < kMaxCols) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red_s[w][threadIdx.x];
+    colsum[threadIdx.x] = s;
+  }
+  __syncthreads();
+  double none[1] = {0.0};
+  if (commit<1>(red, t.seg, seg_tiles(g, t.seg), none, 0, colsum, q)) {
+    for (int c = threadIdx.x; c < q; c += kThreads) norms2[(size_t)t.seg * so + c] = total(red, t.seg, c);
+    release(red, t.seg, q);
+  }
+}
+
+// ------------------------------------------------------------------ random start, convert
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_random(DevGraph g, T* X, int ldx, int b, uint64_t seed) {
+  const Tile t = g.tiles[blockIdx.x];
+  const int base = g.row0[t.seg];
+  for (int e = threadIdx.x; e < (t.r1 - t.r0) * b; e += kThreads) {
+    const int r = t.r0 + e / b, c = e % b;
+    const uint64_t z = splitmix64(seed, (uint64_t)(r - base) * (uint64_t)b + (uint64_t)c);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    X[(size_t)r * ldx + c] = (T)(2.0 * u - 1.0);
+  }
+}
+
+template <typename TX, typename TY>
+__global__ void k_convert(DevGraph g, const TX* __restrict__ X, int ldx, TY* __restrict__ Y, int ldy, int q) {
+  const Tile t = g.tiles[blockIdx.x];
+  for (int e = threadIdx.x; e < (t.r1 - t.r0) * q; e += kThreads) {
+    const int r = t.r0 + e / q, c = e % q;
+    Y[(size_t)r * ldy + c] = (TY)X[(size_t)r * ldx + c];
+  }
+}
+
+// ------------------------------------------------------------------ small per-segment kernels
+__global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, double drop, int absolute,
+                           double* Rinv, int64_t sr, int* keep, const int* __restrict__ seg_skip) {
+  const int seg = blockIdx.x;
+  if (seg_skip && seg_skip[seg]) return;
+  __shared__ double S[kMaxCols][kMaxCols + 1];
+  __shared__ double d0[kMaxCols];
+  __shared__ int kp[kMaxCols];
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) S[e / q][e % q] = Sg[(size_t)seg * ss + e];
+  __syncthreads();
+  if (threadIdx.x < q) d0[threadIdx.x] = absolute ? 1.0 : S[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    __shared__ double rjj;
+    if (threadIdx.x == 0) {
+      const double piv = S[j][j];
+      const bool ok = d0[j] > 0.0 && piv > drop * d0[j] && isfinite(piv);
+      kp[j] = ok ? 1 : 0;
+      rjj = ok ? sqrt(piv) : 0.0;
+    }
+    __syncthreads();
+    const bool ok = kp[j] != 0;
+    for (int i = j + threadIdx.x; i < q; i += blockDim.x) S[j][i] = ok ? (i == j ? rjj : S[j][i] / rjj) : 0.0;
+    __syncthreads();
+    if (ok) {
+      const int m = q - j - 1;
+      for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = j + 1 + e / m, l = j + 1 + e % m;
+        if (l >= i) S[i][l] -= S[j][i] * S[j][l];
+      }
+    }
+    __syncthreads();
+  }
+  // Rinv column c by back substitution (thread c)
+  double* Ro = Rinv + (size_t)seg * sr;
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) Ro[e] = 0.0;
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < q && kp[c]) {
+    double x[kMaxCols];
+    for (int i = c; i >= 0; --i) {
+      if (!kp[i]) { x[i] = 0.0; continue; }
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= c; ++l) s -= S[i][l] * x[l];
+      x[i] = s / S[i][i];
+    }
+    for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = x[i];
+  }
+  if (c < q && keep) keep[(size_t)seg * q + c] = kp[c];
+}
+
+// Parallel cyclic Jacobi (round-robin ordering: m/2 disjoint rotations per step).
+__global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
+                                               double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
+                                               const int* __restrict__ seg_skip, int* sweeps_out) {
+  const int seg = blockIdx.x;
+  if (seg_skip && seg_skip[seg]) return;
+  extern __shared__ double sm[];
+  const int mm = (m + 1) & ~1;  // even
+  const int LD = mm + 1;
+  double* A = sm;               // mm x LD
+  double* V = A + mm * LD;      // mm x LD
+  double* cs = V + mm * LD;     // [mm/2][2]
+  int* pq = reinterpret_cast<int*>(cs + mm);  // [mm/2][2]
+  __shared__ double s_off, s_nrm;
+  const double* H = Hg + (size_t)seg * sh;
+  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+    const int i = e / mm, j = e % mm;
+    A[i * LD + j] = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
+    V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  int sweep = 0;
+  const int half = mm / 2;
+  for (sweep = 0; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) { s_off = 0.0; s_nrm = 0.0; }
+    __syncthreads();
+    double off = 0.0, nrm = 0.0;
+    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+      const int i = e / mm, j = e % mm;
+      const double a = A[i * LD + j];
+      if (i != j) off += a * a; else nrm += a * a;
+    }
+    off = warp_sum(off);
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) { atomicAdd(&s_off, off); atomicAdd(&s_nrm, nrm); }
+    __syncthreads();
+    if (!(s_off > 1e-32 * (s_nrm + s_off))) break;
+    for (int step = 0; step < mm - 1; ++step) {
+      if (threadIdx.x < half) {
+        const int i = threadIdx.x;
+        auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
+        int p = at(i), q = at(mm - 1 - i);
+        if (p > q) { const int tmp = p; p = q; q = tmp; }
+        const double apq = A[p * LD + q];
+        double c = 1.0, s = 0.0;
+        const double app = A[p * LD + p], aqq = A[q * LD + q];
+        if (apq != 0.0 && fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+        }
+        cs[2 * i] = c; cs[2 * i + 1] = s;
+        pq[2 * i] = p; pq[2 * i + 1] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {
+        const int i = e / mm, j = e % mm;
+        const double s = cs[2 * i + 1];
+        if (s == 0.0) continue;
+        const double c = cs[2 * i];
+        const int p = pq[2 * i], q = pq[2 * i + 1];
+        const double ap = A[p * LD + j], aq = A[q * LD + j];
+        A[p * LD + j] = c * ap - s * aq;
+        A[q * LD + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {
+        const int i = e / mm, j = e % mm;
+        const double s = cs[2 * i + 1];
+        if (s == 0.0) continue;
+        const double c = cs[2 * i];
+        const int p = pq[2 * i], q = pq[2 * i + 1];
+        const double ap = A[j * LD + p], aq = A[j * LD + q];
+        A[j * LD + p] = c * ap - s * aq;
+        A[j * LD + q] = s * ap + c * aq;
+        const double vp = V[j * LD + p], vq = V[j * LD + q];
+        V[j * LD + p] = c * vp - s * vq;
+        V[j * LD + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort the m real eigenvalues ascending (rank by counting; ties by index)
+  double* ev = evals + (size_t)seg * se;
+  double* Y = Yg + (size_t)seg * sy;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double di = A[i * LD + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const double dj = A[j * LD + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    ev[rank] = di;
+    for (int r = 0; r < m; ++r) Y[(size_t)r * ldy + rank] = V[r * LD + i];
+  }
+  if (sweeps_out && threadIdx.x == 0) sweeps_out[seg] = sweep;
+}
+
+// ------------------------------------------------------------------ projected PCG passes
+// Elementwise phases map lane -> column (b <= 32) and warp -> row in the chunk.
+
+template <typename T>
+__device__ __forceinline__ void reduce_cols(double v, double* out /*smem [32]*/, double (&scratch)[kThreads / 32][32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  scratch[warp][lane] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s += scratch[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// init: RES = -R (active columns), T = 0, z~ = RES / d; G2 = [1|X]^T z~,
+// rho = RES . z~, res0 = ||RES||.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_init(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
+                                                       int ldx, const T* __restrict__ R, int ldr, T* Tt, T* RES, T* Z,
+                                                       int ld, int b, const int* __restrict__ active,
+                                                       const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  const T* deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
+  __shared__ T Xs[kChunk * 32];
+  __shared__ T Zs[kChunk * 32];
+  __shared__ double scratch[kThreads / 32][32];
+  __shared__ double extra[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool act = lane < b && (active == nullptr || active[(size_t)t.seg * st.bstride + lane]);
+  double rz = 0.0, rr = 0.0;
+  double acc[5];
+#pragma unroll
+  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    stage(Xs, X, ldx, c0, nr, b);
+    for (int r = warp; r < nr; r += kThreads / 32) {
+      if (lane < b) {
+        const size_t o = (size_t)(c0 + r) * ld + lane;
+        const T res = act ? -R[(size_t)(c0 + r) * ldr + lane] : T(0);
+        const T z = res / deg[c0 + r];
+        RES[o] = res;
+        Tt[o] = T(0);
+        Z[o] = z;
+        Zs[r * b + lane] = z;
+        rz += (double)res * (double)z;
+        rr += (double)res * (double)res;
+      }
+    }
+    __syncthreads();
+    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    __syncthreads();
+  }
+  reduce_cols<T>(rz, extra, scratch);
+  reduce_cols<T>(rr, extra + 32, scratch);
+  // pack the extras into [0, b) and [b, 2b)
+  __shared__ double ex2[64];
+  if (threadIdx.x < b) { ex2[threadIdx.x] = extra[threadIdx.x]; ex2[b + threadIdx.x] = extra[32 + threadIdx.x]; }
+  __syncthreads();
+  const int nout = (b + 1) * b;
+  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, ex2, 2 * b)) {
+    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
+    double* G2 = st.G2 + (size_t)t.seg * st.gstride;
+    for (int o = threadIdx.x; o < nout; o += kThreads) G2[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
+    if (threadIdx.x < b) {
+      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
+      const double rho = total(red, t.seg, nout + threadIdx.x);
+      const double r0 = sqrt(total(red, t.seg, nout + b + threadIdx.x));
+      st.rho[k] = rho;
+      st.res0[k] = r0;
+      st.resn[k] = r0;
+      st.beta[k] = 0.0;
+      st.alpha[k] = 0.0;
+      st.done[k] = (r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
+    }
+    release(red, t.seg, nout + 2 * b);
+  }
+}
+
+// pass B: q~ = AP - theta P;  G1 = [1|X]^T q~,  pq = P . q~;  alpha = rho / pq.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_b(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
+                                                    int ldx, const T* __restrict__ P, const T* __restrict__ AP, int ld,
+                                                    int b, const double* __restrict__ theta, int64_t sth,
+                                                    const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  __shared__ T Xs[kChunk * 32];
+  __shared__ T Zs[kChunk * 32];
+  __shared__ double scratch[kThreads / 32][32];
+  __shared__ double extra[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T th = lane < b ? (T)theta[(size_t)t.seg * sth + lane] : T(0);
+  double pq = 0.0;
+  double acc[5];
+#pragma unroll
+  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    stage(Xs, X, ldx, c0, nr, b);
+    for (int r = warp; r < nr; r += kThreads / 32) {
+      if (lane < b) {
+        const size_t o = (size_t)(c0 + r) * ld + lane;
+        const T p = P[o];
+        const T q = AP[o] - th * p;
+        Zs[r * b + lane] = q;
+        pq += (double)p * (double)q;
+      }
+    }
+    __syncthreads();
+    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    __syncthreads();
+  }
+  reduce_cols<T>(pq, extra, scratch);
+  const int nout = (b + 1) * b;
+  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, extra, b)) {
+    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
+    double* G1 = st.G1 + (size_t)t.seg * st.gstride;
+    for (int o = threadIdx.x; o < nout; o += kThreads) G1[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
+    if (threadIdx.x < b) {
+      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
+      const double v = total(red, t.seg, nout + threadIdx.x);
+      double a = 0.0;
+      if (!st.done[k]) {
+        if (v != 0.0 && isfinite(v)) a = st.rho[k] / v;
+        else st.done[k] = 1;
+      }
+      st.alpha[k] = a;
+    }
+    release(red, t.seg, nout + b);
+  }
+}
+
+// pass C: q = q~ - [1|X] G1; T += alpha P; RES -= alpha q; z~ = RES / d;
+//         G2 = [1|X]^T z~, rho' = RES . z~, ||RES||^2; beta = rho'/rho.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_c(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
+                                                    int ldx, const T* __restrict__ P, const T* __restrict__ AP, T* Tt,
+                                                    T* RES, T* Z, int ld, int b, const double* __restrict__ theta,
+                                                    int64_t sth, double delta, const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  const T* deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
+  __shared__ T Xs[kChunk * 32];
+  __shared__ T Zs[kChunk * 32];
+  __shared__ T Gs[33 * 32];
+  __shared__ double scratch[kThreads / 32][32];
+  __shared__ double extra[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nout = (b + 1) * b;
+  const double* G1 = st.G1 + (size_t)t.seg * st.gstride;
+  for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)G1[e];
+  const size_t kk = (size_t)t.seg * st.bstride + lane;
+  const T th = lane < b ? (T)theta[(size_t)t.seg * sth + lane] : T(0);
+  const T al = lane < b ? (T)st.alpha[kk] : T(0);
+  double rz = 0.0, rr = 0.0;
+  double acc[5];
+#pragma unroll
+  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    stage(Xs, X, ldx, c0, nr, b);
+    __syncthreads();
+    for (int r = warp; r < nr; r += kThreads / 32) {
+      if (lane < b) {
+        const size_t o = (size_t)(c0 + r) * ld + lane;
+        const T p = P[o];
+        T q = AP[o] - th * p - Gs[lane];
+        const T* xr = Xs + r * b;
+        for (int i = 0; i < b; ++i) q -= xr[i] * Gs[(i + 1) * b + lane];
+        Tt[o] += al * p;
+        const T res = RES[o] - al * q;
+        RES[o] = res;
+        const T z = res / deg[c0 + r];
+        Z[o] = z;
+        Zs[r * b + lane] = z;
+        rz += (double)res * (double)z;
+        rr += (double)res * (double)res;
+      }
+    }
+    __syncthreads();
+    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    __syncthreads();
+  }
+  reduce_cols<T>(rz, extra, scratch);
+  reduce_cols<T>(rr, extra + 32, scratch);
+  __shared__ double ex2[64];
+  if (threadIdx.x < b) { ex2[threadIdx.x] = extra[threadIdx.x]; ex2[b + threadIdx.x] = extra[32 + threadIdx.x]; }
+  __syncthreads();
+  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, ex2, 2 * b)) {
+    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
+    double* G2 = st.G2 + (size_t)t.seg * st.gstride;
+    for (int o = threadIdx.x; o < nout; o += kThreads) G2[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
+    if (threadIdx.x < b) {
+      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
+      const double rho_new = total(red, t.seg, nout + threadIdx.x);
+      const double rn = sqrt(total(red, t.seg, nout + b + threadIdx.x));
+      st.resn[k] = rn;
+      double be = 0.0;
+      if (!st.done[k]) {
+        if (st.rho[k] != 0.0 && isfinite(rho_new)) be = rho_new / st.rho[k];
+        if (!(rn > delta * st.res0[k]) || !isfinite(rn)) st.done[k] = 1;
+      }
+      st.rho[k] = rho_new;
+      st.beta[k] = be;
+    }
+    release(red, t.seg, nout + 2 * b);
+  }
+}
+
+// pass D: P = (z~ - [1|X] G2) + beta P.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pcg_d(DevGraph g, PcgState st, const T* __restrict__ X, int ldx,
+                                                    const T* __restrict__ Z, T* P, int ld, int b,
+                                                    const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  __shared__ T Xs[kChunk * 32];
+  __shared__ T Gs[33 * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nout = (b + 1) * b;
+  const double* G2 = st.G2 + (size_t)t.seg * st.gstride;
+  for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)G2[e];
+  const size_t kk = (size_t)t.seg * st.bstride + lane;
+  const T be = lane < b ? (T)st.beta[kk] : T(0);
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    __syncthreads();
+    stage(Xs, X, ldx, c0, nr, b);
+    __syncthreads();
+    for (int r = warp; r < nr; r += kThreads / 32) {
+      if (lane < b) {
+        const size_t o = (size_t)(c0 + r) * ld + lane;
+        T z = Z[o] - Gs[lane];
+        const T* xr = Xs + r * b;
+        for (int i = 0; i < b; ++i) z -= xr[i] * Gs[(i + 1) * b + lane];
+        P[o] = (be == T(0)) ? z : z + be * P[o];
+      }
+    }
+  }
+}
+
+template <typename T, int NO>
+void launch_gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, const T* B, int ldb, int q,
+                 int ones, int ones_mean, double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s) {
+  k_gram<T, NO><<<g.ntiles, kThreads, 0, s>>>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host launchers
+template <typename T>
+void gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, const T* B, int ldb, int q, int ones,
+          int ones_mean, double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s) {
+  const int nout = (p + ones) * q;
+  if (nout <= kThreads) launch_gram<T, 1>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
+  else if (nout <= 4 * kThreads) launch_gram<T, 4>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
+  else if (nout <= 8 * kThreads) launch_gram<T, 8>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
+  else launch_gram<T, 17>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
+}
+
+template <typename T>
+void update(const DevGraph& g, T* Y, int ldy, int q, double beta, double alpha, const T* A, int lda, int p, int ones,
+            const double* S, int lds, int64_t ss, const int* seg_skip, cudaStream_t s) {
+  k_update<T><<<g.ntiles, kThreads, 0, s>>>(g, Y, ldy, q, beta, alpha, A, lda, p, ones, S, lds, ss, seg_skip);
+}
+
+template <typename T>
+void coldots(const DevGraph& g, const Reduce& red, const T* A, int lda, const T* B, int ldb, int q, double* out,
+             int64_t so, const int* seg_skip, cudaStream_t s) {
+  k_coldots<T><<<g.ntiles, kThreads, 0, s>>>(g, red, A, lda, B, ldb, q, out, so, seg_skip);
+}
+
+template <typename T>
+void colscale(const DevGraph& g, T* X, int ldx, int q, const double* scale, int64_t ss, const int* seg_skip,
+              cudaStream_t s) {
+  k_colscale<T><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, q, scale, ss, seg_skip);
+}
+
+template <typename T>
+void random_block(const DevGraph& g, T* X, int ldx, int b, uint64_t seed, cudaStream_t s) {
+  k_random<T><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, b, seed);
+}
+
+template <typename TX, typename TY>
+void convert(const DevGraph& g, const TX* X, int ldx, TY* Y, int ldy, int q, cudaStream_t s) {
+  k_convert<TX, TY><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, Y, ldy, q);
+}
+
+template <typename T>
+void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T* LX, int ldlx, const double* theta,
+              int64_t sth, T* R, int ldr, int q, double* norms2, int64_t so, const int* seg_skip, cudaStream_t s) {
+  k_residual<T><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+}
+
+void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv, int64_t sr,
+              int* keep, const int* seg_skip, cudaStream_t s) {
+  k_chol_inv<<<nseg, 64, 0, s>>>(q, S, ss, drop, absolute, Rinv, sr, keep, seg_skip);
+}
+
+void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,
+          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s) {
+  const int mm = (m + 1) & ~1;
+  const size_t smem = sizeof(double) * (2 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
+    attr_set = true;
+  }
+  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out);
+}
+
+template <typename T>
+void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* R, int ldr,
+              T* Tt, T* RES, T* Z, T* P, int ld, int b, const int* active, const int* seg_skip, cudaStream_t s) {
+  k_pcg_init<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, R, ldr, Tt, RES, Z, ld, b, active, seg_skip);
+  k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
+}
+
+template <typename T>
+void pcg_step_b(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
+                const T* AP, int ld, int b, const double* theta, int64_t sth, const int* seg_skip, cudaStream_t s) {
+  k_pcg_b<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, ld, b, theta, sth, seg_skip);
+}
+
+template <typename T>
+void pcg_step_c(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
+                const T* AP, T* Tt, T* RES, T* Z, int ld, int b, const double* theta, int64_t sth, double delta,
+                const int* seg_skip, cudaStream_t s) {
+  k_pcg_c<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, Tt, RES, Z, ld, b, theta, sth, delta, seg_skip);
+}
+
+template <typename T>
+void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z, T* P, int ld, int b,
+                const int* seg_skip, cudaStream_t s) {
+  k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
+}
+
+#define LAPEIG_INST(T)                                                                                            \
+  template void gram<T>(const DevGraph&, const Reduce&, const T*, int, int, const T*, int, int, int, int, double*, \
+                        int, int64_t, const int*, cudaStream_t);                                                  \
+  template void update<T>(const DevGraph&, T*, int, int, double, double, const T*, int, int, int, const double*,  \
+                          int, int64_t, const int*, cudaStream_t);                                                \
+  template void coldots<T>(const DevGraph&, const Reduce&, const T*, int, const T*, int, int, double*, int64_t,    \
+                           const int*, cudaStream_t);                                                             \
+  template void colscale<T>(const DevGraph&, T*, int, int, const double*, int64_t, const int*, cudaStream_t);     \
+  template void random_block<T>(const DevGraph&, T*, int, int, uint64_t, cudaStream_t);                           \
+  template void residual<T>(const DevGraph&, const Reduce&, const T*, int, const T*, int, const double*, int64_t,  \
+                            T*, int, int, double*, int64_t, const int*, cudaStream_t);                            \
+  template void pcg_init<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, int, T*, T*, \
+                            T*, T*, int, int, const int*, const int*, cudaStream_t);                              \
+  template void pcg_step_b<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, const T*,  \
+                              int, int, const double*, int64_t, const int*, cudaStream_t);                        \
+  template void pcg_step_c<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, const T*,  \
+                              T*, T*, T*, int, int, const double*, int64_t, double, const int*, cudaStream_t);    \
+  template void pcg_step_d<T>(const DevGraph&, const PcgState&, const T*, int, T*, T*, int, int, const int*,      \
+                              cudaStream_t);
+
+LAPEIG_INST(float)
+LAPEIG_INST(double)
+template void convert<float, double>(const DevGraph&, const float*, int, double*, int, int, cudaStream_t);
+template void convert<double, float>(const DevGraph&, const double*, int, float*, int, int, cudaStream_t);
+template void convert<double, double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t);
+template void convert<float, float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t);
+
+}  // namespace lapeig

@@ -1,0 +1,239 @@
+// Graph set-up: validation of the input CSR (Section 2: simple, undirected,
+// positive weights), concatenation of a batch into one block-diagonal CSR,
+// generalised degrees, ||L||_1 per graph, row tiles, and the SpMM schedule
+// (lanes per row and the list of hub rows).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace lapeig {
+
+namespace {
+
+template <typename T>
+int dev_alloc_copy(T** dst, const T* src, size_t count) {
+  *dst = nullptr;
+  if (count == 0) return LAP_OK;
+  if (cudaMalloc(reinterpret_cast<void**>(dst), count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc failed in graph set-up");
+    return LAP_ENOMEM;
+  }
+  if (src && cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    set_error("cudaMemcpy failed in graph set-up");
+    return LAP_ECUDA;
+  }
+  return LAP_OK;
+}
+
+int validate(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w) {
+  if (n < 1 || !rowptr || (!colidx && rowptr[n] > 0)) {
+    set_error("n < 1 or NULL CSR array");
+    return LAP_EINVAL;
+  }
+  if (rowptr[0] != 0) { set_error("rowptr[0] != 0"); return LAP_EINVAL; }
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) { set_error("rowptr not monotone"); return LAP_EINVAL; }
+  const int64_t nnz = rowptr[n];
+  if (nnz >= (int64_t(1) << 31) || n >= (int64_t(1) << 31)) { set_error("graph too large for int32 indices"); return LAP_EINVAL; }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int64_t j = colidx[p];
+      if (j < 0 || j >= n) { set_error("column index out of range"); return LAP_EINVAL; }
+      if (j == i) { set_error("diagonal entry (self-loop) in adjacency"); return LAP_ESELFLOOP; }
+      if (p > rowptr[i] && colidx[p - 1] >= j) { set_error("column indices not strictly increasing"); return LAP_EUNSORTED; }
+      if (w && !(std::isfinite(w[p]) && w[p] > 0.0)) { set_error("weight not finite and positive"); return LAP_EWEIGHT; }
+    }
+  }
+  // symmetry: (i, j, w) needs (j, i, w)
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int64_t j = colidx[p];
+      const int32_t* b = colidx + rowptr[j];
+      const int32_t* e = colidx + rowptr[j + 1];
+      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
+      if (f == e || *f != i) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
+      if (w && w[rowptr[j] + (f - b)] != w[p]) { set_error("adjacency values not symmetric"); return LAP_ENOTSYM; }
+    }
+  }
+  return LAP_OK;
+}
+
+}  // namespace
+
+int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
+  if (team != 0) {
+    if (team != 4 && team != 8 && team != 16 && team != 32) { set_error("team must be 4, 8, 16 or 32"); return LAP_EINVAL; }
+    g->dg.team = team;
+  }
+  if (long_thresh > 0) g->dg.long_thresh = long_thresh;
+  // hub rows: degree above the threshold
+  std::vector<int> hubs;
+  const int n = g->hg.n;
+  for (int i = 0; i < n; ++i)
+    if (g->rowptr_h[i + 1] - g->rowptr_h[i] > g->dg.long_thresh) hubs.push_back(i);
+  // longest first so the heaviest CTAs start earliest
+  std::sort(hubs.begin(), hubs.end(), [&](int a, int b) {
+    const int da = g->rowptr_h[a + 1] - g->rowptr_h[a], db = g->rowptr_h[b + 1] - g->rowptr_h[b];
+    return da != db ? da > db : a < b;
+  });
+  if (g->d_long) cudaFree(g->d_long);
+  g->d_long = nullptr;
+  int rc = dev_alloc_copy(&g->d_long, hubs.data(), hubs.size());
+  if (rc) return rc;
+  g->long_rows_h = hubs;
+  g->dg.long_rows = g->d_long;
+  g->dg.nlong = (int)hubs.size();
+  return LAP_OK;
+}
+
+int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
+                const double* const* weights, lap_graph** out) {
+  *out = nullptr;
+  if (nb < 1 || !n || !rowptr || !colidx) { set_error("bad batch arguments"); return LAP_EINVAL; }
+  int64_t ntot = 0, nnztot = 0;
+  bool weighted = false;
+  for (int s = 0; s < nb; ++s) {
+    if (!rowptr[s]) { set_error("NULL rowptr"); return LAP_EINVAL; }
+    const int rc = validate(n[s], rowptr[s], colidx[s], weights ? weights[s] : nullptr);
+    if (rc) return rc;
+    ntot += n[s];
+    nnztot += rowptr[s][n[s]];
+    if (weights && weights[s]) weighted = true;
+  }
+  if (ntot >= (int64_t(1) << 31) || nnztot >= (int64_t(1) << 31)) { set_error("batch too large for int32 indices"); return LAP_EINVAL; }
+
+  lap_graph* g = new lap_graph();
+  g->hg.n = (int)ntot;
+  g->hg.nseg = nb;
+  g->hg.nnz = nnztot;
+  g->hg.weighted = weighted ? 1 : 0;
+
+  std::vector<int> colcat((size_t)nnztot);
+  std::vector<double> w64(weighted ? (size_t)nnztot : 0);
+  std::vector<double> deg((size_t)ntot);
+  g->rowptr_h.assign((size_t)ntot + 1, 0);
+  g->row0.assign(nb + 1, 0);
+  g->norm1.assign(nb, 0.0);
+  int64_t r = 0, p = 0;
+  int maxdeg = 0;
+  for (int s = 0; s < nb; ++s) {
+    g->row0[s] = (int)r;
+    const int64_t* rp = rowptr[s];
+    const double* ws = weights ? weights[s] : nullptr;
+    double dmax = 0.0;
+    for (int64_t i = 0; i < n[s]; ++i, ++r) {
+      double d = 0.0;
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q, ++p) {
+        colcat[p] = (int)(colidx[s][q] + g->row0[s]);
+        const double wv = ws ? ws[q] : 1.0;
+        if (weighted) w64[p] = wv;
+        d += wv;
+      }
+      g->rowptr_h[r + 1] = (int)p;
+      deg[r] = d;
+      dmax = std::max(dmax, d);
+      maxdeg = std::max(maxdeg, (int)(rp[i + 1] - rp[i]));
+    }
+    g->norm1[s] = 2.0 * dmax;
+  }
+  g->row0[nb] = (int)r;
+  g->avg_degree = ntot ? (double)nnztot / (double)ntot : 0.0;
+  g->max_degree = maxdeg;
+
+  // tiles: small enough that every SM holds several CTAs
+  std::vector<Tile> tiles;
+  g->tile_ptr.assign(nb + 1, 0);
+  for (int s = 0; s < nb; ++s) {
+    g->tile_ptr[s] = (int)tiles.size();
+    const int ns = g->row0[s + 1] - g->row0[s];
+    int rows = (ns + 4 * 152 - 1) / (4 * 152);
+    rows = (rows + 31) / 32 * 32;
+    rows = std::max(64, std::min(rows, 256));
+    int idx = 0;
+    for (int a = g->row0[s]; a < g->row0[s + 1]; a += rows) tiles.push_back(Tile{s, a, std::min(a + rows, g->row0[s + 1]), idx++});
+  }
+  g->tile_ptr[nb] = (int)tiles.size();
+  g->hg.ntiles = (int)tiles.size();
+
+  std::vector<float> w32(w64.begin(), w64.end());
+  std::vector<float> deg32(deg.begin(), deg.end());
+  int rc = LAP_OK;
+  rc = rc ? rc : dev_alloc_copy(&g->d_rowptr, g->rowptr_h.data(), g->rowptr_h.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_colidx, colcat.data(), colcat.size());
+  if (weighted) {
+    rc = rc ? rc : dev_alloc_copy(&g->d_w64, w64.data(), w64.size());
+    rc = rc ? rc : dev_alloc_copy(&g->d_w32, w32.data(), w32.size());
+  }
+  rc = rc ? rc : dev_alloc_copy(&g->d_deg64, deg.data(), deg.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_deg32, deg32.data(), deg32.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_row0, g->row0.data(), g->row0.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_tiles, tiles.data(), tiles.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_tile_ptr, g->tile_ptr.data(), g->tile_ptr.size());
+  // reduction scratch, zero at rest
+  g->red.stride = 4608;
+  rc = rc ? rc : dev_alloc_copy<double>(&g->red.acc, nullptr, (size_t)nb * g->red.stride);
+  rc = rc ? rc : dev_alloc_copy<int>(&g->red.counter, nullptr, (size_t)nb);
+  if (rc == LAP_OK) {
+    if (cudaMemset(g->red.acc, 0, sizeof(double) * (size_t)nb * g->red.stride) != cudaSuccess ||
+        cudaMemset(g->red.counter, 0, sizeof(int) * (size_t)nb) != cudaSuccess) {
+      set_error("cudaMemset failed");
+      rc = LAP_ECUDA;
+    }
+  }
+  if (rc) { graph_free(g); return rc; }
+
+  DevGraph& d = g->dg;
+  d.n = (int)ntot;
+  d.nseg = nb;
+  d.nnz = nnztot;
+  d.rowptr = g->d_rowptr;
+  d.colidx = g->d_colidx;
+  d.w32 = g->d_w32;
+  d.w64 = g->d_w64;
+  d.deg64 = g->d_deg64;
+  d.deg32 = g->d_deg32;
+  d.row0 = g->d_row0;
+  d.tiles = g->d_tiles;
+  d.ntiles = (int)tiles.size();
+  d.tile_ptr = g->d_tile_ptr;
+  d.counters = g->red.counter;
+  // schedule heuristic (overridden by the autotuner or the caller)
+  d.team = g->avg_degree <= 6.0 ? 4 : (g->avg_degree <= 24.0 ? 8 : (g->avg_degree <= 96.0 ? 16 : 32));
+  d.long_thresh = 32 * d.team;
+  rc = graph_set_schedule(g, 0, 0);
+  if (rc) { graph_free(g); return rc; }
+  *out = g;
+  return LAP_OK;
+}
+
+void graph_free(lap_graph* g) {
+  if (!g) return;
+  cudaFree(g->d_rowptr); cudaFree(g->d_colidx); cudaFree(g->d_w32); cudaFree(g->d_w64);
+  cudaFree(g->d_deg64); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
+  cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->red.acc); cudaFree(g->red.counter);
+  cudaFree(g->scratch); cudaFree(g->small);
+  delete g;
+}
+
+int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes) {
+  if (bytes > g->scratch_bytes) {
+    cudaFree(g->scratch);
+    g->scratch = nullptr;
+    g->scratch_bytes = 0;
+    if (cudaMalloc(&g->scratch, bytes) != cudaSuccess) { cudaGetLastError(); set_error("scratch allocation failed"); return LAP_ENOMEM; }
+    g->scratch_bytes = bytes;
+  }
+  if (small_bytes > g->small_bytes) {
+    cudaFree(g->small);
+    g->small = nullptr;
+    g->small_bytes = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(&g->small), small_bytes) != cudaSuccess) { cudaGetLastError(); set_error("scratch allocation failed"); return LAP_ENOMEM; }
+    g->small_bytes = small_bytes;
+  }
+  return LAP_OK;
+}
+
+}  // namespace lapeig

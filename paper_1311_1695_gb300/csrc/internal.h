@@ -1,0 +1,65 @@
+// Host-side internals shared by graph.cu, solver.cu and api.cu.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lapeig.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+struct lap_graph {
+  lapeig::DevGraph dg{};
+  lapeig::HostGraph hg{};
+  lapeig::Reduce red{};
+  // device allocations owned by the handle
+  int* d_rowptr = nullptr;
+  int* d_colidx = nullptr;
+  float* d_w32 = nullptr;
+  double* d_w64 = nullptr;
+  double* d_deg64 = nullptr;
+  float* d_deg32 = nullptr;
+  int* d_row0 = nullptr;
+  lapeig::Tile* d_tiles = nullptr;
+  int* d_tile_ptr = nullptr;
+  int* d_long = nullptr;
+  // host copies
+  std::vector<int> row0, tile_ptr;
+  std::vector<double> norm1;
+  std::vector<int> rowptr_h;   // int32 concatenated
+  std::vector<int> long_rows_h;
+  double avg_degree = 0.0;
+  int max_degree = 0;
+  // lazily grown scratch for the step-level entry points
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double* small = nullptr;      // FP64 per-segment scratch
+  size_t small_bytes = 0;
+};
+
+namespace lapeig {
+
+// Validate and upload a batch of host CSR graphs.  Returns LAP_* status.
+int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
+                const double* const* weights, lap_graph** out);
+void graph_free(lap_graph* g);
+int graph_set_schedule(lap_graph* g, int team, int long_thresh);
+// Ensure the handle's step-level scratch holds at least `bytes` (device).
+int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes);
+
+// Error string of the last failure on this thread.
+void set_error(const std::string& msg);
+
+struct SolveOut {
+  std::vector<std::vector<double>> evals;   // per segment [k]
+  std::vector<std::vector<double>> evecs;   // per segment [n_s * k] column-major (may stay empty)
+  std::vector<lap_info> info;               // per segment
+};
+
+// Block Jacobi-Davidson over all segments of the handle (lock-step).
+int solve_jd(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);
+// Single-graph DACG and IRLM on the device kernels.
+int solve_dacg(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);
+int solve_irlm(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);
+
+}  // namespace lapeig

@@ -1,0 +1,103 @@
+// Host-side launchers of the device kernels (internal, not part of the C ABI).
+#pragma once
+#include "common.cuh"
+
+namespace lapeig {
+
+// Scratch for cross-CTA reductions: per-segment FP64 accumulators and
+// arrival counters, zero at rest (every kernel that uses them leaves them
+// zero when it finishes).
+struct Reduce {
+  double* acc;      // [nseg * stride]
+  int* counter;     // [nseg]
+  int stride;       // doubles per segment (>= largest reduction)
+};
+
+// ---- K1: Y = L X (degree fused), b columns
+template <typename T>
+void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s);
+
+// ---- Gram: G[s] = [1 | A]^T B per segment (ones adds a leading row of column
+// sums, divided by the segment's row count when ones_mean is set).  G is
+// written with row stride ldg and segment stride sg (doubles).
+template <typename T>
+void gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, const T* B, int ldb, int q,
+          int ones, int ones_mean, double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s);
+
+// ---- Block update: Y[:, 0:q] = beta Y + alpha ([1 | A] S_s), S_s = S + s*ss,
+// (p + ones) x q with row stride lds.  In-place (Y aliasing A) is allowed.
+template <typename T>
+void update(const DevGraph& g, T* Y, int ldy, int q, double beta, double alpha, const T* A, int lda,
+            int p, int ones, const double* S, int lds, int64_t ss, const int* seg_skip, cudaStream_t s);
+
+// ---- Column dots: out[s*so + c] = sum_rows A[:, c] B[:, c], c < q
+template <typename T>
+void coldots(const DevGraph& g, const Reduce& red, const T* A, int lda, const T* B, int ldb, int q,
+             double* out, int64_t so, const int* seg_skip, cudaStream_t s);
+
+// ---- Column scaling: X[:, c] *= scale[s*ss + c]
+template <typename T>
+void colscale(const DevGraph& g, T* X, int ldx, int q, const double* scale, int64_t ss,
+              const int* seg_skip, cudaStream_t s);
+
+// ---- Random start block: uniform(-1, 1) from SplitMix64, counter (r - row0[s]) * b + c
+template <typename T>
+void random_block(const DevGraph& g, T* X, int ldx, int b, uint64_t seed, cudaStream_t s);
+
+// ---- Copy/convert a block: Y[:, 0:q] = (TY) X[:, 0:q]
+template <typename TX, typename TY>
+void convert(const DevGraph& g, const TX* X, int ldx, TY* Y, int ldy, int q, cudaStream_t s);
+
+// ---- Residual: R[:, c] = LX[:, c] - theta_c X[:, c]; norms2[s*so + c] = ||R[:, c]||^2
+template <typename T>
+void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T* LX, int ldlx,
+              const double* theta, int64_t sth, T* R, int ldr, int q, double* norms2, int64_t so,
+              const int* seg_skip, cudaStream_t s);
+
+// ---- Small per-segment kernels (one CTA per segment)
+// In-block orthonormalisation factor from S = T^T T (q x q): Cholesky with
+// dropping of columns whose pivot falls below drop * (initial diagonal), or
+// below drop itself when absolute is set; out
+// Rinv (q x q upper triangular, dropped columns zero) and keep[s*q + c].
+void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv,
+              int64_t sr, int* keep, const int* seg_skip, cudaStream_t s);
+
+// Symmetric eigensolver (parallel cyclic Jacobi), m <= 64, one CTA per
+// segment.  H (m x m, ld ldh, segment stride sh) is not modified.  evals
+// ascending; Y columns are the matching unit eigenvectors.
+void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se,
+          double* Y, int ldy, int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s);
+
+// ---- Projected preconditioned CG on (I - QQ^T)(L - theta_c I)(I - QQ^T) t_c = -r_c,
+// Q = [e/sqrt(n_s), X] per segment, preconditioner (I-QQ^T) D^{-1} (I-QQ^T).
+struct PcgState {
+  // per segment * bstride doubles
+  double* rho;
+  double* alpha;
+  double* beta;
+  double* res0;
+  double* resn;
+  double* G1;   // per segment (b+1) * b
+  double* G2;
+  int* done;    // per segment * bstride
+  int bstride;
+  int gstride;
+};
+
+template <typename T>
+void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* R,
+              int ldr, T* Tt, T* RES, T* Z, T* P, int ld, int b, const int* active, const int* seg_skip,
+              cudaStream_t s);
+template <typename T>
+void pcg_step_b(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
+                const T* AP, int ld, int b, const double* theta, int64_t sth, const int* seg_skip,
+                cudaStream_t s);
+template <typename T>
+void pcg_step_c(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
+                const T* AP, T* Tt, T* RES, T* Z, int ld, int b, const double* theta, int64_t sth,
+                double delta, const int* seg_skip, cudaStream_t s);
+template <typename T>
+void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z, T* P, int ld, int b,
+                const int* seg_skip, cudaStream_t s);
+
+}  // namespace lapeig

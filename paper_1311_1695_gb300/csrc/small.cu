@@ -1,0 +1,124 @@
+// Small per-segment kernels of the Jacobi-Davidson driver: H bookkeeping
+// (restart to diag(theta), new border rows/columns), column scalings, the
+// output sign convention and the column-major copy-out.
+#include "common.cuh"
+#include "small.cuh"
+
+namespace lapeig {
+
+namespace {
+
+// out[i] = x > floor ? 1/sqrt(x) : 0
+__global__ void k_inv_sqrt(int count, const double* in, double* out, double floor_v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    const double x = in[i];
+    out[i] = (x > floor_v && isfinite(x)) ? 1.0 / sqrt(x) : 0.0;
+  }
+}
+
+// H <- diag(theta[0:mk]) (the restarted projected matrix), zeros elsewhere.
+__global__ void k_h_restart(double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
+                            const int* seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* h = H + (size_t)s * sh;
+  for (int e = threadIdx.x; e < mmax * mmax; e += blockDim.x) {
+    const int i = e / mmax, j = e % mmax;
+    h[(size_t)i * ldh + j] = (i == j && i < mk) ? theta[(size_t)s * st + i] : 0.0;
+  }
+}
+
+// New border of H (Algorithm 2 step 4) from G = V[:, 0:mk+b]^T (L T):
+//   H[i, mk+j] = H[mk+j, i] = G[i, j]           i < mk
+//   H[mk+i, mk+j] = (G[mk+i, j] + G[mk+j, i]) / 2
+// Columns dropped by the orthogonalisation (keep = 0) get an isolated
+// diagonal entry `big`, so their Ritz values sort last and never enter the
+// Ritz block.
+__global__ void k_h_border(double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
+                           const int* keep, int64_t sk, double big, const int* seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* h = H + (size_t)s * sh;
+  const double* gs = G + (size_t)s * sg;
+  const int* kp = keep + (size_t)s * sk;
+  for (int e = threadIdx.x; e < (mk + b) * b; e += blockDim.x) {
+    const int i = e / b, j = e % b;
+    const bool kj = kp[j] != 0;
+    if (i < mk) {
+      const double v = kj ? gs[(size_t)i * ldg + j] : 0.0;
+      h[(size_t)i * ldh + mk + j] = v;
+      h[(size_t)(mk + j) * ldh + i] = v;
+    } else {
+      const int i2 = i - mk;
+      double v;
+      if (!kj || !kp[i2]) v = (i2 == j && !kj) ? big : 0.0;
+      else v = 0.5 * (gs[(size_t)i * ldg + j] + gs[(size_t)(mk + j) * ldg + i2]);
+      h[(size_t)i * ldh + mk + j] = v;
+    }
+  }
+}
+
+// keep = keep1 & keep2
+__global__ void k_and(int count, int* a, const int* b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) a[i] = (a[i] != 0 && b[i] != 0) ? 1 : 0;
+}
+
+// Sign convention: per segment and column, find the entry of largest
+// magnitude (ties -> lowest row) with one packed atomicMax, then flip.
+template <typename T>
+__global__ void k_argmax(const Tile* tiles, const T* X, int ldx, int k, const int* row0,
+                         unsigned long long* best) {
+  const Tile t = tiles[blockIdx.x];
+  for (int e = threadIdx.x; e < (t.r1 - t.r0) * k; e += blockDim.x) {
+    const int r = t.r0 + e / k, c = e % k;
+    const float a = fabsf((float)X[(size_t)r * ldx + c]);
+    const unsigned long long key =
+        ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)(r - row0[t.seg]));
+    atomicMax(best + (size_t)t.seg * k + c, key);
+  }
+}
+
+// out (column-major per segment, double) = sign_c * X[:, c]; seg s starts at row0[s] * k.
+template <typename T>
+__global__ void k_copy_out(const Tile* tiles, const T* X, int ldx, int k, const int* row0,
+                           const unsigned long long* best, double* out) {
+  const Tile t = tiles[blockIdx.x];
+  const int base = row0[t.seg];
+  const int ns = row0[t.seg + 1] - base;
+  for (int e = threadIdx.x; e < (t.r1 - t.r0) * k; e += blockDim.x) {
+    const int r = t.r0 + e / k, c = e % k;
+    const unsigned long long key = best[(size_t)t.seg * k + c];
+    const int rbest = base + (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+    const double sgn = (double)X[(size_t)rbest * ldx + c] < 0.0 ? -1.0 : 1.0;
+    out[(size_t)base * k + (size_t)c * ns + (r - base)] = sgn * (double)X[(size_t)r * ldx + c];
+  }
+}
+
+}  // namespace
+
+void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s) {
+  k_inv_sqrt<<<(count + 255) / 256, 256, 0, s>>>(count, in, out, floor_v);
+}
+void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
+               const int* seg_skip, cudaStream_t s) {
+  k_h_restart<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, theta, st, mk, seg_skip);
+}
+void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
+              const int* keep, int64_t sk, double big, const int* seg_skip, cudaStream_t s) {
+  k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, big, seg_skip);
+}
+void and_flags(int count, int* a, const int* b, cudaStream_t s) {
+  k_and<<<(count + 255) / 256, 256, 0, s>>>(count, a, b);
+}
+template <typename T>
+void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s) {
+  cudaMemsetAsync(best, 0, sizeof(unsigned long long) * (size_t)g.nseg * k, s);
+  k_argmax<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, g.row0, best);
+  k_copy_out<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, g.row0, best, out);
+}
+template void copy_out<float>(const DevGraph&, const float*, int, int, unsigned long long*, double*, cudaStream_t);
+template void copy_out<double>(const DevGraph&, const double*, int, int, unsigned long long*, double*, cudaStream_t);
+
+}  // namespace lapeig

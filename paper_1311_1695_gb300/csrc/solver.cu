@@ -1,0 +1,474 @@
+// Block Jacobi-Davidson for the k smallest eigenpairs of L on the complement
+// of e, on the device (Algorithm 2 of the paper, run on a block of b Ritz
+// vectors at once, with deflation Eq. 5 and the projected Jacobi-
+// preconditioned correction of Section 3.2.1).
+//
+// Outer iteration (all graphs of the handle in lock-step):
+//   1. Rayleigh-Ritz: eig(H) for H = V^T L V (m x m, FP64, one CTA/graph)
+//   2. restart: V <- V Y[:, 0:mk], W <- W Y[:, 0:mk], H <- diag(theta)
+//      (thick restart every iteration: the mk smallest Ritz vectors stay;
+//      the first b of them are the Ritz block X, W[:, 0:b] = L X)
+//   3. residuals R = L X - X diag(theta); stop when every wanted column has
+//      ||r_j|| <= tol ||L||_1 (checked on an explicit L X before stopping)
+//   4. correction: projected PCG (<= ITMAX steps, relative drop delta_PCG)
+//      for every unconverged column, Q = [e/sqrt(n), X]
+//   5. expansion: corrections orthonormalised against [e, V] (CGS2 with
+//      Cholesky-QR), W_new = L T, new border of H.
+// Converged columns are not corrected any more (soft locking); they stay in
+// the basis and in the deflation space Q, which is Eq. 5's
+// Q = [v_1 .. v_{j-1}, u].
+//
+// Mixed precision: phase 1 runs with FP32 basis and FP32 correction solves to
+// a residual of max(tol, tol32) ||L||_1; phase 2 continues from the FP32
+// Ritz vectors with an FP64 basis, FP64 Gram/Rayleigh-Ritz/residuals and FP32
+// correction solves ("refinement sweeps") down to tol.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+#include "small.cuh"
+
+namespace lapeig {
+
+namespace {
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Bump allocator over one device allocation.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  int init(size_t bytes) {
+    if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device workspace allocation failed");
+      return LAP_ENOMEM;
+    }
+    size = bytes;
+    return LAP_OK;
+  }
+  template <typename T>
+  T* take(size_t count) {
+    used = (used + 255) / 256 * 256;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += count * sizeof(T);
+    return p;
+  }
+  ~Arena() { cudaFree(base); }
+};
+
+struct Sizes {
+  int n, nseg, k, b, mk, mmax, ldv, ldb;
+};
+
+template <typename TV, typename TP>
+struct JD {
+  lap_graph* G;
+  const DevGraph& g;
+  const Reduce& red;
+  Sizes z;
+  cudaStream_t st;
+  // blocks
+  TV* V;
+  TV* W;
+  TV* Rv;      // residual block in basis precision (n x ldb)
+  TP* Xp;      // Ritz block copy for the PCG (when TP != TV)
+  TP* Rp;
+  TP* Tt;
+  TP* RES;
+  TP* Zb;
+  TP* P;
+  TP* AP;
+  // small FP64 per segment
+  double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
+  int *keep1, *keep2, *active, *seg_skip, *sweeps;
+  PcgState ps;
+  // host mirrors
+  std::vector<double> rn2_h, theta_h;
+  std::vector<int> active_h, skip_h;
+  int64_t n_matvec = 0;
+  int inner_its = 0;
+
+  JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
+
+  static size_t bytes(const Sizes& z) {
+    const size_t n = z.n, S = z.nseg;
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+    add(2 * n * z.ldv * sizeof(TV));
+    add(n * z.ldb * sizeof(TV));
+    for (int i = 0; i < 7; ++i) add(n * z.ldb * sizeof(TP));
+    const size_t mm = (size_t)z.mmax * z.mmax;
+    add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
+    add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
+    for (int i = 0; i < 5; ++i) add(S * 64 * 4);
+    for (int i = 0; i < 5; ++i) add(S * 64 * 8);
+    add(S * 33 * 32 * 8); add(S * 33 * 32 * 8); add(S * 64 * 4);
+    return b + 4096;
+  }
+
+  void carve(Arena& a) {
+    const size_t n = z.n, S = z.nseg;
+    V = a.take<TV>(n * z.ldv);
+    W = a.take<TV>(n * z.ldv);
+    Rv = a.take<TV>(n * z.ldb);
+    Xp = a.take<TP>(n * z.ldb);
+    Rp = a.take<TP>(n * z.ldb);
+    Tt = a.take<TP>(n * z.ldb);
+    RES = a.take<TP>(n * z.ldb);
+    Zb = a.take<TP>(n * z.ldb);
+    P = a.take<TP>(n * z.ldb);
+    AP = a.take<TP>(n * z.ldb);
+    const size_t mm = (size_t)z.mmax * z.mmax;
+    H = a.take<double>(S * mm);
+    Y = a.take<double>(S * mm);
+    theta = a.take<double>(S * z.mmax);
+    rn2 = a.take<double>(S * 64);
+    Gm = a.take<double>(S * 65 * 64);
+    Sm = a.take<double>(S * 64 * 64);
+    Rinv = a.take<double>(S * 64 * 64);
+    scale = a.take<double>(S * 64);
+    tmp = a.take<double>(S * 64);
+    keep1 = a.take<int>(S * 64);
+    keep2 = a.take<int>(S * 64);
+    active = a.take<int>(S * 64);
+    seg_skip = a.take<int>(S * 64);
+    sweeps = a.take<int>(S * 64);
+    ps.rho = a.take<double>(S * 64);
+    ps.alpha = a.take<double>(S * 64);
+    ps.beta = a.take<double>(S * 64);
+    ps.res0 = a.take<double>(S * 64);
+    ps.resn = a.take<double>(S * 64);
+    ps.G1 = a.take<double>(S * 33 * 32);
+    ps.G2 = a.take<double>(S * 33 * 32);
+    ps.done = a.take<int>(S * 64);
+    ps.bstride = 64;
+    ps.gstride = 33 * 32;
+    rn2_h.assign(S * 64, 0.0);
+    theta_h.assign(S * z.mmax, 0.0);
+    active_h.assign(S * 64, 1);
+    skip_h.assign(S, 0);
+  }
+
+  // CGS2 of columns [m0, m0+q) of V against [e, V[:, 0:m0]]; keep1 = surviving columns.
+  void ortho(int m0, int q, double drop1) {
+    TV* T = V + m0;
+    // unit-normalise the columns
+    coldots<TV>(g, red, T, z.ldv, T, z.ldv, q, tmp, 64, seg_skip, st);
+    inv_sqrt(z.nseg * 64, tmp, scale, 0.0, st);
+    colscale<TV>(g, T, z.ldv, q, scale, 64, seg_skip, st);
+    for (int pass = 0; pass < 2; ++pass) {
+      gram<TV>(g, red, V, z.ldv, m0, T, z.ldv, q, 1, 1, Gm, q, 65 * 64, seg_skip, st);
+      update<TV>(g, T, z.ldv, q, 1.0, -1.0, V, z.ldv, m0, 1, Gm, q, 65 * 64, seg_skip, st);
+      gram<TV>(g, red, T, z.ldv, q, T, z.ldv, q, 0, 0, Sm, q, 64 * 64, seg_skip, st);
+      chol_inv(z.nseg, q, Sm, 64 * 64, pass == 0 ? drop1 : 0.25, 1, Rinv, 64 * 64, pass == 0 ? keep1 : keep2,
+               seg_skip, st);
+      update<TV>(g, T, z.ldv, q, 0.0, 1.0, T, z.ldv, q, 0, Rinv, q, 64 * 64, seg_skip, st);
+    }
+    and_flags(z.nseg * 64, keep1, keep2, st);
+  }
+
+  // Start: V[:, 0:q] from `init` (or random), orthonormalised; W = L V; H = V^T W.
+  int start(const TV* init, int ldi, int q, uint64_t seed, double drop1) {
+    if (init) convert<TV, TV>(g, init, ldi, V, z.ldv, q, st);
+    else random_block<TV>(g, V, z.ldv, q, seed, st);
+    cudaMemsetAsync(seg_skip, 0, sizeof(int) * z.nseg * 64, st);
+    ortho(0, q, drop1);
+    spmm<TV>(g, V, z.ldv, W, z.ldv, q, st);
+    n_matvec += q;
+    gram<TV>(g, red, V, z.ldv, q, W, z.ldv, q, 0, 0, Gm, q, 65 * 64, seg_skip, st);
+    cudaMemsetAsync(H, 0, sizeof(double) * z.nseg * z.mmax * z.mmax, st);
+    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, q, 65 * 64, 0, q, keep1, 64, big(), seg_skip, st);
+    return q;
+  }
+
+  double big() const { return 1e30; }
+
+  // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
+  int rayleigh_ritz(int m) {
+    syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
+         seg_skip, sweeps, st);
+    const int mk = std::min(m, z.mk);
+    update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
+    update<TV>(g, W, z.ldv, mk, 0.0, 1.0, W, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
+    h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
+    return mk;
+  }
+
+  // residuals of the Ritz block into Rv and rn2 (copied to the host).
+  int residuals(bool explicit_lx) {
+    if (explicit_lx) {
+      spmm<TV>(g, V, z.ldv, W, z.ldv, z.b, st);
+      n_matvec += z.b;
+    }
+    residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
+    if (cudaMemcpyAsync(rn2_h.data(), rn2, sizeof(double) * z.nseg * 64, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(theta_h.data(), theta, sizeof(double) * z.nseg * z.mmax, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error(std::string("CUDA error in JD loop: ") + cudaGetErrorString(cudaGetLastError()));
+      return LAP_ECUDA;
+    }
+    return LAP_OK;
+  }
+
+  // correction solves for the active columns, then expansion of the basis.
+  int correct_and_expand(int mk, int itmax, double delta, double drop1) {
+    const TP* X;
+    int ldx;
+    const TP* R;
+    int ldr;
+    if constexpr (std::is_same<TV, TP>::value) {
+      X = V; ldx = z.ldv; R = Rv; ldr = z.ldb;
+    } else {
+      convert<TV, TP>(g, V, z.ldv, Xp, z.ldb, z.b, st);
+      convert<TV, TP>(g, Rv, z.ldb, Rp, z.ldb, z.b, st);
+      X = Xp; ldx = z.ldb; R = Rp; ldr = z.ldb;
+    }
+    pcg_init<TP>(g, red, ps, X, ldx, R, ldr, Tt, RES, Zb, P, z.ldb, z.b, active, seg_skip, st);
+    for (int it = 0; it < itmax; ++it) {
+      spmm<TP>(g, P, z.ldb, AP, z.ldb, z.b, st);
+      pcg_step_b<TP>(g, red, ps, X, ldx, P, AP, z.ldb, z.b, theta, z.mmax, seg_skip, st);
+      pcg_step_c<TP>(g, red, ps, X, ldx, P, AP, Tt, RES, Zb, z.ldb, z.b, theta, z.mmax, delta, seg_skip, st);
+      pcg_step_d<TP>(g, ps, X, ldx, Zb, P, z.ldb, z.b, seg_skip, st);
+    }
+    inner_its += itmax;
+    int nact = 0;
+    for (int s = 0; s < z.nseg; ++s)
+      if (!skip_h[s])
+        for (int j = 0; j < z.b; ++j) nact += active_h[(size_t)s * 64 + j] ? 1 : 0;
+    n_matvec += (int64_t)itmax * nact;
+    // T -> V[:, mk : mk+b]
+    convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
+    ortho(mk, z.b, drop1);
+    spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
+    n_matvec += nact;
+    gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
+    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, big(), seg_skip, st);
+    return mk + z.b;
+  }
+};
+
+struct Params {
+  int k, b, mk, itmax, max_outer, verbose;
+  double tol, delta, max_seconds;
+  std::chrono::steady_clock::time_point t0;
+};
+
+// Run outer iterations until every segment has its k wanted pairs below
+// tol_abs[s]; explicit_check re-forms L X before accepting.  Returns LAP_OK,
+// LAP_ENOCONV, LAP_ETIMEOUT or an error; `outer` accumulates iterations.
+template <typename TV, typename TP>
+int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& tol_abs, bool explicit_check,
+            int& outer, int& m_out, double drop1, int stall_limit) {
+  const int S = jd.z.nseg;
+  std::fill(jd.skip_h.begin(), jd.skip_h.end(), 0);
+  double best = 1e300;
+  int stall = 0;
+  int rc = LAP_ENOCONV;
+  while (outer < P.max_outer) {
+    ++outer;
+    const int mk = jd.rayleigh_ritz(m);
+    m = mk;
+    int e = jd.residuals(false);
+    if (e) return e;
+    // convergence bookkeeping on the host
+    bool all = true, bad = false;
+    double worst = 0.0;
+    for (int s = 0; s < S; ++s) {
+      if (jd.skip_h[s]) continue;
+      bool segc = true;
+      for (int j = 0; j < jd.z.b; ++j) {
+        const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
+        if (!std::isfinite(r)) bad = true;
+        const bool c = r <= tol_abs[s];
+        if (j < P.k) {
+          segc = segc && c;
+          worst = std::max(worst, r / tol_abs[s]);
+        }
+        jd.active_h[(size_t)s * 64 + j] = (j < P.k && c) ? 0 : 1;
+      }
+      if (segc) {
+        if (explicit_check) {
+          jd.skip_h[s] = 2;  // candidate: verify below
+        } else {
+          jd.skip_h[s] = 1;
+        }
+      } else {
+        all = false;
+      }
+    }
+    if (bad) { set_error("NaN/Inf residual in JD"); return LAP_ENUMERIC; }
+    if (P.verbose) fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, worst);
+    bool any_candidate = false;
+    for (int s = 0; s < S; ++s) any_candidate |= jd.skip_h[s] == 2;
+    if (any_candidate) {
+      // explicit check of the candidates: L X formed afresh
+      std::vector<int> mask(S * 64, 1);
+      for (int s = 0; s < S; ++s) mask[(size_t)s * 64] = jd.skip_h[s] == 2 ? 0 : 1;
+      std::vector<int> sk(S);
+      for (int s = 0; s < S; ++s) sk[s] = jd.skip_h[s] == 2 ? 0 : 1;
+      cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
+      e = jd.residuals(true);
+      if (e) return e;
+      all = true;
+      for (int s = 0; s < S; ++s) {
+        if (jd.skip_h[s] == 1) continue;
+        if (jd.skip_h[s] == 0) { all = false; continue; }
+        bool segc = true;
+        for (int j = 0; j < P.k; ++j) {
+          const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
+          const bool c = r <= tol_abs[s];
+          segc = segc && c;
+          jd.active_h[(size_t)s * 64 + j] = c ? 0 : 1;
+        }
+        jd.skip_h[s] = segc ? 1 : 0;
+        all = all && segc;
+      }
+    }
+    if (all) { rc = LAP_OK; break; }
+    if (worst < 0.5 * best) { best = worst; stall = 0; }
+    else if (++stall >= stall_limit) { rc = LAP_ENOCONV; break; }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
+    if (P.max_seconds > 0 && el > P.max_seconds) { set_error("time limit reached"); rc = LAP_ETIMEOUT; break; }
+    cudaMemcpyAsync(jd.active, jd.active_h.data(), sizeof(int) * S * 64, cudaMemcpyHostToDevice, jd.st);
+    std::vector<int> sk(S);
+    for (int s = 0; s < S; ++s) sk[s] = jd.skip_h[s] ? 1 : 0;
+    cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
+    m = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
+  }
+  // make sure skip flags are cleared on the device for whatever comes next
+  cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, jd.st);
+  m_out = m;
+  return rc;
+}
+
+template <typename TV, typename TP>
+void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G, bool want_vecs, SolveOut& out,
+            Arena& arena_out, double* d_out, unsigned long long* d_best) {
+  const int S = jd.z.nseg;
+  cudaStream_t st = jd.st;
+  // explicit FP64-normalised final residuals (one SpMM in the basis precision)
+  jd.residuals(true);
+  out.evals.assign(S, {});
+  out.info.assign(S, lap_info{});
+  for (int s = 0; s < S; ++s) {
+    out.evals[s].assign(jd.theta_h.begin() + (size_t)s * jd.z.mmax, jd.theta_h.begin() + (size_t)s * jd.z.mmax + P.k);
+    lap_info& in = out.info[s];
+    in.status = status;
+    double worst = 0.0;
+    int nconv = 0;
+    bool prefix = true;
+    for (int j = 0; j < P.k; ++j) {
+      const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j])) / G->norm1[s];
+      worst = std::max(worst, r);
+      if (prefix && r <= P.tol) ++nconv; else prefix = false;
+    }
+    in.n_converged = status == LAP_OK ? P.k : nconv;
+    in.outer_its = outer;
+    in.inner_its = jd.inner_its;
+    in.n_matvec = jd.n_matvec;
+    in.norm_L = G->norm1[s];
+    in.max_rel_residual = worst;
+    in.spmm_team = G->dg.team;
+  }
+  if (want_vecs) {
+    copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, d_out, st);
+    out.evecs.assign(S, {});
+    for (int s = 0; s < S; ++s) {
+      const int ns = G->row0[s + 1] - G->row0[s];
+      out.evecs[s].resize((size_t)ns * P.k);
+      cudaMemcpyAsync(out.evecs[s].data(), d_out + (size_t)G->row0[s] * P.k, sizeof(double) * ns * P.k,
+                      cudaMemcpyDeviceToHost, st);
+    }
+    cudaStreamSynchronize(st);
+  }
+  (void)arena_out;
+}
+
+}  // namespace
+
+int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out) {
+  Params P;
+  P.t0 = std::chrono::steady_clock::now();
+  P.k = k;
+  P.b = o.block > 0 ? std::max(o.block, k) : k;
+  if (P.b > 32) { set_error("JD block width must be <= 32"); return LAP_EINVAL; }
+  P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b) : P.b + 2;
+  P.mk = std::min(P.mk, 64 - P.b);
+  P.itmax = o.inner_maxit > 0 ? o.inner_maxit : 20;
+  P.delta = o.inner_tol > 0 ? o.inner_tol : 1e-2;
+  P.max_outer = o.max_outer > 0 ? o.max_outer : 1000;
+  P.tol = tol;
+  P.max_seconds = o.max_seconds;
+  P.verbose = o.verbose;
+  const int S = G->hg.nseg;
+  for (int s = 0; s < S; ++s) {
+    const int ns = G->row0[s + 1] - G->row0[s];
+    if (P.mk + P.b > ns - 1) { set_error("graph too small for the JD block (need n > k + block + m_keep)"); return LAP_EINVAL; }
+  }
+  Sizes z;
+  z.n = G->hg.n; z.nseg = S; z.k = k; z.b = P.b; z.mk = P.mk; z.mmax = P.mk + P.b;
+  z.ldv = round_up(z.mmax, 4); z.ldb = round_up(z.b, 4);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(o.stream);
+  std::vector<double> tol_abs(S);
+  for (int s = 0; s < S; ++s) tol_abs[s] = tol * G->norm1[s];
+
+  Arena outa;
+  int rc = outa.init(sizeof(double) * (size_t)z.n * k + sizeof(unsigned long long) * (size_t)S * k + 1024);
+  if (rc) return rc;
+  double* d_out = outa.take<double>((size_t)z.n * k);
+  unsigned long long* d_best = outa.take<unsigned long long>((size_t)S * k);
+
+  int outer = 0;
+  const bool mixed = o.precision == LAP_PREC_MIXED;
+  if (!mixed) {
+    Arena a;
+    rc = a.init(JD<double, double>::bytes(z));
+    if (rc) return rc;
+    JD<double, double> jd(G, z, st);
+    jd.carve(a);
+    int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20);
+    int m_out = m;
+    const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
+    if (status < 0 && status != LAP_ETIMEOUT) return status;
+    finish(jd, P, status, outer, G, want_vecs, out, outa, d_out, d_best);
+    if (cudaGetLastError() != cudaSuccess) { set_error("CUDA error after JD"); return LAP_ECUDA; }
+    return status;
+  }
+  // ---- phase 1: FP32
+  Arena a1;
+  rc = a1.init(JD<float, float>::bytes(z));
+  if (rc) return rc;
+  JD<float, float> j1(G, z, st);
+  j1.carve(a1);
+  int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10);
+  std::vector<double> tol1(S);
+  for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
+  int m_out = m;
+  Params P1 = P;
+  int st1 = iterate(j1, m, P1, tol1, false, outer, m_out, 1e-10, 8);
+  if (st1 < 0 && st1 != LAP_ETIMEOUT) return st1;
+  const int outer1 = outer;
+  // ---- phase 2: FP64 basis and Rayleigh-Ritz, FP32 corrections
+  Arena a2;
+  rc = a2.init(JD<double, float>::bytes(z));
+  if (rc) return rc;
+  JD<double, float> j2(G, z, st);
+  j2.carve(a2);
+  const int mk = std::min(m_out, z.mk);
+  convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);
+  j2.n_matvec = j1.n_matvec;
+  j2.inner_its = j1.inner_its;
+  m = j2.start(j2.V, z.ldv, mk, 0, 1e-20);
+  int status = (st1 == LAP_ETIMEOUT) ? LAP_ETIMEOUT : iterate(j2, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
+  if (status < 0 && status != LAP_ETIMEOUT) return status;
+  finish(j2, P, status, outer, G, want_vecs, out, outa, d_out, d_best);
+  for (auto& in : out.info) in.phase1_outer = outer1;
+  if (cudaGetLastError() != cudaSuccess) { set_error("CUDA error after JD"); return LAP_ECUDA; }
+  return status;
+}
+
+}  // namespace lapeig

@@ -1,0 +1,175 @@
+// Laplacian SpMM with the degree diagonal fused in (Section 2: L = D - A;
+// Section 3 item 1: the matrix-vector product, applied to a block of b vectors).
+//
+//   Y[i, c] = d_i X[i, c] - sum_{j in row i} w_ij X[j, c],   c < b
+//
+// d_i is never read from memory: it is the row length (unit weights) or the
+// sum of the row's weights, accumulated in the same pass over the row.
+//
+// Load balance for power-law degree skew: rows of ordinary length are handled
+// by a team of TEAM lanes (TEAM | 32) that stride over the row's nonzeros,
+// each lane accumulating all b columns in registers, then a butterfly
+// reduction inside the team.  Rows longer than long_thresh (the hubs) are
+// listed at set-up and each gets a whole 256-thread CTA with a block
+// reduction.  Both kinds run in one launch: the first nlong CTAs take the hub
+// rows, the rest the ordinary rows (which skip the hubs).
+//
+// Gathers of X rows read b contiguous values; with FP32 (FP64) data, 16-byte
+// aligned rows and b padded to 4 (2) inside the leading dimension, they are
+// issued as float4 (double2) loads.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace lapeig {
+
+template <typename T> struct Vec2 {};
+template <> struct Vec2<float> { using type = float4; static constexpr int w = 4; };
+template <> struct Vec2<double> { using type = double2; static constexpr int w = 2; };
+
+template <typename T> __device__ __forceinline__ const T* weights_of(const DevGraph& g);
+template <> __device__ __forceinline__ const float* weights_of<float>(const DevGraph& g) { return g.w32; }
+template <> __device__ __forceinline__ const double* weights_of<double>(const DevGraph& g) { return g.w64; }
+
+template <typename T, int BMAX, bool VEC>
+__device__ __forceinline__ void gather_row(T (&acc)[BMAX], const T* __restrict__ xj, T wv, int b) {
+  if constexpr (VEC) {
+    using V = typename Vec2<T>::type;
+    constexpr int W = Vec2<T>::w;
+    const V* xv = reinterpret_cast<const V*>(xj);
+#pragma unroll
+    for (int c = 0; c < BMAX; c += W) {
+      if (c < b) {
+        V v = __ldg(xv + c / W);
+        if constexpr (W == 4) {
+          acc[c] += wv * v.x; acc[c + 1] += wv * v.y; acc[c + 2] += wv * v.z; acc[c + 3] += wv * v.w;
+        } else {
+          acc[c] += wv * v.x; acc[c + 1] += wv * v.y;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < BMAX; ++c)
+      if (c < b) acc[c] += wv * __ldg(xj + c);
+  }
+}
+
+template <typename T, int BMAX, int TEAM, bool VEC>
+__global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ X, int ldx,
+                                              T* __restrict__ Y, int ldy, int b) {
+  const T* __restrict__ w = weights_of<T>(g);
+  T acc[BMAX];
+#pragma unroll
+  for (int c = 0; c < BMAX; ++c) acc[c] = T(0);
+  T dsum = T(0);
+
+  if ((int)blockIdx.x < g.nlong) {
+    // ---- hub row: one CTA
+    __shared__ T red[8][BMAX + 1];
+    const int row = g.long_rows[blockIdx.x];
+    const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const int j = __ldg(g.colidx + p);
+      const T wv = w ? __ldg(w + p) : T(1);
+      gather_row<T, BMAX, VEC>(acc, X + (size_t)j * ldx, wv, b);
+      dsum += wv;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < BMAX; ++c) {
+      T v = warp_sum(acc[c]);
+      if (lane == 0) red[warp][c] = v;
+    }
+    {
+      T v = warp_sum(dsum);
+      if (lane == 0) red[warp][BMAX] = v;
+    }
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if ((int)threadIdx.x < b) {
+      const int c = threadIdx.x;
+      T s = T(0), ds = T(0);
+      for (int q = 0; q < nw; ++q) { s += red[q][c]; ds += red[q][BMAX]; }
+      const T deg = w ? ds : T(p1 - p0);
+      Y[(size_t)row * ldy + c] = deg * X[(size_t)row * ldx + c] - s;
+    }
+    return;
+  }
+
+  // ---- ordinary rows: TEAM lanes per row
+  const int tid = (blockIdx.x - g.nlong) * blockDim.x + threadIdx.x;
+  const int row = tid / TEAM;
+  const int lane = threadIdx.x & (TEAM - 1);
+  if (row >= g.n) return;  // uniform within a team
+  const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+  if (p1 - p0 > g.long_thresh) return;  // a hub CTA owns it
+  for (int p = p0 + lane; p < p1; p += TEAM) {
+    const int j = __ldg(g.colidx + p);
+    const T wv = w ? __ldg(w + p) : T(1);
+    gather_row<T, BMAX, VEC>(acc, X + (size_t)j * ldx, wv, b);
+    dsum += wv;
+  }
+  if constexpr (TEAM > 1) {
+    const unsigned mask = (TEAM == 32) ? 0xffffffffu
+                                       : (((1u << TEAM) - 1u) << ((threadIdx.x & 31) & ~(TEAM - 1)));
+#pragma unroll
+    for (int o = TEAM / 2; o > 0; o >>= 1) {
+#pragma unroll
+      for (int c = 0; c < BMAX; ++c) acc[c] += __shfl_xor_sync(mask, acc[c], o);
+      dsum += __shfl_xor_sync(mask, dsum, o);
+    }
+  }
+  const T deg = w ? dsum : T(p1 - p0);
+  const T* xr = X + (size_t)row * ldx;
+  T* yr = Y + (size_t)row * ldy;
+#pragma unroll
+  for (int c = 0; c < BMAX; ++c)
+    if (c < b && (c % TEAM) == lane) yr[c] = deg * xr[c] - acc[c];
+}
+
+template <typename T, int BMAX, int TEAM>
+static void launch_team(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, bool vec,
+                        cudaStream_t s) {
+  const int threads = 256;
+  const int rows_per_block = threads / TEAM;
+  const int blocks = g.nlong + (g.n + rows_per_block - 1) / rows_per_block;
+  if (blocks == 0) return;
+  if (vec)
+    k_spmm<T, BMAX, TEAM, true><<<blocks, threads, 0, s>>>(g, X, ldx, Y, ldy, b);
+  else
+    k_spmm<T, BMAX, TEAM, false><<<blocks, threads, 0, s>>>(g, X, ldx, Y, ldy, b);
+}
+
+template <typename T, int BMAX>
+static void launch_bmax(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, bool vec,
+                        cudaStream_t s) {
+  switch (g.team) {
+    case 4: launch_team<T, BMAX, 4>(g, X, ldx, Y, ldy, b, vec, s); break;
+    case 8: launch_team<T, BMAX, 8>(g, X, ldx, Y, ldy, b, vec, s); break;
+    case 16: launch_team<T, BMAX, 16>(g, X, ldx, Y, ldy, b, vec, s); break;
+    default: launch_team<T, BMAX, 32>(g, X, ldx, Y, ldy, b, vec, s); break;
+  }
+}
+
+template <typename T>
+void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
+  constexpr int W = Vec2<T>::w;
+  for (int c0 = 0; c0 < b; c0 += 32) {
+    const int bb = (b - c0) < 32 ? (b - c0) : 32;
+    const T* Xc = X + c0;
+    T* Yc = Y + c0;
+    const int bpad = (bb + W - 1) / W * W;
+    const bool vec = bb > 1 && (reinterpret_cast<uintptr_t>(Xc) % 16 == 0) && (ldx % W == 0) &&
+                     (c0 + bpad <= ldx);
+    if (bb == 1) launch_bmax<T, 1>(g, Xc, ldx, Yc, ldy, bb, false, s);
+    else if (bb <= 4) launch_bmax<T, 4>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+    else if (bb <= 8) launch_bmax<T, 8>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+    else if (bb <= 16) launch_bmax<T, 16>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+    else launch_bmax<T, 32>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+  }
+}
+
+template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t);
+template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t);
+
+}  // namespace lapeig

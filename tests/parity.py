@@ -1,0 +1,59 @@
+"""Parity checks of GPU eigenpairs against the oracle (reading of the
+tolerances: residual, eigenvalue and per-cluster subspace angle)."""
+import numpy as np
+
+from oracle.laplacian import Laplacian
+
+
+def clusters(ev: np.ndarray, gap: float):
+    """Group consecutive sorted eigenvalues whose spacing is below `gap`."""
+    groups, cur = [], [0]
+    for i in range(1, ev.size):
+        if ev[i] - ev[i - 1] < gap:
+            cur.append(i)
+        else:
+            groups.append(cur)
+            cur = [i]
+    groups.append(cur)
+    return groups
+
+
+def check_eigpairs(g, ev, V, ev_ref, V_ref, tol=1e-8, ev_rtol=1e-7, angle=1e-6, k=None):
+    """ev, V: k GPU pairs; ev_ref, V_ref: at least k oracle pairs (more pairs
+    make the one-sided check of a cluster straddling k possible).
+
+    * explicit FP64 residual ||L v - ev v|| <= tol ||L||_1 (recomputed here)
+    * V orthonormal and orthogonal to e
+    * |ev - ev_ref| <= ev_rtol |ev_ref| (absolute ev_rtol ||L||_1 near zero)
+    * per cluster (Davis-Kahan: spacing below max||r|| / angle), the largest
+      principal angle between the GPU vectors of the cluster and the oracle's
+      cluster span is below `angle`
+    """
+    lap = Laplacian(g)
+    k = k or ev.size
+    ev, V = np.asarray(ev)[:k], np.asarray(V)[:, :k]
+    R = lap.matvec(V) - V * ev[None, :]
+    rn = np.linalg.norm(R, axis=0)
+    assert rn.max() <= tol * lap.norm1, f"residual {rn.max() / lap.norm1:.3e} > {tol}"
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-8, "not orthonormal"
+    assert np.abs(V.sum(axis=0)).max() <= 1e-8 * np.sqrt(g.n), "not orthogonal to e"
+    err = np.abs(ev - ev_ref[:k])
+    ref = np.abs(ev_ref[:k])
+    bound = np.where(ref > 1e-9 * lap.norm1, ev_rtol * ref, ev_rtol * 1e-3 * lap.norm1)
+    assert np.all(err <= bound), f"eigenvalue error {err.max():.3e} (rel {np.max(err / np.maximum(np.abs(ev_ref[:k]), 1e-300)):.3e})"
+    gap = max(rn.max(), 1e-300) / angle
+    worst = 0.0
+    for cl in clusters(np.asarray(ev_ref), gap):
+        idx = [i for i in cl if i < k]
+        if not idx:
+            continue
+        if cl[-1] >= ev_ref.size - 1 and cl[-1] >= k:
+            # cluster runs off the end of the oracle's list: cannot judge it
+            continue
+        U = V_ref[:, cl]
+        Vc = V[:, idx]
+        s = np.linalg.norm(Vc - U @ (U.T @ Vc), ord=2)
+        worst = max(worst, s)
+    assert worst <= angle, f"cluster subspace angle {worst:.3e} > {angle}"
+    return dict(max_rel_residual=rn.max() / lap.norm1, max_ev_rel_err=float(np.max(err / np.maximum(np.abs(ev_ref[:k]), 1e-300))),
+                max_angle=worst)

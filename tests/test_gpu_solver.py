@@ -1,0 +1,114 @@
+"""Whole-solve parity: lap_eigs / lap_eigs_batched through the C ABI against the
+oracle's dense definition (and closed forms), with the tolerances of the
+parity helper: explicit FP64 residual <= tol ||L||_1, eigenvalue relative
+error <= 1e-7, per-cluster subspace angle <= 1e-6."""
+import numpy as np
+import pytest
+
+import graphgen as G
+from oracle import dense
+from parity import check_eigpairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1311_1695_gb300 as p
+    from paper_1311_1695_gb300 import build
+    build.build()
+    return p
+
+
+def _solve_and_check(pkg, g, k, precision="fp64", extra=10, **kw):
+    ev, V, info = pkg.lap_eigs(g, k, tol=1e-8, method="jd", precision=precision, **kw)
+    assert info["status"] == 0, info
+    ev_ref, V_ref = dense.smallest_eigpairs(g, min(k + extra, g.n - 1))
+    res = check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)
+    # the sign convention: largest-magnitude entry positive
+    idx = np.argmax(np.abs(V), axis=0)
+    assert np.all(V[idx, np.arange(k)] > 0)
+    return info, res
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c1_ba2000_k10(pkg, precision):
+    """The protein-sized workload: BA n=2,000, m=2, 10 smallest pairs to 1e-8."""
+    g = G.workload_graph("c1")
+    info, res = _solve_and_check(pkg, g, 10, precision)
+    assert info["max_rel_residual"] <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("make,k", [
+    (lambda: G.path_graph(400), 6),
+    (lambda: G.cycle_graph(300), 6),          # doubly degenerate pairs
+    (lambda: G.grid_graph(23, 31), 8),
+    (lambda: G.hypercube(8), 6),              # eigenvalue 2 with multiplicity 8 straddles k
+    (lambda: G.complete_bipartite(40, 70), 5),
+])
+def test_closed_forms(pkg, make, k, precision):
+    g = make()
+    _solve_and_check(pkg, g, k, precision)
+
+
+def test_path_closed_form_values(pkg):
+    n = 500
+    ev, V, info = pkg.lap_eigs(G.path_graph(n), 5, tol=1e-8)
+    ref = 2 - 2 * np.cos(np.pi * np.arange(1, 6) / n)
+    assert np.allclose(ev, ref, rtol=1e-7, atol=0)
+
+
+def test_weighted_graph(pkg):
+    g = G.with_random_weights(G.chung_lu(3000, 2.3, 5.0, 4), 8)
+    _solve_and_check(pkg, g, 8, "fp64")
+    _solve_and_check(pkg, g, 8, "mixed")
+
+
+def test_disconnected_graph_extra_zeros(pkg):
+    g = G.disjoint_union(G.ba_graph(300, 2, 1), G.grid_graph(12, 15), G.cycle_graph(80))
+    ev, V, info = pkg.lap_eigs(g, 5, tol=1e-8)
+    assert info["status"] == 0
+    # c = 3 components: two extra zeros on the complement of e (Section 2)
+    assert np.abs(ev[:2]).max() <= 1e-8 * info["norm_L"]
+    ev_ref, V_ref = dense.smallest_eigpairs(g, 15)
+    check_eigpairs(g, ev, V, ev_ref, V_ref, k=5)
+
+
+def test_include_null(pkg):
+    g = G.ba_graph(500, 3, 2)
+    ev, V, info = pkg.lap_eigs(g, 5, tol=1e-8, include_null=True)
+    assert ev[0] == 0.0 and np.allclose(V[:, 0], 1 / np.sqrt(g.n))
+    ev_ref, V_ref = dense.smallest_eigpairs(g, 14)
+    check_eigpairs(g, ev[1:], V[:, 1:], ev_ref, V_ref, k=4)
+
+
+def test_smallest_graph_for_block(pkg):
+    # n just above k + block + m_keep
+    g = G.ba_graph(20, 2, 3)
+    _solve_and_check(pkg, g, 3, "fp64", extra=5)
+
+
+def test_batched_matches_solo(pkg):
+    specs = G.batch_specs(9, seed=77, n_lo=300, n_hi=3000)
+    gs = [G.graph_from_spec(s) for s in specs]
+    evs, Vs, infos = pkg.lap_eigs_batched(gs, 8, tol=1e-8, precision="mixed")
+    for g, ev, V, info in zip(gs, evs, Vs, infos):
+        assert info["status"] == 0, info
+        ev_ref, V_ref = dense.smallest_eigpairs(g, 18)
+        check_eigpairs(g, ev, V, ev_ref, V_ref, k=8)
+
+
+def test_partial_result_on_iteration_cap(pkg):
+    g = G.workload_graph("c1")
+    ev, V, info = pkg.lap_eigs(g, 10, tol=1e-8, max_outer=2)
+    assert info["status"] == 1  # LAP_ENOCONV
+    assert 0 <= info["n_converged"] < 10
+    assert np.all(np.isfinite(ev)) and np.all(np.isfinite(V))
+
+
+def test_seed_independence(pkg):
+    g = G.workload_graph("c1")
+    e1, _, _ = pkg.lap_eigs(g, 6, tol=1e-8, seed=1)
+    e2, _, _ = pkg.lap_eigs(g, 6, tol=1e-8, seed=99)
+    assert np.allclose(e1, e2, rtol=1e-9)

@@ -1,0 +1,242 @@
+"""Step-level parity: each kernel of the Jacobi-Davidson outer loop, called
+through the C ABI on device blocks, against the oracle's definition on the
+same seeded inputs.  Sizes span several row tiles with a ragged tail; graphs
+include power-law hubs (the one-CTA-per-row path), weights and batches."""
+import numpy as np
+import pytest
+
+import graphgen as G
+from oracle import blockops, dense
+from oracle.laplacian import Laplacian
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+EPS = {torch.float64: np.finfo(np.float64).eps, torch.float32: np.finfo(np.float32).eps}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1311_1695_gb300 as p
+    from paper_1311_1695_gb300 import build
+    build.build()
+    return p
+
+
+GRAPHS = {
+    "ba": lambda: G.ba_graph(3001, 2, 5),
+    "cl_hubs": lambda: G.chung_lu(20000, 2.1, 7.0, 3, cap=2000.0),
+    "weighted": lambda: G.with_random_weights(G.chung_lu(5000, 2.3, 5.0, 4), 8),
+    "grid": lambda: G.grid_graph(37, 41),
+}
+
+
+def _dev(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dt).cuda()
+
+
+def _abs_bound(g, X):
+    """|L| |X| row by row and the row lengths, for a rounding bound."""
+    lap = Laplacian(g)
+    absL = abs(lap.L)
+    return absL @ np.abs(X), np.diff(g.rowptr) + 2
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("b", [1, 3, 10, 20, 33])
+def test_spmm(pkg, name, dt, b):
+    g = GRAPHS[name]()
+    Gd = pkg.Graph(g)
+    X = G.random_block(g.n, b, 11).astype(np.float32 if dt == torch.float32 else np.float64)
+    Xd = _dev(X, dt)
+    Yd = torch.empty_like(Xd)
+    Gd.spmm(Xd, Yd)
+    Y = Yd.cpu().double().numpy()
+    ref = blockops.lap_spmm(g, X.astype(np.float64))
+    S, deg = _abs_bound(g, X.astype(np.float64))
+    bound = 2 * EPS[dt] * deg[:, None] * S + 1e-300
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / bound)
+    Gd.close()
+
+
+@pytest.mark.parametrize("team", [4, 8, 16, 32])
+def test_spmm_schedules_agree(pkg, team):
+    g = GRAPHS["cl_hubs"]()
+    Gd = pkg.Graph(g)
+    X = _dev(G.random_block(g.n, 8, 3), torch.float64)
+    Y0 = torch.empty_like(X)
+    Gd.spmm(X, Y0)
+    Gd.set_schedule(team=team, long_thresh=16)
+    assert Gd.info()["nlong"] > 0
+    Y1 = torch.empty_like(X)
+    Gd.spmm(X, Y1)
+    assert torch.allclose(Y0, Y1, rtol=1e-12, atol=1e-12 * Y0.abs().max().item())
+    Gd.close()
+
+
+def test_spmm_batched_block_diagonal(pkg):
+    gs = [G.ba_graph(700, 3, 1), G.grid_graph(20, 30), G.chung_lu(3000, 2.5, 4.0, 9)]
+    Gd = pkg.Graph(gs)
+    n = sum(x.n for x in gs)
+    X = G.random_block(n, 6, 2)
+    Yd = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    Gd.spmm(_dev(X, torch.float64), Yd)
+    Y = Yd.cpu().numpy()
+    off = 0
+    for x in gs:
+        ref = blockops.lap_spmm(x, X[off:off + x.n])
+        assert np.abs(Y[off:off + x.n] - ref).max() <= 1e-12 * np.abs(ref).max()
+        off += x.n
+    Gd.close()
+
+
+def test_spmm_empty_rows_and_tiny(pkg):
+    # a star has one hub and n-1 rows of length 1; a 2-node path the smallest graph
+    for g in (G.star_graph(5000), G.path_graph(2)):
+        Gd = pkg.Graph(g)
+        X = G.random_block(g.n, 4, 1)
+        Yd = torch.empty((g.n, 4), dtype=torch.float64, device="cuda")
+        Gd.spmm(_dev(X, torch.float64), Yd)
+        ref = blockops.lap_spmm(g, X)
+        assert np.abs(Yd.cpu().numpy() - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+        Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("p,q,ones", [(0, 5, 1), (7, 3, 0), (12, 12, 1), (40, 10, 0), (63, 20, 1)])
+def test_gram(pkg, dt, p, q, ones):
+    g = GRAPHS["cl_hubs"]()
+    Gd = pkg.Graph(g)
+    A = G.random_block(g.n, max(p, 1), 1)[:, :p] if p else None
+    B = G.random_block(g.n, q, 2)
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    Ad = None if A is None else _dev(A.astype(npdt), dt)
+    Gm = Gd.gram(Ad, _dev(B.astype(npdt), dt), ones=bool(ones)).cpu().numpy()[0]
+    A64 = np.zeros((g.n, 0)) if A is None else A.astype(npdt).astype(np.float64)
+    B64 = B.astype(npdt).astype(np.float64)
+    ref = blockops.gram(A64, B64)
+    if ones:
+        ref = np.vstack([B64.mean(axis=0, keepdims=True), ref])
+    tol = (64 if dt == torch.float64 else 64 * 32) * EPS[dt] * g.n
+    assert np.abs(Gm - ref).max() <= tol, np.abs(Gm - ref).max()
+    Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_project(pkg, dt):
+    g = GRAPHS["weighted"]()
+    Gd = pkg.Graph(g)
+    Q, _ = np.linalg.qr(blockops.project(G.random_block(g.n, 6, 5), None))
+    X = G.random_block(g.n, 9, 6)
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    Xd = _dev(X.astype(npdt), dt)
+    Gd.project(_dev(Q.astype(npdt), dt), Xd)
+    ref = blockops.project(X.astype(npdt).astype(np.float64), Q.astype(npdt).astype(np.float64))
+    tol = 1e-12 if dt == torch.float64 else 2e-5
+    assert np.abs(Xd.cpu().double().numpy() - ref).max() <= tol * np.abs(X).max() * 10
+    Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("m,b", [(0, 4), (6, 10), (20, 12)])
+def test_cgs2(pkg, dt, m, b):
+    g = GRAPHS["ba"]()
+    Gd = pkg.Graph(g)
+    V = np.linalg.qr(blockops.project(G.random_block(g.n, max(m, 1), 4), None))[0][:, :m]
+    T = G.random_block(g.n, b, 8)
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    Td = _dev(T.astype(npdt), dt)
+    kept = Gd.cgs2(_dev(V.astype(npdt), dt) if m else None, Td)
+    assert kept.all()
+    U = Td.cpu().double().numpy()
+    ref, _ = blockops.orthonormalize(V.astype(npdt).astype(np.float64) if m else None, T.astype(npdt).astype(np.float64))
+    tol = 1e-10 if dt == torch.float64 else 2e-4
+    assert np.abs(U - ref).max() <= tol
+    assert np.abs(U.T @ U - np.eye(b)).max() <= (1e-12 if dt == torch.float64 else 2e-6)
+    Gd.close()
+
+
+def test_cgs2_drops_dependent_columns(pkg):
+    g = GRAPHS["grid"]()
+    Gd = pkg.Graph(g)
+    V = np.linalg.qr(blockops.project(G.random_block(g.n, 5, 4), None))[0]
+    T = G.random_block(g.n, 6, 9)
+    T[:, 2] = V @ np.arange(1, 6)  # inside span(V)
+    T[:, 4] = 2 * T[:, 1] - T[:, 0]  # dependent on earlier columns
+    T[:, 5] = 0.0  # empty
+    Td = _dev(T, torch.float64)
+    kept = Gd.cgs2(_dev(V, torch.float64), Td)
+    assert list(kept[0]) == [1, 1, 0, 1, 0, 0]
+    U = Td.cpu().numpy()
+    assert np.abs(U[:, [2, 4, 5]]).max() == 0.0
+    ref, _ = blockops.orthonormalize(V, T[:, [0, 1, 3]])
+    assert np.abs(U[:, [0, 1, 3]] - ref).max() <= 1e-10
+    Gd.close()
+
+
+@pytest.mark.parametrize("m", [1, 2, 7, 24, 44, 64])
+def test_syev(pkg, m):
+    rng = np.random.default_rng(m)
+    H = rng.standard_normal((3, m, m))
+    H = H + H.transpose(0, 2, 1)
+    H[1] = np.diag(np.arange(m, dtype=float)) + 1e-3 * H[1]  # nearly diagonal
+    H[2] = np.kron(np.eye((m + 1) // 2), np.ones((2, 2)))[:m, :m]  # repeated eigenvalues
+    ev, Y = pkg.lap_syev_batched(torch.from_numpy(H).cuda())
+    ev, Y = ev.cpu().numpy(), Y.cpu().numpy()
+    for i in range(3):
+        ref = np.linalg.eigvalsh(H[i])
+        assert np.abs(ev[i] - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max()) * m
+        assert np.abs(Y[i].T @ Y[i] - np.eye(m)).max() <= 1e-13 * m
+        assert np.abs(H[i] @ Y[i] - Y[i] * ev[i][None, :]).max() <= 1e-13 * m * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_rayleigh_ritz_and_residuals(pkg, dt):
+    g = GRAPHS["ba"]()
+    Gd = pkg.Graph(g)
+    ev, U = dense.smallest_eigpairs(g, 12)
+    # a basis whose span contains the 8 smallest eigenvectors exactly, plus noise directions
+    B = np.column_stack([U[:, :8], blockops.project(G.random_block(g.n, 4, 3), U[:, :8])])
+    B = np.linalg.qr(B)[0] @ np.linalg.qr(G.random_block(12, 12, 4))[0]
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    Vd = _dev(B.astype(npdt), dt)
+    theta = Gd.rayleigh_ritz(Vd)
+    th = theta.cpu().numpy()[0]
+    tol = 1e-10 if dt == torch.float64 else 1e-4
+    assert np.abs(th[:8] - ev[:8]).max() <= tol * max(1, ev[7])
+    rn = Gd.residual_norms(Vd[:, :8].contiguous(), theta[:, :8].contiguous()).cpu().numpy()[0]
+    ref = blockops.residual_norms(g, Vd[:, :8].cpu().double().numpy(), th[:8])
+    assert np.abs(rn - ref).max() <= (1e-11 if dt == torch.float64 else 1e-4) * Laplacian(g).norm1
+    Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("name", ["ba", "weighted"])
+def test_pcg_correction_fixed_steps(pkg, dt, name):
+    g = GRAPHS[name]()
+    Gd = pkg.Graph(g)
+    ev, U = dense.smallest_eigpairs(g, 6) if g.n <= 4000 else (None, None)
+    if U is None:
+        U = np.linalg.qr(blockops.project(G.random_block(g.n, 6, 1), None))[0]
+        lap = Laplacian(g)
+        th0 = np.einsum("ij,ij->j", U, lap.matvec(U))
+    else:
+        th0 = ev
+    # perturbed Ritz-like block: X orthonormal, theta its Rayleigh quotients, R its residuals
+    X = np.linalg.qr(blockops.project(U + 1e-2 * G.random_block(g.n, 6, 2), None))[0]
+    lap = Laplacian(g)
+    # Ritz vectors of span(X): the residuals are then orthogonal to [e, X]
+    theta, Yr = np.linalg.eigh(X.T @ lap.matvec(X))
+    X = X @ Yr
+    R = lap.matvec(X) - X * theta[None, :]
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    X, R = X.astype(npdt), R.astype(npdt)
+    iters = 8
+    Td = Gd.pcg_correction(_dev(X, dt), torch.from_numpy(theta[None, :]).cuda(), _dev(R, dt), iters)
+    T = Td.cpu().double().numpy()
+    ref = blockops.pcg_correction(g, theta, R.astype(np.float64), X.astype(np.float64), iters)
+    scale = np.abs(ref).max(axis=0)
+    err = (np.abs(T - ref).max(axis=0) / scale).max()
+    assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
+    Gd.close()
