@@ -141,6 +141,24 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
  * above which a row gets a whole CTA (0 keeps the current value). */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
 
+/* Solve on a handle whose graphs are already on the device (the CSR is not
+ * copied again).  evals: host [nseg * k] (graph s at s*k); evecs_dev: device
+ * FP64 or NULL, graph s's n_s x k column-major block at offset row0[s] * k
+ * where row0 is the running sum of the graph sizes; infos: host [nseg] or
+ * NULL.  DACG and IRLM need a single-graph handle.  include_null is not
+ * supported with device eigenvectors. */
+int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* opts, double* evals,
+                   double* evecs_dev, lap_info* infos);
+
+/* Kernel timing (tracing aid): when enabled, each kernel launch of the
+ * library is bracketed by CUDA events on its stream and tagged with its
+ * algorithmic bytes.  lap_profile_read synchronises the device and returns,
+ * per kernel name, total milliseconds, total algorithmic bytes and launch
+ * count (up to max entries; names are written as NUL-terminated strings of
+ * name_len bytes each), then clears the totals.  Not thread-safe. */
+int lap_profile_enable(int on);
+int lap_profile_read(int max, char* names, int name_len, double* ms, double* bytes, int64_t* launches, int* count);
+
 /* ---------------------------------------------------------------- step-level entry points
  * The steps of the Jacobi-Davidson outer loop on device blocks (row-major,
  * rows = all rows of the handle, segments concatenated).  dtype selects FP64

@@ -96,6 +96,9 @@ _SIGNATURES = {
     "lap_eigs_batched": (_I, [_I, _PI64, ctypes.POINTER(_PI64), ctypes.POINTER(_PI32), ctypes.POINTER(_PD), _I, _D,
                               ctypes.POINTER(lap_opts), ctypes.POINTER(_PD), ctypes.POINTER(_PD),
                               ctypes.POINTER(lap_info)]),
+    "lap_eigs_graph": (_I, [_P, _I, _D, _I, ctypes.POINTER(lap_opts), _PD, _P, ctypes.POINTER(lap_info)]),
+    "lap_profile_enable": (_I, [_I]),
+    "lap_profile_read": (_I, [_I, ctypes.c_char_p, _I, _PD, _PD, _PI64, _PI]),
     "lap_graph_create": (_I, [_I64, _PI64, _PI32, _PD, ctypes.POINTER(_P)]),
     "lap_graph_create_batched": (_I, [_I, _PI64, ctypes.POINTER(_PI64), ctypes.POINTER(_PI32), ctypes.POINTER(_PD),
                                       ctypes.POINTER(_P)]),
@@ -278,6 +281,20 @@ class Graph:
     def set_schedule(self, team=0, long_thresh=0):
         _check(lib().lap_graph_set_schedule(self.h, team, long_thresh), "lap_graph_set_schedule")
 
+    def eigs(self, k: int, tol: float = 1e-8, method: str = "jd", evecs=None, **opts):
+        """Solve on the resident graph(s) (lap_eigs_graph).  evecs: optional
+        float64 CUDA tensor of n_total * k elements receiving each graph's
+        column-major eigenvector block at offset row0[s] * k.  Returns
+        (evals [nseg, k] numpy, infos list)."""
+        o, _keep = make_opts(**opts)
+        evals = np.zeros(self.nseg * k)
+        infos = (lap_info * self.nseg)()
+        pv = None if evecs is None else ctypes.c_void_p(evecs.data_ptr())
+        st = lib().lap_eigs_graph(self.h, k, tol, _METHODS[method] if isinstance(method, str) else int(method),
+                                  ctypes.byref(o), _ptr(evals, ctypes.c_double), pv, infos)
+        _check(st, "lap_eigs_graph", allow_partial=True)
+        return evals.reshape(self.nseg, k), [i.as_dict() for i in infos]
+
     # Steps of the outer loop (device tensors in, device tensors out)
     def spmm(self, X, Y):
         px, ldx = _blk(X)
@@ -353,3 +370,25 @@ def lap_syev_batched(H):
     _check(lib().lap_syev_batched(nmat, m, ctypes.c_void_p(H.data_ptr()), m, ctypes.c_void_p(ev.data_ptr()),
                                   ctypes.c_void_p(Y.data_ptr()), m, _stream()), "lap_syev_batched")
     return ev, Y
+
+
+def lap_profile_enable(on: bool = True):
+    _check(lib().lap_profile_enable(int(bool(on))), "lap_profile_enable")
+
+
+def lap_profile_read(max_entries: int = 64):
+    """{kernel name: dict(ms, bytes, launches)} accumulated since the last read
+    (synchronises the device)."""
+    L = 48
+    names = ctypes.create_string_buffer(max_entries * L)
+    ms = np.zeros(max_entries)
+    by = np.zeros(max_entries)
+    la = np.zeros(max_entries, dtype=np.int64)
+    cnt = ctypes.c_int()
+    _check(lib().lap_profile_read(max_entries, names, L, _ptr(ms, ctypes.c_double), _ptr(by, ctypes.c_double),
+                                  _ptr(la, ctypes.c_int64), ctypes.byref(cnt)), "lap_profile_read")
+    out = {}
+    for i in range(cnt.value):
+        nm = names.raw[i * L:(i + 1) * L].split(b"\0")[0].decode()
+        out[nm] = dict(ms=float(ms[i]), bytes=float(by[i]), launches=int(la[i]))
+    return out

@@ -176,6 +176,43 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   return rc;
 }
 
+int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* opts, double* evals, double* evecs_dev,
+                   lap_info* infos) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!g || !evals || k < 1 || !(tol > 0.0) || method < LAP_JD || method > LAP_IRLM ||
+      (method != LAP_JD && g->hg.nseg > 1)) {
+    set_error("bad arguments to lap_eigs_graph");
+    return LAP_EINVAL;
+  }
+  lap_opts o = merged(opts);
+  const int kk = o.include_null ? k - 1 : k;
+  const int S = g->hg.nseg;
+  std::vector<int> nrows(S);
+  for (int s = 0; s < S; ++s) {
+    nrows[s] = g->row0[s + 1] - g->row0[s];
+    if (kk < 1 || kk > nrows[s] - 1) { set_error("k out of range for a graph"); return LAP_EINVAL; }
+  }
+  if (o.include_null && evecs_dev) { set_error("include_null needs host eigenvectors (use lap_eigs)"); return LAP_EINVAL; }
+  if (o.team) {
+    const int rc = graph_set_schedule(g, o.team, 0);
+    if (rc) return rc;
+  }
+  SolveOut out;
+  out.dev_vecs = evecs_dev;
+  int rc = solve(g, kk, tol, method, o, evecs_dev != nullptr, out);
+  if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+  if (o.include_null) add_null(out, nrows, kk);
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int s = 0; s < S; ++s) {
+    std::memcpy(evals + (size_t)s * k, out.evals[s].data(), sizeof(double) * k);
+    if (infos) {
+      infos[s] = out.info[s];
+      infos[s].elapsed_ms = ms;
+    }
+  }
+  return rc;
+}
+
 int lap_graph_create(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights, lap_graph** out) {
   if (!out) { set_error("NULL output handle"); return LAP_EINVAL; }
   const double* w[1] = {weights};

@@ -15,6 +15,7 @@
 // and in FP64 across chunks and tiles.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.h"
 
 namespace lapeig {
 
@@ -687,6 +688,7 @@ void launch_gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int 
 template <typename T>
 void gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, const T* B, int ldb, int q, int ones,
           int ones_mean, double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("gram", (double)sizeof(T) * g.n * (p + q), s);
   const int nout = (p + ones) * q;
   if (nout <= kThreads) launch_gram<T, 1>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
   else if (nout <= 4 * kThreads) launch_gram<T, 4>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
@@ -697,44 +699,52 @@ void gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, cons
 template <typename T>
 void update(const DevGraph& g, T* Y, int ldy, int q, double beta, double alpha, const T* A, int lda, int p, int ones,
             const double* S, int lds, int64_t ss, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("update", (double)sizeof(T) * g.n * (p + (beta != 0.0 ? 2 * q : q)), s);
   k_update<T><<<g.ntiles, kThreads, 0, s>>>(g, Y, ldy, q, beta, alpha, A, lda, p, ones, S, lds, ss, seg_skip);
 }
 
 template <typename T>
 void coldots(const DevGraph& g, const Reduce& red, const T* A, int lda, const T* B, int ldb, int q, double* out,
              int64_t so, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("coldots", (double)sizeof(T) * g.n * 2 * q, s);
   k_coldots<T><<<g.ntiles, kThreads, 0, s>>>(g, red, A, lda, B, ldb, q, out, so, seg_skip);
 }
 
 template <typename T>
 void colscale(const DevGraph& g, T* X, int ldx, int q, const double* scale, int64_t ss, const int* seg_skip,
               cudaStream_t s) {
+  LAP_PROF("colscale", (double)sizeof(T) * g.n * 2 * q, s);
   k_colscale<T><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, q, scale, ss, seg_skip);
 }
 
 template <typename T>
 void random_block(const DevGraph& g, T* X, int ldx, int b, uint64_t seed, cudaStream_t s) {
+  LAP_PROF("random", (double)sizeof(T) * g.n * b, s);
   k_random<T><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, b, seed);
 }
 
 template <typename TX, typename TY>
 void convert(const DevGraph& g, const TX* X, int ldx, TY* Y, int ldy, int q, cudaStream_t s) {
+  LAP_PROF("convert", (double)(sizeof(TX) + sizeof(TY)) * g.n * q, s);
   k_convert<TX, TY><<<g.ntiles, kThreads, 0, s>>>(g, X, ldx, Y, ldy, q);
 }
 
 template <typename T>
 void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T* LX, int ldlx, const double* theta,
               int64_t sth, T* R, int ldr, int q, double* norms2, int64_t so, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("residual", (double)sizeof(T) * g.n * (R ? 3 : 2) * q, s);
   k_residual<T><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
 }
 
 void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv, int64_t sr,
               int* keep, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("chol_inv", 0.0, s);
   k_chol_inv<<<nseg, 64, 0, s>>>(q, S, ss, drop, absolute, Rinv, sr, keep, seg_skip);
 }
 
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,
           int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s) {
+  LAP_PROF("syev", 0.0, s);
   const int mm = (m + 1) & ~1;
   const size_t smem = sizeof(double) * (2 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
   static bool attr_set = false;
@@ -748,6 +758,7 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
 template <typename T>
 void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* R, int ldr,
               T* Tt, T* RES, T* Z, T* P, int ld, int b, const int* active, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("pcg_init", (double)sizeof(T) * g.n * (9 * b + 1), s);
   k_pcg_init<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, R, ldr, Tt, RES, Z, ld, b, active, seg_skip);
   k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
 }
@@ -755,6 +766,7 @@ void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T*
 template <typename T>
 void pcg_step_b(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
                 const T* AP, int ld, int b, const double* theta, int64_t sth, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("pcg_b", (double)sizeof(T) * g.n * 3 * b, s);
   k_pcg_b<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, ld, b, theta, sth, seg_skip);
 }
 
@@ -762,12 +774,14 @@ template <typename T>
 void pcg_step_c(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
                 const T* AP, T* Tt, T* RES, T* Z, int ld, int b, const double* theta, int64_t sth, double delta,
                 const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("pcg_c", (double)sizeof(T) * g.n * (8 * b + 1), s);
   k_pcg_c<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, Tt, RES, Z, ld, b, theta, sth, delta, seg_skip);
 }
 
 template <typename T>
 void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z, T* P, int ld, int b,
                 const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("pcg_d", (double)sizeof(T) * g.n * 4 * b, s);
   k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
 }
 

@@ -170,6 +170,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   rc = rc ? rc : dev_alloc_copy(&g->d_deg64, deg.data(), deg.size());
   rc = rc ? rc : dev_alloc_copy(&g->d_deg32, deg32.data(), deg32.size());
   rc = rc ? rc : dev_alloc_copy(&g->d_row0, g->row0.data(), g->row0.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_norm1, g->norm1.data(), g->norm1.size());
   rc = rc ? rc : dev_alloc_copy(&g->d_tiles, tiles.data(), tiles.size());
   rc = rc ? rc : dev_alloc_copy(&g->d_tile_ptr, g->tile_ptr.data(), g->tile_ptr.size());
   // reduction scratch, zero at rest
@@ -212,7 +213,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 void graph_free(lap_graph* g) {
   if (!g) return;
   cudaFree(g->d_rowptr); cudaFree(g->d_colidx); cudaFree(g->d_w32); cudaFree(g->d_w64);
-  cudaFree(g->d_deg64); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
+  cudaFree(g->d_deg64); cudaFree(g->d_norm1); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
   cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->red.acc); cudaFree(g->red.counter);
   cudaFree(g->scratch); cudaFree(g->small);
   delete g;

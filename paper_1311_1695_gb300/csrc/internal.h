@@ -18,6 +18,7 @@ struct lap_graph {
   float* d_w32 = nullptr;
   double* d_w64 = nullptr;
   double* d_deg64 = nullptr;
+  double* d_norm1 = nullptr;   // [nseg] ||L||_1 per graph
   float* d_deg32 = nullptr;
   int* d_row0 = nullptr;
   lapeig::Tile* d_tiles = nullptr;
@@ -54,6 +55,7 @@ struct SolveOut {
   std::vector<std::vector<double>> evals;   // per segment [k]
   std::vector<std::vector<double>> evecs;   // per segment [n_s * k] column-major (may stay empty)
   std::vector<lap_info> info;               // per segment
+  double* dev_vecs = nullptr;               // if set: eigenvectors stay on the device here
 };
 
 // Block Jacobi-Davidson over all segments of the handle (lock-step).

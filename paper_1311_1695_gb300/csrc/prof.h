@@ -1,0 +1,26 @@
+// Optional kernel timing: when enabled, every launcher brackets its launch
+// with a pair of CUDA events on the launch stream and records the kernel's
+// algorithmic bytes (what a perfect cache would move).  lap_profile_read()
+// synchronises, converts the event pairs into per-kernel totals and clears.
+// Off by default; the events cost a timestamp write each on the GPU.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lapeig {
+
+bool prof_on();
+int prof_begin(const char* name, double bytes, cudaStream_t s);  // returns a slot or -1
+void prof_end(int slot, cudaStream_t s);
+
+struct ProfScope {
+  int slot;
+  cudaStream_t s;
+  ProfScope(const char* name, double bytes, cudaStream_t st) : slot(prof_on() ? prof_begin(name, bytes, st) : -1), s(st) {}
+  ~ProfScope() {
+    if (slot >= 0) prof_end(slot, s);
+  }
+};
+
+}  // namespace lapeig
+
+#define LAP_PROF(name, bytes, stream) ::lapeig::ProfScope _lap_prof_scope((name), (bytes), (stream))

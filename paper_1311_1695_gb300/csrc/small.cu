@@ -3,6 +3,7 @@
 // output sign convention and the column-major copy-out.
 #include "common.cuh"
 #include "small.cuh"
+#include "prof.h"
 
 namespace lapeig {
 
@@ -33,12 +34,14 @@ __global__ void k_h_restart(double* H, int ldh, int64_t sh, int mmax, const doub
 //   H[i, mk+j] = H[mk+j, i] = G[i, j]           i < mk
 //   H[mk+i, mk+j] = (G[mk+i, j] + G[mk+j, i]) / 2
 // Columns dropped by the orthogonalisation (keep = 0) get an isolated
-// diagonal entry `big`, so their Ritz values sort last and never enter the
-// Ritz block.
+// diagonal entry 2 ||L||_1 + 1 (above every eigenvalue of L), so their Ritz
+// values sort last and never enter the Ritz block, while the scale of H (and
+// the Jacobi stopping test) stays that of L.
 __global__ void k_h_border(double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
-                           const int* keep, int64_t sk, double big, const int* seg_skip) {
+                           const int* keep, int64_t sk, const double* norm1, const int* seg_skip) {
   const int s = blockIdx.x;
   if (seg_skip && seg_skip[s]) return;
+  const double big = 2.0 * norm1[s] + 1.0;
   double* h = H + (size_t)s * sh;
   const double* gs = G + (size_t)s * sg;
   const int* kp = keep + (size_t)s * sk;
@@ -65,32 +68,42 @@ __global__ void k_and(int count, int* a, const int* b) {
   if (i < count) a[i] = (a[i] != 0 && b[i] != 0) ? 1 : 0;
 }
 
-// Sign convention: per segment and column, find the entry of largest
-// magnitude (ties -> lowest row) with one packed atomicMax, then flip.
+// Sign convention: per segment and column, the entry of largest magnitude
+// (first row among exact ties) is made positive.  Pass 1: atomicMax of the
+// FP64 bit pattern of |v| (non-negative doubles order like their bits);
+// pass 2: atomicMin of the row index among entries equal to that maximum.
 template <typename T>
-__global__ void k_argmax(const Tile* tiles, const T* X, int ldx, int k, const int* row0,
-                         unsigned long long* best) {
+__global__ void k_absmax(const Tile* tiles, const T* X, int ldx, int k, unsigned long long* best) {
   const Tile t = tiles[blockIdx.x];
   for (int e = threadIdx.x; e < (t.r1 - t.r0) * k; e += blockDim.x) {
     const int r = t.r0 + e / k, c = e % k;
-    const float a = fabsf((float)X[(size_t)r * ldx + c]);
-    const unsigned long long key =
-        ((unsigned long long)__float_as_uint(a) << 32) | (unsigned long long)(0xffffffffu - (unsigned)(r - row0[t.seg]));
-    atomicMax(best + (size_t)t.seg * k + c, key);
+    const double a = fabs((double)X[(size_t)r * ldx + c]);
+    atomicMax(best + (size_t)t.seg * k + c, (unsigned long long)__double_as_longlong(a));
+  }
+}
+
+template <typename T>
+__global__ void k_first_at_max(const Tile* tiles, const T* X, int ldx, int k, const unsigned long long* best,
+                               int* first) {
+  const Tile t = tiles[blockIdx.x];
+  for (int e = threadIdx.x; e < (t.r1 - t.r0) * k; e += blockDim.x) {
+    const int r = t.r0 + e / k, c = e % k;
+    const double a = fabs((double)X[(size_t)r * ldx + c]);
+    if ((unsigned long long)__double_as_longlong(a) == best[(size_t)t.seg * k + c])
+      atomicMin(first + (size_t)t.seg * k + c, r);
   }
 }
 
 // out (column-major per segment, double) = sign_c * X[:, c]; seg s starts at row0[s] * k.
 template <typename T>
-__global__ void k_copy_out(const Tile* tiles, const T* X, int ldx, int k, const int* row0,
-                           const unsigned long long* best, double* out) {
+__global__ void k_copy_out(const Tile* tiles, const T* X, int ldx, int k, const int* row0, const int* first,
+                           double* out) {
   const Tile t = tiles[blockIdx.x];
   const int base = row0[t.seg];
   const int ns = row0[t.seg + 1] - base;
   for (int e = threadIdx.x; e < (t.r1 - t.r0) * k; e += blockDim.x) {
     const int r = t.r0 + e / k, c = e % k;
-    const unsigned long long key = best[(size_t)t.seg * k + c];
-    const int rbest = base + (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+    const int rbest = first[(size_t)t.seg * k + c];
     const double sgn = (double)X[(size_t)rbest * ldx + c] < 0.0 ? -1.0 : 1.0;
     out[(size_t)base * k + (size_t)c * ns + (r - base)] = sgn * (double)X[(size_t)r * ldx + c];
   }
@@ -99,24 +112,32 @@ __global__ void k_copy_out(const Tile* tiles, const T* X, int ldx, int k, const 
 }  // namespace
 
 void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
   k_inv_sqrt<<<(count + 255) / 256, 256, 0, s>>>(count, in, out, floor_v);
 }
 void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
   k_h_restart<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, theta, st, mk, seg_skip);
 }
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
-              const int* keep, int64_t sk, double big, const int* seg_skip, cudaStream_t s) {
-  k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, big, seg_skip);
+              const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
+  k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, norm1, seg_skip);
 }
 void and_flags(int count, int* a, const int* b, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
   k_and<<<(count + 255) / 256, 256, 0, s>>>(count, a, b);
 }
 template <typename T>
 void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s) {
+  LAP_PROF("copy_out", 8.0 * g.n * k + sizeof(T) * 3.0 * g.n * k, s);
+  int* first = reinterpret_cast<int*>(best + (size_t)g.nseg * k);
   cudaMemsetAsync(best, 0, sizeof(unsigned long long) * (size_t)g.nseg * k, s);
-  k_argmax<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, g.row0, best);
-  k_copy_out<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, g.row0, best, out);
+  cudaMemsetAsync(first, 0x7f, sizeof(int) * (size_t)g.nseg * k, s);
+  k_absmax<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, best);
+  k_first_at_max<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, best, first);
+  k_copy_out<T><<<g.ntiles, 256, 0, s>>>(g.tiles, X, ldx, k, g.row0, first, out);
 }
 template void copy_out<float>(const DevGraph&, const float*, int, int, unsigned long long*, double*, cudaStream_t);
 template void copy_out<double>(const DevGraph&, const double*, int, int, unsigned long long*, double*, cudaStream_t);

@@ -180,11 +180,9 @@ struct JD {
     n_matvec += q;
     gram<TV>(g, red, V, z.ldv, q, W, z.ldv, q, 0, 0, Gm, q, 65 * 64, seg_skip, st);
     cudaMemsetAsync(H, 0, sizeof(double) * z.nseg * z.mmax * z.mmax, st);
-    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, q, 65 * 64, 0, q, keep1, 64, big(), seg_skip, st);
+    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, q, 65 * 64, 0, q, keep1, 64, G->d_norm1, seg_skip, st);
     return q;
   }
-
-  double big() const { return 1e30; }
 
   // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
   int rayleigh_ritz(int m) {
@@ -246,7 +244,7 @@ struct JD {
     spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
     n_matvec += nact;
     gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
-    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, big(), seg_skip, st);
+    h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, G->d_norm1, seg_skip, st);
     return mk + z.b;
   }
 };
@@ -374,7 +372,10 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     in.max_rel_residual = worst;
     in.spmm_team = G->dg.team;
   }
-  if (want_vecs) {
+  if (want_vecs && out.dev_vecs) {
+    copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, out.dev_vecs, st);
+    cudaStreamSynchronize(st);
+  } else if (want_vecs) {
     copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, d_out, st);
     out.evecs.assign(S, {});
     for (int s = 0; s < S; ++s) {
@@ -417,10 +418,10 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   for (int s = 0; s < S; ++s) tol_abs[s] = tol * G->norm1[s];
 
   Arena outa;
-  int rc = outa.init(sizeof(double) * (size_t)z.n * k + sizeof(unsigned long long) * (size_t)S * k + 1024);
+  int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k + 1024);
   if (rc) return rc;
   double* d_out = outa.take<double>((size_t)z.n * k);
-  unsigned long long* d_best = outa.take<unsigned long long>((size_t)S * k);
+  unsigned long long* d_best = outa.take<unsigned long long>(2 * (size_t)S * k);
 
   int outer = 0;
   const bool mixed = o.precision == LAP_PREC_MIXED;

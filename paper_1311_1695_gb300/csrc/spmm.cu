@@ -19,6 +19,7 @@
 // issued as float4 (double2) loads.
 #include "common.cuh"
 #include "kernels.cuh"
+#include "prof.h"
 
 namespace lapeig {
 
@@ -151,8 +152,19 @@ static void launch_bmax(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, i
   }
 }
 
+// Algorithmic bytes of one launch: row pointers and column indices once, the
+// weights once if present, X read once and Y written once.
+template <typename T>
+double spmm_bytes(const DevGraph& g, int b) {
+  const double n = g.n, nnz = (double)g.nnz;
+  return 4.0 * (n + 1) + 4.0 * nnz + (g.w64 ? sizeof(T) * nnz : 0.0) + 2.0 * sizeof(T) * b * n;
+}
+template double spmm_bytes<float>(const DevGraph&, int);
+template double spmm_bytes<double>(const DevGraph&, int);
+
 template <typename T>
 void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
+  LAP_PROF(sizeof(T) == 4 ? "spmm_f32" : "spmm_f64", spmm_bytes<T>(g, b), s);
   constexpr int W = Vec2<T>::w;
   for (int c0 = 0; c0 < b; c0 += 32) {
     const int bb = (b - c0) < 32 ? (b - c0) : 32;
