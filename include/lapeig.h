@@ -61,7 +61,7 @@ typedef enum { LAP_F64 = 0, LAP_F32 = 1 } lap_dtype;
  * lap_opts_default); a zero field means "default". */
 typedef struct {
   uint32_t struct_size;
-  int block;          /* JD block width b (default k, at most 32) */
+  int block;          /* JD block width b >= k (default min(k + 2, 32), at most 32) */
   int m_keep;         /* JD: Ritz vectors kept at each restart (default b + 2);
                          the paper's m_min (Section 3.2, Section 4) */
   int inner_maxit;    /* correction-solve PCG steps, ITMAX (default 20, Section 4) */

@@ -407,21 +407,13 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
   const int S = g->hg.nseg;
   const size_t es = dtype == LAP_F32 ? 4 : 8;
   const size_t n = (size_t)g->hg.n;
-  int rc = graph_scratch(g, 4 * n * b * es + 256, sizeof(double) * S * (64 * 6 + 33 * 32 * 2) + sizeof(int) * S * 64 + 1024);
+  int rc = graph_scratch(g, 4 * n * b * es + 256, sizeof(double) * S * 64 + 1024);
   if (rc) return rc;
-  PcgState ps;
-  double* base = g->small;
-  ps.rho = base;
-  ps.alpha = base + (size_t)S * 64;
-  ps.beta = base + (size_t)S * 128;
-  ps.res0 = base + (size_t)S * 192;
-  ps.resn = base + (size_t)S * 256;
-  double* th = base + (size_t)S * 320;
-  ps.G1 = base + (size_t)S * 384;
-  ps.G2 = ps.G1 + (size_t)S * 33 * 32;
-  ps.done = reinterpret_cast<int*>(ps.G2 + (size_t)S * 33 * 32);
-  ps.bstride = 64;
-  ps.gstride = 33 * 32;
+  if (!g->pcg.acc1) {
+    rc = g->pcg.init(S);
+    if (rc) return rc;
+  }
+  double* th = g->small;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaMemcpy2DAsync(th, 64 * sizeof(double), theta, b * sizeof(double), b * sizeof(double), S, cudaMemcpyDeviceToDevice,
                     s);
@@ -430,14 +422,11 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     T* Z = RES + n * b;
     T* P = Z + n * b;
     T* AP = P + n * b;
-    pcg_init<T>(g->dg, g->red, ps, (const T*)X, ldx, (const T*)R, ldr, (T*)Tout, RES, Z, P, b, b, nullptr, nullptr, s);
-    for (int it = 0; it < iters; ++it) {
-      spmm<T>(g->dg, P, b, AP, b, b, s);
-      pcg_step_b<T>(g->dg, g->red, ps, (const T*)X, ldx, P, AP, b, b, th, 64, nullptr, s);
-      pcg_step_c<T>(g->dg, g->red, ps, (const T*)X, ldx, P, AP, (T*)Tout, RES, Z, b, b, th, 64, delta, nullptr, s);
-      pcg_step_d<T>(g->dg, ps, (const T*)X, ldx, Z, P, b, b, nullptr, s);
-    }
+    const FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, b, b, th, 64, nullptr, nullptr, delta, iters,
+                                   g->d_long_seg);
+    if (pcg_fused<T>(g->dg, f, s, 0) != 0) return check_cuda("lap_pcg_correction launch");
   });
+  if (g->pcg.error_flag(s)) { set_error("grid barrier timed out"); return LAP_ETIMEOUT; }
   return check_cuda("lap_pcg_correction");
 }
 

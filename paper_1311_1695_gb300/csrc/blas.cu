@@ -343,30 +343,35 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   double* V = A + mm * LD;      // mm x LD
   double* cs = V + mm * LD;     // [mm/2][2]
   int* pq = reinterpret_cast<int*>(cs + mm);  // [mm/2][2]
-  __shared__ double s_off, s_nrm;
+  __shared__ double s_fro;
+  __shared__ int s_rot;
   const double* H = Hg + (size_t)seg * sh;
   for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
     const int i = e / mm, j = e % mm;
     A[i * LD + j] = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
     V[i * LD + j] = (i == j) ? 1.0 : 0.0;
   }
+  if (threadIdx.x == 0) s_fro = 0.0;
   __syncthreads();
+  {
+    double f = 0.0;
+    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+      const double a = A[(e / mm) * LD + (e % mm)];
+      f += a * a;
+    }
+    f = warp_sum(f);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_fro, f);
+  }
+  __syncthreads();
+  // A rotation is skipped when |a_pq| is negligible relative to its diagonal
+  // pair (high relative accuracy) or absolutely tiny against ||A||_F; the
+  // iteration stops after the first sweep that rotates nothing.
+  const double tol_abs = 1e-17 * sqrt(s_fro);
   int sweep = 0;
   const int half = mm / 2;
-  for (sweep = 0; sweep < 30; ++sweep) {
-    if (threadIdx.x == 0) { s_off = 0.0; s_nrm = 0.0; }
+  for (sweep = 0; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
-    double off = 0.0, nrm = 0.0;
-    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-      const int i = e / mm, j = e % mm;
-      const double a = A[i * LD + j];
-      if (i != j) off += a * a; else nrm += a * a;
-    }
-    off = warp_sum(off);
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) { atomicAdd(&s_off, off); atomicAdd(&s_nrm, nrm); }
-    __syncthreads();
-    if (!(s_off > 1e-32 * (s_nrm + s_off))) break;
     for (int step = 0; step < mm - 1; ++step) {
       if (threadIdx.x < half) {
         const int i = threadIdx.x;
@@ -376,11 +381,12 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
         const double apq = A[p * LD + q];
         double c = 1.0, s = 0.0;
         const double app = A[p * LD + p], aqq = A[q * LD + q];
-        if (apq != 0.0 && fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+        if (fabs(apq) > tol_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
           const double tau = (aqq - app) / (2.0 * apq);
           const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + tt * tt);
           s = tt * c;
+          s_rot = 1;
         }
         cs[2 * i] = c; cs[2 * i + 1] = s;
         pq[2 * i] = p; pq[2 * i + 1] = q;
@@ -414,6 +420,8 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
       }
       __syncthreads();
     }
+    if (s_rot == 0) break;
+    __syncthreads();
   }
   // sort the m real eigenvalues ascending (rank by counting; ties by index)
   double* ev = evals + (size_t)seg * se;

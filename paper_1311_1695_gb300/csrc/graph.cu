@@ -80,8 +80,15 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     return da != db ? da > db : a < b;
   });
   if (g->d_long) cudaFree(g->d_long);
+  if (g->d_long_seg) cudaFree(g->d_long_seg);
   g->d_long = nullptr;
+  g->d_long_seg = nullptr;
+  std::vector<int> hseg(hubs.size());
+  for (size_t h = 0; h < hubs.size(); ++h)
+    hseg[h] = (int)(std::upper_bound(g->row0.begin(), g->row0.end(), hubs[h]) - g->row0.begin()) - 1;
   int rc = dev_alloc_copy(&g->d_long, hubs.data(), hubs.size());
+  if (rc) return rc;
+  rc = dev_alloc_copy(&g->d_long_seg, hseg.data(), hseg.size());
   if (rc) return rc;
   g->long_rows_h = hubs;
   g->dg.long_rows = g->d_long;
@@ -214,8 +221,9 @@ void graph_free(lap_graph* g) {
   if (!g) return;
   cudaFree(g->d_rowptr); cudaFree(g->d_colidx); cudaFree(g->d_w32); cudaFree(g->d_w64);
   cudaFree(g->d_deg64); cudaFree(g->d_norm1); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
-  cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->red.acc); cudaFree(g->red.counter);
+  cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->red.acc); cudaFree(g->red.counter);
   cudaFree(g->scratch); cudaFree(g->small);
+  g->pcg.release();
   delete g;
 }
 
@@ -235,6 +243,57 @@ int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes) {
     g->small_bytes = small_bytes;
   }
   return LAP_OK;
+}
+
+}  // namespace lapeig
+
+namespace lapeig {
+
+int PcgWork::init(int nseg_) {
+  nseg = nseg_;
+  const size_t a = (size_t)nseg * acc_stride;
+  const size_t st = (size_t)nseg * 64;
+  const size_t bytes = sizeof(double) * (2 * a + 2 * st + 2 * st) + sizeof(int) * 2 * st + 64;
+  char* base = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("PCG workspace allocation failed");
+    return LAP_ENOMEM;
+  }
+  if (cudaMemset(base, 0, bytes) != cudaSuccess) { set_error("cudaMemset failed"); cudaFree(base); return LAP_ECUDA; }
+  acc1 = reinterpret_cast<double*>(base);
+  acc2 = acc1 + a;
+  rho = acc2 + a;
+  res0 = rho + 2 * st;
+  resn = res0 + st;
+  done = reinterpret_cast<int*>(resn + st);
+  bar = reinterpret_cast<unsigned*>(done + 2 * st);
+  return LAP_OK;
+}
+
+void PcgWork::release() {
+  cudaFree(acc1);
+  acc1 = nullptr;
+}
+
+FusedPcg PcgWork::args(const void* X, int ldx, const void* R, int ldr, void* Tt, void* RES, void* Z, void* P, void* AP,
+                       int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip,
+                       double delta, int itmax, const int* hub_seg) const {
+  FusedPcg f;
+  f.Xv = X; f.ldx = ldx; f.Rv = R; f.ldr = ldr; f.Ttv = Tt; f.RESv = RES; f.Zv = Z; f.Pv = P; f.APv = AP;
+  f.ld = ld; f.b = b; f.theta = theta; f.sth = sth; f.active = active; f.bstride = 64; f.seg_skip = seg_skip;
+  f.delta = delta; f.itmax = itmax; f.acc1 = acc1; f.acc2 = acc2; f.acc_stride = acc_stride; f.rho = rho;
+  f.done = done; f.res0 = res0; f.resn = resn; f.state_stride = (int64_t)nseg * 64; f.hub_seg = hub_seg;
+  f.bar.count = bar; f.bar.gen = bar + 1; f.bar.err = reinterpret_cast<int*>(bar + 2);
+  return f;
+}
+
+int PcgWork::error_flag(cudaStream_t s) const {
+  int e = 0;
+  cudaMemcpyAsync(&e, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (e) cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
+  return e;
 }
 
 }  // namespace lapeig

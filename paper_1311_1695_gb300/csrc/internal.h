@@ -7,6 +7,32 @@
 #include "../../include/lapeig.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "pcg_fused.cuh"
+
+namespace lapeig {
+
+// Device state of the persistent correction solve for a handle (sized for
+// b <= 32 and the handle's graph count); zero-initialised accumulators and
+// barrier, as the kernel expects.
+struct PcgWork {
+  double* acc1 = nullptr;
+  double* acc2 = nullptr;
+  double* rho = nullptr;
+  int* done = nullptr;
+  double* res0 = nullptr;
+  double* resn = nullptr;
+  unsigned* bar = nullptr;  // count, gen, err
+  int acc_stride = 33 * 32 + 3 * 32;
+  int nseg = 0;
+  int init(int nseg_);
+  void release();
+  FusedPcg args(const void* X, int ldx, const void* R, int ldr, void* Tt, void* RES, void* Z, void* P, void* AP,
+                int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip, double delta,
+                int itmax, const int* hub_seg) const;
+  int error_flag(cudaStream_t s) const;  // reads and clears the barrier error flag
+};
+
+}  // namespace lapeig
 
 struct lap_graph {
   lapeig::DevGraph dg{};
@@ -24,6 +50,7 @@ struct lap_graph {
   lapeig::Tile* d_tiles = nullptr;
   int* d_tile_ptr = nullptr;
   int* d_long = nullptr;
+  int* d_long_seg = nullptr;   // segment of each hub row
   // host copies
   std::vector<int> row0, tile_ptr;
   std::vector<double> norm1;
@@ -36,6 +63,7 @@ struct lap_graph {
   size_t scratch_bytes = 0;
   double* small = nullptr;      // FP64 per-segment scratch
   size_t small_bytes = 0;
+  lapeig::PcgWork pcg;          // persistent correction-solve state (lazy)
 };
 
 namespace lapeig {

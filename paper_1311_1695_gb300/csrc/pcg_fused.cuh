@@ -1,0 +1,44 @@
+// Arguments of the persistent correction-solve kernel (pcg.cu).
+#pragma once
+#include "common.cuh"
+
+namespace lapeig {
+
+struct GridBar {
+  unsigned* count;  // zero at rest
+  unsigned* gen;
+  int* err;         // set when a barrier gave up waiting
+};
+
+struct FusedPcg {
+  const void* Xv;      // Ritz block X (ldx), b columns
+  int ldx;
+  const void* Rv;      // residual block (ldr); must be orthogonal to [e, X]
+  int ldr;
+  void *Ttv, *RESv, *Zv, *Pv, *APv;  // n x ld work blocks; Tt receives the correction
+  int ld;
+  int b;
+  const double* theta;  // [nseg * sth]
+  int64_t sth;
+  const int* active;    // [nseg * bstride] or null (all active)
+  int bstride;
+  const int* seg_skip;  // [nseg] or null
+  double delta;
+  int itmax;
+  double* acc1;         // [nseg * acc_stride], zero at rest
+  double* acc2;
+  int acc_stride;
+  double* rho;          // [2 * state_stride]
+  int* done;            // [2 * state_stride]
+  double* res0;         // [state_stride]
+  double* resn;
+  int64_t state_stride; // nseg * bstride
+  const int* hub_seg;   // segment of each hub row
+  GridBar bar;
+};
+
+// Launch the whole correction solve; returns 0 or -1 (launch failure).
+template <typename T>
+int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas);
+
+}  // namespace lapeig

@@ -90,6 +90,7 @@ struct JD {
   std::vector<int> active_h, skip_h;
   int64_t n_matvec = 0;
   int inner_its = 0;
+  PcgWork* pw = nullptr;
 
   JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
 
@@ -225,12 +226,11 @@ struct JD {
       convert<TV, TP>(g, Rv, z.ldb, Rp, z.ldb, z.b, st);
       X = Xp; ldx = z.ldb; R = Rp; ldr = z.ldb;
     }
-    pcg_init<TP>(g, red, ps, X, ldx, R, ldr, Tt, RES, Zb, P, z.ldb, z.b, active, seg_skip, st);
-    for (int it = 0; it < itmax; ++it) {
-      spmm<TP>(g, P, z.ldb, AP, z.ldb, z.b, st);
-      pcg_step_b<TP>(g, red, ps, X, ldx, P, AP, z.ldb, z.b, theta, z.mmax, seg_skip, st);
-      pcg_step_c<TP>(g, red, ps, X, ldx, P, AP, Tt, RES, Zb, z.ldb, z.b, theta, z.mmax, delta, seg_skip, st);
-      pcg_step_d<TP>(g, ps, X, ldx, Zb, P, z.ldb, z.b, seg_skip, st);
+    const FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, z.ldb, z.b, theta, z.mmax, active, seg_skip,
+                                delta, itmax, G->d_long_seg);
+    if (pcg_fused<TP>(g, f, st, 0) != 0) {
+      set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+      return -1;
     }
     inner_its += itmax;
     int nact = 0;
@@ -336,6 +336,8 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     for (int s = 0; s < S; ++s) sk[s] = jd.skip_h[s] ? 1 : 0;
     cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
     m = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
+    if (m < 0) return LAP_ECUDA;
+    if (jd.pw->error_flag(jd.st)) { set_error("grid barrier in the correction solve timed out"); return LAP_ETIMEOUT; }
   }
   // make sure skip flags are cleared on the device for whatever comes next
   cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, jd.st);
@@ -395,7 +397,9 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   Params P;
   P.t0 = std::chrono::steady_clock::now();
   P.k = k;
-  P.b = o.block > 0 ? std::max(o.block, k) : k;
+  // default block: k plus two guard columns (they are corrected but need not
+  // converge; they keep a cluster that straddles k from being missed)
+  P.b = o.block > 0 ? std::max(o.block, k) : std::min(k + 2, 32);
   if (P.b > 32) { set_error("JD block width must be <= 32"); return LAP_EINVAL; }
   P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b) : P.b + 2;
   P.mk = std::min(P.mk, 64 - P.b);
@@ -423,6 +427,10 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   double* d_out = outa.take<double>((size_t)z.n * k);
   unsigned long long* d_best = outa.take<unsigned long long>(2 * (size_t)S * k);
 
+  PcgWork pw;
+  rc = pw.init(S);
+  if (rc) return rc;
+  struct PwGuard { PcgWork& p; ~PwGuard() { p.release(); } } pw_guard{pw};
   int outer = 0;
   const bool mixed = o.precision == LAP_PREC_MIXED;
   if (!mixed) {
@@ -431,6 +439,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     if (rc) return rc;
     JD<double, double> jd(G, z, st);
     jd.carve(a);
+    jd.pw = &pw;
     int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20);
     int m_out = m;
     const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
@@ -445,6 +454,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   if (rc) return rc;
   JD<float, float> j1(G, z, st);
   j1.carve(a1);
+  j1.pw = &pw;
   int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10);
   std::vector<double> tol1(S);
   for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
@@ -459,6 +469,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   if (rc) return rc;
   JD<double, float> j2(G, z, st);
   j2.carve(a2);
+  j2.pw = &pw;
   const int mk = std::min(m_out, z.mk);
   convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);
   j2.n_matvec = j1.n_matvec;
