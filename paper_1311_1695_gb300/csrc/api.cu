@@ -131,6 +131,9 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
   if (o.include_null) add_null(out, nrows, kk);
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  bool all_ok = true;
+  for (int s = 0; s < nb; ++s) all_ok = all_ok && out.info[s].status == LAP_OK;
+  if (rc == LAP_ENOCONV && all_ok) rc = LAP_OK;
   for (int s = 0; s < nb; ++s) {
     std::memcpy(evals[s], out.evals[s].data(), sizeof(double) * k);
     if (want && evecs[s]) std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k);

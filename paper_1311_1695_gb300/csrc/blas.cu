@@ -327,7 +327,7 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
     }
     for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = x[i];
   }
-  if (c < q && keep) keep[(size_t)seg * q + c] = kp[c];
+  if (c < q && keep) keep[(size_t)seg * 64 + c] = kp[c];
 }
 
 // Parallel cyclic Jacobi (round-robin ordering: m/2 disjoint rotations per step).

@@ -58,7 +58,7 @@ void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T
 // In-block orthonormalisation factor from S = T^T T (q x q): Cholesky with
 // dropping of columns whose pivot falls below drop * (initial diagonal), or
 // below drop itself when absolute is set; out
-// Rinv (q x q upper triangular, dropped columns zero) and keep[s*q + c].
+// Rinv (q x q upper triangular, dropped columns zero) and keep[s*64 + c].
 void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv,
               int64_t sr, int* keep, const int* seg_skip, cudaStream_t s);
 

@@ -366,7 +366,11 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
       worst = std::max(worst, r);
       if (prefix && r <= P.tol) ++nconv; else prefix = false;
     }
-    in.n_converged = status == LAP_OK ? P.k : nconv;
+    in.n_converged = nconv;
+    // per graph: a batch member whose k pairs all meet the test is converged
+    // even when another member hit the cap
+    if (status == LAP_ENOCONV && nconv == P.k) in.status = LAP_OK;
+    if (status == LAP_OK && nconv < P.k) in.status = LAP_ENOCONV;
     in.outer_its = outer;
     in.inner_its = jd.inner_its;
     in.n_matvec = jd.n_matvec;
