@@ -174,6 +174,24 @@ int lap_spmm(lap_graph* g, int dtype, const void* X, int ldx, void* Y, int ldy, 
 int lap_gram(lap_graph* g, int dtype, const void* A, int lda, int p, const void* B, int ldb, int q, int ones,
              double* G, void* stream);
 
+/* Allocation-free Gram product.  The paper has no counterpart: this exists
+ * for callers that may not allocate device memory -- a plug-in whose host
+ * framework owns all device memory through its own pool, or code on a
+ * latency-critical path where cudaMalloc/cudaFree (which can synchronise the
+ * device) are not acceptable.  Computes the same G = [1 | A]^T B as
+ * lap_gram for ONE graph's rows (n rows, no handle needed): G (device FP64)
+ * [(p + ones) x q] row-major, first row = column means of B when ones = 1.
+ * Limits: p + ones <= 65, q <= 64, p <= 64, n < 2^31; larger sizes return
+ * LAP_EINVAL.  Its reduction scratch is a fixed ~33 KB array in device
+ * global memory, held by every GPU that loads the library until the process
+ * exits; the first call on each device (with that device current) looks up
+ * the array's device address, so make that first call before any stream
+ * capture.  Each call clears the scratch it uses before reducing.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and give wrong results.  Allocates nothing. */
+int lap_gram_noalloc(int64_t n, int dtype, const void* A, int lda, int p, const void* B, int ldb, int q, int ones,
+                     double* G, void* stream);
+
 /* Deflation (Eq. 5): X <- X - e e^T X / n - Q Q^T X per graph, with Q
  * (device, nq orthonormal columns orthogonal to e; nq may be 0). */
 int lap_project(lap_graph* g, int dtype, const void* Q, int ldq, int nq, void* X, int ldx, int b, void* stream);

@@ -107,6 +107,7 @@ _SIGNATURES = {
     "lap_graph_set_schedule": (_I, [_P, _I, _I]),
     "lap_spmm": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gram": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
+    "lap_gram_noalloc": (_I, [_I64, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
     "lap_project": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _P]),
     "lap_cgs2": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _PI, _P]),
     "lap_syev_batched": (_I, [_I, _I, _P, _I, _P, _P, _I, _P]),
