@@ -330,47 +330,17 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
   if (c < q && keep) keep[(size_t)seg * 64 + c] = kp[c];
 }
 
-// Parallel cyclic Jacobi (round-robin ordering: m/2 disjoint rotations per step).
-__global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
-                                               double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
-                                               const int* __restrict__ seg_skip, int* sweeps_out) {
-  const int seg = blockIdx.x;
-  if (seg_skip && seg_skip[seg]) return;
-  extern __shared__ double sm[];
-  const int mm = (m + 1) & ~1;  // even
-  const int LD = mm + 1;
-  double* A = sm;               // mm x LD
-  double* V = A + mm * LD;      // mm x LD
-  double* cs = V + mm * LD;     // [mm/2][2]
-  int* pq = reinterpret_cast<int*>(cs + mm);  // [mm/2][2]
-  __shared__ double s_fro;
-  __shared__ int s_rot;
-  const double* H = Hg + (size_t)seg * sh;
-  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-    const int i = e / mm, j = e % mm;
-    A[i * LD + j] = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
-    V[i * LD + j] = (i == j) ? 1.0 : 0.0;
-  }
-  if (threadIdx.x == 0) s_fro = 0.0;
-  __syncthreads();
-  {
-    double f = 0.0;
-    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-      const double a = A[(e / mm) * LD + (e % mm)];
-      f += a * a;
-    }
-    f = warp_sum(f);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_fro, f);
-  }
-  __syncthreads();
-  // A rotation is skipped when |a_pq| is negligible relative to its diagonal
-  // pair (high relative accuracy) or absolutely tiny against ||A||_F; the
-  // iteration stops after the first sweep that rotates nothing.
-  const double tol_abs = 1e-17 * sqrt(s_fro);
-  int sweep = 0;
+// Parallel cyclic Jacobi sweeps (round-robin ordering: mm/2 disjoint
+// rotations per step) on A (mm x LD, symmetric) accumulating V <- V J.  A
+// rotation is skipped when |a_pq| <= rel * sqrt(|a_pp a_qq|) or <= abs_tol;
+// returns after the first sweep that rotates nothing (or max_sweeps).
+template <typename T>
+__device__ int jacobi_sweeps(T* A, T* V, int LD, int mm, T rel, T abs_tol, int max_sweeps, T* cs, int* pq,
+                             int* s_rot) {
   const int half = mm / 2;
-  for (sweep = 0; sweep < 40; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
+  int sweep = 0;
+  for (sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *s_rot = 0;
     __syncthreads();
     for (int step = 0; step < mm - 1; ++step) {
       if (threadIdx.x < half) {
@@ -378,65 +348,162 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
         auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
         int p = at(i), q = at(mm - 1 - i);
         if (p > q) { const int tmp = p; p = q; q = tmp; }
-        const double apq = A[p * LD + q];
-        double c = 1.0, s = 0.0;
-        const double app = A[p * LD + p], aqq = A[q * LD + q];
-        if (fabs(apq) > tol_abs && fabs(apq) > 1e-15 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + tt * tt);
-          s = tt * c;
-          s_rot = 1;
+        const T apq = A[p * LD + q];
+        T c = T(1), sn = T(0);
+        const T app = A[p * LD + p], aqq = A[q * LD + q];
+        if (fabs(apq) > abs_tol && fabs(apq) > rel * sqrt(fabs(app * aqq))) {
+          const T tau = (aqq - app) / (T(2) * apq);
+          const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + tt * tt);
+          sn = tt * c;
+          *s_rot = 1;
         }
-        cs[2 * i] = c; cs[2 * i + 1] = s;
+        cs[2 * i] = c; cs[2 * i + 1] = sn;
         pq[2 * i] = p; pq[2 * i + 1] = q;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {
+      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {  // rows: A <- J^T A
         const int i = e / mm, j = e % mm;
-        const double s = cs[2 * i + 1];
-        if (s == 0.0) continue;
-        const double c = cs[2 * i];
+        const T sn = cs[2 * i + 1];
+        if (sn == T(0)) continue;
+        const T c = cs[2 * i];
         const int p = pq[2 * i], q = pq[2 * i + 1];
-        const double ap = A[p * LD + j], aq = A[q * LD + j];
-        A[p * LD + j] = c * ap - s * aq;
-        A[q * LD + j] = s * ap + c * aq;
+        const T ap = A[p * LD + j], aq = A[q * LD + j];
+        A[p * LD + j] = c * ap - sn * aq;
+        A[q * LD + j] = sn * ap + c * aq;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {
+      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {  // columns: A <- A J, V <- V J
         const int i = e / mm, j = e % mm;
-        const double s = cs[2 * i + 1];
-        if (s == 0.0) continue;
-        const double c = cs[2 * i];
+        const T sn = cs[2 * i + 1];
+        if (sn == T(0)) continue;
+        const T c = cs[2 * i];
         const int p = pq[2 * i], q = pq[2 * i + 1];
-        const double ap = A[j * LD + p], aq = A[j * LD + q];
-        A[j * LD + p] = c * ap - s * aq;
-        A[j * LD + q] = s * ap + c * aq;
-        const double vp = V[j * LD + p], vq = V[j * LD + q];
-        V[j * LD + p] = c * vp - s * vq;
-        V[j * LD + q] = s * vp + c * vq;
+        const T ap = A[j * LD + p], aq = A[j * LD + q];
+        A[j * LD + p] = c * ap - sn * aq;
+        A[j * LD + q] = sn * ap + c * aq;
+        const T vp = V[j * LD + p], vq = V[j * LD + q];
+        V[j * LD + p] = c * vp - sn * vq;
+        V[j * LD + q] = sn * vp + c * vq;
       }
       __syncthreads();
     }
-    if (s_rot == 0) break;
+    const int any = *s_rot;
+    __syncthreads();
+    if (any == 0) break;
+  }
+  return sweep;
+}
+
+// Symmetric eigensolver, FP64 result, one CTA per matrix (m <= 64).
+// GB300 runs FP32 58x faster than FP64, so the rotations are first found in
+// FP32: FP32 Jacobi sweeps diagonalise fl32(H) to ~1e-7; the FP32
+// eigenvector matrix is then orthonormalised in FP64 (modified Gram-Schmidt),
+// B = Y^T H Y is formed in FP64 (nearly diagonal), and FP64 Jacobi sweeps
+// started from Y finish the job (typically one sweep plus one that finds
+// nothing to rotate).  The result has the accuracy of an all-FP64 Jacobi.
+__global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
+                                               double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
+                                               const int* __restrict__ seg_skip, int* sweeps_out) {
+  const int seg = blockIdx.x;
+  if (seg_skip && seg_skip[seg]) return;
+  extern __shared__ double sm[];
+  const int mm = (m + 1) & ~1;  // even; the padding index is uncoupled
+  const int LD = mm + 1;
+  double* A = sm;                                  // mm x LD
+  double* V = A + mm * LD;                         // mm x LD
+  double* Wd = V + mm * LD;                        // mm x LD (scratch), overlays A32/V32
+  float* A32 = reinterpret_cast<float*>(Wd);
+  float* V32 = A32 + mm * LD;
+  double* cs = Wd + mm * LD;                       // [mm]
+  float* cs32 = reinterpret_cast<float*>(cs);
+  int* pq = reinterpret_cast<int*>(cs + mm);       // [mm]
+  __shared__ double s_fro;
+  __shared__ int s_rot;
+  __shared__ double s_red[8];
+  const double* H = Hg + (size_t)seg * sh;
+  if (threadIdx.x == 0) s_fro = 0.0;
+  __syncthreads();
+  {
+    double f = 0.0;
+    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+      const int i = e / mm, j = e % mm;
+      const double a = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
+      A[i * LD + j] = a;
+      A32[i * LD + j] = (float)a;
+      V32[i * LD + j] = (i == j) ? 1.f : 0.f;
+      f += a * a;
+    }
+    f = warp_sum(f);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_fro, f);
+  }
+  __syncthreads();
+  const double fro = sqrt(s_fro);
+  // 1. FP32 sweeps
+  int sw32 = jacobi_sweeps<float>(A32, V32, LD, mm, 1e-7f, (float)(1e-9 * fro), 30, cs32, pq, &s_rot);
+  // 2. Y = V32 in FP64, orthonormalised by modified Gram-Schmidt (columns)
+  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) V[(e / mm) * LD + (e % mm)] = (double)V32[(e / mm) * LD + (e % mm)];
+  __syncthreads();
+  for (int j = 0; j < mm; ++j) {
+    double nrm = 0.0;
+    for (int r = threadIdx.x; r < mm; r += blockDim.x) nrm += V[r * LD + j] * V[r * LD + j];
+    nrm = warp_sum(nrm);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+      s_red[0] = 1.0 / sqrt(t);
+    }
+    __syncthreads();
+    const double inv = s_red[0];
+    for (int r = threadIdx.x; r < mm; r += blockDim.x) V[r * LD + j] *= inv;
+    __syncthreads();
+    // subtract column j from the later columns: one thread per later column
+    for (int l = j + 1 + threadIdx.x; l < mm; l += blockDim.x) {
+      double d = 0.0;
+      for (int r = 0; r < mm; ++r) d += V[r * LD + j] * V[r * LD + l];
+      for (int r = 0; r < mm; ++r) V[r * LD + l] -= d * V[r * LD + j];
+    }
     __syncthreads();
   }
-  // sort the m real eigenvalues ascending (rank by counting; ties by index)
+  // 3. B = Y^T A Y in FP64: Wd = A Y, then A <- Y^T Wd
+  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+    const int i = e / mm, j = e % mm;
+    double t = 0.0;
+    for (int r = 0; r < mm; ++r) t += A[i * LD + r] * V[r * LD + j];
+    Wd[i * LD + j] = t;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+    const int i = e / mm, j = e % mm;
+    if (j < i) continue;
+    double t = 0.0;
+    for (int r = 0; r < mm; ++r) t += V[r * LD + i] * Wd[r * LD + j];
+    A[i * LD + j] = t;
+    A[j * LD + i] = t;
+  }
+  __syncthreads();
+  // 4. FP64 sweeps from V = Y
+  const int sw64 = jacobi_sweeps<double>(A, V, LD, mm, 1e-15, 1e-17 * fro, 30, cs, pq, &s_rot);
+  // sort the m eigenvalues ascending (rank by counting; ties by index); the
+  // padding index (if any) is dropped: its column is e_{mm-1}, uncoupled
   double* ev = evals + (size_t)seg * se;
   double* Y = Yg + (size_t)seg * sy;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+    // identify real columns: the padding column has its weight in row mm-1
+    if (mm != m && fabs(V[(mm - 1) * LD + i]) > 0.5) continue;
     const double di = A[i * LD + i];
     int rank = 0;
-    for (int j = 0; j < m; ++j) {
+    for (int j = 0; j < mm; ++j) {
+      if (mm != m && fabs(V[(mm - 1) * LD + j]) > 0.5) continue;
       const double dj = A[j * LD + j];
       rank += (dj < di) || (dj == di && j < i);
     }
     ev[rank] = di;
     for (int r = 0; r < m; ++r) Y[(size_t)r * ldy + rank] = V[r * LD + i];
   }
-  if (sweeps_out && threadIdx.x == 0) sweeps_out[seg] = sweep;
+  if (sweeps_out && threadIdx.x == 0) sweeps_out[seg] = sw32 * 100 + sw64;
 }
 
 // ------------------------------------------------------------------ projected PCG passes
@@ -754,10 +821,10 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
           int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s) {
   LAP_PROF("syev", 0.0, s);
   const int mm = (m + 1) & ~1;
-  const size_t smem = sizeof(double) * (2 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
+  const size_t smem = sizeof(double) * (3 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
+    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
     attr_set = true;
   }
   k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out);

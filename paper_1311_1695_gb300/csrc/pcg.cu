@@ -67,56 +67,6 @@ __device__ bool grid_barrier(const GridBar& bar) {
 }
 
 template <typename T>
-__device__ __forceinline__ void stage_rows(T* dst, const T* __restrict__ src, int ld, int r0, int nr, int w) {
-  const int n = nr * w;
-  for (int e = threadIdx.x; e < n; e += kThreads) {
-    const int r = e / w, c = e - r * w;
-    dst[e] = src[(size_t)(r0 + r) * ld + c];
-  }
-}
-
-// acc[u] += sum_r [1|Xs][r, i] * Zs[r, j], output o = i*b + j, o = tid + 256 u
-template <typename T, int NO>
-__device__ __forceinline__ void gram_acc(const T* Xs, const T* Zs, int b, int nr, double (&acc)[NO]) {
-  const int nout = (b + 1) * b;
-#pragma unroll
-  for (int u = 0; u < NO; ++u) {
-    const int o = threadIdx.x + kThreads * u;
-    if (o < nout) {
-      const int i = o / b, j = o - (o / b) * b;
-      T s = T(0);
-      if (i == 0) {
-        for (int r = 0; r < nr; ++r) s += Zs[r * b + j];
-      } else {
-        const T* a = Xs + (i - 1);
-        for (int r = 0; r < nr; ++r) s += a[r * b] * Zs[r * b + j];
-      }
-      acc[u] += (double)s;
-    }
-  }
-}
-
-// Flush register partials (and per-column extras held in smem) into the
-// accumulators of segment seg.
-template <int NO>
-__device__ void flush(double* accs, int b, int nextra, double (&acc)[NO], double* ex) {
-  const int nout = (b + 1) * b;
-#pragma unroll
-  for (int u = 0; u < NO; ++u) {
-    const int o = threadIdx.x + kThreads * u;
-    if (o < nout && acc[u] != 0.0) atomicAdd(accs + o, acc[u]);
-    acc[u] = 0.0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nextra * b; e += kThreads) {
-    if (ex[e] != 0.0) atomicAdd(accs + nout + e, ex[e]);
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 3 * 32; e += kThreads) ex[e] = 0.0;
-  __syncthreads();
-}
-
-template <typename T>
 struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
@@ -124,350 +74,384 @@ struct View {
   int64_t state_stride; const int* hub_seg; GridBar bar;
 };
 
-template <typename T, int BMAX, int TEAM>
-__global__ void __launch_bounds__(kThreads) k_pcg_fused(DevGraph g, View<T> f) {
-  constexpr int CH = kThreads / TEAM;  // rows per chunk (one row per team)
-  constexpr int NO = (33 * 32 + kThreads - 1) / kThreads;
-  __shared__ T Xs[CH * BMAX];
-  __shared__ T Zs[CH * BMAX];
-  __shared__ T Gs[(BMAX + 1) * BMAX];
-  __shared__ double ex[3 * 32];  // per-column extras of the current segment
-  __shared__ T th_s[BMAX], al_s[BMAX], be_s[BMAX];
+// Per-thread accumulators of one phase for the current graph: thread (warp,
+// sub-row slot, column c) owns acc[0] = sum z_c, acc[1+i] = sum x_i z_c and
+// two per-column extras.  At a graph change (and at the end of the phase)
+// they are summed over the row slots of the warp (shuffles), over the warps
+// (shared memory), and added to the graph's FP64 accumulators with one
+// atomic per output per CTA.
+template <typename T, int BMAX, int BWL>
+__device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&ex)[2], double* red) {
+  constexpr int NW = kThreads / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL;
+  constexpr int NV = BMAX + 3;
+#pragma unroll
+  for (int o = BWL; o < 32; o <<= 1) {
+#pragma unroll
+    for (int i = 0; i <= BMAX; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    ex[0] += __shfl_xor_sync(0xffffffffu, ex[0], o);
+    ex[1] += __shfl_xor_sync(0xffffffffu, ex[1], o);
+  }
+  if (lane < BWL) {
+#pragma unroll
+    for (int i = 0; i <= BMAX; ++i) red[(warp * NV + i) * BWL + c] = (double)acc[i];
+    red[(warp * NV + BMAX + 1) * BWL + c] = (double)ex[0];
+    red[(warp * NV + BMAX + 2) * BWL + c] = (double)ex[1];
+  }
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
+  ex[0] = ex[1] = T(0);
+  __syncthreads();
+  const int nout = (b + 1) * b;
+  for (int o = threadIdx.x; o < nout + nextra * b; o += kThreads) {
+    int v, cc;
+    if (o < nout) { v = o / b; cc = o - v * b; }
+    else { v = BMAX + 1 + (o - nout) / b; cc = (o - nout) % b; }
+    double t = 0.0;
+    for (int w = 0; w < NW; ++w) t += red[(w * NV + v) * BWL + cc];
+    if (t != 0.0) atomicAdd(accs + o, t);
+  }
+  __syncthreads();
+}
+
+// Projection row update shared by phases B, C and init-C:
+//   y_c - G[0][c] - sum_i x_i G[i+1][c], x_i broadcast from the row's lanes.
+template <typename T, int BMAX, int BWL>
+__device__ __forceinline__ T project_col(T y, T xc, const T (&Gc)[BMAX + 1], int b) {
+  y -= Gc[0];
+#pragma unroll
+  for (int i = 0; i < BMAX; ++i) {
+    const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+    if (i < b) y -= xi * Gc[i + 1];
+  }
+  return y;
+}
+
+template <typename T, int BMAX, int BWL>
+__device__ __forceinline__ void gram_col(T (&acc)[BMAX + 1], T xc, T z, int b) {
+  acc[0] += z;
+#pragma unroll
+  for (int i = 0; i < BMAX; ++i) {
+    const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+    if (i < b) acc[i + 1] += xi * z;
+  }
+}
+
+template <typename T, int BMAX, int TEAM, int BWL>
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
+  extern __shared__ double red[];  // [warps][BMAX+3][BWL]
+  constexpr int RW = 32 / BWL;     // rows per warp pass
+  constexpr int NW = kThreads / 32;
   const int b = f.b;
   const int ld = f.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL;
+  const int slot = warp * RW + lane / BWL;  // row slot in the CTA
+  constexpr int SLOTS = NW * RW;
+  const bool colok = c < b;
   const int stride1 = f.acc_stride;
-  const T* deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
-  const T* __restrict__ w = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.w32 : (const void*)g.w64);
   const int nout = (b + 1) * b;
-  double acc[NO];
+  const T* __restrict__ deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
+  const T* __restrict__ w = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.w32 : (const void*)g.w64);
+  const T* __restrict__ X = f.X;
+  T acc[BMAX + 1];
+  T ex[2] = {T(0), T(0)};
 #pragma unroll
-  for (int u = 0; u < NO; ++u) acc[u] = 0.0;
-  for (int e = threadIdx.x; e < 3 * 32; e += kThreads) ex[e] = 0.0;
-  __syncthreads();
-
+  for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
+  T Gc[BMAX + 1];
   auto owner = [&](const Tile& t) { return t.idx_in_seg == 0; };
+  auto load_G = [&](const double* A, int seg) {
+    const double inv_n = 1.0 / (double)seg_rows(g, seg);
+#pragma unroll
+    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)(__ldcg(A + i * b + c) * (i == 0 ? inv_n : 1.0)) : T(0);
+  };
 
-  // ---------------------------------------------------------------- init: RES = -R, T = 0, z~ = RES/d
+  // ---------------------------------------------------------------- init
   {
     int cur = -1;
     for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
       const Tile t = g.tiles[ti];
       if (f.seg_skip && f.seg_skip[t.seg]) continue;
       if (t.seg != cur) {
-        if (cur >= 0) flush<NO>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex);
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
         cur = t.seg;
       }
-      const bool act = lane < b && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + lane]);
-      for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
-        const int nr = min(CH, t.r1 - c0);
-        __syncthreads();
-        stage_rows(Xs, f.X, f.ldx, c0, nr, b);
-        double rz = 0.0, rr = 0.0;
-        for (int r = warp; r < nr; r += kThreads / 32) {
-          if (lane < b) {
-            const size_t o = (size_t)(c0 + r) * ld + lane;
-            const T res = act ? -f.R[(size_t)(c0 + r) * f.ldr + lane] : T(0);
-            const T z = res / deg[c0 + r];
-            f.RES[o] = res;
-            f.Tt[o] = T(0);
-            f.Z[o] = z;
-            Zs[r * b + lane] = z;
-            rz += (double)res * (double)z;
-            rr += (double)res * (double)res;
-          }
-        }
-        if (lane < b) {
-          atomicAdd(&ex[lane], rz);
-          atomicAdd(&ex[b + lane], rr);
-        }
-        __syncthreads();
-        gram_acc<T, NO>(Xs, Zs, b, nr, acc);
+      const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
+      for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+        const size_t o = (size_t)r * ld + c;
+        const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
+        const T z = colok ? res / deg[r] : T(0);
+        if (colok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
+        gram_col<T, BMAX, BWL>(acc, xc, z, b);
+        ex[0] += res * z;
+        ex[1] += res * res;
       }
     }
-    if (cur >= 0) flush<NO>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex);
+    if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
   }
   if (!grid_barrier(f.bar)) return;
-  // init-C: p = z~ - [1|X] G2 (beta = 0); owner records rho, res0, done
+  // init-C: p = z~ - [1|X] G2; owner records rho, res0, done (parity 0)
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (f.seg_skip && f.seg_skip[t.seg]) continue;
     const double* A2 = f.acc2 + (size_t)t.seg * stride1;
-    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)(__ldcg(A2 + e) * (e < b ? inv_n : 1.0));
+    load_G(A2, t.seg);
     if (owner(t) && threadIdx.x < b) {
       const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
       const double rho = __ldcg(A2 + nout + threadIdx.x);
       const double r0 = sqrt(__ldcg(A2 + nout + b + threadIdx.x));
       const int act = f.active == nullptr || f.active[k];
-      f.rho[k] = rho;  // parity 0
+      f.rho[k] = rho;
       f.res0[k] = r0;
       f.resn[k] = r0;
       f.done[k] = (!act || r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
     }
-    for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
-      const int nr = min(CH, t.r1 - c0);
-      __syncthreads();
-      stage_rows(Xs, f.X, f.ldx, c0, nr, b);
-      __syncthreads();
-      for (int r = warp; r < nr; r += kThreads / 32) {
-        if (lane < b) {
-          const size_t o = (size_t)(c0 + r) * ld + lane;
-          T z = f.Z[o] - Gs[lane];
-          const T* xr = Xs + r * b;
-          for (int i = 0; i < b; ++i) z -= xr[i] * Gs[(i + 1) * b + lane];
-          f.P[o] = z;
-        }
-      }
+    for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+      const size_t o = (size_t)r * ld + c;
+      const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
+      const T z = project_col<T, BMAX, BWL>(colok ? f.Z[o] : T(0), xc, Gc, b);
+      if (colok) f.P[o] = z;
     }
   }
   if (!grid_barrier(f.bar)) return;
 
   for (int it = 0; it < f.itmax; ++it) {
     const int par = it & 1;
-    // ---------------------------------------------------------------- phase A
-    // owner zeroes acc2 (last read in the previous phase C / init-C)
+    // ---------------------------------------------------------------- phase A1: q~ = L p - theta p
     for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
       const Tile t = g.tiles[ti];
       if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
         for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = 0.0;
     }
     {
-      int cur = -1;
+      const int tl = threadIdx.x & (TEAM - 1);
+      const int tslot = threadIdx.x / TEAM;
+      constexpr int TSLOTS = kThreads / TEAM;
+      const unsigned tmask = (TEAM == 32) ? 0xffffffffu : (((1u << TEAM) - 1u) << ((threadIdx.x & 31) & ~(TEAM - 1)));
       for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
-        if (t.seg != cur) {
-          if (cur >= 0) flush<NO>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex);
-          cur = t.seg;
-          __syncthreads();
-          if (threadIdx.x < b) th_s[threadIdx.x] = (T)f.theta[(size_t)t.seg * f.sth + threadIdx.x];
-          __syncthreads();
-        }
-        for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
-          const int nr = min(CH, t.r1 - c0);
-          __syncthreads();
-          stage_rows(Xs, f.X, f.ldx, c0, nr, b);
-          // SpMM: team per row, all b columns in registers
-          {
-            const int tr = threadIdx.x / TEAM, tl = threadIdx.x & (TEAM - 1);
-            const int row = c0 + tr;
-            T a[BMAX];
+        const double* th = f.theta + (size_t)t.seg * f.sth;
+        for (int rb = t.r0; rb < t.r1; rb += TSLOTS) {
+          const int row = rb + tslot;
+          const bool valid = row < t.r1;
+          int p0 = 0, p1 = 0;
+          if (valid) { p0 = g.rowptr[row]; p1 = g.rowptr[row + 1]; }
+          const bool hub = valid && (p1 - p0 > g.long_thresh);
+          T a[BMAX];
 #pragma unroll
-            for (int c = 0; c < BMAX; ++c) a[c] = T(0);
-            T dsum = T(0);
-            int p0 = 0, p1 = 0;
-            const bool valid = tr < nr;
-            if (valid) { p0 = g.rowptr[row]; p1 = g.rowptr[row + 1]; }
-            const bool hub = valid && (p1 - p0 > g.long_thresh);
-            if (valid && !hub) {
-              for (int p = p0 + tl; p < p1; p += TEAM) {
-                const int j = __ldg(g.colidx + p);
-                const T wv = w ? __ldg(w + p) : T(1);
-                const T* xj = f.P + (size_t)j * ld;
+          for (int q = 0; q < BMAX; ++q) a[q] = T(0);
+          T dsum = T(0);
+          if (valid && !hub) {
+            for (int p = p0 + tl; p < p1; p += TEAM) {
+              const int j = __ldg(g.colidx + p);
+              const T wv = w ? __ldg(w + p) : T(1);
+              const T* xj = f.P + (size_t)j * ld;
+              if constexpr (sizeof(T) == 4) {
+                const float4* xv = reinterpret_cast<const float4*>(xj);
 #pragma unroll
-                for (int c = 0; c < BMAX; ++c)
-                  if (c < b) a[c] += wv * xj[c];
-                dsum += wv;
+                for (int q = 0; q < BMAX; q += 4)
+                  if (q < b) {
+                    const float4 v = __ldcg(xv + q / 4);
+                    a[q] += wv * v.x; a[q + 1] += wv * v.y; a[q + 2] += wv * v.z; a[q + 3] += wv * v.w;
+                  }
+              } else {
+                const double2* xv = reinterpret_cast<const double2*>(xj);
+#pragma unroll
+                for (int q = 0; q < BMAX; q += 2)
+                  if (q < b) {
+                    const double2 v = __ldcg(xv + q / 2);
+                    a[q] += wv * v.x; a[q + 1] += wv * v.y;
+                  }
               }
-            }
-            const unsigned mask = (TEAM == 32) ? 0xffffffffu : (((1u << TEAM) - 1u) << ((threadIdx.x & 31) & ~(TEAM - 1)));
-#pragma unroll
-            for (int o = TEAM / 2; o > 0; o >>= 1) {
-#pragma unroll
-              for (int c = 0; c < BMAX; ++c) a[c] += __shfl_xor_sync(mask, a[c], o);
-              dsum += __shfl_xor_sync(mask, dsum, o);
-            }
-            if (valid) {
-              const T d = w ? dsum : T(p1 - p0);
-              const T* pr = f.P + (size_t)row * ld;
-#pragma unroll
-              for (int c = 0; c < BMAX; ++c) {
-                if (c < b && (c % TEAM) == tl) {
-                  const T pv = pr[c];
-                  const T q = hub ? T(0) : d * pv - a[c] - th_s[c] * pv;
-                  if (!hub) f.AP[(size_t)row * ld + c] = q;
-                  Zs[tr * b + c] = q;
-                }
-              }
+              dsum += wv;
             }
           }
-          __syncthreads();
-          // p . q~ on the chunk (hub rows are zero in Zs)
-          double pq = 0.0;
-          for (int r = warp; r < nr; r += kThreads / 32)
-            if (lane < b) pq += (double)f.P[(size_t)(c0 + r) * ld + lane] * (double)Zs[r * b + lane];
-          if (lane < b) atomicAdd(&ex[lane], pq);
-          gram_acc<T, NO>(Xs, Zs, b, nr, acc);
-        }
-      }
-      if (cur >= 0) flush<NO>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex);
-      // hub rows, round-robin over the CTAs: whole-CTA reduction per row
-      for (int h = blockIdx.x; h < g.nlong; h += gridDim.x) {
-        const int row = g.long_rows[h];
-        const int seg = f.hub_seg[h];
-        if (f.seg_skip && f.seg_skip[seg]) continue;
-        const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-        T a[BMAX];
 #pragma unroll
-        for (int c = 0; c < BMAX; ++c) a[c] = T(0);
-        T dsum = T(0);
-        for (int p = p0 + threadIdx.x; p < p1; p += kThreads) {
-          const int j = __ldg(g.colidx + p);
-          const T wv = w ? __ldg(w + p) : T(1);
-          const T* xj = f.P + (size_t)j * ld;
+          for (int o = TEAM / 2; o > 0; o >>= 1) {
 #pragma unroll
-          for (int c = 0; c < BMAX; ++c)
-            if (c < b) a[c] += wv * xj[c];
-          dsum += wv;
-        }
-        __shared__ T red[kThreads / 32][BMAX + 1];
+            for (int q = 0; q < BMAX; ++q) a[q] += __shfl_xor_sync(tmask, a[q], o);
+            dsum += __shfl_xor_sync(tmask, dsum, o);
+          }
+          if (valid && !hub) {
+            const T d = w ? dsum : T(p1 - p0);
+            const T* pr = f.P + (size_t)row * ld;
+            T* apr = f.AP + (size_t)row * ld;
 #pragma unroll
-        for (int c = 0; c < BMAX; ++c) {
-          const T v = warp_sum(a[c]);
-          if (lane == 0) red[warp][c] = v;
+            for (int q = 0; q < BMAX; ++q)
+              if (q < b && (q % TEAM) == tl) {
+                const T pv = pr[q];
+                apr[q] = d * pv - a[q] - (T)th[q] * pv;
+              }
+          }
         }
-        {
-          const T v = warp_sum(dsum);
-          if (lane == 0) red[warp][BMAX] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < b) {
-          const int c = threadIdx.x;
-          T s = T(0), ds = T(0);
-          for (int q = 0; q < kThreads / 32; ++q) { s += red[q][c]; ds += red[q][BMAX]; }
-          const T d = w ? ds : T(p1 - p0);
-          const T pv = f.P[(size_t)row * ld + c];
-          const T q = d * pv - s - (T)f.theta[(size_t)seg * f.sth + c] * pv;
-          f.AP[(size_t)row * ld + c] = q;
-          Zs[c] = q;
-          Xs[c] = f.X[(size_t)row * f.ldx + c];
-          atomicAdd(f.acc1 + (size_t)seg * stride1 + nout + c, (double)pv * (double)q);
-        }
-        __syncthreads();
-        // this row's share of [1|X]^T q~
-        double* A1 = f.acc1 + (size_t)seg * stride1;
-        for (int o = threadIdx.x; o < nout; o += kThreads) {
-          const int i = o / b, j = o - i * b;
-          const double v = (double)(i == 0 ? Zs[j] : Xs[i - 1] * Zs[j]);
-          if (v != 0.0) atomicAdd(A1 + o, v);
-        }
-        __syncthreads();
       }
     }
-    if (!grid_barrier(f.bar)) return;
-    // ---------------------------------------------------------------- phase B
+    __syncthreads();
+    // ---------------------------------------------------------------- phase A2: G1 = [1|X]^T q~, p.q~ (own rows)
     {
       int cur = -1;
       for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
-          if (cur >= 0) flush<NO>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex);
+          if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
           cur = t.seg;
-          const double* A1 = f.acc1 + (size_t)t.seg * stride1;
-          const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-          __syncthreads();
-          for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)(__ldcg(A1 + e) * (e < b ? inv_n : 1.0));
-          if (threadIdx.x < b) {
-            const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-            const double pq = __ldcg(A1 + nout + threadIdx.x);
-            const double rho = f.rho[(size_t)par * f.state_stride + k];
-            const int dn = f.done[(size_t)par * f.state_stride + k];
-            double a = 0.0;
-            if (!dn && pq != 0.0 && isfinite(pq)) a = rho / pq;
-            al_s[threadIdx.x] = (T)a;
-            th_s[threadIdx.x] = (T)f.theta[(size_t)t.seg * f.sth + threadIdx.x];
-          }
-          __syncthreads();
         }
-        for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
-          const int nr = min(CH, t.r1 - c0);
-          __syncthreads();
-          stage_rows(Xs, f.X, f.ldx, c0, nr, b);
-          __syncthreads();
-          double rz = 0.0, rr = 0.0;
-          for (int r = warp; r < nr; r += kThreads / 32) {
-            if (lane < b) {
-              const size_t o = (size_t)(c0 + r) * ld + lane;
-              const T p = f.P[o];
-              T q = f.AP[o] - Gs[lane];
-              const T* xr = Xs + r * b;
-              for (int i = 0; i < b; ++i) q -= xr[i] * Gs[(i + 1) * b + lane];
-              const T al = al_s[lane];
-              f.Tt[o] += al * p;
-              const T res = f.RES[o] - al * q;
-              f.RES[o] = res;
-              const T z = res / deg[c0 + r];
-              f.Z[o] = z;
-              Zs[r * b + lane] = z;
-              rz += (double)res * (double)z;
-              rr += (double)res * (double)res;
-            }
-          }
-          if (lane < b) {
-            atomicAdd(&ex[lane], rz);
-            atomicAdd(&ex[b + lane], rr);
-          }
-          __syncthreads();
-          gram_acc<T, NO>(Xs, Zs, b, nr, acc);
+        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+          const bool hub = (g.rowptr[r + 1] - g.rowptr[r]) > g.long_thresh;
+          const size_t o = (size_t)r * ld + c;
+          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
+          const T q = (colok && !hub) ? f.AP[o] : T(0);
+          const T pv = colok ? f.P[o] : T(0);
+          gram_col<T, BMAX, BWL>(acc, xc, q, b);
+          ex[0] += pv * q;
         }
       }
-      if (cur >= 0) flush<NO>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex);
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
+    }
+    // hub rows, round-robin over the CTAs: whole-CTA reduction per row
+    for (int h = blockIdx.x; h < g.nlong; h += gridDim.x) {
+      const int row = g.long_rows[h];
+      const int seg = f.hub_seg[h];
+      if (f.seg_skip && f.seg_skip[seg]) continue;
+      const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+      T a[BMAX];
+#pragma unroll
+      for (int q = 0; q < BMAX; ++q) a[q] = T(0);
+      T dsum = T(0);
+      for (int p = p0 + threadIdx.x; p < p1; p += kThreads) {
+        const int j = __ldg(g.colidx + p);
+        const T wv = w ? __ldg(w + p) : T(1);
+        const T* xj = f.P + (size_t)j * ld;
+#pragma unroll
+        for (int q = 0; q < BMAX; ++q)
+          if (q < b) a[q] += wv * xj[q];
+        dsum += wv;
+      }
+      T* hred = reinterpret_cast<T*>(red);  // [NW][BMAX+1], then q~ [BMAX], x [BMAX]
+#pragma unroll
+      for (int q = 0; q < BMAX; ++q) {
+        const T v = warp_sum(a[q]);
+        if (lane == 0) hred[warp * (BMAX + 1) + q] = v;
+      }
+      {
+        const T v = warp_sum(dsum);
+        if (lane == 0) hred[warp * (BMAX + 1) + BMAX] = v;
+      }
+      __syncthreads();
+      T* qs = hred + NW * (BMAX + 1);
+      T* xs = qs + BMAX;
+      if (threadIdx.x < b) {
+        const int q = threadIdx.x;
+        T sum = T(0), ds = T(0);
+        for (int v = 0; v < NW; ++v) { sum += hred[v * (BMAX + 1) + q]; ds += hred[v * (BMAX + 1) + BMAX]; }
+        const T d = w ? ds : T(p1 - p0);
+        const T pv = f.P[(size_t)row * ld + q];
+        const T qq = d * pv - sum - (T)f.theta[(size_t)seg * f.sth + q] * pv;
+        f.AP[(size_t)row * ld + q] = qq;
+        qs[q] = qq;
+        xs[q] = X[(size_t)row * f.ldx + q];
+        atomicAdd(f.acc1 + (size_t)seg * stride1 + nout + q, (double)pv * (double)qq);
+      }
+      __syncthreads();
+      double* A1 = f.acc1 + (size_t)seg * stride1;
+      for (int o = threadIdx.x; o < nout; o += kThreads) {
+        const int i = o / b, j = o - i * b;
+        const double v = (double)(i == 0 ? qs[j] : xs[i - 1] * qs[j]);
+        if (v != 0.0) atomicAdd(A1 + o, v);
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(f.bar)) return;
+    // ---------------------------------------------------------------- phase B
+    {
+      int cur = -1;
+      T al = T(0);
+      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+        const Tile t = g.tiles[ti];
+        if (f.seg_skip && f.seg_skip[t.seg]) continue;
+        if (t.seg != cur) {
+          if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
+          cur = t.seg;
+          const double* A1 = f.acc1 + (size_t)t.seg * stride1;
+          load_G(A1, t.seg);
+          al = T(0);
+          if (colok) {
+            const size_t k = (size_t)t.seg * f.bstride + c;
+            const double pq = __ldcg(A1 + nout + c);
+            const double rho = f.rho[(size_t)par * f.state_stride + k];
+            const int dn = f.done[(size_t)par * f.state_stride + k];
+            if (!dn && pq != 0.0 && isfinite(pq)) al = (T)(rho / pq);
+          }
+        }
+        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+          const size_t o = (size_t)r * ld + c;
+          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
+          const T pv = colok ? f.P[o] : T(0);
+          const T qt = colok ? f.AP[o] : T(0);
+          const T tv = colok ? f.Tt[o] : T(0);
+          const T rv = colok ? f.RES[o] : T(0);
+          const T dv = deg[r];
+          const T q = project_col<T, BMAX, BWL>(qt, xc, Gc, b);
+          const T res = rv - al * q;
+          const T z = colok ? res / dv : T(0);
+          if (colok) { f.Tt[o] = tv + al * pv; f.RES[o] = res; f.Z[o] = z; }
+          gram_col<T, BMAX, BWL>(acc, xc, z, b);
+          ex[0] += colok ? res * z : T(0);
+          ex[1] += colok ? res * res : T(0);
+        }
+      }
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
     }
     if (!grid_barrier(f.bar)) return;
     // ---------------------------------------------------------------- phase C
-    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-      const Tile t = g.tiles[ti];
-      if (f.seg_skip && f.seg_skip[t.seg]) continue;
-      const double* A2 = f.acc2 + (size_t)t.seg * stride1;
-      const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-      __syncthreads();
-      for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)(__ldcg(A2 + e) * (e < b ? inv_n : 1.0));
-      if (threadIdx.x < b) {
-        const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-        const double rho_new = __ldcg(A2 + nout + threadIdx.x);
-        const double rn = sqrt(__ldcg(A2 + nout + b + threadIdx.x));
-        const double rho = f.rho[(size_t)par * f.state_stride + k];
-        int dn = f.done[(size_t)par * f.state_stride + k];
-        double be = 0.0;
-        if (!dn) {
-          if (rho != 0.0 && isfinite(rho_new)) be = rho_new / rho;
-          if (!(rn > f.delta * f.res0[k]) || !isfinite(rn)) dn = 1;
-        }
-        be_s[threadIdx.x] = (T)be;
-        if (owner(t)) {
-          f.rho[(size_t)(par ^ 1) * f.state_stride + k] = rho_new;
-          f.done[(size_t)(par ^ 1) * f.state_stride + k] = dn;
-          f.resn[k] = rn;
-        }
-      }
-      // owner zeroes acc1 (its last read was phase B)
-      if (owner(t))
-        for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = 0.0;
-      __syncthreads();
-      for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
-        const int nr = min(CH, t.r1 - c0);
-        __syncthreads();
-        stage_rows(Xs, f.X, f.ldx, c0, nr, b);
-        __syncthreads();
-        for (int r = warp; r < nr; r += kThreads / 32) {
-          if (lane < b) {
-            const size_t o = (size_t)(c0 + r) * ld + lane;
-            T z = f.Z[o] - Gs[lane];
-            const T* xr = Xs + r * b;
-            for (int i = 0; i < b; ++i) z -= xr[i] * Gs[(i + 1) * b + lane];
-            const T be = be_s[lane];
-            f.P[o] = (be == T(0)) ? z : z + be * f.P[o];
+    {
+      int cur = -1;
+      T be = T(0);
+      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+        const Tile t = g.tiles[ti];
+        if (f.seg_skip && f.seg_skip[t.seg]) continue;
+        if (t.seg != cur) {
+          cur = t.seg;
+          const double* A2 = f.acc2 + (size_t)t.seg * stride1;
+          load_G(A2, t.seg);
+          be = T(0);
+          if (colok) {
+            const size_t k = (size_t)t.seg * f.bstride + c;
+            const double rho_new = __ldcg(A2 + nout + c);
+            const double rn = sqrt(__ldcg(A2 + nout + b + c));
+            const double rho = f.rho[(size_t)par * f.state_stride + k];
+            int dn = f.done[(size_t)par * f.state_stride + k];
+            double bb = 0.0;
+            if (!dn) {
+              if (rho != 0.0 && isfinite(rho_new)) bb = rho_new / rho;
+              if (!(rn > f.delta * f.res0[k]) || !isfinite(rn)) dn = 1;
+            }
+            be = (T)bb;
+            if (owner(t) && threadIdx.x < 32 && lane < b && lane / BWL == 0 && warp == 0) {
+              f.rho[(size_t)(par ^ 1) * f.state_stride + k] = rho_new;
+              f.done[(size_t)(par ^ 1) * f.state_stride + k] = dn;
+              f.resn[k] = rn;
+            }
           }
+        }
+        if (owner(t))
+          for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = 0.0;
+        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+          const size_t o = (size_t)r * ld + c;
+          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
+          const T zt = colok ? f.Z[o] : T(0);
+          const T pv = colok ? f.P[o] : T(0);
+          const T z = project_col<T, BMAX, BWL>(zt, xc, Gc, b);
+          if (colok) f.P[o] = (be == T(0)) ? z : z + be * pv;
         }
       }
     }
     if (!grid_barrier(f.bar)) return;
   }
-  // leave acc1/acc2 zero for the next launch: acc1 was zeroed in the last
-  // phase C; acc2 is zeroed here by the owners (all reads are done).
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
@@ -477,11 +461,14 @@ __global__ void __launch_bounds__(kThreads) k_pcg_fused(DevGraph g, View<T> f) {
 
 template <typename T, int BMAX, int TEAM>
 int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
-  auto kern = k_pcg_fused<T, BMAX, TEAM>;
+  constexpr int BWL = BMAX <= 4 ? 4 : BMAX;  // lanes per row in the column phases
+  auto kern = k_pcg_fused<T, BMAX, TEAM, BWL>;
+  const size_t smem = sizeof(double) * (size_t)(kThreads / 32) * (BMAX + 3) * BWL;
+  cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   int grid = per_sm * nsm;
   if (max_ctas > 0) grid = grid < max_ctas ? grid : max_ctas;
   grid = grid < g.ntiles ? grid : g.ntiles;
@@ -492,7 +479,7 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
              f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar};
   void* args[] = {&gg, &ff};
-  const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, 0, s);
+  const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;
 }
 
