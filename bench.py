@@ -35,6 +35,8 @@ WORKLOAD_TEXT = {
     "c1": "Barabasi-Albert n=2,000 m=2, unit weights, 10 smallest pairs, tol 1e-8",
     "c2": "Chung-Lu gamma=2.2 n=22,000 (LCC) mean degree 4.2, unit weights, 20 smallest pairs, tol 1e-8",
     "c3": "Chung-Lu gamma=2.1 n=325,000 (LCC) mean degree 7 max ~1e4, unit weights, 10 smallest pairs, tol 1e-8",
+    "c4": "256 graphs, n log-uniform [500, 50,000]: Barabasi-Albert (m 2-4), Chung-Lu (gamma 2.0-2.8, mean degree 3-8), "
+          "2-D grids; 8 smallest pairs each, tol 1e-8, one lock-step batched solve",
     "c5": "Chung-Lu gamma=2.5 n=1,000,000 (LCC) mean degree 6, unit weights, 10 smallest pairs, tol 1e-8",
 }
 
@@ -47,6 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=list(WORKLOAD_TEXT))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--warm", default="random", choices=["random", "gnn"],
+                    help="start block: seeded random, or the trained message-passing network")
+    ap.add_argument("--autotune", action="store_true", help="autotune the SpMM schedule before timing")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ncu-window", action="store_true",
@@ -164,15 +169,31 @@ def bench_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     build.build()
-    k = graphgen.WORKLOADS[args.workload]["k"]
-    g = graphgen.workload_graph(args.workload)
-    n = g.n
+    if args.workload == "c4":
+        k = 8
+        graphs = [graphgen.graph_from_spec(sp_) for sp_ in graphgen.batch_specs(256)]
+    else:
+        k = graphgen.WORKLOADS[args.workload]["k"]
+        graphs = [graphgen.workload_graph(args.workload)]
+    g = graphs[0]
+    n = sum(x.n for x in graphs)
+    nnz_total = sum(int(x.nnz) for x in graphs)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    G = pkg.Graph(g)
+    G = pkg.Graph(graphs)
+    tuned = None
+    if args.autotune:
+        t_ = (ctypes_int(), ctypes_int())
+        pkg._check(pkg.lib().lap_graph_autotune(G.h, pkg.LAP_F32 if args.precision == "mixed" else pkg.LAP_F64,
+                                                 min(k + 2, 32), t_[0], t_[1], None), "autotune")
+        tuned = {"team": t_[0].value, "hub_threshold": t_[1].value}
     evecs = torch.empty(n * k, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     opts = dict(precision=args.precision, stream=sp)
+    gnn_params = None
+    if args.warm == "gnn":
+        from paper_1311_1695_gb300 import gnn as gnn_mod
+        gnn_params, _ = gnn_mod.load_params()
 
     def barrier():
         if world > 1:
@@ -181,8 +202,14 @@ def bench_ours(args):
 
     for _ in range(args.warmup):
         flush.zero_()
-        G.eigs(k, 1e-8, evecs=evecs, **opts)
+        if gnn_params is not None:
+            from paper_1311_1695_gb300 import gnn as gnn_mod
+            G.eigs(k, 1e-8, evecs=evecs, x0_dev=gnn_mod.warm_start(G, gnn_params), **opts)
+        else:
+            G.eigs(k, 1e-8, evecs=evecs, **opts)
     torch.cuda.synchronize()
+
+    infos_all_ = []
 
     def timed_loop(profile: bool):
         if profile:
@@ -196,11 +223,17 @@ def bench_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            ev, inf = G.eigs(k, 1e-8, evecs=evecs, **opts)
+            if gnn_params is not None:
+                from paper_1311_1695_gb300 import gnn as gnn_mod
+                x0 = gnn_mod.warm_start(G, gnn_params)
+                ev, inf = G.eigs(k, 1e-8, evecs=evecs, x0_dev=x0, **opts)
+            else:
+                ev, inf = G.eigs(k, 1e-8, evecs=evecs, **opts)
             e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
             infos.append(inf[0])
+            infos_all_[:] = inf
         torch.cuda.synchronize()
         barrier()
         prof = None
@@ -263,32 +296,58 @@ def bench_ours(args):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ev2, V2, inf2 = pkg.lap_eigs(g, k, 1e-8, precision=args.precision)
+            if len(graphs) > 1:
+                ev2, V2, infl = pkg.lap_eigs_batched(graphs, k, 1e-8, precision=args.precision)
+                inf2 = infl[0]
+            else:
+                ev2, V2, inf2 = pkg.lap_eigs(g, k, 1e-8, precision=args.precision)
             torch.cuda.synchronize()
             et.append((time.perf_counter() - t0) * 1e3)
-        h2d = 4 * (n + 1) + 4 * g.nnz + 12 * n
-        d2h = 8 * k + 8 * n * k + inf2["outer_its"] * 8 * (64 + 2 * k + 4) * 2
+        h2d = 4 * (n + len(graphs)) + 4 * nnz_total + 12 * n
+        d2h = 8 * k * len(graphs) + 8 * n * k + inf2["outer_its"] * 8 * (64 + 2 * k + 4) * 2 * len(graphs)
         e2e = {"value": round(sum(et) / len(et), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    compare = None
+    if args.workload == "c4" and rank == 0:
+        # the same 256 graphs solved one after another with plain FP64 JD, graphs resident
+        handles = [pkg.Graph(x) for x in graphs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h in handles:
+            h.eigs(k, 1e-8, precision="fp64", stream=sp)
+        torch.cuda.synchronize()
+        compare = {"sequential_fp64_ms": round((time.perf_counter() - t0) * 1e3, 1)}
+        for h in handles:
+            h.close()
+    if args.warm == "gnn" and rank == 0:
+        t0 = time.perf_counter()
+        _, infr = G.eigs(k, 1e-8, evecs=evecs, **opts)
+        torch.cuda.synchronize()
+        compare = {"random_start_ms": round((time.perf_counter() - t0) * 1e3, 1),
+                   "random_start_outer": infr[0]["outer_its"], "random_start_matvecs": infr[0]["n_matvec"]}
     base = None
-    if rank == 0 and world == 1 and not args.no_baseline:
+    if rank == 0 and world == 1 and not args.no_baseline and args.workload != "c4":
         bms, sample, d = run_oracle_sample(args.workload, k)
         base = {"value": round(bms, 1), "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
 
     inf = infos[-1]
+    infos_all = list(infos_all_) or [inf]
     out = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "graph": WORKLOAD_TEXT[args.workload], "n": n, "nnz": int(g.nnz),
+        "config": {"workload": args.workload, "graph": WORKLOAD_TEXT[args.workload], "n": n, "nnz": nnz_total,
+                   "graphs": len(graphs),
                    "k": k, "tol": 1e-8, "precision": args.precision, "method": "block Jacobi-Davidson",
                    "l2": "flushed before each step (256 MiB write)", "parallelism": f"replicas x{world}"},
         "result": {"outer_its": inf["outer_its"], "phase1_outer": inf["phase1_outer"], "n_matvec": inf["n_matvec"],
-                   "max_rel_residual": inf["max_rel_residual"], "lambda_2": float(ev[0][0]),
-                   "lambda_k+1": float(ev[0][k - 1]), "step_ms": [round(x, 3) for x in times]},
+                   "max_rel_residual": max(i_["max_rel_residual"] for i_ in infos_all),
+                   "lambda_2": float(ev[0][0]), "lambda_k+1": float(ev[0][k - 1]),
+                   "step_ms": [round(x, 3) for x in times]},
         "roofline": roofline, "spmm_roofline": spmm_roof, "kernels": kern_table,
         "gpu_launches": int(launches) * args.steps, "clocks": clk, "e2e": e2e, "cpu_baseline": base,
+        "compare": compare, "schedule": tuned, "start": args.warm,
     }
     G.close()
     if rank == 0:
@@ -296,6 +355,11 @@ def bench_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ctypes_int():
+    import ctypes
+    return ctypes.c_int()
 
 
 def traffic_for(kernel: str, workload: str):

@@ -76,8 +76,12 @@ typedef struct {
   int k0;
   void* stream;       /* cudaStream_t for all device work (NULL = default) */
   double max_seconds; /* wall-clock cap (0 = none) -> LAP_ETIMEOUT */
-  int team;           /* SpMM lanes per row: 4, 8, 16, 32 (0 = autotuned) */
+  int team;           /* SpMM lanes per row: 4, 8, 16, 32; 0 = degree heuristic;
+                         -1 = autotune on the graph (timed trial launches) */
   int verbose;        /* 1: per-iteration log on stderr */
+  const double* x0_dev; /* optional device warm start, row-major n x k0 (ld = ldx0), FP64;
+                           used instead of x0 when set (single-graph solves) */
+  int ldx0;
 } lap_opts;
 
 typedef struct {
@@ -158,6 +162,31 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
  * name_len bytes each), then clears the totals.  Not thread-safe. */
 int lap_profile_enable(int on);
 int lap_profile_read(int max, char* names, int name_len, double* ms, double* bytes, int64_t* launches, int* count);
+
+/* ---------------------------------------------------------------- learned warm start
+ * Kernels of a small message-passing network that proposes the initial
+ * Jacobi-Davidson block (no counterpart in the paper).  All blocks are FP32
+ * device arrays, row-major, over all rows of the handle.
+ *   lap_gnn_features : F[:, 0] = 1, F[:, 1] = log(1 + d_i) / log(1 + d_max),
+ *                      F[:, 2:nfeat] = SplitMix64 uniform(-1, 1) (counter
+ *                      local_row * nfeat + column).
+ *   lap_gnn_aggregate: Y = D^{-1} A X (transpose = 0) or A D^{-1} X (transpose = 1),
+ *                      w <= 32 columns.
+ *   lap_gnn_tanh     : mode 0 Z <- tanh(Z); mode 1 Z <- Z * (1 - H^2).
+ * lap_block_update: Y[:, 0:q] = beta Y + alpha [1 | A] S_s per graph s, with S
+ * device FP64 ((p + ones) x q, row stride lds, graph stride ss); the dense
+ * layers and the loss gradient of the network, usable for any block update. */
+int lap_gnn_features(lap_graph* g, uint64_t seed, int nfeat, float* F, int ldf, void* stream);
+int lap_gnn_aggregate(lap_graph* g, int transpose, const float* X, int ldx, float* Y, int ldy, int w, void* stream);
+int lap_gnn_tanh(lap_graph* g, int mode, float* Z, int ldz, const float* H, int ldh, int w, void* stream);
+int lap_block_update(lap_graph* g, int dtype, void* Y, int ldy, int q, double beta, double alpha, const void* A,
+                     int lda, int p, int ones, const double* S, int lds, int64_t ss, void* stream);
+
+/* Autotune the SpMM schedule of the handle: time the degree-fused SpMM on a
+ * b-column block of dtype for lanes-per-row 4, 8, 16, 32 and several hub
+ * thresholds with CUDA events, keep the fastest (returned in team/thresh,
+ * nullable).  Allocates a scratch block for the trial. */
+int lap_graph_autotune(lap_graph* g, int dtype, int b, int* team, int* thresh, void* stream);
 
 /* ---------------------------------------------------------------- step-level entry points
  * The steps of the Jacobi-Davidson outer loop on device blocks (row-major,

@@ -1,0 +1,114 @@
+"""The warm-start message-passing network and its subspace loss, in FP64.
+
+The paper has no learned component; this is the definition the GPU's
+training and inference kernels are checked against.  Network (width w = 32):
+
+  H_0 = F                                   (n x f node features)
+  Z_l = (M H_l) W_l + H_l U_l + 1 b_l^T     M = D^{-1} A (mean over neighbours)
+  H_{l+1} = tanh(Z_l),  l = 0, 1, 2
+  X = H_3 W_out                             (n x k proposed start block)
+
+Loss, invariant to the sign and rotation of the target eigenvectors U
+(n x k, orthonormal) and to any invertible recombination of X's columns:
+
+  loss(X) = 1 - tr((X^T X)^{-1} X^T U U^T X) / k
+
+which is 0 exactly when span(X) = span(U).  Its gradient is
+  dloss/dX = -(2/k) (U (U^T X) G^{-1} - X G^{-1} (X^T U)(U^T X) G^{-1}),  G = X^T X.
+
+Node features: column 0 = 1, column 1 = log(1 + d_i) / log(1 + d_max), the
+rest uniform(-1, 1) from SplitMix64 (counter node * f + column).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .laplacian import Laplacian
+from .rng import splitmix64
+
+WIDTH = 32
+LAYERS = 3
+NFEAT = 16
+
+
+def features(g, seed: int, nfeat: int = NFEAT) -> np.ndarray:
+    lap = Laplacian(g)
+    d = lap.d
+    F = np.empty((g.n, nfeat))
+    F[:, 0] = 1.0
+    F[:, 1] = np.log1p(d) / np.log1p(d.max())
+    z = splitmix64(seed, np.arange(g.n * nfeat, dtype=np.uint64)).reshape(g.n, nfeat)
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    F[:, 2:] = (2.0 * u - 1.0)[:, 2:]
+    return F
+
+
+def param_shapes(k: int, nfeat: int = NFEAT, width: int = WIDTH):
+    shapes = []
+    fin = nfeat
+    for _ in range(LAYERS):
+        shapes += [("W", (fin, width)), ("U", (fin, width)), ("b", (width,))]
+        fin = width
+    shapes.append(("Wout", (width, k)))
+    return shapes
+
+
+def init_params(k: int, seed: int = 0, nfeat: int = NFEAT, width: int = WIDTH):
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shp in param_shapes(k, nfeat, width):
+        if name == "b":
+            out.append(np.zeros(shp))
+        else:
+            out.append(rng.standard_normal(shp) / np.sqrt(shp[0]))
+    return out
+
+
+def _mean_agg(g, H):
+    lap = Laplacian(g)
+    return (lap.A @ H) / lap.d[:, None]
+
+
+def _mean_agg_T(g, H):
+    lap = Laplacian(g)
+    return lap.A @ (H / lap.d[:, None])
+
+
+def forward(g, F, params):
+    H = F
+    cache = []
+    for l in range(LAYERS):
+        W, U, b = params[3 * l: 3 * l + 3]
+        MH = _mean_agg(g, H)
+        Z = MH @ W + H @ U + b[None, :]
+        Hn = np.tanh(Z)
+        cache.append((H, MH, Hn))
+        H = Hn
+    X = H @ params[-1]
+    return X, cache
+
+
+def backward(g, cache, params, dX):
+    grads = [None] * len(params)
+    H3 = cache[-1][2]
+    grads[-1] = H3.T @ dX
+    dH = dX @ params[-1].T
+    for l in reversed(range(LAYERS)):
+        H, MH, Hn = cache[l]
+        W, U, b = params[3 * l: 3 * l + 3]
+        dZ = dH * (1.0 - Hn * Hn)
+        grads[3 * l] = MH.T @ dZ
+        grads[3 * l + 1] = H.T @ dZ
+        grads[3 * l + 2] = dZ.sum(axis=0)
+        dH = _mean_agg_T(g, dZ @ W.T) + dZ @ U.T
+    return grads
+
+
+def subspace_loss(X, U):
+    k = U.shape[1]
+    Gm = X.T @ X
+    Gi = np.linalg.inv(Gm)
+    UX = U.T @ X
+    loss = 1.0 - np.trace(Gi @ UX.T @ UX) / k
+    dX = -(2.0 / k) * (U @ UX @ Gi - X @ Gi @ UX.T @ UX @ Gi)
+    return loss, dX

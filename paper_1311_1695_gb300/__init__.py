@@ -55,6 +55,8 @@ class lap_opts(ctypes.Structure):
         ("max_seconds", ctypes.c_double),
         ("team", ctypes.c_int),
         ("verbose", ctypes.c_int),
+        ("x0_dev", ctypes.c_void_p),
+        ("ldx0", ctypes.c_int),
     ]
 
 
@@ -108,6 +110,11 @@ _SIGNATURES = {
     "lap_spmm": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gram": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
     "lap_gram_noalloc": (_I, [_I64, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
+    "lap_gnn_features": (_I, [_P, ctypes.c_uint64, _I, _P, _I, _P]),
+    "lap_gnn_aggregate": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
+    "lap_gnn_tanh": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
+    "lap_block_update": (_I, [_P, _I, _P, _I, _I, _D, _D, _P, _I, _I, _I, _P, _I, _I64, _P]),
+    "lap_graph_autotune": (_I, [_P, _I, _I, _PI, _PI, _P]),
     "lap_project": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _P]),
     "lap_cgs2": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _PI, _P]),
     "lap_syev_batched": (_I, [_I, _I, _P, _I, _P, _P, _I, _P]),
@@ -157,7 +164,8 @@ def _ptr(a, ct):
 
 
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
-              include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False):
+              include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
+              x0_dev=None):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -168,6 +176,10 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.max_seconds, o.team, o.verbose = max_seconds, team, int(bool(verbose))
     o.stream = stream
     keep = None
+    if x0_dev is not None:  # a row-major float64 CUDA tensor n x k0
+        o.x0_dev = ctypes.c_void_p(x0_dev.data_ptr())
+        o.ldx0 = x0_dev.stride(0)
+        o.k0 = x0_dev.shape[1]
     if x0 is not None:
         keep = np.asfortranarray(x0, dtype=np.float64)
         o.x0 = keep.ctypes.data_as(_PD)

@@ -65,6 +65,14 @@ void add_null(SolveOut& out, const std::vector<int>& nrows, int kk) {
   }
 }
 
+// opts.team: > 0 fixed lanes per row, -1 autotuned on the graph
+int apply_team(lap_graph* g, const lap_opts& o, int k) {
+  if (o.team > 0) return graph_set_schedule(g, o.team, 0);
+  const int b = o.block > 0 ? std::max(o.block, k) : std::min(k + 2, 32);
+  return graph_autotune(g, o.precision == LAP_PREC_MIXED ? LAP_F32 : LAP_F64, std::min(b, 32), nullptr, nullptr,
+                        reinterpret_cast<cudaStream_t>(o.stream));
+}
+
 }  // namespace
 }  // namespace lapeig
 
@@ -121,7 +129,7 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
   int rc = graph_build(nb, n, rowptr, colidx, weights, &g);
   if (rc) return rc;
   if (o.team) {
-    rc = graph_set_schedule(g, o.team, 0);
+    rc = apply_team(g, o, k);
     if (rc) { graph_free(g); return rc; }
   }
   SolveOut out;
@@ -162,7 +170,7 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   int rc = graph_build(1, &n, rp, ci, w, &g);
   if (rc) return rc;
   if (o.team) {
-    rc = graph_set_schedule(g, o.team, 0);
+    rc = apply_team(g, o, k);
     if (rc) { graph_free(g); return rc; }
   }
   SolveOut out;
@@ -197,7 +205,7 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
   }
   if (o.include_null && evecs_dev) { set_error("include_null needs host eigenvectors (use lap_eigs)"); return LAP_EINVAL; }
   if (o.team) {
-    const int rc = graph_set_schedule(g, o.team, 0);
+    const int rc = apply_team(g, o, k);
     if (rc) return rc;
   }
   SolveOut out;

@@ -73,6 +73,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
                 const double* const* weights, lap_graph** out);
 void graph_free(lap_graph* g);
 int graph_set_schedule(lap_graph* g, int team, int long_thresh);
+int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_out, cudaStream_t s);
 // Ensure the handle's step-level scratch holds at least `bytes` (device).
 int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes);
 

@@ -19,6 +19,11 @@
 // no CTA reads a value while another rewrites it.  Accumulators are zeroed
 // by that owner one phase after their last read.
 //
+// Data written by another CTA inside the launch (gathered P rows, hub rows,
+// the persistent scalars, the accumulators) is read with L2 loads (__ldcg):
+// L1 is not coherent across SMs.  Rows a CTA owns are only ever written and
+// read by that CTA.
+//
 // Co-residency of all CTAs is guaranteed by the cooperative launch; the
 // barrier still bounds its spin and raises an error flag (the kernel then
 // returns early and the host reports LAP_ETIMEOUT) rather than hang.
@@ -71,7 +76,7 @@ struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
   double delta; int itmax; double *acc1, *acc2; int acc_stride; double* rho; int* done; double *res0, *resn;
-  int64_t state_stride; const int* hub_seg; GridBar bar;
+  int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int vec;
 };
 
 // Per-thread accumulators of one phase for the current graph: thread (warp,
@@ -178,12 +183,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         cur = t.seg;
       }
       const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-      for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
+      for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
+        const int r = rg + lane / BWL;
+        const bool rv_ = r < t.r1;
+        const bool ok = colok && rv_;
         const size_t o = (size_t)r * ld + c;
-        const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
-        const T z = colok ? res / deg[r] : T(0);
-        if (colok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
+        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T res = (ok && act) ? -f.R[(size_t)r * f.ldr + c] : T(0);
+        const T z = ok ? res / deg[r] : T(0);
+        if (ok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
         gram_col<T, BMAX, BWL>(acc, xc, z, b);
         ex[0] += res * z;
         ex[1] += res * res;
@@ -208,12 +216,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
       f.resn[k] = r0;
       f.done[k] = (!act || r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
     }
-    for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
-      const size_t o = (size_t)r * ld + c;
-      const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
-      const T z = project_col<T, BMAX, BWL>(colok ? f.Z[o] : T(0), xc, Gc, b);
-      if (colok) f.P[o] = z;
-    }
+    for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
+        const int r = rg + lane / BWL;
+        const bool rv_ = r < t.r1;
+        const bool ok = colok && rv_;
+        const size_t o = (size_t)r * ld + c;
+        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T z = project_col<T, BMAX, BWL>(ok ? f.Z[o] : T(0), xc, Gc, b);
+        if (ok) f.P[o] = z;
+      }
   }
   if (!grid_barrier(f.bar)) return;
 
@@ -249,7 +260,11 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
               const int j = __ldg(g.colidx + p);
               const T wv = w ? __ldg(w + p) : T(1);
               const T* xj = f.P + (size_t)j * ld;
-              if constexpr (sizeof(T) == 4) {
+              if (!f.vec) {
+#pragma unroll
+                for (int q = 0; q < BMAX; ++q)
+                  if (q < b) a[q] += wv * __ldcg(xj + q);
+              } else if constexpr (sizeof(T) == 4) {
                 const float4* xv = reinterpret_cast<const float4*>(xj);
 #pragma unroll
                 for (int q = 0; q < BMAX; q += 4)
@@ -300,15 +315,18 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
           if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
           cur = t.seg;
         }
-        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
-          const bool hub = (g.rowptr[r + 1] - g.rowptr[r]) > g.long_thresh;
-          const size_t o = (size_t)r * ld + c;
-          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
-          const T q = (colok && !hub) ? f.AP[o] : T(0);
-          const T pv = colok ? f.P[o] : T(0);
-          gram_col<T, BMAX, BWL>(acc, xc, q, b);
-          ex[0] += pv * q;
-        }
+        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
+        const int r = rg + lane / BWL;
+        const bool rv_ = r < t.r1;
+        const bool ok = colok && rv_;
+        const bool hub = rv_ && (g.rowptr[r + 1] - g.rowptr[r]) > g.long_thresh;
+        const size_t o = (size_t)r * ld + c;
+        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T q = (ok && !hub) ? f.AP[o] : T(0);
+        const T pv = ok ? f.P[o] : T(0);
+        gram_col<T, BMAX, BWL>(acc, xc, q, b);
+        ex[0] += pv * q;
+      }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
     }
@@ -328,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         const T* xj = f.P + (size_t)j * ld;
 #pragma unroll
         for (int q = 0; q < BMAX; ++q)
-          if (q < b) a[q] += wv * xj[q];
+          if (q < b) a[q] += wv * __ldcg(xj + q);
         dsum += wv;
       }
       T* hred = reinterpret_cast<T*>(red);  // [NW][BMAX+1], then q~ [BMAX], x [BMAX]
@@ -349,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         T sum = T(0), ds = T(0);
         for (int v = 0; v < NW; ++v) { sum += hred[v * (BMAX + 1) + q]; ds += hred[v * (BMAX + 1) + BMAX]; }
         const T d = w ? ds : T(p1 - p0);
-        const T pv = f.P[(size_t)row * ld + q];
+        const T pv = __ldcg(f.P + (size_t)row * ld + q);
         const T qq = d * pv - sum - (T)f.theta[(size_t)seg * f.sth + q] * pv;
         f.AP[(size_t)row * ld + q] = qq;
         qs[q] = qq;
@@ -382,32 +400,37 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
           if (colok) {
             const size_t k = (size_t)t.seg * f.bstride + c;
             const double pq = __ldcg(A1 + nout + c);
-            const double rho = f.rho[(size_t)par * f.state_stride + k];
-            const int dn = f.done[(size_t)par * f.state_stride + k];
+            const double rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
+            const int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
             if (!dn && pq != 0.0 && isfinite(pq)) al = (T)(rho / pq);
           }
         }
-        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
-          const size_t o = (size_t)r * ld + c;
-          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
-          const T pv = colok ? f.P[o] : T(0);
-          const T qt = colok ? f.AP[o] : T(0);
-          const T tv = colok ? f.Tt[o] : T(0);
-          const T rv = colok ? f.RES[o] : T(0);
-          const T dv = deg[r];
-          const T q = project_col<T, BMAX, BWL>(qt, xc, Gc, b);
-          const T res = rv - al * q;
-          const T z = colok ? res / dv : T(0);
-          if (colok) { f.Tt[o] = tv + al * pv; f.RES[o] = res; f.Z[o] = z; }
-          gram_col<T, BMAX, BWL>(acc, xc, z, b);
-          ex[0] += colok ? res * z : T(0);
-          ex[1] += colok ? res * res : T(0);
-        }
+        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
+        const int r = rg + lane / BWL;
+        const bool rv_ = r < t.r1;
+        const bool ok = colok && rv_;
+        const size_t o = (size_t)r * ld + c;
+        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T pv = ok ? f.P[o] : T(0);
+        const T qt = ok ? __ldcg(f.AP + o) : T(0);
+        const T tv = ok ? f.Tt[o] : T(0);
+        const T rv = ok ? f.RES[o] : T(0);
+        const T dv = rv_ ? deg[r] : T(1);
+        const T q = project_col<T, BMAX, BWL>(qt, xc, Gc, b);
+        const T res = rv - al * q;
+        const T z = ok ? res / dv : T(0);
+        if (ok) { f.Tt[o] = tv + al * pv; f.RES[o] = res; f.Z[o] = z; }
+        gram_col<T, BMAX, BWL>(acc, xc, z, b);
+        ex[0] += ok ? res * z : T(0);
+        ex[1] += ok ? res * res : T(0);
+      }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
     }
     if (!grid_barrier(f.bar)) return;
     // ---------------------------------------------------------------- phase C
+    int all_known = 0;
+    __shared__ int s_all;
     {
       int cur = -1;
       T be = T(0);
@@ -423,12 +446,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
             const size_t k = (size_t)t.seg * f.bstride + c;
             const double rho_new = __ldcg(A2 + nout + c);
             const double rn = sqrt(__ldcg(A2 + nout + b + c));
-            const double rho = f.rho[(size_t)par * f.state_stride + k];
-            int dn = f.done[(size_t)par * f.state_stride + k];
+            const double rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
+            int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
             double bb = 0.0;
             if (!dn) {
               if (rho != 0.0 && isfinite(rho_new)) bb = rho_new / rho;
-              if (!(rn > f.delta * f.res0[k]) || !isfinite(rn)) dn = 1;
+              if (!(rn > f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
             }
             be = (T)bb;
             if (owner(t) && threadIdx.x < 32 && lane < b && lane / BWL == 0 && warp == 0) {
@@ -440,17 +463,34 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         }
         if (owner(t))
           for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = 0.0;
-        for (int r = t.r0 + slot; r < t.r1; r += SLOTS) {
-          const size_t o = (size_t)r * ld + c;
-          const T xc = colok ? X[(size_t)r * f.ldx + c] : T(0);
-          const T zt = colok ? f.Z[o] : T(0);
-          const T pv = colok ? f.P[o] : T(0);
-          const T z = project_col<T, BMAX, BWL>(zt, xc, Gc, b);
-          if (colok) f.P[o] = (be == T(0)) ? z : z + be * pv;
+        if (f.early_exit && !all_known) {
+          // every CTA derives the same per-column decisions from the same
+          // totals, so the exit below is taken by all CTAs together
+          int mine = 1;
+          if (threadIdx.x < b) {
+            const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
+            const double rn = sqrt(__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
+            const int d0 = __ldcg(f.done + (size_t)par * f.state_stride + k);
+            mine = d0 || !(rn > f.delta * __ldcg(f.res0 + k)) || !isfinite(rn);
+          }
+          s_all = __syncthreads_and(mine);
+          all_known = 1;
         }
+        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
+        const int r = rg + lane / BWL;
+        const bool rv_ = r < t.r1;
+        const bool ok = colok && rv_;
+        const size_t o = (size_t)r * ld + c;
+        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+        const T zt = ok ? f.Z[o] : T(0);
+        const T pv = ok ? f.P[o] : T(0);
+        const T z = project_col<T, BMAX, BWL>(zt, xc, Gc, b);
+        if (ok) f.P[o] = (be == T(0)) ? z : z + be * pv;
+      }
       }
     }
     if (!grid_barrier(f.bar)) return;
+    if (f.early_exit && all_known && s_all) break;
   }
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
@@ -474,10 +514,13 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   grid = grid < g.ntiles ? grid : g.ntiles;
   if (grid < 1) grid = 1;
   DevGraph gg = g;
+  // vector gathers of P rows need 16-byte aligned rows
+  constexpr int W = sizeof(T) == 4 ? 4 : 2;
+  const bool vec = (reinterpret_cast<uintptr_t>(f.Pv) % 16 == 0) && (f.ld % W == 0);
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
-             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar};
+             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, vec ? 1 : 0};
   void* args[] = {&gg, &ff};
   const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;

@@ -35,6 +35,7 @@ struct FusedPcg {
   int64_t state_stride; // nseg * bstride
   const int* hub_seg;   // segment of each hub row
   GridBar bar;
+  int early_exit = 0;   // single graph: stop when every column has converged
 };
 
 // Launch the whole correction solve; returns 0 or -1 (launch failure).

@@ -172,9 +172,13 @@ struct JD {
   }
 
   // Start: V[:, 0:q] from `init` (or random), orthonormalised; W = L V; H = V^T W.
-  int start(const TV* init, int ldi, int q, uint64_t seed, double drop1) {
+  // x0d (device, row-major n x ldx0, FP64): optional warm-start columns that
+  // replace the first k0 random columns.
+  int start(const TV* init, int ldi, int q, uint64_t seed, double drop1, const double* x0d = nullptr, int ldx0 = 0,
+            int k0 = 0) {
     if (init) convert<TV, TV>(g, init, ldi, V, z.ldv, q, st);
     else random_block<TV>(g, V, z.ldv, q, seed, st);
+    if (!init && x0d && k0 > 0) convert<double, TV>(g, x0d, ldx0, V, z.ldv, k0 < q ? k0 : q, st);
     cudaMemsetAsync(seg_skip, 0, sizeof(int) * z.nseg * 64, st);
     ortho(0, q, drop1);
     spmm<TV>(g, V, z.ldv, W, z.ldv, q, st);
@@ -426,11 +430,32 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   for (int s = 0; s < S; ++s) tol_abs[s] = tol * G->norm1[s];
 
   Arena outa;
-  int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k + 1024);
+  int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k +
+                     sizeof(double) * (size_t)z.n * (o.x0 ? std::min(std::max(o.k0, 0), 64) : 0) + 4096);
   if (rc) return rc;
   double* d_out = outa.take<double>((size_t)z.n * k);
   unsigned long long* d_best = outa.take<unsigned long long>(2 * (size_t)S * k);
 
+  // optional warm start (single graph): host n x k0 column-major -> device row-major
+  double* x0d = nullptr;
+  int k0 = 0, ldx0 = 0;
+  if (o.x0_dev && o.k0 > 0 && S == 1) {
+    k0 = std::min(o.k0, z.b);
+    ldx0 = o.ldx0 > 0 ? o.ldx0 : o.k0;
+    x0d = const_cast<double*>(o.x0_dev);
+  } else if (o.x0 && o.k0 > 0 && S == 1) {
+    k0 = std::min(o.k0, z.b);
+    ldx0 = k0;
+    std::vector<double> h((size_t)z.n * k0);
+    for (int c = 0; c < k0; ++c)
+      for (int r = 0; r < z.n; ++r) h[(size_t)r * k0 + c] = o.x0[(size_t)c * z.n + r];
+    x0d = outa.take<double>((size_t)z.n * k0);
+    if (cudaMemcpyAsync(x0d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("warm-start upload failed");
+      return LAP_ECUDA;
+    }
+  }
   PcgWork pw;
   rc = pw.init(S);
   if (rc) return rc;
@@ -444,7 +469,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     JD<double, double> jd(G, z, st);
     jd.carve(a);
     jd.pw = &pw;
-    int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20);
+    int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
     const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
     if (status < 0 && status != LAP_ETIMEOUT) return status;
@@ -459,7 +484,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   JD<float, float> j1(G, z, st);
   j1.carve(a1);
   j1.pw = &pw;
-  int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10);
+  int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
   std::vector<double> tol1(S);
   for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
   int m_out = m;

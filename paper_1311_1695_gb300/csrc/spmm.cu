@@ -185,3 +185,66 @@ template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, 
 template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t);
 
 }  // namespace lapeig
+
+// ---------------------------------------------------------------- autotuner
+#include "internal.h"
+
+namespace lapeig {
+
+int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_out, cudaStream_t s) {
+  const size_t es = dtype == LAP_F32 ? 4 : 8;
+  const int ld = (b + 3) / 4 * 4;
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, 2 * es * (size_t)g->hg.n * ld + 256) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("autotune scratch allocation failed");
+    return LAP_ENOMEM;
+  }
+  char* X = static_cast<char*>(buf);
+  char* Y = X + es * (size_t)g->hg.n * ld;
+  if (dtype == LAP_F32) random_block<float>(g->dg, (float*)X, ld, ld, 12345, s);
+  else random_block<double>(g->dg, (double*)X, ld, ld, 12345, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int teams[4] = {4, 8, 16, 32};
+  const int threshs[4] = {64, 256, 1024, 1 << 30};
+  float best = 1e30f;
+  int bt = g->dg.team, bh = g->dg.long_thresh;
+  for (int ti = 0; ti < 4; ++ti) {
+    for (int hi = 0; hi < 4; ++hi) {
+      if (threshs[hi] < teams[ti] * 8) continue;  // hub CTAs only pay off for long rows
+      if (graph_set_schedule(g, teams[ti], threshs[hi]) != LAP_OK) continue;
+      auto run = [&]() {
+        if (dtype == LAP_F32) spmm<float>(g->dg, (const float*)X, ld, (float*)Y, ld, b, s);
+        else spmm<double>(g->dg, (const double*)X, ld, (double*)Y, ld, b, s);
+      };
+      run();
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 5; ++r) run();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bt = teams[ti]; bh = threshs[hi]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  const int rc = graph_set_schedule(g, bt, bh);
+  if (team_out) *team_out = bt;
+  if (thresh_out) *thresh_out = bh;
+  if (cudaGetLastError() != cudaSuccess) { set_error("CUDA error in autotune"); return LAP_ECUDA; }
+  return rc;
+}
+
+}  // namespace lapeig
+
+extern "C" int lap_graph_autotune(lap_graph* g, int dtype, int b, int* team, int* thresh, void* stream) {
+  if (!g || b < 1 || b > 32 || (dtype != LAP_F32 && dtype != LAP_F64)) {
+    lapeig::set_error("bad arguments to lap_graph_autotune");
+    return LAP_EINVAL;
+  }
+  return lapeig::graph_autotune(g, dtype, b, team, thresh, reinterpret_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,219 @@
+"""Learned warm start: a 3-layer message-passing network (width 32) that
+proposes the initial Jacobi-Davidson block, trained on eigenvectors the
+solver itself computed.  The paper has no learned component.
+
+Every forward and backward step runs in the library's kernels
+(lap_gnn_features / lap_gnn_aggregate / lap_gnn_tanh / lap_block_update /
+lap_gram); this module only lays out the device buffers and marshals the
+small parameter matrices.  Weights are kept as FP64 masters and rounded to
+BF16 for every use (the kernels compute with FP32 data and accumulate in FP32
+within a row, FP64 across rows).
+
+Network, for a batch handle of graphs (each graph its own segment):
+    H_0 = F (features),  [M H_l | H_l] [W_l; U_l] + b_l -> tanh -> H_{l+1},
+    X = H_3 W_out,       M = D^{-1} A.
+Loss per graph: 1 - tr((X^T X)^{-1} X^T U U^T X) / k (U = solver eigenvectors).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+from . import LAP_F32, LAP_F64, Graph, _check, _stream, lib
+
+WIDTH = 32
+NFEAT = 16
+LAYERS = 3
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gnn_weights.json")
+
+
+def to_bf16(x: np.ndarray) -> np.ndarray:
+    """Round FP64 values to the nearest BF16 (ties to even), returned as FP64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return (r.astype(np.uint32)).view(np.float32).astype(np.float64)
+
+
+def param_shapes(k: int):
+    shapes, fin = [], NFEAT
+    for _ in range(LAYERS):
+        shapes += [("W", (fin, WIDTH)), ("U", (fin, WIDTH)), ("b", (WIDTH,))]
+        fin = WIDTH
+    shapes.append(("Wout", (WIDTH, k)))
+    return shapes
+
+
+def init_params(k: int, seed: int = 0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, shp in param_shapes(k):
+        out.append(np.zeros(shp) if name == "b" else rng.standard_normal(shp) / np.sqrt(shp[0]))
+    return out
+
+
+def save_params(params, path=WEIGHTS, meta=None):
+    json.dump({"k": int(params[-1].shape[1]), "params": [p.tolist() for p in params], "meta": meta or {}},
+              open(path, "w"))
+
+
+def load_params(path=WEIGHTS):
+    d = json.load(open(path))
+    return [np.asarray(p, dtype=np.float64) for p in d["params"]], d.get("meta", {})
+
+
+class Net:
+    """Device buffers of one batch handle; forward/backward on them."""
+
+    def __init__(self, G: Graph, k: int):
+        import torch
+        self.G, self.k = G, k
+        n = G.n
+        dev = "cuda"
+        f32 = torch.float32
+        # AH_l = [M H_l | H_l]; layer 0 holds the features in its right half
+        self.AH = [torch.zeros((n, 2 * NFEAT), dtype=f32, device=dev)] + \
+                  [torch.zeros((n, 2 * WIDTH), dtype=f32, device=dev) for _ in range(LAYERS)]
+        self.UX = torch.zeros((n, 2 * k), dtype=f32, device=dev)  # [U | X]
+        self.dX = torch.zeros((n, k), dtype=f32, device=dev)
+        self.dH = torch.zeros((n, WIDTH), dtype=f32, device=dev)
+        self.T1 = torch.zeros((n, WIDTH), dtype=f32, device=dev)
+        self.dHn = torch.zeros((n, WIDTH), dtype=f32, device=dev)
+        self.nseg = G.nseg
+        self.rows = np.diff(G.row0)
+
+    # -- helpers
+    def _S(self, mats, nseg=1):
+        import torch
+        S = np.concatenate([np.atleast_2d(m) for m in mats], axis=0)
+        S = np.ascontiguousarray(np.broadcast_to(S, (nseg,) + S.shape))
+        return torch.from_numpy(S).cuda(), S.shape[-1], S.shape[-2] * S.shape[-1]
+
+    def _update(self, Y, ldy, q, beta, A, lda, p, ones, S, lds, ss):
+        _check(lib().lap_block_update(self.G.h, LAP_F32, ctypes.c_void_p(Y), ldy, q, beta, 1.0,
+                                      None if A is None else ctypes.c_void_p(A), lda, p, ones,
+                                      ctypes.c_void_p(S.data_ptr()), lds, ss, _stream()), "lap_block_update")
+
+    def _gram(self, A, lda, p, B, ldb, q, ones):
+        import torch
+        Gm = torch.zeros((self.nseg, p + ones, q), dtype=torch.float64, device="cuda")
+        _check(lib().lap_gram(self.G.h, LAP_F32, None if A is None else ctypes.c_void_p(A), lda, p,
+                              ctypes.c_void_p(B), ldb, q, ones, ctypes.c_void_p(Gm.data_ptr()), _stream()), "lap_gram")
+        return Gm
+
+    # -- forward: returns X (view of UX[:, k:])
+    def forward(self, params, seed: int):
+        P = [to_bf16(p) for p in params]
+        AH = self.AH
+        e4 = 4
+        # features into the right half of AH_0
+        _check(lib().lap_gnn_features(self.G.h, seed, NFEAT, ctypes.c_void_p(AH[0].data_ptr() + e4 * NFEAT),
+                                      2 * NFEAT, _stream()), "lap_gnn_features")
+        fin = NFEAT
+        for l in range(LAYERS):
+            A = AH[l]
+            # left half = M H_l
+            _check(lib().lap_gnn_aggregate(self.G.h, 0, ctypes.c_void_p(A.data_ptr() + e4 * fin), 2 * fin,
+                                           ctypes.c_void_p(A.data_ptr()), 2 * fin, fin, _stream()),
+                   "lap_gnn_aggregate")
+            W, U, b = P[3 * l: 3 * l + 3]
+            S, lds, ss = self._S([b[None, :], W, U])
+            out = AH[l + 1]
+            Hn = out.data_ptr() + e4 * WIDTH
+            self._update(Hn, 2 * WIDTH, WIDTH, 0.0, A.data_ptr(), 2 * fin, 2 * fin, 1, S, lds, 0)
+            _check(lib().lap_gnn_tanh(self.G.h, 0, ctypes.c_void_p(Hn), 2 * WIDTH, None, 0, WIDTH, _stream()),
+                   "lap_gnn_tanh")
+            fin = WIDTH
+        S, lds, ss = self._S([P[-1]])
+        X = self.UX.data_ptr() + e4 * self.k
+        self._update(X, 2 * self.k, self.k, 0.0, AH[LAYERS].data_ptr() + e4 * WIDTH, 2 * WIDTH, WIDTH, 0, S, lds, 0)
+        self._P = P
+        return self.UX[:, self.k:]
+
+    def set_targets(self, U):
+        """U: float32 CUDA tensor n x k (each graph's solver eigenvectors in its rows)."""
+        self.UX[:, :self.k] = U
+
+    # -- loss per graph and dX
+    def loss(self):
+        k = self.k
+        UXp = self.UX.data_ptr()
+        UtX = self._gram(UXp, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).cpu().numpy()
+        XtX = self._gram(UXp + 4 * k, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).cpu().numpy()
+        losses = np.zeros(self.nseg)
+        S = np.zeros((self.nseg, 2 * k, k))
+        for s in range(self.nseg):
+            Gi = np.linalg.inv(XtX[s])
+            UX = UtX[s]
+            losses[s] = 1.0 - np.trace(Gi @ UX.T @ UX) / k
+            # mean over graphs: scale by 1/nseg
+            S[s, :k] = -(2.0 / k) * UX @ Gi / self.nseg
+            S[s, k:] = (2.0 / k) * Gi @ UX.T @ UX @ Gi / self.nseg
+        import torch
+        St = torch.from_numpy(S).cuda()
+        self._update(self.dX.data_ptr(), k, k, 0.0, UXp, 2 * k, 2 * k, 0, St, k, 2 * k * k)
+        return losses
+
+    # -- backward: gradients (summed over the graphs of the batch), FP64 numpy
+    def backward(self):
+        P, k, AH = self._P, self.k, self.AH
+        e4 = 4
+        grads = [None] * len(P)
+        H3 = AH[LAYERS].data_ptr() + e4 * WIDTH
+        grads[-1] = self._gram(H3, 2 * WIDTH, WIDTH, self.dX.data_ptr(), k, k, 0).cpu().numpy().sum(axis=0)
+        S, lds, _ = self._S([P[-1].T])
+        self._update(self.dH.data_ptr(), WIDTH, WIDTH, 0.0, self.dX.data_ptr(), k, k, 0, S, lds, 0)
+        fin_of = [NFEAT] + [WIDTH] * (LAYERS - 1)
+        for l in reversed(range(LAYERS)):
+            fin = fin_of[l]
+            Hn = AH[l + 1].data_ptr() + e4 * WIDTH
+            dZ = self.dH.data_ptr()
+            _check(lib().lap_gnn_tanh(self.G.h, 1, ctypes.c_void_p(dZ), WIDTH, ctypes.c_void_p(Hn), 2 * WIDTH,
+                                      WIDTH, _stream()), "lap_gnn_tanh")
+            Gm = self._gram(AH[l].data_ptr(), 2 * fin, 2 * fin, dZ, WIDTH, WIDTH, 1).cpu().numpy()
+            # the leading row is a per-graph mean: back to a sum
+            db = (Gm[:, 0, :] * self.rows[:, None]).sum(axis=0)
+            grads[3 * l] = Gm[:, 1:1 + fin, :].sum(axis=0)
+            grads[3 * l + 1] = Gm[:, 1 + fin:, :].sum(axis=0)
+            grads[3 * l + 2] = db
+            if l > 0:
+                W, U = P[3 * l], P[3 * l + 1]
+                S, lds, _ = self._S([W.T])
+                self._update(self.T1.data_ptr(), WIDTH, fin, 0.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
+                _check(lib().lap_gnn_aggregate(self.G.h, 1, ctypes.c_void_p(self.T1.data_ptr()), WIDTH,
+                                               ctypes.c_void_p(self.dHn.data_ptr()), WIDTH, fin, _stream()),
+                       "lap_gnn_aggregate")
+                S, lds, _ = self._S([U.T])
+                self._update(self.dHn.data_ptr(), WIDTH, fin, 1.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
+                self.dH, self.dHn = self.dHn, self.dH
+        return grads
+
+
+class Adam:
+    def __init__(self, params, lr=3e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.m = [np.zeros_like(p) for p in params]
+        self.v = [np.zeros_like(p) for p in params]
+        self.t, self.lr, self.b1, self.b2, self.eps = 0, lr, b1, b2, eps
+
+    def step(self, params, grads):
+        self.t += 1
+        for p, g, m, v in zip(params, grads, self.m, self.v):
+            m *= self.b1
+            m += (1 - self.b1) * g
+            v *= self.b2
+            v += (1 - self.b2) * g * g
+            mh = m / (1 - self.b1 ** self.t)
+            vh = v / (1 - self.b2 ** self.t)
+            p -= self.lr * mh / (np.sqrt(vh) + self.eps)
+
+
+def warm_start(G: Graph, params, seed: int = 0x5EED):
+    """The network's proposal for graph handle G as a float64 CUDA tensor
+    (n x k), ready for lap_eigs_graph's x0_dev."""
+    k = params[-1].shape[1]
+    net = Net(G, k)
+    X = net.forward(params, seed)
+    return X.double().contiguous()

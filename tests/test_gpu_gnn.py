@@ -1,0 +1,78 @@
+"""The warm-start network's device forward and backward against the FP64
+oracle definition (same BF16-rounded weights), and the gain of the trained
+network over the random start."""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as G
+from oracle import dense
+from oracle import gnn as ognn
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1311_1695_gb300 as p
+    from paper_1311_1695_gb300 import build
+    build.build()
+    return p
+
+
+def _graphs():
+    return [G.with_random_weights(G.chung_lu(1500, 2.4, 6.0, 3), 2), G.ba_graph(900, 3, 4)]
+
+
+def test_forward_backward_match_oracle(pkg):
+    from paper_1311_1695_gb300 import gnn
+    gs = _graphs()
+    k = 6
+    params = gnn.init_params(k, seed=3)
+    pb = [gnn.to_bf16(p) for p in params]
+    H = pkg.Graph(gs)
+    net = gnn.Net(H, k)
+    U = [dense.smallest_eigpairs(g, k)[1] for g in gs]
+    net.set_targets(torch.from_numpy(np.vstack(U)).float().cuda())
+    X = net.forward(params, seed=11).cpu().numpy()
+    losses = net.loss()
+    grads = net.backward()
+    ref_grads = [np.zeros_like(p) for p in params]
+    off = 0
+    for g, Ug in zip(gs, U):
+        F = ognn.features(g, 11, nfeat=gnn.NFEAT)
+        Xr, cache = ognn.forward(g, F, pb)
+        assert np.abs(X[off:off + g.n] - Xr).max() <= 2e-4 * max(1.0, np.abs(Xr).max())
+        loss, dX = ognn.subspace_loss(Xr, Ug)
+        gr = ognn.backward(g, cache, pb, dX / len(gs))
+        for a, b in zip(ref_grads, gr):
+            a += b
+        off += g.n
+    ref_loss = [ognn.subspace_loss(ognn.forward(g, ognn.features(g, 11, nfeat=gnn.NFEAT), pb)[0], Ug)[0]
+                for g, Ug in zip(gs, U)]
+    assert np.allclose(losses, ref_loss, atol=2e-4)
+    for i, (a, b) in enumerate(zip(grads, ref_grads)):
+        scale = max(np.abs(b).max(), 1e-6)
+        assert np.abs(a - b).max() <= 2e-3 * scale, (i, np.abs(a - b).max(), scale)
+    H.close()
+
+
+def test_trained_warm_start_beats_random(pkg):
+    from paper_1311_1695_gb300 import gnn
+    if not os.path.exists(gnn.WEIGHTS):
+        pytest.skip("no trained weights committed")
+    params, meta = gnn.load_params()
+    k = params[-1].shape[1]
+    gains = []
+    for seed in (901, 902, 903):
+        g = G.chung_lu(30000, 2.5, 6.0, seed)
+        H = pkg.Graph(g)
+        x0 = gnn.warm_start(H, params)
+        _, infos_r = H.eigs(k, 1e-8, precision="mixed")
+        ev_w, infos_w = H.eigs(k, 1e-8, precision="mixed", x0_dev=x0)
+        assert infos_w[0]["status"] == 0 and infos_r[0]["status"] == 0
+        gains.append(infos_r[0]["n_matvec"] / infos_w[0]["n_matvec"])
+        H.close()
+    assert np.median(gains) > 1.0, gains

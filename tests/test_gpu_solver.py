@@ -112,3 +112,30 @@ def test_seed_independence(pkg):
     e1, _, _ = pkg.lap_eigs(g, 6, tol=1e-8, seed=1)
     e2, _, _ = pkg.lap_eigs(g, 6, tol=1e-8, seed=99)
     assert np.allclose(e1, e2, rtol=1e-9)
+
+
+@pytest.mark.parametrize("method", ["dacg", "irlm"])
+@pytest.mark.parametrize("make,k", [
+    (lambda: G.ba_graph(600, 2, 31), 5),
+    (lambda: G.grid_graph(17, 23), 4),
+    (lambda: G.with_random_weights(G.chung_lu(1500, 2.4, 5.0, 12), 3), 4),
+])
+def test_dacg_irlm_match_definition(pkg, method, make, k):
+    """Algorithm 3 (DACG) and Algorithm 1 right (Lanczos on L^+ with implicit
+    restarts) on the device, against the dense definition."""
+    g = make()
+    ev, V, info = pkg.lap_eigs(g, k, tol=1e-8, method=method)
+    assert info["status"] == 0, info
+    ev_ref, V_ref = dense.smallest_eigpairs(g, k + 8)
+    check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)
+    assert info["n_matvec"] > 0
+
+
+def test_three_methods_agree_c1(pkg):
+    """JD, DACG and IRLM return the same pairs on the protein-sized workload."""
+    g = G.workload_graph("c1")
+    res = {m: pkg.lap_eigs(g, 4, tol=1e-8, method=m) for m in ("jd", "dacg", "irlm")}
+    ev_ref, V_ref = dense.smallest_eigpairs(g, 12)
+    for m, (ev, V, info) in res.items():
+        assert info["status"] == 0, (m, info)
+        check_eigpairs(g, ev, V, ev_ref, V_ref, k=4)

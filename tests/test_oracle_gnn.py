@@ -1,0 +1,61 @@
+"""Pins of the warm-start network's FP64 definition: finite differences for
+every parameter gradient, and the subspace loss's invariances."""
+import numpy as np
+
+import graphgen as G
+from oracle import dense, gnn
+
+
+def test_backward_matches_finite_differences():
+    g = G.with_random_weights(G.ba_graph(40, 2, 3), 5)
+    k = 3
+    F = gnn.features(g, 7, nfeat=6)
+    params = gnn.init_params(k, seed=1, nfeat=6, width=5)
+    _, U = dense.smallest_eigpairs(g, k)
+
+    def loss_of(ps):
+        X, _ = gnn.forward(g, F, ps)
+        return gnn.subspace_loss(X, U)[0]
+
+    X, cache = gnn.forward(g, F, params)
+    loss, dX = gnn.subspace_loss(X, U)
+    grads = gnn.backward(g, cache, params, dX)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for pi, P in enumerate(params):
+        flat = P.reshape(-1)
+        for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = loss_of(params)
+            flat[idx] = old - h
+            lm = loss_of(params)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - grads[pi].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd)), (pi, idx, fd)
+
+
+def test_subspace_loss_invariances():
+    rng = np.random.default_rng(2)
+    U, _ = np.linalg.qr(rng.standard_normal((50, 4)))
+    # zero on span(U), for any invertible recombination
+    X = U @ rng.standard_normal((4, 4))
+    assert abs(gnn.subspace_loss(X, U)[0]) < 1e-12
+    # invariant under X -> X R and under U -> U Q (orthogonal Q)
+    Y = rng.standard_normal((50, 4))
+    R = rng.standard_normal((4, 4))
+    Q, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    l0 = gnn.subspace_loss(Y, U)[0]
+    assert abs(gnn.subspace_loss(Y @ R, U)[0] - l0) < 1e-10
+    assert abs(gnn.subspace_loss(Y, U @ Q)[0] - l0) < 1e-10
+    # one for a block orthogonal to span(U)
+    Z = Y - U @ (U.T @ Y)
+    assert abs(gnn.subspace_loss(Z, U)[0] - 1.0) < 1e-12
+
+
+def test_features_shape_and_range():
+    g = G.ba_graph(30, 2, 1)
+    F = gnn.features(g, 3)
+    assert F.shape == (30, gnn.NFEAT)
+    assert np.all(F[:, 0] == 1.0) and F[:, 1].max() == 1.0
+    assert np.abs(F[:, 2:]).max() < 1.0
