@@ -285,7 +285,15 @@ FusedPcg PcgWork::args(const void* X, int ldx, const void* R, int ldr, void* Tt,
   f.delta = delta; f.itmax = itmax; f.acc1 = acc1; f.acc2 = acc2; f.acc_stride = acc_stride; f.rho = rho;
   f.done = done; f.res0 = res0; f.resn = resn; f.state_stride = (int64_t)nseg * 64; f.hub_seg = hub_seg;
   f.bar.count = bar; f.bar.gen = bar + 1; f.bar.err = reinterpret_cast<int*>(bar + 2);
+  f.iters_out = reinterpret_cast<int*>(bar + 3);
   return f;
+}
+
+int PcgWork::steps_done(cudaStream_t s) const {
+  int v = 0;
+  cudaMemcpyAsync(&v, bar + 3, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return v;
 }
 
 int PcgWork::error_flag(cudaStream_t s) const {

@@ -21,7 +21,7 @@ struct PcgWork {
   int* done = nullptr;
   double* res0 = nullptr;
   double* resn = nullptr;
-  unsigned* bar = nullptr;  // count, gen, err
+  unsigned* bar = nullptr;  // count, gen, err, PCG steps done
   int acc_stride = 33 * 32 + 3 * 32;
   int nseg = 0;
   int init(int nseg_);
@@ -30,6 +30,7 @@ struct PcgWork {
                 int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip, double delta,
                 int itmax, const int* hub_seg) const;
   int error_flag(cudaStream_t s) const;  // reads and clears the barrier error flag
+  int steps_done(cudaStream_t s) const;  // PCG steps of the last launch
 };
 
 }  // namespace lapeig

@@ -421,6 +421,11 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
       if (pcg_fused<double>(g, fe, st, 0) != 0) { set_error("IRLM inner solve launch failed"); return LAP_ECUDA; }
       if (G->pcg.error_flag(st)) { set_error("grid barrier timed out in IRLM"); return LAP_ETIMEOUT; }
       ++solves;
+      {
+        const int steps = G->pcg.steps_done(st);
+        inner += steps;
+        nmv += steps + 1;
+      }
       // w = -t, projected off e; alpha_j = w.v_j
       std::vector<double> S1 = {-1.0};
       cudaMemcpyAsync(Sv, S1.data(), sizeof(double), cudaMemcpyHostToDevice, st);

@@ -76,7 +76,7 @@ struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
   double delta; int itmax; double *acc1, *acc2; int acc_stride; double* rho; int* done; double *res0, *resn;
-  int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int vec;
+  int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int vec; int* iters_out;
 };
 
 // Per-thread accumulators of one phase for the current graph: thread (warp,
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
   }
   if (!grid_barrier(f.bar)) return;
 
+  int it_done = 0;
   for (int it = 0; it < f.itmax; ++it) {
     const int par = it & 1;
     // ---------------------------------------------------------------- phase A1: q~ = L p - theta p
@@ -490,8 +491,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
       }
     }
     if (!grid_barrier(f.bar)) return;
+    it_done = it + 1;
     if (f.early_exit && all_known && s_all) break;
   }
+  if (f.iters_out && blockIdx.x == 0 && threadIdx.x == 0) *f.iters_out = it_done;
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
@@ -520,7 +523,8 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
-             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, vec ? 1 : 0};
+             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, vec ? 1 : 0,
+             f.iters_out};
   void* args[] = {&gg, &ff};
   const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;

@@ -36,6 +36,7 @@ struct FusedPcg {
   const int* hub_seg;   // segment of each hub row
   GridBar bar;
   int early_exit = 0;   // single graph: stop when every column has converged
+  int* iters_out = nullptr;  // receives the number of PCG steps done
 };
 
 // Launch the whole correction solve; returns 0 or -1 (launch failure).

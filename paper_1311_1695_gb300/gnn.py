@@ -89,7 +89,7 @@ class Net:
     def _S(self, mats, nseg=1):
         import torch
         S = np.concatenate([np.atleast_2d(m) for m in mats], axis=0)
-        S = np.ascontiguousarray(np.broadcast_to(S, (nseg,) + S.shape))
+        S = np.array(np.broadcast_to(S, (nseg,) + S.shape), dtype=np.float64, copy=True)
         return torch.from_numpy(S).cuda(), S.shape[-1], S.shape[-2] * S.shape[-1]
 
     def _update(self, Y, ldy, q, beta, A, lda, p, ones, S, lds, ss):
