@@ -231,143 +231,86 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
   int it_done = 0;
   for (int it = 0; it < f.itmax; ++it) {
     const int par = it & 1;
-    // ---------------------------------------------------------------- phase A1: q~ = L p - theta p
+    // ---------------------------------------------------------------- phase A: q~ = L p - theta p, G1, p.q~
+    // owner zeroes acc2 (its last read was the previous phase C / init-C)
     for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
       const Tile t = g.tiles[ti];
       if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
         for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = 0.0;
     }
     {
-      const int tl = threadIdx.x & (TEAM - 1);
-      const int tslot = threadIdx.x / TEAM;
-      constexpr int TSLOTS = kThreads / TEAM;
-      const unsigned tmask = (TEAM == 32) ? 0xffffffffu : (((1u << TEAM) - 1u) << ((threadIdx.x & 31) & ~(TEAM - 1)));
-      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-        const Tile t = g.tiles[ti];
-        if (f.seg_skip && f.seg_skip[t.seg]) continue;
-        const double* th = f.theta + (size_t)t.seg * f.sth;
-        for (int rb = t.r0; rb < t.r1; rb += TSLOTS) {
-          const int row = rb + tslot;
-          const bool valid = row < t.r1;
-          int p0 = 0, p1 = 0;
-          if (valid) { p0 = g.rowptr[row]; p1 = g.rowptr[row + 1]; }
-          const bool hub = valid && (p1 - p0 > g.long_thresh);
-          T a[BMAX];
-#pragma unroll
-          for (int q = 0; q < BMAX; ++q) a[q] = T(0);
-          T dsum = T(0);
-          if (valid && !hub) {
-            for (int p = p0 + tl; p < p1; p += TEAM) {
-              const int j = __ldg(g.colidx + p);
-              const T wv = w ? __ldg(w + p) : T(1);
-              const T* xj = f.P + (size_t)j * ld;
-              if (!f.vec) {
-#pragma unroll
-                for (int q = 0; q < BMAX; ++q)
-                  if (q < b) a[q] += wv * __ldcg(xj + q);
-              } else if constexpr (sizeof(T) == 4) {
-                const float4* xv = reinterpret_cast<const float4*>(xj);
-#pragma unroll
-                for (int q = 0; q < BMAX; q += 4)
-                  if (q < b) {
-                    const float4 v = __ldcg(xv + q / 4);
-                    a[q] += wv * v.x; a[q + 1] += wv * v.y; a[q + 2] += wv * v.z; a[q + 3] += wv * v.w;
-                  }
-              } else {
-                const double2* xv = reinterpret_cast<const double2*>(xj);
-#pragma unroll
-                for (int q = 0; q < BMAX; q += 2)
-                  if (q < b) {
-                    const double2 v = __ldcg(xv + q / 2);
-                    a[q] += wv * v.x; a[q + 1] += wv * v.y;
-                  }
-              }
-              dsum += wv;
-            }
-          }
-#pragma unroll
-          for (int o = TEAM / 2; o > 0; o >>= 1) {
-#pragma unroll
-            for (int q = 0; q < BMAX; ++q) a[q] += __shfl_xor_sync(tmask, a[q], o);
-            dsum += __shfl_xor_sync(tmask, dsum, o);
-          }
-          if (valid && !hub) {
-            const T d = w ? dsum : T(p1 - p0);
-            const T* pr = f.P + (size_t)row * ld;
-            T* apr = f.AP + (size_t)row * ld;
-#pragma unroll
-            for (int q = 0; q < BMAX; ++q)
-              if (q < b && (q % TEAM) == tl) {
-                const T pv = pr[q];
-                apr[q] = d * pv - a[q] - (T)th[q] * pv;
-              }
-          }
-        }
-      }
-    }
-    __syncthreads();
-    // ---------------------------------------------------------------- phase A2: G1 = [1|X]^T q~, p.q~ (own rows)
-    {
+      // lanes as columns: a row group of BWL lanes walks the row's nonzeros,
+      // lane c accumulating column c (broadcast index load, contiguous row
+      // gather); the row's share of [1|X]^T q~ follows in the same pass.
       int cur = -1;
+      T thc = T(0);
       for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
           if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
           cur = t.seg;
+          thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
         }
         for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-        const int r = rg + lane / BWL;
-        const bool rv_ = r < t.r1;
-        const bool ok = colok && rv_;
-        const bool hub = rv_ && (g.rowptr[r + 1] - g.rowptr[r]) > g.long_thresh;
-        const size_t o = (size_t)r * ld + c;
-        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T q = (ok && !hub) ? f.AP[o] : T(0);
-        const T pv = ok ? f.P[o] : T(0);
-        gram_col<T, BMAX, BWL>(acc, xc, q, b);
-        ex[0] += pv * q;
-      }
+          const int r = rg + lane / BWL;
+          const bool rv_ = r < t.r1;
+          const bool ok = colok && rv_;
+          int p0 = 0, p1 = 0;
+          if (rv_) { p0 = g.rowptr[r]; p1 = g.rowptr[r + 1]; }
+          const bool hub = (p1 - p0) > g.long_thresh;
+          T a = T(0), ws = T(0);
+          if (!hub) {
+#pragma unroll 4
+            for (int p = p0; p < p1; ++p) {
+              const int j = __ldg(g.colidx + p);
+              const T wv = w ? __ldg(w + p) : T(1);
+              if (colok) a += wv * __ldcg(f.P + (size_t)j * ld + c);
+              ws += wv;
+            }
+          }
+          const size_t o = (size_t)r * ld + c;
+          const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
+          const T pv = ok ? f.P[o] : T(0);
+          const T d = w ? ws : T(p1 - p0);
+          const T q = (ok && !hub) ? d * pv - a - thc * pv : T(0);
+          if (ok && !hub) f.AP[o] = q;
+          gram_col<T, BMAX, BWL>(acc, xc, q, b);
+          ex[0] += pv * q;
+        }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
     }
-    // hub rows, round-robin over the CTAs: whole-CTA reduction per row
+    // hub rows, round-robin over the CTAs: the CTA's row groups split the
+    // row's nonzeros (lanes as columns), then reduce over groups and warps
     for (int h = blockIdx.x; h < g.nlong; h += gridDim.x) {
       const int row = g.long_rows[h];
       const int seg = f.hub_seg[h];
       if (f.seg_skip && f.seg_skip[seg]) continue;
       const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-      T a[BMAX];
-#pragma unroll
-      for (int q = 0; q < BMAX; ++q) a[q] = T(0);
-      T dsum = T(0);
-      for (int p = p0 + threadIdx.x; p < p1; p += kThreads) {
+      T a = T(0), ws = T(0);
+      for (int p = p0 + slot; p < p1; p += SLOTS) {
         const int j = __ldg(g.colidx + p);
         const T wv = w ? __ldg(w + p) : T(1);
-        const T* xj = f.P + (size_t)j * ld;
+        if (colok) a += wv * __ldcg(f.P + (size_t)j * ld + c);
+        ws += wv;
+      }
 #pragma unroll
-        for (int q = 0; q < BMAX; ++q)
-          if (q < b) a[q] += wv * __ldcg(xj + q);
-        dsum += wv;
+      for (int o = BWL; o < 32; o <<= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
       }
-      T* hred = reinterpret_cast<T*>(red);  // [NW][BMAX+1], then q~ [BMAX], x [BMAX]
-#pragma unroll
-      for (int q = 0; q < BMAX; ++q) {
-        const T v = warp_sum(a[q]);
-        if (lane == 0) hred[warp * (BMAX + 1) + q] = v;
-      }
-      {
-        const T v = warp_sum(dsum);
-        if (lane == 0) hred[warp * (BMAX + 1) + BMAX] = v;
-      }
+      T* hred = reinterpret_cast<T*>(red);  // [NW][BWL + 1], then q~ [BMAX], x [BMAX]
+      if (lane < BWL) hred[warp * (BWL + 1) + lane] = a;
+      if (lane == 0) hred[warp * (BWL + 1) + BWL] = ws;
       __syncthreads();
-      T* qs = hred + NW * (BMAX + 1);
+      T* qs = hred + NW * (BWL + 1);
       T* xs = qs + BMAX;
       if (threadIdx.x < b) {
         const int q = threadIdx.x;
-        T sum = T(0), ds = T(0);
-        for (int v = 0; v < NW; ++v) { sum += hred[v * (BMAX + 1) + q]; ds += hred[v * (BMAX + 1) + BMAX]; }
-        const T d = w ? ds : T(p1 - p0);
+        T sum = T(0), dsum = T(0);
+        for (int v = 0; v < NW; ++v) { sum += hred[v * (BWL + 1) + q]; dsum += hred[v * (BWL + 1) + BWL]; }
+        const T d = w ? dsum : T(p1 - p0);
         const T pv = __ldcg(f.P + (size_t)row * ld + q);
         const T qq = d * pv - sum - (T)f.theta[(size_t)seg * f.sth + q] * pv;
         f.AP[(size_t)row * ld + q] = qq;
