@@ -404,7 +404,8 @@ __device__ int jacobi_sweeps(T* A, T* V, int LD, int mm, T rel, T abs_tol, int m
 // nothing to rotate).  The result has the accuracy of an all-FP64 Jacobi.
 __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
                                                double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
-                                               const int* __restrict__ seg_skip, int* sweeps_out) {
+                                               const int* __restrict__ seg_skip, int* sweeps_out, int polish,
+                                               double* Bg, int ldb, int64_t sb) {
   const int seg = blockIdx.x;
   if (seg_skip && seg_skip[seg]) return;
   extern __shared__ double sm[];
@@ -484,12 +485,14 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
     A[j * LD + i] = t;
   }
   __syncthreads();
-  // 4. FP64 sweeps from V = Y
-  const int sw64 = jacobi_sweeps<double>(A, V, LD, mm, 1e-15, 1e-17 * fro, 30, cs, pq, &s_rot);
+  // 4. FP64 sweeps from V = Y (skipped when an FP32-accurate rotation is
+  //    enough: B then keeps small off-diagonal entries, returned in Bg)
+  const int sw64 = polish ? jacobi_sweeps<double>(A, V, LD, mm, 1e-15, 1e-17 * fro, 30, cs, pq, &s_rot) : 0;
   // sort the m eigenvalues ascending (rank by counting; ties by index); the
   // padding index (if any) is dropped: its column is e_{mm-1}, uncoupled
   double* ev = evals + (size_t)seg * se;
   double* Y = Yg + (size_t)seg * sy;
+  __shared__ int s_rank[64];
   for (int i = threadIdx.x; i < mm; i += blockDim.x) {
     // identify real columns: the padding column has its weight in row mm-1
     if (mm != m && fabs(V[(mm - 1) * LD + i]) > 0.5) continue;
@@ -501,7 +504,20 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
       rank += (dj < di) || (dj == di && j < i);
     }
     ev[rank] = di;
+    s_rank[i] = rank;
     for (int r = 0; r < m; ++r) Y[(size_t)r * ldy + rank] = V[r * LD + i];
+  }
+  if (Bg) {
+    // B in the sorted order: Bout[rank_i][rank_j] = A[i][j] (padding skipped)
+    for (int i = threadIdx.x; i < mm; i += blockDim.x)
+      if (mm != m && fabs(V[(mm - 1) * LD + i]) > 0.5) s_rank[i] = -1;
+    __syncthreads();
+    double* B = Bg + (size_t)seg * sb;
+    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
+      const int i = e / mm, j = e % mm;
+      const int ri = s_rank[i], rj = s_rank[j];
+      if (ri >= 0 && rj >= 0) B[(size_t)ri * ldb + rj] = 0.5 * (A[i * LD + j] + A[j * LD + i]);
+    }
   }
   if (sweeps_out && threadIdx.x == 0) sweeps_out[seg] = sw32 * 100 + sw64;
 }
@@ -818,7 +834,7 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 }
 
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,
-          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s) {
+          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int polish, double* B, int ldb, int64_t sb) {
   LAP_PROF("syev", 0.0, s);
   const int mm = (m + 1) & ~1;
   const size_t smem = sizeof(double) * (3 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
@@ -827,7 +843,7 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
     cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
     attr_set = true;
   }
-  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out);
+  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out, polish, B, ldb, sb);
 }
 
 template <typename T>
