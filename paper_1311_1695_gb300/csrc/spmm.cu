@@ -6,10 +6,10 @@
 // d_i is never read from memory: it is the row length (unit weights) or the
 // sum of the row's weights, accumulated in the same pass over the row.
 //
-// Load balance for power-law degree skew: rows of ordinary length are handled
-// by a team of TEAM lanes (TEAM | 32) that stride over the row's nonzeros,
-// each lane accumulating all b columns in registers, then a butterfly
-// reduction inside the team.  Rows longer than long_thresh (the hubs) are
+// Load balance for power-law degree skew.  For b >= 3 (k_spmm_cols) a group
+// of lanes owns a row with one lane per column; for b <= 2 a team of TEAM
+// lanes (TEAM | 32) strides over the row's nonzeros, each lane accumulating
+// the b columns in registers, then a butterfly reduction inside the team.  Rows longer than long_thresh (the hubs) are
 // listed at set-up and each gets a whole 256-thread CTA with a block
 // reduction.  Both kinds run in one launch: the first nlong CTAs take the hub
 // rows, the rest the ordinary rows (which skip the hubs).
@@ -128,6 +128,70 @@ __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ 
     if (c < b && (c % TEAM) == lane) yr[c] = deg * xr[c] - acc[c];
 }
 
+// Lanes as columns (b >= 3): a group of BWL lanes (BWL = next power of two
+// >= b) owns a row; for every nonzero, lane c loads column c of the
+// neighbour's row (one broadcast index load, one contiguous b-value gather
+// per group) and accumulates it; no reduction across lanes is needed.  Hub
+// rows (degree > long_thresh) are split over the row groups of a whole CTA.
+template <typename T, int BWL>
+__global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restrict__ X, int ldx,
+                                                   T* __restrict__ Y, int ldy, int b) {
+  const T* __restrict__ w = weights_of<T>(g);
+  constexpr int RW = 32 / BWL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL;
+  const bool colok = c < b;
+  if ((int)blockIdx.x < g.nlong) {
+    __shared__ T red[8][BWL + 1];
+    const int row = g.long_rows[blockIdx.x];
+    const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+    const int slot = warp * RW + lane / BWL;
+    T a = T(0), ws = T(0);
+    for (int p = p0 + slot; p < p1; p += 8 * RW) {
+      const int j = __ldg(g.colidx + p);
+      const T wv = w ? __ldg(w + p) : T(1);
+      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+      ws += wv;
+    }
+#pragma unroll
+    for (int o = BWL; o < 32; o <<= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      ws += __shfl_xor_sync(0xffffffffu, ws, o);
+    }
+    if (lane < BWL) red[warp][lane] = a;
+    if (lane == 0) red[warp][BWL] = ws;
+    __syncthreads();
+    if ((int)threadIdx.x < b) {
+      T sum = T(0), ds = T(0);
+      for (int v = 0; v < 8; ++v) { sum += red[v][threadIdx.x]; ds += red[v][BWL]; }
+      const T deg = w ? ds : T(p1 - p0);
+      Y[(size_t)row * ldy + threadIdx.x] = deg * X[(size_t)row * ldx + threadIdx.x] - sum;
+    }
+    return;
+  }
+  const int row = ((blockIdx.x - g.nlong) * 8 + warp) * RW + lane / BWL;
+  if (row >= g.n) return;  // no cross-group shuffles below
+  const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+  if (p1 - p0 > g.long_thresh || !colok) return;
+  T a = T(0), ws = T(0);
+#pragma unroll 4
+  for (int p = p0; p < p1; ++p) {
+    const int j = __ldg(g.colidx + p);
+    const T wv = w ? __ldg(w + p) : T(1);
+    a += wv * __ldg(X + (size_t)j * ldx + c);
+    ws += wv;
+  }
+  const T deg = w ? ws : T(p1 - p0);
+  Y[(size_t)row * ldy + c] = deg * X[(size_t)row * ldx + c] - a;
+}
+
+template <typename T, int BWL>
+static void launch_cols(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
+  constexpr int RPB = 8 * (32 / BWL);  // rows per block
+  const int blocks = g.nlong + (g.n + RPB - 1) / RPB;
+  if (blocks > 0) k_spmm_cols<T, BWL><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+}
+
 template <typename T, int BMAX, int TEAM>
 static void launch_team(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, bool vec,
                         cudaStream_t s) {
@@ -174,10 +238,11 @@ void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStre
     const bool vec = bb > 1 && (reinterpret_cast<uintptr_t>(Xc) % 16 == 0) && (ldx % W == 0) &&
                      (c0 + bpad <= ldx);
     if (bb == 1) launch_bmax<T, 1>(g, Xc, ldx, Yc, ldy, bb, false, s);
-    else if (bb <= 4) launch_bmax<T, 4>(g, Xc, ldx, Yc, ldy, bb, vec, s);
-    else if (bb <= 8) launch_bmax<T, 8>(g, Xc, ldx, Yc, ldy, bb, vec, s);
-    else if (bb <= 16) launch_bmax<T, 16>(g, Xc, ldx, Yc, ldy, bb, vec, s);
-    else launch_bmax<T, 32>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+    else if (bb == 2) launch_bmax<T, 4>(g, Xc, ldx, Yc, ldy, bb, vec, s);
+    else if (bb <= 4) launch_cols<T, 4>(g, Xc, ldx, Yc, ldy, bb, s);
+    else if (bb <= 8) launch_cols<T, 8>(g, Xc, ldx, Yc, ldy, bb, s);
+    else if (bb <= 16) launch_cols<T, 16>(g, Xc, ldx, Yc, ldy, bb, s);
+    else launch_cols<T, 32>(g, Xc, ldx, Yc, ldy, bb, s);
   }
 }
 

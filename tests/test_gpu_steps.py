@@ -240,3 +240,25 @@ def test_pcg_correction_fixed_steps(pkg, dt, name):
     err = (np.abs(T - ref).max(axis=0) / scale).max()
     assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
     Gd.close()
+
+
+@pytest.mark.parametrize("p,q,ld_in,beta,ones", [(4, 32, 4, 0.0, 0), (6, 32, 6, 1.0, 1), (32, 16, 32, 0.0, 0),
+                                                 (65 - 1, 24, 64, 0.0, 1)])
+def test_block_update(pkg, p, q, ld_in, beta, ones):
+    """lap_block_update: Y = beta Y + [1 | A] S, including p < q."""
+    import ctypes
+    g = GRAPHS["grid"]()
+    Gd = pkg.Graph(g)
+    A = G.random_block(g.n, ld_in, 3).astype(np.float32)
+    Y0 = G.random_block(g.n, q, 4).astype(np.float32)
+    S = np.random.default_rng(5).standard_normal((p + ones, q))
+    Ad, Yd = _dev(A, torch.float32), _dev(Y0, torch.float32)
+    Sd = torch.from_numpy(S).cuda()
+    st = pkg.lib().lap_block_update(Gd.h, pkg.LAP_F32, ctypes.c_void_p(Yd.data_ptr()), q, q, beta, 1.0,
+                                    ctypes.c_void_p(Ad.data_ptr()), ld_in, p, ones, ctypes.c_void_p(Sd.data_ptr()), q, 0,
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    A64 = A[:, :p].astype(np.float64)
+    ref = beta * Y0 + (np.hstack([np.ones((g.n, 1)), A64]) if ones else A64) @ S
+    assert np.abs(Yd.cpu().double().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    Gd.close()
