@@ -142,7 +142,10 @@ void lap_graph_destroy(lap_graph* g);
  * SpMM lanes per row, number of hub rows. */
 int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm1, int* team, int* nlong);
 /* Override the SpMM schedule: lanes per row (4, 8, 16, 32) and the degree
- * above which a row gets a whole CTA (0 keeps the current value). */
+ * above which a row is a hub, split into chunks of 128 nonzeros that are
+ * spread over warps and combined (0 keeps the current value; default 64).
+ * Calls that run SpMM-type kernels on one handle must be stream-ordered:
+ * the handle's reduction and hub-chunk scratch is shared by them. */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
 
 /* Solve on a handle whose graphs are already on the device (the CSR is not

@@ -330,196 +330,248 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
   if (c < q && keep) keep[(size_t)seg * 64 + c] = kp[c];
 }
 
-// Parallel cyclic Jacobi sweeps (round-robin ordering: mm/2 disjoint
-// rotations per step) on A (mm x LD, symmetric) accumulating V <- V J.  A
-// rotation is skipped when |a_pq| <= rel * sqrt(|a_pp a_qq|) or <= abs_tol;
-// returns after the first sweep that rotates nothing (or max_sweeps).
-template <typename T>
-__device__ int jacobi_sweeps(T* A, T* V, int LD, int mm, T rel, T abs_tol, int max_sweeps, T* cs, int* pq,
-                             int* s_rot) {
+// Parallel cyclic Jacobi in FP32 on A (mm x LD, symmetric, mm even),
+// accumulating V <- V J.  Round-robin ordering: each of the mm - 1 steps of a
+// sweep rotates mm/2 disjoint pairs; thread i < mm/2 finds pair i's rotation,
+// then the two-sided update J^T A J is applied in independent 2x2 blocks
+// (pair i's rows x pair i2's columns, i <= i2, mirrored below the diagonal):
+// two barriers per step.  A rotated pair's own 2x2 block is set to its exact
+// values (a_pq = 0, a_pp - t a_pq, a_qq + t a_pq: Rutishauser's form), so
+// a_pq is not left as rounding noise of order eps |a_pp|.  A rotation is
+// skipped when |a_pq| <= rel sqrt|a_pp a_qq| or <= abs_tol; the sweeps stop
+// once every off-diagonal entry passes that test (checked after each sweep).
+// cs: 4 floats per pair (c, s, a_pp', a_qq'); pq: 2 ints per pair; blk: the
+// (i, i2) block list.  Returns the number of sweeps.
+__device__ int jacobi32(float* A, float* V, int LD, int mm, float rel, float abs_tol, int max_sweeps, float* cs,
+                        int* pq, const short2* blk, int nblk) {
   const int half = mm / 2;
-  int sweep = 0;
-  for (sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) *s_rot = 0;
-    __syncthreads();
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int step = 0; step < mm - 1; ++step) {
-      if (threadIdx.x < half) {
-        const int i = threadIdx.x;
+      if (tid < half) {
         auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
-        int p = at(i), q = at(mm - 1 - i);
-        if (p > q) { const int tmp = p; p = q; q = tmp; }
-        const T apq = A[p * LD + q];
-        T c = T(1), sn = T(0);
-        const T app = A[p * LD + p], aqq = A[q * LD + q];
-        if (fabs(apq) > abs_tol && fabs(apq) > rel * sqrt(fabs(app * aqq))) {
-          const T tau = (aqq - app) / (T(2) * apq);
-          const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-          c = T(1) / sqrt(T(1) + tt * tt);
-          sn = tt * c;
-          *s_rot = 1;
+        int p = at(tid), q = at(mm - 1 - tid);
+        if (p > q) { const int t = p; p = q; q = t; }
+        const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        float c = 1.f, sn = 0.f, dp = app, dq = aqq;
+        if (fabsf(apq) > abs_tol && fabsf(apq) > rel * sqrtf(fabsf(app * aqq))) {
+          const float tau = (aqq - app) / (2.f * apq);
+          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+          c = 1.f / sqrtf(1.f + t * t);
+          sn = t * c;
+          dp = app - t * apq;
+          dq = aqq + t * apq;
         }
-        cs[2 * i] = c; cs[2 * i + 1] = sn;
-        pq[2 * i] = p; pq[2 * i + 1] = q;
+        cs[4 * tid] = c; cs[4 * tid + 1] = sn; cs[4 * tid + 2] = dp; cs[4 * tid + 3] = dq;
+        pq[2 * tid] = p; pq[2 * tid + 1] = q;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {  // rows: A <- J^T A
-        const int i = e / mm, j = e % mm;
-        const T sn = cs[2 * i + 1];
-        if (sn == T(0)) continue;
-        const T c = cs[2 * i];
+      for (int u = tid; u < nblk; u += NT) {
+        const short2 ii = blk[u];
+        const int i = ii.x, i2 = ii.y;
+        const float s1 = cs[4 * i + 1], s2 = cs[4 * i2 + 1];
+        if (s1 == 0.f && s2 == 0.f) continue;
         const int p = pq[2 * i], q = pq[2 * i + 1];
-        const T ap = A[p * LD + j], aq = A[q * LD + j];
-        A[p * LD + j] = c * ap - sn * aq;
-        A[q * LD + j] = sn * ap + c * aq;
+        if (i == i2) {
+          A[p * LD + p] = cs[4 * i + 2];
+          A[q * LD + q] = cs[4 * i + 3];
+          A[p * LD + q] = 0.f;
+          A[q * LD + p] = 0.f;
+          continue;
+        }
+        const int p2 = pq[2 * i2], q2 = pq[2 * i2 + 1];
+        const float c1 = cs[4 * i], c2 = cs[4 * i2];
+        const float a = A[p * LD + p2], b = A[p * LD + q2], c = A[q * LD + p2], d = A[q * LD + q2];
+        const float ra = c1 * a - s1 * c, rb = c1 * b - s1 * d, rc = s1 * a + c1 * c, rd = s1 * b + c1 * d;
+        const float na = c2 * ra - s2 * rb, nb = s2 * ra + c2 * rb, nc = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
+        A[p * LD + p2] = na; A[p * LD + q2] = nb; A[q * LD + p2] = nc; A[q * LD + q2] = nd;
+        A[p2 * LD + p] = na; A[q2 * LD + p] = nb; A[p2 * LD + q] = nc; A[q2 * LD + q] = nd;
       }
-      __syncthreads();
-      for (int e = threadIdx.x; e < half * mm; e += blockDim.x) {  // columns: A <- A J, V <- V J
-        const int i = e / mm, j = e % mm;
-        const T sn = cs[2 * i + 1];
-        if (sn == T(0)) continue;
-        const T c = cs[2 * i];
+      for (int e = tid; e < mm * half; e += NT) {
+        const int r = e / half, i = e - r * half;
+        const float sn = cs[4 * i + 1];
+        if (sn == 0.f) continue;
+        const float c = cs[4 * i];
         const int p = pq[2 * i], q = pq[2 * i + 1];
-        const T ap = A[j * LD + p], aq = A[j * LD + q];
-        A[j * LD + p] = c * ap - sn * aq;
-        A[j * LD + q] = sn * ap + c * aq;
-        const T vp = V[j * LD + p], vq = V[j * LD + q];
-        V[j * LD + p] = c * vp - sn * vq;
-        V[j * LD + q] = sn * vp + c * vq;
+        const float vp = V[r * LD + p], vq = V[r * LD + q];
+        V[r * LD + p] = c * vp - sn * vq;
+        V[r * LD + q] = sn * vp + c * vq;
       }
       __syncthreads();
     }
-    const int any = *s_rot;
-    __syncthreads();
-    if (any == 0) break;
+    int big = 0;
+    for (int e = tid; e < mm * mm; e += NT) {
+      const int i = e / mm, j = e - i * mm;
+      if (i < j) {
+        const float a = fabsf(A[i * LD + j]);
+        if (a > abs_tol && a > rel * sqrtf(fabsf(A[i * LD + i] * A[j * LD + j]))) big = 1;
+      }
+    }
+    if (!__syncthreads_or(big)) return sweep + 1;
   }
-  return sweep;
+  return max_sweeps;
 }
 
-// Symmetric eigensolver, FP64 result, one CTA per matrix (m <= 64).
-// GB300 runs FP32 58x faster than FP64, so the rotations are first found in
-// FP32: FP32 Jacobi sweeps diagonalise fl32(H) to ~1e-7; the FP32
-// eigenvector matrix is then orthonormalised in FP64 (modified Gram-Schmidt),
-// B = Y^T H Y is formed in FP64 (nearly diagonal), and FP64 Jacobi sweeps
-// started from Y finish the job (typically one sweep plus one that finds
-// nothing to rotate).  The result has the accuracy of an all-FP64 Jacobi.
+// Symmetric eigensolver for m <= 64, FP64 result, one CTA per matrix.
+// GB300 issues FP32 about 58x faster than FP64, so the O(m^3 sweeps) work is
+// FP32 and the FP64 work is four matrix products per refinement step:
+//  1. FP32 Jacobi (jacobi32) on fl32(H): eigenvectors X to about 1e-7.
+//  2. Sort ascending (padding index of odd m dropped).
+//  3. `iters` refinement steps (Ogita and Aishima, "Iterative refinement for
+//     symmetric eigenvalue decomposition", 2018) in FP64 on the first nref
+//     columns X_r:  R = I - X^T X_r,  S = X^T H X_r,  lambda_j = s_jj / (1 - r_jj),
+//     delta = 2 (||S - diag(lambda)||_F + ||H||_F ||R||_F),
+//     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
+//     |lambda_j - lambda_i| > delta, else r_ij / 2 (i != j);  E_jj = r_jj / 2;
+//     X_r <- X_r + X E.  A step squares the error of well separated pairs;
+//     a cluster closer than delta keeps an orthonormal basis of its invariant
+//     subspace without resolving it (its couplings are at the FP32 level of
+//     its own eigenvalues).  Columns >= nref keep the FP32 result.
 __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
                                                double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
-                                               const int* __restrict__ seg_skip, int* sweeps_out, int polish,
-                                               double* Bg, int ldb, int64_t sb) {
+                                               const int* __restrict__ seg_skip, int* sweeps_out, int nref,
+                                               int iters) {
   const int seg = blockIdx.x;
   if (seg_skip && seg_skip[seg]) return;
+  const int tid = threadIdx.x, NT = blockDim.x;
   extern __shared__ double sm[];
   const int mm = (m + 1) & ~1;  // even; the padding index is uncoupled
-  const int LD = mm + 1;
-  double* A = sm;                                  // mm x LD
-  double* V = A + mm * LD;                         // mm x LD
-  double* Wd = V + mm * LD;                        // mm x LD (scratch), overlays A32/V32
-  float* A32 = reinterpret_cast<float*>(Wd);
+  const int LD = mm + 1, LM = m + 1;
+  const int nr = nref;
+  const int LR = nr + 1;
+  double* Hs = sm;              // m x LM
+  double* X = Hs + m * LM;      // m x LM (sorted eigenvectors)
+  double* lam = X + m * LM;     // [m]
+  double* W = lam + m;          // union: FP32 Jacobi arrays, or Z, S, R, Xn
+  float* A32 = reinterpret_cast<float*>(W);
   float* V32 = A32 + mm * LD;
-  double* cs = Wd + mm * LD;                       // [mm]
-  float* cs32 = reinterpret_cast<float*>(cs);
-  int* pq = reinterpret_cast<int*>(cs + mm);       // [mm]
-  __shared__ double s_fro;
-  __shared__ int s_rot;
-  __shared__ double s_red[8];
+  double* Z = W;
+  double* S = Z + m * LR;
+  double* R = S + m * LR;
+  double* Xn = R + m * LR;
+  __shared__ float s_cs[4 * 32];
+  __shared__ int s_pq[2 * 32];
+  __shared__ short2 s_blk[32 * 33 / 2];
+  __shared__ int s_rank[64];
+  __shared__ double s_red[3][8];
   const double* H = Hg + (size_t)seg * sh;
-  if (threadIdx.x == 0) s_fro = 0.0;
+
+  // load H (symmetrised) and fl32(H); ||H||_F
+  double fro = 0.0;
+  for (int e = tid; e < mm * mm; e += NT) {
+    const int i = e / mm, j = e - i * mm;
+    const double a = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
+    if (i < m && j < m) Hs[i * LM + j] = a;
+    A32[i * LD + j] = (float)a;
+    V32[i * LD + j] = (i == j) ? 1.f : 0.f;
+    fro += a * a;
+  }
+  const int half = mm / 2;
+  const int nblk = half * (half + 1) / 2;
+  for (int u = tid; u < half * half; u += NT) {
+    const int i = u / half, i2 = u - i * half;
+    if (i2 >= i) s_blk[i * half - i * (i - 1) / 2 + (i2 - i)] = make_short2((short)i, (short)i2);
+  }
+  fro = warp_sum(fro);
+  if ((tid & 31) == 0) s_red[0][tid >> 5] = fro;
   __syncthreads();
-  {
-    double f = 0.0;
-    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-      const int i = e / mm, j = e % mm;
-      const double a = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
-      A[i * LD + j] = a;
-      A32[i * LD + j] = (float)a;
-      V32[i * LD + j] = (i == j) ? 1.f : 0.f;
-      f += a * a;
+  double nH = 0.0;
+  for (int w = 0; w < (NT >> 5); ++w) nH += s_red[0][w];
+  nH = sqrt(nH);
+  // 1. FP32 Jacobi
+  const int sw = jacobi32(A32, V32, LD, mm, 1e-7f, (float)(1e-30 + 1e-12 * nH), 40, s_cs, s_pq, s_blk, nblk);
+  // 2. sort ascending (rank by counting; ties by index)
+  for (int i = tid; i < mm; i += NT) {
+    int rank = -1;
+    if (!(mm != m && fabsf(V32[(mm - 1) * LD + i]) > 0.5f)) {
+      const float di = A32[i * LD + i];
+      rank = 0;
+      for (int j = 0; j < mm; ++j) {
+        if (mm != m && fabsf(V32[(mm - 1) * LD + j]) > 0.5f) continue;
+        const float dj = A32[j * LD + j];
+        rank += (dj < di) || (dj == di && j < i);
+      }
     }
-    f = warp_sum(f);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&s_fro, f);
+    s_rank[i] = rank;
   }
   __syncthreads();
-  const double fro = sqrt(s_fro);
-  // 1. FP32 sweeps
-  int sw32 = jacobi_sweeps<float>(A32, V32, LD, mm, 1e-7f, (float)(1e-9 * fro), 30, cs32, pq, &s_rot);
-  // 2. Y = V32 in FP64, orthonormalised by modified Gram-Schmidt (columns)
-  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) V[(e / mm) * LD + (e % mm)] = (double)V32[(e / mm) * LD + (e % mm)];
+  for (int e = tid; e < mm * m; e += NT) {
+    const int r = e / mm, i = e - r * mm;  // row r < m, source column i
+    const int k = s_rank[i];
+    if (k >= 0) X[r * LM + k] = (double)V32[r * LD + i];
+  }
+  for (int i = tid; i < mm; i += NT)
+    if (s_rank[i] >= 0) lam[s_rank[i]] = (double)A32[i * LD + i];
   __syncthreads();
-  for (int j = 0; j < mm; ++j) {
-    double nrm = 0.0;
-    for (int r = threadIdx.x; r < mm; r += blockDim.x) nrm += V[r * LD + j] * V[r * LD + j];
-    nrm = warp_sum(nrm);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nrm;
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  // 3. refinement of the first nr columns
+  for (int it = 0; it < iters && nr > 0; ++it) {
+    for (int e = tid; e < m * nr; e += NT) {  // Z = H X_r
+      const int r = e / nr, j = e - r * nr;
       double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
-      s_red[0] = 1.0 / sqrt(t);
+      for (int l = 0; l < m; ++l) t = fma(Hs[r * LM + l], X[l * LM + j], t);
+      Z[r * LR + j] = t;
     }
     __syncthreads();
-    const double inv = s_red[0];
-    for (int r = threadIdx.x; r < mm; r += blockDim.x) V[r * LD + j] *= inv;
+    for (int e = tid; e < m * nr; e += NT) {  // S = X^T Z, R = I - X^T X_r
+      const int i = e / nr, j = e - i * nr;
+      double ts = 0.0, tr = 0.0;
+      for (int r = 0; r < m; ++r) {
+        const double xi = X[r * LM + i];
+        ts = fma(xi, Z[r * LR + j], ts);
+        tr = fma(xi, X[r * LM + j], tr);
+      }
+      S[i * LR + j] = ts;
+      R[i * LR + j] = (i == j ? 1.0 : 0.0) - tr;
+    }
     __syncthreads();
-    // subtract column j from the later columns: one thread per later column
-    for (int l = j + 1 + threadIdx.x; l < mm; l += blockDim.x) {
-      double d = 0.0;
-      for (int r = 0; r < mm; ++r) d += V[r * LD + j] * V[r * LD + l];
-      for (int r = 0; r < mm; ++r) V[r * LD + l] -= d * V[r * LD + j];
+    for (int j = tid; j < nr; j += NT) lam[j] = S[j * LR + j] / (1.0 - R[j * LR + j]);
+    __syncthreads();
+    double offs = 0.0, nrr = 0.0;
+    for (int e = tid; e < m * nr; e += NT) {
+      const int i = e / nr, j = e - i * nr;
+      const double d = S[i * LR + j] - (i == j ? lam[j] : 0.0);
+      offs += d * d;
+      nrr += R[i * LR + j] * R[i * LR + j];
+    }
+    offs = warp_sum(offs);
+    nrr = warp_sum(nrr);
+    if ((tid & 31) == 0) { s_red[1][tid >> 5] = offs; s_red[2][tid >> 5] = nrr; }
+    __syncthreads();
+    double so = 0.0, sr = 0.0;
+    for (int w = 0; w < (NT >> 5); ++w) { so += s_red[1][w]; sr += s_red[2][w]; }
+    const double delta = 2.0 * (sqrt(so) + nH * sqrt(sr));
+    for (int e = tid; e < m * nr; e += NT) {  // E in place of S
+      const int i = e / nr, j = e - i * nr;
+      double ev;
+      if (i == j) ev = 0.5 * R[i * LR + j];
+      else {
+        const double gap = lam[j] - lam[i];
+        ev = fabs(gap) > delta ? (S[i * LR + j] + lam[j] * R[i * LR + j]) / gap : 0.5 * R[i * LR + j];
+      }
+      S[i * LR + j] = ev;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * nr; e += NT) {  // Xn = X_r + X E
+      const int r = e / nr, j = e - r * nr;
+      double t = X[r * LM + j];
+      for (int i = 0; i < m; ++i) t = fma(X[r * LM + i], S[i * LR + j], t);
+      Xn[r * LR + j] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * nr; e += NT) {
+      const int r = e / nr, j = e - r * nr;
+      X[r * LM + j] = Xn[r * LR + j];
     }
     __syncthreads();
   }
-  // 3. B = Y^T A Y in FP64: Wd = A Y, then A <- Y^T Wd
-  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-    const int i = e / mm, j = e % mm;
-    double t = 0.0;
-    for (int r = 0; r < mm; ++r) t += A[i * LD + r] * V[r * LD + j];
-    Wd[i * LD + j] = t;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-    const int i = e / mm, j = e % mm;
-    if (j < i) continue;
-    double t = 0.0;
-    for (int r = 0; r < mm; ++r) t += V[r * LD + i] * Wd[r * LD + j];
-    A[i * LD + j] = t;
-    A[j * LD + i] = t;
-  }
-  __syncthreads();
-  // 4. FP64 sweeps from V = Y (skipped when an FP32-accurate rotation is
-  //    enough: B then keeps small off-diagonal entries, returned in Bg)
-  const int sw64 = polish ? jacobi_sweeps<double>(A, V, LD, mm, 1e-15, 1e-17 * fro, 30, cs, pq, &s_rot) : 0;
-  // sort the m eigenvalues ascending (rank by counting; ties by index); the
-  // padding index (if any) is dropped: its column is e_{mm-1}, uncoupled
   double* ev = evals + (size_t)seg * se;
   double* Y = Yg + (size_t)seg * sy;
-  __shared__ int s_rank[64];
-  for (int i = threadIdx.x; i < mm; i += blockDim.x) {
-    // identify real columns: the padding column has its weight in row mm-1
-    if (mm != m && fabs(V[(mm - 1) * LD + i]) > 0.5) continue;
-    const double di = A[i * LD + i];
-    int rank = 0;
-    for (int j = 0; j < mm; ++j) {
-      if (mm != m && fabs(V[(mm - 1) * LD + j]) > 0.5) continue;
-      const double dj = A[j * LD + j];
-      rank += (dj < di) || (dj == di && j < i);
-    }
-    ev[rank] = di;
-    s_rank[i] = rank;
-    for (int r = 0; r < m; ++r) Y[(size_t)r * ldy + rank] = V[r * LD + i];
+  for (int j = tid; j < m; j += NT) ev[j] = lam[j];
+  for (int e = tid; e < m * m; e += NT) {
+    const int r = e / m, j = e - r * m;
+    Y[(size_t)r * ldy + j] = X[r * LM + j];
   }
-  if (Bg) {
-    // B in the sorted order: Bout[rank_i][rank_j] = A[i][j] (padding skipped)
-    for (int i = threadIdx.x; i < mm; i += blockDim.x)
-      if (mm != m && fabs(V[(mm - 1) * LD + i]) > 0.5) s_rank[i] = -1;
-    __syncthreads();
-    double* B = Bg + (size_t)seg * sb;
-    for (int e = threadIdx.x; e < mm * mm; e += blockDim.x) {
-      const int i = e / mm, j = e % mm;
-      const int ri = s_rank[i], rj = s_rank[j];
-      if (ri >= 0 && rj >= 0) B[(size_t)ri * ldb + rj] = 0.5 * (A[i * LD + j] + A[j * LD + i]);
-    }
-  }
-  if (sweeps_out && threadIdx.x == 0) sweeps_out[seg] = sw32 * 100 + sw64;
+  if (sweeps_out && tid == 0) sweeps_out[seg] = sw;
 }
 
 // ------------------------------------------------------------------ projected PCG passes
@@ -834,16 +886,19 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 }
 
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,
-          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int polish, double* B, int ldb, int64_t sb) {
+          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref, int iters) {
   LAP_PROF("syev", 0.0, s);
   const int mm = (m + 1) & ~1;
-  const size_t smem = sizeof(double) * (3 * (size_t)mm * (mm + 1) + mm) + sizeof(int) * mm;
+  const int nr = (nref < 0 || nref > m) ? m : nref;
+  const size_t jac = sizeof(float) * 2 * (size_t)mm * (mm + 1);
+  const size_t ref = sizeof(double) * 4 * (size_t)m * (nr + 1);
+  const size_t smem = sizeof(double) * (2 * (size_t)m * (m + 1) + m) + (jac > ref ? jac : ref);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 110 * 1024);
+    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
     attr_set = true;
   }
-  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out, polish, B, ldb, sb);
+  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out, nr, iters);
 }
 
 template <typename T>

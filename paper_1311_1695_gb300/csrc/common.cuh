@@ -47,11 +47,23 @@ struct DevGraph {
   int ntiles;
   const int* tile_ptr;   // [nseg+1] device: tiles of segment s are [tile_ptr[s], tile_ptr[s+1])
   int* counters;         // [nseg] zero-initialised, self-resetting
-  const int* long_rows;  // rows with degree > long_thresh, handled one CTA per row
+  const int* long_rows;  // hub rows: degree > long_thresh, longest first
   int nlong;
   int long_thresh;
   int team;              // lanes per row in the SpMM (autotuned)
+  // Hub rows are split into chunks of at most kHubChunk nonzeros, one warp
+  // per chunk.  A hub with several chunks combines them through hub_part
+  // (per chunk: kMaxCols column sums + the weight sum) and an arrival
+  // counter; the last chunk to arrive sums the partials in chunk order.
+  const int4* chunks;    // [nchunk] {row, p0, p1, hub index}
+  int nchunk;
+  const int2* hub_chunks;  // [nlong] {first chunk, number of chunks}
+  int* hub_cnt;          // [nlong] arrival counters, zero at rest
+  double* hub_part;      // [nchunk * kPartStride]
 };
+
+constexpr int kHubChunk = 128;
+constexpr int kPartStride = kMaxCols + 1;
 
 // Host-side mirror kept next to the device arrays.
 struct HostGraph {

@@ -79,20 +79,40 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     const int da = g->rowptr_h[a + 1] - g->rowptr_h[a], db = g->rowptr_h[b + 1] - g->rowptr_h[b];
     return da != db ? da > db : a < b;
   });
-  if (g->d_long) cudaFree(g->d_long);
-  if (g->d_long_seg) cudaFree(g->d_long_seg);
-  g->d_long = nullptr;
-  g->d_long_seg = nullptr;
+  cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks);
+  cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part);
+  g->d_long = nullptr; g->d_long_seg = nullptr; g->d_chunks = nullptr; g->d_hub_chunks = nullptr;
+  g->d_hub_cnt = nullptr; g->d_hub_part = nullptr;
   std::vector<int> hseg(hubs.size());
   for (size_t h = 0; h < hubs.size(); ++h)
     hseg[h] = (int)(std::upper_bound(g->row0.begin(), g->row0.end(), hubs[h]) - g->row0.begin()) - 1;
+  // chunks of at most kHubChunk nonzeros, hubs in order (longest first)
+  std::vector<int4> chunks;
+  std::vector<int2> hub_chunks(hubs.size());
+  for (size_t h = 0; h < hubs.size(); ++h) {
+    const int r = hubs[h], p0 = g->rowptr_h[r], p1 = g->rowptr_h[r + 1];
+    hub_chunks[h] = make_int2((int)chunks.size(), (p1 - p0 + kHubChunk - 1) / kHubChunk);
+    for (int p = p0; p < p1; p += kHubChunk) chunks.push_back(make_int4(r, p, std::min(p + kHubChunk, p1), (int)h));
+  }
   int rc = dev_alloc_copy(&g->d_long, hubs.data(), hubs.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_long_seg, hseg.data(), hseg.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_chunks, chunks.data(), chunks.size());
+  rc = rc ? rc : dev_alloc_copy(&g->d_hub_chunks, hub_chunks.data(), hub_chunks.size());
+  rc = rc ? rc : dev_alloc_copy<int>(&g->d_hub_cnt, nullptr, hubs.size());
+  rc = rc ? rc : dev_alloc_copy<double>(&g->d_hub_part, nullptr, chunks.size() * kPartStride);
   if (rc) return rc;
-  rc = dev_alloc_copy(&g->d_long_seg, hseg.data(), hseg.size());
-  if (rc) return rc;
+  if (!hubs.empty() && cudaMemset(g->d_hub_cnt, 0, sizeof(int) * hubs.size()) != cudaSuccess) {
+    set_error("cudaMemset failed");
+    return LAP_ECUDA;
+  }
   g->long_rows_h = hubs;
   g->dg.long_rows = g->d_long;
   g->dg.nlong = (int)hubs.size();
+  g->dg.chunks = g->d_chunks;
+  g->dg.nchunk = (int)chunks.size();
+  g->dg.hub_chunks = g->d_hub_chunks;
+  g->dg.hub_cnt = g->d_hub_cnt;
+  g->dg.hub_part = g->d_hub_part;
   return LAP_OK;
 }
 
@@ -210,7 +230,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   d.counters = g->red.counter;
   // schedule heuristic (overridden by the autotuner or the caller)
   d.team = g->avg_degree <= 6.0 ? 4 : (g->avg_degree <= 24.0 ? 8 : (g->avg_degree <= 96.0 ? 16 : 32));
-  d.long_thresh = 32 * d.team;
+  d.long_thresh = 64;
   rc = graph_set_schedule(g, 0, 0);
   if (rc) { graph_free(g); return rc; }
   *out = g;
@@ -222,6 +242,7 @@ void graph_free(lap_graph* g) {
   cudaFree(g->d_rowptr); cudaFree(g->d_colidx); cudaFree(g->d_w32); cudaFree(g->d_w64);
   cudaFree(g->d_deg64); cudaFree(g->d_norm1); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
   cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->red.acc); cudaFree(g->red.counter);
+  cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks); cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part);
   cudaFree(g->scratch); cudaFree(g->small);
   g->pcg.release();
   delete g;

@@ -52,6 +52,10 @@ struct lap_graph {
   int* d_tile_ptr = nullptr;
   int* d_long = nullptr;
   int* d_long_seg = nullptr;   // segment of each hub row
+  int4* d_chunks = nullptr;    // hub chunks {row, p0, p1, hub}
+  int2* d_hub_chunks = nullptr;
+  int* d_hub_cnt = nullptr;
+  double* d_hub_part = nullptr;
   // host copies
   std::vector<int> row0, tile_ptr;
   std::vector<double> norm1;

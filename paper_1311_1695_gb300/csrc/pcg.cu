@@ -6,8 +6,9 @@
 // indefinite system is the paper's choice, Section 3.2).
 //
 // Each iteration has three phases separated by grid-wide barriers:
-//   A  q~ = L p - theta p (degree-fused SpMM of the CTA's rows, hub rows
-//      spread round-robin over the CTAs), partial G1 = [1|X]^T q~, p.q~
+//   A  q~ = L p - theta p (degree-fused SpMM of the CTA's rows, chunks of
+//      hub rows spread round-robin over all warps), partial G1 = [1|X]^T q~,
+//      p.q~
 //   B  alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
 //      z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r
 //   C  beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
@@ -28,6 +29,7 @@
 // barrier still bounds its spin and raises an error flag (the kernel then
 // returns early and the host reports LAP_ETIMEOUT) rather than hang.
 #include "common.cuh"
+#include "hub.cuh"
 #include "kernels.cuh"
 #include "pcg_fused.cuh"
 #include "prof.h"
@@ -152,7 +154,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
   const int ld = f.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
-  const int slot = warp * RW + lane / BWL;  // row slot in the CTA
   constexpr int SLOTS = NW * RW;
   const bool colok = c < b;
   const int stride1 = f.acc_stride;
@@ -259,73 +260,73 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
           int p0 = 0, p1 = 0;
           if (rv_) { p0 = g.rowptr[r]; p1 = g.rowptr[r + 1]; }
           const bool hub = (p1 - p0) > g.long_thresh;
-          T a = T(0), ws = T(0);
-          if (!hub) {
+          T a = T(0);
+          if (!hub && colok) {
+            if (w) {
 #pragma unroll 4
-            for (int p = p0; p < p1; ++p) {
-              const int j = __ldg(g.colidx + p);
-              const T wv = w ? __ldg(w + p) : T(1);
-              if (colok) a += wv * __ldcg(f.P + (size_t)j * ld + c);
-              ws += wv;
+              for (int p = p0; p < p1; ++p) a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+            } else {
+#pragma unroll 4
+              for (int p = p0; p < p1; ++p) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
             }
           }
           const size_t o = (size_t)r * ld + c;
           const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
           const T pv = ok ? f.P[o] : T(0);
-          const T d = w ? ws : T(p1 - p0);
+          const T d = rv_ ? deg[r] : T(0);
           const T q = (ok && !hub) ? d * pv - a - thc * pv : T(0);
           if (ok && !hub) f.AP[o] = q;
           gram_col<T, BMAX, BWL>(acc, xc, q, b);
           ex[0] += pv * q;
         }
       }
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
-    }
-    // hub rows, round-robin over the CTAs: the CTA's row groups split the
-    // row's nonzeros (lanes as columns), then reduce over groups and warps
-    for (int h = blockIdx.x; h < g.nlong; h += gridDim.x) {
-      const int row = g.long_rows[h];
-      const int seg = f.hub_seg[h];
-      if (f.seg_skip && f.seg_skip[seg]) continue;
-      const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-      T a = T(0), ws = T(0);
-      for (int p = p0 + slot; p < p1; p += SLOTS) {
-        const int j = __ldg(g.colidx + p);
-        const T wv = w ? __ldg(w + p) : T(1);
-        if (colok) a += wv * __ldcg(f.P + (size_t)j * ld + c);
-        ws += wv;
-      }
+      // hub rows: chunks of at most kHubChunk nonzeros, one warp each,
+      // round-robin over all warps of the grid; the warp completing a hub
+      // (hub.cuh) writes its q~ row and adds its share of G1 and p.q~ (to
+      // the CTA's registers when the hub is in the CTA's current graph,
+      // else with atomics)
+      for (int ch = blockIdx.x * NW + warp; ch < g.nchunk; ch += gridDim.x * NW) {
+        const int4 cc = g.chunks[ch];
+        const int row = cc.x;
+        const int seg = f.hub_seg[cc.w];
+        if (f.seg_skip && f.seg_skip[seg]) continue;  // whole warp
+        T a = T(0);
+        if (colok) {
+          if (w) {
+#pragma unroll 8
+            for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
+              a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          } else {
+#pragma unroll 8
+            for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          }
+        }
 #pragma unroll
-      for (int o = BWL; o < 32; o <<= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        ws += __shfl_xor_sync(0xffffffffu, ws, o);
+        for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (!hub_finish<T>(g, ch, cc, a, b)) continue;
+        const bool own = colok && lane < BWL;  // group 0 holds the row
+        const T d = deg[row];
+        const T pv = own ? __ldcg(f.P + (size_t)row * ld + c) : T(0);
+        const T thc = own ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
+        const T q = own ? d * pv - a - thc * pv : T(0);
+        if (own) f.AP[(size_t)row * ld + c] = q;
+        const T xc = own ? X[(size_t)row * f.ldx + c] : T(0);
+        if (seg == cur) {
+          gram_col<T, BMAX, BWL>(acc, xc, q, b);
+          ex[0] += pv * q;
+        } else {
+          double* A1 = f.acc1 + (size_t)seg * stride1;
+          for (int i = 0; i < b; ++i) {
+            const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+            if (own) atomicAdd(A1 + (size_t)(1 + i) * b + c, (double)(xi * q));
+          }
+          if (own) {
+            atomicAdd(A1 + c, (double)q);
+            atomicAdd(A1 + nout + c, (double)(pv * q));
+          }
+        }
       }
-      T* hred = reinterpret_cast<T*>(red);  // [NW][BWL + 1], then q~ [BMAX], x [BMAX]
-      if (lane < BWL) hred[warp * (BWL + 1) + lane] = a;
-      if (lane == 0) hred[warp * (BWL + 1) + BWL] = ws;
-      __syncthreads();
-      T* qs = hred + NW * (BWL + 1);
-      T* xs = qs + BMAX;
-      if (threadIdx.x < b) {
-        const int q = threadIdx.x;
-        T sum = T(0), dsum = T(0);
-        for (int v = 0; v < NW; ++v) { sum += hred[v * (BWL + 1) + q]; dsum += hred[v * (BWL + 1) + BWL]; }
-        const T d = w ? dsum : T(p1 - p0);
-        const T pv = __ldcg(f.P + (size_t)row * ld + q);
-        const T qq = d * pv - sum - (T)f.theta[(size_t)seg * f.sth + q] * pv;
-        f.AP[(size_t)row * ld + q] = qq;
-        qs[q] = qq;
-        xs[q] = X[(size_t)row * f.ldx + q];
-        atomicAdd(f.acc1 + (size_t)seg * stride1 + nout + q, (double)pv * (double)qq);
-      }
-      __syncthreads();
-      double* A1 = f.acc1 + (size_t)seg * stride1;
-      for (int o = threadIdx.x; o < nout; o += kThreads) {
-        const int i = o / b, j = o - i * b;
-        const double v = (double)(i == 0 ? qs[j] : xs[i - 1] * qs[j]);
-        if (v != 0.0) atomicAdd(A1 + o, v);
-      }
-      __syncthreads();
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
     }
     if (!grid_barrier(f.bar)) return;
     // ---------------------------------------------------------------- phase B

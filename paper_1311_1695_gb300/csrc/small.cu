@@ -18,18 +18,15 @@ __global__ void k_inv_sqrt(int count, const double* in, double* out, double floo
   }
 }
 
-// H <- the leading mk x mk block of B = Y^T H Y (the restarted projected
-// matrix in the rotated basis: diagonal up to rounding when the eigensolve
-// was polished), zeros elsewhere.
-__global__ void k_h_restart(double* H, int ldh, int64_t sh, int mmax, const double* B, int64_t sb, int mk,
+// H <- diag(theta[0:mk]) (the restarted projected matrix), zeros elsewhere.
+__global__ void k_h_restart(double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                             const int* seg_skip) {
   const int s = blockIdx.x;
   if (seg_skip && seg_skip[s]) return;
   double* h = H + (size_t)s * sh;
-  const double* bs = B + (size_t)s * sb;
   for (int e = threadIdx.x; e < mmax * mmax; e += blockDim.x) {
     const int i = e / mmax, j = e % mmax;
-    h[(size_t)i * ldh + j] = (i < mk && j < mk) ? bs[(size_t)i * ldh + j] : 0.0;
+    h[(size_t)i * ldh + j] = (i == j && i < mk) ? theta[(size_t)s * st + i] : 0.0;
   }
 }
 
@@ -118,10 +115,10 @@ void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStre
   LAP_PROF("small", 0.0, s);
   k_inv_sqrt<<<(count + 255) / 256, 256, 0, s>>>(count, in, out, floor_v);
 }
-void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* B, int64_t sb, int mk,
+void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                const int* seg_skip, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
-  k_h_restart<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, B, sb, mk, seg_skip);
+  k_h_restart<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, theta, st, mk, seg_skip);
 }
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s) {

@@ -5,7 +5,7 @@
 namespace lapeig {
 
 void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s);
-void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* B, int64_t sb, int mk,
+void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                const int* seg_skip, cudaStream_t s);
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s);

@@ -82,7 +82,7 @@ struct JD {
   TP* P;
   TP* AP;
   // small FP64 per segment
-  double *H, *Y, *Bm, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
+  double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
   PcgState ps;
   // host mirrors
@@ -102,7 +102,7 @@ struct JD {
     add(n * z.ldb * sizeof(TV));
     for (int i = 0; i < 7; ++i) add(n * z.ldb * sizeof(TP));
     const size_t mm = (size_t)z.mmax * z.mmax;
-    add(S * mm * 8); add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
+    add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
     for (int i = 0; i < 5; ++i) add(S * 64 * 4);
     for (int i = 0; i < 5; ++i) add(S * 64 * 8);
@@ -125,7 +125,6 @@ struct JD {
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
     Y = a.take<double>(S * mm);
-    Bm = a.take<double>(S * mm);
     theta = a.take<double>(S * z.mmax);
     rn2 = a.take<double>(S * 64);
     Gm = a.take<double>(S * 65 * 64);
@@ -192,15 +191,14 @@ struct JD {
 
   // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
   int rayleigh_ritz(int m) {
-    // FP64 basis: fully FP64-accurate eigensolve; FP32 basis: FP32-accurate
-    // rotation (exactly orthonormal), H restarted to the exact Y^T H Y block.
-    const int polish = sizeof(TV) == 8 ? 1 : 0;
-    syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
-         seg_skip, sweeps, st, polish, Bm, z.mmax, (int64_t)z.mmax * z.mmax);
+    // only the mk kept Ritz pairs are refined to FP64 accuracy (one step
+    // from the FP32 Jacobi result); H restarts as diag(theta[0:mk])
     const int mk = std::min(m, z.mk);
+    syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
+         seg_skip, sweeps, st, mk, 1);
     update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     update<TV>(g, W, z.ldv, mk, 0.0, 1.0, W, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
-    h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, Bm, z.mmax, mk, seg_skip, st);
+    h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
     return mk;
   }
 

@@ -3,21 +3,25 @@
 //
 //   Y[i, c] = d_i X[i, c] - sum_{j in row i} w_ij X[j, c],   c < b
 //
-// d_i is never read from memory: it is the row length (unit weights) or the
-// sum of the row's weights, accumulated in the same pass over the row.
+// d_i is read once per row from the stored degrees (FP64 sum of the weights,
+// or its FP32 rounding): accumulating it in the pass would double the FP64
+// arithmetic of an FP64 SpMM, which on GB300 is bound by the FP64 pipe.
 //
 // Load balance for power-law degree skew.  For b >= 3 (k_spmm_cols) a group
 // of lanes owns a row with one lane per column; for b <= 2 a team of TEAM
 // lanes (TEAM | 32) strides over the row's nonzeros, each lane accumulating
-// the b columns in registers, then a butterfly reduction inside the team.  Rows longer than long_thresh (the hubs) are
-// listed at set-up and each gets a whole 256-thread CTA with a block
-// reduction.  Both kinds run in one launch: the first nlong CTAs take the hub
-// rows, the rest the ordinary rows (which skip the hubs).
+// the b columns in registers, then a butterfly reduction inside the team.
+// Rows longer than long_thresh (the hubs) are cut at set-up into chunks of at
+// most kHubChunk nonzeros; one warp takes a chunk and the chunks of a hub are
+// combined by the last to finish (hub.cuh), so no row costs more than a
+// chunk's worth of dependent loads.  Both kinds run in one launch: the first
+// blocks take the chunks (a warp each), the rest the ordinary rows.
 //
 // Gathers of X rows read b contiguous values; with FP32 (FP64) data, 16-byte
 // aligned rows and b padded to 4 (2) inside the leading dimension, they are
 // issued as float4 (double2) loads.
 #include "common.cuh"
+#include "hub.cuh"
 #include "kernels.cuh"
 #include "prof.h"
 
@@ -26,6 +30,10 @@ namespace lapeig {
 template <typename T> struct Vec2 {};
 template <> struct Vec2<float> { using type = float4; static constexpr int w = 4; };
 template <> struct Vec2<double> { using type = double2; static constexpr int w = 2; };
+
+template <typename T> __device__ __forceinline__ T degree_of(const DevGraph& g, int row);
+template <> __device__ __forceinline__ float degree_of<float>(const DevGraph& g, int row) { return __ldg(g.deg32 + row); }
+template <> __device__ __forceinline__ double degree_of<double>(const DevGraph& g, int row) { return __ldg(g.deg64 + row); }
 
 template <typename T> __device__ __forceinline__ const T* weights_of(const DevGraph& g);
 template <> __device__ __forceinline__ const float* weights_of<float>(const DevGraph& g) { return g.w32; }
@@ -62,53 +70,41 @@ __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ 
   T acc[BMAX];
 #pragma unroll
   for (int c = 0; c < BMAX; ++c) acc[c] = T(0);
-  T dsum = T(0);
 
-  if ((int)blockIdx.x < g.nlong) {
-    // ---- hub row: one CTA
-    __shared__ T red[8][BMAX + 1];
-    const int row = g.long_rows[blockIdx.x];
-    const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+  const int nhb = (g.nchunk + 7) / 8;  // blocks of hub chunks, a warp each
+  if ((int)blockIdx.x < nhb) {
+    const int lane = threadIdx.x & 31;
+    const int ch = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (ch >= g.nchunk) return;  // whole warp
+    const int4 cc = g.chunks[ch];
+    for (int p = cc.y + lane; p < cc.z; p += 32) {
       const int j = __ldg(g.colidx + p);
       const T wv = w ? __ldg(w + p) : T(1);
       gather_row<T, BMAX, VEC>(acc, X + (size_t)j * ldx, wv, b);
-      dsum += wv;
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T a = T(0);
 #pragma unroll
     for (int c = 0; c < BMAX; ++c) {
-      T v = warp_sum(acc[c]);
-      if (lane == 0) red[warp][c] = v;
+      const T v = warp_sum(acc[c]);
+      if (lane == c) a = v;
     }
-    {
-      T v = warp_sum(dsum);
-      if (lane == 0) red[warp][BMAX] = v;
-    }
-    __syncthreads();
-    const int nw = blockDim.x >> 5;
-    if ((int)threadIdx.x < b) {
-      const int c = threadIdx.x;
-      T s = T(0), ds = T(0);
-      for (int q = 0; q < nw; ++q) { s += red[q][c]; ds += red[q][BMAX]; }
-      const T deg = w ? ds : T(p1 - p0);
-      Y[(size_t)row * ldy + c] = deg * X[(size_t)row * ldx + c] - s;
-    }
+    if (!hub_finish<T>(g, ch, cc, a, b)) return;
+    const int row = cc.x;
+    if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
     return;
   }
 
   // ---- ordinary rows: TEAM lanes per row
-  const int tid = (blockIdx.x - g.nlong) * blockDim.x + threadIdx.x;
+  const int tid = (blockIdx.x - nhb) * blockDim.x + threadIdx.x;
   const int row = tid / TEAM;
   const int lane = threadIdx.x & (TEAM - 1);
   if (row >= g.n) return;  // uniform within a team
   const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-  if (p1 - p0 > g.long_thresh) return;  // a hub CTA owns it
+  if (p1 - p0 > g.long_thresh) return;  // a hub: its chunks are done by the first blocks
   for (int p = p0 + lane; p < p1; p += TEAM) {
     const int j = __ldg(g.colidx + p);
     const T wv = w ? __ldg(w + p) : T(1);
     gather_row<T, BMAX, VEC>(acc, X + (size_t)j * ldx, wv, b);
-    dsum += wv;
   }
   if constexpr (TEAM > 1) {
     const unsigned mask = (TEAM == 32) ? 0xffffffffu
@@ -117,10 +113,9 @@ __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ 
     for (int o = TEAM / 2; o > 0; o >>= 1) {
 #pragma unroll
       for (int c = 0; c < BMAX; ++c) acc[c] += __shfl_xor_sync(mask, acc[c], o);
-      dsum += __shfl_xor_sync(mask, dsum, o);
     }
   }
-  const T deg = w ? dsum : T(p1 - p0);
+  const T deg = degree_of<T>(g, row);
   const T* xr = X + (size_t)row * ldx;
   T* yr = Y + (size_t)row * ldy;
 #pragma unroll
@@ -131,8 +126,8 @@ __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ 
 // Lanes as columns (b >= 3): a group of BWL lanes (BWL = next power of two
 // >= b) owns a row; for every nonzero, lane c loads column c of the
 // neighbour's row (one broadcast index load, one contiguous b-value gather
-// per group) and accumulates it; no reduction across lanes is needed.  Hub
-// rows (degree > long_thresh) are split over the row groups of a whole CTA.
+// per group) and accumulates it; no reduction across lanes is needed.  A hub
+// chunk is shared by the warp's RW = 32 / BWL groups, reduced by shuffles.
 template <typename T, int BWL>
 __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restrict__ X, int ldx,
                                                    T* __restrict__ Y, int ldy, int b) {
@@ -141,54 +136,52 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
   const bool colok = c < b;
-  if ((int)blockIdx.x < g.nlong) {
-    __shared__ T red[8][BWL + 1];
-    const int row = g.long_rows[blockIdx.x];
-    const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-    const int slot = warp * RW + lane / BWL;
-    T a = T(0), ws = T(0);
-    for (int p = p0 + slot; p < p1; p += 8 * RW) {
-      const int j = __ldg(g.colidx + p);
-      const T wv = w ? __ldg(w + p) : T(1);
-      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
-      ws += wv;
+  const int nhb = (g.nchunk + 7) / 8;
+  if ((int)blockIdx.x < nhb) {
+    const int ch = blockIdx.x * 8 + warp;
+    if (ch >= g.nchunk) return;  // whole warp
+    const int4 cc = g.chunks[ch];
+    T a = T(0);
+    if (w) {
+#pragma unroll 8
+      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+        const int j = __ldg(g.colidx + p);
+        const T wv = __ldg(w + p);
+        if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+      }
+    } else {
+#pragma unroll 8
+      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+        const int j = __ldg(g.colidx + p);
+        if (colok) a += __ldg(X + (size_t)j * ldx + c);
+      }
     }
 #pragma unroll
-    for (int o = BWL; o < 32; o <<= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      ws += __shfl_xor_sync(0xffffffffu, ws, o);
-    }
-    if (lane < BWL) red[warp][lane] = a;
-    if (lane == 0) red[warp][BWL] = ws;
-    __syncthreads();
-    if ((int)threadIdx.x < b) {
-      T sum = T(0), ds = T(0);
-      for (int v = 0; v < 8; ++v) { sum += red[v][threadIdx.x]; ds += red[v][BWL]; }
-      const T deg = w ? ds : T(p1 - p0);
-      Y[(size_t)row * ldy + threadIdx.x] = deg * X[(size_t)row * ldx + threadIdx.x] - sum;
-    }
+    for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (!hub_finish<T>(g, ch, cc, a, b)) return;
+    const int row = cc.x;
+    if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
     return;
   }
-  const int row = ((blockIdx.x - g.nlong) * 8 + warp) * RW + lane / BWL;
+  const int row = ((blockIdx.x - nhb) * 8 + warp) * RW + lane / BWL;
   if (row >= g.n) return;  // no cross-group shuffles below
   const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
   if (p1 - p0 > g.long_thresh || !colok) return;
-  T a = T(0), ws = T(0);
+  T a = T(0);
+  if (w) {
 #pragma unroll 4
-  for (int p = p0; p < p1; ++p) {
-    const int j = __ldg(g.colidx + p);
-    const T wv = w ? __ldg(w + p) : T(1);
-    a += wv * __ldg(X + (size_t)j * ldx + c);
-    ws += wv;
+    for (int p = p0; p < p1; ++p) a += __ldg(w + p) * __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
+  } else {
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) a += __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
   }
-  const T deg = w ? ws : T(p1 - p0);
-  Y[(size_t)row * ldy + c] = deg * X[(size_t)row * ldx + c] - a;
+  Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
 }
 
 template <typename T, int BWL>
 static void launch_cols(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
   constexpr int RPB = 8 * (32 / BWL);  // rows per block
-  const int blocks = g.nlong + (g.n + RPB - 1) / RPB;
+  const int blocks = (g.nchunk + 7) / 8 + (g.n + RPB - 1) / RPB;
   if (blocks > 0) k_spmm_cols<T, BWL><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
 }
 
@@ -197,7 +190,7 @@ static void launch_team(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, i
                         cudaStream_t s) {
   const int threads = 256;
   const int rows_per_block = threads / TEAM;
-  const int blocks = g.nlong + (g.n + rows_per_block - 1) / rows_per_block;
+  const int blocks = (g.nchunk + 7) / 8 + (g.n + rows_per_block - 1) / rows_per_block;
   if (blocks == 0) return;
   if (vec)
     k_spmm<T, BMAX, TEAM, true><<<blocks, threads, 0, s>>>(g, X, ldx, Y, ldy, b);
@@ -273,12 +266,11 @@ int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_ou
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int teams[4] = {4, 8, 16, 32};
-  const int threshs[4] = {64, 256, 1024, 1 << 30};
+  const int threshs[4] = {32, 64, 128, 1 << 30};
   float best = 1e30f;
   int bt = g->dg.team, bh = g->dg.long_thresh;
   for (int ti = 0; ti < 4; ++ti) {
     for (int hi = 0; hi < 4; ++hi) {
-      if (threshs[hi] < teams[ti] * 8) continue;  // hub CTAs only pay off for long rows
       if (graph_set_schedule(g, teams[ti], threshs[hi]) != LAP_OK) continue;
       auto run = [&]() {
         if (dtype == LAP_F32) spmm<float>(g->dg, (const float*)X, ld, (float*)Y, ld, b, s);

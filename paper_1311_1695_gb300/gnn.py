@@ -89,8 +89,10 @@ class Net:
     def _S(self, mats, nseg=1):
         import torch
         S = np.concatenate([np.atleast_2d(m) for m in mats], axis=0)
-        S = np.array(np.broadcast_to(S, (nseg,) + S.shape), dtype=np.float64, copy=True)
-        return torch.from_numpy(S).cuda(), S.shape[-1], S.shape[-2] * S.shape[-1]
+        # row-major (C order) whatever the layout of the inputs (a transposed
+        # weight is an F-ordered view): the kernel reads S[i * lds + j]
+        S = np.ascontiguousarray(np.broadcast_to(S, (nseg,) + S.shape), dtype=np.float64)
+        return torch.from_numpy(S).cuda().contiguous(), S.shape[-1], S.shape[-2] * S.shape[-1]
 
     def _update(self, Y, ldy, q, beta, A, lda, p, ones, S, lds, ss):
         _check(lib().lap_block_update(self.G.h, LAP_F32, ctypes.c_void_p(Y), ldy, q, beta, 1.0,

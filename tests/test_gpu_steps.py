@@ -178,13 +178,17 @@ def test_cgs2_drops_dependent_columns(pkg):
 @pytest.mark.parametrize("m", [1, 2, 7, 24, 44, 64])
 def test_syev(pkg, m):
     rng = np.random.default_rng(m)
-    H = rng.standard_normal((3, m, m))
+    H = rng.standard_normal((4, m, m))
     H = H + H.transpose(0, 2, 1)
     H[1] = np.diag(np.arange(m, dtype=float)) + 1e-3 * H[1]  # nearly diagonal
     H[2] = np.kron(np.eye((m + 1) // 2), np.ones((2, 2)))[:m, :m]  # repeated eigenvalues
+    # graded spectrum over six decades (the spread of a Laplacian's Ritz values)
+    Q = np.linalg.qr(rng.standard_normal((m, m)))[0]
+    H[3] = (Q * np.logspace(-6, 0, m)[None, :]) @ Q.T
+    H[3] = 0.5 * (H[3] + H[3].T)
     ev, Y = pkg.lap_syev_batched(torch.from_numpy(H).cuda())
     ev, Y = ev.cpu().numpy(), Y.cpu().numpy()
-    for i in range(3):
+    for i in range(4):
         ref = np.linalg.eigvalsh(H[i])
         assert np.abs(ev[i] - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max()) * m
         assert np.abs(Y[i].T @ Y[i] - np.eye(m)).max() <= 1e-13 * m
@@ -261,4 +265,36 @@ def test_block_update(pkg, p, q, ld_in, beta, ones):
     A64 = A[:, :p].astype(np.float64)
     ref = beta * Y0 + (np.hstack([np.ones((g.n, 1)), A64]) if ones else A64) @ S
     assert np.abs(Yd.cpu().double().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+def test_pcg_correction_batched_with_hubs(pkg, dt):
+    """The fused correction solve on a batch handle: per-graph scalars and
+    hub rows (chunked; several graphs' hubs) against the oracle graph by graph."""
+    # (no star graph here: its eigenvalue 1 of multiplicity n - 2 makes the
+    # shifted system at theta ~ 1 singular and both solves diverge)
+    gs = [G.chung_lu(4000, 2.1, 6.0, 21, cap=900.0), G.grid_graph(25, 30), G.ba_graph(1500, 4, 23),
+          G.with_random_weights(G.chung_lu(2500, 2.3, 5.0, 22), 5)]
+    Gd = pkg.Graph(gs)
+    assert Gd.info()["nlong"] > 0
+    b, iters = 5, 7
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    Xs, Rs, ths = [], [], []
+    for i, g in enumerate(gs):
+        lap = Laplacian(g)
+        X = np.linalg.qr(blockops.project(G.random_block(g.n, b, 30 + i), None))[0]
+        theta, Yr = np.linalg.eigh(X.T @ lap.matvec(X))
+        X = X @ Yr
+        R = lap.matvec(X) - X * theta[None, :]
+        Xs.append(X.astype(npdt)); Rs.append(R.astype(npdt)); ths.append(theta)
+    Td = Gd.pcg_correction(_dev(np.vstack(Xs), dt), torch.from_numpy(np.vstack(ths)).cuda(),
+                           _dev(np.vstack(Rs), dt), iters)
+    T = Td.cpu().double().numpy()
+    off = 0
+    for g, X, R, th in zip(gs, Xs, Rs, ths):
+        ref = blockops.pcg_correction(g, th, R.astype(np.float64), X.astype(np.float64), iters)
+        err = (np.abs(T[off:off + g.n] - ref).max(axis=0) / np.abs(ref).max(axis=0)).max()
+        assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
+        off += g.n
     Gd.close()
