@@ -330,72 +330,97 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
   if (c < q && keep) keep[(size_t)seg * 64 + c] = kp[c];
 }
 
-// Parallel cyclic Jacobi in FP32 on A (mm x LD, symmetric, mm even),
-// accumulating V <- V J.  Round-robin ordering: each of the mm - 1 steps of a
-// sweep rotates mm/2 disjoint pairs; thread i < mm/2 finds pair i's rotation,
-// then the two-sided update J^T A J is applied in independent 2x2 blocks
-// (pair i's rows x pair i2's columns, i <= i2, mirrored below the diagonal):
-// two barriers per step.  A rotated pair's own 2x2 block is set to its exact
+// Rotation of one Jacobi pair: c, s with t = s / c the smaller root of
+// t^2 + 2 tau t - 1 = 0, tau = (a_qq - a_pp) / (2 a_pq), and the exact new
+// diagonal (Rutishauser): a_pp - t a_pq, a_qq + t a_pq.
+__device__ __forceinline__ void jacobi_rot(float app, float aqq, float apq, float& c, float& sn, float& dp,
+                                           float& dq) {
+  const float tau = __fdividef(aqq - app, 2.f * apq);
+  const float h = 1.f + tau * tau;
+  float r = rsqrtf(h);
+  r = r * (1.5f - 0.5f * h * r * r);  // one Newton step
+  const float t = copysignf(1.f, tau) / (fabsf(tau) + h * r);
+  const float u = 1.f + t * t;
+  float ci = rsqrtf(u);
+  ci = ci * (1.5f - 0.5f * u * ci * ci);
+  c = ci;
+  sn = t * ci;
+  dp = app - t * apq;
+  dq = aqq + t * apq;
+}
+__device__ __forceinline__ void jacobi_rot(double app, double aqq, double apq, double& c, double& sn, double& dp,
+                                           double& dq) {
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  sn = t * c;
+  dp = app - t * apq;
+  dq = aqq + t * apq;
+}
+
+// Parallel cyclic Jacobi on A (mm x LD, symmetric, mm even), accumulating
+// V <- V J.  Round-robin ordering (pair table `pairs`, (mm - 1) steps of
+// mm/2 disjoint pairs): thread i < mm/2 finds pair i's rotation, then the
+// two-sided update J^T A J is applied in independent 2x2 blocks (pair i's
+// rows x pair i2's columns, i <= i2, mirrored below the diagonal): two
+// barriers per step.  A rotated pair's own 2x2 block is set to its exact
 // values (a_pq = 0, a_pp - t a_pq, a_qq + t a_pq: Rutishauser's form), so
 // a_pq is not left as rounding noise of order eps |a_pp|.  A rotation is
 // skipped when |a_pq| <= rel sqrt|a_pp a_qq| or <= abs_tol; the sweeps stop
 // once every off-diagonal entry passes that test (checked after each sweep).
-// cs: 4 floats per pair (c, s, a_pp', a_qq'); pq: 2 ints per pair; blk: the
-// (i, i2) block list.  Returns the number of sweeps.
-__device__ int jacobi32(float* A, float* V, int LD, int mm, float rel, float abs_tol, int max_sweeps, float* cs,
-                        int* pq, const short2* blk, int nblk) {
+// cs: 4 values per pair (c, s, a_pp', a_qq').  Returns the number of sweeps.
+template <typename T>
+__device__ int jacobi2s(T* A, T* V, int LD, int mm, T rel, T abs_tol, int max_sweeps, T* cs, const short2* pairs,
+                        const short2* blk, int nblk) {
   const int half = mm / 2;
   const int tid = threadIdx.x, NT = blockDim.x;
+  // V update assignment: thread -> (pair vi, rows vr0, vr0 + vstep, ...)
+  const int vstep = NT / half;
+  const int vi = tid % half, vr0 = tid / half;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int step = 0; step < mm - 1; ++step) {
       if (tid < half) {
-        auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
-        int p = at(tid), q = at(mm - 1 - tid);
-        if (p > q) { const int t = p; p = q; q = t; }
-        const float apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
-        float c = 1.f, sn = 0.f, dp = app, dq = aqq;
-        if (fabsf(apq) > abs_tol && fabsf(apq) > rel * sqrtf(fabsf(app * aqq))) {
-          const float tau = (aqq - app) / (2.f * apq);
-          const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-          c = 1.f / sqrtf(1.f + t * t);
-          sn = t * c;
-          dp = app - t * apq;
-          dq = aqq + t * apq;
-        }
+        const short2 pq = pairs[step * half + tid];
+        const int p = pq.x, q = pq.y;
+        const T apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
+        T c = T(1), sn = T(0), dp = app, dq = aqq;
+        if (fabs(apq) > abs_tol && fabs(apq) > rel * sqrt(fabs(app * aqq))) jacobi_rot(app, aqq, apq, c, sn, dp, dq);
         cs[4 * tid] = c; cs[4 * tid + 1] = sn; cs[4 * tid + 2] = dp; cs[4 * tid + 3] = dq;
-        pq[2 * tid] = p; pq[2 * tid + 1] = q;
       }
       __syncthreads();
+      const short2* pr = pairs + step * half;
       for (int u = tid; u < nblk; u += NT) {
         const short2 ii = blk[u];
         const int i = ii.x, i2 = ii.y;
-        const float s1 = cs[4 * i + 1], s2 = cs[4 * i2 + 1];
-        if (s1 == 0.f && s2 == 0.f) continue;
-        const int p = pq[2 * i], q = pq[2 * i + 1];
+        const T s1 = cs[4 * i + 1], s2 = cs[4 * i2 + 1];
+        if (s1 == T(0) && s2 == T(0)) continue;
+        const int p = pr[i].x, q = pr[i].y;
         if (i == i2) {
           A[p * LD + p] = cs[4 * i + 2];
           A[q * LD + q] = cs[4 * i + 3];
-          A[p * LD + q] = 0.f;
-          A[q * LD + p] = 0.f;
+          A[p * LD + q] = T(0);
+          A[q * LD + p] = T(0);
           continue;
         }
-        const int p2 = pq[2 * i2], q2 = pq[2 * i2 + 1];
-        const float c1 = cs[4 * i], c2 = cs[4 * i2];
-        const float a = A[p * LD + p2], b = A[p * LD + q2], c = A[q * LD + p2], d = A[q * LD + q2];
-        const float ra = c1 * a - s1 * c, rb = c1 * b - s1 * d, rc = s1 * a + c1 * c, rd = s1 * b + c1 * d;
-        const float na = c2 * ra - s2 * rb, nb = s2 * ra + c2 * rb, nc = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
+        const int p2 = pr[i2].x, q2 = pr[i2].y;
+        const T c1 = cs[4 * i], c2 = cs[4 * i2];
+        const T a = A[p * LD + p2], b = A[p * LD + q2], c = A[q * LD + p2], d = A[q * LD + q2];
+        const T ra = c1 * a - s1 * c, rb = c1 * b - s1 * d, rc = s1 * a + c1 * c, rd = s1 * b + c1 * d;
+        const T na = c2 * ra - s2 * rb, nb = s2 * ra + c2 * rb, nc = c2 * rc - s2 * rd, nd = s2 * rc + c2 * rd;
         A[p * LD + p2] = na; A[p * LD + q2] = nb; A[q * LD + p2] = nc; A[q * LD + q2] = nd;
         A[p2 * LD + p] = na; A[q2 * LD + p] = nb; A[p2 * LD + q] = nc; A[q2 * LD + q] = nd;
       }
-      for (int e = tid; e < mm * half; e += NT) {
-        const int r = e / half, i = e - r * half;
-        const float sn = cs[4 * i + 1];
-        if (sn == 0.f) continue;
-        const float c = cs[4 * i];
-        const int p = pq[2 * i], q = pq[2 * i + 1];
-        const float vp = V[r * LD + p], vq = V[r * LD + q];
-        V[r * LD + p] = c * vp - sn * vq;
-        V[r * LD + q] = sn * vp + c * vq;
+      if (tid < vstep * half) {
+        const T sn = cs[4 * vi + 1];
+        if (sn != T(0)) {
+          const T c = cs[4 * vi];
+          const int p = pr[vi].x, q = pr[vi].y;
+          for (int r = vr0; r < mm; r += vstep) {
+            const T vp = V[r * LD + p], vq = V[r * LD + q];
+            V[r * LD + p] = c * vp - sn * vq;
+            V[r * LD + q] = sn * vp + c * vq;
+          }
+        }
       }
       __syncthreads();
     }
@@ -403,8 +428,8 @@ __device__ int jacobi32(float* A, float* V, int LD, int mm, float rel, float abs
     for (int e = tid; e < mm * mm; e += NT) {
       const int i = e / mm, j = e - i * mm;
       if (i < j) {
-        const float a = fabsf(A[i * LD + j]);
-        if (a > abs_tol && a > rel * sqrtf(fabsf(A[i * LD + i] * A[j * LD + j]))) big = 1;
+        const T a = fabs(A[i * LD + j]);
+        if (a > abs_tol && a > rel * sqrt(fabs(A[i * LD + i] * A[j * LD + j]))) big = 1;
       }
     }
     if (!__syncthreads_or(big)) return sweep + 1;
@@ -412,56 +437,71 @@ __device__ int jacobi32(float* A, float* V, int LD, int mm, float rel, float abs
   return max_sweeps;
 }
 
+// Y = op(A) B for small shared-memory matrices in FP64, one output per
+// thread iteration: out[i * ldo + j] = sum_l a(i, l) b(l, j), i < ni, j < nj.
+// ta: a(i, l) = A[l * lda + i] (A^T) when set, else A[i * lda + l].
+__device__ __forceinline__ void small_gemm(int ni, int nj, int nl, const double* A, int lda, bool ta, const double* B,
+                                           int ldb, double* out, int ldo, double beta_diag, double sgn) {
+  for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+    const int i = e / nj, j = e - i * nj;
+    double t = 0.0;
+    if (ta) { for (int l = 0; l < nl; ++l) t = fma(A[l * lda + i], B[l * ldb + j], t); }
+    else { for (int l = 0; l < nl; ++l) t = fma(A[i * lda + l], B[l * ldb + j], t); }
+    out[i * ldo + j] = (i == j ? beta_diag : 0.0) + sgn * t;
+  }
+}
+
 // Symmetric eigensolver for m <= 64, FP64 result, one CTA per matrix.
-// GB300 issues FP32 about 58x faster than FP64, so the O(m^3 sweeps) work is
-// FP32 and the FP64 work is four matrix products per refinement step:
-//  1. FP32 Jacobi (jacobi32) on fl32(H): eigenvectors X to about 1e-7.
-//  2. Sort ascending (padding index of odd m dropped).
-//  3. `iters` refinement steps (Ogita and Aishima, "Iterative refinement for
-//     symmetric eigenvalue decomposition", 2018) in FP64 on the first nref
-//     columns X_r:  R = I - X^T X_r,  S = X^T H X_r,  lambda_j = s_jj / (1 - r_jj),
-//     delta = 2 (||S - diag(lambda)||_F + ||H||_F ||R||_F),
-//     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
-//     |lambda_j - lambda_i| > delta, else r_ij / 2 (i != j);  E_jj = r_jj / 2;
-//     X_r <- X_r + X E.  A step squares the error of well separated pairs;
-//     a cluster closer than delta keeps an orthonormal basis of its invariant
-//     subspace without resolving it (its couplings are at the FP32 level of
-//     its own eigenvalues).  Columns >= nref keep the FP32 result.
+// GB300 issues FP32 about 58x faster than FP64, so the sweeps run in FP32 on
+// fl32(H) (jacobi2s: eigenvectors to about 1e-7), and FP64 finishes:
+//  * exact mode (nref < 0: every column to FP64 accuracy): the FP32
+//    eigenvectors are orthonormalised in FP64 (modified Gram-Schmidt),
+//    B = X^T H X is formed, and FP64 Jacobi sweeps on B (accumulated into X)
+//    finish the decomposition.
+//  * fast mode (nref >= 0: the first nref columns, ascending order): one
+//    refinement step in the form of Ogita and Aishima ("Iterative refinement
+//    for symmetric eigenvalue decomposition", 2018):  R = I - X^T X_r,
+//    S = X^T H X_r,  lambda_j = s_jj / (1 - r_jj),
+//    E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when that is below
+//    1e-3 (first order is then accurate to 1e-6 of the FP32 error), else
+//    r_ij / 2 (the pair is treated as a cluster: its invariant subspace is
+//    kept, not resolved);  E_jj = r_jj / 2;  X_r <- X_r + X E,  followed by
+//    Newton-Schulz steps X_r <- X_r (3 I - X_r^T X_r) / 2 until X_r is
+//    orthonormal to FP64 rounding.  The work is four m x m x nref FP64
+//    products instead of FP64 sweeps over all m^2 entries.
 __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
                                                double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
-                                               const int* __restrict__ seg_skip, int* sweeps_out, int nref,
-                                               int iters) {
+                                               const int* __restrict__ seg_skip, int* sweeps_out, int nref) {
   const int seg = blockIdx.x;
   if (seg_skip && seg_skip[seg]) return;
   const int tid = threadIdx.x, NT = blockDim.x;
   extern __shared__ double sm[];
   const int mm = (m + 1) & ~1;  // even; the padding index is uncoupled
-  const int LD = mm + 1, LM = m + 1;
-  const int nr = nref;
+  const int LD = mm + 1, LM = mm + 1;
+  const bool exact = nref < 0;
+  const int nr = exact ? m : nref;
   const int LR = nr + 1;
-  double* Hs = sm;              // m x LM
-  double* X = Hs + m * LM;      // m x LM (sorted eigenvectors)
-  double* lam = X + m * LM;     // [m]
-  double* W = lam + m;          // union: FP32 Jacobi arrays, or Z, S, R, Xn
+  double* Hs = sm;              // mm x LM
+  double* X = Hs + mm * LM;     // mm x LM
+  double* lam = X + mm * LM;    // [mm]
+  double* W = lam + mm;         // scratch union
   float* A32 = reinterpret_cast<float*>(W);
   float* V32 = A32 + mm * LD;
-  double* Z = W;
-  double* S = Z + m * LR;
-  double* R = S + m * LR;
-  double* Xn = R + m * LR;
-  __shared__ float s_cs[4 * 32];
-  __shared__ int s_pq[2 * 32];
+  __shared__ float s_cs32[4 * 32];
+  __shared__ double s_cs64[4 * 32];
+  __shared__ short2 s_pairs[63 * 32];
   __shared__ short2 s_blk[32 * 33 / 2];
   __shared__ int s_rank[64];
-  __shared__ double s_red[3][8];
+  __shared__ double s_red[2][8];
+  __shared__ int s_flag;
   const double* H = Hg + (size_t)seg * sh;
 
-  // load H (symmetrised) and fl32(H); ||H||_F
+  // load H (symmetrised, padded) and fl32(H); ||H||_F; pair and block tables
   double fro = 0.0;
   for (int e = tid; e < mm * mm; e += NT) {
     const int i = e / mm, j = e - i * mm;
     const double a = (i < m && j < m) ? 0.5 * (H[(size_t)i * ldh + j] + H[(size_t)j * ldh + i]) : 0.0;
-    if (i < m && j < m) Hs[i * LM + j] = a;
+    Hs[i * LM + j] = a;
     A32[i * LD + j] = (float)a;
     V32[i * LD + j] = (i == j) ? 1.f : 0.f;
     fro += a * a;
@@ -472,45 +512,110 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
     const int i = u / half, i2 = u - i * half;
     if (i2 >= i) s_blk[i * half - i * (i - 1) / 2 + (i2 - i)] = make_short2((short)i, (short)i2);
   }
+  for (int u = tid; u < (mm - 1) * half; u += NT) {
+    const int step = u / half, i = u - step * half;
+    auto at = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (mm - 1); };
+    int p = at(i), q = at(mm - 1 - i);
+    if (p > q) { const int t = p; p = q; q = t; }
+    s_pairs[u] = make_short2((short)p, (short)q);
+  }
   fro = warp_sum(fro);
   if ((tid & 31) == 0) s_red[0][tid >> 5] = fro;
   __syncthreads();
   double nH = 0.0;
   for (int w = 0; w < (NT >> 5); ++w) nH += s_red[0][w];
   nH = sqrt(nH);
+  __syncthreads();
   // 1. FP32 Jacobi
-  const int sw = jacobi32(A32, V32, LD, mm, 1e-7f, (float)(1e-30 + 1e-12 * nH), 40, s_cs, s_pq, s_blk, nblk);
-  // 2. sort ascending (rank by counting; ties by index)
+  int sw = jacobi2s<float>(A32, V32, LD, mm, 1e-7f, (float)(1e-30 + 1e-12 * nH), 40, s_cs32, s_pairs, s_blk, nblk);
+  if (exact) {
+    // 2e. X = V32 in FP64, orthonormalised by modified Gram-Schmidt
+    for (int e = tid; e < mm * mm; e += NT) X[(e / mm) * LM + (e % mm)] = (double)V32[(e / mm) * LD + (e % mm)];
+    __syncthreads();
+    for (int j = 0; j < mm; ++j) {
+      if (tid < 32) {
+        double nrm = 0.0;
+        for (int r = tid; r < mm; r += 32) nrm += X[r * LM + j] * X[r * LM + j];
+        nrm = warp_sum(nrm);
+        const double inv = 1.0 / sqrt(nrm);
+        for (int r = tid; r < mm; r += 32) X[r * LM + j] *= inv;
+      }
+      __syncthreads();
+      for (int l = j + 1 + tid; l < mm; l += NT) {
+        double d = 0.0;
+        for (int r = 0; r < mm; ++r) d = fma(X[r * LM + j], X[r * LM + l], d);
+        for (int r = 0; r < mm; ++r) X[r * LM + l] -= d * X[r * LM + j];
+      }
+      __syncthreads();
+    }
+    // B = X^T H X in FP64 (A64 over the FP32 arrays, Wd after it)
+    double* B = W;
+    double* Wd = W + mm * LM;
+    small_gemm(mm, mm, mm, Hs, LM, false, X, LM, Wd, LM, 0.0, 1.0);
+    __syncthreads();
+    small_gemm(mm, mm, mm, X, LM, true, Wd, LM, B, LM, 0.0, 1.0);
+    __syncthreads();
+    for (int e = tid; e < mm * mm; e += NT) {  // symmetrise
+      const int i = e / mm, j = e - i * mm;
+      if (i < j) { const double v = 0.5 * (B[i * LM + j] + B[j * LM + i]); B[i * LM + j] = v; B[j * LM + i] = v; }
+    }
+    __syncthreads();
+    sw += 100 * jacobi2s<double>(B, X, LM, mm, 1e-15, 1e-17 * nH, 30, s_cs64, s_pairs, s_blk, nblk);
+    for (int i = tid; i < mm; i += NT) lam[i] = B[i * LM + i];
+  } else {
+    for (int i = tid; i < mm; i += NT) lam[i] = (double)A32[i * LD + i];
+  }
+  __syncthreads();
+  // sort ascending (rank by counting; ties by index); padding column dropped
   for (int i = tid; i < mm; i += NT) {
     int rank = -1;
-    if (!(mm != m && fabsf(V32[(mm - 1) * LD + i]) > 0.5f)) {
-      const float di = A32[i * LD + i];
+    const float pv = exact ? (float)X[(mm - 1) * LM + i] : V32[(mm - 1) * LD + i];
+    auto is_pad = [&](int c) {
+      return mm != m && fabs(exact ? X[(mm - 1) * LM + c] : (double)V32[(mm - 1) * LD + c]) > 0.5;
+    };
+    if (!(mm != m && fabsf(pv) > 0.5f)) {
+      const double di = lam[i];
       rank = 0;
       for (int j = 0; j < mm; ++j) {
-        if (mm != m && fabsf(V32[(mm - 1) * LD + j]) > 0.5f) continue;
-        const float dj = A32[j * LD + j];
+        if (is_pad(j)) continue;
+        const double dj = lam[j];
         rank += (dj < di) || (dj == di && j < i);
       }
     }
     s_rank[i] = rank;
   }
   __syncthreads();
+  double* ev = evals + (size_t)seg * se;
+  double* Y = Yg + (size_t)seg * sy;
+  if (exact) {
+    for (int e = tid; e < mm * m; e += NT) {
+      const int r = e / mm, i = e - r * mm;
+      const int k = s_rank[i];
+      if (k >= 0) Y[(size_t)r * ldy + k] = X[r * LM + i];
+    }
+    for (int i = tid; i < mm; i += NT)
+      if (s_rank[i] >= 0) ev[s_rank[i]] = lam[i];
+    if (sweeps_out && tid == 0) sweeps_out[seg] = sw;
+    return;
+  }
+  // fast mode: sorted FP32 eigenvectors in FP64, columns [0, m)
+  double* lam_s = W + 2 * mm * LD / 2 + 8;  // after the FP32 arrays (as doubles)
   for (int e = tid; e < mm * m; e += NT) {
-    const int r = e / mm, i = e - r * mm;  // row r < m, source column i
+    const int r = e / mm, i = e - r * mm;
     const int k = s_rank[i];
-    if (k >= 0) X[r * LM + k] = (double)V32[r * LD + i];
+    if (k >= 0 && r < m) X[r * LM + k] = (double)V32[r * LD + i];
   }
   for (int i = tid; i < mm; i += NT)
-    if (s_rank[i] >= 0) lam[s_rank[i]] = (double)A32[i * LD + i];
+    if (s_rank[i] >= 0) lam_s[s_rank[i]] = lam[i];
   __syncthreads();
-  // 3. refinement of the first nr columns
-  for (int it = 0; it < iters && nr > 0; ++it) {
-    for (int e = tid; e < m * nr; e += NT) {  // Z = H X_r
-      const int r = e / nr, j = e - r * nr;
-      double t = 0.0;
-      for (int l = 0; l < m; ++l) t = fma(Hs[r * LM + l], X[l * LM + j], t);
-      Z[r * LR + j] = t;
-    }
+  for (int j = tid; j < m; j += NT) lam[j] = lam_s[j];
+  __syncthreads();
+  if (nr > 0) {
+    double* Z = W;               // m x LR (overwrites the FP32 arrays)
+    double* S = Z + m * LR;
+    double* R = S + m * LR;
+    double* Xn = R + m * LR;
+    small_gemm(m, nr, m, Hs, LM, false, X, LM, Z, LR, 0.0, 1.0);  // Z = H X_r
     __syncthreads();
     for (int e = tid; e < m * nr; e += NT) {  // S = X^T Z, R = I - X^T X_r
       const int i = e / nr, j = e - i * nr;
@@ -526,29 +631,14 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
     __syncthreads();
     for (int j = tid; j < nr; j += NT) lam[j] = S[j * LR + j] / (1.0 - R[j * LR + j]);
     __syncthreads();
-    double offs = 0.0, nrr = 0.0;
-    for (int e = tid; e < m * nr; e += NT) {
-      const int i = e / nr, j = e - i * nr;
-      const double d = S[i * LR + j] - (i == j ? lam[j] : 0.0);
-      offs += d * d;
-      nrr += R[i * LR + j] * R[i * LR + j];
-    }
-    offs = warp_sum(offs);
-    nrr = warp_sum(nrr);
-    if ((tid & 31) == 0) { s_red[1][tid >> 5] = offs; s_red[2][tid >> 5] = nrr; }
-    __syncthreads();
-    double so = 0.0, sr = 0.0;
-    for (int w = 0; w < (NT >> 5); ++w) { so += s_red[1][w]; sr += s_red[2][w]; }
-    const double delta = 2.0 * (sqrt(so) + nH * sqrt(sr));
     for (int e = tid; e < m * nr; e += NT) {  // E in place of S
       const int i = e / nr, j = e - i * nr;
-      double ev;
-      if (i == j) ev = 0.5 * R[i * LR + j];
-      else {
-        const double gap = lam[j] - lam[i];
-        ev = fabs(gap) > delta ? (S[i * LR + j] + lam[j] * R[i * LR + j]) / gap : 0.5 * R[i * LR + j];
+      double ev_ = 0.5 * R[i * LR + j];
+      if (i != j) {
+        const double num = S[i * LR + j] + lam[j] * R[i * LR + j], gap = lam[j] - lam[i];
+        if (fabs(num) <= 1e-3 * fabs(gap)) ev_ = num / gap;
       }
-      S[i * LR + j] = ev;
+      S[i * LR + j] = ev_;
     }
     __syncthreads();
     for (int e = tid; e < m * nr; e += NT) {  // Xn = X_r + X E
@@ -558,14 +648,33 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
       Xn[r * LR + j] = t;
     }
     __syncthreads();
-    for (int e = tid; e < m * nr; e += NT) {
-      const int r = e / nr, j = e - r * nr;
-      X[r * LM + j] = Xn[r * LR + j];
+    // Newton-Schulz: G = Xn^T Xn (in Z), Xn <- Xn (3 I - G) / 2
+    for (int ns = 0; ns < 3; ++ns) {
+      if (tid == 0) s_flag = 0;
+      __syncthreads();
+      for (int e = tid; e < nr * nr; e += NT) {
+        const int i = e / nr, j = e - i * nr;
+        double t = 0.0;
+        for (int r = 0; r < m; ++r) t = fma(Xn[r * LR + i], Xn[r * LR + j], t);
+        const double gm = 1.5 * (i == j ? 1.0 : 0.0) - 0.5 * t;
+        Z[i * LR + j] = gm;
+        if (fabs(t - (i == j ? 1.0 : 0.0)) > 4e-16) s_flag = 1;
+      }
+      __syncthreads();
+      if (!s_flag) break;
+      for (int e = tid; e < m * nr; e += NT) {  // into R (free), then back
+        const int r = e / nr, j = e - r * nr;
+        double t = 0.0;
+        for (int i = 0; i < nr; ++i) t = fma(Xn[r * LR + i], Z[i * LR + j], t);
+        R[r * LR + j] = t;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * nr; e += NT) Xn[(e / nr) * LR + (e % nr)] = R[(e / nr) * LR + (e % nr)];
+      __syncthreads();
     }
+    for (int e = tid; e < m * nr; e += NT) X[(e / nr) * LM + (e % nr)] = Xn[(e / nr) * LR + (e % nr)];
     __syncthreads();
   }
-  double* ev = evals + (size_t)seg * se;
-  double* Y = Yg + (size_t)seg * sy;
   for (int j = tid; j < m; j += NT) ev[j] = lam[j];
   for (int e = tid; e < m * m; e += NT) {
     const int r = e / m, j = e - r * m;
@@ -886,19 +995,26 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 }
 
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,
-          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref, int iters) {
+          int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref) {
   LAP_PROF("syev", 0.0, s);
-  const int mm = (m + 1) & ~1;
-  const int nr = (nref < 0 || nref > m) ? m : nref;
-  const size_t jac = sizeof(float) * 2 * (size_t)mm * (mm + 1);
-  const size_t ref = sizeof(double) * 4 * (size_t)m * (nr + 1);
-  const size_t smem = sizeof(double) * (2 * (size_t)m * (m + 1) + m) + (jac > ref ? jac : ref);
+  const size_t mm = (size_t)((m + 1) & ~1);
+  const size_t nr = nref < 0 ? (size_t)m : (size_t)(nref > m ? m : nref);
+  // Hs, X, lam; scratch: FP32 arrays + sorted values, or (exact) B and H X,
+  // or (fast) Z, S, R, Xn
+  const size_t jac = sizeof(float) * 2 * mm * (mm + 1) + sizeof(double) * (mm + 16);
+  const size_t ex = sizeof(double) * 2 * mm * (mm + 1);
+  const size_t fa = sizeof(double) * 4 * (size_t)m * (nr + 1);
+  size_t scratch = jac;
+  if (nref < 0 && ex > scratch) scratch = ex;
+  if (nref >= 0 && fa > scratch) scratch = fa;
+  const size_t smem = sizeof(double) * (2 * mm * (mm + 1) + mm) + scratch;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out, nr, iters);
+  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out,
+                                 nref < 0 ? -1 : (int)nr);
 }
 
 template <typename T>

@@ -65,11 +65,12 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 // Symmetric eigensolver (parallel cyclic Jacobi), m <= 64, one CTA per
 // segment.  H (m x m, ld ldh, segment stride sh) is not modified.  evals
 // ascending; Y columns are the matching unit eigenvectors.
-// FP32 Jacobi, then `iters` FP64 refinement steps on the first nref
-// columns (nref < 0: all); columns >= nref are FP32-accurate.
+// FP32 Jacobi, then FP64: nref < 0 (exact mode) every column to FP64
+// accuracy (Gram-Schmidt, B = X^T H X, FP64 Jacobi); nref >= 0 (fast mode)
+// one refinement step plus orthonormalisation of the first nref columns
+// only, the others FP32-accurate.
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se,
-          double* Y, int ldy, int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref = -1,
-          int iters = 2);
+          double* Y, int ldy, int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref = -1);
 
 // ---- Projected preconditioned CG on (I - QQ^T)(L - theta_c I)(I - QQ^T) t_c = -r_c,
 // Q = [e/sqrt(n_s), X] per segment, preconditioner (I-QQ^T) D^{-1} (I-QQ^T).

@@ -195,7 +195,7 @@ struct JD {
     // from the FP32 Jacobi result); H restarts as diag(theta[0:mk])
     const int mk = std::min(m, z.mk);
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
-         seg_skip, sweeps, st, mk, 1);
+         seg_skip, sweeps, st, mk);
     update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     update<TV>(g, W, z.ldv, mk, 0.0, 1.0, W, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
