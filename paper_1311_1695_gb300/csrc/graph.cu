@@ -317,6 +317,15 @@ int PcgWork::steps_done(cudaStream_t s) const {
   return v;
 }
 
+void PcgWork::status(cudaStream_t s, int* err, int* steps) const {
+  int v[2] = {0, 0};
+  cudaMemcpyAsync(v, bar + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (v[0]) cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
+  if (err) *err = v[0];
+  if (steps) *steps = v[1];
+}
+
 int PcgWork::error_flag(cudaStream_t s) const {
   int e = 0;
   cudaMemcpyAsync(&e, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -31,6 +31,9 @@ struct PcgWork {
                 int itmax, const int* hub_seg) const;
   int error_flag(cudaStream_t s) const;  // reads and clears the barrier error flag
   int steps_done(cudaStream_t s) const;  // PCG steps of the last launch
+  // error flag and steps of the last launch in one read (synchronises s);
+  // a set error flag is cleared
+  void status(cudaStream_t s, int* err, int* steps) const;
 };
 
 }  // namespace lapeig

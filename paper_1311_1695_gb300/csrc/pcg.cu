@@ -481,10 +481,16 @@ int launch_team(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ct
 
 }  // namespace
 
+// Algorithmic bytes of a solve of `iters` steps: per step the CSR once and
+// about 17 passes over n x b blocks (P gathered, AP, T, RES, Z, X twice...),
+// plus 9 passes for the set-up.
+double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
+  return (double)elem * g.n * b * (iters * 17.0 + 9.0) + (4.0 * g.n + 4.0 * g.nnz) * iters;
+}
+
 template <typename T>
 int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
-  LAP_PROF("pcg_fused", (double)sizeof(T) * g.n * f.b * (f.itmax * 17.0 + 9.0) +
-                            (4.0 * g.n + 4.0 * g.nnz) * f.itmax, s);
+  LAP_PROF("pcg_fused", pcg_bytes(g, f.b, f.itmax, (int)sizeof(T)), s);
   if (f.b <= 8) return launch_team<T, 8>(g, f, s, max_ctas);
   if (f.b <= 16) return launch_team<T, 16>(g, f, s, max_ctas);
   return launch_team<T, 32>(g, f, s, max_ctas);

@@ -42,5 +42,7 @@ struct FusedPcg {
 // Launch the whole correction solve; returns 0 or -1 (launch failure).
 template <typename T>
 int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas);
+// Algorithmic bytes of a solve of `iters` steps with elem-byte values.
+double pcg_bytes(const DevGraph& g, int b, int iters, int elem);
 
 }  // namespace lapeig

@@ -87,6 +87,14 @@ int prof_begin(const char* name, double bytes, cudaStream_t s) {
 
 void prof_end(int slot, cudaStream_t s) { cudaEventRecord(P().pending[slot].b, s); }
 
+void prof_set_last_bytes(const char* name, double bytes) {
+  Profiler& p = P();
+  auto it = p.index.find(name);
+  if (it == p.index.end()) return;
+  for (size_t i = p.pending.size(); i-- > 0;)
+    if (p.pending[i].name == it->second) { p.pending[i].bytes = bytes; return; }
+}
+
 }  // namespace lapeig
 
 extern "C" {

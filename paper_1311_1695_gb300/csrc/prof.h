@@ -11,6 +11,9 @@ namespace lapeig {
 bool prof_on();
 int prof_begin(const char* name, double bytes, cudaStream_t s);  // returns a slot or -1
 void prof_end(int slot, cudaStream_t s);
+// Replace the bytes of the most recent pending launch named `name` (for a
+// kernel whose work is known only after it ran, e.g. a solve that stops early).
+void prof_set_last_bytes(const char* name, double bytes);
 
 struct ProfScope {
   int slot;

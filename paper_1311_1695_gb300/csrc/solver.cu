@@ -28,6 +28,7 @@
 #include <cstring>
 
 #include "internal.h"
+#include "prof.h"
 #include "small.cuh"
 
 namespace lapeig {
@@ -90,6 +91,7 @@ struct JD {
   std::vector<int> active_h, skip_h;
   int64_t n_matvec = 0;
   int inner_its = 0;
+  int last_nact = 0;  // columns corrected by the last correction solve
   PcgWork* pw = nullptr;
 
   JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
@@ -232,18 +234,19 @@ struct JD {
       convert<TV, TP>(g, Rv, z.ldb, Rp, z.ldb, z.b, st);
       X = Xp; ldx = z.ldb; R = Rp; ldr = z.ldb;
     }
-    const FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, z.ldb, z.b, theta, z.mmax, active, seg_skip,
-                                delta, itmax, G->d_long_seg);
+    // single graph: the solve stops once every active column met delta
+    FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, z.ldb, z.b, theta, z.mmax, active, seg_skip,
+                          delta, itmax, G->d_long_seg);
+    f.early_exit = 1;
     if (pcg_fused<TP>(g, f, st, 0) != 0) {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;
     }
-    inner_its += itmax;
     int nact = 0;
     for (int s = 0; s < z.nseg; ++s)
       if (!skip_h[s])
         for (int j = 0; j < z.b; ++j) nact += active_h[(size_t)s * 64 + j] ? 1 : 0;
-    n_matvec += (int64_t)itmax * nact;
+    last_nact = nact;
     // T -> V[:, mk : mk+b]
     convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
     ortho(mk, z.b, drop1);
@@ -343,7 +346,12 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
     m = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
     if (m < 0) return LAP_ECUDA;
-    if (jd.pw->error_flag(jd.st)) { set_error("grid barrier in the correction solve timed out"); return LAP_ETIMEOUT; }
+    int perr = 0, steps = 0;
+    jd.pw->status(jd.st, &perr, &steps);
+    if (perr) { set_error("grid barrier in the correction solve timed out"); return LAP_ETIMEOUT; }
+    jd.inner_its += steps;
+    jd.n_matvec += (int64_t)steps * jd.last_nact;
+    if (prof_on()) prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, steps, (int)sizeof(TP)));
   }
   // make sure skip flags are cleared on the device for whatever comes next
   cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, jd.st);
