@@ -1,20 +1,26 @@
 """The warm-start message-passing network and its subspace loss, in FP64.
 
 The paper has no learned component; this is the definition the GPU's
-training and inference kernels are checked against.  Network (width w = 32):
+training and inference kernels are checked against.  Network (width w = 32,
+s = HOPS aggregation steps per layer):
 
   H_0 = F                                   (n x f node features)
-  Z_l = (M H_l) W_l + H_l U_l + 1 b_l^T     M = D^{-1} A (mean over neighbours)
+  Z_l = (M^s H_l) W_l + H_l U_l + 1 b_l^T   M = D^{-1} A (mean over neighbours)
   H_{l+1} = tanh(Z_l),  l = 0, 1, 2
-  X = H_3 W_out                             (n x k proposed start block)
+  X = C H_3 W_out,   C = I - 1 1^T / n      (n x k proposed start block,
+                                             centred: the wanted eigenvectors
+                                             are orthogonal to 1)
 
 Loss, invariant to the sign and rotation of the target eigenvectors U
-(n x k, orthonormal) and to any invertible recombination of X's columns:
+(n x k, orthonormal) and, for eps = 0, to any invertible recombination of X's
+columns:
 
-  loss(X) = 1 - tr((X^T X)^{-1} X^T U U^T X) / k
+  loss(X) = 1 - tr(G^{-1} X^T U U^T X) / k,   G = X^T X + eps (tr(X^T X) / k) I
 
-which is 0 exactly when span(X) = span(U).  Its gradient is
-  dloss/dX = -(2/k) (U (U^T X) G^{-1} - X G^{-1} (X^T U)(U^T X) G^{-1}),  G = X^T X.
+which is 0 exactly when span(X) = span(U) (eps = 0).  The small ridge eps
+keeps the loss and its gradient finite when X is nearly rank deficient.
+With A = G^{-1} (X^T U U^T X) G^{-1}, its gradient is
+  dloss/dX = -(2/k) (U U^T X G^{-1} - X A - (eps / k) tr(A) X).
 
 Node features: column 0 = 1, column 1 = log(1 + d_i) / log(1 + d_max), the
 rest uniform(-1, 1) from SplitMix64 (counter node * f + column).
@@ -29,6 +35,8 @@ from .rng import splitmix64
 WIDTH = 32
 LAYERS = 3
 NFEAT = 16
+HOPS = 4
+EPS_RIDGE = 1e-6
 
 
 def features(g, seed: int, nfeat: int = NFEAT) -> np.ndarray:
@@ -79,18 +87,22 @@ def forward(g, F, params):
     cache = []
     for l in range(LAYERS):
         W, U, b = params[3 * l: 3 * l + 3]
-        MH = _mean_agg(g, H)
+        MH = H
+        for _ in range(HOPS):
+            MH = _mean_agg(g, MH)
         Z = MH @ W + H @ U + b[None, :]
         Hn = np.tanh(Z)
         cache.append((H, MH, Hn))
         H = Hn
     X = H @ params[-1]
+    X = X - X.mean(axis=0)[None, :]
     return X, cache
 
 
 def backward(g, cache, params, dX):
     grads = [None] * len(params)
     H3 = cache[-1][2]
+    dX = dX - dX.mean(axis=0)[None, :]   # the centring is its own adjoint
     grads[-1] = H3.T @ dX
     dH = dX @ params[-1].T
     for l in reversed(range(LAYERS)):
@@ -100,15 +112,21 @@ def backward(g, cache, params, dX):
         grads[3 * l] = MH.T @ dZ
         grads[3 * l + 1] = H.T @ dZ
         grads[3 * l + 2] = dZ.sum(axis=0)
-        dH = _mean_agg_T(g, dZ @ W.T) + dZ @ U.T
+        T = dZ @ W.T
+        for _ in range(HOPS):
+            T = _mean_agg_T(g, T)
+        dH = T + dZ @ U.T
     return grads
 
 
-def subspace_loss(X, U):
+def subspace_loss(X, U, eps: float = EPS_RIDGE):
     k = U.shape[1]
     Gm = X.T @ X
+    Gm = Gm + eps * (np.trace(Gm) / k) * np.eye(k)
     Gi = np.linalg.inv(Gm)
     UX = U.T @ X
-    loss = 1.0 - np.trace(Gi @ UX.T @ UX) / k
-    dX = -(2.0 / k) * (U @ UX @ Gi - X @ Gi @ UX.T @ UX @ Gi)
+    M = UX.T @ UX
+    loss = 1.0 - np.trace(Gi @ M) / k
+    A = Gi @ M @ Gi
+    dX = -(2.0 / k) * (U @ UX @ Gi - X @ A - (eps / k) * np.trace(A) * X)
     return loss, dX

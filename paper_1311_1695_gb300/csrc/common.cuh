@@ -21,7 +21,7 @@
 
 namespace lapeig {
 
-constexpr int kTileRows = 512;
+constexpr int kTileRows = 256;  // a tile never has more rows
 constexpr int kMaxCols = 64;  // widest block handled by the tall-skinny kernels
 
 struct Tile {
@@ -55,6 +55,9 @@ struct DevGraph {
   // per chunk.  A hub with several chunks combines them through hub_part
   // (per chunk: kMaxCols column sums + the weight sum) and an arrival
   // counter; the last chunk to arrive sums the partials in chunk order.
+  const int* erp;        // [n+1] effective row pointer: prefix of the row
+                         // lengths with hub rows counted as 0 (merge-path
+                         // splits of a tile's ordinary nonzeros)
   const int4* chunks;    // [nchunk] {row, p0, p1, hub index}
   int nchunk;
   const int2* hub_chunks;  // [nlong] {first chunk, number of chunks}

@@ -80,9 +80,14 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     return da != db ? da > db : a < b;
   });
   cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks);
-  cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part);
+  cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part); cudaFree(g->d_erp);
   g->d_long = nullptr; g->d_long_seg = nullptr; g->d_chunks = nullptr; g->d_hub_chunks = nullptr;
-  g->d_hub_cnt = nullptr; g->d_hub_part = nullptr;
+  g->d_hub_cnt = nullptr; g->d_hub_part = nullptr; g->d_erp = nullptr;
+  std::vector<int> erp((size_t)n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const int d = g->rowptr_h[i + 1] - g->rowptr_h[i];
+    erp[i + 1] = erp[i] + (d > g->dg.long_thresh ? 0 : d);
+  }
   std::vector<int> hseg(hubs.size());
   for (size_t h = 0; h < hubs.size(); ++h)
     hseg[h] = (int)(std::upper_bound(g->row0.begin(), g->row0.end(), hubs[h]) - g->row0.begin()) - 1;
@@ -100,6 +105,7 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   rc = rc ? rc : dev_alloc_copy(&g->d_hub_chunks, hub_chunks.data(), hub_chunks.size());
   rc = rc ? rc : dev_alloc_copy<int>(&g->d_hub_cnt, nullptr, hubs.size());
   rc = rc ? rc : dev_alloc_copy<double>(&g->d_hub_part, nullptr, chunks.size() * kPartStride);
+  rc = rc ? rc : dev_alloc_copy(&g->d_erp, erp.data(), erp.size());
   if (rc) return rc;
   if (!hubs.empty() && cudaMemset(g->d_hub_cnt, 0, sizeof(int) * hubs.size()) != cudaSuccess) {
     set_error("cudaMemset failed");
@@ -113,6 +119,7 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   g->dg.hub_chunks = g->d_hub_chunks;
   g->dg.hub_cnt = g->d_hub_cnt;
   g->dg.hub_part = g->d_hub_part;
+  g->dg.erp = g->d_erp;
   return LAP_OK;
 }
 
@@ -170,7 +177,9 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   g->avg_degree = ntot ? (double)nnztot / (double)ntot : 0.0;
   g->max_degree = maxdeg;
 
-  // tiles: small enough that every SM holds several CTAs
+  // tiles: small enough that every SM holds several CTAs; cut at `rows`
+  // rows or at twice the mean work of such a tile (row lengths capped at 64,
+  // the default hub threshold), so tiles carry similar SpMM work
   std::vector<Tile> tiles;
   g->tile_ptr.assign(nb + 1, 0);
   for (int s = 0; s < nb; ++s) {
@@ -178,9 +187,21 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
     const int ns = g->row0[s + 1] - g->row0[s];
     int rows = (ns + 4 * 152 - 1) / (4 * 152);
     rows = (rows + 31) / 32 * 32;
-    rows = std::max(64, std::min(rows, 256));
-    int idx = 0;
-    for (int a = g->row0[s]; a < g->row0[s + 1]; a += rows) tiles.push_back(Tile{s, a, std::min(a + rows, g->row0[s + 1]), idx++});
+    rows = std::max(64, std::min(rows, kTileRows));
+    int64_t work_s = 0;
+    for (int r = g->row0[s]; r < g->row0[s + 1]; ++r) work_s += std::min(g->rowptr_h[r + 1] - g->rowptr_h[r], 64);
+    const int64_t budget = std::max<int64_t>(64, 2 * work_s * rows / std::max(ns, 1));
+    int idx = 0, a = g->row0[s];
+    while (a < g->row0[s + 1]) {
+      int e = a;
+      int64_t w = 0;
+      while (e < g->row0[s + 1] && e - a < rows && (e == a || w < budget)) {
+        w += std::min(g->rowptr_h[e + 1] - g->rowptr_h[e], 64);
+        ++e;
+      }
+      tiles.push_back(Tile{s, a, e, idx++});
+      a = e;
+    }
   }
   g->tile_ptr[nb] = (int)tiles.size();
   g->hg.ntiles = (int)tiles.size();
@@ -243,6 +264,7 @@ void graph_free(lap_graph* g) {
   cudaFree(g->d_deg64); cudaFree(g->d_norm1); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
   cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->red.acc); cudaFree(g->red.counter);
   cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks); cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part);
+  cudaFree(g->d_erp);
   cudaFree(g->scratch); cudaFree(g->small);
   g->pcg.release();
   delete g;

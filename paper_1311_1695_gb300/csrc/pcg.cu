@@ -6,9 +6,7 @@
 // indefinite system is the paper's choice, Section 3.2).
 //
 // Each iteration has three phases separated by grid-wide barriers:
-//   A  q~ = L p - theta p (degree-fused SpMM of the CTA's rows, chunks of
-//      hub rows spread round-robin over all warps), partial G1 = [1|X]^T q~,
-//      p.q~
+//   A  q~ = L p - theta p (the degree-fused SpMM), partial G1 = [1|X]^T q~, p.q~
 //   B  alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
 //      z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r
 //   C  beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
@@ -19,6 +17,21 @@
 // iteration parity and written by the CTA owning the graph's first tile, so
 // no CTA reads a value while another rewrites it.  Accumulators are zeroed
 // by that owner one phase after their last read.
+//
+// Work layout.  A CTA owns whole row tiles (tile k goes to CTA k mod grid) in
+// every phase; within a tile a "row group" of BWL lanes handles a row, lane c
+// column c (lanes as columns, BWL >= b).  The tile's X rows are staged in
+// shared memory, zero-padded to BMAX columns, so the projections
+// y - [1|X] G and the Gram terms [1|X]^T z read x_i as broadcast vector
+// loads with no per-column predicate.  Phase A balances the SpMM inside a
+// tile merge-path style: the tile's nonzeros (hub rows excluded, see below)
+// are cut into equal ranges, one per row group; a group walks its range with
+// U independent gathers in flight and adds each finished (or cut) row into a
+// shared-memory row accumulator; after a CTA barrier the rows' epilogue
+// (q~ = d p - A p - theta p, the Gram terms) runs row by row.  Hub rows
+// (degree > long_thresh) are cut into chunks of kHubChunk nonzeros spread
+// over all warps of the grid and combined by the last chunk to finish
+// (hub.cuh).
 //
 // Data written by another CTA inside the launch (gathered P rows, hub rows,
 // the persistent scalars, the accumulators) is read with L2 loads (__ldcg):
@@ -39,6 +52,8 @@ namespace lapeig {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kU = 8;  // gathers in flight per row group in the merge-path walk
 
 __device__ __forceinline__ int seg_rows(const DevGraph& g, int s) { return g.row0[s + 1] - g.row0[s]; }
 
@@ -78,18 +93,69 @@ struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
   double delta; int itmax; double *acc1, *acc2; int acc_stride; double* rho; int* done; double *res0, *resn;
-  int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int vec; int* iters_out;
+  int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int* iters_out;
 };
 
+template <typename T> struct VecOf {};
+template <> struct VecOf<float> { using type = float4; static constexpr int w = 4; };
+template <> struct VecOf<double> { using type = double2; static constexpr int w = 2; };
+
+// y - G[0] - sum_i x_i G[i+1] with x the tile row in shared memory (zero
+// padded to BMAX; G[i+1] is zero for i >= b too).
+template <typename T, int BMAX>
+__device__ __forceinline__ T project_xs(T y, const T* __restrict__ xr, const T (&Gc)[BMAX + 1]) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  y -= Gc[0];
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    const V v = *reinterpret_cast<const V*>(xr + i);
+    if constexpr (W == 4) {
+      y -= v.x * Gc[i + 1]; y -= v.y * Gc[i + 2]; y -= v.z * Gc[i + 3]; y -= v.w * Gc[i + 4];
+    } else {
+      y -= v.x * Gc[i + 1]; y -= v.y * Gc[i + 2];
+    }
+  }
+  return y;
+}
+
+// acc[0] += z, acc[1 + i] += x_i z
+template <typename T, int BMAX>
+__device__ __forceinline__ void gram_xs(T (&acc)[BMAX + 1], const T* __restrict__ xr, T z) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  acc[0] += z;
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    const V v = *reinterpret_cast<const V*>(xr + i);
+    if constexpr (W == 4) {
+      acc[i + 1] += v.x * z; acc[i + 2] += v.y * z; acc[i + 3] += v.z * z; acc[i + 4] += v.w * z;
+    } else {
+      acc[i + 1] += v.x * z; acc[i + 2] += v.y * z;
+    }
+  }
+}
+
+// The same Gram terms for a row outside the tile (a hub row): x_i broadcast
+// from lane i of the row group.
+template <typename T, int BMAX, int BWL>
+__device__ __forceinline__ void gram_col(T (&acc)[BMAX + 1], T xc, T z, int b) {
+  acc[0] += z;
+#pragma unroll
+  for (int i = 0; i < BMAX; ++i) {
+    const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+    if (i < b) acc[i + 1] += xi * z;
+  }
+}
+
 // Per-thread accumulators of one phase for the current graph: thread (warp,
-// sub-row slot, column c) owns acc[0] = sum z_c, acc[1+i] = sum x_i z_c and
+// row group, column c) owns acc[0] = sum z_c, acc[1+i] = sum x_i z_c and
 // two per-column extras.  At a graph change (and at the end of the phase)
-// they are summed over the row slots of the warp (shuffles), over the warps
+// they are summed over the row groups of the warp (shuffles), over the warps
 // (shared memory), and added to the graph's FP64 accumulators with one
 // atomic per output per CTA.
 template <typename T, int BMAX, int BWL>
-__device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&ex)[2], double* red) {
-  constexpr int NW = kThreads / 32;
+__device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&ex)[2], T* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
   constexpr int NV = BMAX + 3;
@@ -102,9 +168,9 @@ __device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], 
   }
   if (lane < BWL) {
 #pragma unroll
-    for (int i = 0; i <= BMAX; ++i) red[(warp * NV + i) * BWL + c] = (double)acc[i];
-    red[(warp * NV + BMAX + 1) * BWL + c] = (double)ex[0];
-    red[(warp * NV + BMAX + 2) * BWL + c] = (double)ex[1];
+    for (int i = 0; i <= BMAX; ++i) red[(warp * NV + i) * BWL + c] = acc[i];
+    red[(warp * NV + BMAX + 1) * BWL + c] = ex[0];
+    red[(warp * NV + BMAX + 2) * BWL + c] = ex[1];
   }
 #pragma unroll
   for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
@@ -116,45 +182,36 @@ __device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], 
     if (o < nout) { v = o / b; cc = o - v * b; }
     else { v = BMAX + 1 + (o - nout) / b; cc = (o - nout) % b; }
     double t = 0.0;
-    for (int w = 0; w < NW; ++w) t += red[(w * NV + v) * BWL + cc];
+    for (int w = 0; w < kWarps; ++w) t += (double)red[(w * NV + v) * BWL + cc];
     if (t != 0.0) atomicAdd(accs + o, t);
   }
   __syncthreads();
 }
 
-// Projection row update shared by phases B, C and init-C:
-//   y_c - G[0][c] - sum_i x_i G[i+1][c], x_i broadcast from the row's lanes.
-template <typename T, int BMAX, int BWL>
-__device__ __forceinline__ T project_col(T y, T xc, const T (&Gc)[BMAX + 1], int b) {
-  y -= Gc[0];
-#pragma unroll
-  for (int i = 0; i < BMAX; ++i) {
-    const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-    if (i < b) y -= xi * Gc[i + 1];
-  }
-  return y;
-}
-
-template <typename T, int BMAX, int BWL>
-__device__ __forceinline__ void gram_col(T (&acc)[BMAX + 1], T xc, T z, int b) {
-  acc[0] += z;
-#pragma unroll
-  for (int i = 0; i < BMAX; ++i) {
-    const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-    if (i < b) acc[i + 1] += xi * z;
+// Stage rows [r0, r0 + nrows) of X into xs (row stride BMAX, zero padded).
+template <typename T, int BMAX>
+__device__ __forceinline__ void stage_x(T* xs, const T* __restrict__ X, int ldx, int r0, int nrows, int b) {
+  for (int e = threadIdx.x; e < nrows * BMAX; e += kThreads) {
+    const int r = e / BMAX, i = e - r * BMAX;
+    xs[e] = i < b ? X[(size_t)(r0 + r) * ldx + i] : T(0);
   }
 }
 
-template <typename T, int BMAX, int TEAM, int BWL>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
-  extern __shared__ double red[];  // [warps][BMAX+3][BWL]
-  constexpr int RW = 32 / BWL;     // rows per warp pass
-  constexpr int NW = kThreads / 32;
+template <typename T, int BMAX, int BWL>
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);                          // [warps][BMAX+3][BWL]
+  T* xs = red + kWarps * (BMAX + 3) * BWL;                          // [kTileRows][BMAX]
+  T* accA = xs + kTileRows * BMAX;                                  // [kTileRows][BMAX]
+  int* s_rp = reinterpret_cast<int*>(accA + kTileRows * BMAX);      // [kTileRows + 1]
+  int* s_erp = s_rp + kTileRows + 1;                                // [kTileRows + 1]
+  constexpr int RW = 32 / BWL;        // rows per warp pass
+  constexpr int SLOTS = kWarps * RW;  // row groups per CTA
   const int b = f.b;
   const int ld = f.ld;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
-  constexpr int SLOTS = NW * RW;
+  const int grp = warp * RW + lane / BWL;
   const bool colok = c < b;
   const int stride1 = f.acc_stride;
   const int nout = (b + 1) * b;
@@ -172,6 +229,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
 #pragma unroll
     for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)(__ldcg(A + i * b + c) * (i == 0 ? inv_n : 1.0)) : T(0);
   };
+  auto stage = [&](const Tile& t) {
+    __syncthreads();  // the previous tile's readers are done
+    stage_x<T, BMAX>(xs, X, f.ldx, t.r0, t.r1 - t.r0, b);
+    __syncthreads();
+  };
+  for (int e = threadIdx.x; e < kTileRows * BMAX; e += kThreads) accA[e] = T(0);
 
   // ---------------------------------------------------------------- init
   {
@@ -183,17 +246,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
         cur = t.seg;
       }
+      stage(t);
       const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-      for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-        const int r = rg + lane / BWL;
-        const bool rv_ = r < t.r1;
-        const bool ok = colok && rv_;
+      for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
         const size_t o = (size_t)r * ld + c;
-        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T res = (ok && act) ? -f.R[(size_t)r * f.ldr + c] : T(0);
-        const T z = ok ? res / deg[r] : T(0);
-        if (ok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
-        gram_col<T, BMAX, BWL>(acc, xc, z, b);
+        const T res = (colok && act) ? -f.R[(size_t)r * f.ldr + c] : T(0);
+        const T z = colok ? res / deg[r] : T(0);
+        if (colok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
+        gram_xs<T, BMAX>(acc, xs + (r - t.r0) * BMAX, z);
         ex[0] += res * z;
         ex[1] += res * res;
       }
@@ -217,15 +277,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
       f.resn[k] = r0;
       f.done[k] = (!act || r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
     }
-    for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-        const int r = rg + lane / BWL;
-        const bool rv_ = r < t.r1;
-        const bool ok = colok && rv_;
-        const size_t o = (size_t)r * ld + c;
-        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T z = project_col<T, BMAX, BWL>(ok ? f.Z[o] : T(0), xc, Gc, b);
-        if (ok) f.P[o] = z;
-      }
+    stage(t);
+    for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
+      if (!colok) continue;
+      const size_t o = (size_t)r * ld + c;
+      f.P[o] = project_xs<T, BMAX>(f.Z[o], xs + (r - t.r0) * BMAX, Gc);
+    }
   }
   if (!grid_barrier(f.bar)) return;
 
@@ -240,9 +297,6 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
         for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = 0.0;
     }
     {
-      // lanes as columns: a row group of BWL lanes walks the row's nonzeros,
-      // lane c accumulating column c (broadcast index load, contiguous row
-      // gather); the row's share of [1|X]^T q~ follows in the same pass.
       int cur = -1;
       T thc = T(0);
       for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
@@ -253,30 +307,84 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
           cur = t.seg;
           thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
         }
-        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-          const int r = rg + lane / BWL;
-          const bool rv_ = r < t.r1;
-          const bool ok = colok && rv_;
-          int p0 = 0, p1 = 0;
-          if (rv_) { p0 = g.rowptr[r]; p1 = g.rowptr[r + 1]; }
-          const bool hub = (p1 - p0) > g.long_thresh;
+        const int nrows = t.r1 - t.r0;
+        __syncthreads();
+        stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
+        for (int i = threadIdx.x; i <= nrows; i += kThreads) {
+          s_rp[i] = g.rowptr[t.r0 + i];
+          s_erp[i] = g.erp[t.r0 + i];
+        }
+        __syncthreads();
+        // merge-path walk over the tile's ordinary nonzeros
+        const int E0 = s_erp[0], E = s_erp[nrows] - E0;
+        const int es = E0 + (int)((long long)E * grp / SLOTS);
+        const int ee = E0 + (int)((long long)E * (grp + 1) / SLOTS);
+        if (es < ee) {
+          int lo = 0, hi = nrows - 1;  // last row i with s_erp[i] <= es
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_erp[mid] <= es) lo = mid; else hi = mid - 1;
+          }
+          int i = lo;
+          int nx = s_erp[i + 1];
+          int pb = s_rp[i] - s_erp[i];  // p = pb + e inside row i
           T a = T(0);
-          if (!hub && colok) {
-            if (w) {
-#pragma unroll 4
-              for (int p = p0; p < p1; ++p) a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-            } else {
-#pragma unroll 4
-              for (int p = p0; p < p1; ++p) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          for (int e0 = es; e0 < ee; e0 += kU) {
+            int pu[kU], iu[kU];
+            int ii = i;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              const int e = e0 + u;
+              pu[u] = -1;
+              iu[u] = ii;
+              if (e < ee) {
+                while (e >= nx) {
+                  ++ii;
+                  nx = s_erp[ii + 1];
+                  pb = s_rp[ii] - s_erp[ii];
+                }
+                pu[u] = pb + e;
+                iu[u] = ii;
+              }
+            }
+            T v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              v[u] = T(0);
+              if (pu[u] >= 0 && colok) {
+                const T x = __ldcg(f.P + (size_t)__ldg(g.colidx + pu[u]) * ld + c);
+                v[u] = w ? __ldg(w + pu[u]) * x : x;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              if (pu[u] >= 0) {
+                if (iu[u] != i) {
+                  if (colok) atomicAdd(accA + i * BMAX + c, a);
+                  a = T(0);
+                  i = iu[u];
+                }
+                a += v[u];
+              }
             }
           }
+          if (colok) atomicAdd(accA + i * BMAX + c, a);
+        }
+        __syncthreads();
+        // row epilogue: q~ = d p - (A p) - theta p; the Gram terms
+        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
+          const int il = r - t.r0;
+          if (s_rp[il + 1] - s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
+          T a = T(0);
+          if (colok) {
+            a = accA[il * BMAX + c];
+            accA[il * BMAX + c] = T(0);
+          }
           const size_t o = (size_t)r * ld + c;
-          const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-          const T pv = ok ? f.P[o] : T(0);
-          const T d = rv_ ? deg[r] : T(0);
-          const T q = (ok && !hub) ? d * pv - a - thc * pv : T(0);
-          if (ok && !hub) f.AP[o] = q;
-          gram_col<T, BMAX, BWL>(acc, xc, q, b);
+          const T pv = colok ? f.P[o] : T(0);
+          const T q = colok ? deg[r] * pv - a - thc * pv : T(0);
+          if (colok) f.AP[o] = q;
+          gram_xs<T, BMAX>(acc, xs + il * BMAX, q);
           ex[0] += pv * q;
         }
       }
@@ -285,7 +393,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
       // (hub.cuh) writes its q~ row and adds its share of G1 and p.q~ (to
       // the CTA's registers when the hub is in the CTA's current graph,
       // else with atomics)
-      for (int ch = blockIdx.x * NW + warp; ch < g.nchunk; ch += gridDim.x * NW) {
+      for (int ch = blockIdx.x * kWarps + warp; ch < g.nchunk; ch += gridDim.x * kWarps) {
         const int4 cc = g.chunks[ch];
         const int row = cc.x;
         const int seg = f.hub_seg[cc.w];
@@ -350,25 +458,21 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
             if (!dn && pq != 0.0 && isfinite(pq)) al = (T)(rho / pq);
           }
         }
-        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-        const int r = rg + lane / BWL;
-        const bool rv_ = r < t.r1;
-        const bool ok = colok && rv_;
-        const size_t o = (size_t)r * ld + c;
-        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T pv = ok ? f.P[o] : T(0);
-        const T qt = ok ? __ldcg(f.AP + o) : T(0);
-        const T tv = ok ? f.Tt[o] : T(0);
-        const T rv = ok ? f.RES[o] : T(0);
-        const T dv = rv_ ? deg[r] : T(1);
-        const T q = project_col<T, BMAX, BWL>(qt, xc, Gc, b);
-        const T res = rv - al * q;
-        const T z = ok ? res / dv : T(0);
-        if (ok) { f.Tt[o] = tv + al * pv; f.RES[o] = res; f.Z[o] = z; }
-        gram_col<T, BMAX, BWL>(acc, xc, z, b);
-        ex[0] += ok ? res * z : T(0);
-        ex[1] += ok ? res * res : T(0);
-      }
+        stage(t);
+        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
+          if (!colok) continue;
+          const size_t o = (size_t)r * ld + c;
+          const T* xr = xs + (r - t.r0) * BMAX;
+          const T q = project_xs<T, BMAX>(__ldcg(f.AP + o), xr, Gc);
+          const T res = f.RES[o] - al * q;
+          const T z = res / deg[r];
+          f.Tt[o] += al * f.P[o];
+          f.RES[o] = res;
+          f.Z[o] = z;
+          gram_xs<T, BMAX>(acc, xr, z);
+          ex[0] += res * z;
+          ex[1] += res * res;
+        }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
     }
@@ -399,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
               if (!(rn > f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
             }
             be = (T)bb;
-            if (owner(t) && threadIdx.x < 32 && lane < b && lane / BWL == 0 && warp == 0) {
+            if (owner(t) && threadIdx.x < BWL) {
               f.rho[(size_t)(par ^ 1) * f.state_stride + k] = rho_new;
               f.done[(size_t)(par ^ 1) * f.state_stride + k] = dn;
               f.resn[k] = rn;
@@ -421,17 +525,13 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
           s_all = __syncthreads_and(mine);
           all_known = 1;
         }
-        for (int rg = t.r0 + warp * RW; rg < t.r1; rg += SLOTS) {  // warp-uniform trip count
-        const int r = rg + lane / BWL;
-        const bool rv_ = r < t.r1;
-        const bool ok = colok && rv_;
-        const size_t o = (size_t)r * ld + c;
-        const T xc = ok ? X[(size_t)r * f.ldx + c] : T(0);
-        const T zt = ok ? f.Z[o] : T(0);
-        const T pv = ok ? f.P[o] : T(0);
-        const T z = project_col<T, BMAX, BWL>(zt, xc, Gc, b);
-        if (ok) f.P[o] = (be == T(0)) ? z : z + be * pv;
-      }
+        stage(t);
+        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
+          if (!colok) continue;
+          const size_t o = (size_t)r * ld + c;
+          const T z = project_xs<T, BMAX>(f.Z[o], xs + (r - t.r0) * BMAX, Gc);
+          f.P[o] = (be == T(0)) ? z : z + be * f.P[o];
+        }
       }
     }
     if (!grid_barrier(f.bar)) return;
@@ -446,11 +546,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX == 32) ? 1 :
   }
 }
 
-template <typename T, int BMAX, int TEAM>
+template <typename T, int BMAX>
 int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
-  constexpr int BWL = BMAX <= 4 ? 4 : BMAX;  // lanes per row in the column phases
-  auto kern = k_pcg_fused<T, BMAX, TEAM, BWL>;
-  const size_t smem = sizeof(double) * (size_t)(kThreads / 32) * (BMAX + 3) * BWL;
+  constexpr int BWL = BMAX <= 4 ? 4 : (BMAX > 16 ? 32 : BMAX);  // lanes per row
+  auto kern = k_pcg_fused<T, BMAX, BWL>;
+  const size_t smem = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL + 2 * (size_t)kTileRows * BMAX) +
+                      sizeof(int) * 2 * (kTileRows + 1);
   cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -461,22 +562,13 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   grid = grid < g.ntiles ? grid : g.ntiles;
   if (grid < 1) grid = 1;
   DevGraph gg = g;
-  // vector gathers of P rows need 16-byte aligned rows
-  constexpr int W = sizeof(T) == 4 ? 4 : 2;
-  const bool vec = (reinterpret_cast<uintptr_t>(f.Pv) % 16 == 0) && (f.ld % W == 0);
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
-             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, vec ? 1 : 0,
-             f.iters_out};
+             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, f.iters_out};
   void* args[] = {&gg, &ff};
   const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;
-}
-
-template <typename T, int BMAX>
-int launch_team(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
-  return g.team <= 4 ? launch<T, BMAX, 4>(g, f, s, max_ctas) : launch<T, BMAX, 8>(g, f, s, max_ctas);
 }
 
 }  // namespace
@@ -491,9 +583,10 @@ double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
 template <typename T>
 int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   LAP_PROF("pcg_fused", pcg_bytes(g, f.b, f.itmax, (int)sizeof(T)), s);
-  if (f.b <= 8) return launch_team<T, 8>(g, f, s, max_ctas);
-  if (f.b <= 16) return launch_team<T, 16>(g, f, s, max_ctas);
-  return launch_team<T, 32>(g, f, s, max_ctas);
+  if (f.b <= 8) return launch<T, 8>(g, f, s, max_ctas);
+  if (f.b <= 16) return launch<T, 16>(g, f, s, max_ctas);
+  if (f.b <= 24) return launch<T, 24>(g, f, s, max_ctas);
+  return launch<T, 32>(g, f, s, max_ctas);
 }
 
 template int pcg_fused<float>(const DevGraph&, const FusedPcg&, cudaStream_t, int);

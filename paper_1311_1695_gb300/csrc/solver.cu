@@ -183,6 +183,22 @@ struct JD {
     if (!init && x0d && k0 > 0) convert<double, TV>(g, x0d, ldx0, V, z.ldv, k0 < q ? k0 : q, st);
     cudaMemsetAsync(seg_skip, 0, sizeof(int) * z.nseg * 64, st);
     ortho(0, q, drop1);
+    // a start column dropped as dependent (a degenerate warm start, or one
+    // parallel to e) is replaced by a fresh random column: the search space
+    // must start with q independent directions
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      std::vector<int> kp((size_t)z.nseg * 64);
+      cudaMemcpyAsync(kp.data(), keep1, sizeof(int) * kp.size(), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      std::vector<int> refill;
+      for (int c = 0; c < q; ++c)
+        for (int s = 0; s < z.nseg; ++s)
+          if (!kp[(size_t)s * 64 + c]) { refill.push_back(c); break; }
+      if (refill.empty()) break;
+      for (int c : refill)
+        random_block<TV>(g, V + c, z.ldv, 1, seed ^ (0xD1B54A32D192ED03ull * (uint64_t)(c + 1 + 64 * (attempt + 1))), st);
+      ortho(0, q, drop1);
+    }
     spmm<TV>(g, V, z.ldv, W, z.ldv, q, st);
     n_matvec += q;
     gram<TV>(g, red, V, z.ldv, q, W, z.ldv, q, 0, 0, Gm, q, 65 * 64, seg_skip, st);
@@ -290,7 +306,9 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
       for (int j = 0; j < jd.z.b; ++j) {
         const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
         if (!std::isfinite(r)) bad = true;
-        const bool c = r <= tol_abs[s];
+        // every eigenvalue of L is <= ||L||_1: a larger Ritz value marks a
+        // dropped (zero) column, never a converged pair
+        const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
         if (j < P.k) {
           segc = segc && c;
           worst = std::max(worst, r / tol_abs[s]);
@@ -327,7 +345,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
         bool segc = true;
         for (int j = 0; j < P.k; ++j) {
           const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
-          const bool c = r <= tol_abs[s];
+          const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
           segc = segc && c;
           jd.active_h[(size_t)s * 64 + j] = c ? 0 : 1;
         }
@@ -377,8 +395,9 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     bool prefix = true;
     for (int j = 0; j < P.k; ++j) {
       const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j])) / G->norm1[s];
-      worst = std::max(worst, r);
-      if (prefix && r <= P.tol) ++nconv; else prefix = false;
+      const bool real = jd.theta_h[(size_t)s * jd.z.mmax + j] <= G->norm1[s];
+      worst = std::max(worst, real ? r : 1.0);
+      if (prefix && real && r <= P.tol) ++nconv; else prefix = false;
     }
     in.n_converged = nconv;
     // per graph: a batch member whose k pairs all meet the test is converged

@@ -10,9 +10,10 @@ BF16 for every use (the kernels compute with FP32 data and accumulate in FP32
 within a row, FP64 across rows).
 
 Network, for a batch handle of graphs (each graph its own segment):
-    H_0 = F (features),  [M H_l | H_l] [W_l; U_l] + b_l -> tanh -> H_{l+1},
-    X = H_3 W_out,       M = D^{-1} A.
-Loss per graph: 1 - tr((X^T X)^{-1} X^T U U^T X) / k (U = solver eigenvectors).
+    H_0 = F (features),  [M^s H_l | H_l] [W_l; U_l] + b_l -> tanh -> H_{l+1},
+    X = C H_3 W_out,     M = D^{-1} A,  s = HOPS,  C = per-graph centring.
+Loss per graph: 1 - tr(G^{-1} X^T U U^T X) / k with G = X^T X + eps tr(X^T X)/k I
+(U = solver eigenvectors); the k x k algebra of the loss runs on the host.
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ from . import LAP_F32, LAP_F64, Graph, _check, _stream, lib
 WIDTH = 32
 NFEAT = 16
 LAYERS = 3
+HOPS = 4
+EPS_RIDGE = 1e-6
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gnn_weights.json")
 
 
@@ -82,6 +85,7 @@ class Net:
         self.dH = torch.zeros((n, WIDTH), dtype=f32, device=dev)
         self.T1 = torch.zeros((n, WIDTH), dtype=f32, device=dev)
         self.dHn = torch.zeros((n, WIDTH), dtype=f32, device=dev)
+        self.tmp = [torch.zeros((n, WIDTH), dtype=f32, device=dev) for _ in range(2)]
         self.nseg = G.nseg
         self.rows = np.diff(G.row0)
 
@@ -91,7 +95,7 @@ class Net:
         S = np.concatenate([np.atleast_2d(m) for m in mats], axis=0)
         # row-major (C order) whatever the layout of the inputs (a transposed
         # weight is an F-ordered view): the kernel reads S[i * lds + j]
-        S = np.ascontiguousarray(np.broadcast_to(S, (nseg,) + S.shape), dtype=np.float64)
+        S = np.array(np.broadcast_to(S, (nseg,) + S.shape), dtype=np.float64, order="C", copy=True)
         return torch.from_numpy(S).cuda().contiguous(), S.shape[-1], S.shape[-2] * S.shape[-1]
 
     def _update(self, Y, ldy, q, beta, A, lda, p, ones, S, lds, ss):
@@ -106,6 +110,22 @@ class Net:
                               ctypes.c_void_p(B), ldb, q, ones, ctypes.c_void_p(Gm.data_ptr()), _stream()), "lap_gram")
         return Gm
 
+    def _aggregate(self, transpose, src, lds, dst, ldd, w):
+        """dst = M^s src (transpose = 0) or (M^T)^s src, s = HOPS."""
+        cur, ldc = src, lds
+        for h in range(HOPS):
+            last = h == HOPS - 1
+            out, ldo = (dst, ldd) if last else (self.tmp[h % 2].data_ptr(), WIDTH)
+            _check(lib().lap_gnn_aggregate(self.G.h, transpose, ctypes.c_void_p(cur), ldc, ctypes.c_void_p(out), ldo, w,
+                                           _stream()), "lap_gnn_aggregate")
+            cur, ldc = out, ldo
+
+    def _centre(self, Y, ldy, q):
+        """Subtract each graph's column means from Y (n x q, FP32)."""
+        Gm = self._gram(None, 0, 0, Y, ldy, q, 1)  # per-graph column means
+        S = (-Gm).contiguous()
+        self._update(Y, ldy, q, 1.0, None, 0, 0, 1, S, q, q)
+
     # -- forward: returns X (view of UX[:, k:])
     def forward(self, params, seed: int):
         P = [to_bf16(p) for p in params]
@@ -117,10 +137,8 @@ class Net:
         fin = NFEAT
         for l in range(LAYERS):
             A = AH[l]
-            # left half = M H_l
-            _check(lib().lap_gnn_aggregate(self.G.h, 0, ctypes.c_void_p(A.data_ptr() + e4 * fin), 2 * fin,
-                                           ctypes.c_void_p(A.data_ptr()), 2 * fin, fin, _stream()),
-                   "lap_gnn_aggregate")
+            # left half = M^s H_l
+            self._aggregate(0, A.data_ptr() + e4 * fin, 2 * fin, A.data_ptr(), 2 * fin, fin)
             W, U, b = P[3 * l: 3 * l + 3]
             S, lds, ss = self._S([b[None, :], W, U])
             out = AH[l + 1]
@@ -132,6 +150,7 @@ class Net:
         S, lds, ss = self._S([P[-1]])
         X = self.UX.data_ptr() + e4 * self.k
         self._update(X, 2 * self.k, self.k, 0.0, AH[LAYERS].data_ptr() + e4 * WIDTH, 2 * WIDTH, WIDTH, 0, S, lds, 0)
+        self._centre(X, 2 * self.k, self.k)
         self._P = P
         return self.UX[:, self.k:]
 
@@ -148,12 +167,15 @@ class Net:
         losses = np.zeros(self.nseg)
         S = np.zeros((self.nseg, 2 * k, k))
         for s in range(self.nseg):
-            Gi = np.linalg.inv(XtX[s])
+            Gr = XtX[s] + EPS_RIDGE * (np.trace(XtX[s]) / k) * np.eye(k)
+            Gi = np.linalg.inv(Gr)
             UX = UtX[s]
-            losses[s] = 1.0 - np.trace(Gi @ UX.T @ UX) / k
-            # mean over graphs: scale by 1/nseg
+            M = UX.T @ UX
+            losses[s] = 1.0 - np.trace(Gi @ M) / k
+            A = Gi @ M @ Gi
+            # dX = U S_u + X S_x; mean over graphs: scale by 1/nseg
             S[s, :k] = -(2.0 / k) * UX @ Gi / self.nseg
-            S[s, k:] = (2.0 / k) * Gi @ UX.T @ UX @ Gi / self.nseg
+            S[s, k:] = (2.0 / k) * (A + (EPS_RIDGE / k) * np.trace(A) * np.eye(k)) / self.nseg
         import torch
         St = torch.from_numpy(S).cuda()
         self._update(self.dX.data_ptr(), k, k, 0.0, UXp, 2 * k, 2 * k, 0, St, k, 2 * k * k)
@@ -164,6 +186,7 @@ class Net:
         P, k, AH = self._P, self.k, self.AH
         e4 = 4
         grads = [None] * len(P)
+        self._centre(self.dX.data_ptr(), k, k)  # the centring is its own adjoint
         H3 = AH[LAYERS].data_ptr() + e4 * WIDTH
         grads[-1] = self._gram(H3, 2 * WIDTH, WIDTH, self.dX.data_ptr(), k, k, 0).cpu().numpy().sum(axis=0)
         S, lds, _ = self._S([P[-1].T])
@@ -185,9 +208,7 @@ class Net:
                 W, U = P[3 * l], P[3 * l + 1]
                 S, lds, _ = self._S([W.T])
                 self._update(self.T1.data_ptr(), WIDTH, fin, 0.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
-                _check(lib().lap_gnn_aggregate(self.G.h, 1, ctypes.c_void_p(self.T1.data_ptr()), WIDTH,
-                                               ctypes.c_void_p(self.dHn.data_ptr()), WIDTH, fin, _stream()),
-                       "lap_gnn_aggregate")
+                self._aggregate(1, self.T1.data_ptr(), WIDTH, self.dHn.data_ptr(), WIDTH, fin)
                 S, lds, _ = self._S([U.T])
                 self._update(self.dHn.data_ptr(), WIDTH, fin, 1.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
                 self.dH, self.dHn = self.dHn, self.dH

@@ -1,7 +1,7 @@
 """Train the warm-start network on eigenvectors computed by this library.
 
     python -m paper_1311_1695_gb300.train_gnn [--graphs 10000] [--k 10]
-        [--batch 32] [--epochs 2] [--out gnn_weights.json]
+        [--batch 32] [--epochs 3] [--lr 1e-3] [--out gnn_weights.json]
 
 Training set: Chung-Lu graphs (largest component), n log-uniform in
 [1,000, 20,000], degree exponent uniform in [2.2, 2.8], mean degree 6, seeds
@@ -45,8 +45,8 @@ def main(argv=None):
     ap.add_argument("--graphs", type=int, default=10000)
     ap.add_argument("--k", type=int, default=10)
     ap.add_argument("--batch", type=int, default=32)
-    ap.add_argument("--epochs", type=int, default=2)
-    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 4))
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)

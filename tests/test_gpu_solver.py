@@ -139,3 +139,18 @@ def test_three_methods_agree_c1(pkg):
     for m, (ev, V, info) in res.items():
         assert info["status"] == 0, (m, info)
         check_eigpairs(g, ev, V, ev_ref, V_ref, k=4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_degenerate_warm_start(pkg, precision):
+    """A warm start whose columns are parallel to e (or to each other) loses
+    those columns in the orthonormalisation; they are refilled at random and
+    no dropped column is ever reported as a converged pair."""
+    g = G.ba_graph(800, 3, 17)
+    n, k = g.n, 6
+    x0 = np.ones((n, k))
+    x0[:, 3:] = np.arange(n)[:, None] % 7  # three equal columns
+    ev, V, info = pkg.lap_eigs(g, k, tol=1e-8, precision=precision, x0=x0)
+    assert info["status"] == 0, info
+    ev_ref, V_ref = dense.smallest_eigpairs(g, k + 8)
+    check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)

@@ -38,19 +38,47 @@ def test_backward_matches_finite_differences():
 def test_subspace_loss_invariances():
     rng = np.random.default_rng(2)
     U, _ = np.linalg.qr(rng.standard_normal((50, 4)))
-    # zero on span(U), for any invertible recombination
+    # without the ridge: zero on span(U), for any invertible recombination
     X = U @ rng.standard_normal((4, 4))
-    assert abs(gnn.subspace_loss(X, U)[0]) < 1e-12
+    assert abs(gnn.subspace_loss(X, U, eps=0.0)[0]) < 1e-12
     # invariant under X -> X R and under U -> U Q (orthogonal Q)
     Y = rng.standard_normal((50, 4))
     R = rng.standard_normal((4, 4))
     Q, _ = np.linalg.qr(rng.standard_normal((4, 4)))
-    l0 = gnn.subspace_loss(Y, U)[0]
-    assert abs(gnn.subspace_loss(Y @ R, U)[0] - l0) < 1e-10
-    assert abs(gnn.subspace_loss(Y, U @ Q)[0] - l0) < 1e-10
+    l0 = gnn.subspace_loss(Y, U, eps=0.0)[0]
+    assert abs(gnn.subspace_loss(Y @ R, U, eps=0.0)[0] - l0) < 1e-10
+    assert abs(gnn.subspace_loss(Y, U @ Q, eps=0.0)[0] - l0) < 1e-10
+    # still invariant under U -> U Q with the ridge
+    assert abs(gnn.subspace_loss(Y, U @ Q)[0] - gnn.subspace_loss(Y, U)[0]) < 1e-10
     # one for a block orthogonal to span(U)
     Z = Y - U @ (U.T @ Y)
-    assert abs(gnn.subspace_loss(Z, U)[0] - 1.0) < 1e-12
+    assert abs(gnn.subspace_loss(Z, U, eps=0.0)[0] - 1.0) < 1e-12
+    # with the ridge, X = U gives 1 - 1/(1 + eps) exactly; a rank-deficient X
+    # stays finite
+    assert abs(gnn.subspace_loss(U, U)[0] - gnn.EPS_RIDGE / (1 + gnn.EPS_RIDGE)) < 1e-14
+    Xd = np.column_stack([X[:, :3], X[:, 0]])
+    assert np.isfinite(gnn.subspace_loss(Xd, U)[0])
+
+
+def test_ridge_gradient_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((30, 3)))
+    X = rng.standard_normal((30, 3))
+    _, dX = gnn.subspace_loss(X, U, eps=1e-2)
+    h = 1e-6
+    for (i, j) in [(0, 0), (7, 2), (29, 1)]:
+        Xp, Xm = X.copy(), X.copy()
+        Xp[i, j] += h
+        Xm[i, j] -= h
+        fd = (gnn.subspace_loss(Xp, U, eps=1e-2)[0] - gnn.subspace_loss(Xm, U, eps=1e-2)[0]) / (2 * h)
+        assert abs(fd - dX[i, j]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_output_is_centred():
+    g = G.ba_graph(60, 2, 4)
+    F = gnn.features(g, 3)
+    X, _ = gnn.forward(g, F, gnn.init_params(4, seed=2))
+    assert np.abs(X.sum(axis=0)).max() < 1e-10
 
 
 def test_features_shape_and_range():
