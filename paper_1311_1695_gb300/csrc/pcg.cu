@@ -53,7 +53,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kU = 8;  // gathers in flight per row group in the merge-path walk
+constexpr int kU = 8;   // gathers in flight per row group in the merge-path walk
+// rows whose loads a row group issues together (fewer for the register-heavy
+// instantiations, which would spill)
+template <typename T, int BMAX> struct RowsInFlight { static constexpr int v = (sizeof(T) == 8 || BMAX >= 32) ? 2 : 4; };
 
 __device__ __forceinline__ int seg_rows(const DevGraph& g, int s) { return g.row0[s + 1] - g.row0[s]; }
 
@@ -94,6 +97,7 @@ struct View {
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
   double delta; int itmax; double *acc1, *acc2; int acc_stride; double* rho; int* done; double *res0, *resn;
   int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int* iters_out;
+  int xres;  // > 0: the X rows of all of this CTA's tiles stay staged (xres slots)
 };
 
 template <typename T> struct VecOf {};
@@ -198,13 +202,14 @@ __device__ __forceinline__ void stage_x(T* xs, const T* __restrict__ X, int ldx,
 }
 
 template <typename T, int BMAX, int BWL>
-__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
+__global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* red = reinterpret_cast<T*>(smem_raw);                          // [warps][BMAX+3][BWL]
-  T* xs = red + kWarps * (BMAX + 3) * BWL;                          // [kTileRows][BMAX]
-  T* accA = xs + kTileRows * BMAX;                                  // [kTileRows][BMAX]
+  T* xs = red + kWarps * (BMAX + 3) * BWL;                          // [max(1, xres)][kTileRows][BMAX]
+  T* accA = xs + (size_t)(f.xres > 1 ? f.xres : 1) * kTileRows * BMAX;  // [kTileRows][BMAX]
   int* s_rp = reinterpret_cast<int*>(accA + kTileRows * BMAX);      // [kTileRows + 1]
   int* s_erp = s_rp + kTileRows + 1;                                // [kTileRows + 1]
+  constexpr int kRU = RowsInFlight<T, BMAX>::v;
   constexpr int RW = 32 / BWL;        // rows per warp pass
   constexpr int SLOTS = kWarps * RW;  // row groups per CTA
   const int b = f.b;
@@ -229,40 +234,64 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
 #pragma unroll
     for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)(__ldcg(A + i * b + c) * (i == 0 ? inv_n : 1.0)) : T(0);
   };
-  auto stage = [&](const Tile& t) {
+  // X rows of the k-th tile of this CTA: resident slot k, or the one
+  // staging buffer refilled per tile and phase
+  auto stage = [&](const Tile& t, int k) -> const T* {
+    if (f.xres) return xs + (size_t)k * kTileRows * BMAX;
     __syncthreads();  // the previous tile's readers are done
     stage_x<T, BMAX>(xs, X, f.ldx, t.r0, t.r1 - t.r0, b);
     __syncthreads();
+    return xs;
   };
   for (int e = threadIdx.x; e < kTileRows * BMAX; e += kThreads) accA[e] = T(0);
+  if (f.xres) {
+    for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
+      const Tile t = g.tiles[ti];
+      stage_x<T, BMAX>(xs + (size_t)k * kTileRows * BMAX, X, f.ldx, t.r0, t.r1 - t.r0, b);
+    }
+    __syncthreads();
+  }
 
   // ---------------------------------------------------------------- init
   {
     int cur = -1;
-    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
       const Tile t = g.tiles[ti];
       if (f.seg_skip && f.seg_skip[t.seg]) continue;
       if (t.seg != cur) {
         if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
         cur = t.seg;
       }
-      stage(t);
+      const T* xt = stage(t, k);
       const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-      for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
-        const size_t o = (size_t)r * ld + c;
-        const T res = (colok && act) ? -f.R[(size_t)r * f.ldr + c] : T(0);
-        const T z = colok ? res / deg[r] : T(0);
-        if (colok) { f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z; }
-        gram_xs<T, BMAX>(acc, xs + (r - t.r0) * BMAX, z);
-        ex[0] += res * z;
-        ex[1] += res * res;
+      if (!colok) continue;
+      for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+        T rr[kRU], dv[kRU];
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          const int r = rb + u * SLOTS;
+          rr[u] = T(0); dv[u] = T(1);
+          if (r < t.r1) { rr[u] = act ? -f.R[(size_t)r * f.ldr + c] : T(0); dv[u] = deg[r]; }
+        }
+#pragma unroll
+        for (int u = 0; u < kRU; ++u) {
+          const int r = rb + u * SLOTS;
+          if (r < t.r1) {
+            const size_t o = (size_t)r * ld + c;
+            const T res = rr[u], z = res / dv[u];
+            f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
+            gram_xs<T, BMAX>(acc, xt + (r - t.r0) * BMAX, z);
+            ex[0] += res * z;
+            ex[1] += res * res;
+          }
+        }
       }
     }
     if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
   }
   if (!grid_barrier(f.bar)) return;
   // init-C: p = z~ - [1|X] G2; owner records rho, res0, done (parity 0)
-  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+  for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
     const Tile t = g.tiles[ti];
     if (f.seg_skip && f.seg_skip[t.seg]) continue;
     const double* A2 = f.acc2 + (size_t)t.seg * stride1;
@@ -277,11 +306,20 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
       f.resn[k] = r0;
       f.done[k] = (!act || r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
     }
-    stage(t);
-    for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
-      if (!colok) continue;
-      const size_t o = (size_t)r * ld + c;
-      f.P[o] = project_xs<T, BMAX>(f.Z[o], xs + (r - t.r0) * BMAX, Gc);
+    const T* xt = stage(t, k);
+    if (!colok) continue;
+    for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+      T zv[kRU];
+#pragma unroll
+      for (int u = 0; u < kRU; ++u) {
+        const int r = rb + u * SLOTS;
+        zv[u] = r < t.r1 ? f.Z[(size_t)r * ld + c] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kRU; ++u) {
+        const int r = rb + u * SLOTS;
+        if (r < t.r1) f.P[(size_t)r * ld + c] = project_xs<T, BMAX>(zv[u], xt + (r - t.r0) * BMAX, Gc);
+      }
     }
   }
   if (!grid_barrier(f.bar)) return;
@@ -299,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
     {
       int cur = -1;
       T thc = T(0);
-      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+      for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
@@ -308,8 +346,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
           thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
         }
         const int nrows = t.r1 - t.r0;
+        const T* xt = f.xres ? xs + (size_t)k * kTileRows * BMAX : xs;
         __syncthreads();
-        stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
+        if (!f.xres) stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
         for (int i = threadIdx.x; i <= nrows; i += kThreads) {
           s_rp[i] = g.rowptr[t.r0 + i];
           s_erp[i] = g.erp[t.r0 + i];
@@ -372,20 +411,29 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
         }
         __syncthreads();
         // row epilogue: q~ = d p - (A p) - theta p; the Gram terms
-        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
-          const int il = r - t.r0;
-          if (s_rp[il + 1] - s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
-          T a = T(0);
-          if (colok) {
-            a = accA[il * BMAX + c];
-            accA[il * BMAX + c] = T(0);
+        if (colok) {
+          for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+            T pv[kRU], dv[kRU];
+#pragma unroll
+            for (int u = 0; u < kRU; ++u) {
+              const int r = rb + u * SLOTS;
+              pv[u] = T(0); dv[u] = T(0);
+              if (r < t.r1) { pv[u] = f.P[(size_t)r * ld + c]; dv[u] = deg[r]; }
+            }
+#pragma unroll
+            for (int u = 0; u < kRU; ++u) {
+              const int r = rb + u * SLOTS;
+              if (r >= t.r1) continue;
+              const int il = r - t.r0;
+              if (s_rp[il + 1] - s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
+              const T a = accA[il * BMAX + c];
+              accA[il * BMAX + c] = T(0);
+              const T q = dv[u] * pv[u] - a - thc * pv[u];
+              f.AP[(size_t)r * ld + c] = q;
+              gram_xs<T, BMAX>(acc, xt + il * BMAX, q);
+              ex[0] += pv[u] * q;
+            }
           }
-          const size_t o = (size_t)r * ld + c;
-          const T pv = colok ? f.P[o] : T(0);
-          const T q = colok ? deg[r] * pv - a - thc * pv : T(0);
-          if (colok) f.AP[o] = q;
-          gram_xs<T, BMAX>(acc, xs + il * BMAX, q);
-          ex[0] += pv * q;
         }
       }
       // hub rows: chunks of at most kHubChunk nonzeros, one warp each,
@@ -441,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
     {
       int cur = -1;
       T al = T(0);
-      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+      for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
@@ -458,20 +506,35 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
             if (!dn && pq != 0.0 && isfinite(pq)) al = (T)(rho / pq);
           }
         }
-        stage(t);
-        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
-          if (!colok) continue;
-          const size_t o = (size_t)r * ld + c;
-          const T* xr = xs + (r - t.r0) * BMAX;
-          const T q = project_xs<T, BMAX>(__ldcg(f.AP + o), xr, Gc);
-          const T res = f.RES[o] - al * q;
-          const T z = res / deg[r];
-          f.Tt[o] += al * f.P[o];
-          f.RES[o] = res;
-          f.Z[o] = z;
-          gram_xs<T, BMAX>(acc, xr, z);
-          ex[0] += res * z;
-          ex[1] += res * res;
+        const T* xt = stage(t, k);
+        if (!colok) continue;
+        for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+          T ap[kRU], rs[kRU], dv[kRU], tv[kRU], pv[kRU];
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            ap[u] = rs[u] = tv[u] = pv[u] = T(0); dv[u] = T(1);
+            if (r < t.r1) {
+              const size_t o = (size_t)r * ld + c;
+              ap[u] = __ldcg(f.AP + o); rs[u] = f.RES[o]; tv[u] = f.Tt[o]; pv[u] = f.P[o]; dv[u] = deg[r];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            if (r >= t.r1) continue;
+            const size_t o = (size_t)r * ld + c;
+            const T* xr = xt + (r - t.r0) * BMAX;
+            const T q = project_xs<T, BMAX>(ap[u], xr, Gc);
+            const T res = rs[u] - al * q;
+            const T z = res / dv[u];
+            f.Tt[o] = tv[u] + al * pv[u];
+            f.RES[o] = res;
+            f.Z[o] = z;
+            gram_xs<T, BMAX>(acc, xr, z);
+            ex[0] += res * z;
+            ex[1] += res * res;
+          }
         }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
@@ -483,7 +546,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
     {
       int cur = -1;
       T be = T(0);
-      for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+      for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
         const Tile t = g.tiles[ti];
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
@@ -525,12 +588,23 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 24) ? 1 :
           s_all = __syncthreads_and(mine);
           all_known = 1;
         }
-        stage(t);
-        for (int r = t.r0 + grp; r < t.r1; r += SLOTS) {
-          if (!colok) continue;
-          const size_t o = (size_t)r * ld + c;
-          const T z = project_xs<T, BMAX>(f.Z[o], xs + (r - t.r0) * BMAX, Gc);
-          f.P[o] = (be == T(0)) ? z : z + be * f.P[o];
+        const T* xt = stage(t, k);
+        if (!colok) continue;
+        for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+          T zv[kRU], pv[kRU];
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            zv[u] = pv[u] = T(0);
+            if (r < t.r1) { zv[u] = f.Z[(size_t)r * ld + c]; pv[u] = f.P[(size_t)r * ld + c]; }
+          }
+#pragma unroll
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            if (r >= t.r1) continue;
+            const T z = project_xs<T, BMAX>(zv[u], xt + (r - t.r0) * BMAX, Gc);
+            f.P[(size_t)r * ld + c] = (be == T(0)) ? z : z + be * pv[u];
+          }
         }
       }
     }
@@ -550,22 +624,44 @@ template <typename T, int BMAX>
 int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   constexpr int BWL = BMAX <= 4 ? 4 : (BMAX > 16 ? 32 : BMAX);  // lanes per row
   auto kern = k_pcg_fused<T, BMAX, BWL>;
-  const size_t smem = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL + 2 * (size_t)kTileRows * BMAX) +
-                      sizeof(int) * 2 * (kTileRows + 1);
-  cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t tile_x = sizeof(T) * (size_t)kTileRows * BMAX;
+  const size_t base = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL) + 2 * tile_x + sizeof(int) * 2 * (kTileRows + 1);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  int grid = per_sm * nsm;
-  if (max_ctas > 0) grid = grid < max_ctas ? grid : max_ctas;
-  grid = grid < g.ntiles ? grid : g.ntiles;
-  if (grid < 1) grid = 1;
+  auto grid_for = [&](size_t smem) {
+    cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    int grid = per_sm * nsm;
+    if (max_ctas > 0) grid = grid < max_ctas ? grid : max_ctas;
+    grid = grid < g.ntiles ? grid : g.ntiles;
+    return grid < 1 ? 1 : grid;
+  };
+  size_t smem = base;
+  int grid = grid_for(smem);
+  // keep every tile's X rows resident when they fit without costing
+  // occupancy (always when each CTA owns one tile)
+  int xres = 0;
+  const int tiles_per_cta = (g.ntiles + grid - 1) / grid;
+  if (tiles_per_cta == 1) {
+    xres = 1;
+  } else if (tiles_per_cta <= 8) {
+    const size_t smem2 = base + (tiles_per_cta - 1) * tile_x;
+    const int per_sm1 = per_sm;
+    const int grid2 = grid_for(smem2);
+    if (per_sm >= per_sm1 && smem2 <= 200 * 1024 && (g.ntiles + grid2 - 1) / grid2 <= tiles_per_cta) {
+      xres = tiles_per_cta;
+      smem = smem2;
+      grid = grid2;
+    } else {
+      grid = grid_for(smem);
+    }
+  }
   DevGraph gg = g;
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
-             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, f.iters_out};
+             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, f.iters_out, xres};
   void* args[] = {&gg, &ff};
   const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;

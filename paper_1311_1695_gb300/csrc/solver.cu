@@ -92,6 +92,8 @@ struct JD {
   int64_t n_matvec = 0;
   int inner_its = 0;
   int last_nact = 0;  // columns corrected by the last correction solve
+  bool inject = false;  // next expansion adds random directions (stagnation)
+  int injections = 0;
   PcgWork* pw = nullptr;
 
   JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
@@ -265,6 +267,14 @@ struct JD {
     last_nact = nact;
     // T -> V[:, mk : mk+b]
     convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
+    if (inject) {
+      // stagnation: the guard columns' slots (or the last slot) get random
+      // directions, so the search space keeps growing when corrections lie
+      // in span(V) and would be dropped
+      const int c0 = z.k < z.b ? z.k : z.b - 1;
+      random_block<TV>(g, V + mk + c0, z.ldv, z.b - c0, 0xA076'1D64'78BD'642Full ^ (uint64_t)(++injections), st);
+      inject = false;
+    }
     ortho(mk, z.b, drop1);
     spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
     n_matvec += nact;
@@ -289,7 +299,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
   const int S = jd.z.nseg;
   std::fill(jd.skip_h.begin(), jd.skip_h.end(), 0);
   double best = 1e300;
-  int stall = 0;
+  int stall = 0, stag = 0;
   int rc = LAP_ENOCONV;
   while (outer < P.max_outer) {
     ++outer;
@@ -354,8 +364,11 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
       }
     }
     if (all) { rc = LAP_OK; break; }
-    if (worst < 0.5 * best) { best = worst; stall = 0; }
-    else if (++stall >= stall_limit) { rc = LAP_ENOCONV; break; }
+    if (worst < 0.5 * best) { best = worst; stall = 0; stag = 0; }
+    else {
+      if (++stall >= stall_limit) { rc = LAP_ENOCONV; break; }
+      if (++stag >= 20) { jd.inject = true; stag = 0; }
+    }
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
     if (P.max_seconds > 0 && el > P.max_seconds) { set_error("time limit reached"); rc = LAP_ETIMEOUT; break; }
     cudaMemcpyAsync(jd.active, jd.active_h.data(), sizeof(int) * S * 64, cudaMemcpyHostToDevice, jd.st);
