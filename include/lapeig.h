@@ -82,6 +82,8 @@ typedef struct {
   const double* x0_dev; /* optional device warm start, row-major n x k0 (ld = ldx0), FP64;
                            used instead of x0 when set (single-graph solves) */
   int ldx0;
+  int cuda_graph;     /* JD: 0 (default) replays each steady-state outer iteration
+                         as one captured CUDA graph; -1 enqueues it kernel by kernel */
 } lap_opts;
 
 typedef struct {

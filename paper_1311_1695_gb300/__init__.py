@@ -57,6 +57,7 @@ class lap_opts(ctypes.Structure):
         ("verbose", ctypes.c_int),
         ("x0_dev", ctypes.c_void_p),
         ("ldx0", ctypes.c_int),
+        ("cuda_graph", ctypes.c_int),
     ]
 
 
@@ -165,7 +166,7 @@ def _ptr(a, ct):
 
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
               include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
-              x0_dev=None):
+              x0_dev=None, cuda_graph=True):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -175,6 +176,7 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.seed = seed
     o.max_seconds, o.team, o.verbose = max_seconds, team, int(bool(verbose))
     o.stream = stream
+    o.cuda_graph = 0 if cuda_graph else -1
     keep = None
     if x0_dev is not None:  # a row-major float64 CUDA tensor n x k0
         o.x0_dev = ctypes.c_void_p(x0_dev.data_ptr())

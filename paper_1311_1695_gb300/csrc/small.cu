@@ -68,6 +68,59 @@ __global__ void k_and(int count, int* a, const int* b) {
   if (i < count) a[i] = (a[i] != 0 && b[i] != 0) ? 1 : 0;
 }
 
+// One CTA walks the graphs (thread per graph), then reduces in a fixed order.
+__global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
+                           const double* __restrict__ norm1, const double* __restrict__ tol_abs, int k, int b,
+                           int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
+                           JdStatus* status) {
+  __shared__ double s_w[256];
+  __shared__ int s_c[256], s_bad[256], s_act[256], s_open[256];
+  double worst = 0.0;
+  int cand = 0, bad = 0, nact = 0, open = 0;
+  for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+    int st = state[s];
+    if (st != 1) {
+      bool segc = true;
+      int na = 0;
+      for (int j = 0; j < b; ++j) {
+        const double r = sqrt(fmax(0.0, rn2[(size_t)s * 64 + j]));
+        if (!isfinite(r)) bad = 1;
+        const bool c = r <= tol_abs[s] && theta[(size_t)s * mmax + j] <= norm1[s];
+        if (j < k) {
+          segc = segc && c;
+          worst = fmax(worst, r / tol_abs[s]);
+        }
+        const int a = (j < k && c) ? 0 : 1;
+        active[(size_t)s * 64 + j] = a;
+        na += a;
+      }
+      st = segc ? (explicit_check ? 2 : 1) : 0;
+      state[s] = st;
+      if (st == 0) nact += na;
+    }
+    skip[s] = st != 0 ? 1 : 0;
+    cand += st == 2;
+    open += st != 1;
+  }
+  s_w[threadIdx.x] = worst; s_c[threadIdx.x] = cand; s_bad[threadIdx.x] = bad;
+  s_act[threadIdx.x] = nact; s_open[threadIdx.x] = open;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w = 0.0;
+    int c = 0, bd = 0, na = 0, op = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      w = fmax(w, s_w[i]); c += s_c[i]; bd |= s_bad[i]; na += s_act[i]; op += s_open[i];
+    }
+    status->worst = w;
+    status->all_done = op == 0;
+    status->candidates = c;
+    status->bad = bd;
+    status->nact = na;
+    status->pcg_err = (int)bar[2];
+    status->pcg_steps = (int)bar[3];
+  }
+}
+
 // Sign convention: per segment and column, the entry of largest magnitude
 // (first row among exact ties) is made positive.  Pass 1: atomicMax of the
 // FP64 bit pattern of |v| (non-negative doubles order like their bits);
@@ -124,6 +177,13 @@ void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
   k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, norm1, seg_skip);
+}
+void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
+              int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
+              JdStatus* status, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
+  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, b, explicit_check, state, active, skip, bar,
+                               status);
 }
 void and_flags(int count, int* a, const int* b, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);

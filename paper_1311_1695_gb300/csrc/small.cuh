@@ -10,6 +10,26 @@ void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double*
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s);
 void and_flags(int count, int* a, const int* b, cudaStream_t s);
+
+// Convergence bookkeeping of one JD outer iteration on the device (so the
+// iteration can be replayed as a captured CUDA graph).  Per graph s with
+// state[s] != 1 (1 = converged, skipped): column j < b is converged when
+// ||r_j|| <= tol_abs[s] and theta_j <= ||L||_1 (a larger Ritz value marks a
+// dropped column); active[s*64 + j] = !(j < k and converged).  A graph whose
+// k wanted columns all converged becomes 2 (candidate, when explicit_check:
+// the host verifies it with an explicit L X) or 1.  skip[s] = state[s] != 0.
+struct JdStatus {
+  double worst;      // max over graphs and j < k of ||r_j|| / tol_abs
+  int all_done;      // every graph in state 1
+  int candidates;    // graphs in state 2
+  int bad;           // a non-finite residual
+  int nact;          // active columns of graphs in state 0
+  int pcg_err;       // grid-barrier error flag of the last correction solve
+  int pcg_steps;     // its PCG steps
+};
+void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
+              int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
+              JdStatus* status, cudaStream_t s);
 // best: device scratch of 2 * nseg * k 64-bit words.
 template <typename T>
 void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s);

@@ -95,8 +95,25 @@ struct JD {
   bool inject = false;  // next expansion adds random directions (stagnation)
   int injections = 0;
   PcgWork* pw = nullptr;
+  // device-side convergence state (one outer iteration replays as a graph)
+  int* state = nullptr;        // [S] 0 open, 1 converged, 2 candidate
+  double* tol_d = nullptr;     // [S]
+  JdStatus* status_d = nullptr;
+  JdStatus* status_h = nullptr;  // pinned
+  int* state_h = nullptr;        // pinned [S]
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_m = 0;  // basis size after a replayed iteration
 
   JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
+  ~JD() {
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (status_h) cudaFreeHost(status_h);
+    if (state_h) cudaFreeHost(state_h);
+  }
+  JD(const JD&) = delete;
+  JD& operator=(const JD&) = delete;
 
   static size_t bytes(const Sizes& z) {
     const size_t n = z.n, S = z.nseg;
@@ -111,6 +128,7 @@ struct JD {
     for (int i = 0; i < 5; ++i) add(S * 64 * 4);
     for (int i = 0; i < 5; ++i) add(S * 64 * 8);
     add(S * 33 * 32 * 8); add(S * 33 * 32 * 8); add(S * 64 * 4);
+    add(S * 4); add(S * 8); add(sizeof(JdStatus));
     return b + 4096;
   }
 
@@ -151,6 +169,11 @@ struct JD {
     ps.done = a.take<int>(S * 64);
     ps.bstride = 64;
     ps.gstride = 33 * 32;
+    state = a.take<int>(S);
+    tol_d = a.take<double>(S);
+    status_d = a.take<JdStatus>(1);
+    if (cudaMallocHost(reinterpret_cast<void**>(&status_h), sizeof(JdStatus)) != cudaSuccess) status_h = nullptr;
+    if (cudaMallocHost(reinterpret_cast<void**>(&state_h), sizeof(int) * S) != cudaSuccess) state_h = nullptr;
     rn2_h.assign(S * 64, 0.0);
     theta_h.assign(S * z.mmax, 0.0);
     active_h.assign(S * 64, 1);
@@ -222,6 +245,19 @@ struct JD {
     return mk;
   }
 
+  // Rayleigh-Ritz, residuals and the device convergence bookkeeping, with
+  // the status copied to pinned host memory: the tail of an outer iteration
+  // (no host synchronisation, capturable).  Returns the new basis size.
+  int tail(int m, bool explicit_check) {
+    const int mk = rayleigh_ritz(m);
+    residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
+    converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, z.b, explicit_check ? 1 : 0, state, active, seg_skip,
+             pw->bar, status_d, st);
+    cudaMemcpyAsync(status_h, status_d, sizeof(JdStatus), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(state_h, state, sizeof(int) * z.nseg, cudaMemcpyDeviceToHost, st);
+    return mk;
+  }
+
   // residuals of the Ritz block into Rv and rn2 (copied to the host).
   int residuals(bool explicit_lx) {
     if (explicit_lx) {
@@ -260,11 +296,6 @@ struct JD {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;
     }
-    int nact = 0;
-    for (int s = 0; s < z.nseg; ++s)
-      if (!skip_h[s])
-        for (int j = 0; j < z.b; ++j) nact += active_h[(size_t)s * 64 + j] ? 1 : 0;
-    last_nact = nact;
     // T -> V[:, mk : mk+b]
     convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
     if (inject) {
@@ -277,7 +308,6 @@ struct JD {
     }
     ortho(mk, z.b, drop1);
     spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
-    n_matvec += nact;
     gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
     h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, G->d_norm1, seg_skip, st);
     return mk + z.b;
@@ -293,77 +323,64 @@ struct Params {
 // Run outer iterations until every segment has its k wanted pairs below
 // tol_abs[s]; explicit_check re-forms L X before accepting.  Returns LAP_OK,
 // LAP_ENOCONV, LAP_ETIMEOUT or an error; `outer` accumulates iterations.
+// The steady-state iteration (correction + expansion + Rayleigh-Ritz +
+// residuals + bookkeeping) runs as one captured CUDA graph replayed each
+// iteration; the host reads a small status block and decides to stop,
+// to verify candidates with an explicit L X, or to continue.  Iterations that
+// add random directions, and profiled runs, are enqueued eagerly.
 template <typename TV, typename TP>
 int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& tol_abs, bool explicit_check,
-            int& outer, int& m_out, double drop1, int stall_limit) {
+            int& outer, int& m_out, double drop1, int stall_limit, bool use_graph) {
   const int S = jd.z.nseg;
+  cudaStream_t st = jd.st;
+  if (!jd.status_h || !jd.state_h) { set_error("pinned host allocation failed"); return LAP_ENOMEM; }
   std::fill(jd.skip_h.begin(), jd.skip_h.end(), 0);
+  cudaMemsetAsync(jd.state, 0, sizeof(int) * S, st);
+  cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, st);
+  cudaMemcpyAsync(jd.tol_d, tol_abs.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st);
+  use_graph = use_graph && !prof_on();
   double best = 1e300;
   int stall = 0, stag = 0;
   int rc = LAP_ENOCONV;
-  while (outer < P.max_outer) {
-    ++outer;
-    const int mk = jd.rayleigh_ritz(m);
-    m = mk;
-    int e = jd.residuals(false);
-    if (e) return e;
-    // convergence bookkeeping on the host
-    bool all = true, bad = false;
-    double worst = 0.0;
-    for (int s = 0; s < S; ++s) {
-      if (jd.skip_h[s]) continue;
-      bool segc = true;
-      for (int j = 0; j < jd.z.b; ++j) {
-        const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
-        if (!std::isfinite(r)) bad = true;
-        // every eigenvalue of L is <= ||L||_1: a larger Ritz value marks a
-        // dropped (zero) column, never a converged pair
-        const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
-        if (j < P.k) {
-          segc = segc && c;
-          worst = std::max(worst, r / tol_abs[s]);
-        }
-        jd.active_h[(size_t)s * 64 + j] = (j < P.k && c) ? 0 : 1;
-      }
-      if (segc) {
-        if (explicit_check) {
-          jd.skip_h[s] = 2;  // candidate: verify below
-        } else {
-          jd.skip_h[s] = 1;
-        }
-      } else {
-        all = false;
-      }
-    }
-    if (bad) { set_error("NaN/Inf residual in JD"); return LAP_ENUMERIC; }
-    if (P.verbose) fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, worst);
-    bool any_candidate = false;
-    for (int s = 0; s < S; ++s) any_candidate |= jd.skip_h[s] == 2;
-    if (any_candidate) {
-      // explicit check of the candidates: L X formed afresh
-      std::vector<int> mask(S * 64, 1);
-      for (int s = 0; s < S; ++s) mask[(size_t)s * 64] = jd.skip_h[s] == 2 ? 0 : 1;
+  ++outer;
+  m = jd.tail(m, explicit_check);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("CUDA error in JD loop"); return LAP_ECUDA; }
+  while (true) {
+    const JdStatus stt = *jd.status_h;
+    if (stt.bad) { set_error("NaN/Inf residual in JD"); return LAP_ENUMERIC; }
+    if (P.verbose) fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, stt.worst);
+    bool all = stt.all_done != 0;
+    if (stt.candidates > 0) {
+      // explicit check of the candidates: L X formed afresh (eager)
       std::vector<int> sk(S);
-      for (int s = 0; s < S; ++s) sk[s] = jd.skip_h[s] == 2 ? 0 : 1;
-      cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
-      e = jd.residuals(true);
+      for (int s = 0; s < S; ++s) sk[s] = jd.state_h[s] == 2 ? 0 : 1;
+      cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
+      int e = jd.residuals(true);
       if (e) return e;
       all = true;
+      std::vector<int> act((size_t)S * 64);
+      cudaMemcpyAsync(act.data(), jd.active, sizeof(int) * act.size(), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
       for (int s = 0; s < S; ++s) {
-        if (jd.skip_h[s] == 1) continue;
-        if (jd.skip_h[s] == 0) { all = false; continue; }
-        bool segc = true;
-        for (int j = 0; j < P.k; ++j) {
-          const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
-          const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
-          segc = segc && c;
-          jd.active_h[(size_t)s * 64 + j] = c ? 0 : 1;
+        if (jd.state_h[s] == 2) {
+          bool segc = true;
+          for (int j = 0; j < P.k; ++j) {
+            const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
+            const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
+            segc = segc && c;
+            act[(size_t)s * 64 + j] = c ? 0 : 1;
+          }
+          jd.state_h[s] = segc ? 1 : 0;
         }
-        jd.skip_h[s] = segc ? 1 : 0;
-        all = all && segc;
+        all = all && jd.state_h[s] == 1;
+        sk[s] = jd.state_h[s] != 0 ? 1 : 0;
       }
+      cudaMemcpyAsync(jd.state, jd.state_h, sizeof(int) * S, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(jd.active, act.data(), sizeof(int) * act.size(), cudaMemcpyHostToDevice, st);
     }
     if (all) { rc = LAP_OK; break; }
+    const double worst = stt.worst;
     if (worst < 0.5 * best) { best = worst; stall = 0; stag = 0; }
     else {
       if (++stall >= stall_limit) { rc = LAP_ENOCONV; break; }
@@ -371,21 +388,78 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     }
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
     if (P.max_seconds > 0 && el > P.max_seconds) { set_error("time limit reached"); rc = LAP_ETIMEOUT; break; }
-    cudaMemcpyAsync(jd.active, jd.active_h.data(), sizeof(int) * S * 64, cudaMemcpyHostToDevice, jd.st);
-    std::vector<int> sk(S);
-    for (int s = 0; s < S; ++s) sk[s] = jd.skip_h[s] ? 1 : 0;
-    cudaMemcpyAsync(jd.seg_skip, sk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, jd.st);
-    m = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
-    if (m < 0) return LAP_ECUDA;
-    int perr = 0, steps = 0;
-    jd.pw->status(jd.st, &perr, &steps);
-    if (perr) { set_error("grid barrier in the correction solve timed out"); return LAP_ETIMEOUT; }
-    jd.inner_its += steps;
-    jd.n_matvec += (int64_t)steps * jd.last_nact;
-    if (prof_on()) prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, steps, (int)sizeof(TP)));
+    if (outer >= P.max_outer) { rc = LAP_ENOCONV; break; }
+    // the next iteration
+    ++outer;
+    int nact = stt.nact;
+    if (stt.candidates > 0) {
+      // candidates re-opened by the explicit check add their active columns
+      std::vector<int> act((size_t)S * 64);
+      cudaMemcpyAsync(act.data(), jd.active, sizeof(int) * act.size(), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      nact = 0;
+      for (int s = 0; s < S; ++s)
+        if (jd.state_h[s] == 0)
+          for (int j = 0; j < jd.z.b; ++j) nact += act[(size_t)s * 64 + j];
+    }
+    const bool eager = !use_graph || jd.inject;
+    int m2 = m;
+    if (eager) {
+      m2 = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
+      if (m2 < 0) return LAP_ECUDA;
+      m2 = jd.tail(m2, explicit_check);
+    } else {
+      if (!jd.graph_exec) {
+        cudaGetLastError();
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+          int mm = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
+          if (mm >= 0) mm = jd.tail(mm, explicit_check);
+          cudaGraph_t gr = nullptr;
+          const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+          if (ec == cudaSuccess && mm >= 0 && gr &&
+              cudaGraphInstantiate(&jd.graph_exec, gr, nullptr, nullptr, 0) == cudaSuccess) {
+            jd.graph = gr;
+            jd.graph_m = mm;
+          } else {
+            if (gr) cudaGraphDestroy(gr);
+            jd.graph_exec = nullptr;
+          }
+        }
+        cudaGetLastError();
+        if (!jd.graph_exec) {  // capture not possible: stay eager
+          use_graph = false;
+          m2 = jd.correct_and_expand(m, P.itmax, P.delta, drop1);
+          if (m2 < 0) return LAP_ECUDA;
+          m2 = jd.tail(m2, explicit_check);
+        }
+      }
+      if (jd.graph_exec) {
+        if (cudaGraphLaunch(jd.graph_exec, st) != cudaSuccess) { set_error("CUDA graph launch failed"); return LAP_ECUDA; }
+        m2 = jd.graph_m;
+      }
+    }
+    m = m2;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error(std::string("CUDA error in JD loop: ") + cudaGetErrorString(cudaGetLastError()));
+      return LAP_ECUDA;
+    }
+    const JdStatus& s2 = *jd.status_h;
+    if (s2.pcg_err) {
+      jd.pw->status(st, nullptr, nullptr);  // clears the flag
+      set_error("grid barrier in the correction solve timed out");
+      return LAP_ETIMEOUT;
+    }
+    jd.inner_its += s2.pcg_steps;
+    jd.n_matvec += (int64_t)(s2.pcg_steps + 1) * nact;
+    if (prof_on()) prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));
   }
+  for (int s = 0; s < S; ++s) jd.skip_h[s] = jd.state_h[s] != 0 ? 1 : 0;
   // make sure skip flags are cleared on the device for whatever comes next
-  cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, jd.st);
+  cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, st);
+  // the host copies of the residuals and Ritz values for the caller
+  cudaMemcpyAsync(jd.rn2_h.data(), jd.rn2, sizeof(double) * S * 64, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(jd.theta_h.data(), jd.theta, sizeof(double) * S * jd.z.mmax, cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
   m_out = m;
   return rc;
 }
@@ -513,7 +587,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     jd.pw = &pw;
     int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
-    const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
+    const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30, o.cuda_graph >= 0);
     if (status < 0 && status != LAP_ETIMEOUT) return status;
     finish(jd, P, status, outer, G, want_vecs, out, outa, d_out, d_best);
     if (cudaGetLastError() != cudaSuccess) { set_error("CUDA error after JD"); return LAP_ECUDA; }
@@ -531,7 +605,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
   int m_out = m;
   Params P1 = P;
-  int st1 = iterate(j1, m, P1, tol1, false, outer, m_out, 1e-10, 8);
+  int st1 = iterate(j1, m, P1, tol1, false, outer, m_out, 1e-10, 8, o.cuda_graph >= 0);
   if (st1 < 0 && st1 != LAP_ETIMEOUT) return st1;
   const int outer1 = outer;
   // ---- phase 2: FP64 basis and Rayleigh-Ritz, FP32 corrections
@@ -546,7 +620,8 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   j2.n_matvec = j1.n_matvec;
   j2.inner_its = j1.inner_its;
   m = j2.start(j2.V, z.ldv, mk, 0, 1e-20);
-  int status = (st1 == LAP_ETIMEOUT) ? LAP_ETIMEOUT : iterate(j2, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30);
+  int status = (st1 == LAP_ETIMEOUT) ? LAP_ETIMEOUT : iterate(j2, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30,
+                                                                o.cuda_graph >= 0);
   if (status < 0 && status != LAP_ETIMEOUT) return status;
   finish(j2, P, status, outer, G, want_vecs, out, outa, d_out, d_best);
   for (auto& in : out.info) in.phase1_outer = outer1;

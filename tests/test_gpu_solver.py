@@ -154,3 +154,22 @@ def test_degenerate_warm_start(pkg, precision):
     assert info["status"] == 0, info
     ev_ref, V_ref = dense.smallest_eigpairs(g, k + 8)
     check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cuda_graph_replay_matches_eager(pkg, precision):
+    """The outer iteration replayed as a captured CUDA graph gives the same
+    pairs as the kernel-by-kernel path (single graph and a batch)."""
+    g = G.workload_graph("c1")
+    ev_g, V_g, info_g = pkg.lap_eigs(g, 8, tol=1e-8, precision=precision, cuda_graph=True)
+    ev_e, V_e, info_e = pkg.lap_eigs(g, 8, tol=1e-8, precision=precision, cuda_graph=False)
+    assert info_g["status"] == 0 and info_e["status"] == 0
+    ev_ref, V_ref = dense.smallest_eigpairs(g, 16)
+    check_eigpairs(g, ev_g, V_g, ev_ref, V_ref, k=8)
+    assert np.allclose(ev_g, ev_e, rtol=1e-9)
+    gs = [G.ba_graph(700, 3, 41), G.grid_graph(21, 30), G.chung_lu(2500, 2.4, 5.0, 42)]
+    evs, Vs, infos = pkg.lap_eigs_batched(gs, 6, tol=1e-8, precision=precision, cuda_graph=True)
+    for x, ev, V, info in zip(gs, evs, Vs, infos):
+        assert info["status"] == 0, info
+        ev_ref, V_ref = dense.smallest_eigpairs(x, 14)
+        check_eigpairs(x, ev, V, ev_ref, V_ref, k=6)
