@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="autotune the SpMM schedule before timing")
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="enqueue each outer iteration kernel by kernel instead of replaying a captured CUDA graph")
     ap.add_argument("--ncu-window", action="store_true",
                     help="bracket only the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off); "
                          "skips the profiled pass, e2e and the CPU leg")
@@ -189,7 +191,7 @@ def bench_ours(args):
         tuned = {"team": t_[0].value, "hub_threshold": t_[1].value}
     evecs = torch.empty(n * k, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    opts = dict(precision=args.precision, stream=sp)
+    opts = dict(precision=args.precision, stream=sp, cuda_graph=not args.no_graph)
     gnn_params = None
     if args.warm == "gnn":
         from paper_1311_1695_gb300 import gnn as gnn_mod
@@ -340,7 +342,8 @@ def bench_ours(args):
         "config": {"workload": args.workload, "graph": WORKLOAD_TEXT[args.workload], "n": n, "nnz": nnz_total,
                    "graphs": len(graphs),
                    "k": k, "tol": 1e-8, "precision": args.precision, "method": "block Jacobi-Davidson",
-                   "l2": "flushed before each step (256 MiB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed before each step (256 MiB write)", "parallelism": f"replicas x{world}",
+                   "outer_iteration": "eager" if args.no_graph else "CUDA graph replay"},
         "result": {"outer_its": inf["outer_its"], "phase1_outer": inf["phase1_outer"], "n_matvec": inf["n_matvec"],
                    "max_rel_residual": max(i_["max_rel_residual"] for i_ in infos_all),
                    "lambda_2": float(ev[0][0]), "lambda_k+1": float(ev[0][k - 1]),
