@@ -185,9 +185,10 @@ __device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], 
     int v, cc;
     if (o < nout) { v = o / b; cc = o - v * b; }
     else { v = BMAX + 1 + (o - nout) / b; cc = (o - nout) % b; }
-    double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += (double)red[(w * NV + v) * BWL + cc];
-    if (t != 0.0) atomicAdd(accs + o, t);
+    T t = T(0);
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += red[(w * NV + v) * BWL + cc];
+    if (t != T(0)) atomicAdd(accs + o, (double)t);
   }
   __syncthreads();
 }
@@ -207,8 +208,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   T* red = reinterpret_cast<T*>(smem_raw);                          // [warps][BMAX+3][BWL]
   T* xs = red + kWarps * (BMAX + 3) * BWL;                          // [max(1, xres)][kTileRows][BMAX]
   T* accA = xs + (size_t)(f.xres > 1 ? f.xres : 1) * kTileRows * BMAX;  // [kTileRows][BMAX]
-  int* s_rp = reinterpret_cast<int*>(accA + kTileRows * BMAX);      // [kTileRows + 1]
-  int* s_erp = s_rp + kTileRows + 1;                                // [kTileRows + 1]
+  const int nslots = f.xres > 1 ? f.xres : 1;
+  int* s_rp0 = reinterpret_cast<int*>(accA + kTileRows * BMAX);     // [nslots][kTileRows + 1]
+  int* s_erp0 = s_rp0 + nslots * (kTileRows + 1);                   // [nslots][kTileRows + 1]
   constexpr int kRU = RowsInFlight<T, BMAX>::v;
   constexpr int RW = 32 / BWL;        // rows per warp pass
   constexpr int SLOTS = kWarps * RW;  // row groups per CTA
@@ -229,10 +231,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
   T Gc[BMAX + 1];
   auto owner = [&](const Tile& t) { return t.idx_in_seg == 0; };
+  // G[0] (the ones row) is a sum: scaled by 1/n_s to the mean; all in T
+  // (FP64 issues ~60x slower on GB300)
   auto load_G = [&](const double* A, int seg) {
-    const double inv_n = 1.0 / (double)seg_rows(g, seg);
 #pragma unroll
-    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)(__ldcg(A + i * b + c) * (i == 0 ? inv_n : 1.0)) : T(0);
+    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)__ldcg(A + i * b + c) : T(0);
+    Gc[0] *= T(1) / (T)seg_rows(g, seg);
   };
   // X rows of the k-th tile of this CTA: resident slot k, or the one
   // staging buffer refilled per tile and phase
@@ -248,6 +252,10 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
     for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
       const Tile t = g.tiles[ti];
       stage_x<T, BMAX>(xs + (size_t)k * kTileRows * BMAX, X, f.ldx, t.r0, t.r1 - t.r0, b);
+      for (int i = threadIdx.x; i <= t.r1 - t.r0; i += kThreads) {
+        s_rp0[k * (kTileRows + 1) + i] = g.rowptr[t.r0 + i];
+        s_erp0[k * (kTileRows + 1) + i] = g.erp[t.r0 + i];
+      }
     }
     __syncthreads();
   }
@@ -347,13 +355,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         }
         const int nrows = t.r1 - t.r0;
         const T* xt = f.xres ? xs + (size_t)k * kTileRows * BMAX : xs;
-        __syncthreads();
-        if (!f.xres) stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
-        for (int i = threadIdx.x; i <= nrows; i += kThreads) {
-          s_rp[i] = g.rowptr[t.r0 + i];
-          s_erp[i] = g.erp[t.r0 + i];
+        const int* s_rp = f.xres ? s_rp0 + k * (kTileRows + 1) : s_rp0;
+        const int* s_erp = f.xres ? s_erp0 + k * (kTileRows + 1) : s_erp0;
+        if (!f.xres) {
+          __syncthreads();
+          stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
+          for (int i = threadIdx.x; i <= nrows; i += kThreads) {
+            s_rp0[i] = g.rowptr[t.r0 + i];
+            s_erp0[i] = g.erp[t.r0 + i];
+          }
+          __syncthreads();
+        } else if (k > 0) {
+          __syncthreads();  // the previous tile's epilogue is done with accA
         }
-        __syncthreads();
         // merge-path walk over the tile's ordinary nonzeros
         const int E0 = s_erp[0], E = s_erp[nrows] - E0;
         const int es = E0 + (int)((long long)E * grp / SLOTS);
@@ -625,7 +639,8 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   constexpr int BWL = BMAX <= 4 ? 4 : (BMAX > 16 ? 32 : BMAX);  // lanes per row
   auto kern = k_pcg_fused<T, BMAX, BWL>;
   const size_t tile_x = sizeof(T) * (size_t)kTileRows * BMAX;
-  const size_t base = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL) + 2 * tile_x + sizeof(int) * 2 * (kTileRows + 1);
+  const size_t tile_rp = sizeof(int) * 2 * (kTileRows + 1);
+  const size_t base = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL) + 2 * tile_x + tile_rp;
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -646,7 +661,7 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   if (tiles_per_cta == 1) {
     xres = 1;
   } else if (tiles_per_cta <= 8) {
-    const size_t smem2 = base + (tiles_per_cta - 1) * tile_x;
+    const size_t smem2 = base + (tiles_per_cta - 1) * (tile_x + tile_rp);
     const int per_sm1 = per_sm;
     const int grid2 = grid_for(smem2);
     if (per_sm >= per_sm1 && smem2 <= 200 * 1024 && (g.ntiles + grid2 - 1) / grid2 <= tiles_per_cta) {
