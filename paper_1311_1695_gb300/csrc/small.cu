@@ -72,13 +72,14 @@ __global__ void k_and(int count, int* a, const int* b) {
 __global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
                            const double* __restrict__ norm1, const double* __restrict__ tol_abs, int k, int b,
                            int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-                           JdStatus* status) {
+                           JdStatus* status, double* segw) {
   __shared__ double s_w[256];
   __shared__ int s_c[256], s_bad[256], s_act[256], s_open[256];
   double worst = 0.0;
   int cand = 0, bad = 0, nact = 0, open = 0;
   for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
     int st = state[s];
+    double ws = 0.0;
     if (st != 1) {
       bool segc = true;
       int na = 0;
@@ -88,7 +89,7 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
         const bool c = r <= tol_abs[s] && theta[(size_t)s * mmax + j] <= norm1[s];
         if (j < k) {
           segc = segc && c;
-          worst = fmax(worst, r / tol_abs[s]);
+          ws = fmax(ws, r / tol_abs[s]);
         }
         const int a = (j < k && c) ? 0 : 1;
         active[(size_t)s * 64 + j] = a;
@@ -98,6 +99,8 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
       state[s] = st;
       if (st == 0) nact += na;
     }
+    segw[s] = ws;
+    worst = fmax(worst, ws);
     skip[s] = st != 0 ? 1 : 0;
     cand += st == 2;
     open += st != 1;
@@ -180,10 +183,10 @@ void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg
 }
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
               int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-              JdStatus* status, cudaStream_t s) {
+              JdStatus* status, double* segw, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
   k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, b, explicit_check, state, active, skip, bar,
-                               status);
+                               status, segw);
 }
 void and_flags(int count, int* a, const int* b, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);

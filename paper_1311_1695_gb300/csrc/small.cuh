@@ -27,9 +27,10 @@ struct JdStatus {
   int pcg_err;       // grid-barrier error flag of the last correction solve
   int pcg_steps;     // its PCG steps
 };
+// segw[s]: graph s's worst ||r_j|| / tol_abs over j < k (0 once converged).
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
               int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-              JdStatus* status, cudaStream_t s);
+              JdStatus* status, double* segw, cudaStream_t s);
 // best: device scratch of 2 * nseg * k 64-bit words.
 template <typename T>
 void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s);

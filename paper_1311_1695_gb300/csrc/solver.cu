@@ -101,6 +101,8 @@ struct JD {
   JdStatus* status_d = nullptr;
   JdStatus* status_h = nullptr;  // pinned
   int* state_h = nullptr;        // pinned [S]
+  double* segw = nullptr;        // [S] per-graph worst residual / tol
+  double* segw_h = nullptr;      // pinned [S]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_m = 0;  // basis size after a replayed iteration
@@ -111,6 +113,7 @@ struct JD {
     if (graph) cudaGraphDestroy(graph);
     if (status_h) cudaFreeHost(status_h);
     if (state_h) cudaFreeHost(state_h);
+    if (segw_h) cudaFreeHost(segw_h);
   }
   JD(const JD&) = delete;
   JD& operator=(const JD&) = delete;
@@ -128,7 +131,7 @@ struct JD {
     for (int i = 0; i < 5; ++i) add(S * 64 * 4);
     for (int i = 0; i < 5; ++i) add(S * 64 * 8);
     add(S * 33 * 32 * 8); add(S * 33 * 32 * 8); add(S * 64 * 4);
-    add(S * 4); add(S * 8); add(sizeof(JdStatus));
+    add(S * 4); add(S * 8); add(sizeof(JdStatus)); add(S * 8);
     return b + 4096;
   }
 
@@ -174,6 +177,8 @@ struct JD {
     status_d = a.take<JdStatus>(1);
     if (cudaMallocHost(reinterpret_cast<void**>(&status_h), sizeof(JdStatus)) != cudaSuccess) status_h = nullptr;
     if (cudaMallocHost(reinterpret_cast<void**>(&state_h), sizeof(int) * S) != cudaSuccess) state_h = nullptr;
+    segw = a.take<double>(S);
+    if (cudaMallocHost(reinterpret_cast<void**>(&segw_h), sizeof(double) * S) != cudaSuccess) segw_h = nullptr;
     rn2_h.assign(S * 64, 0.0);
     theta_h.assign(S * z.mmax, 0.0);
     active_h.assign(S * 64, 1);
@@ -252,9 +257,10 @@ struct JD {
     const int mk = rayleigh_ritz(m);
     residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
     converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, z.b, explicit_check ? 1 : 0, state, active, seg_skip,
-             pw->bar, status_d, st);
+             pw->bar, status_d, segw, st);
     cudaMemcpyAsync(status_h, status_d, sizeof(JdStatus), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(state_h, state, sizeof(int) * z.nseg, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(segw_h, segw, sizeof(double) * z.nseg, cudaMemcpyDeviceToHost, st);
     return mk;
   }
 
@@ -333,7 +339,12 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
             int& outer, int& m_out, double drop1, int stall_limit, bool use_graph) {
   const int S = jd.z.nseg;
   cudaStream_t st = jd.st;
-  if (!jd.status_h || !jd.state_h) { set_error("pinned host allocation failed"); return LAP_ENOMEM; }
+  if (!jd.status_h || !jd.state_h || !jd.segw_h) { set_error("pinned host allocation failed"); return LAP_ENOMEM; }
+  // per-graph stagnation: the loop gives up (stall_limit) only when every
+  // open graph has failed to halve its worst residual for stall_limit
+  // iterations, so one slow graph of a batch does not end the others' phase
+  std::vector<double> best_s(S, 1e300);
+  std::vector<int> stall_s(S, 0);
   std::fill(jd.skip_h.begin(), jd.skip_h.end(), 0);
   cudaMemsetAsync(jd.state, 0, sizeof(int) * S, st);
   cudaMemsetAsync(jd.seg_skip, 0, sizeof(int) * S * 64, st);
@@ -381,11 +392,17 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     }
     if (all) { rc = LAP_OK; break; }
     const double worst = stt.worst;
-    if (worst < 0.5 * best) { best = worst; stall = 0; stag = 0; }
-    else {
-      if (++stall >= stall_limit) { rc = LAP_ENOCONV; break; }
-      if (++stag >= 20) { jd.inject = true; stag = 0; }
+    if (worst < 0.5 * best) { best = worst; stag = 0; }
+    else if (++stag >= 20) { jd.inject = true; stag = 0; }
+    bool all_stalled = true;
+    for (int s = 0; s < S; ++s) {
+      if (jd.state_h[s] == 1) continue;
+      if (jd.segw_h[s] < 0.5 * best_s[s]) { best_s[s] = jd.segw_h[s]; stall_s[s] = 0; }
+      else ++stall_s[s];
+      all_stalled = all_stalled && stall_s[s] >= stall_limit;
     }
+    (void)stall;
+    if (all_stalled) { rc = LAP_ENOCONV; break; }
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - P.t0).count();
     if (P.max_seconds > 0 && el > P.max_seconds) { set_error("time limit reached"); rc = LAP_ETIMEOUT; break; }
     if (outer >= P.max_outer) { rc = LAP_ENOCONV; break; }
