@@ -512,12 +512,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           const double* A1 = f.acc1 + (size_t)t.seg * stride1;
           load_G(A1, t.seg);
           al = T(0);
-          if (colok) {
+          if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const double pq = __ldcg(A1 + nout + c);
-            const double rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
+            const T pq = (T)__ldcg(A1 + nout + c);
+            const T rho = (T)__ldcg(f.rho + (size_t)par * f.state_stride + k);
             const int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            if (!dn && pq != 0.0 && isfinite(pq)) al = (T)(rho / pq);
+            if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
           }
         }
         const T* xt = stage(t, k);
@@ -568,18 +568,18 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           const double* A2 = f.acc2 + (size_t)t.seg * stride1;
           load_G(A2, t.seg);
           be = T(0);
-          if (colok) {
+          if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const double rho_new = __ldcg(A2 + nout + c);
-            const double rn = sqrt(__ldcg(A2 + nout + b + c));
-            const double rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
+            const T rho_new = (T)__ldcg(A2 + nout + c);
+            const T rn = sqrt((T)__ldcg(A2 + nout + b + c));
+            const T rho = (T)__ldcg(f.rho + (size_t)par * f.state_stride + k);
             int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            double bb = 0.0;
+            T bb = T(0);
             if (!dn) {
-              if (rho != 0.0 && isfinite(rho_new)) bb = rho_new / rho;
-              if (!(rn > f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
+              if (rho != T(0) && isfinite(rho_new)) bb = rho_new / rho;
+              if (!(rn > (T)f.delta * (T)__ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
             }
-            be = (T)bb;
+            be = bb;
             if (owner(t) && threadIdx.x < BWL) {
               f.rho[(size_t)(par ^ 1) * f.state_stride + k] = rho_new;
               f.done[(size_t)(par ^ 1) * f.state_stride + k] = dn;
@@ -595,9 +595,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           int mine = 1;
           if (threadIdx.x < b) {
             const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-            const double rn = sqrt(__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
+            const T rn = sqrt((T)__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
             const int d0 = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            mine = d0 || !(rn > f.delta * __ldcg(f.res0 + k)) || !isfinite(rn);
+            mine = d0 || !(rn > (T)f.delta * (T)__ldcg(f.res0 + k)) || !isfinite(rn);
           }
           s_all = __syncthreads_and(mine);
           all_known = 1;

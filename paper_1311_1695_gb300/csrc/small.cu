@@ -68,50 +68,55 @@ __global__ void k_and(int count, int* a, const int* b) {
   if (i < count) a[i] = (a[i] != 0 && b[i] != 0) ? 1 : 0;
 }
 
-// One CTA walks the graphs (thread per graph), then reduces in a fixed order.
+// One CTA; a warp per graph (lane j = column j, b <= 32), warp reductions,
+// then a fixed-order reduction over the warps.
 __global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
                            const double* __restrict__ norm1, const double* __restrict__ tol_abs, int k, int b,
                            int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
                            JdStatus* status, double* segw) {
-  __shared__ double s_w[256];
-  __shared__ int s_c[256], s_bad[256], s_act[256], s_open[256];
+  constexpr int NW = 8;
+  __shared__ double s_w[NW];
+  __shared__ int s_c[NW], s_bad[NW], s_act[NW], s_open[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double worst = 0.0;
   int cand = 0, bad = 0, nact = 0, open = 0;
-  for (int s = threadIdx.x; s < nseg; s += blockDim.x) {
+  for (int s = warp; s < nseg; s += NW) {
     int st = state[s];
     double ws = 0.0;
     if (st != 1) {
-      bool segc = true;
-      int na = 0;
-      for (int j = 0; j < b; ++j) {
+      const int j = lane;
+      bool c = true, fin = true;
+      double ratio = 0.0;
+      if (j < b) {
         const double r = sqrt(fmax(0.0, rn2[(size_t)s * 64 + j]));
-        if (!isfinite(r)) bad = 1;
-        const bool c = r <= tol_abs[s] && theta[(size_t)s * mmax + j] <= norm1[s];
-        if (j < k) {
-          segc = segc && c;
-          ws = fmax(ws, r / tol_abs[s]);
-        }
-        const int a = (j < k && c) ? 0 : 1;
-        active[(size_t)s * 64 + j] = a;
-        na += a;
+        fin = isfinite(r);
+        c = r <= tol_abs[s] && theta[(size_t)s * mmax + j] <= norm1[s];
+        ratio = j < k ? r / tol_abs[s] : 0.0;
+        active[(size_t)s * 64 + j] = (j < k && c) ? 0 : 1;
       }
+      const bool segc = __all_sync(0xffffffffu, j >= k || c);
+      bad |= !__all_sync(0xffffffffu, fin);
+      for (int o = 16; o > 0; o >>= 1) ratio = fmax(ratio, __shfl_xor_sync(0xffffffffu, ratio, o));
+      ws = ratio;
+      const int na = __popc(__ballot_sync(0xffffffffu, j < b && !(j < k && c)));
       st = segc ? (explicit_check ? 2 : 1) : 0;
-      state[s] = st;
       if (st == 0) nact += na;
     }
-    segw[s] = ws;
+    if (lane == 0) {
+      state[s] = st;
+      skip[s] = st != 0 ? 1 : 0;
+      segw[s] = ws;
+    }
     worst = fmax(worst, ws);
-    skip[s] = st != 0 ? 1 : 0;
     cand += st == 2;
     open += st != 1;
   }
-  s_w[threadIdx.x] = worst; s_c[threadIdx.x] = cand; s_bad[threadIdx.x] = bad;
-  s_act[threadIdx.x] = nact; s_open[threadIdx.x] = open;
+  if (lane == 0) { s_w[warp] = worst; s_c[warp] = cand; s_bad[warp] = bad; s_act[warp] = nact; s_open[warp] = open; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double w = 0.0;
     int c = 0, bd = 0, na = 0, op = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
+    for (int i = 0; i < NW; ++i) {
       w = fmax(w, s_w[i]); c += s_c[i]; bd |= s_bad[i]; na += s_act[i]; op += s_open[i];
     }
     status->worst = w;

@@ -163,19 +163,28 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
     if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
     return;
   }
+  // ordinary rows: the group loads up to BWL of the row's column indices in
+  // one coalesced load (lane u takes index u), then broadcasts them with
+  // shuffles, so all of the row's gathers are in flight together instead of
+  // an index load and a gather per nonzero in sequence
   const int row = ((blockIdx.x - nhb) * 8 + warp) * RW + lane / BWL;
-  if (row >= g.n) return;  // no cross-group shuffles below
+  if (row >= g.n) return;  // whole group (rows are group-uniform)
   const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-  if (p1 - p0 > g.long_thresh || !colok) return;
+  if (p1 - p0 > g.long_thresh) return;  // a hub: its chunks are done by the first blocks
+  const unsigned gmask = BWL == 32 ? 0xffffffffu : (((1u << BWL) - 1u) << (lane & ~(BWL - 1)));
   T a = T(0);
-  if (w) {
-#pragma unroll 4
-    for (int p = p0; p < p1; ++p) a += __ldg(w + p) * __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
-  } else {
-#pragma unroll 4
-    for (int p = p0; p < p1; ++p) a += __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
+  for (int q0 = p0; q0 < p1; q0 += BWL) {
+    const int cnt = min(BWL, p1 - q0);
+    const int myj = c < cnt ? __ldg(g.colidx + q0 + c) : 0;
+    const T myw = (w && c < cnt) ? __ldg(w + q0 + c) : T(1);
+#pragma unroll 8
+    for (int u = 0; u < cnt; ++u) {
+      const int j = __shfl_sync(gmask, myj, u, BWL);
+      const T wv = w ? __shfl_sync(gmask, myw, u, BWL) : T(1);
+      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+    }
   }
-  Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
+  if (colok) Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
 }
 
 template <typename T, int BWL>
