@@ -141,21 +141,10 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
     const int ch = blockIdx.x * 8 + warp;
     if (ch >= g.nchunk) return;  // whole warp
     const int4 cc = g.chunks[ch];
-    T a = T(0);
-    if (w) {
-#pragma unroll 8
-      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
-        const int j = __ldg(g.colidx + p);
-        const T wv = __ldg(w + p);
-        if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
-      }
-    } else {
-#pragma unroll 8
-      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
-        const int j = __ldg(g.colidx + p);
-        if (colok) a += __ldg(X + (size_t)j * ldx + c);
-      }
-    }
+    // the warp's RW row groups take contiguous parts of the chunk
+    const int gi = lane / BWL, len = cc.z - cc.y;
+    T a = gather_range<T, BWL, false>(g.colidx, w, X, ldx, c, colok, cc.y + len * gi / RW,
+                                      cc.y + len * (gi + 1) / RW);
 #pragma unroll
     for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (!hub_finish<T>(g, ch, cc, a, b)) return;
@@ -167,24 +156,18 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
   // one coalesced load (lane u takes index u), then broadcasts them with
   // shuffles, so all of the row's gathers are in flight together instead of
   // an index load and a gather per nonzero in sequence
+  // (every lane takes part in the gathers' shuffles; rows past n and hub
+  // rows, done by their chunks, have empty ranges)
   const int row = ((blockIdx.x - nhb) * 8 + warp) * RW + lane / BWL;
-  if (row >= g.n) return;  // whole group (rows are group-uniform)
-  const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
-  if (p1 - p0 > g.long_thresh) return;  // a hub: its chunks are done by the first blocks
-  const unsigned gmask = BWL == 32 ? 0xffffffffu : (((1u << BWL) - 1u) << (lane & ~(BWL - 1)));
-  T a = T(0);
-  for (int q0 = p0; q0 < p1; q0 += BWL) {
-    const int cnt = min(BWL, p1 - q0);
-    const int myj = c < cnt ? __ldg(g.colidx + q0 + c) : 0;
-    const T myw = (w && c < cnt) ? __ldg(w + q0 + c) : T(1);
-#pragma unroll 8
-    for (int u = 0; u < cnt; ++u) {
-      const int j = __shfl_sync(gmask, myj, u, BWL);
-      const T wv = w ? __shfl_sync(gmask, myw, u, BWL) : T(1);
-      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
-    }
+  int p0 = 0, p1 = 0;
+  if (row < g.n) {
+    p0 = g.rowptr[row];
+    p1 = g.rowptr[row + 1];
   }
-  if (colok) Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
+  const bool mine = row < g.n && p1 - p0 <= g.long_thresh;
+  if (!mine) p1 = p0;
+  const T a = gather_range<T, BWL, false>(g.colidx, w, X, ldx, c, colok, p0, p1);
+  if (mine && colok) Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
 }
 
 template <typename T, int BWL>
