@@ -291,6 +291,9 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
   __syncthreads();
   if (threadIdx.x < q) d0[threadIdx.x] = absolute ? 1.0 : S[threadIdx.x][threadIdx.x];
   __syncthreads();
+  // FP64 divisions and square roots are long dependent sequences on GB300:
+  // one reciprocal per pivot (kept in rinv) and multiplications elsewhere
+  __shared__ double rinv[kMaxCols];
   for (int j = 0; j < q; ++j) {
     __shared__ double rjj;
     if (threadIdx.x == 0) {
@@ -298,10 +301,12 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
       const bool ok = d0[j] > 0.0 && piv > drop * d0[j] && isfinite(piv);
       kp[j] = ok ? 1 : 0;
       rjj = ok ? sqrt(piv) : 0.0;
+      rinv[j] = ok ? 1.0 / rjj : 0.0;
     }
     __syncthreads();
     const bool ok = kp[j] != 0;
-    for (int i = j + threadIdx.x; i < q; i += blockDim.x) S[j][i] = ok ? (i == j ? rjj : S[j][i] / rjj) : 0.0;
+    const double ri = rinv[j];
+    for (int i = j + threadIdx.x; i < q; i += blockDim.x) S[j][i] = ok ? (i == j ? rjj : S[j][i] * ri) : 0.0;
     __syncthreads();
     if (ok) {
       const int m = q - j - 1;
@@ -323,7 +328,7 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
       if (!kp[i]) { x[i] = 0.0; continue; }
       double s = (i == c) ? 1.0 : 0.0;
       for (int l = i + 1; l <= c; ++l) s -= S[i][l] * x[l];
-      x[i] = s / S[i][i];
+      x[i] = s * rinv[i];
     }
     for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = x[i];
   }

@@ -65,7 +65,7 @@ struct DevGraph {
   double* hub_part;      // [nchunk * kPartStride]
 };
 
-constexpr int kHubChunk = 64;
+constexpr int kHubChunk = 128;
 constexpr int kPartStride = kMaxCols + 1;
 
 // Host-side mirror kept next to the device arrays.

@@ -25,9 +25,8 @@
 // y - [1|X] G and the Gram terms [1|X]^T z read x_i as broadcast vector
 // loads with no per-column predicate.  Phase A balances the SpMM inside a
 // tile merge-path style: the tile's nonzeros (hub rows excluded, see below)
-// are cut into equal ranges, one per row group; a group walks its range in
-// rounds of BWL entries (indices loaded cooperatively, BWL gathers in flight)
-// and adds each finished (or cut) row into a
+// are cut into equal ranges, one per row group; a group walks its range with
+// U independent gathers in flight and adds each finished (or cut) row into a
 // shared-memory row accumulator; after a CTA barrier the rows' epilogue
 // (q~ = d p - A p - theta p, the Gram terms) runs row by row.  Hub rows
 // (degree > long_thresh) are cut into chunks of kHubChunk nonzeros spread
@@ -54,6 +53,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kU = 8;   // gathers in flight per row group in the merge-path walk
 // rows whose loads a row group issues together (fewer for the register-heavy
 // instantiations, which would spill)
 template <typename T, int BMAX> struct RowsInFlight { static constexpr int v = (sizeof(T) == 8 || BMAX >= 32) ? 2 : 4; };
@@ -372,54 +372,57 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         const int E0 = s_erp[0], E = s_erp[nrows] - E0;
         const int es = E0 + (int)((long long)E * grp / SLOTS);
         const int ee = E0 + (int)((long long)E * (grp + 1) / SLOTS);
-        // the group's current row: the last row i with s_erp[i] <= es
-        int i = 0;
         if (es < ee) {
-          int lo = 0, hi = nrows - 1;
+          int lo = 0, hi = nrows - 1;  // last row i with s_erp[i] <= es
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_erp[mid] <= es) lo = mid; else hi = mid - 1;
           }
-          i = lo;
-        }
-        // rounds of BWL entries: lane u finds the row of entry e0 + u (a short
-        // walk from the current row in shared memory) and loads its column
-        // index, then the group broadcasts index and row with shuffles, so
-        // BWL gathers are in flight per round; trip counts are the warp's
-        // maxima (no divergence around the shuffles)
-        T a = T(0);
-        const int rounds = __reduce_max_sync(0xffffffffu, (ee - es + BWL - 1) / BWL);
-        for (int r = 0; r < rounds; ++r) {
-          const int e0 = es + r * BWL;
-          const int cnt = max(0, min(BWL, ee - e0));
-          int myrow = i, myj = 0;
-          T myw = T(1);
-          if (c < cnt) {
-            const int e = e0 + c;
+          int i = lo;
+          int nx = s_erp[i + 1];
+          int pb = s_rp[i] - s_erp[i];  // p = pb + e inside row i
+          T a = T(0);
+          for (int e0 = es; e0 < ee; e0 += kU) {
+            int pu[kU], iu[kU];
             int ii = i;
-            while (s_erp[ii + 1] <= e) ++ii;  // hub rows have zero length
-            myrow = ii;
-            const int pe = s_rp[ii] + (e - s_erp[ii]);
-            myj = __ldg(g.colidx + pe);
-            if (w) myw = __ldg(w + pe);
-          }
-          const int umax = __reduce_max_sync(0xffffffffu, cnt);
-#pragma unroll 8
-          for (int u = 0; u < umax; ++u) {
-            const int j = __shfl_sync(0xffffffffu, myj, u, BWL);
-            const int ru = __shfl_sync(0xffffffffu, myrow, u, BWL);
-            const T wv = w ? __shfl_sync(0xffffffffu, myw, u, BWL) : T(1);
-            if (u < cnt) {
-              if (ru != i) {
-                if (colok) atomicAdd(accA + i * BMAX + c, a);
-                a = T(0);
-                i = ru;
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              const int e = e0 + u;
+              pu[u] = -1;
+              iu[u] = ii;
+              if (e < ee) {
+                while (e >= nx) {
+                  ++ii;
+                  nx = s_erp[ii + 1];
+                  pb = s_rp[ii] - s_erp[ii];
+                }
+                pu[u] = pb + e;
+                iu[u] = ii;
               }
-              if (colok) a += wv * __ldcg(f.P + (size_t)j * ld + c);
+            }
+            T v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              v[u] = T(0);
+              if (pu[u] >= 0 && colok) {
+                const T x = __ldcg(f.P + (size_t)__ldg(g.colidx + pu[u]) * ld + c);
+                v[u] = w ? __ldg(w + pu[u]) * x : x;
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+              if (pu[u] >= 0) {
+                if (iu[u] != i) {
+                  if (colok) atomicAdd(accA + i * BMAX + c, a);
+                  a = T(0);
+                  i = iu[u];
+                }
+                a += v[u];
+              }
             }
           }
+          if (colok) atomicAdd(accA + i * BMAX + c, a);
         }
-        if (es < ee && colok) atomicAdd(accA + i * BMAX + c, a);
         __syncthreads();
         // row epilogue: q~ = d p - (A p) - theta p; the Gram terms
         if (colok) {
@@ -457,10 +460,17 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         const int row = cc.x;
         const int seg = f.hub_seg[cc.w];
         if (f.seg_skip && f.seg_skip[seg]) continue;  // whole warp
-        // the warp's RW row groups take contiguous parts of the chunk
-        const int gi = lane / BWL, len = cc.z - cc.y;
-        T a = gather_range<T, BWL, true>(g.colidx, w, f.P, ld, c, colok, cc.y + len * gi / RW,
-                                         cc.y + len * (gi + 1) / RW);
+        T a = T(0);
+        if (colok) {
+          if (w) {
+#pragma unroll 8
+            for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
+              a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          } else {
+#pragma unroll 8
+            for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          }
+        }
 #pragma unroll
         for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         if (!hub_finish<T>(g, ch, cc, a, b)) continue;

@@ -141,10 +141,21 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
     const int ch = blockIdx.x * 8 + warp;
     if (ch >= g.nchunk) return;  // whole warp
     const int4 cc = g.chunks[ch];
-    // the warp's RW row groups take contiguous parts of the chunk
-    const int gi = lane / BWL, len = cc.z - cc.y;
-    T a = gather_range<T, BWL, false>(g.colidx, w, X, ldx, c, colok, cc.y + len * gi / RW,
-                                      cc.y + len * (gi + 1) / RW);
+    T a = T(0);
+    if (w) {
+#pragma unroll 8
+      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+        const int j = __ldg(g.colidx + p);
+        const T wv = __ldg(w + p);
+        if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+      }
+    } else {
+#pragma unroll 8
+      for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+        const int j = __ldg(g.colidx + p);
+        if (colok) a += __ldg(X + (size_t)j * ldx + c);
+      }
+    }
 #pragma unroll
     for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
     if (!hub_finish<T>(g, ch, cc, a, b)) return;
@@ -152,22 +163,19 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
     if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
     return;
   }
-  // ordinary rows: the group loads up to BWL of the row's column indices in
-  // one coalesced load (lane u takes index u), then broadcasts them with
-  // shuffles, so all of the row's gathers are in flight together instead of
-  // an index load and a gather per nonzero in sequence
-  // (every lane takes part in the gathers' shuffles; rows past n and hub
-  // rows, done by their chunks, have empty ranges)
   const int row = ((blockIdx.x - nhb) * 8 + warp) * RW + lane / BWL;
-  int p0 = 0, p1 = 0;
-  if (row < g.n) {
-    p0 = g.rowptr[row];
-    p1 = g.rowptr[row + 1];
+  if (row >= g.n) return;  // no cross-group shuffles below
+  const int p0 = g.rowptr[row], p1 = g.rowptr[row + 1];
+  if (p1 - p0 > g.long_thresh || !colok) return;
+  T a = T(0);
+  if (w) {
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) a += __ldg(w + p) * __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
+  } else {
+#pragma unroll 4
+    for (int p = p0; p < p1; ++p) a += __ldg(X + (size_t)__ldg(g.colidx + p) * ldx + c);
   }
-  const bool mine = row < g.n && p1 - p0 <= g.long_thresh;
-  if (!mine) p1 = p0;
-  const T a = gather_range<T, BWL, false>(g.colidx, w, X, ldx, c, colok, p0, p1);
-  if (mine && colok) Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
+  Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
 }
 
 template <typename T, int BWL>
