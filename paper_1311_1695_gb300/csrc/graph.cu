@@ -3,6 +3,8 @@
 // generalised degrees, ||L||_1 per graph, row tiles, and the SpMM schedule
 // (lanes per row and the list of hub rows).
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 
@@ -177,30 +179,50 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   g->avg_degree = ntot ? (double)nnztot / (double)ntot : 0.0;
   g->max_degree = maxdeg;
 
-  // tiles: small enough that every SM holds several CTAs; cut at `rows`
-  // rows or at twice the mean work of such a tile (row lengths capped at 64,
-  // the default hub threshold), so tiles carry similar SpMM work
+  // tiles: every phase of the persistent correction solve ends at a grid
+  // barrier, so the CTAs must get equal work.  A row costs its SpMM work (row
+  // length capped at 64, the default hub threshold: longer rows are spread
+  // over all warps as chunks) plus 8 for the row-wise phases.  A graph of
+  // more than 4,096 rows is cut into a multiple of 304 (= 2 CTAs x 152 SMs)
+  // tiles of equal cost (at most 256 rows each); a smaller graph (a batch
+  // member) into tiles of about 64 rows.
   std::vector<Tile> tiles;
   g->tile_ptr.assign(nb + 1, 0);
   for (int s = 0; s < nb; ++s) {
     g->tile_ptr[s] = (int)tiles.size();
-    const int ns = g->row0[s + 1] - g->row0[s];
-    int rows = (ns + 4 * 152 - 1) / (4 * 152);
-    rows = (rows + 31) / 32 * 32;
-    rows = std::max(64, std::min(rows, kTileRows));
-    int64_t work_s = 0;
-    for (int r = g->row0[s]; r < g->row0[s + 1]; ++r) work_s += std::min(g->rowptr_h[r + 1] - g->rowptr_h[r], 64);
-    const int64_t budget = std::max<int64_t>(64, 2 * work_s * rows / std::max(ns, 1));
-    int idx = 0, a = g->row0[s];
-    while (a < g->row0[s + 1]) {
-      int e = a;
-      int64_t w = 0;
-      while (e < g->row0[s + 1] && e - a < rows && (e == a || w < budget)) {
-        w += std::min(g->rowptr_h[e + 1] - g->rowptr_h[e], 64);
-        ++e;
+    const int a0 = g->row0[s], a1 = g->row0[s + 1], ns = a1 - a0;
+    auto cost = [&](int r) { return (int64_t)std::min(g->rowptr_h[r + 1] - g->rowptr_h[r], 64) + 8; };
+    int64_t total = 0;
+    for (int r = a0; r < a1; ++r) total += cost(r);
+    if (ns > 4096) {
+      // T tiles (a multiple of 304, with headroom so the row cap rarely
+      // binds), cut at the cost quantiles k * total / T
+      const int64_t want = (ns + kTileRows - 1) / kTileRows;
+      const int64_t T = std::max<int64_t>(1, (want * 5 / 4 + 303) / 304) * 304;
+      int idx = 0, a = a0;
+      int64_t cum = 0;
+      for (int64_t kq = 1; kq <= T && a < a1; ++kq) {
+        const int64_t goal = (kq == T) ? INT64_MAX : (total * kq + T - 1) / T;
+        int e = a;
+        while (e < a1 && e - a < kTileRows && (e == a || cum < goal)) cum += cost(e++);
+        tiles.push_back(Tile{s, a, e, idx++});
+        a = e;
       }
-      tiles.push_back(Tile{s, a, e, idx++});
-      a = e;
+      while (a < a1) {  // only if the row cap bound somewhere
+        const int e = std::min(a + kTileRows, a1);
+        tiles.push_back(Tile{s, a, e, idx++});
+        a = e;
+      }
+    } else {
+      const int64_t target = std::max<int64_t>(1, total * 64 / std::max(ns, 1));
+      int idx = 0, a = a0;
+      while (a < a1) {
+        int e = a;
+        int64_t w = 0;
+        while (e < a1 && e - a < kTileRows && (e == a || w < target)) w += cost(e++);
+        tiles.push_back(Tile{s, a, e, idx++});
+        a = e;
+      }
     }
   }
   g->tile_ptr[nb] = (int)tiles.size();
