@@ -182,10 +182,9 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   // tiles: every phase of the persistent correction solve ends at a grid
   // barrier, so the CTAs must get equal work.  A row costs its SpMM work (row
   // length capped at 64, the default hub threshold: longer rows are spread
-  // over all warps as chunks) plus 8 for the row-wise phases.  A graph of
-  // more than 4,096 rows is cut into a multiple of 304 (= 2 CTAs x 152 SMs)
-  // tiles of equal cost (at most 256 rows each); a smaller graph (a batch
-  // member) into tiles of about 64 rows.
+  // over all warps as chunks) plus 8 for the row-wise phases.  A single graph
+  // of more than 4,096 rows is cut into a multiple of 304 (= 2 CTAs x 152
+  // SMs) tiles of equal cost (at most 256 rows each).
   std::vector<Tile> tiles;
   g->tile_ptr.assign(nb + 1, 0);
   for (int s = 0; s < nb; ++s) {
@@ -194,7 +193,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
     auto cost = [&](int r) { return (int64_t)std::min(g->rowptr_h[r + 1] - g->rowptr_h[r], 64) + 8; };
     int64_t total = 0;
     for (int r = a0; r < a1; ++r) total += cost(r);
-    if (ns > 4096) {
+    if (nb == 1 && ns > 4096) {
       // T tiles (a multiple of 304, with headroom so the row cap rarely
       // binds), cut at the cost quantiles k * total / T
       const int64_t want = (ns + kTileRows - 1) / kTileRows;
@@ -214,12 +213,16 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
         a = e;
       }
     } else {
-      const int64_t target = std::max<int64_t>(1, total * 64 / std::max(ns, 1));
+      // a batch (many tiles per CTA) or a small graph: rows per tile from the
+      // graph size (several CTAs per SM), cut early at twice the mean cost
+      int rows = (ns + 4 * 152 - 1) / (4 * 152);
+      rows = std::max(64, std::min((rows + 31) / 32 * 32, kTileRows));
+      const int64_t budget = std::max<int64_t>(64, 2 * total * rows / std::max(ns, 1));
       int idx = 0, a = a0;
       while (a < a1) {
         int e = a;
         int64_t w = 0;
-        while (e < a1 && e - a < kTileRows && (e == a || w < target)) w += cost(e++);
+        while (e < a1 && e - a < rows && (e == a || w < budget)) w += cost(e++);
         tiles.push_back(Tile{s, a, e, idx++});
         a = e;
       }
