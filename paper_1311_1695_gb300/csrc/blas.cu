@@ -1018,10 +1018,7 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
     cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  // up to 48 x 48: four warps (the sweeps are barrier-bound; fewer warps
-  // meet at each of the ~2 m barriers of a sweep faster)
-  const int threads = m <= 48 ? 128 : 256;
-  k_syev<<<nseg, threads, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out,
+  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out,
                                  nref < 0 ? -1 : (int)nr);
 }
 
