@@ -450,30 +450,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           }
         }
       }
-      // hub rows: chunks of at most kHubChunk nonzeros, one warp each,
-      // round-robin over all warps of the grid; the warp completing a hub
-      // (hub.cuh) writes its q~ row and adds its share of G1 and p.q~ (to
-      // the CTA's registers when the hub is in the CTA's current graph,
-      // else with atomics)
-      for (int ch = blockIdx.x * kWarps + warp; ch < g.nchunk; ch += gridDim.x * kWarps) {
-        const int4 cc = g.chunks[ch];
+      // hub rows: chunks of at most kHubChunk nonzeros.  The warp completing
+      // a hub (hub.cuh) writes its q~ row and adds its share of G1 and p.q~
+      // (to the CTA's registers when the hub is in the CTA's current graph,
+      // else with atomics); `a` is lane c's column sum (lanes < BWL).
+      auto finish_row = [&](const int4& cc, int seg, T a) {
         const int row = cc.x;
-        const int seg = f.hub_seg[cc.w];
-        if (f.seg_skip && f.seg_skip[seg]) continue;  // whole warp
-        T a = T(0);
-        if (colok) {
-          if (w) {
-#pragma unroll 8
-            for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
-              a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-          } else {
-#pragma unroll 8
-            for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-          }
-        }
-#pragma unroll
-        for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (!hub_finish<T>(g, ch, cc, a, b)) continue;
         const bool own = colok && lane < BWL;  // group 0 holds the row
         const T d = deg[row];
         const T pv = own ? __ldcg(f.P + (size_t)row * ld + c) : T(0);
@@ -494,6 +476,71 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
             atomicAdd(A1 + c, (double)q);
             atomicAdd(A1 + nout + c, (double)(pv * q));
           }
+        }
+      };
+      auto chunk_sum = [&](int q0, int q1) {  // lane c: sum over [q0, q1) of w P[col][c]
+        T a = T(0);
+        if (colok) {
+          if (w) {
+#pragma unroll 8
+            for (int p = q0; p < q1; ++p) a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          } else {
+#pragma unroll 8
+            for (int p = q0; p < q1; ++p) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+          }
+        }
+        return a;
+      };
+      if (g.nchunk <= (int)gridDim.x) {
+        // few chunks: one per CTA, split over all of the CTA's row groups
+        // (a chunk then costs a couple of gather rounds, not kHubChunk / RW)
+        const int ch = blockIdx.x;
+        bool doit = ch < g.nchunk;
+        int4 cc = make_int4(0, 0, 0, 0);
+        int seg = 0;
+        if (doit) {
+          cc = g.chunks[ch];
+          seg = f.hub_seg[cc.w];
+          doit = !(f.seg_skip && f.seg_skip[seg]);
+        }
+        if (doit) {  // CTA-uniform
+          const int len = cc.z - cc.y;
+          T a = chunk_sum(cc.y + (int)((long long)len * grp / SLOTS), cc.y + (int)((long long)len * (grp + 1) / SLOTS));
+#pragma unroll
+          for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          __syncthreads();
+          if (lane < BWL) red[warp * BWL + c] = a;
+          __syncthreads();
+          if (warp == 0) {
+            T sum = T(0);
+            if (lane < BWL)
+              for (int v = 0; v < kWarps; ++v) sum += red[v * BWL + c];
+            if (hub_finish<T>(g, ch, cc, sum, b)) finish_row(cc, seg, sum);
+          }
+          __syncthreads();
+        }
+      } else {
+        // many chunks: one warp each, round-robin over all warps of the grid;
+        // the warp's row groups take interleaved nonzeros
+        for (int ch = blockIdx.x * kWarps + warp; ch < g.nchunk; ch += gridDim.x * kWarps) {
+          const int4 cc = g.chunks[ch];
+          const int seg = f.hub_seg[cc.w];
+          if (f.seg_skip && f.seg_skip[seg]) continue;  // whole warp
+          T a = T(0);
+          if (colok) {
+            if (w) {
+#pragma unroll 8
+              for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
+                a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+            } else {
+#pragma unroll 8
+              for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
+            }
+          }
+#pragma unroll
+          for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+          if (!hub_finish<T>(g, ch, cc, a, b)) continue;
+          finish_row(cc, seg, a);
         }
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
