@@ -384,15 +384,20 @@ __device__ int jacobi2s(T* A, T* V, int LD, int mm, T rel, T abs_tol, int max_sw
   const int vi = tid % half, vr0 = tid / half;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int step = 0; step < mm - 1; ++step) {
+      int rot = 0;
       if (tid < half) {
         const short2 pq = pairs[step * half + tid];
         const int p = pq.x, q = pq.y;
         const T apq = A[p * LD + q], app = A[p * LD + p], aqq = A[q * LD + q];
         T c = T(1), sn = T(0), dp = app, dq = aqq;
-        if (fabs(apq) > abs_tol && fabs(apq) > rel * sqrt(fabs(app * aqq))) jacobi_rot(app, aqq, apq, c, sn, dp, dq);
+        if (fabs(apq) > abs_tol && fabs(apq) > rel * sqrt(fabs(app * aqq))) {
+          jacobi_rot(app, aqq, apq, c, sn, dp, dq);
+          rot = 1;
+        }
         cs[4 * tid] = c; cs[4 * tid + 1] = sn; cs[4 * tid + 2] = dp; cs[4 * tid + 3] = dq;
       }
-      __syncthreads();
+      // a step in which no pair rotates needs no update and no second barrier
+      if (!__syncthreads_or(rot)) continue;
       const short2* pr = pairs + step * half;
       for (int u = tid; u < nblk; u += NT) {
         const short2 ii = blk[u];

@@ -95,7 +95,9 @@ template <typename T>
 struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
-  double delta; int itmax; double *acc1, *acc2; int acc_stride; double* rho; int* done; double *res0, *resn;
+  // accumulators and per-column scalars in T: for an FP32 solve no FP64
+  // conversions (they issue on the slow FP64 pipe) in the hot loop
+  double delta; int itmax; T *acc1, *acc2; int acc_stride; T* rho; int* done; T *res0, *resn;
   int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int* iters_out;
   int xres;  // > 0: the X rows of all of this CTA's tiles stay staged (xres slots)
 };
@@ -159,7 +161,7 @@ __device__ __forceinline__ void gram_col(T (&acc)[BMAX + 1], T xc, T z, int b) {
 // (shared memory), and added to the graph's FP64 accumulators with one
 // atomic per output per CTA.
 template <typename T, int BMAX, int BWL>
-__device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&ex)[2], T* red) {
+__device__ void flush_cols(T* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&ex)[2], T* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
   constexpr int NV = BMAX + 3;
@@ -188,7 +190,7 @@ __device__ void flush_cols(double* accs, int b, int nextra, T (&acc)[BMAX + 1], 
     T t = T(0);
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) t += red[(w * NV + v) * BWL + cc];
-    if (t != T(0)) atomicAdd(accs + o, (double)t);
+    if (t != T(0)) atomicAdd(accs + o, t);
   }
   __syncthreads();
 }
@@ -233,9 +235,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   auto owner = [&](const Tile& t) { return t.idx_in_seg == 0; };
   // G[0] (the ones row) is a sum: scaled by 1/n_s to the mean; all in T
   // (FP64 issues ~60x slower on GB300)
-  auto load_G = [&](const double* A, int seg) {
+  auto load_G = [&](const T* A, int seg) {
 #pragma unroll
-    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? (T)__ldcg(A + i * b + c) : T(0);
+    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? __ldcg(A + i * b + c) : T(0);
     Gc[0] *= T(1) / (T)seg_rows(g, seg);
   };
   // X rows of the k-th tile of this CTA: resident slot k, or the one
@@ -302,17 +304,17 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
     const Tile t = g.tiles[ti];
     if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    const double* A2 = f.acc2 + (size_t)t.seg * stride1;
+    const T* A2 = f.acc2 + (size_t)t.seg * stride1;
     load_G(A2, t.seg);
     if (owner(t) && threadIdx.x < b) {
       const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-      const double rho = __ldcg(A2 + nout + threadIdx.x);
-      const double r0 = sqrt(__ldcg(A2 + nout + b + threadIdx.x));
+      const T rho = __ldcg(A2 + nout + threadIdx.x);
+      const T r0 = sqrt(__ldcg(A2 + nout + b + threadIdx.x));
       const int act = f.active == nullptr || f.active[k];
       f.rho[k] = rho;
       f.res0[k] = r0;
       f.resn[k] = r0;
-      f.done[k] = (!act || r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
+      f.done[k] = (!act || r0 == T(0) || rho == T(0) || !isfinite(rho)) ? 1 : 0;
     }
     const T* xt = stage(t, k);
     if (!colok) continue;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
     for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
       const Tile t = g.tiles[ti];
       if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
-        for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = 0.0;
+        for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = T(0);
     }
     {
       int cur = -1;
@@ -467,14 +469,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           gram_col<T, BMAX, BWL>(acc, xc, q, b);
           ex[0] += pv * q;
         } else {
-          double* A1 = f.acc1 + (size_t)seg * stride1;
+          T* A1 = f.acc1 + (size_t)seg * stride1;
           for (int i = 0; i < b; ++i) {
             const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-            if (own) atomicAdd(A1 + (size_t)(1 + i) * b + c, (double)(xi * q));
+            if (own) atomicAdd(A1 + (size_t)(1 + i) * b + c, xi * q);
           }
           if (own) {
-            atomicAdd(A1 + c, (double)q);
-            atomicAdd(A1 + nout + c, (double)(pv * q));
+            atomicAdd(A1 + c, q);
+            atomicAdd(A1 + nout + c, pv * q);
           }
         }
       };
@@ -556,13 +558,13 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         if (t.seg != cur) {
           if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
           cur = t.seg;
-          const double* A1 = f.acc1 + (size_t)t.seg * stride1;
+          const T* A1 = f.acc1 + (size_t)t.seg * stride1;
           load_G(A1, t.seg);
           al = T(0);
           if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const T pq = (T)__ldcg(A1 + nout + c);
-            const T rho = (T)__ldcg(f.rho + (size_t)par * f.state_stride + k);
+            const T pq = __ldcg(A1 + nout + c);
+            const T rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
             const int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
             if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
           }
@@ -612,19 +614,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         if (f.seg_skip && f.seg_skip[t.seg]) continue;
         if (t.seg != cur) {
           cur = t.seg;
-          const double* A2 = f.acc2 + (size_t)t.seg * stride1;
+          const T* A2 = f.acc2 + (size_t)t.seg * stride1;
           load_G(A2, t.seg);
           be = T(0);
           if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const T rho_new = (T)__ldcg(A2 + nout + c);
-            const T rn = sqrt((T)__ldcg(A2 + nout + b + c));
-            const T rho = (T)__ldcg(f.rho + (size_t)par * f.state_stride + k);
+            const T rho_new = __ldcg(A2 + nout + c);
+            const T rn = sqrt(__ldcg(A2 + nout + b + c));
+            const T rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
             int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
             T bb = T(0);
             if (!dn) {
               if (rho != T(0) && isfinite(rho_new)) bb = rho_new / rho;
-              if (!(rn > (T)f.delta * (T)__ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
+              if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
             }
             be = bb;
             if (owner(t) && threadIdx.x < BWL) {
@@ -635,16 +637,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           }
         }
         if (owner(t))
-          for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = 0.0;
+          for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = T(0);
         if (f.early_exit && !all_known) {
           // every CTA derives the same per-column decisions from the same
           // totals, so the exit below is taken by all CTAs together
           int mine = 1;
           if (threadIdx.x < b) {
             const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-            const T rn = sqrt((T)__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
+            const T rn = sqrt(__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
             const int d0 = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            mine = d0 || !(rn > (T)f.delta * (T)__ldcg(f.res0 + k)) || !isfinite(rn);
+            mine = d0 || !(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn);
           }
           s_all = __syncthreads_and(mine);
           all_known = 1;
@@ -677,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
-      for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = 0.0;
+      for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = T(0);
   }
 }
 
@@ -722,8 +724,10 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   DevGraph gg = g;
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
-             f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, f.acc1, f.acc2, f.acc_stride, f.rho,
-             f.done, f.res0, f.resn, f.state_stride, f.hub_seg, f.bar, f.early_exit && g.nseg == 1, f.iters_out, xres};
+             f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, reinterpret_cast<T*>(f.acc1),
+             reinterpret_cast<T*>(f.acc2), f.acc_stride, reinterpret_cast<T*>(f.rho), f.done,
+             reinterpret_cast<T*>(f.res0), reinterpret_cast<T*>(f.resn), f.state_stride, f.hub_seg, f.bar,
+             f.early_exit && g.nseg == 1, f.iters_out, xres};
   void* args[] = {&gg, &ff};
   const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), grid, kThreads, args, smem, s);
   return e == cudaSuccess ? 0 : -1;
