@@ -468,8 +468,8 @@ __device__ __forceinline__ void small_gemm(int ni, int nj, int nl, const double*
 //    eigenvectors are orthonormalised in FP64 (modified Gram-Schmidt),
 //    B = X^T H X is formed, and FP64 Jacobi sweeps on B (accumulated into X)
 //    finish the decomposition.
-//  * fast mode (nref >= 0: the first nref columns, ascending order): one
-//    refinement step in the form of Ogita and Aishima ("Iterative refinement
+//  * fast mode (nref >= 0: the first nref columns, ascending order): two
+//    refinement steps in the form of Ogita and Aishima ("Iterative refinement
 //    for symmetric eigenvalue decomposition", 2018):  R = I - X^T X_r,
 //    S = X^T H X_r,  lambda_j = s_jj / (1 - r_jj),
 //    E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when that is below
@@ -537,7 +537,10 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   nH = sqrt(nH);
   __syncthreads();
   // 1. FP32 Jacobi
-  int sw = jacobi2s<float>(A32, V32, LD, mm, 1e-7f, (float)(1e-30 + 1e-12 * nH), 40, s_cs32, s_pairs, s_blk, nblk);
+  // (fast mode: the FP32 sweeps stop at a 1e-4 relative off-diagonal; two
+  // FP64 refinement steps take that to FP64 accuracy for fewer sweeps)
+  int sw = jacobi2s<float>(A32, V32, LD, mm, exact ? 1e-7f : 1e-4f, (float)(1e-30 + 1e-12 * nH), 40, s_cs32, s_pairs,
+                           s_blk, nblk);
   if (exact) {
     // 2e. X = V32 in FP64, orthonormalised by modified Gram-Schmidt
     for (int e = tid; e < mm * mm; e += NT) X[(e / mm) * LM + (e % mm)] = (double)V32[(e / mm) * LD + (e % mm)];
@@ -620,7 +623,7 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   __syncthreads();
   for (int j = tid; j < m; j += NT) lam[j] = lam_s[j];
   __syncthreads();
-  if (nr > 0) {
+  for (int rstep = 0; rstep < 2 && nr > 0; ++rstep) {
     double* Z = W;               // m x LR (overwrites the FP32 arrays)
     double* S = Z + m * LR;
     double* R = S + m * LR;

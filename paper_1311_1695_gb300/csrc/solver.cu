@@ -239,7 +239,7 @@ struct JD {
 
   // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
   int rayleigh_ritz(int m) {
-    // only the mk kept Ritz pairs are refined to FP64 accuracy (one step
+    // only the mk kept Ritz pairs are refined to FP64 accuracy (two steps
     // from the FP32 Jacobi result); H restarts as diag(theta[0:mk])
     const int mk = std::min(m, z.mk);
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
