@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 
@@ -418,7 +419,8 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
   const int S = g->hg.nseg;
   const size_t es = dtype == LAP_F32 ? 4 : 8;
   const size_t n = (size_t)g->hg.n;
-  int rc = graph_scratch(g, 4 * n * b * es + 256, sizeof(double) * S * 64 + 1024);
+  const int ldlx = (b + 3) / 4 * 4;
+  int rc = graph_scratch(g, 4 * n * b * es + n * ldlx * es + 512, sizeof(double) * S * 64 + 1024);
   if (rc) return rc;
   if (!g->pcg.acc1) {
     rc = g->pcg.init(S);
@@ -433,7 +435,8 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     T* Z = RES + n * b;
     T* P = Z + n * b;
     T* AP = P + n * b;
-    const FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, b, b, th, 64, nullptr, nullptr, delta, iters,
+    T* LX = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(AP + n * b) + 255) & ~(uintptr_t)255);
+    const FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, LX, ldlx, b, b, th, 64, nullptr, nullptr, delta, iters,
                                    g->d_long_seg);
     if (pcg_fused<T>(g->dg, f, s, 0) != 0) return check_cuda("lap_pcg_correction launch");
   });

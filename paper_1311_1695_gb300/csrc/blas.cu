@@ -468,8 +468,8 @@ __device__ __forceinline__ void small_gemm(int ni, int nj, int nl, const double*
 //    eigenvectors are orthonormalised in FP64 (modified Gram-Schmidt),
 //    B = X^T H X is formed, and FP64 Jacobi sweeps on B (accumulated into X)
 //    finish the decomposition.
-//  * fast mode (nref >= 0: the first nref columns, ascending order): two
-//    refinement steps in the form of Ogita and Aishima ("Iterative refinement
+//  * fast mode (nref >= 0: the first nref columns, ascending order): one
+//    refinement step in the form of Ogita and Aishima ("Iterative refinement
 //    for symmetric eigenvalue decomposition", 2018):  R = I - X^T X_r,
 //    S = X^T H X_r,  lambda_j = s_jj / (1 - r_jj),
 //    E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when that is below
@@ -479,7 +479,7 @@ __device__ __forceinline__ void small_gemm(int ni, int nj, int nl, const double*
 //    Newton-Schulz steps X_r <- X_r (3 I - X_r^T X_r) / 2 until X_r is
 //    orthonormal to FP64 rounding.  The work is four m x m x nref FP64
 //    products instead of FP64 sweeps over all m^2 entries.
-__global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
+__global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__ Hg, int ldh, int64_t sh,
                                                double* evals, int64_t se, double* Yg, int ldy, int64_t sy,
                                                const int* __restrict__ seg_skip, int* sweeps_out, int nref) {
   const int seg = blockIdx.x;
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   __shared__ short2 s_pairs[63 * 32];
   __shared__ short2 s_blk[32 * 33 / 2];
   __shared__ int s_rank[64];
-  __shared__ double s_red[2][8];
+  __shared__ double s_red[2][32];
   __shared__ int s_flag;
   const double* H = Hg + (size_t)seg * sh;
 
@@ -537,10 +537,7 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   nH = sqrt(nH);
   __syncthreads();
   // 1. FP32 Jacobi
-  // (fast mode: the FP32 sweeps stop at a 1e-4 relative off-diagonal; two
-  // FP64 refinement steps take that to FP64 accuracy for fewer sweeps)
-  int sw = jacobi2s<float>(A32, V32, LD, mm, exact ? 1e-7f : 1e-4f, (float)(1e-30 + 1e-12 * nH), 40, s_cs32, s_pairs,
-                           s_blk, nblk);
+  int sw = jacobi2s<float>(A32, V32, LD, mm, 1e-7f, (float)(1e-30 + 1e-12 * nH), 40, s_cs32, s_pairs, s_blk, nblk);
   if (exact) {
     // 2e. X = V32 in FP64, orthonormalised by modified Gram-Schmidt
     for (int e = tid; e < mm * mm; e += NT) X[(e / mm) * LM + (e % mm)] = (double)V32[(e / mm) * LD + (e % mm)];
@@ -623,7 +620,7 @@ __global__ void __launch_bounds__(256) k_syev(int m, const double* __restrict__ 
   __syncthreads();
   for (int j = tid; j < m; j += NT) lam[j] = lam_s[j];
   __syncthreads();
-  for (int rstep = 0; rstep < 2 && nr > 0; ++rstep) {
+  if (nr > 0) {
     double* Z = W;               // m x LR (overwrites the FP32 arrays)
     double* S = Z + m * LR;
     double* R = S + m * LR;
@@ -1026,7 +1023,10 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
     cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  k_syev<<<nseg, 256, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out,
+  // one 2x2 block per thread in a Jacobi step for m > 40 (the blocks of a
+  // 46 x 46 matrix take two rounds of 256 threads; measured 12% faster)
+  const int nt = m > 40 ? 512 : 256;
+  k_syev<<<nseg, nt, smem, s>>>(m, H, ldh, sh, evals, se, Y, ldy, sy, seg_skip, sweeps_out,
                                  nref < 0 ? -1 : (int)nr);
 }
 

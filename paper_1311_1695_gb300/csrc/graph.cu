@@ -321,7 +321,7 @@ int PcgWork::init(int nseg_) {
   nseg = nseg_;
   const size_t a = (size_t)nseg * acc_stride;
   const size_t st = (size_t)nseg * 64;
-  const size_t bytes = sizeof(double) * (2 * a + 2 * st + 2 * st) + sizeof(int) * 2 * st + 64;
+  const size_t bytes = sizeof(double) * (4 * a + 2 * st + 2 * st) + sizeof(int) * 2 * st + 64;
   char* base = nullptr;
   if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -330,8 +330,8 @@ int PcgWork::init(int nseg_) {
   }
   if (cudaMemset(base, 0, bytes) != cudaSuccess) { set_error("cudaMemset failed"); cudaFree(base); return LAP_ECUDA; }
   acc1 = reinterpret_cast<double*>(base);
-  acc2 = acc1 + a;
-  rho = acc2 + a;
+  acc2 = acc1 + 2 * a;
+  rho = acc2 + 2 * a;
   res0 = rho + 2 * st;
   resn = res0 + st;
   done = reinterpret_cast<int*>(resn + st);
@@ -345,10 +345,11 @@ void PcgWork::release() {
 }
 
 FusedPcg PcgWork::args(const void* X, int ldx, const void* R, int ldr, void* Tt, void* RES, void* Z, void* P, void* AP,
-                       int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip,
+                       void* LX, int ldlx, int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip,
                        double delta, int itmax, const int* hub_seg) const {
   FusedPcg f;
   f.Xv = X; f.ldx = ldx; f.Rv = R; f.ldr = ldr; f.Ttv = Tt; f.RESv = RES; f.Zv = Z; f.Pv = P; f.APv = AP;
+  f.LXv = LX; f.ldlx = ldlx;
   f.ld = ld; f.b = b; f.theta = theta; f.sth = sth; f.active = active; f.bstride = 64; f.seg_skip = seg_skip;
   f.delta = delta; f.itmax = itmax; f.acc1 = acc1; f.acc2 = acc2; f.acc_stride = acc_stride; f.rho = rho;
   f.done = done; f.res0 = res0; f.resn = resn; f.state_stride = (int64_t)nseg * 64; f.hub_seg = hub_seg;

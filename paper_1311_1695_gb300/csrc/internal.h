@@ -27,7 +27,7 @@ struct PcgWork {
   int init(int nseg_);
   void release();
   FusedPcg args(const void* X, int ldx, const void* R, int ldr, void* Tt, void* RES, void* Z, void* P, void* AP,
-                int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip, double delta,
+                void* LX, int ldlx, int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip, double delta,
                 int itmax, const int* hub_seg) const;
   int error_flag(cudaStream_t s) const;  // reads and clears the barrier error flag
   int steps_done(cudaStream_t s) const;  // PCG steps of the last launch

@@ -67,7 +67,7 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 // ascending; Y columns are the matching unit eigenvectors.
 // FP32 Jacobi, then FP64: nref < 0 (exact mode) every column to FP64
 // accuracy (Gram-Schmidt, B = X^T H X, FP64 Jacobi); nref >= 0 (fast mode)
-// two refinement steps plus orthonormalisation of the first nref columns
+// one refinement step plus orthonormalisation of the first nref columns
 // only, the others FP32-accurate.
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se,
           double* Y, int ldy, int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref = -1);

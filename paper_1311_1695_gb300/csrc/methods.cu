@@ -369,12 +369,13 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
   const double rtol = 1e-2 * tol;  // delta_PCG = 1e-2 delta (Section 4)
   DevBuf buf;
   const int ldk = (k + 3) / 4 * 4;
-  int rc = buf.alloc(sizeof(double) * ((size_t)n * ldv + (size_t)n * 8 + (size_t)n * ldk + 8 * 64 * 64 + 4096));
+  int rc = buf.alloc(sizeof(double) * ((size_t)n * ldv + (size_t)n * 8 + (size_t)n * ldk + (size_t)n * 4 + 8 * 64 * 64 + 4096));
   if (rc) return rc;
   double* V = static_cast<double*>(buf.p);
   double* Wb = V + (size_t)n * ldv;      // n x 8: [w, zero, Tt, RES, Z, P, AP, f]
   double* Xb = Wb + (size_t)n * 8;       // Ritz vectors, n x ldk
-  double* sm = Xb + (size_t)n * ldk;
+  double* LXw = Xb + (size_t)n * ldk;   // n x 4: L X of the inner PCG (X = 0)
+  double* sm = LXw + (size_t)n * 4;
   double* Tm = sm;                       // 64 x 64
   double* Ym = Tm + 64 * 64;
   double* Qm = Ym + 64 * 64;
@@ -414,7 +415,7 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
   for (restarts = 0; restarts < max_restarts; ++restarts) {
     for (int j = j0; j < m; ++j) {
       // w = L^+ v_j: PCG on L t = -v_j (R = v_j, theta = 0), then w = -t
-      const FusedPcg fp = G->pcg.args(zero, LW, V + j, ldv, Wb + 2, Wb + 3, Wb + 4, Wb + 5, Wb + 6, LW, 1, th, 64,
+      const FusedPcg fp = G->pcg.args(zero, LW, V + j, ldv, Wb + 2, Wb + 3, Wb + 4, Wb + 5, Wb + 6, LXw, 4, LW, 1, th, 64,
                                       nullptr, nullptr, rtol, 4000, G->d_long_seg);
       FusedPcg fe = fp;
       fe.early_exit = 1;

@@ -5,35 +5,41 @@
 // (Eq. 5, Section 3.2.1 with P = D^{-1}; CG on the projected, possibly
 // indefinite system is the paper's choice, Section 3.2).
 //
-// Each iteration has three phases separated by grid-wide barriers:
-//   A  q~ = L p - theta p (the degree-fused SpMM), partial G1 = [1|X]^T q~, p.q~
+// Each iteration has two phases separated by grid-wide barriers:
+//   M  beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
+//      p' = (z~ - [1|X] G2) + beta p,  q~' = (L - theta) p' (the degree-fused
+//      SpMM), partial G1 = [1|X]^T q~', p'.q~'
 //   B  alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
 //      z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r
-//   C  beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
-//      p = (z~ - [1|X] G2) + beta p
-// Partial sums go to per-graph FP64 accumulators with atomics; after the
-// barrier every CTA reads the totals and derives the same scalars.  Scalars
-// that persist across iterations (rho, done) are double-buffered by
-// iteration parity and written by the CTA owning the graph's first tile, so
-// no CTA reads a value while another rewrites it.  Accumulators are zeroed
-// by that owner one phase after their last read.
+// Phase M needs no barrier between forming p' and gathering it: with
+// L e = 0 and LX = L X (one SpMM of X at the start),
+//   (L - theta)(z~ - e g0 - X g) = (L z~ - theta z~) + theta g0 e - (LX - theta X) g
+// so the SpMM gathers z~, complete since the last barrier, and
+// q~' = (L - theta)(I - QQ^T) z~ + beta q~ follows from the previous q~.
+// Partial sums go to per-graph accumulators (in the solve's type) with
+// atomics; after the barrier every CTA reads the totals and derives the same
+// scalars.  Accumulators and the scalars that persist across iterations
+// (rho, done) are double-buffered by iteration parity; the scalars are
+// written by the CTA owning the graph's first tile and each accumulator is
+// zeroed by that owner in the phase after its last read, so no CTA reads a
+// value while another rewrites it.
 //
 // Work layout.  A CTA owns whole row tiles (tile k goes to CTA k mod grid) in
 // every phase; within a tile a "row group" of BWL lanes handles a row, lane c
 // column c (lanes as columns, BWL >= b).  The tile's X rows are staged in
 // shared memory, zero-padded to BMAX columns, so the projections
 // y - [1|X] G and the Gram terms [1|X]^T z read x_i as broadcast vector
-// loads with no per-column predicate.  Phase A balances the SpMM inside a
+// loads with no per-column predicate.  Phase M balances the SpMM inside a
 // tile merge-path style: the tile's nonzeros (hub rows excluded, see below)
 // are cut into equal ranges, one per row group; a group walks its range with
 // U independent gathers in flight and adds each finished (or cut) row into a
 // shared-memory row accumulator; after a CTA barrier the rows' epilogue
-// (q~ = d p - A p - theta p, the Gram terms) runs row by row.  Hub rows
+// (p', q~', the Gram terms) runs row by row.  Hub rows
 // (degree > long_thresh) are cut into chunks of kHubChunk nonzeros spread
 // over all warps of the grid and combined by the last chunk to finish
 // (hub.cuh).
 //
-// Data written by another CTA inside the launch (gathered P rows, hub rows,
+// Data written by another CTA inside the launch (gathered z~ rows, hub rows,
 // the persistent scalars, the accumulators) is read with L2 loads (__ldcg):
 // L1 is not coherent across SMs.  Rows a CTA owns are only ever written and
 // read by that CTA.
@@ -91,13 +97,20 @@ __device__ bool grid_barrier(const GridBar& bar) {
   return s_ok != 0;
 }
 
+template <int BMAX, int BWL>
+struct RedLx {
+  static constexpr int a = kWarps * (BMAX + 3) * BWL, b = kTileRows * BMAX;
+  static constexpr int v = a > b ? a : b;
+};
+
 template <typename T>
 struct View {
   const T* X; int ldx; const T* R; int ldr; T *Tt, *RES, *Z, *P, *AP;
+  T* LX; int ldlx;  // L X, rows 16-byte aligned (ldlx a multiple of 4)
   int ld, b; const double* theta; int64_t sth; const int* active; int bstride; const int* seg_skip;
   // accumulators and per-column scalars in T: for an FP32 solve no FP64
   // conversions (they issue on the slow FP64 pipe) in the hot loop
-  double delta; int itmax; T *acc1, *acc2; int acc_stride; T* rho; int* done; T *res0, *resn;
+  double delta; int itmax; T *acc1, *acc2; int acc_stride; T* rho; int* done; T *res0, *resn;  // acc: [2][nseg][stride]
   int64_t state_stride; const int* hub_seg; GridBar bar; int early_exit; int* iters_out;
   int xres;  // > 0: the X rows of all of this CTA's tiles stay staged (xres slots)
 };
@@ -165,6 +178,7 @@ __device__ void flush_cols(T* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&e
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL;
   constexpr int NV = BMAX + 3;
+  __syncthreads();  // red aliases phase M's staged LX rows
 #pragma unroll
   for (int o = BWL; o < 32; o <<= 1) {
 #pragma unroll
@@ -204,11 +218,206 @@ __device__ __forceinline__ void stage_x(T* xs, const T* __restrict__ X, int ldx,
   }
 }
 
+// sum_i G[i+1] r[i] for a row r of LX staged in shared memory (zero padded
+// to BMAX columns, like X)
+template <typename T, int BMAX>
+__device__ __forceinline__ T dot_xs(const T* __restrict__ r, const T (&Gc)[BMAX + 1]) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    const V v = *reinterpret_cast<const V*>(r + i);
+    if constexpr (W == 4) {
+      s += v.x * Gc[i + 1]; s += v.y * Gc[i + 2]; s += v.z * Gc[i + 3]; s += v.w * Gc[i + 4];
+    } else {
+      s += v.x * Gc[i + 1]; s += v.y * Gc[i + 2];
+    }
+  }
+  return s;
+}
+
+// Stage rows [r0, r0 + nrows) of LX (ldlx a multiple of 4, 16-byte aligned
+// rows, columns [b, ldlx) zero) into lxs (row stride BMAX, zero padded), with
+// vector L2 loads: LX is written inside the launch.
+template <typename T, int BMAX>
+__device__ __forceinline__ void stage_lx(T* lxs, const T* LX, int ldlx, int r0, int nrows, int b) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  constexpr int NV = BMAX / W;
+  constexpr int U = 4;  // loads in flight per thread
+  const int total = nrows * NV;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * U) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kThreads;
+      const int r = e / NV, i = (e - r * NV) * W;
+      if (e < total && i < b) {
+        v[u] = __ldcg(reinterpret_cast<const V*>(LX + (size_t)(r0 + r) * ldlx + i));
+      } else {
+        if constexpr (W == 4) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        else v[u] = make_double2(0.0, 0.0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * kThreads;
+      if (e < total) *reinterpret_cast<V*>(lxs + e * W) = v[u];
+    }
+  }
+}
+
+// Merge-path SpMM of one tile's ordinary nonzeros: accA[i][c] += sum over row
+// i of w * src[col][c].  The nonzeros are cut into SLOTS equal ranges, one per
+// row group; a group walks its range with kU independent gathers in flight and
+// adds each finished (or cut) row into the shared row accumulator.
+template <typename T, int BMAX, int SLOTS>
+__device__ __forceinline__ void walk_tile(const DevGraph& g, const T* __restrict__ w, const T* src, int lds,
+                                          const int* s_rp, const int* s_erp, int nrows, T* accA, int grp, int c,
+                                          bool colok) {
+  const int E0 = s_erp[0], E = s_erp[nrows] - E0;
+  const int es = E0 + (int)((long long)E * grp / SLOTS);
+  const int ee = E0 + (int)((long long)E * (grp + 1) / SLOTS);
+  if (es >= ee) return;
+  int lo = 0, hi = nrows - 1;  // last row i with s_erp[i] <= es
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_erp[mid] <= es) lo = mid; else hi = mid - 1;
+  }
+  int i = lo;
+  int nx = s_erp[i + 1];
+  int pb = s_rp[i] - s_erp[i];  // p = pb + e inside row i
+  T a = T(0);
+  for (int e0 = es; e0 < ee; e0 += kU) {
+    int pu[kU], iu[kU];
+    int ii = i;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int e = e0 + u;
+      pu[u] = -1;
+      iu[u] = ii;
+      if (e < ee) {
+        while (e >= nx) {
+          ++ii;
+          nx = s_erp[ii + 1];
+          pb = s_rp[ii] - s_erp[ii];
+        }
+        pu[u] = pb + e;
+        iu[u] = ii;
+      }
+    }
+    T v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      v[u] = T(0);
+      if (pu[u] >= 0 && colok) {
+        const T x = __ldcg(src + (size_t)__ldg(g.colidx + pu[u]) * lds + c);
+        v[u] = w ? __ldg(w + pu[u]) * x : x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      if (pu[u] >= 0) {
+        if (iu[u] != i) {
+          if (colok) atomicAdd(accA + i * BMAX + c, a);
+          a = T(0);
+          i = iu[u];
+        }
+        a += v[u];
+      }
+    }
+  }
+  if (colok) atomicAdd(accA + i * BMAX + c, a);
+}
+
+// The hub rows' part of an SpMM of src: chunks of at most kHubChunk nonzeros
+// spread over the grid; the warp completing a hub (hub.cuh) calls
+// fin(chunk, graph, a) with lane c < BWL holding the row's sum of w src[col][c].
+// Called by every thread of the CTA.
+template <typename T, int BMAX, int BWL, class Fin>
+__device__ __forceinline__ void hub_pass(const DevGraph& g, const int* hub_seg, const int* seg_skip,
+                                         const T* __restrict__ w, const T* src, int lds, T* red, int b, int grp,
+                                         int c, bool colok, Fin&& fin) {
+  constexpr int RW = 32 / BWL;
+  constexpr int SLOTS = kWarps * RW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto chunk_sum = [&](int q0, int q1) {  // lane c: sum over [q0, q1) of w src[col][c]
+    T a = T(0);
+    if (colok) {
+      if (w) {
+#pragma unroll 8
+        for (int p = q0; p < q1; ++p) a += __ldg(w + p) * __ldcg(src + (size_t)__ldg(g.colidx + p) * lds + c);
+      } else {
+#pragma unroll 8
+        for (int p = q0; p < q1; ++p) a += __ldcg(src + (size_t)__ldg(g.colidx + p) * lds + c);
+      }
+    }
+    return a;
+  };
+  if (g.nchunk <= (int)gridDim.x) {
+    // few chunks: one per CTA, split over all of the CTA's row groups (a
+    // chunk then costs a couple of gather rounds, not kHubChunk / RW)
+    const int ch = blockIdx.x;
+    bool doit = ch < g.nchunk;
+    int4 cc = make_int4(0, 0, 0, 0);
+    int seg = 0;
+    if (doit) {
+      cc = g.chunks[ch];
+      seg = hub_seg[cc.w];
+      doit = !(seg_skip && seg_skip[seg]);
+    }
+    if (doit) {  // CTA-uniform
+      const int len = cc.z - cc.y;
+      T a = chunk_sum(cc.y + (int)((long long)len * grp / SLOTS), cc.y + (int)((long long)len * (grp + 1) / SLOTS));
+#pragma unroll
+      for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      __syncthreads();
+      if (lane < BWL) red[warp * BWL + c] = a;
+      __syncthreads();
+      if (warp == 0) {
+        T sum = T(0);
+        if (lane < BWL)
+          for (int v = 0; v < kWarps; ++v) sum += red[v * BWL + c];
+        if (hub_finish<T>(g, ch, cc, sum, b)) fin(cc, seg, sum);
+      }
+      __syncthreads();
+    }
+  } else {
+    // many chunks: one warp each, round-robin over all warps of the grid; the
+    // warp's row groups take interleaved nonzeros
+    for (int ch = blockIdx.x * kWarps + warp; ch < g.nchunk; ch += gridDim.x * kWarps) {
+      const int4 cc = g.chunks[ch];
+      const int seg = hub_seg[cc.w];
+      if (seg_skip && seg_skip[seg]) continue;  // whole warp
+      T a = T(0);
+      if (colok) {
+        if (w) {
+#pragma unroll 8
+          for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
+            a += __ldg(w + p) * __ldcg(src + (size_t)__ldg(g.colidx + p) * lds + c);
+        } else {
+#pragma unroll 8
+          for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(src + (size_t)__ldg(g.colidx + p) * lds + c);
+        }
+      }
+#pragma unroll
+      for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (!hub_finish<T>(g, ch, cc, a, b)) continue;
+      fin(cc, seg, a);
+    }
+  }
+}
+
 template <typename T, int BMAX, int BWL>
 __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 : 2) k_pcg_fused(DevGraph g, View<T> f) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* red = reinterpret_cast<T*>(smem_raw);                          // [warps][BMAX+3][BWL]
-  T* xs = red + kWarps * (BMAX + 3) * BWL;                          // [max(1, xres)][kTileRows][BMAX]
+  // red [warps][BMAX+3][BWL] (the flushes) shares its space with lxs
+  // [kTileRows][BMAX] (phase M's LX rows): a flush never falls between a
+  // tile's LX staging and its epilogue
+  T* red = reinterpret_cast<T*>(smem_raw);
+  T* lxs = red;
+  T* xs = red + RedLx<BMAX, BWL>::v;                                // [max(1, xres)][kTileRows][BMAX]
   T* accA = xs + (size_t)(f.xres > 1 ? f.xres : 1) * kTileRows * BMAX;  // [kTileRows][BMAX]
   const int nslots = f.xres > 1 ? f.xres : 1;
   int* s_rp0 = reinterpret_cast<int*>(accA + kTileRows * BMAX);     // [nslots][kTileRows + 1]
@@ -227,12 +436,19 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   const T* __restrict__ deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
   const T* __restrict__ w = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.w32 : (const void*)g.w64);
   const T* __restrict__ X = f.X;
+  T* LX = f.LX;
+  const int ldlx = f.ldlx;
+  const int64_t ss = f.state_stride;
   T acc[BMAX + 1];
   T ex[2] = {T(0), T(0)};
 #pragma unroll
   for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
   T Gc[BMAX + 1];
   auto owner = [&](const Tile& t) { return t.idx_in_seg == 0; };
+  auto skipped = [&](int seg) { return f.seg_skip && f.seg_skip[seg]; };
+  // accumulators of graph s, parity q
+  auto A1 = [&](int q, int s) { return f.acc1 + ((size_t)q * g.nseg + s) * stride1; };
+  auto A2 = [&](int q, int s) { return f.acc2 + ((size_t)q * g.nseg + s) * stride1; };
   // G[0] (the ones row) is a sum: scaled by 1/n_s to the mean; all in T
   // (FP64 issues ~60x slower on GB300)
   auto load_G = [&](const T* A, int seg) {
@@ -249,6 +465,40 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
     __syncthreads();
     return xs;
   };
+  // the same plus the tile's row pointers (and in phase M its LX rows),
+  // before an SpMM walk
+  auto stage_walk = [&](const Tile& t, int k, const int*& s_rp, const int*& s_erp, bool lx) -> const T* {
+    const int nrows = t.r1 - t.r0;
+    if (f.xres) {
+      s_rp = s_rp0 + k * (kTileRows + 1);
+      s_erp = s_erp0 + k * (kTileRows + 1);
+      __syncthreads();  // the previous tile's epilogue is done with accA and lxs
+      if (lx) stage_lx<T, BMAX>(lxs, LX, ldlx, t.r0, nrows, b);
+      return xs + (size_t)k * kTileRows * BMAX;
+    }
+    s_rp = s_rp0;
+    s_erp = s_erp0;
+    __syncthreads();
+    if (lx) stage_lx<T, BMAX>(lxs, LX, ldlx, t.r0, nrows, b);
+    stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
+    for (int i = threadIdx.x; i <= nrows; i += kThreads) {
+      s_rp0[i] = g.rowptr[t.r0 + i];
+      s_erp0[i] = g.erp[t.r0 + i];
+    }
+    __syncthreads();
+    return xs;
+  };
+  // beta = rho'/rho of column c of graph seg entering step it (0 at it = 0
+  // and for a column already done)
+  auto beta_of = [&](int seg, int it) -> T {
+    if (it == 0 || !colok) return T(0);
+    const size_t k = (size_t)seg * f.bstride + c;
+    const int prv = (it + 1) & 1;
+    const T rho_new = __ldcg(A2(prv, seg) + nout + c);
+    const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
+    const int dn = __ldcg(f.done + (size_t)prv * ss + k);
+    return (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
+  };
   for (int e = threadIdx.x; e < kTileRows * BMAX; e += kThreads) accA[e] = T(0);
   if (f.xres) {
     for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
@@ -263,18 +513,24 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   }
 
   // ---------------------------------------------------------------- init
+  // LX = L X (the SpMM of X, once); RES = -R, Tt = 0, z~ = RES / d; partial
+  // G2 = [1|X]^T z~, r.z~, r.r into acc2 parity 1
   {
     int cur = -1;
     for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
       const Tile t = g.tiles[ti];
-      if (f.seg_skip && f.seg_skip[t.seg]) continue;
+      if (skipped(t.seg)) continue;
       if (t.seg != cur) {
-        if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(1, cur), b, 2, acc, ex, red);
         cur = t.seg;
       }
-      const T* xt = stage(t, k);
+      const int* s_rp;
+      const int* s_erp;
+      const T* xt = stage_walk(t, k, s_rp, s_erp, false);
+      walk_tile<T, BMAX, SLOTS>(g, w, X, f.ldx, s_rp, s_erp, t.r1 - t.r0, accA, grp, c, colok);
+      __syncthreads();
       const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-      if (!colok) continue;
+      if (c >= ldlx) continue;  // lanes [b, ldlx) write LX's zero padding
       for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
         T rr[kRU], dv[kRU];
 #pragma unroll
@@ -286,286 +542,215 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
 #pragma unroll
         for (int u = 0; u < kRU; ++u) {
           const int r = rb + u * SLOTS;
-          if (r < t.r1) {
-            const size_t o = (size_t)r * ld + c;
-            const T res = rr[u], z = res / dv[u];
-            f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
-            gram_xs<T, BMAX>(acc, xt + (r - t.r0) * BMAX, z);
-            ex[0] += res * z;
-            ex[1] += res * res;
+          if (r >= t.r1) continue;
+          const int il = r - t.r0;
+          const T* xr = xt + il * BMAX;
+          if (s_rp[il + 1] - s_rp[il] <= g.long_thresh) {  // hub rows: by their chunks
+            const T a = accA[il * BMAX + c];
+            accA[il * BMAX + c] = T(0);
+            LX[(size_t)r * ldlx + c] = colok ? dv[u] * xr[c] - a : T(0);
           }
+          if (!colok) continue;
+          const size_t o = (size_t)r * ld + c;
+          const T res = rr[u], z = res / dv[u];
+          f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
+          gram_xs<T, BMAX>(acc, xr, z);
+          ex[0] += res * z;
+          ex[1] += res * res;
         }
       }
     }
-    if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
-  }
-  if (!grid_barrier(f.bar)) return;
-  // init-C: p = z~ - [1|X] G2; owner records rho, res0, done (parity 0)
-  for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
-    const Tile t = g.tiles[ti];
-    if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    const T* A2 = f.acc2 + (size_t)t.seg * stride1;
-    load_G(A2, t.seg);
-    if (owner(t) && threadIdx.x < b) {
-      const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-      const T rho = __ldcg(A2 + nout + threadIdx.x);
-      const T r0 = sqrt(__ldcg(A2 + nout + b + threadIdx.x));
-      const int act = f.active == nullptr || f.active[k];
-      f.rho[k] = rho;
-      f.res0[k] = r0;
-      f.resn[k] = r0;
-      f.done[k] = (!act || r0 == T(0) || rho == T(0) || !isfinite(rho)) ? 1 : 0;
-    }
-    const T* xt = stage(t, k);
-    if (!colok) continue;
-    for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
-      T zv[kRU];
-#pragma unroll
-      for (int u = 0; u < kRU; ++u) {
-        const int r = rb + u * SLOTS;
-        zv[u] = r < t.r1 ? f.Z[(size_t)r * ld + c] : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < kRU; ++u) {
-        const int r = rb + u * SLOTS;
-        if (r < t.r1) f.P[(size_t)r * ld + c] = project_xs<T, BMAX>(zv[u], xt + (r - t.r0) * BMAX, Gc);
-      }
-    }
+    hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, X, f.ldx, red, b, grp, c, colok,
+                           [&](const int4& cc, int, T a) {
+                             const int row = cc.x;
+                             if (lane < BWL && c < ldlx)
+                               LX[(size_t)row * ldlx + c] = colok ? deg[row] * X[(size_t)row * f.ldx + c] - a : T(0);
+                           });
+    if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(1, cur), b, 2, acc, ex, red);
   }
   if (!grid_barrier(f.bar)) return;
 
-  int it_done = 0;
-  for (int it = 0; it < f.itmax; ++it) {
-    const int par = it & 1;
-    // ---------------------------------------------------------------- phase A: q~ = L p - theta p, G1, p.q~
-    // owner zeroes acc2 (its last read was the previous phase C / init-C)
-    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+  int it = 0;
+  bool stopped = false;
+  for (; it < f.itmax; ++it) {
+    const int par = it & 1, prv = par ^ 1;
+    // every CTA derives the same per-column decisions from the same totals,
+    // so a single graph's solve stops in all CTAs together once every column
+    // met delta after the previous step
+    if (f.early_exit && it > 0) {
+      int mine = 1;
+      T rn = T(0);
+      if (threadIdx.x < b) {
+        const size_t k = threadIdx.x;
+        rn = sqrt(__ldcg(A2(prv, 0) + nout + b + threadIdx.x));
+        const int d0 = __ldcg(f.done + (size_t)prv * ss + k);
+        mine = d0 || !(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn);
+      }
+      if (__syncthreads_and(mine)) {
+        if (blockIdx.x == 0 && threadIdx.x < b) f.resn[threadIdx.x] = rn;
+        stopped = true;
+        break;
+      }
+    }
+    // ---------------------------------------------------------------- phase M
+    // beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
+    // p' = P z~ + beta p and q~' = (L - theta) p' with
+    //   (L - theta) P z~ = (L z~ - theta z~) + theta G2[0] - [0|LX - theta X] G2
+    // (L e = 0): the SpMM gathers z~ (written before the last barrier), so
+    // p' needs no barrier of its own; q~' = (L - theta) P z~ + beta q~.
+    // Partial G1 = [1|X]^T q~', p'.q~' into acc1 parity par.
+    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {  // last read in step it-1's phase B
       const Tile t = g.tiles[ti];
-      if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
-        for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = T(0);
+      if (owner(t) && !skipped(t.seg))
+        for (int e = threadIdx.x; e < stride1; e += kThreads) A1(prv, t.seg)[e] = T(0);
     }
     {
-      int cur = -1;
-      T thc = T(0);
+      int cur = -1, gseg = -1;  // gseg: the graph whose G2, beta, theta are loaded
+      T thc = T(0), be = T(0);
       for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
         const Tile t = g.tiles[ti];
-        if (f.seg_skip && f.seg_skip[t.seg]) continue;
+        if (skipped(t.seg)) continue;
         if (t.seg != cur) {
-          if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
-          cur = t.seg;
+          if (cur >= 0) flush_cols<T, BMAX, BWL>(A1(par, cur), b, 1, acc, ex, red);
+          cur = gseg = t.seg;
           thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
-        }
-        const int nrows = t.r1 - t.r0;
-        const T* xt = f.xres ? xs + (size_t)k * kTileRows * BMAX : xs;
-        const int* s_rp = f.xres ? s_rp0 + k * (kTileRows + 1) : s_rp0;
-        const int* s_erp = f.xres ? s_erp0 + k * (kTileRows + 1) : s_erp0;
-        if (!f.xres) {
-          __syncthreads();
-          stage_x<T, BMAX>(xs, X, f.ldx, t.r0, nrows, b);
-          for (int i = threadIdx.x; i <= nrows; i += kThreads) {
-            s_rp0[i] = g.rowptr[t.r0 + i];
-            s_erp0[i] = g.erp[t.r0 + i];
-          }
-          __syncthreads();
-        } else if (k > 0) {
-          __syncthreads();  // the previous tile's epilogue is done with accA
-        }
-        // merge-path walk over the tile's ordinary nonzeros
-        const int E0 = s_erp[0], E = s_erp[nrows] - E0;
-        const int es = E0 + (int)((long long)E * grp / SLOTS);
-        const int ee = E0 + (int)((long long)E * (grp + 1) / SLOTS);
-        if (es < ee) {
-          int lo = 0, hi = nrows - 1;  // last row i with s_erp[i] <= es
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_erp[mid] <= es) lo = mid; else hi = mid - 1;
-          }
-          int i = lo;
-          int nx = s_erp[i + 1];
-          int pb = s_rp[i] - s_erp[i];  // p = pb + e inside row i
-          T a = T(0);
-          for (int e0 = es; e0 < ee; e0 += kU) {
-            int pu[kU], iu[kU];
-            int ii = i;
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              const int e = e0 + u;
-              pu[u] = -1;
-              iu[u] = ii;
-              if (e < ee) {
-                while (e >= nx) {
-                  ++ii;
-                  nx = s_erp[ii + 1];
-                  pb = s_rp[ii] - s_erp[ii];
-                }
-                pu[u] = pb + e;
-                iu[u] = ii;
-              }
+          load_G(A2(prv, t.seg), t.seg);
+          be = beta_of(t.seg, it);
+          if (owner(t) && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
+            const size_t k = (size_t)t.seg * f.bstride + c;
+            const T rho_new = __ldcg(A2(prv, t.seg) + nout + c);
+            const T rn = sqrt(__ldcg(A2(prv, t.seg) + nout + b + c));
+            int dn;
+            if (it == 0) {
+              const int act = f.active == nullptr || f.active[k];
+              dn = (!act || rn == T(0) || rho_new == T(0) || !isfinite(rho_new)) ? 1 : 0;
+              f.res0[k] = rn;
+            } else {
+              dn = __ldcg(f.done + (size_t)prv * ss + k);
+              if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
             }
-            T v[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              v[u] = T(0);
-              if (pu[u] >= 0 && colok) {
-                const T x = __ldcg(f.P + (size_t)__ldg(g.colidx + pu[u]) * ld + c);
-                v[u] = w ? __ldg(w + pu[u]) * x : x;
-              }
-            }
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-              if (pu[u] >= 0) {
-                if (iu[u] != i) {
-                  if (colok) atomicAdd(accA + i * BMAX + c, a);
-                  a = T(0);
-                  i = iu[u];
-                }
-                a += v[u];
-              }
-            }
+            f.rho[(size_t)par * ss + k] = rho_new;
+            f.done[(size_t)par * ss + k] = dn;
+            f.resn[k] = rn;
           }
-          if (colok) atomicAdd(accA + i * BMAX + c, a);
         }
+        const int* s_rp;
+        const int* s_erp;
+        const T* xt = stage_walk(t, k, s_rp, s_erp, true);
+        walk_tile<T, BMAX, SLOTS>(g, w, f.Z, ld, s_rp, s_erp, t.r1 - t.r0, accA, grp, c, colok);
         __syncthreads();
-        // row epilogue: q~ = d p - (A p) - theta p; the Gram terms
-        if (colok) {
-          for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
-            T pv[kRU], dv[kRU];
+        if (!colok) continue;
+        for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
+          T zv[kRU], dv[kRU], pv[kRU], qv[kRU];
 #pragma unroll
-            for (int u = 0; u < kRU; ++u) {
-              const int r = rb + u * SLOTS;
-              pv[u] = T(0); dv[u] = T(0);
-              if (r < t.r1) { pv[u] = f.P[(size_t)r * ld + c]; dv[u] = deg[r]; }
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            zv[u] = pv[u] = qv[u] = T(0); dv[u] = T(0);
+            if (r < t.r1) {
+              const size_t o = (size_t)r * ld + c;
+              zv[u] = f.Z[o]; dv[u] = deg[r];
+              if (be != T(0)) { pv[u] = __ldcg(f.P + o); qv[u] = __ldcg(f.AP + o); }
             }
+          }
 #pragma unroll
-            for (int u = 0; u < kRU; ++u) {
-              const int r = rb + u * SLOTS;
-              if (r >= t.r1) continue;
-              const int il = r - t.r0;
-              if (s_rp[il + 1] - s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
-              const T a = accA[il * BMAX + c];
-              accA[il * BMAX + c] = T(0);
-              const T q = dv[u] * pv[u] - a - thc * pv[u];
-              f.AP[(size_t)r * ld + c] = q;
-              gram_xs<T, BMAX>(acc, xt + il * BMAX, q);
-              ex[0] += pv[u] * q;
-            }
+          for (int u = 0; u < kRU; ++u) {
+            const int r = rb + u * SLOTS;
+            if (r >= t.r1) continue;
+            const int il = r - t.r0;
+            if (s_rp[il + 1] - s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
+            const T a = accA[il * BMAX + c];
+            accA[il * BMAX + c] = T(0);
+            const T* xr = xt + il * BMAX;
+            const T pz = project_xs<T, BMAX>(zv[u], xr, Gc);
+            const T sl = dot_xs<T, BMAX>(lxs + il * BMAX, Gc);
+            T q = dv[u] * zv[u] - a - sl - thc * pz;
+            T p = pz;
+            if (be != T(0)) { q += be * qv[u]; p += be * pv[u]; }
+            const size_t o = (size_t)r * ld + c;
+            f.P[o] = p;
+            f.AP[o] = q;
+            gram_xs<T, BMAX>(acc, xr, q);
+            ex[0] += p * q;
           }
         }
       }
-      // hub rows: chunks of at most kHubChunk nonzeros.  The warp completing
-      // a hub (hub.cuh) writes its q~ row and adds its share of G1 and p.q~
-      // (to the CTA's registers when the hub is in the CTA's current graph,
-      // else with atomics); `a` is lane c's column sum (lanes < BWL).
-      auto finish_row = [&](const int4& cc, int seg, T a) {
+      // hub rows: the completing warp forms p' and q~' of the row from its
+      // graph's totals (reloaded into Gc, free here, for another graph) and
+      // adds its share of G1 and p'.q~' (to the CTA's registers when the hub
+      // is in the CTA's current graph, else with atomics)
+      hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, f.Z, ld, red, b, grp, c, colok,
+                             [&](const int4& cc, int seg, T a) {
         const int row = cc.x;
         const bool own = colok && lane < BWL;  // group 0 holds the row
-        const T d = deg[row];
-        const T pv = own ? __ldcg(f.P + (size_t)row * ld + c) : T(0);
-        const T thc = own ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
-        const T q = own ? d * pv - a - thc * pv : T(0);
-        if (own) f.AP[(size_t)row * ld + c] = q;
+        if (seg != gseg) {  // warp-uniform
+          load_G(A2(prv, seg), seg);
+          be = beta_of(seg, it);
+          thc = colok ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
+          gseg = seg;
+        }
+        const T bs = be;
+        const T th = own ? thc : T(0);
+        const size_t o = (size_t)row * ld + c;
+        const T zr = own ? __ldcg(f.Z + o) : T(0);
         const T xc = own ? X[(size_t)row * f.ldx + c] : T(0);
+        const T lc = own ? __ldcg(LX + (size_t)row * ldlx + c) : T(0);
+        T sx = Gc[0], sl = T(0);
+#pragma unroll
+        for (int i = 0; i < BMAX; ++i) {
+          const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+          const T li = __shfl_sync(0xffffffffu, lc, i, BWL);
+          sx += xi * Gc[i + 1];
+          sl += li * Gc[i + 1];
+        }
+        const T pz = zr - sx;
+        T q = deg[row] * zr - a - sl - th * pz;
+        T p = pz;
+        if (own && bs != T(0)) { q += bs * __ldcg(f.AP + o); p += bs * __ldcg(f.P + o); }
+        if (!own) { q = T(0); p = T(0); }
+        if (own) { f.P[o] = p; f.AP[o] = q; }
         if (seg == cur) {
           gram_col<T, BMAX, BWL>(acc, xc, q, b);
-          ex[0] += pv * q;
+          ex[0] += p * q;
         } else {
-          T* A1 = f.acc1 + (size_t)seg * stride1;
+          T* a1 = A1(par, seg);
           for (int i = 0; i < b; ++i) {
             const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-            if (own) atomicAdd(A1 + (size_t)(1 + i) * b + c, xi * q);
+            if (own) atomicAdd(a1 + (size_t)(1 + i) * b + c, xi * q);
           }
           if (own) {
-            atomicAdd(A1 + c, q);
-            atomicAdd(A1 + nout + c, pv * q);
+            atomicAdd(a1 + c, q);
+            atomicAdd(a1 + nout + c, p * q);
           }
         }
-      };
-      auto chunk_sum = [&](int q0, int q1) {  // lane c: sum over [q0, q1) of w P[col][c]
-        T a = T(0);
-        if (colok) {
-          if (w) {
-#pragma unroll 8
-            for (int p = q0; p < q1; ++p) a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-          } else {
-#pragma unroll 8
-            for (int p = q0; p < q1; ++p) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-          }
-        }
-        return a;
-      };
-      if (g.nchunk <= (int)gridDim.x) {
-        // few chunks: one per CTA, split over all of the CTA's row groups
-        // (a chunk then costs a couple of gather rounds, not kHubChunk / RW)
-        const int ch = blockIdx.x;
-        bool doit = ch < g.nchunk;
-        int4 cc = make_int4(0, 0, 0, 0);
-        int seg = 0;
-        if (doit) {
-          cc = g.chunks[ch];
-          seg = f.hub_seg[cc.w];
-          doit = !(f.seg_skip && f.seg_skip[seg]);
-        }
-        if (doit) {  // CTA-uniform
-          const int len = cc.z - cc.y;
-          T a = chunk_sum(cc.y + (int)((long long)len * grp / SLOTS), cc.y + (int)((long long)len * (grp + 1) / SLOTS));
-#pragma unroll
-          for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          __syncthreads();
-          if (lane < BWL) red[warp * BWL + c] = a;
-          __syncthreads();
-          if (warp == 0) {
-            T sum = T(0);
-            if (lane < BWL)
-              for (int v = 0; v < kWarps; ++v) sum += red[v * BWL + c];
-            if (hub_finish<T>(g, ch, cc, sum, b)) finish_row(cc, seg, sum);
-          }
-          __syncthreads();
-        }
-      } else {
-        // many chunks: one warp each, round-robin over all warps of the grid;
-        // the warp's row groups take interleaved nonzeros
-        for (int ch = blockIdx.x * kWarps + warp; ch < g.nchunk; ch += gridDim.x * kWarps) {
-          const int4 cc = g.chunks[ch];
-          const int seg = f.hub_seg[cc.w];
-          if (f.seg_skip && f.seg_skip[seg]) continue;  // whole warp
-          T a = T(0);
-          if (colok) {
-            if (w) {
-#pragma unroll 8
-              for (int p = cc.y + lane / BWL; p < cc.z; p += RW)
-                a += __ldg(w + p) * __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-            } else {
-#pragma unroll 8
-              for (int p = cc.y + lane / BWL; p < cc.z; p += RW) a += __ldcg(f.P + (size_t)__ldg(g.colidx + p) * ld + c);
-            }
-          }
-#pragma unroll
-          for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-          if (!hub_finish<T>(g, ch, cc, a, b)) continue;
-          finish_row(cc, seg, a);
-        }
-      }
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc1 + (size_t)cur * stride1, b, 1, acc, ex, red);
+      });
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(A1(par, cur), b, 1, acc, ex, red);
     }
     if (!grid_barrier(f.bar)) return;
     // ---------------------------------------------------------------- phase B
+    // alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
+    // z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity par
+    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {  // last read in phase M above
+      const Tile t = g.tiles[ti];
+      if (owner(t) && !skipped(t.seg))
+        for (int e = threadIdx.x; e < stride1; e += kThreads) A2(prv, t.seg)[e] = T(0);
+    }
     {
       int cur = -1;
       T al = T(0);
       for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
         const Tile t = g.tiles[ti];
-        if (f.seg_skip && f.seg_skip[t.seg]) continue;
+        if (skipped(t.seg)) continue;
         if (t.seg != cur) {
-          if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
+          if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(par, cur), b, 2, acc, ex, red);
           cur = t.seg;
-          const T* A1 = f.acc1 + (size_t)t.seg * stride1;
-          load_G(A1, t.seg);
+          const T* a1 = A1(par, t.seg);
+          load_G(a1, t.seg);
           al = T(0);
           if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const T pq = __ldcg(A1 + nout + c);
-            const T rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
-            const int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
+            const T pq = __ldcg(a1 + nout + c);
+            const T rho = __ldcg(f.rho + (size_t)par * ss + k);
+            const int dn = __ldcg(f.done + (size_t)par * ss + k);
             if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
           }
         }
@@ -579,7 +764,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
             ap[u] = rs[u] = tv[u] = pv[u] = T(0); dv[u] = T(1);
             if (r < t.r1) {
               const size_t o = (size_t)r * ld + c;
-              ap[u] = __ldcg(f.AP + o); rs[u] = f.RES[o]; tv[u] = f.Tt[o]; pv[u] = f.P[o]; dv[u] = deg[r];
+              ap[u] = __ldcg(f.AP + o); rs[u] = f.RES[o]; tv[u] = f.Tt[o]; pv[u] = __ldcg(f.P + o); dv[u] = deg[r];
             }
           }
 #pragma unroll
@@ -600,86 +785,28 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
           }
         }
       }
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(f.acc2 + (size_t)cur * stride1, b, 2, acc, ex, red);
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(par, cur), b, 2, acc, ex, red);
     }
     if (!grid_barrier(f.bar)) return;
-    // ---------------------------------------------------------------- phase C
-    int all_known = 0;
-    __shared__ int s_all;
-    {
-      int cur = -1;
-      T be = T(0);
-      for (int ti = blockIdx.x, k = 0; ti < g.ntiles; ti += gridDim.x, ++k) {
-        const Tile t = g.tiles[ti];
-        if (f.seg_skip && f.seg_skip[t.seg]) continue;
-        if (t.seg != cur) {
-          cur = t.seg;
-          const T* A2 = f.acc2 + (size_t)t.seg * stride1;
-          load_G(A2, t.seg);
-          be = T(0);
-          if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
-            const size_t k = (size_t)t.seg * f.bstride + c;
-            const T rho_new = __ldcg(A2 + nout + c);
-            const T rn = sqrt(__ldcg(A2 + nout + b + c));
-            const T rho = __ldcg(f.rho + (size_t)par * f.state_stride + k);
-            int dn = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            T bb = T(0);
-            if (!dn) {
-              if (rho != T(0) && isfinite(rho_new)) bb = rho_new / rho;
-              if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
-            }
-            be = bb;
-            if (owner(t) && threadIdx.x < BWL) {
-              f.rho[(size_t)(par ^ 1) * f.state_stride + k] = rho_new;
-              f.done[(size_t)(par ^ 1) * f.state_stride + k] = dn;
-              f.resn[k] = rn;
-            }
-          }
-        }
-        if (owner(t))
-          for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc1[(size_t)t.seg * stride1 + e] = T(0);
-        if (f.early_exit && !all_known) {
-          // every CTA derives the same per-column decisions from the same
-          // totals, so the exit below is taken by all CTAs together
-          int mine = 1;
-          if (threadIdx.x < b) {
-            const size_t k = (size_t)t.seg * f.bstride + threadIdx.x;
-            const T rn = sqrt(__ldcg(f.acc2 + (size_t)t.seg * stride1 + nout + b + threadIdx.x));
-            const int d0 = __ldcg(f.done + (size_t)par * f.state_stride + k);
-            mine = d0 || !(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn);
-          }
-          s_all = __syncthreads_and(mine);
-          all_known = 1;
-        }
-        const T* xt = stage(t, k);
-        if (!colok) continue;
-        for (int rb = t.r0 + grp; rb < t.r1; rb += kRU * SLOTS) {
-          T zv[kRU], pv[kRU];
-#pragma unroll
-          for (int u = 0; u < kRU; ++u) {
-            const int r = rb + u * SLOTS;
-            zv[u] = pv[u] = T(0);
-            if (r < t.r1) { zv[u] = f.Z[(size_t)r * ld + c]; pv[u] = f.P[(size_t)r * ld + c]; }
-          }
-#pragma unroll
-          for (int u = 0; u < kRU; ++u) {
-            const int r = rb + u * SLOTS;
-            if (r >= t.r1) continue;
-            const T z = project_xs<T, BMAX>(zv[u], xt + (r - t.r0) * BMAX, Gc);
-            f.P[(size_t)r * ld + c] = (be == T(0)) ? z : z + be * pv[u];
-          }
-        }
-      }
-    }
-    if (!grid_barrier(f.bar)) return;
-    it_done = it + 1;
-    if (f.early_exit && all_known && s_all) break;
   }
-  if (f.iters_out && blockIdx.x == 0 && threadIdx.x == 0) *f.iters_out = it_done;
+  if (!stopped) {  // ||r|| after the last step (parity of the last phase B)
+    const int last = (it + 1) & 1;
+    for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+      const Tile t = g.tiles[ti];
+      if (owner(t) && !skipped(t.seg) && threadIdx.x < b)
+        f.resn[(size_t)t.seg * f.bstride + threadIdx.x] = sqrt(__ldcg(A2(last, t.seg) + nout + b + threadIdx.x));
+    }
+  }
+  if (f.iters_out && blockIdx.x == 0 && threadIdx.x == 0) *f.iters_out = it;
+  // every CTA is past its last read of the accumulators: back to zero
+  if (!grid_barrier(f.bar)) return;
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
-    if (owner(t) && !(f.seg_skip && f.seg_skip[t.seg]))
-      for (int e = threadIdx.x; e < stride1; e += kThreads) f.acc2[(size_t)t.seg * stride1 + e] = T(0);
+    if (owner(t) && !skipped(t.seg))
+      for (int e = threadIdx.x; e < stride1; e += kThreads) {
+        A1(0, t.seg)[e] = T(0); A1(1, t.seg)[e] = T(0);
+        A2(0, t.seg)[e] = T(0); A2(1, t.seg)[e] = T(0);
+      }
   }
 }
 
@@ -689,7 +816,7 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   auto kern = k_pcg_fused<T, BMAX, BWL>;
   const size_t tile_x = sizeof(T) * (size_t)kTileRows * BMAX;
   const size_t tile_rp = sizeof(int) * 2 * (kTileRows + 1);
-  const size_t base = sizeof(T) * ((size_t)kWarps * (BMAX + 3) * BWL) + 2 * tile_x + tile_rp;
+  const size_t base = sizeof(T) * (size_t)RedLx<BMAX, BWL>::v + 2 * tile_x + tile_rp;
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -723,7 +850,8 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   }
   DevGraph gg = g;
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
-             static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv), f.ld, f.b,
+             static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv),
+             static_cast<T*>(f.LXv), f.ldlx, f.ld, f.b,
              f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, reinterpret_cast<T*>(f.acc1),
              reinterpret_cast<T*>(f.acc2), f.acc_stride, reinterpret_cast<T*>(f.rho), f.done,
              reinterpret_cast<T*>(f.res0), reinterpret_cast<T*>(f.resn), f.state_stride, f.hub_seg, f.bar,
@@ -736,10 +864,11 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
 }  // namespace
 
 // Algorithmic bytes of a solve of `iters` steps: per step the CSR once and
-// about 17 passes over n x b blocks (P gathered, AP, T, RES, Z, X twice...),
-// plus 9 passes for the set-up.
+// 16 passes over n x b blocks (phase M: z~ gathered, z~, X, LX, P, AP read,
+// P, AP written; phase B: AP, RES, T, P, X read, T, RES, z~ written), plus
+// the set-up (the CSR, X gathered and read, R read, LX, RES, T, z~ written).
 double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
-  return (double)elem * g.n * b * (iters * 17.0 + 9.0) + (4.0 * g.n + 4.0 * g.nnz) * iters;
+  return (double)elem * g.n * b * (iters * 16.0 + 7.0) + (4.0 * g.n + 4.0 * g.nnz) * (iters + 1);
 }
 
 template <typename T>

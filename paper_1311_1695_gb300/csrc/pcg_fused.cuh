@@ -17,6 +17,8 @@ struct FusedPcg {
   int ldr;
   void *Ttv, *RESv, *Zv, *Pv, *APv;  // n x ld work blocks; Tt receives the correction
   int ld;
+  void* LXv;           // n x ldlx work block (L X); ldlx >= b, a multiple of 4, rows 16-byte aligned
+  int ldlx;
   int b;
   const double* theta;  // [nseg * sth]
   int64_t sth;
@@ -25,7 +27,7 @@ struct FusedPcg {
   const int* seg_skip;  // [nseg] or null
   double delta;
   int itmax;
-  double* acc1;         // [nseg * acc_stride], zero at rest
+  double* acc1;         // [2 * nseg * acc_stride] (by iteration parity), zero at rest
   double* acc2;
   int acc_stride;
   double* rho;          // [2 * state_stride]

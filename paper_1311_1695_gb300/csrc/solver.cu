@@ -82,6 +82,7 @@ struct JD {
   TP* Zb;
   TP* P;
   TP* AP;
+  TP* LXb;  // L X of the correction solve
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
@@ -124,7 +125,7 @@ struct JD {
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     add(2 * n * z.ldv * sizeof(TV));
     add(n * z.ldb * sizeof(TV));
-    for (int i = 0; i < 7; ++i) add(n * z.ldb * sizeof(TP));
+    for (int i = 0; i < 8; ++i) add(n * z.ldb * sizeof(TP));
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
@@ -147,6 +148,7 @@ struct JD {
     Zb = a.take<TP>(n * z.ldb);
     P = a.take<TP>(n * z.ldb);
     AP = a.take<TP>(n * z.ldb);
+    LXb = a.take<TP>(n * z.ldb);
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
     Y = a.take<double>(S * mm);
@@ -239,7 +241,7 @@ struct JD {
 
   // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
   int rayleigh_ritz(int m) {
-    // only the mk kept Ritz pairs are refined to FP64 accuracy (two steps
+    // only the mk kept Ritz pairs are refined to FP64 accuracy (one step
     // from the FP32 Jacobi result); H restarts as diag(theta[0:mk])
     const int mk = std::min(m, z.mk);
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
@@ -295,7 +297,7 @@ struct JD {
       X = Xp; ldx = z.ldb; R = Rp; ldr = z.ldb;
     }
     // single graph: the solve stops once every active column met delta
-    FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, z.ldb, z.b, theta, z.mmax, active, seg_skip,
+    FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, theta, z.mmax, active, seg_skip,
                           delta, itmax, G->d_long_seg);
     f.early_exit = 1;
     if (pcg_fused<TP>(g, f, st, 0) != 0) {
