@@ -280,39 +280,49 @@ __global__ void k_convert(DevGraph g, const TX* __restrict__ X, int ldx, TY* __r
 }
 
 // ------------------------------------------------------------------ small per-segment kernels
+// 1/sqrt(x) in FP64: an FP32 seed and two Newton steps y <- y (3 - x y^2) / 2
+// (each squares the relative error: ~1e-7 -> ~1e-14 -> below FP64 rounding);
+// exact sqrt and division outside the seed's range.
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
+// S = R^T R (right-looking Cholesky, one barrier per column) and R^-1 by
+// back substitution.  Every thread derives column j's pivot test and
+// 1/sqrt(pivot) itself, so a step needs no barrier of its own: the strictly
+// upper part of row j of R, S[j][i] / sqrt(pivot), goes to the unused lower
+// triangle (S[i][j]), and the trailing update S[i][l] -= S[j][i] S[j][l] /
+// pivot (l >= i > j) reads row j of S, which no thread writes in step j.  A
+// column whose pivot fails the drop test is dropped (zero row in R^-1,
+// keep = 0).
 __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, double drop, int absolute,
                            double* Rinv, int64_t sr, int* keep, const int* __restrict__ seg_skip) {
   const int seg = blockIdx.x;
   if (seg_skip && seg_skip[seg]) return;
-  __shared__ double S[kMaxCols][kMaxCols + 1];
+  __shared__ double S[kMaxCols][kMaxCols + 1];  // upper: trailing matrix; lower: R^T
   __shared__ double d0[kMaxCols];
+  __shared__ double rinv[kMaxCols];
   __shared__ int kp[kMaxCols];
   for (int e = threadIdx.x; e < q * q; e += blockDim.x) S[e / q][e % q] = Sg[(size_t)seg * ss + e];
   __syncthreads();
   if (threadIdx.x < q) d0[threadIdx.x] = absolute ? 1.0 : S[threadIdx.x][threadIdx.x];
   __syncthreads();
-  // FP64 divisions and square roots are long dependent sequences on GB300:
-  // one reciprocal per pivot (kept in rinv) and multiplications elsewhere
-  __shared__ double rinv[kMaxCols];
   for (int j = 0; j < q; ++j) {
-    __shared__ double rjj;
-    if (threadIdx.x == 0) {
-      const double piv = S[j][j];
-      const bool ok = d0[j] > 0.0 && piv > drop * d0[j] && isfinite(piv);
-      kp[j] = ok ? 1 : 0;
-      rjj = ok ? sqrt(piv) : 0.0;
-      rinv[j] = ok ? 1.0 / rjj : 0.0;
-    }
-    __syncthreads();
-    const bool ok = kp[j] != 0;
-    const double ri = rinv[j];
-    for (int i = j + threadIdx.x; i < q; i += blockDim.x) S[j][i] = ok ? (i == j ? rjj : S[j][i] * ri) : 0.0;
-    __syncthreads();
+    const double piv = S[j][j];
+    const bool ok = d0[j] > 0.0 && piv > drop * d0[j] && isfinite(piv);
+    const double y = ok ? rsqrt_newton(piv) : 0.0;
+    if (threadIdx.x == 0) { kp[j] = ok ? 1 : 0; rinv[j] = y; }
+    for (int i = j + 1 + threadIdx.x; i < q; i += blockDim.x) S[i][j] = S[j][i] * y;
     if (ok) {
+      const double y2 = y * y;
       const int m = q - j - 1;
       for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = j + 1 + e / m, l = j + 1 + e % m;
-        if (l >= i) S[i][l] -= S[j][i] * S[j][l];
+        if (l >= i) S[i][l] -= S[j][i] * S[j][l] * y2;
       }
     }
     __syncthreads();
@@ -327,7 +337,7 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
     for (int i = c; i >= 0; --i) {
       if (!kp[i]) { x[i] = 0.0; continue; }
       double s = (i == c) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= c; ++l) s -= S[i][l] * x[l];
+      for (int l = i + 1; l <= c; ++l) s -= S[l][i] * x[l];
       x[i] = s * rinv[i];
     }
     for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = x[i];

@@ -218,9 +218,20 @@ __device__ void flush_cols(T* accs, int b, int nextra, T (&acc)[BMAX + 1], T (&e
 // Stage rows [r0, r0 + nrows) of X into xs (row stride BMAX, zero padded).
 template <typename T, int BMAX>
 __device__ __forceinline__ void stage_x(T* xs, const T* __restrict__ X, int ldx, int r0, int nrows, int b) {
-  for (int e = threadIdx.x; e < nrows * BMAX; e += kThreads) {
-    const int r = e / BMAX, i = e - r * BMAX;
-    xs[e] = i < b ? X[(size_t)(r0 + r) * ldx + i] : T(0);
+  constexpr int U = 4;  // unpredicated loads in flight per thread
+  const int total = nrows * BMAX;
+  for (int e0 = threadIdx.x; e0 < total; e0 += kThreads * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = min(e0 + u * kThreads, total - 1);
+      const int r = e / BMAX, i = e - r * BMAX;
+      v[u] = X[(size_t)(r0 + r) * ldx + (i < b ? i : 0)];
+      if (i >= b) v[u] = T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u * kThreads < total) xs[e0 + u * kThreads] = v[u];
   }
 }
 
@@ -462,9 +473,15 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   auto A2 = [&](int q, int s) { return f.acc2 + ((size_t)q * g.nseg + s) * stride1; };
   // G[0] (the ones row) is a sum: scaled by 1/n_s to the mean; all in T
   // (FP64 issues ~60x slower on GB300)
+  // (unpredicated loads from clamped indices, so the BMAX + 1 loads issue
+  // back to back)
   auto load_G = [&](const T* A, int seg) {
+    const int cc = colok ? c : 0;
 #pragma unroll
-    for (int i = 0; i <= BMAX; ++i) Gc[i] = (colok && i <= b) ? __ldcg(A + i * b + c) : T(0);
+    for (int i = 0; i <= BMAX; ++i) {
+      const T v = __ldcg(A + (i <= b ? i : b) * b + cc);
+      Gc[i] = (colok && i <= b) ? v : T(0);
+    }
     Gc[0] *= T(1) / (T)seg_rows(g, seg);
   };
   // X rows of the k-th tile of this CTA: resident slot k, or the one
