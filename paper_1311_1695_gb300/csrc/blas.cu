@@ -282,7 +282,8 @@ __global__ void k_convert(DevGraph g, const TX* __restrict__ X, int ldx, TY* __r
 // ------------------------------------------------------------------ small per-segment kernels
 // 1/sqrt(x) in FP64: an FP32 seed and two Newton steps y <- y (3 - x y^2) / 2
 // (each squares the relative error: ~1e-7 -> ~1e-14 -> below FP64 rounding);
-// exact sqrt and division outside the seed's range.
+// exact sqrt and division outside the seed's range.  In FP32: the seed and
+// one Newton step.
 __device__ __forceinline__ double rsqrt_newton(double x) {
   if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
   double y = (double)rsqrtf((float)x);
@@ -290,35 +291,42 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   y = y * (1.5 - 0.5 * x * y * y);
   return y;
 }
+__device__ __forceinline__ float rsqrt_newton(float x) {
+  const float y = rsqrtf(x);
+  return y * (1.5f - 0.5f * x * y * y);
+}
 
 // S = R^T R (right-looking Cholesky, one barrier per column) and R^-1 by
-// back substitution.  Every thread derives column j's pivot test and
-// 1/sqrt(pivot) itself, so a step needs no barrier of its own: the strictly
-// upper part of row j of R, S[j][i] / sqrt(pivot), goes to the unused lower
-// triangle (S[i][j]), and the trailing update S[i][l] -= S[j][i] S[j][l] /
-// pivot (l >= i > j) reads row j of S, which no thread writes in step j.  A
-// column whose pivot fails the drop test is dropped (zero row in R^-1,
-// keep = 0).
+// back substitution, in TC (FP32 for a basis held in FP32, whose update
+// rounds R^-1 to FP32 anyway; FP64 issues ~60x slower).  Every thread
+// derives column j's pivot test and 1/sqrt(pivot) itself, so a step needs no
+// barrier of its own: the strictly upper part of row j of R,
+// S[j][i] / sqrt(pivot), goes to the unused lower triangle (S[i][j]), and the
+// trailing update S[i][l] -= S[j][i] S[j][l] / pivot (l >= i > j) reads row j
+// of S, which no thread writes in step j.  A column whose pivot fails the drop
+// test is dropped (zero row in R^-1, keep = 0).
+template <typename TC>
 __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, double drop, int absolute,
                            double* Rinv, int64_t sr, int* keep, const int* __restrict__ seg_skip) {
   const int seg = blockIdx.x;
   if (seg_skip && seg_skip[seg]) return;
-  __shared__ double S[kMaxCols][kMaxCols + 1];  // upper: trailing matrix; lower: R^T
-  __shared__ double d0[kMaxCols];
-  __shared__ double rinv[kMaxCols];
+  __shared__ TC S[kMaxCols][kMaxCols + 1];  // upper: trailing matrix; lower: R^T
+  __shared__ TC d0[kMaxCols];
+  __shared__ TC rinv[kMaxCols];
   __shared__ int kp[kMaxCols];
-  for (int e = threadIdx.x; e < q * q; e += blockDim.x) S[e / q][e % q] = Sg[(size_t)seg * ss + e];
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) S[e / q][e % q] = (TC)Sg[(size_t)seg * ss + e];
   __syncthreads();
-  if (threadIdx.x < q) d0[threadIdx.x] = absolute ? 1.0 : S[threadIdx.x][threadIdx.x];
+  if (threadIdx.x < q) d0[threadIdx.x] = absolute ? TC(1) : S[threadIdx.x][threadIdx.x];
   __syncthreads();
+  const TC dr = (TC)drop;
   for (int j = 0; j < q; ++j) {
-    const double piv = S[j][j];
-    const bool ok = d0[j] > 0.0 && piv > drop * d0[j] && isfinite(piv);
-    const double y = ok ? rsqrt_newton(piv) : 0.0;
+    const TC piv = S[j][j];
+    const bool ok = d0[j] > TC(0) && piv > dr * d0[j] && isfinite(piv);
+    const TC y = ok ? rsqrt_newton(piv) : TC(0);
     if (threadIdx.x == 0) { kp[j] = ok ? 1 : 0; rinv[j] = y; }
     for (int i = j + 1 + threadIdx.x; i < q; i += blockDim.x) S[i][j] = S[j][i] * y;
     if (ok) {
-      const double y2 = y * y;
+      const TC y2 = y * y;
       const int m = q - j - 1;
       for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
         const int i = j + 1 + e / m, l = j + 1 + e % m;
@@ -333,14 +341,14 @@ __global__ void k_chol_inv(int q, const double* __restrict__ Sg, int64_t ss, dou
   __syncthreads();
   const int c = threadIdx.x;
   if (c < q && kp[c]) {
-    double x[kMaxCols];
+    TC x[kMaxCols];
     for (int i = c; i >= 0; --i) {
-      if (!kp[i]) { x[i] = 0.0; continue; }
-      double s = (i == c) ? 1.0 : 0.0;
+      if (!kp[i]) { x[i] = TC(0); continue; }
+      TC s = (i == c) ? TC(1) : TC(0);
       for (int l = i + 1; l <= c; ++l) s -= S[l][i] * x[l];
       x[i] = s * rinv[i];
     }
-    for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = x[i];
+    for (int i = 0; i <= c; ++i) Ro[(size_t)i * q + c] = (double)x[i];
   }
   if (c < q && keep) keep[(size_t)seg * 64 + c] = kp[c];
 }
@@ -1009,9 +1017,10 @@ void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T
 }
 
 void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv, int64_t sr,
-              int* keep, const int* seg_skip, cudaStream_t s) {
+              int* keep, const int* seg_skip, cudaStream_t s, bool fp32) {
   LAP_PROF("chol_inv", 0.0, s);
-  k_chol_inv<<<nseg, 64, 0, s>>>(q, S, ss, drop, absolute, Rinv, sr, keep, seg_skip);
+  if (fp32) k_chol_inv<float><<<nseg, 64, 0, s>>>(q, S, ss, drop, absolute, Rinv, sr, keep, seg_skip);
+  else k_chol_inv<double><<<nseg, 64, 0, s>>>(q, S, ss, drop, absolute, Rinv, sr, keep, seg_skip);
 }
 
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se, double* Y, int ldy,

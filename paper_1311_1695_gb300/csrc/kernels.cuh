@@ -59,8 +59,9 @@ void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T
 // dropping of columns whose pivot falls below drop * (initial diagonal), or
 // below drop itself when absolute is set; out
 // Rinv (q x q upper triangular, dropped columns zero) and keep[s*64 + c].
+// fp32: factor and invert in FP32 (for a basis held in FP32).
 void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv,
-              int64_t sr, int* keep, const int* seg_skip, cudaStream_t s);
+              int64_t sr, int* keep, const int* seg_skip, cudaStream_t s, bool fp32 = false);
 
 // Symmetric eigensolver (parallel cyclic Jacobi), m <= 64, one CTA per
 // segment.  H (m x m, ld ldh, segment stride sh) is not modified.  evals

@@ -516,13 +516,32 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
     __syncthreads();
     return xs;
   };
+  // the same from totals staged in shared memory
+  auto load_Gs = [&](const T* tot, int seg) {
+    const int cc = colok ? c : 0;
+#pragma unroll
+    for (int i = 0; i <= BMAX; ++i) {
+      const T v = tot[(i <= b ? i : b) * b + cc];
+      Gc[i] = (colok && i <= b) ? v : T(0);
+    }
+    Gc[0] *= T(1) / (T)seg_rows(g, seg);
+  };
+  // a graph's nout + 2b totals into shared memory (red, free between a flush
+  // and the next tile's LX staging), one load per value for the whole CTA
+  // instead of one per warp: every CTA reads the same few lines right after
+  // the grid barrier
+  auto stage_tot = [&](const T* A) -> const T* {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nout + 2 * b; e += kThreads) red[e] = __ldcg(A + e);
+    __syncthreads();
+    return red;
+  };
   // beta = rho'/rho of column c of graph seg entering step it (0 at it = 0
-  // and for a column already done)
-  auto beta_of = [&](int seg, int it) -> T {
+  // and for a column already done); rho_new = r'.z~' of column c
+  auto beta_of = [&](int seg, int it, T rho_new) -> T {
     if (it == 0 || !colok) return T(0);
     const size_t k = (size_t)seg * f.bstride + c;
     const int prv = (it + 1) & 1;
-    const T rho_new = __ldcg(A2(prv, seg) + nout + c);
     const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
     const int dn = __ldcg(f.done + (size_t)prv * ss + k);
     return (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
@@ -642,13 +661,14 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         if (t.seg != cur) {
           if (cur >= 0) flush_cols<T, BMAX, BWL>(A1(par, cur), b, 1, acc, ex, red);
           cur = gseg = t.seg;
+          const T* tot = stage_tot(A2(prv, t.seg));
           thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
-          load_G(A2(prv, t.seg), t.seg);
-          be = beta_of(t.seg, it);
+          load_Gs(tot, t.seg);
+          be = beta_of(t.seg, it, colok ? tot[nout + c] : T(0));
           if (owner(t) && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const T rho_new = __ldcg(A2(prv, t.seg) + nout + c);
-            const T rn = sqrt(__ldcg(A2(prv, t.seg) + nout + b + c));
+            const T rho_new = tot[nout + c];
+            const T rn = sqrt(tot[nout + b + c]);
             int dn;
             if (it == 0) {
               const int act = f.active == nullptr || f.active[k];
@@ -710,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         const bool own = colok && lane < BWL;  // group 0 holds the row
         if (seg != gseg) {  // warp-uniform
           load_G(A2(prv, seg), seg);
-          be = beta_of(seg, it);
+          be = beta_of(seg, it, colok ? __ldcg(A2(prv, seg) + nout + c) : T(0));
           thc = colok ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
           gseg = seg;
         }
@@ -769,12 +789,12 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
         if (t.seg != cur) {
           if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(par, cur), b, 2, acc, ex, red);
           cur = t.seg;
-          const T* a1 = A1(par, t.seg);
-          load_G(a1, t.seg);
+          const T* tot = stage_tot(A1(par, t.seg));
+          load_Gs(tot, t.seg);
           al = T(0);
           if (colok) {  // per-column scalars in T (FP64 issues ~60x slower)
             const size_t k = (size_t)t.seg * f.bstride + c;
-            const T pq = __ldcg(a1 + nout + c);
+            const T pq = tot[nout + c];
             const T rho = __ldcg(f.rho + (size_t)par * ss + k);
             const int dn = __ldcg(f.done + (size_t)par * ss + k);
             if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;

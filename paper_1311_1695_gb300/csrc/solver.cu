@@ -199,7 +199,7 @@ struct JD {
       update<TV>(g, T, z.ldv, q, 1.0, -1.0, V, z.ldv, m0, 1, Gm, q, 65 * 64, seg_skip, st);
       gram<TV>(g, red, T, z.ldv, q, T, z.ldv, q, 0, 0, Sm, q, 64 * 64, seg_skip, st);
       chol_inv(z.nseg, q, Sm, 64 * 64, pass == 0 ? drop1 : 0.25, 1, Rinv, 64 * 64, pass == 0 ? keep1 : keep2,
-               seg_skip, st);
+               seg_skip, st, std::is_same<TV, float>::value);
       update<TV>(g, T, z.ldv, q, 0.0, 1.0, T, z.ldv, q, 0, Rinv, q, 64 * 64, seg_skip, st);
     }
     and_flags(z.nseg * 64, keep1, keep2, st);
