@@ -71,10 +71,33 @@ __device__ __forceinline__ void stage(T* dst, const T* __restrict__ src, int ld,
   }
 }
 
-// acc[u] += sum_r [1|As][r, i] * Bs[r, j] for output o = i*q + j.
+// acc[u] += sum_r [1|As][r, i] * Bs[r, j] for output o = i*q + j (oi[u],
+// oj[u] precomputed; oi[u] < 0: no output).  The partial sums stay in T: for
+// an FP32 block no FP64 conversion per chunk (FP64 issues ~60x slower).
 template <typename T, int NO>
 __device__ __forceinline__ void gram_chunk(const T* As, int p, int ones, const T* Bs, int q, int nr,
-                                           double (&acc)[NO]) {
+                                           const int (&oi)[NO], const int (&oj)[NO], T (&acc)[NO]) {
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int i = oi[u], j = oj[u];
+    if (i >= 0) {
+      T s = T(0);
+      if (i < ones) {
+        for (int r = 0; r < nr; ++r) s += Bs[r * q + j];
+      } else {
+        const T* a = As + (i - ones);
+        for (int r = 0; r < nr; ++r) s += a[r * p] * Bs[r * q + j];
+      }
+      acc[u] += s;
+    }
+  }
+}
+
+// The same with FP64 partial sums and the output indices derived per call
+// (the step-by-step correction-solve kernels).
+template <typename T, int NO>
+__device__ __forceinline__ void gram_chunk64(const T* As, int p, int ones, const T* Bs, int q, int nr,
+                                             double (&acc)[NO]) {
   const int nout = (p + ones) * q;
 #pragma unroll
   for (int u = 0; u < NO; ++u) {
@@ -103,25 +126,42 @@ __global__ void __launch_bounds__(kThreads) k_gram(DevGraph g, Reduce red, const
   if (seg_skip && seg_skip[t.seg]) return;
   __shared__ T As[kChunk * kMaxCols];
   __shared__ T Bs[kChunk * kMaxCols];
-  double acc[NO];
+  const int nout = (p + ones) * q;
+  T acc[NO];
+  int oi[NO], oj[NO];
 #pragma unroll
-  for (int u = 0; u < NO; ++u) acc[u] = 0.0;
+  for (int u = 0; u < NO; ++u) {
+    const int o = threadIdx.x + kThreads * u;
+    acc[u] = T(0);
+    oi[u] = o < nout ? o / q : -1;
+    oj[u] = o < nout ? o - (o / q) * q : 0;
+  }
   for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
     const int nr = min(kChunk, t.r1 - c0);
     if (p > 0) stage(As, A, lda, c0, nr, p);
     stage(Bs, B, ldb, c0, nr, q);
     __syncthreads();
-    gram_chunk<T, NO>(As, p, ones, Bs, q, nr, acc);
+    gram_chunk<T, NO>(As, p, ones, Bs, q, nr, oi, oj, acc);
     __syncthreads();
   }
-  const int nout = (p + ones) * q;
-  if (commit<NO>(red, t.seg, seg_tiles(g, t.seg), acc, nout, nullptr, 0)) {
+  double accd[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) accd[u] = (double)acc[u];
+  if (commit<NO>(red, t.seg, seg_tiles(g, t.seg), accd, nout, nullptr, 0)) {
     const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-    for (int o = threadIdx.x; o < nout; o += kThreads) {
-      const int i = o / q, j = o - i * q;
-      double v = total(red, t.seg, o);
-      if (i < ones && ones_mean) v *= inv_n;
-      G[(size_t)t.seg * sg + (size_t)i * ldg + j] = v;
+    double v[NO];  // every total loaded before any is stored
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int o = threadIdx.x + kThreads * u;
+      v[u] = o < nout ? total(red, t.seg, o) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int o = threadIdx.x + kThreads * u;
+      if (o < nout) {
+        const int i = oi[u], j = oj[u];
+        G[(size_t)t.seg * sg + (size_t)i * ldg + j] = (i < ones && ones_mean) ? v[u] * inv_n : v[u];
+      }
     }
     release(red, t.seg, nout);
   }
@@ -142,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_update(DevGraph g, T* Y, int ldy, 
   const double* Sg = S + (size_t)t.seg * ss;
   for (int e = threadIdx.x; e < p1 * q; e += kThreads) {
     const int i = e / q, j = e - i * q;
-    Ss[e] = (T)(alpha * Sg[(size_t)i * lds + j]);
+    Ss[e] = (T)Sg[(size_t)i * lds + j] * (T)alpha;  // no FP64 multiply for an FP32 block
   }
   const T tb = (T)beta;
   for (int c0 = t.r0; c0 < t.r1; c0 += CH) {
@@ -152,11 +192,12 @@ __global__ void __launch_bounds__(kThreads) k_update(DevGraph g, T* Y, int ldy, 
     __syncthreads();
     for (int e = threadIdx.x; e < nr * q; e += kThreads) {
       const int r = e / q, c = e - r * q;
+      T* y = Y + (size_t)(c0 + r) * ldy + c;
+      const T y0 = (beta == 0.0) ? T(0) : tb * *y;  // issued before the dot product, not after it
       T s = ones ? Ss[c] : T(0);
       const T* a = As + r * p;
       for (int i = 0; i < p; ++i) s += a[i] * Ss[(i + ones) * q + c];
-      T* y = Y + (size_t)(c0 + r) * ldy + c;
-      *y = (beta == 0.0) ? s : tb * (*y) + s;
+      *y = y0 + s;
     }
   }
 }
@@ -764,7 +805,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_init(DevGraph g, Reduce red, P
       }
     }
     __syncthreads();
-    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
     __syncthreads();
   }
   reduce_cols<T>(rz, extra, scratch);
@@ -824,7 +865,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_b(DevGraph g, Reduce red, PcgS
       }
     }
     __syncthreads();
-    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
     __syncthreads();
   }
   reduce_cols<T>(pq, extra, scratch);
@@ -895,7 +936,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_c(DevGraph g, Reduce red, PcgS
       }
     }
     __syncthreads();
-    gram_chunk<T, 5>(Xs, b, 1, Zs, b, nr, acc);
+    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
     __syncthreads();
   }
   reduce_cols<T>(rz, extra, scratch);
