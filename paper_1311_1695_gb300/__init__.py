@@ -174,7 +174,7 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.precision = _PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.include_null = int(bool(include_null))
     o.seed = seed
-    o.max_seconds, o.team, o.verbose = max_seconds, team, int(bool(verbose))
+    o.max_seconds, o.team, o.verbose = max_seconds, team, int(verbose)
     o.stream = stream
     o.cuda_graph = 0 if cuda_graph else -1
     keep = None

@@ -402,7 +402,10 @@ int lap_residual_norms(lap_graph* g, int dtype, const void* X, int ldx, const do
       return check_cuda("lap_residual_norms");
     std::vector<double> o((size_t)S * b);
     for (int q = 0; q < S; ++q)
-      for (int c = 0; c < b; ++c) o[(size_t)q * b + c] = std::sqrt(std::max(0.0, h[(size_t)q * 64 + c]));
+      for (int c = 0; c < b; ++c) {  // rounding below zero -> 0; NaN stays NaN
+        const double v = h[(size_t)q * 64 + c];
+        o[(size_t)q * b + c] = v >= 0.0 ? std::sqrt(v) : (v < 0.0 ? 0.0 : v);
+      }
     if (cudaMemcpy(norms, o.data(), sizeof(double) * S * b, cudaMemcpyHostToDevice) != cudaSuccess)
       return check_cuda("lap_residual_norms");
   }

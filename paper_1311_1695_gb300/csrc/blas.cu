@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__
       double ev_ = 0.5 * R[i * LR + j];
       if (i != j) {
         const double num = S[i * LR + j] + lam[j] * R[i * LR + j], gap = lam[j] - lam[i];
-        if (fabs(num) <= 1e-3 * fabs(gap)) ev_ = num / gap;
+        if (fabs(num) < 1e-3 * fabs(gap)) ev_ = num / gap;  // strict: equal Ritz values (gap 0) are a cluster, not 0/0
       }
       S[i * LR + j] = ev_;
     }

@@ -150,7 +150,8 @@ int finish_pairs(lap_graph* G, const double* U, int ldu, int k, std::vector<doub
   bool prefix = true;
   for (int i = 0; i < k; ++i) {
     out.evals[0][i] = lam[ord[i]];
-    const double r = std::sqrt(std::max(0.0, r2[ord[i]])) / G->norm1[0];
+    const double v = r2[ord[i]];  // NaN: never converged
+    const double r = (v >= 0.0 ? std::sqrt(v) : (v < 0.0 ? 0.0 : HUGE_VAL)) / G->norm1[0];
     worst = std::max(worst, r);
     if (prefix && r <= tol) ++nconv; else prefix = false;
   }

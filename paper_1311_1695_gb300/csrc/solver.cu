@@ -37,6 +37,10 @@ namespace {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// ||r|| from a computed ||r||^2: rounding below zero is 0, NaN is +inf (never
+// converged)
+inline double res_norm(double r2) { return r2 >= 0.0 ? std::sqrt(r2) : (r2 < 0.0 ? 0.0 : HUGE_VAL); }
+
 // Bump allocator over one device allocation.
 struct Arena {
   char* base = nullptr;
@@ -86,6 +90,7 @@ struct JD {
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
+  double* oacc;  // accumulators of the fused orthonormalisation
   PcgState ps;
   // host mirrors
   std::vector<double> rn2_h, theta_h;
@@ -94,6 +99,13 @@ struct JD {
   int inner_its = 0;
   int last_nact = 0;  // columns corrected by the last correction solve
   bool inject = false;  // next expansion adds random directions (stagnation)
+  // The restart recomputes the kept block of H as V^T W instead of taking
+  // diag(theta) (always for an FP64 basis, else after stagnation): with a
+  // near-degenerate cluster diag(theta) can carry a Ritz value that is off by
+  // ~1e-7 (a value below the cluster's eigenvalue was seen), and its error
+  // (rho(x) - theta) x lies in span(V), which the correction equation
+  // projects out, so only a fresh projected matrix removes it.
+  bool explicit_h = std::is_same<TV, double>::value;
   int injections = 0;
   PcgWork* pw = nullptr;
   // device-side convergence state (one outer iteration replays as a graph)
@@ -133,6 +145,7 @@ struct JD {
     for (int i = 0; i < 5; ++i) add(S * 64 * 8);
     add(S * 33 * 32 * 8); add(S * 33 * 32 * 8); add(S * 64 * 4);
     add(S * 4); add(S * 8); add(sizeof(JdStatus)); add(S * 8);
+    add(ortho_acc_doubles((int)S) * 8);
     return b + 4096;
   }
 
@@ -161,6 +174,8 @@ struct JD {
     tmp = a.take<double>(S * 64);
     keep1 = a.take<int>(S * 64);
     keep2 = a.take<int>(S * 64);
+    oacc = a.take<double>(ortho_acc_doubles(S));
+    cudaMemsetAsync(oacc, 0, sizeof(double) * ortho_acc_doubles(S), st);
     active = a.take<int>(S * 64);
     seg_skip = a.take<int>(S * 64);
     sweeps = a.take<int>(S * 64);
@@ -189,6 +204,8 @@ struct JD {
 
   // CGS2 of columns [m0, m0+q) of V against [e, V[:, 0:m0]]; keep1 = surviving columns.
   void ortho(int m0, int q, double drop1) {
+    const GridBar bar{pw->bar, pw->bar + 1, reinterpret_cast<int*>(pw->bar + 2)};
+    if (ortho_fused<TV>(g, V, z.ldv, m0, q, drop1, oacc, keep1, seg_skip, bar, st) == 0) return;
     TV* T = V + m0;
     // unit-normalise the columns
     coldots<TV>(g, red, T, z.ldv, T, z.ldv, q, tmp, 64, seg_skip, st);
@@ -242,13 +259,16 @@ struct JD {
   // One Rayleigh-Ritz + restart on a basis of m columns; returns the new size.
   int rayleigh_ritz(int m) {
     // only the mk kept Ritz pairs are refined to FP64 accuracy (one step
-    // from the FP32 Jacobi result); H restarts as diag(theta[0:mk])
+    // from the FP32 Jacobi result); H restarts as diag(theta[0:mk]), or as
+    // V^T W over the kept columns (explicit_h)
     const int mk = std::min(m, z.mk);
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
          seg_skip, sweeps, st, mk);
     update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     update<TV>(g, W, z.ldv, mk, 0.0, 1.0, W, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
+    if (explicit_h)
+      gram<TV>(g, red, V, z.ldv, mk, W, z.ldv, mk, 0, 0, H, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     return mk;
   }
 
@@ -361,7 +381,15 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
   while (true) {
     const JdStatus stt = *jd.status_h;
     if (stt.bad) { set_error("NaN/Inf residual in JD"); return LAP_ENUMERIC; }
-    if (P.verbose) fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, stt.worst);
+    if (P.verbose) {
+      fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, stt.worst);
+      if (P.verbose > 1) {  // graph 0's Ritz values and residual norms
+        std::vector<double> th(jd.z.b), r2(jd.z.b);
+        cudaMemcpy(th.data(), jd.theta, sizeof(double) * jd.z.b, cudaMemcpyDeviceToHost);
+        cudaMemcpy(r2.data(), jd.rn2, sizeof(double) * jd.z.b, cudaMemcpyDeviceToHost);
+        for (int j = 0; j < jd.z.b; ++j) fprintf(stderr, "    theta %.12f  ||r|| %.3e\n", th[j], std::sqrt(std::max(0.0, r2[j])));
+      }
+    }
     bool all = stt.all_done != 0;
     if (stt.candidates > 0) {
       // explicit check of the candidates: L X formed afresh (eager)
@@ -378,7 +406,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
         if (jd.state_h[s] == 2) {
           bool segc = true;
           for (int j = 0; j < P.k; ++j) {
-            const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j]));
+            const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
             const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
             segc = segc && c;
             act[(size_t)s * 64 + j] = c ? 0 : 1;
@@ -396,6 +424,11 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     const double worst = stt.worst;
     if (worst < 0.5 * best) { best = worst; stag = 0; }
     else if (++stag >= 20) { jd.inject = true; stag = 0; }
+    if (stag == 8 && !jd.explicit_h) {  // from now on the explicit restart (the graph is re-captured)
+      jd.explicit_h = true;
+      if (jd.graph_exec) { cudaGraphExecDestroy(jd.graph_exec); jd.graph_exec = nullptr; }
+      if (jd.graph) { cudaGraphDestroy(jd.graph); jd.graph = nullptr; }
+    }
     bool all_stalled = true;
     for (int s = 0; s < S; ++s) {
       if (jd.state_h[s] == 1) continue;
@@ -500,7 +533,7 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     int nconv = 0;
     bool prefix = true;
     for (int j = 0; j < P.k; ++j) {
-      const double r = std::sqrt(std::max(0.0, jd.rn2_h[(size_t)s * 64 + j])) / G->norm1[s];
+      const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]) / G->norm1[s];
       const bool real = jd.theta_h[(size_t)s * jd.z.mmax + j] <= G->norm1[s];
       worst = std::max(worst, real ? r : 1.0);
       if (prefix && real && r <= P.tol) ++nconv; else prefix = false;
