@@ -52,6 +52,17 @@ def test_closed_forms(pkg, make, k, precision):
     _solve_and_check(pkg, g, k, precision)
 
 
+@pytest.mark.parametrize("seed", [1, 2, 4, 7])
+def test_degenerate_cluster_seeds(pkg, seed):
+    """hypercube(8): the eigenvalue 2 of multiplicity 8 straddles k = 6.  Seeds
+    for which an FP64 solve once stalled (a Ritz value of the restarted
+    diag(theta) off by ~1e-7, its error inside span(V)) must converge, with
+    finite vectors."""
+    g = G.hypercube(8)
+    info, _ = _solve_and_check(pkg, g, 6, "fp64", seed=seed)
+    assert info["outer_its"] < 100
+
+
 def test_path_closed_form_values(pkg):
     n = 500
     ev, V, info = pkg.lap_eigs(G.path_graph(n), 5, tol=1e-8)
