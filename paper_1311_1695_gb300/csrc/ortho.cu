@@ -77,30 +77,31 @@ __device__ bool obar(const GridBar& bar) {
   return s_ok != 0;
 }
 
-// rows [r0, r0 + nr) x cols [0, w) of a row-major block into dst (row stride w)
+// rows [r0, r0 + nr) x cols [0, w) of a row-major block into dst (row stride
+// w), nr <= kCh, w <= 64: warp w_ takes rows w_, w_ + 8, ..., lane c columns
+// c and c + 32; the loads of a thread go out together (no index division)
 template <typename T>
 __device__ __forceinline__ void stage_rows(T* dst, const T* src, int ld, int r0, int nr, int w) {
-  constexpr int U = 4;
-  const int n = nr * w;
-  for (int e0 = threadIdx.x; e0 < n; e0 += kThreads * U) {
-    T v[U];
+  constexpr int RPW = kCh / (kThreads / 32);  // rows per warp
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  T v[RPW][2];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = min(e0 + u * kThreads, n - 1);
-      const int r = e / w;
-      v[u] = src[(size_t)(r0 + r) * ld + (e - r * w)];
+  for (int i = 0; i < RPW; ++i) {
+    const int r = min(wp + 8 * i, nr - 1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      v[i][h] = src[(size_t)(r0 + r) * ld + (c < w ? c : 0)];
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (e0 + u * kThreads < n) dst[e0 + u * kThreads] = v[u];
   }
-}
-
-template <typename T>
-__device__ __forceinline__ void write_rows(T* dstg, int ld, const T* src, int r0, int nr, int w) {
-  for (int e = threadIdx.x; e < nr * w; e += kThreads) {
-    const int r = e / w;
-    dstg[(size_t)(r0 + r) * ld + (e - r * w)] = src[e];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = wp + 8 * i;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      if (r < nr && c < w) dst[r * w + c] = v[i][h];
+    }
   }
 }
 
@@ -199,12 +200,12 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
       __syncthreads();
       const T y = s_rinv[j];
       for (int i = j + 1 + tid; i < q; i += kThreads) Ss[i * (kQ + 1) + j] = Ss[j * (kQ + 1) + i] * y;
-      if (s_kp[j]) {
+      if (s_kp[j]) {  // warp: rows i, lane: column l >= i
         const T y2 = y * y;
-        const int m = q - j - 1;
-        for (int e = tid; e < m * m; e += kThreads) {
-          const int i = j + 1 + e / m, l = j + 1 + e % m;
-          if (l >= i) Ss[i * (kQ + 1) + l] -= Ss[j * (kQ + 1) + i] * Ss[j * (kQ + 1) + l] * y2;
+        const int l = j + 1 + (tid & 31);
+        if (l < q) {
+          const T sl = Ss[j * (kQ + 1) + l] * y2;
+          for (int i = j + 1 + (tid >> 5); i <= l; i += kThreads / 32) Ss[i * (kQ + 1) + l] -= Ss[j * (kQ + 1) + i] * sl;
         }
       }
       __syncthreads();
@@ -229,24 +230,40 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
     }
     __syncthreads();
   };
-  // Bs <- Bs - [1|As] Gs over nr staged rows (each element by one thread, in place)
+  // Row-wise passes over the nr staged rows: a group of QW = pow2 >= q lanes
+  // takes a row (lane c: column c), 32 / QW rows per warp pass.
+  int qsh = 0;
+  while ((1 << qsh) < q) ++qsh;
+  const int gl = (tid & 31) & ((1 << qsh) - 1);              // column
+  const int gr = ((tid & 31) >> qsh) + (tid >> 5) * (32 >> qsh);  // first row
+  const int gstep = (kThreads / 32) * (32 >> qsh);           // rows per CTA pass
+  // Bs <- Bs - [1|As] Gs (each element by one thread, in place)
   auto project = [&](int nr) {
-    for (int e = tid; e < nr * q; e += kThreads) {
-      const int r = e / q, c = e - r * q;
-      T s = Gs[c];
+    if (gl >= q) return;
+    for (int r = gr; r < nr; r += gstep) {
+      T s = Gs[gl];
       const T* x = As + r * m0;
-      for (int i = 0; i < m0; ++i) s += x[i] * Gs[(i + 1) * q + c];
-      Bs[e] -= s;
+      for (int i = 0; i < m0; ++i) s += x[i] * Gs[(i + 1) * q + gl];
+      Bs[r * q + gl] -= s;
     }
   };
   // Cs <- Bs R^-1 (R^-1 in Gs, upper triangular)
   auto apply_rinv = [&](int nr) {
-    for (int e = tid; e < nr * q; e += kThreads) {
-      const int r = e / q, c = e - r * q;
+    if (gl >= q) return;
+    for (int r = gr; r < nr; r += gstep) {
       T s = T(0);
-      for (int j = 0; j <= c; ++j) s += Bs[r * q + j] * Gs[j * q + c];
-      Cs[e] = s;
+      for (int j = 0; j <= gl; ++j) s += Bs[r * q + j] * Gs[j * q + gl];
+      Cs[r * q + gl] = s;
     }
+  };
+  auto scale_rows = [&](int nr) {
+    if (gl >= q) return;
+    for (int r = gr; r < nr; r += gstep) Bs[r * q + gl] *= s_scale[gl];
+  };
+  // staged rows (q columns) back to T
+  auto write_back = [&](const T* src, int r0, int nr) {
+    if (gl >= q) return;
+    for (int r = gr; r < nr; r += gstep) Tb[(size_t)(r0 + r) * ldv + gl] = src[r * q + gl];
   };
 
   // ------------------------------------------------------------ P0: norms
@@ -302,9 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
         if (m0 > 0) stage_rows(As, V, ldv, r0, nr, m0);
         stage_rows(Bs, Tb, ldv, r0, nr, q);
         __syncthreads();
-        for (int e = tid; e < nr * q; e += kThreads) Bs[e] *= s_scale[e % q];
+        scale_rows(nr);
         __syncthreads();
-        write_rows(Tb, ldv, Bs, r0, nr, q);
+        write_back(Bs, r0, nr);
         gram_rows(As, m0, 1, Bs, nr);
       }
     }
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
         __syncthreads();
         project(nr);
         __syncthreads();
-        write_rows(Tb, ldv, Bs, r0, nr, q);
+        write_back(Bs, r0, nr);
         gram_rows(Bs, q, 0, Bs, nr);
       }
     }
@@ -375,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
         __syncthreads();
         apply_rinv(nr);
         __syncthreads();
-        write_rows(Tb, ldv, Cs, r0, nr, q);
+        write_back(Cs, r0, nr);
         if (gram_next) gram_rows(As, m0, 1, Cs, nr);
       }
     }
