@@ -78,7 +78,7 @@ typedef struct {
   double max_seconds; /* wall-clock cap (0 = none) -> LAP_ETIMEOUT */
   int team;           /* SpMM lanes per row: 4, 8, 16, 32; 0 = degree heuristic;
                          -1 = autotune on the graph (timed trial launches) */
-  int verbose;        /* 1: per-iteration log on stderr */
+  int verbose;        /* 1: per-iteration log on stderr; 2: also graph 0's Ritz values and residual norms */
   const double* x0_dev; /* optional device warm start, row-major n x k0 (ld = ldx0), FP64;
                            used instead of x0 when set (single-graph solves) */
   int ldx0;
