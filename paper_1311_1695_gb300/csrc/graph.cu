@@ -14,21 +14,40 @@ namespace lapeig {
 
 namespace {
 
-template <typename T>
-int dev_alloc_copy(T** dst, const T* src, size_t count) {
-  *dst = nullptr;
-  if (count == 0) return LAP_OK;
-  if (cudaMalloc(reinterpret_cast<void**>(dst), count * sizeof(T)) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("cudaMalloc failed in graph set-up");
-    return LAP_ENOMEM;
+// Several device arrays carved from one allocation, filled by one copy from a
+// host staging buffer (arrays without a source are zero): graph set-up costs
+// one cudaMalloc and one cudaMemcpy instead of one pair per array.
+struct Packer {
+  struct Item { void** dst; const void* src; size_t bytes, off; };
+  std::vector<Item> items;
+  size_t total = 0;
+  template <typename T>
+  void add(T** dst, const T* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return;
+    total = (total + 255) / 256 * 256;
+    items.push_back({reinterpret_cast<void**>(dst), src, count * sizeof(T), total});
+    total += count * sizeof(T);
   }
-  if (src && cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
-    set_error("cudaMemcpy failed in graph set-up");
-    return LAP_ECUDA;
+  int upload(void** block) {
+    *block = nullptr;
+    if (total == 0) return LAP_OK;
+    if (cudaMalloc(block, total) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc failed in graph set-up");
+      return LAP_ENOMEM;
+    }
+    std::vector<char> h(total, 0);
+    for (const Item& it : items)
+      if (it.src) std::memcpy(h.data() + it.off, it.src, it.bytes);
+    if (cudaMemcpy(*block, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+      set_error("cudaMemcpy failed in graph set-up");
+      return LAP_ECUDA;
+    }
+    for (const Item& it : items) *it.dst = static_cast<char*>(*block) + it.off;
+    return LAP_OK;
   }
-  return LAP_OK;
-}
+};
 
 int validate(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w) {
   if (n < 1 || !rowptr || (!colidx && rowptr[n] > 0)) {
@@ -81,8 +100,8 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     const int da = g->rowptr_h[a + 1] - g->rowptr_h[a], db = g->rowptr_h[b + 1] - g->rowptr_h[b];
     return da != db ? da > db : a < b;
   });
-  cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks);
-  cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part); cudaFree(g->d_erp);
+  cudaFree(g->d_sched);
+  g->d_sched = nullptr;
   g->d_long = nullptr; g->d_long_seg = nullptr; g->d_chunks = nullptr; g->d_hub_chunks = nullptr;
   g->d_hub_cnt = nullptr; g->d_hub_part = nullptr; g->d_erp = nullptr;
   std::vector<int> erp((size_t)n + 1, 0);
@@ -101,18 +120,16 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     hub_chunks[h] = make_int2((int)chunks.size(), (p1 - p0 + kHubChunk - 1) / kHubChunk);
     for (int p = p0; p < p1; p += kHubChunk) chunks.push_back(make_int4(r, p, std::min(p + kHubChunk, p1), (int)h));
   }
-  int rc = dev_alloc_copy(&g->d_long, hubs.data(), hubs.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_long_seg, hseg.data(), hseg.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_chunks, chunks.data(), chunks.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_hub_chunks, hub_chunks.data(), hub_chunks.size());
-  rc = rc ? rc : dev_alloc_copy<int>(&g->d_hub_cnt, nullptr, hubs.size());
-  rc = rc ? rc : dev_alloc_copy<double>(&g->d_hub_part, nullptr, chunks.size() * kPartStride);
-  rc = rc ? rc : dev_alloc_copy(&g->d_erp, erp.data(), erp.size());
+  Packer pk;  // hub counters start at zero (no source)
+  pk.add(&g->d_long, hubs.data(), hubs.size());
+  pk.add(&g->d_long_seg, hseg.data(), hseg.size());
+  pk.add(&g->d_chunks, chunks.data(), chunks.size());
+  pk.add(&g->d_hub_chunks, hub_chunks.data(), hub_chunks.size());
+  pk.add<int>(&g->d_hub_cnt, nullptr, hubs.size());
+  pk.add<double>(&g->d_hub_part, nullptr, chunks.size() * kPartStride);
+  pk.add(&g->d_erp, erp.data(), erp.size());
+  const int rc = pk.upload(&g->d_sched);
   if (rc) return rc;
-  if (!hubs.empty() && cudaMemset(g->d_hub_cnt, 0, sizeof(int) * hubs.size()) != cudaSuccess) {
-    set_error("cudaMemset failed");
-    return LAP_ECUDA;
-  }
   g->long_rows_h = hubs;
   g->dg.long_rows = g->d_long;
   g->dg.nlong = (int)hubs.size();
@@ -233,30 +250,24 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 
   std::vector<float> w32(w64.begin(), w64.end());
   std::vector<float> deg32(deg.begin(), deg.end());
-  int rc = LAP_OK;
-  rc = rc ? rc : dev_alloc_copy(&g->d_rowptr, g->rowptr_h.data(), g->rowptr_h.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_colidx, colcat.data(), colcat.size());
+  Packer pk;
+  pk.add(&g->d_rowptr, g->rowptr_h.data(), g->rowptr_h.size());
+  pk.add(&g->d_colidx, colcat.data(), colcat.size());
   if (weighted) {
-    rc = rc ? rc : dev_alloc_copy(&g->d_w64, w64.data(), w64.size());
-    rc = rc ? rc : dev_alloc_copy(&g->d_w32, w32.data(), w32.size());
+    pk.add(&g->d_w64, w64.data(), w64.size());
+    pk.add(&g->d_w32, w32.data(), w32.size());
   }
-  rc = rc ? rc : dev_alloc_copy(&g->d_deg64, deg.data(), deg.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_deg32, deg32.data(), deg32.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_row0, g->row0.data(), g->row0.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_norm1, g->norm1.data(), g->norm1.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_tiles, tiles.data(), tiles.size());
-  rc = rc ? rc : dev_alloc_copy(&g->d_tile_ptr, g->tile_ptr.data(), g->tile_ptr.size());
-  // reduction scratch, zero at rest
+  pk.add(&g->d_deg64, deg.data(), deg.size());
+  pk.add(&g->d_deg32, deg32.data(), deg32.size());
+  pk.add(&g->d_row0, g->row0.data(), g->row0.size());
+  pk.add(&g->d_norm1, g->norm1.data(), g->norm1.size());
+  pk.add(&g->d_tiles, tiles.data(), tiles.size());
+  pk.add(&g->d_tile_ptr, g->tile_ptr.data(), g->tile_ptr.size());
+  // reduction scratch, zero at rest (no source: zero-filled)
   g->red.stride = 4608;
-  rc = rc ? rc : dev_alloc_copy<double>(&g->red.acc, nullptr, (size_t)nb * g->red.stride);
-  rc = rc ? rc : dev_alloc_copy<int>(&g->red.counter, nullptr, (size_t)nb);
-  if (rc == LAP_OK) {
-    if (cudaMemset(g->red.acc, 0, sizeof(double) * (size_t)nb * g->red.stride) != cudaSuccess ||
-        cudaMemset(g->red.counter, 0, sizeof(int) * (size_t)nb) != cudaSuccess) {
-      set_error("cudaMemset failed");
-      rc = LAP_ECUDA;
-    }
-  }
+  pk.add<double>(&g->red.acc, nullptr, (size_t)nb * g->red.stride);
+  pk.add<int>(&g->red.counter, nullptr, (size_t)nb);
+  int rc = pk.upload(&g->d_block);
   if (rc) { graph_free(g); return rc; }
 
   DevGraph& d = g->dg;
@@ -285,11 +296,8 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 
 void graph_free(lap_graph* g) {
   if (!g) return;
-  cudaFree(g->d_rowptr); cudaFree(g->d_colidx); cudaFree(g->d_w32); cudaFree(g->d_w64);
-  cudaFree(g->d_deg64); cudaFree(g->d_norm1); cudaFree(g->d_deg32); cudaFree(g->d_row0); cudaFree(g->d_tiles);
-  cudaFree(g->d_tile_ptr); cudaFree(g->d_long); cudaFree(g->d_long_seg); cudaFree(g->red.acc); cudaFree(g->red.counter);
-  cudaFree(g->d_chunks); cudaFree(g->d_hub_chunks); cudaFree(g->d_hub_cnt); cudaFree(g->d_hub_part);
-  cudaFree(g->d_erp);
+  cudaFree(g->d_block);  // every array of the graph
+  cudaFree(g->d_sched);  // the hub schedule
   cudaFree(g->scratch); cudaFree(g->small);
   g->pcg.release();
   delete g;

@@ -43,6 +43,8 @@ struct lap_graph {
   lapeig::HostGraph hg{};
   lapeig::Reduce red{};
   // device allocations owned by the handle
+  void* d_block = nullptr;   // one allocation holding the arrays below up to red (Packer)
+  void* d_sched = nullptr;   // one allocation holding the hub schedule arrays
   int* d_rowptr = nullptr;
   int* d_colidx = nullptr;
   float* d_w32 = nullptr;

@@ -26,6 +26,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 #include "prof.h"
@@ -37,17 +40,104 @@ namespace {
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Small pinned host buffers (the per-iteration status block and its
+// companions), kept in a process-wide free list: cudaMallocHost and
+// cudaFreeHost cost far more than a solve's use of them.  A buffer goes back
+// to the list only after its stream has been synchronised.
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<void*, size_t>> free_list;
+  std::vector<std::pair<void*, size_t>> all;
+  void* get(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    std::lock_guard<std::mutex> lock(mu);
+    for (size_t i = 0; i < free_list.size(); ++i)
+      if (free_list[i].second >= bytes) {
+        void* p = free_list[i].first;
+        free_list.erase(free_list.begin() + (long)i);
+        return p;
+      }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    all.push_back({p, bytes});
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& a : all)
+      if (a.first == p) { free_list.push_back(a); return; }
+  }
+};
+PinnedPool& pinned() {
+  static PinnedPool* pool = new PinnedPool();  // lives as long as the process
+  return *pool;
+}
+
 // ||r|| from a computed ||r||^2: rounding below zero is 0, NaN is +inf (never
 // converged)
 inline double res_norm(double r2) { return r2 >= 0.0 ? std::sqrt(r2) : (r2 < 0.0 ? 0.0 : HUGE_VAL); }
+
+// Solver workspaces, kept in a small process-wide free list (best fit, at
+// most 8 blocks): a solve's cudaMalloc and cudaFree (which synchronises the
+// device) cost more than reusing the last solve's block.  A block returns to
+// the list only after the solve that used it has synchronised its stream
+// (the JD objects, destroyed first, do so).
+struct DevicePool {
+  std::mutex mu;
+  std::vector<std::pair<void*, size_t>> free_list;
+  std::vector<std::pair<void*, size_t>> all;
+  void* get(size_t bytes) {
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      long best = -1;
+      for (size_t i = 0; i < free_list.size(); ++i)
+        if (free_list[i].second >= bytes && (best < 0 || free_list[i].second < free_list[(size_t)best].second))
+          best = (long)i;
+      if (best >= 0 && free_list[(size_t)best].second <= 2 * bytes + (64u << 20)) {
+        void* p = free_list[(size_t)best].first;
+        free_list.erase(free_list.begin() + best);
+        return p;
+      }
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    all.push_back({p, bytes});
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(mu);
+    for (size_t i = 0; i < all.size(); ++i)
+      if (all[i].first == p) {
+        free_list.push_back(all[i]);
+        break;
+      }
+    while (free_list.size() > 8) {  // release the smallest
+      size_t k = 0;
+      for (size_t i = 1; i < free_list.size(); ++i)
+        if (free_list[i].second < free_list[k].second) k = i;
+      void* q = free_list[k].first;
+      free_list.erase(free_list.begin() + (long)k);
+      for (size_t i = 0; i < all.size(); ++i)
+        if (all[i].first == q) { all.erase(all.begin() + (long)i); break; }
+      cudaFree(q);
+    }
+  }
+};
+DevicePool& device_pool() {
+  static DevicePool* pool = new DevicePool();  // lives as long as the process
+  return *pool;
+}
 
 // Bump allocator over one device allocation.
 struct Arena {
   char* base = nullptr;
   size_t size = 0, used = 0;
   int init(size_t bytes) {
-    if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
-      cudaGetLastError();
+    base = static_cast<char*>(device_pool().get(bytes));
+    if (!base) {
       set_error("device workspace allocation failed");
       return LAP_ENOMEM;
     }
@@ -61,7 +151,7 @@ struct Arena {
     used += count * sizeof(T);
     return p;
   }
-  ~Arena() { cudaFree(base); }
+  ~Arena() { device_pool().put(base); }
 };
 
 struct Sizes {
@@ -124,9 +214,10 @@ struct JD {
   ~JD() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     if (graph) cudaGraphDestroy(graph);
-    if (status_h) cudaFreeHost(status_h);
-    if (state_h) cudaFreeHost(state_h);
-    if (segw_h) cudaFreeHost(segw_h);
+    cudaStreamSynchronize(st);  // no copy into the pinned buffers still in flight
+    pinned().put(status_h);
+    pinned().put(state_h);
+    pinned().put(segw_h);
   }
   JD(const JD&) = delete;
   JD& operator=(const JD&) = delete;
@@ -192,10 +283,10 @@ struct JD {
     state = a.take<int>(S);
     tol_d = a.take<double>(S);
     status_d = a.take<JdStatus>(1);
-    if (cudaMallocHost(reinterpret_cast<void**>(&status_h), sizeof(JdStatus)) != cudaSuccess) status_h = nullptr;
-    if (cudaMallocHost(reinterpret_cast<void**>(&state_h), sizeof(int) * S) != cudaSuccess) state_h = nullptr;
+    status_h = static_cast<JdStatus*>(pinned().get(sizeof(JdStatus)));
+    state_h = static_cast<int*>(pinned().get(sizeof(int) * S));
     segw = a.take<double>(S);
-    if (cudaMallocHost(reinterpret_cast<void**>(&segw_h), sizeof(double) * S) != cudaSuccess) segw_h = nullptr;
+    segw_h = static_cast<double*>(pinned().get(sizeof(double) * S));
     rn2_h.assign(S * 64, 0.0);
     theta_h.assign(S * z.mmax, 0.0);
     active_h.assign(S * 64, 1);
