@@ -68,16 +68,24 @@ int validate(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
       if (w && !(std::isfinite(w[p]) && w[p] > 0.0)) { set_error("weight not finite and positive"); return LAP_EWEIGHT; }
     }
   }
-  // symmetry: (i, j, w) needs (j, i, w)
-  for (int64_t i = 0; i < n; ++i) {
+  // symmetry: (i, j, w) needs (j, i, w).  The transpose by a counting sort
+  // (rows visited in order, so each transposed row comes out sorted) must
+  // equal the matrix itself: sequential passes instead of a binary search
+  // per nonzero in another row.
+  std::vector<int64_t> next(rowptr, rowptr + n);
+  std::vector<int32_t> tcol((size_t)nnz);
+  std::vector<double> tw(w ? (size_t)nnz : 0);
+  for (int64_t i = 0; i < n; ++i)
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
       const int64_t j = colidx[p];
-      const int32_t* b = colidx + rowptr[j];
-      const int32_t* e = colidx + rowptr[j + 1];
-      const int32_t* f = std::lower_bound(b, e, (int32_t)i);
-      if (f == e || *f != i) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
-      if (w && w[rowptr[j] + (f - b)] != w[p]) { set_error("adjacency values not symmetric"); return LAP_ENOTSYM; }
+      const int64_t q = next[j]++;
+      if (q >= rowptr[j + 1]) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
+      tcol[q] = (int32_t)i;
+      if (w) tw[q] = w[p];
     }
+  for (int64_t q = 0; q < nnz; ++q) {
+    if (tcol[q] != colidx[q]) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
+    if (w && tw[q] != w[q]) { set_error("adjacency values not symmetric"); return LAP_ENOTSYM; }
   }
   return LAP_OK;
 }
