@@ -72,6 +72,29 @@ def test_rejects_asymmetric(lib):
     assert _call(bad) == pkg.LAP_ENOTSYM
 
 
+def test_rejects_asymmetric_values_and_counts(lib):
+    """The symmetry check (a counting-sort transpose compared with the matrix):
+    equal patterns with unequal weights, and a row with an extra one-way edge
+    whose row counts still add up, are both rejected; a symmetric weighted
+    graph passes the host checks."""
+    g = G.with_random_weights(G.cycle_graph(8), 3)
+    g.weights = g.weights.copy()
+    g.weights[0] *= 2.0  # (0, 1) no longer equals (1, 0)
+    assert _call(g) == pkg.LAP_ENOTSYM
+    # edges 0->1, 1->2, 2->0 only one way: every row has one entry, the sum
+    # matches, the transpose does not
+    one_way = G.CSRGraph(3, np.array([0, 1, 2, 3]), np.array([1, 2, 0], dtype=np.int32), None)
+    assert _call(one_way, k=1) == pkg.LAP_ENOTSYM
+    # a hub row with a missing reverse entry
+    star = G.csr_from_edges(6, [0, 0, 0, 0, 0], [1, 2, 3, 4, 5])
+    rp, ci = star.rowptr.copy(), star.colidx.copy()
+    keep = np.ones(ci.size, bool)
+    keep[rp[3]] = False  # drop (3, 0)
+    rp2 = rp.copy()
+    rp2[4:] -= 1
+    assert _call(G.CSRGraph(6, rp2, ci[keep], None)) == pkg.LAP_ENOTSYM
+
+
 def test_rejects_bad_weight(lib):
     g = G.with_random_weights(G.cycle_graph(8), 1)
     g.weights = g.weights.copy()
