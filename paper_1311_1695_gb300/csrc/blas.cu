@@ -93,29 +93,6 @@ __device__ __forceinline__ void gram_chunk(const T* As, int p, int ones, const T
   }
 }
 
-// The same with FP64 partial sums and the output indices derived per call
-// (the step-by-step correction-solve kernels).
-template <typename T, int NO>
-__device__ __forceinline__ void gram_chunk64(const T* As, int p, int ones, const T* Bs, int q, int nr,
-                                             double (&acc)[NO]) {
-  const int nout = (p + ones) * q;
-#pragma unroll
-  for (int u = 0; u < NO; ++u) {
-    const int o = threadIdx.x + kThreads * u;
-    if (o < nout) {
-      const int i = o / q, j = o - (o / q) * q;
-      T s = T(0);
-      if (i < ones) {
-        for (int r = 0; r < nr; ++r) s += Bs[r * q + j];
-      } else {
-        const T* a = As + (i - ones);
-        for (int r = 0; r < nr; ++r) s += a[r * p] * Bs[r * q + j];
-      }
-      acc[u] += (double)s;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ Gram
 template <typename T, int NO>
 __global__ void __launch_bounds__(kThreads) k_gram(DevGraph g, Reduce red, const T* __restrict__ A, int lda,
@@ -752,251 +729,6 @@ __global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__
   if (sweeps_out && tid == 0) sweeps_out[seg] = sw;
 }
 
-// ------------------------------------------------------------------ projected PCG passes
-// Elementwise phases map lane -> column (b <= 32) and warp -> row in the chunk.
-
-template <typename T>
-__device__ __forceinline__ void reduce_cols(double v, double* out /*smem [32]*/, double (&scratch)[kThreads / 32][32]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  scratch[warp][lane] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double s = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) s += scratch[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-// init: RES = -R (active columns), T = 0, z~ = RES / d; G2 = [1|X]^T z~,
-// rho = RES . z~, res0 = ||RES||.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pcg_init(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
-                                                       int ldx, const T* __restrict__ R, int ldr, T* Tt, T* RES, T* Z,
-                                                       int ld, int b, const int* __restrict__ active,
-                                                       const int* __restrict__ seg_skip) {
-  const Tile t = g.tiles[blockIdx.x];
-  if (seg_skip && seg_skip[t.seg]) return;
-  const T* deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
-  __shared__ T Xs[kChunk * 32];
-  __shared__ T Zs[kChunk * 32];
-  __shared__ double scratch[kThreads / 32][32];
-  __shared__ double extra[64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool act = lane < b && (active == nullptr || active[(size_t)t.seg * st.bstride + lane]);
-  double rz = 0.0, rr = 0.0;
-  double acc[5];
-#pragma unroll
-  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
-  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
-    const int nr = min(kChunk, t.r1 - c0);
-    stage(Xs, X, ldx, c0, nr, b);
-    for (int r = warp; r < nr; r += kThreads / 32) {
-      if (lane < b) {
-        const size_t o = (size_t)(c0 + r) * ld + lane;
-        const T res = act ? -R[(size_t)(c0 + r) * ldr + lane] : T(0);
-        const T z = res / deg[c0 + r];
-        RES[o] = res;
-        Tt[o] = T(0);
-        Z[o] = z;
-        Zs[r * b + lane] = z;
-        rz += (double)res * (double)z;
-        rr += (double)res * (double)res;
-      }
-    }
-    __syncthreads();
-    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
-    __syncthreads();
-  }
-  reduce_cols<T>(rz, extra, scratch);
-  reduce_cols<T>(rr, extra + 32, scratch);
-  // pack the extras into [0, b) and [b, 2b)
-  __shared__ double ex2[64];
-  if (threadIdx.x < b) { ex2[threadIdx.x] = extra[threadIdx.x]; ex2[b + threadIdx.x] = extra[32 + threadIdx.x]; }
-  __syncthreads();
-  const int nout = (b + 1) * b;
-  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, ex2, 2 * b)) {
-    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-    double* G2 = st.G2 + (size_t)t.seg * st.gstride;
-    for (int o = threadIdx.x; o < nout; o += kThreads) G2[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
-    if (threadIdx.x < b) {
-      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
-      const double rho = total(red, t.seg, nout + threadIdx.x);
-      const double r0 = sqrt(total(red, t.seg, nout + b + threadIdx.x));
-      st.rho[k] = rho;
-      st.res0[k] = r0;
-      st.resn[k] = r0;
-      st.beta[k] = 0.0;
-      st.alpha[k] = 0.0;
-      st.done[k] = (r0 == 0.0 || rho == 0.0 || !isfinite(rho)) ? 1 : 0;
-    }
-    release(red, t.seg, nout + 2 * b);
-  }
-}
-
-// pass B: q~ = AP - theta P;  G1 = [1|X]^T q~,  pq = P . q~;  alpha = rho / pq.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pcg_b(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
-                                                    int ldx, const T* __restrict__ P, const T* __restrict__ AP, int ld,
-                                                    int b, const double* __restrict__ theta, int64_t sth,
-                                                    const int* __restrict__ seg_skip) {
-  const Tile t = g.tiles[blockIdx.x];
-  if (seg_skip && seg_skip[t.seg]) return;
-  __shared__ T Xs[kChunk * 32];
-  __shared__ T Zs[kChunk * 32];
-  __shared__ double scratch[kThreads / 32][32];
-  __shared__ double extra[32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const T th = lane < b ? (T)theta[(size_t)t.seg * sth + lane] : T(0);
-  double pq = 0.0;
-  double acc[5];
-#pragma unroll
-  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
-  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
-    const int nr = min(kChunk, t.r1 - c0);
-    stage(Xs, X, ldx, c0, nr, b);
-    for (int r = warp; r < nr; r += kThreads / 32) {
-      if (lane < b) {
-        const size_t o = (size_t)(c0 + r) * ld + lane;
-        const T p = P[o];
-        const T q = AP[o] - th * p;
-        Zs[r * b + lane] = q;
-        pq += (double)p * (double)q;
-      }
-    }
-    __syncthreads();
-    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
-    __syncthreads();
-  }
-  reduce_cols<T>(pq, extra, scratch);
-  const int nout = (b + 1) * b;
-  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, extra, b)) {
-    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-    double* G1 = st.G1 + (size_t)t.seg * st.gstride;
-    for (int o = threadIdx.x; o < nout; o += kThreads) G1[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
-    if (threadIdx.x < b) {
-      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
-      const double v = total(red, t.seg, nout + threadIdx.x);
-      double a = 0.0;
-      if (!st.done[k]) {
-        if (v != 0.0 && isfinite(v)) a = st.rho[k] / v;
-        else st.done[k] = 1;
-      }
-      st.alpha[k] = a;
-    }
-    release(red, t.seg, nout + b);
-  }
-}
-
-// pass C: q = q~ - [1|X] G1; T += alpha P; RES -= alpha q; z~ = RES / d;
-//         G2 = [1|X]^T z~, rho' = RES . z~, ||RES||^2; beta = rho'/rho.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pcg_c(DevGraph g, Reduce red, PcgState st, const T* __restrict__ X,
-                                                    int ldx, const T* __restrict__ P, const T* __restrict__ AP, T* Tt,
-                                                    T* RES, T* Z, int ld, int b, const double* __restrict__ theta,
-                                                    int64_t sth, double delta, const int* __restrict__ seg_skip) {
-  const Tile t = g.tiles[blockIdx.x];
-  if (seg_skip && seg_skip[t.seg]) return;
-  const T* deg = reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
-  __shared__ T Xs[kChunk * 32];
-  __shared__ T Zs[kChunk * 32];
-  __shared__ T Gs[33 * 32];
-  __shared__ double scratch[kThreads / 32][32];
-  __shared__ double extra[64];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nout = (b + 1) * b;
-  const double* G1 = st.G1 + (size_t)t.seg * st.gstride;
-  for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)G1[e];
-  const size_t kk = (size_t)t.seg * st.bstride + lane;
-  const T th = lane < b ? (T)theta[(size_t)t.seg * sth + lane] : T(0);
-  const T al = lane < b ? (T)st.alpha[kk] : T(0);
-  double rz = 0.0, rr = 0.0;
-  double acc[5];
-#pragma unroll
-  for (int u = 0; u < 5; ++u) acc[u] = 0.0;
-  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
-    const int nr = min(kChunk, t.r1 - c0);
-    stage(Xs, X, ldx, c0, nr, b);
-    __syncthreads();
-    for (int r = warp; r < nr; r += kThreads / 32) {
-      if (lane < b) {
-        const size_t o = (size_t)(c0 + r) * ld + lane;
-        const T p = P[o];
-        T q = AP[o] - th * p - Gs[lane];
-        const T* xr = Xs + r * b;
-        for (int i = 0; i < b; ++i) q -= xr[i] * Gs[(i + 1) * b + lane];
-        Tt[o] += al * p;
-        const T res = RES[o] - al * q;
-        RES[o] = res;
-        const T z = res / deg[c0 + r];
-        Z[o] = z;
-        Zs[r * b + lane] = z;
-        rz += (double)res * (double)z;
-        rr += (double)res * (double)res;
-      }
-    }
-    __syncthreads();
-    gram_chunk64<T, 5>(Xs, b, 1, Zs, b, nr, acc);
-    __syncthreads();
-  }
-  reduce_cols<T>(rz, extra, scratch);
-  reduce_cols<T>(rr, extra + 32, scratch);
-  __shared__ double ex2[64];
-  if (threadIdx.x < b) { ex2[threadIdx.x] = extra[threadIdx.x]; ex2[b + threadIdx.x] = extra[32 + threadIdx.x]; }
-  __syncthreads();
-  if (commit<5>(red, t.seg, seg_tiles(g, t.seg), acc, nout, ex2, 2 * b)) {
-    const double inv_n = 1.0 / (double)seg_rows(g, t.seg);
-    double* G2 = st.G2 + (size_t)t.seg * st.gstride;
-    for (int o = threadIdx.x; o < nout; o += kThreads) G2[o] = total(red, t.seg, o) * (o < b ? inv_n : 1.0);
-    if (threadIdx.x < b) {
-      const size_t k = (size_t)t.seg * st.bstride + threadIdx.x;
-      const double rho_new = total(red, t.seg, nout + threadIdx.x);
-      const double rn = sqrt(total(red, t.seg, nout + b + threadIdx.x));
-      st.resn[k] = rn;
-      double be = 0.0;
-      if (!st.done[k]) {
-        if (st.rho[k] != 0.0 && isfinite(rho_new)) be = rho_new / st.rho[k];
-        if (!(rn > delta * st.res0[k]) || !isfinite(rn)) st.done[k] = 1;
-      }
-      st.rho[k] = rho_new;
-      st.beta[k] = be;
-    }
-    release(red, t.seg, nout + 2 * b);
-  }
-}
-
-// pass D: P = (z~ - [1|X] G2) + beta P.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_pcg_d(DevGraph g, PcgState st, const T* __restrict__ X, int ldx,
-                                                    const T* __restrict__ Z, T* P, int ld, int b,
-                                                    const int* __restrict__ seg_skip) {
-  const Tile t = g.tiles[blockIdx.x];
-  if (seg_skip && seg_skip[t.seg]) return;
-  __shared__ T Xs[kChunk * 32];
-  __shared__ T Gs[33 * 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nout = (b + 1) * b;
-  const double* G2 = st.G2 + (size_t)t.seg * st.gstride;
-  for (int e = threadIdx.x; e < nout; e += kThreads) Gs[e] = (T)G2[e];
-  const size_t kk = (size_t)t.seg * st.bstride + lane;
-  const T be = lane < b ? (T)st.beta[kk] : T(0);
-  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
-    const int nr = min(kChunk, t.r1 - c0);
-    __syncthreads();
-    stage(Xs, X, ldx, c0, nr, b);
-    __syncthreads();
-    for (int r = warp; r < nr; r += kThreads / 32) {
-      if (lane < b) {
-        const size_t o = (size_t)(c0 + r) * ld + lane;
-        T z = Z[o] - Gs[lane];
-        const T* xr = Xs + r * b;
-        for (int i = 0; i < b; ++i) z -= xr[i] * Gs[(i + 1) * b + lane];
-        P[o] = (be == T(0)) ? z : z + be * P[o];
-      }
-    }
-  }
-}
-
 template <typename T, int NO>
 void launch_gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, const T* B, int ldb, int q,
                  int ones, int ones_mean, double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s) {
@@ -1090,36 +822,6 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
                                  nref < 0 ? -1 : (int)nr);
 }
 
-template <typename T>
-void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* R, int ldr,
-              T* Tt, T* RES, T* Z, T* P, int ld, int b, const int* active, const int* seg_skip, cudaStream_t s) {
-  LAP_PROF("pcg_init", (double)sizeof(T) * g.n * (9 * b + 1), s);
-  k_pcg_init<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, R, ldr, Tt, RES, Z, ld, b, active, seg_skip);
-  k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
-}
-
-template <typename T>
-void pcg_step_b(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
-                const T* AP, int ld, int b, const double* theta, int64_t sth, const int* seg_skip, cudaStream_t s) {
-  LAP_PROF("pcg_b", (double)sizeof(T) * g.n * 3 * b, s);
-  k_pcg_b<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, ld, b, theta, sth, seg_skip);
-}
-
-template <typename T>
-void pcg_step_c(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
-                const T* AP, T* Tt, T* RES, T* Z, int ld, int b, const double* theta, int64_t sth, double delta,
-                const int* seg_skip, cudaStream_t s) {
-  LAP_PROF("pcg_c", (double)sizeof(T) * g.n * (8 * b + 1), s);
-  k_pcg_c<T><<<g.ntiles, kThreads, 0, s>>>(g, red, st, X, ldx, P, AP, Tt, RES, Z, ld, b, theta, sth, delta, seg_skip);
-}
-
-template <typename T>
-void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z, T* P, int ld, int b,
-                const int* seg_skip, cudaStream_t s) {
-  LAP_PROF("pcg_d", (double)sizeof(T) * g.n * 4 * b, s);
-  k_pcg_d<T><<<g.ntiles, kThreads, 0, s>>>(g, st, X, ldx, Z, P, ld, b, seg_skip);
-}
-
 #define LAPEIG_INST(T)                                                                                            \
   template void gram<T>(const DevGraph&, const Reduce&, const T*, int, int, const T*, int, int, int, int, double*, \
                         int, int64_t, const int*, cudaStream_t);                                                  \
@@ -1130,15 +832,7 @@ void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z
   template void colscale<T>(const DevGraph&, T*, int, int, const double*, int64_t, const int*, cudaStream_t);     \
   template void random_block<T>(const DevGraph&, T*, int, int, uint64_t, cudaStream_t);                           \
   template void residual<T>(const DevGraph&, const Reduce&, const T*, int, const T*, int, const double*, int64_t,  \
-                            T*, int, int, double*, int64_t, const int*, cudaStream_t);                            \
-  template void pcg_init<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, int, T*, T*, \
-                            T*, T*, int, int, const int*, const int*, cudaStream_t);                              \
-  template void pcg_step_b<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, const T*,  \
-                              int, int, const double*, int64_t, const int*, cudaStream_t);                        \
-  template void pcg_step_c<T>(const DevGraph&, const Reduce&, const PcgState&, const T*, int, const T*, const T*,  \
-                              T*, T*, T*, int, int, const double*, int64_t, double, const int*, cudaStream_t);    \
-  template void pcg_step_d<T>(const DevGraph&, const PcgState&, const T*, int, T*, T*, int, int, const int*,      \
-                              cudaStream_t);
+                            T*, int, int, double*, int64_t, const int*, cudaStream_t);
 
 LAPEIG_INST(float)
 LAPEIG_INST(double)

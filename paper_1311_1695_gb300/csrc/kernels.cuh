@@ -73,36 +73,4 @@ void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int abs
 void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, int64_t se,
           double* Y, int ldy, int64_t sy, const int* seg_skip, int* sweeps_out, cudaStream_t s, int nref = -1);
 
-// ---- Projected preconditioned CG on (I - QQ^T)(L - theta_c I)(I - QQ^T) t_c = -r_c,
-// Q = [e/sqrt(n_s), X] per segment, preconditioner (I-QQ^T) D^{-1} (I-QQ^T).
-struct PcgState {
-  // per segment * bstride doubles
-  double* rho;
-  double* alpha;
-  double* beta;
-  double* res0;
-  double* resn;
-  double* G1;   // per segment (b+1) * b
-  double* G2;
-  int* done;    // per segment * bstride
-  int bstride;
-  int gstride;
-};
-
-template <typename T>
-void pcg_init(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* R,
-              int ldr, T* Tt, T* RES, T* Z, T* P, int ld, int b, const int* active, const int* seg_skip,
-              cudaStream_t s);
-template <typename T>
-void pcg_step_b(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
-                const T* AP, int ld, int b, const double* theta, int64_t sth, const int* seg_skip,
-                cudaStream_t s);
-template <typename T>
-void pcg_step_c(const DevGraph& g, const Reduce& red, const PcgState& st, const T* X, int ldx, const T* P,
-                const T* AP, T* Tt, T* RES, T* Z, int ld, int b, const double* theta, int64_t sth,
-                double delta, const int* seg_skip, cudaStream_t s);
-template <typename T>
-void pcg_step_d(const DevGraph& g, const PcgState& st, const T* X, int ldx, T* Z, T* P, int ld, int b,
-                const int* seg_skip, cudaStream_t s);
-
 }  // namespace lapeig

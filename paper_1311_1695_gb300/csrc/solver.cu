@@ -181,7 +181,6 @@ struct JD {
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
   double* oacc;  // accumulators of the fused orthonormalisation
-  PcgState ps;
   // host mirrors
   std::vector<double> rn2_h, theta_h;
   std::vector<int> active_h, skip_h;
@@ -233,8 +232,6 @@ struct JD {
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
     for (int i = 0; i < 5; ++i) add(S * 64 * 4);
-    for (int i = 0; i < 5; ++i) add(S * 64 * 8);
-    add(S * 33 * 32 * 8); add(S * 33 * 32 * 8); add(S * 64 * 4);
     add(S * 4); add(S * 8); add(sizeof(JdStatus)); add(S * 8);
     add(ortho_acc_doubles((int)S) * 8);
     return b + 4096;
@@ -270,16 +267,6 @@ struct JD {
     active = a.take<int>(S * 64);
     seg_skip = a.take<int>(S * 64);
     sweeps = a.take<int>(S * 64);
-    ps.rho = a.take<double>(S * 64);
-    ps.alpha = a.take<double>(S * 64);
-    ps.beta = a.take<double>(S * 64);
-    ps.res0 = a.take<double>(S * 64);
-    ps.resn = a.take<double>(S * 64);
-    ps.G1 = a.take<double>(S * 33 * 32);
-    ps.G2 = a.take<double>(S * 33 * 32);
-    ps.done = a.take<int>(S * 64);
-    ps.bstride = 64;
-    ps.gstride = 33 * 32;
     state = a.take<int>(S);
     tol_d = a.take<double>(S);
     status_d = a.take<JdStatus>(1);
