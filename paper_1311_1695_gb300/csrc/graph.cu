@@ -3,6 +3,7 @@
 // generalised degrees, ||L||_1 per graph, row tiles, and the SpMM schedule
 // (lanes per row and the list of hub rows).
 #include <algorithm>
+#include <functional>
 #include <climits>
 #include <cstdint>
 #include <cmath>
@@ -205,17 +206,20 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   g->max_degree = maxdeg;
 
   // tiles: every phase of the persistent correction solve ends at a grid
-  // barrier, so the CTAs must get equal work.  A row costs its SpMM work (row
-  // length capped at 64, the default hub threshold: longer rows are spread
-  // over all warps as chunks) plus 8 for the row-wise phases.  A single graph
-  // of more than 4,096 rows is cut into a multiple of 304 (= 2 CTAs x 152
-  // SMs) tiles of equal cost (at most 256 rows each).
+  // barrier, so the CTAs must get equal work.  A row costs its SpMM work (its
+  // length; a hub row, longer than the default threshold 64, nothing: its
+  // nonzeros go to chunks) plus 8 for the row-wise phases.  A single graph of
+  // more than 4,096 rows is cut into a multiple of 304 (= 2 CTAs x 152 SMs)
+  // tiles of equal cost (at most 256 rows each).
   std::vector<Tile> tiles;
   g->tile_ptr.assign(nb + 1, 0);
   for (int s = 0; s < nb; ++s) {
     g->tile_ptr[s] = (int)tiles.size();
     const int a0 = g->row0[s], a1 = g->row0[s + 1], ns = a1 - a0;
-    auto cost = [&](int r) { return (int64_t)std::min(g->rowptr_h[r + 1] - g->rowptr_h[r], 64) + 8; };
+    auto cost = [&](int r) {
+      const int d = g->rowptr_h[r + 1] - g->rowptr_h[r];
+      return (int64_t)(d > 64 ? 0 : d) + 8;
+    };
     int64_t total = 0;
     for (int r = a0; r < a1; ++r) total += cost(r);
     if (nb == 1 && ns > 4096) {
@@ -223,10 +227,28 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
       // binds), cut at the cost quantiles k * total / T
       const int64_t want = (ns + kTileRows - 1) / kTileRows;
       const int64_t T = std::max<int64_t>(1, (want * 5 / 4 + 303) / 304) * 304;
+      // With no more hub chunks (of at most kHubChunk nonzeros, hubs longest
+      // first) than tiles, the correction solve hands chunk i to CTA i, which
+      // holds tile i: the chunk's gathers plus its completion (about 100 row
+      // units, measured) count against tile i's budget.
+      std::vector<int> hub_deg;
+      for (int r = a0; r < a1; ++r)
+        if (g->rowptr_h[r + 1] - g->rowptr_h[r] > 64) hub_deg.push_back(g->rowptr_h[r + 1] - g->rowptr_h[r]);
+      std::sort(hub_deg.begin(), hub_deg.end(), std::greater<int>());
+      std::vector<int64_t> xpre((size_t)T + 1, 0);  // prefix sums of the chunk costs per tile
+      int64_t nchunk = 0;
+      for (int d : hub_deg) nchunk += (d + kHubChunk - 1) / kHubChunk;
+      if (nchunk <= T) {
+        int64_t i = 0;
+        for (int d : hub_deg)
+          for (int q0 = 0; q0 < d; q0 += kHubChunk, ++i) xpre[(size_t)i + 1] = std::min(kHubChunk, d - q0) + 100;
+        for (int64_t k = 1; k <= T; ++k) xpre[(size_t)k] += xpre[(size_t)k - 1];
+      }
+      const int64_t work = total + xpre[(size_t)T];
       int idx = 0, a = a0;
       int64_t cum = 0;
       for (int64_t kq = 1; kq <= T && a < a1; ++kq) {
-        const int64_t goal = (kq == T) ? INT64_MAX : (total * kq + T - 1) / T;
+        const int64_t goal = (kq == T) ? INT64_MAX : (work * kq + T - 1) / T - xpre[(size_t)kq];
         int e = a;
         while (e < a1 && e - a < kTileRows && (e == a || cum < goal)) cum += cost(e++);
         tiles.push_back(Tile{s, a, e, idx++});
