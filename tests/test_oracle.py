@@ -239,6 +239,26 @@ def test_pcg_correction_solves_projected_system():
         assert np.allclose(T[:, j], Z @ y, atol=1e-9)
 
 
+def test_projected_product_identity_of_the_two_phase_step():
+    """The reading behind the correction solve's two-phase step: with L e = 0
+    and Q = [e/sqrt(n), X] orthonormal, for any z and theta
+        (L - theta)(I - QQ^T) z = (L z - theta z) + theta g0 e - (LX - theta X) g,
+    g0 = mean(z), g = X^T z; so the product of the new search direction needs
+    only the SpMM of z and the fixed block LX."""
+    g = G.with_random_weights(G.ba_graph(90, 3, 4), 2)
+    lap = Laplacian(g)
+    Q = np.linalg.qr(blockops.project(uniform_block(5, g.n, 4), None))[0]
+    X = Q
+    LX = lap.matvec(X)
+    z = uniform_block(6, g.n, 1)[:, 0]
+    B = np.column_stack([np.ones(g.n) / np.sqrt(g.n), X])
+    for theta in (0.0, 0.37, 2.5):
+        lhs = lap.matvec((z - B @ (B.T @ z))[:, None])[:, 0] - theta * (z - B @ (B.T @ z))
+        g0, gx = z.mean(), X.T @ z
+        rhs = (lap.matvec(z[:, None])[:, 0] - theta * z) + theta * g0 * np.ones(g.n) - (LX - theta * X) @ gx
+        assert np.allclose(lhs, rhs, atol=1e-12)
+
+
 # ---------------------------------------------------------------- generator
 
 def test_splitmix64_reference_vector():
