@@ -48,7 +48,8 @@ enum {
   LAP_ESELFLOOP = -4,    /* diagonal entry in the adjacency */
   LAP_ENUMERIC = -5,     /* NaN/Inf appeared during the iteration */
   LAP_ENOMEM = -6,       /* device allocation failed */
-  LAP_ETIMEOUT = -7,     /* opts.max_seconds exceeded; partial result in outputs */
+  LAP_ETIMEOUT = -7,     /* opts.max_seconds exceeded (partial result in outputs), or a
+                            grid barrier of a persistent kernel gave up waiting */
   LAP_ECUDA = -8,        /* CUDA runtime error (see lap_last_error) */
   LAP_EUNSORTED = -9     /* column indices not strictly increasing in a row */
 };
