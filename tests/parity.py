@@ -5,6 +5,14 @@ import numpy as np
 from oracle.laplacian import Laplacian
 
 
+def all_pairs(g):
+    """Every eigenpair of L on the complement of e by the dense definition
+    (graphs small enough for a dense eigensolve): no cluster can run past
+    the end of this list."""
+    from oracle import dense
+    return dense.smallest_eigpairs(g, g.n - 1)
+
+
 def clusters(ev: np.ndarray, gap: float):
     """Group consecutive sorted eigenvalues whose spacing is below `gap`."""
     groups, cur = [], [0]
@@ -19,8 +27,11 @@ def clusters(ev: np.ndarray, gap: float):
 
 
 def check_eigpairs(g, ev, V, ev_ref, V_ref, tol=1e-8, ev_rtol=1e-7, angle=1e-6, k=None):
-    """ev, V: k GPU pairs; ev_ref, V_ref: at least k oracle pairs (more pairs
-    make the one-sided check of a cluster straddling k possible).
+    """ev, V: k GPU pairs; ev_ref, V_ref: at least k oracle pairs.  A cluster
+    that holds one of the first k pairs must end before the oracle's list
+    does (a spacing above the threshold), unless the list is the whole
+    spectrum on the complement of e; otherwise the check fails and asks for
+    more oracle pairs.
 
     * explicit FP64 residual ||L v - ev v|| <= tol ||L||_1 (recomputed here)
     * V orthonormal and orthogonal to e
@@ -47,9 +58,13 @@ def check_eigpairs(g, ev, V, ev_ref, V_ref, tol=1e-8, ev_rtol=1e-7, angle=1e-6, 
         idx = [i for i in cl if i < k]
         if not idx:
             continue
-        if cl[-1] >= ev_ref.size - 1 and cl[-1] >= k:
-            # cluster runs off the end of the oracle's list: cannot judge it
-            continue
+        if cl[-1] >= ev_ref.size - 1 and ev_ref.size < g.n - 1:
+            # the cluster runs to the end of the oracle's list, which is not
+            # the whole spectrum on the complement of e: eigenvalues beyond
+            # the list may belong to it, so its span is unknown
+            raise AssertionError(
+                f"cluster {cl[0]}..{cl[-1]} reaches the end of the {ev_ref.size} oracle pairs "
+                f"(spacing threshold {gap:.3e}): compute more oracle pairs")
         U = V_ref[:, cl]
         Vc = V[:, idx]
         s = np.linalg.norm(Vc - U @ (U.T @ Vc), ord=2)

@@ -269,3 +269,84 @@ def test_splitmix64_reference_vector():
         assert [int(v) for v in got] == [int(x, 16) for x in r[1:]]
     u = uniform_block(0, 100, 3)
     assert u.min() >= -1 and u.max() < 1 and abs(u.mean()) < 0.2
+
+
+# ---------------------------------------------------------------- pins of the correction solve, IC(0), signs
+
+def _cg_krylov_minimiser(A, M, rhs, j):
+    """The j-th iterate of preconditioned CG from t = 0, by its defining
+    property and not by its recurrences: on an SPD operator A with SPD
+    preconditioner M, t_j minimises (t* - t)^T A (t* - t) over the Krylov space
+    K_j(M A, M rhs), so t_j = K (K^T A K)^{-1} K^T rhs for any basis K of it."""
+    cols = [M @ rhs]
+    for _ in range(j - 1):
+        cols.append(M @ (A @ cols[-1]))
+    K = np.linalg.qr(np.column_stack(cols))[0]  # orthonormal basis of the same span
+    return K @ np.linalg.solve(K.T @ A @ K, K.T @ rhs)
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_pcg_correction_iterates_are_cg_optimal(weighted):
+    """Algorithm 2 step 8 after j steps (not only at convergence): with Q =
+    [e/sqrt(n), X] and theta below the spectrum of L on the complement of Q
+    (the SPD case), the projected operator A = Pi (L - theta) Pi and the
+    projected preconditioner M = Pi D^{-1} Pi (Section 3.2.1 with P = D^{-1})
+    are SPD on range(Pi), and the oracle's iterate after j steps must be the
+    A-norm minimiser over K_j(M A, M rhs), rhs = -Pi r.  A dropped outer
+    projection, a wrong beta or alpha, or a missing preconditioner changes the
+    Krylov space or the minimiser and fails this."""
+    g = G.ba_graph(48, 2, 11)
+    if weighted:
+        g = G.with_random_weights(g, 5)
+    lap = Laplacian(g)
+    n = g.n
+    X = np.linalg.qr(blockops.project(uniform_block(21, n, 3), None))[0]
+    B = np.column_stack([np.ones(n) / np.sqrt(n), X])
+    Pi = np.eye(n) - B @ B.T
+    Lm = lap.dense()
+    # smallest eigenvalue of L on range(Pi)
+    Z = np.linalg.svd(Pi)[0][:, :n - 4]
+    lam = np.linalg.eigvalsh(Z.T @ Lm @ Z)[0]
+    theta = np.array([0.5 * lam, 0.1 * lam, 0.9 * lam])
+    R = uniform_block(22, n, 3)
+    M = Pi @ np.diag(1.0 / lap.d) @ Pi
+    for j in (1, 2, 3, 5, 8):
+        T = blockops.pcg_correction(g, theta, R, X, iters=j)
+        for c in range(3):
+            A = Pi @ (Lm - theta[c] * np.eye(n)) @ Pi
+            ref = _cg_krylov_minimiser(A, M, -Pi @ R[:, c], j)
+            assert np.allclose(T[:, c], ref, rtol=0, atol=1e-10 * np.abs(ref).max()), (j, c)
+
+
+def test_ic0_factor_reproduces_the_pattern_entries():
+    """IC(0) (Section 4, Section 3.1.1): F is lower triangular with exactly the
+    pattern of tril(M), M = L + alpha diag(L), and (F F^T)_ij = M_ij on that
+    pattern (no fill-in is kept, the kept entries are exact)."""
+    g = G.with_random_weights(G.chung_lu(150, 2.3, 4.0, 6), 3)
+    lap = Laplacian(g)
+    alpha = 1e-3
+    from oracle import precond
+    F = precond.ic0_factor(lap.L, alpha)
+    assert F is not None
+    M = (lap.L + alpha * __import__("scipy.sparse", fromlist=["diags"]).diags(lap.L.diagonal())).toarray()
+    Fd = F.toarray()
+    pat = np.tril(M) != 0
+    assert np.array_equal(Fd != 0, pat)
+    FF = Fd @ Fd.T
+    assert np.allclose(FF[pat], M[pat], rtol=0, atol=1e-12 * np.abs(M).max())
+    # off the pattern F F^T differs from M (fill-in was dropped), so the test is not vacuous
+    assert np.abs(FF[~pat & np.tri(g.n, dtype=bool)]).max() > 1e-6
+
+
+def test_canonical_signs_convention():
+    """Sign reading: the entry of largest magnitude of each returned vector is
+    positive, the first such entry on an exact tie."""
+    V = np.array([[0.1, 0.5, -0.5, 0.0],
+                  [-0.9, -0.5, 0.5, -0.2],
+                  [0.3, 0.1, 0.1, 0.0]])
+    W = dense.canonical_signs(V)
+    assert np.array_equal(W[:, 0], -V[:, 0])
+    assert np.array_equal(W[:, 1], V[:, 1])
+    assert np.array_equal(W[:, 2], -V[:, 2])
+    assert np.array_equal(W[:, 3], -V[:, 3])
+    assert np.array_equal(V[0], [0.1, 0.5, -0.5, 0.0])  # input untouched
