@@ -85,6 +85,18 @@ typedef struct {
   int ldx0;
   int cuda_graph;     /* JD: 0 (default) replays each steady-state outer iteration
                          as one captured CUDA graph; -1 enqueues it kernel by kernel */
+  double device_timeout_ms; /* longest wait of one CTA at one grid barrier of a
+                         persistent kernel (correction solve, orthonormalisation);
+                         0 = the handle's setting (default 4000 ms).  A wait that
+                         runs out ends the kernel early and the call returns
+                         LAP_ETIMEOUT; the handle stays usable. */
+  int max_ctas;       /* cap on the CTAs of the persistent kernels (0 = the
+                         handle's setting, default all co-resident CTAs); fewer
+                         CTAs give each more row tiles (tuning, sharing the GPU) */
+  double ev_rtol;     /* JD: a pair also needs its Ritz value within ev_rtol
+                         relative of an eigenvalue by the Kato-Temple bound
+                         ||r||^2 / delta (delta = distance to the nearest other
+                         Ritz value farther than ||r||); 0 = 1e-7, < 0 = off */
 } lap_opts;
 
 typedef struct {
@@ -110,7 +122,8 @@ const char* lap_last_error(void);
  * paper's "smallest strictly positive" eigenvalues, Section 4), with
  * orthonormal eigenvectors, each orthogonal to e, sign fixed so that the
  * entry of largest magnitude is positive.  Converged means
- * ||L v - lambda v||_2 <= tol * ||L||_1 for every pair (checked in FP64).
+ * ||L v - lambda v||_2 <= tol * ||L||_1 for every pair (checked in FP64),
+ * and for JD also the eigenvalue-accuracy estimate of opts.ev_rtol.
  *   method = LAP_JD   : block Jacobi-Davidson (Algorithm 2 with the deflated
  *                       correction equation Eq. 5, projected Jacobi-
  *                       preconditioned CG, Section 3.2.1)
@@ -150,6 +163,15 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
  * Calls that run SpMM-type kernels on one handle must be stream-ordered:
  * the handle's reduction and hub-chunk scratch is shared by them. */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
+
+/* Launch settings of the persistent kernels on this handle, used by the
+ * step-level entry points and by solves whose opts leave them at 0:
+ * max_ctas caps the grid (0 = every co-resident CTA; a smaller grid gives
+ * each CTA more row tiles), device_timeout_ms bounds one CTA's wait at one
+ * grid barrier (0 = 4000 ms; a wait that runs out makes the call return
+ * LAP_ETIMEOUT and the handle's device state is restored).  Negative values
+ * return LAP_EINVAL. */
+int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms);
 
 /* Solve on a handle whose graphs are already on the device (the CSR is not
  * copied again).  evals: host [nseg * k] (graph s at s*k); evecs_dev: device

@@ -58,6 +58,9 @@ class lap_opts(ctypes.Structure):
         ("x0_dev", ctypes.c_void_p),
         ("ldx0", ctypes.c_int),
         ("cuda_graph", ctypes.c_int),
+        ("device_timeout_ms", ctypes.c_double),
+        ("max_ctas", ctypes.c_int),
+        ("ev_rtol", ctypes.c_double),
     ]
 
 
@@ -108,6 +111,7 @@ _SIGNATURES = {
     "lap_graph_destroy": (None, [_P]),
     "lap_graph_info": (_I, [_P, _PI64, _PI, _PD, _PI, _PI]),
     "lap_graph_set_schedule": (_I, [_P, _I, _I]),
+    "lap_graph_set_launch": (_I, [_P, _I, _D]),
     "lap_spmm": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gram": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
     "lap_gram_noalloc": (_I, [_I64, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
@@ -166,7 +170,7 @@ def _ptr(a, ct):
 
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
               include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
-              x0_dev=None, cuda_graph=True):
+              x0_dev=None, cuda_graph=True, device_timeout_ms=0.0, max_ctas=0, ev_rtol=0.0):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -177,6 +181,7 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.max_seconds, o.team, o.verbose = max_seconds, team, int(verbose)
     o.stream = stream
     o.cuda_graph = 0 if cuda_graph else -1
+    o.device_timeout_ms, o.max_ctas, o.ev_rtol = device_timeout_ms, max_ctas, ev_rtol
     keep = None
     if x0_dev is not None:  # a row-major float64 CUDA tensor n x k0
         o.x0_dev = ctypes.c_void_p(x0_dev.data_ptr())
@@ -295,6 +300,10 @@ class Graph:
 
     def set_schedule(self, team=0, long_thresh=0):
         _check(lib().lap_graph_set_schedule(self.h, team, long_thresh), "lap_graph_set_schedule")
+
+    def set_launch(self, max_ctas=0, device_timeout_ms=0.0):
+        """CTA cap and grid-barrier wait limit of the persistent kernels."""
+        _check(lib().lap_graph_set_launch(self.h, max_ctas, device_timeout_ms), "lap_graph_set_launch")
 
     def eigs(self, k: int, tol: float = 1e-8, method: str = "jd", evecs=None, **opts):
         """Solve on the resident graph(s) (lap_eigs_graph).  evecs: optional

@@ -256,6 +256,13 @@ int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   return graph_set_schedule(g, team, long_thresh);
 }
 
+int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms) {
+  if (!g || max_ctas < 0 || !(device_timeout_ms >= 0.0)) { set_error("bad arguments to lap_graph_set_launch"); return LAP_EINVAL; }
+  g->max_ctas = max_ctas;
+  g->timeout_ms = device_timeout_ms;
+  return LAP_OK;
+}
+
 #define LAP_DTYPE_SWITCH(dtype, ...)                            \
   do {                                                          \
     if ((dtype) == LAP_F64) { using T = double; __VA_ARGS__; }  \
@@ -429,6 +436,10 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     rc = g->pcg.init(S);
     if (rc) return rc;
   }
+  g->pcg.timeout_ns = timeout_ns_of(0.0, g->timeout_ms);
+  g->pcg.max_ctas = g->max_ctas;
+  g->pcg.hub_cnt = g->d_hub_cnt;
+  g->pcg.nlong = g->dg.nlong;
   double* th = g->small;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaMemcpy2DAsync(th, 64 * sizeof(double), theta, b * sizeof(double), b * sizeof(double), S, cudaMemcpyDeviceToDevice,
@@ -441,7 +452,7 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     T* LX = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(AP + n * b) + 255) & ~(uintptr_t)255);
     const FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, LX, ldlx, b, b, th, 64, nullptr, nullptr, delta, iters,
                                    g->d_long_seg);
-    if (pcg_fused<T>(g->dg, f, s, 0) != 0) return check_cuda("lap_pcg_correction launch");
+    if (pcg_fused<T>(g->dg, f, s, g->pcg.max_ctas) != 0) return check_cuda("lap_pcg_correction launch");
   });
   if (g->pcg.error_flag(s)) { set_error("grid barrier timed out"); return LAP_ETIMEOUT; }
   return check_cuda("lap_pcg_correction");

@@ -810,11 +810,9 @@ void syev(int nseg, int m, const double* H, int ldh, int64_t sh, double* evals, 
   if (nref < 0 && ex > scratch) scratch = ex;
   if (nref >= 0 && fa > scratch) scratch = fa;
   const size_t smem = sizeof(double) * (2 * mm * (mm + 1) + mm) + scratch;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  // the shared-memory opt-in belongs to the current device: set it at every
+  // launch (cheap) rather than once per process
+  cudaFuncSetAttribute(k_syev, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   // one 2x2 block per thread in a Jacobi step for m > 40 (the blocks of a
   // 46 x 46 matrix take two rounds of 256 threads; measured 12% faster)
   const int nt = m > 40 ? 512 : 256;

@@ -333,6 +333,13 @@ void graph_free(lap_graph* g) {
   delete g;
 }
 
+unsigned long long timeout_ns_of(double opts_ms, double handle_ms) {
+  const double ms = opts_ms > 0.0 ? opts_ms : (handle_ms > 0.0 ? handle_ms : 0.0);
+  if (ms <= 0.0) return kDefaultTimeoutNs;
+  const double ns = ms * 1e6;
+  return ns >= 1.8e19 ? ~0ull : (ns < 1.0 ? 1ull : (unsigned long long)ns);
+}
+
 int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes) {
   if (bytes > g->scratch_bytes) {
     cudaFree(g->scratch);
@@ -359,7 +366,7 @@ int PcgWork::init(int nseg_) {
   nseg = nseg_;
   const size_t a = (size_t)nseg * acc_stride;
   const size_t st = (size_t)nseg * 64;
-  const size_t bytes = sizeof(double) * (4 * a + 2 * st + 2 * st) + sizeof(int) * 2 * st + 64;
+  bytes = sizeof(double) * (4 * a + 2 * st + 2 * st) + sizeof(int) * 2 * st + 64;
   char* base = nullptr;
   if (cudaMalloc(reinterpret_cast<void**>(&base), bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -391,7 +398,7 @@ FusedPcg PcgWork::args(const void* X, int ldx, const void* R, int ldr, void* Tt,
   f.ld = ld; f.b = b; f.theta = theta; f.sth = sth; f.active = active; f.bstride = 64; f.seg_skip = seg_skip;
   f.delta = delta; f.itmax = itmax; f.acc1 = acc1; f.acc2 = acc2; f.acc_stride = acc_stride; f.rho = rho;
   f.done = done; f.res0 = res0; f.resn = resn; f.state_stride = (int64_t)nseg * 64; f.hub_seg = hub_seg;
-  f.bar.count = bar; f.bar.gen = bar + 1; f.bar.err = reinterpret_cast<int*>(bar + 2);
+  f.bar = gridbar();
   f.iters_out = reinterpret_cast<int*>(bar + 3);
   return f;
 }
@@ -407,7 +414,7 @@ void PcgWork::status(cudaStream_t s, int* err, int* steps) const {
   int v[2] = {0, 0};
   cudaMemcpyAsync(v, bar + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  if (v[0]) cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
+  if (v[0]) reset(s);
   if (err) *err = v[0];
   if (steps) *steps = v[1];
 }
@@ -416,8 +423,16 @@ int PcgWork::error_flag(cudaStream_t s) const {
   int e = 0;
   cudaMemcpyAsync(&e, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  if (e) cudaMemsetAsync(bar, 0, 3 * sizeof(unsigned), s);
+  if (e) reset(s);
   return e;
+}
+
+void PcgWork::reset(cudaStream_t s) const {
+  if (acc1) cudaMemsetAsync(acc1, 0, bytes, s);
+  // a CTA that passed a barrier before the flag was set may have left a hub
+  // row with only some of its chunks counted
+  if (hub_cnt && nlong > 0) cudaMemsetAsync(hub_cnt, 0, sizeof(int) * (size_t)nlong, s);
+  cudaStreamSynchronize(s);
 }
 
 }  // namespace lapeig

@@ -24,15 +24,24 @@ struct PcgWork {
   unsigned* bar = nullptr;  // count, gen, err, PCG steps done
   int acc_stride = 33 * 32 + 3 * 32;
   int nseg = 0;
+  size_t bytes = 0;         // the whole block (zero at rest)
+  unsigned long long timeout_ns = kDefaultTimeoutNs;  // grid-barrier wait limit
+  int max_ctas = 0;         // CTA cap of the persistent launches (0: all co-resident)
+  int* hub_cnt = nullptr;   // the graph's hub arrival counters (zero at rest), reset with the rest
+  int nlong = 0;
   int init(int nseg_);
   void release();
+  GridBar gridbar() const { return GridBar{bar, bar + 1, reinterpret_cast<int*>(bar + 2), timeout_ns}; }
+  // back to the zero-at-rest state after a launch that gave up at a barrier
+  // (counter, generation, flag and every accumulator)
+  void reset(cudaStream_t s) const;
   FusedPcg args(const void* X, int ldx, const void* R, int ldr, void* Tt, void* RES, void* Z, void* P, void* AP,
                 void* LX, int ldlx, int ld, int b, const double* theta, int64_t sth, const int* active, const int* seg_skip, double delta,
                 int itmax, const int* hub_seg) const;
-  int error_flag(cudaStream_t s) const;  // reads and clears the barrier error flag
+  int error_flag(cudaStream_t s) const;  // reads the barrier error flag; when set, reset()
   int steps_done(cudaStream_t s) const;  // PCG steps of the last launch
   // error flag and steps of the last launch in one read (synchronises s);
-  // a set error flag is cleared
+  // when the flag is set, reset()
   void status(cudaStream_t s, int* err, int* steps) const;
 };
 
@@ -75,6 +84,8 @@ struct lap_graph {
   double* small = nullptr;      // FP64 per-segment scratch
   size_t small_bytes = 0;
   lapeig::PcgWork pcg;          // persistent correction-solve state (lazy)
+  int max_ctas = 0;             // persistent-kernel CTA cap (0: all co-resident)
+  double timeout_ms = 0.0;      // grid-barrier wait limit (0: default)
 };
 
 namespace lapeig {
@@ -85,6 +96,8 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 void graph_free(lap_graph* g);
 int graph_set_schedule(lap_graph* g, int team, int long_thresh);
 int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_out, cudaStream_t s);
+// Barrier wait limit in ns: the first positive of (opts, handle), else the default.
+unsigned long long timeout_ns_of(double opts_ms, double handle_ms);
 // Ensure the handle's step-level scratch holds at least `bytes` (device).
 int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes);
 

@@ -392,6 +392,10 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
     rc = G->pcg.init(1);
     if (rc) return rc;
   }
+  G->pcg.timeout_ns = timeout_ns_of(o.device_timeout_ms, G->timeout_ms);
+  G->pcg.max_ctas = o.max_ctas > 0 ? o.max_ctas : G->max_ctas;
+  G->pcg.hub_cnt = G->d_hub_cnt;
+  G->pcg.nlong = G->dg.nlong;
   const int LW = 8;
   double* w = Wb;            // col 0
   double* zero = Wb + 1;     // col 1 (stays 0: X of the inner PCG, so Q = [e] only)
@@ -420,7 +424,7 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
                                       nullptr, nullptr, rtol, 4000, G->d_long_seg);
       FusedPcg fe = fp;
       fe.early_exit = 1;
-      if (pcg_fused<double>(g, fe, st, 0) != 0) { set_error("IRLM inner solve launch failed"); return LAP_ECUDA; }
+      if (pcg_fused<double>(g, fe, st, G->pcg.max_ctas) != 0) { set_error("IRLM inner solve launch failed"); return LAP_ECUDA; }
       if (G->pcg.error_flag(st)) { set_error("grid barrier timed out in IRLM"); return LAP_ETIMEOUT; }
       ++solves;
       {

@@ -45,38 +45,6 @@ constexpr int kStride = kA2b + kQ * kQ;
 
 __device__ __forceinline__ int seg_rows(const DevGraph& g, int s) { return g.row0[s + 1] - g.row0[s]; }
 
-// Generation barrier over all CTAs (acquire-release; bounded spin, error flag).
-__device__ bool obar(const GridBar& bar) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    unsigned g0, old;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(bar.gen) : "memory");
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar.count) : "memory");
-    int ok = 1;
-    if (old == gridDim.x - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar.count), "r"(0u) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.gen) : "memory");
-    } else {
-      long long spins = 0;
-      unsigned gv;
-      while (true) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gv) : "l"(bar.gen) : "memory");
-        if (gv != g0) break;
-        if (++spins > (1ll << 26) || *(volatile int*)bar.err) {
-          atomicExch(bar.err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    s_ok = ok && (*(volatile int*)bar.err == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // rows [r0, r0 + nr) x cols [0, w) of a row-major block into dst (row stride
 // w), nr <= kCh, w <= 64: warp w_ takes rows w_, w_ + 8, ..., lane c columns
 // c and c + 32; the loads of a thread go out together (no index division)
@@ -294,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
     }
     if (cur >= 0 && tid < q && nrm != T(0)) atomicAdd(acc_of(cur) + kA0 + tid, (double)nrm);
   }
-  if (!obar(a.bar)) return;
+  if (!grid_sync(a.bar)) return;
 
   // ------------------------------------------------------------ P1: scale, G (pass 0)
   {
@@ -327,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
     }
     if (cur >= 0) flush(acc_of(cur) + kA1a, nout1);
   }
-  if (!obar(a.bar)) return;
+  if (!grid_sync(a.bar)) return;
 
   // ------------------------------------------------------------ P2 / P4: project, S
   auto project_phase = [&](int a1, int a2, int zero_off, int zero_n) {
@@ -361,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
     if (cur >= 0) flush(acc_of(cur) + a2, nout2);
   };
   project_phase(kA1a, kA2a, kA0, kQ);
-  if (!obar(a.bar)) return;
+  if (!grid_sync(a.bar)) return;
 
   // ------------------------------------------------------------ P3 / P5: T R^-1 (and G)
   auto rinv_phase = [&](int a2, T drop, bool gram_next, int a1n, int zero_off, int zero_n, bool last) {
@@ -399,26 +367,25 @@ __global__ void __launch_bounds__(kThreads) k_ortho(DevGraph g, OrthoView a) {
     if (cur >= 0 && gram_next) flush(acc_of(cur) + a1n, nout1);
   };
   rinv_phase(kA2a, (T)a.drop1, true, kA1b, kA1a, (kM0 + 1) * kQ, false);
-  if (!obar(a.bar)) return;
+  if (!grid_sync(a.bar)) return;
   project_phase(kA1b, kA2b, kA2a, kQ * kQ);
-  if (!obar(a.bar)) return;
+  if (!grid_sync(a.bar)) return;
   rinv_phase(kA2b, T(0.25), false, 0, kA1b, (kM0 + 1) * kQ, true);
 }
 
 template <typename T, int NO>
-int launch(const DevGraph& g, const OrthoView& a, cudaStream_t s) {
+int launch(const DevGraph& g, const OrthoView& a, cudaStream_t s, int max_ctas) {
   auto kern = k_ortho<T, NO>;
   const size_t smem = sizeof(T) * ((size_t)kCh * kM0 + 2 * kCh * kQ + (kM0 + 1) * kQ + kQ * (kQ + 1));
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  // the shared-memory opt-in is a property of the function on the current
+  // device: set it at every launch (cheap) rather than once per process
+  cudaFuncSetAttribute(reinterpret_cast<const void*>(kern), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   int grid = per_sm * nsm;
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   grid = grid < g.ntiles ? grid : g.ntiles;
   if (grid < 1) grid = 1;
   DevGraph gg = g;
@@ -429,18 +396,18 @@ int launch(const DevGraph& g, const OrthoView& a, cudaStream_t s) {
 }
 
 template <typename T>
-int dispatch(const DevGraph& g, const OrthoView& a, cudaStream_t s) {
+int dispatch(const DevGraph& g, const OrthoView& a, cudaStream_t s, int mc) {
   const int nout = std::max((a.m0 + 1) * a.q, a.q * a.q);
   switch ((nout + kThreads - 1) / kThreads) {
-    case 1: return launch<T, 1>(g, a, s);
-    case 2: return launch<T, 2>(g, a, s);
-    case 3: return launch<T, 3>(g, a, s);
-    case 4: return launch<T, 4>(g, a, s);
-    case 5: return launch<T, 5>(g, a, s);
-    case 6: return launch<T, 6>(g, a, s);
-    case 7: return launch<T, 7>(g, a, s);
-    case 8: return launch<T, 8>(g, a, s);
-    default: return launch<T, 9>(g, a, s);
+    case 1: return launch<T, 1>(g, a, s, mc);
+    case 2: return launch<T, 2>(g, a, s, mc);
+    case 3: return launch<T, 3>(g, a, s, mc);
+    case 4: return launch<T, 4>(g, a, s, mc);
+    case 5: return launch<T, 5>(g, a, s, mc);
+    case 6: return launch<T, 6>(g, a, s, mc);
+    case 7: return launch<T, 7>(g, a, s, mc);
+    case 8: return launch<T, 8>(g, a, s, mc);
+    default: return launch<T, 9>(g, a, s, mc);
   }
 }
 
@@ -450,16 +417,16 @@ size_t ortho_acc_doubles(int nseg) { return (size_t)nseg * kStride; }
 
 template <typename T>
 int ortho_fused(const DevGraph& g, T* V, int ldv, int m0, int q, double drop1, double* acc, int* keep,
-                const int* seg_skip, const GridBar& bar, cudaStream_t s) {
+                const int* seg_skip, const GridBar& bar, cudaStream_t s, int max_ctas) {
   if (m0 < 0 || m0 > kM0 || q < 1 || q > kQ) return -1;
   LAP_PROF("ortho", (double)sizeof(T) * g.n * (q * 9.0 + m0 * 4.0), s);
   OrthoView a{V, ldv, m0, q, drop1, acc, keep, seg_skip, bar};
-  return dispatch<T>(g, a, s);
+  return dispatch<T>(g, a, s, max_ctas);
 }
 
 template int ortho_fused<float>(const DevGraph&, float*, int, int, int, double, double*, int*, const int*,
-                                const GridBar&, cudaStream_t);
+                                const GridBar&, cudaStream_t, int);
 template int ortho_fused<double>(const DevGraph&, double*, int, int, int, double, double*, int*, const int*,
-                                 const GridBar&, cudaStream_t);
+                                 const GridBar&, cudaStream_t, int);
 
 }  // namespace lapeig

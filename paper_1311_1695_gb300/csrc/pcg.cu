@@ -45,8 +45,9 @@
 // read by that CTA.
 //
 // Co-residency of all CTAs is guaranteed by the cooperative launch; the
-// barrier still bounds its spin and raises an error flag (the kernel then
-// returns early and the host reports LAP_ETIMEOUT) rather than hang.
+// barrier (gridbar.cuh) still bounds its wait and raises an error flag (the
+// kernel then returns early and the host reports LAP_ETIMEOUT) rather than
+// hang.
 #include "common.cuh"
 #include "hub.cuh"
 #include "kernels.cuh"
@@ -65,43 +66,6 @@ constexpr int kU = 8;   // gathers in flight per row group in the merge-path wal
 template <typename T, int BMAX> struct RowsInFlight { static constexpr int v = (sizeof(T) == 8 || BMAX >= 32) ? 2 : 4; };
 
 __device__ __forceinline__ int seg_rows(const DevGraph& g, int s) { return g.row0[s + 1] - g.row0[s]; }
-
-// Generation barrier over all CTAs of the launch, with a bounded spin.
-// Thread 0 of each CTA (after the CTA barrier, so its release covers the
-// whole CTA's writes) arrives with an acquire-release add on the counter; the
-// last arrival resets the counter and publishes the next generation with a
-// release add; the others poll the generation with acquire loads.  (Measured
-// 2.4 us per barrier over 304 CTAs, 2.9 us with full fences.)
-__device__ bool grid_barrier(const GridBar& bar) {
-  __syncthreads();
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    unsigned g0, old;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(bar.gen) : "memory");
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar.count) : "memory");
-    int ok = 1;
-    if (old == gridDim.x - 1) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar.count), "r"(0u) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar.gen) : "memory");
-    } else {
-      long long spins = 0;
-      unsigned gv;
-      while (true) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gv) : "l"(bar.gen) : "memory");
-        if (gv != g0) break;
-        if (++spins > (1ll << 26) || *(volatile int*)bar.err) {
-          atomicExch(bar.err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    s_ok = ok && (*(volatile int*)bar.err == 0);
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 template <int BMAX, int BWL>
 struct RedLx {
@@ -616,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
                            });
     if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(1, cur), b, 2, acc, ex, red);
   }
-  if (!grid_barrier(f.bar)) return;
+  if (!grid_sync(f.bar)) return;
 
   int it = 0;
   bool stopped = false;
@@ -771,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
       });
       if (cur >= 0) flush_cols<T, BMAX, BWL>(A1(par, cur), b, 1, acc, ex, red);
     }
-    if (!grid_barrier(f.bar)) return;
+    if (!grid_sync(f.bar)) return;
     // ---------------------------------------------------------------- phase B
     // alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
     // z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity par
@@ -830,7 +794,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
       }
       if (cur >= 0) flush_cols<T, BMAX, BWL>(A2(par, cur), b, 2, acc, ex, red);
     }
-    if (!grid_barrier(f.bar)) return;
+    if (!grid_sync(f.bar)) return;
   }
   if (!stopped) {  // ||r|| after the last step (parity of the last phase B)
     const int last = (it + 1) & 1;
@@ -842,7 +806,7 @@ __global__ void __launch_bounds__(kThreads, (sizeof(T) == 8 && BMAX >= 16) ? 1 :
   }
   if (f.iters_out && blockIdx.x == 0 && threadIdx.x == 0) *f.iters_out = it;
   // every CTA is past its last read of the accumulators: back to zero
-  if (!grid_barrier(f.bar)) return;
+  if (!grid_sync(f.bar)) return;
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (owner(t) && !skipped(t.seg))
@@ -906,12 +870,19 @@ int launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
 
 }  // namespace
 
-// Algorithmic bytes of a solve of `iters` steps: per step the CSR once and
-// 16 passes over n x b blocks (phase M: z~ gathered, z~, X, LX, P, AP read,
-// P, AP written; phase B: AP, RES, T, P, X read, T, RES, z~ written), plus
-// the set-up (the CSR, X gathered and read, R read, LX, RES, T, z~ written).
+// Algorithmic bytes of a solve of `iters` steps, counted per matrix-vector
+// product with its share of the step (the set-up's product L X is one more):
+// the CSR once (row pointers, column indices, weights if any), the gathered
+// block read once and the product written once (2 b n values), the
+// projection against Q = [e, X] reading Q twice (2 (b + 1) n values), and
+// seven more b n passes of CG vectors (t, r, p, q updates and the
+// preconditioned residual; the Jacobi preconditioner is the stored degrees,
+// no extra bytes).  What the kernel actually moves is larger (X, L X, P and
+// q~ are re-read in both phases); ncu's DRAM counters report that.
 double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
-  return (double)elem * g.n * b * (iters * 16.0 + 7.0) + (4.0 * g.n + 4.0 * g.nnz) * (iters + 1);
+  const double n = g.n, nnz = (double)g.nnz;
+  const double unit = 4.0 * (n + 1) + 4.0 * nnz + (g.w64 ? elem * nnz : 0.0) + (double)elem * n * (9.0 * b + 2.0 * (b + 1));
+  return unit * (iters + 1);
 }
 
 template <typename T>

@@ -1,14 +1,9 @@
 // Arguments of the persistent correction-solve kernel (pcg.cu).
 #pragma once
 #include "common.cuh"
+#include "gridbar.cuh"
 
 namespace lapeig {
-
-struct GridBar {
-  unsigned* count;  // zero at rest
-  unsigned* gen;
-  int* err;         // set when a barrier gave up waiting
-};
 
 struct FusedPcg {
   const void* Xv;      // Ritz block X (ldx), b columns
@@ -44,12 +39,12 @@ struct FusedPcg {
 // The expansion's CGS2 with Cholesky-QR of V[:, m0 : m0+q] against
 // [e, V[:, 0:m0]] (m0 <= 64, q <= 32) as one cooperative launch (ortho.cu);
 // keep[s*64 + c] = column c survived both passes.  acc: ortho_acc_doubles(nseg)
-// doubles, zero before the first launch.  Returns 0 or -1 (launch failure or
-// shape out of range).
+// doubles, zero before the first launch.  max_ctas > 0 caps the grid.
+// Returns 0 or -1 (launch failure or shape out of range).
 size_t ortho_acc_doubles(int nseg);
 template <typename T>
 int ortho_fused(const DevGraph& g, T* V, int ldv, int m0, int q, double drop1, double* acc, int* keep,
-                const int* seg_skip, const GridBar& bar, cudaStream_t s);
+                const int* seg_skip, const GridBar& bar, cudaStream_t s, int max_ctas);
 
 // Launch the whole correction solve; returns 0 or -1 (launch failure).
 template <typename T>

@@ -1,6 +1,8 @@
 // Small per-segment kernels of the Jacobi-Davidson driver: H bookkeeping
 // (restart to diag(theta), new border rows/columns), column scalings, the
 // output sign convention and the column-major copy-out.
+#include <cmath>
+
 #include "common.cuh"
 #include "small.cuh"
 #include "prof.h"
@@ -68,12 +70,30 @@ __global__ void k_and(int count, int* a, const int* b) {
   if (i < count) a[i] = (a[i] != 0 && b[i] != 0) ? 1 : 0;
 }
 
+// Eigenvalue accuracy of Ritz pair j (Kato-Temple): a Ritz value theta_j
+// with residual norm r lies within r^2 / delta of an eigenvalue, delta the
+// distance from theta_j to the rest of the spectrum, here estimated by the
+// nearest other Ritz value of the basis that is farther than r (closer ones
+// are the same eigenvalue within the residual).  Accurate when that bound is
+// at most ev_rtol * max(|theta_j|, tol_abs).  Shared by the device
+// bookkeeping and the host's explicit check.
+__host__ __device__ inline bool ev_accurate(const double* th, int nrv, int j, double r, double tol_abs,
+                                            double ev_rtol) {
+  double delta = HUGE_VAL;
+  for (int i = 0; i < nrv; ++i) {
+    const double d = fabs(th[i] - th[j]);
+    if (i != j && d > r && d < delta) delta = d;
+  }
+  const double scale = fmax(fabs(th[j]), tol_abs);
+  return r * r <= ev_rtol * scale * delta;
+}
+
 // One CTA; a warp per graph (lane j = column j, b <= 32), warp reductions,
 // then a fixed-order reduction over the warps.
 __global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
                            const double* __restrict__ norm1, const double* __restrict__ tol_abs, int k, int b,
-                           int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-                           JdStatus* status, double* segw) {
+                           int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
+                           const unsigned* bar, JdStatus* status, double* segw) {
   constexpr int NW = 8;
   __shared__ double s_w[NW];
   __shared__ int s_c[NW], s_bad[NW], s_act[NW], s_open[NW];
@@ -89,8 +109,10 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
       double ratio = 0.0;
       if (j < b) {
         const double r = sqrt(fmax(0.0, rn2[(size_t)s * 64 + j]));
+        const double* th = theta + (size_t)s * mmax;
         fin = isfinite(r);
-        c = r <= tol_abs[s] && theta[(size_t)s * mmax + j] <= norm1[s];
+        c = r <= tol_abs[s] && th[j] <= norm1[s];
+        if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, j, r, tol_abs[s], ev_rtol);
         ratio = j < k ? r / tol_abs[s] : 0.0;
         active[(size_t)s * 64 + j] = (j < k && c) ? 0 : 1;
       }
@@ -187,11 +209,15 @@ void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg
   k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, norm1, seg_skip);
 }
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-              JdStatus* status, double* segw, cudaStream_t s) {
+              int k, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
+              const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
-  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, b, explicit_check, state, active, skip, bar,
-                               status, segw);
+  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, b, nrv, ev_rtol, explicit_check, state,
+                               active, skip, bar, status, segw);
+}
+
+bool ev_accurate_host(const double* th, int nrv, int j, double r, double tol_abs, double ev_rtol) {
+  return ev_rtol <= 0.0 || ev_accurate(th, nrv, j, r, tol_abs, ev_rtol);
 }
 void and_flags(int count, int* a, const int* b, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);

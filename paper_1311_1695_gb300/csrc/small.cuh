@@ -28,9 +28,15 @@ struct JdStatus {
   int pcg_steps;     // its PCG steps
 };
 // segw[s]: graph s's worst ||r_j|| / tol_abs over j < k (0 once converged).
+// ev_rtol > 0 adds the eigenvalue-accuracy test (Kato-Temple estimate over
+// the nrv Ritz values of the basis, ev_accurate_host).
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, int b, int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
-              JdStatus* status, double* segw, cudaStream_t s);
+              int k, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
+              const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s);
+// Pair j's Ritz value is within ev_rtol * max(|theta_j|, tol_abs) of an
+// eigenvalue by the Kato-Temple bound r^2 / delta, delta from the other
+// Ritz values th[0:nrv] (always true for ev_rtol <= 0).
+bool ev_accurate_host(const double* th, int nrv, int j, double r, double tol_abs, double ev_rtol);
 // best: device scratch of 2 * nseg * k 64-bit words.
 template <typename T>
 void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s);

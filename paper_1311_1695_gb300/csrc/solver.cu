@@ -196,6 +196,8 @@ struct JD {
   // projects out, so only a fresh projected matrix removes it.
   bool explicit_h = std::is_same<TV, double>::value;
   int injections = 0;
+  double ev_rtol = 0.0;  // eigenvalue-accuracy test of an explicit check (0: off)
+  int nrv = 0;           // Ritz values of the last Rayleigh-Ritz (theta[0:nrv])
   PcgWork* pw = nullptr;
   // device-side convergence state (one outer iteration replays as a graph)
   int* state = nullptr;        // [S] 0 open, 1 converged, 2 candidate
@@ -282,8 +284,7 @@ struct JD {
 
   // CGS2 of columns [m0, m0+q) of V against [e, V[:, 0:m0]]; keep1 = surviving columns.
   void ortho(int m0, int q, double drop1) {
-    const GridBar bar{pw->bar, pw->bar + 1, reinterpret_cast<int*>(pw->bar + 2)};
-    if (ortho_fused<TV>(g, V, z.ldv, m0, q, drop1, oacc, keep1, seg_skip, bar, st) == 0) return;
+    if (ortho_fused<TV>(g, V, z.ldv, m0, q, drop1, oacc, keep1, seg_skip, pw->gridbar(), st, pw->max_ctas) == 0) return;
     TV* T = V + m0;
     // unit-normalise the columns
     coldots<TV>(g, red, T, z.ldv, T, z.ldv, q, tmp, 64, seg_skip, st);
@@ -355,9 +356,10 @@ struct JD {
   // (no host synchronisation, capturable).  Returns the new basis size.
   int tail(int m, bool explicit_check) {
     const int mk = rayleigh_ritz(m);
+    nrv = m;
     residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
-    converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, z.b, explicit_check ? 1 : 0, state, active, seg_skip,
-             pw->bar, status_d, segw, st);
+    converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, z.b, m, explicit_check ? ev_rtol : 0.0,
+             explicit_check ? 1 : 0, state, active, seg_skip, pw->bar, status_d, segw, st);
     cudaMemcpyAsync(status_h, status_d, sizeof(JdStatus), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(state_h, state, sizeof(int) * z.nseg, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(segw_h, segw, sizeof(double) * z.nseg, cudaMemcpyDeviceToHost, st);
@@ -398,7 +400,7 @@ struct JD {
     FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, theta, z.mmax, active, seg_skip,
                           delta, itmax, G->d_long_seg);
     f.early_exit = 1;
-    if (pcg_fused<TP>(g, f, st, 0) != 0) {
+    if (pcg_fused<TP>(g, f, st, pw->max_ctas) != 0) {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;
     }
@@ -422,7 +424,7 @@ struct JD {
 
 struct Params {
   int k, b, mk, itmax, max_outer, verbose;
-  double tol, delta, max_seconds;
+  double tol, delta, max_seconds, ev_rtol;
   std::chrono::steady_clock::time_point t0;
 };
 
@@ -458,6 +460,11 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("CUDA error in JD loop"); return LAP_ECUDA; }
   while (true) {
     const JdStatus stt = *jd.status_h;
+    if (stt.pcg_err) {  // a grid barrier of the start's orthonormalisation gave up
+      jd.pw->status(st, nullptr, nullptr);  // restores the zero-at-rest state
+      set_error("grid barrier of a persistent kernel timed out");
+      return LAP_ETIMEOUT;
+    }
     if (stt.bad) { set_error("NaN/Inf residual in JD"); return LAP_ENUMERIC; }
     if (P.verbose) {
       fprintf(stderr, "[lapeig] outer %d m %d worst residual/tol %.3e\n", outer, m, stt.worst);
@@ -485,7 +492,9 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
           bool segc = true;
           for (int j = 0; j < P.k; ++j) {
             const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
-            const bool c = r <= tol_abs[s] && jd.theta_h[(size_t)s * jd.z.mmax + j] <= jd.G->norm1[s];
+            const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
+            const bool c = r <= tol_abs[s] && th[j] <= jd.G->norm1[s] &&
+                           ev_accurate_host(th, jd.nrv, j, r, tol_abs[s], jd.ev_rtol);
             segc = segc && c;
             act[(size_t)s * 64 + j] = c ? 0 : 1;
           }
@@ -575,8 +584,8 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     }
     const JdStatus& s2 = *jd.status_h;
     if (s2.pcg_err) {
-      jd.pw->status(st, nullptr, nullptr);  // clears the flag
-      set_error("grid barrier in the correction solve timed out");
+      jd.pw->status(st, nullptr, nullptr);  // restores the zero-at-rest state
+      set_error("grid barrier of a persistent kernel timed out");
       return LAP_ETIMEOUT;
     }
     jd.inner_its += s2.pcg_steps;
@@ -610,11 +619,14 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     double worst = 0.0;
     int nconv = 0;
     bool prefix = true;
+    const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
     for (int j = 0; j < P.k; ++j) {
-      const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]) / G->norm1[s];
-      const bool real = jd.theta_h[(size_t)s * jd.z.mmax + j] <= G->norm1[s];
+      const double ra = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
+      const double r = ra / G->norm1[s];
+      const bool real = th[j] <= G->norm1[s];
       worst = std::max(worst, real ? r : 1.0);
-      if (prefix && real && r <= P.tol) ++nconv; else prefix = false;
+      const bool acc = ev_accurate_host(th, jd.nrv, j, ra, P.tol * G->norm1[s], P.ev_rtol);
+      if (prefix && real && r <= P.tol && acc) ++nconv; else prefix = false;
     }
     in.n_converged = nconv;
     // per graph: a batch member whose k pairs all meet the test is converged
@@ -663,6 +675,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   P.tol = tol;
   P.max_seconds = o.max_seconds;
   P.verbose = o.verbose;
+  P.ev_rtol = o.ev_rtol > 0.0 ? o.ev_rtol : (o.ev_rtol < 0.0 ? 0.0 : 1e-7);
   const int S = G->hg.nseg;
   for (int s = 0; s < S; ++s) {
     const int ns = G->row0[s + 1] - G->row0[s];
@@ -705,6 +718,10 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   PcgWork pw;
   rc = pw.init(S);
   if (rc) return rc;
+  pw.timeout_ns = timeout_ns_of(o.device_timeout_ms, G->timeout_ms);
+  pw.max_ctas = o.max_ctas > 0 ? o.max_ctas : G->max_ctas;
+  pw.hub_cnt = G->d_hub_cnt;
+  pw.nlong = G->dg.nlong;
   struct PwGuard { PcgWork& p; ~PwGuard() { p.release(); } } pw_guard{pw};
   int outer = 0;
   const bool mixed = o.precision == LAP_PREC_MIXED;
@@ -715,6 +732,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     JD<double, double> jd(G, z, st);
     jd.carve(a);
     jd.pw = &pw;
+    jd.ev_rtol = P.ev_rtol;
     int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
     const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30, o.cuda_graph >= 0);
@@ -745,6 +763,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   JD<double, float> j2(G, z, st);
   j2.carve(a2);
   j2.pw = &pw;
+  j2.ev_rtol = P.ev_rtol;
   const int mk = std::min(m_out, z.mk);
   convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);
   j2.n_matvec = j1.n_matvec;

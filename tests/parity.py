@@ -72,3 +72,47 @@ def check_eigpairs(g, ev, V, ev_ref, V_ref, tol=1e-8, ev_rtol=1e-7, angle=1e-6, 
     assert worst <= angle, f"cluster subspace angle {worst:.3e} > {angle}"
     return dict(max_rel_residual=rn.max() / lap.norm1, max_ev_rel_err=float(np.max(err / np.maximum(np.abs(ev_ref[:k]), 1e-300))),
                 max_angle=worst)
+
+
+def check_against_values(g, ev, V, ev_ref, tol=1e-8, ev_rtol=1e-7, angle=1e-6):
+    """Parity at sizes where the oracle's vectors are not kept: ev_ref holds
+    the m smallest eigenvalues on the complement of e (m > k, ascending, from
+    the oracle), V the k GPU vectors.
+
+    * explicit FP64 residual ||L v - ev v|| <= tol ||L||_1, V orthonormal, V
+      orthogonal to e;
+    * completeness and values: the k GPU values are the k smallest of ev_ref
+      within ev_rtol (nothing below them was missed, by the oracle's order);
+    * subspace angle per cluster without vectors (Davis-Kahan sin-theta): the
+      GPU vectors of a cluster of eigenvalues (spacing below max||r|| / angle)
+      are within ||R_c||_F / gap of the true eigenspace, gap = the distance
+      from the cluster to the nearest eigenvalue outside it (above the last
+      stored value every eigenvalue is >= that value); the bound must be
+      below `angle`, and a cluster reaching the end of the list fails."""
+    lap = Laplacian(g)
+    k = ev.size
+    R = lap.matvec(V) - V * ev[None, :]
+    rn = np.linalg.norm(R, axis=0)
+    assert rn.max() <= tol * lap.norm1, f"residual {rn.max() / lap.norm1:.3e} > {tol}"
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-8, "not orthonormal"
+    assert np.abs(V.sum(axis=0)).max() <= 1e-8 * np.sqrt(g.n), "not orthogonal to e"
+    assert ev_ref.size > k, "need more stored values than pairs"
+    err = np.abs(ev - ev_ref[:k])
+    rel = err / np.abs(ev_ref[:k])
+    assert np.all(rel <= ev_rtol), f"eigenvalue error {rel.max():.3e}"
+    gapc = max(rn.max(), 1e-300) / angle
+    worst = 0.0
+    for cl in clusters(ev_ref, gapc):
+        idx = [i for i in cl if i < k]
+        if not idx:
+            continue
+        if cl[-1] >= ev_ref.size - 1:
+            raise AssertionError(f"cluster {cl[0]}..{cl[-1]} reaches the end of the {ev_ref.size} stored values")
+        lo = ev_ref[cl[0] - 1] if cl[0] > 0 else -np.inf
+        hi = ev_ref[cl[-1] + 1]
+        th = ev[idx]
+        gap = min(th.min() - lo, hi - th.max())  # the GPU values to the spectrum outside the cluster
+        bound = np.linalg.norm(R[:, idx]) / gap
+        worst = max(worst, bound)
+    assert worst <= angle, f"certified cluster angle {worst:.3e} > {angle}"
+    return dict(max_rel_residual=rn.max() / lap.norm1, max_ev_rel_err=float(rel.max()), angle_bound=worst)

@@ -298,3 +298,55 @@ def test_pcg_correction_batched_with_hubs(pkg, dt):
         assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
         off += g.n
     Gd.close()
+
+
+_WIDE = {}
+
+
+def _wide_graph():
+    """A weighted BA graph (3,001 nodes, hubs) and its 30 smallest eigenvectors, once."""
+    if not _WIDE:
+        g = G.with_random_weights(G.ba_graph(3001, 2, 5), 8)
+        _WIDE["g"] = g
+        _WIDE["U"] = dense.smallest_eigpairs(g, 30)[1]
+    return _WIDE["g"], _WIDE["U"]
+
+
+def _ritz_block(g, U, b, seed):
+    """X: b Ritz vectors of a block near the smallest eigenvectors U (orthonormal,
+    orthogonal to e), theta their Ritz values, R their residuals (orthogonal to
+    [e, X]), as in a JD outer iteration."""
+    lap = Laplacian(g)
+    U = U[:, :b]
+    X = np.linalg.qr(blockops.project(U + 1e-2 * G.random_block(g.n, b, seed), None))[0]
+    theta, Yr = np.linalg.eigh(X.T @ lap.matvec(X))
+    X = X @ Yr
+    R = lap.matvec(X) - X * theta[None, :]
+    return X, theta, R
+
+
+@pytest.mark.parametrize("dt", [torch.float64, torch.float32])
+@pytest.mark.parametrize("b", [12, 20, 22, 30])
+@pytest.mark.parametrize("max_ctas", [0, 16, 2])
+def test_pcg_correction_wide_blocks_and_tiles_per_cta(pkg, dt, b, max_ctas):
+    """The correction solve at the block widths the benchmarked solves use
+    (b = 12: 16-lane row groups; b = 20, 22: the 24-column instantiation;
+    b = 30: 32 columns) and with several row tiles per CTA: max_ctas = 0 gives
+    one tile per CTA (X rows resident), 16 gives about three per CTA (resident
+    where shared memory allows, else re-staged per tile and phase), 2 gives
+    more than twenty (re-staged), against the oracle's fixed-step projected
+    PCG.  Weighted edges and hub rows included."""
+    g, U = _wide_graph()
+    Gd = pkg.Graph(g)
+    assert Gd.info()["nlong"] > 0
+    Gd.set_launch(max_ctas=max_ctas)
+    X, theta, R = _ritz_block(g, U, b, 40 + b)
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    X, R = X.astype(npdt), R.astype(npdt)
+    iters = 8
+    Td = Gd.pcg_correction(_dev(X, dt), torch.from_numpy(theta[None, :]).cuda(), _dev(R, dt), iters)
+    T = Td.cpu().double().numpy()
+    ref = blockops.pcg_correction(g, theta, R.astype(np.float64), X.astype(np.float64), iters)
+    err = (np.abs(T - ref).max(axis=0) / np.abs(ref).max(axis=0)).max()
+    assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
+    Gd.close()

@@ -39,3 +39,20 @@ def test_refuses_a_cluster_past_a_truncated_list():
         check_eigpairs(g, ev, V, ev_ref[:3], V_ref[:, :3], k=3)
     ev_all, V_all = all_pairs(g)
     check_eigpairs(g, ev_all[:4], V_all[:, :4], ev_all, V_all, k=4)
+
+
+def test_value_based_check_certifies_and_rejects():
+    g = G.grid_graph(9, 14)
+    ev_ref, V_ref = all_pairs(g)
+    from parity import check_against_values
+    k = 6
+    out = check_against_values(g, ev_ref[:k], V_ref[:, :k], ev_ref[:12])
+    assert out["angle_bound"] < 1e-6
+    # a missed eigenvalue: the pairs 0, 1, 2, 3, 4, 6 claimed as the six smallest
+    idx = [0, 1, 2, 3, 4, 6]
+    with pytest.raises(AssertionError, match="eigenvalue"):
+        check_against_values(g, ev_ref[idx], V_ref[:, idx], ev_ref[:12])
+    # a list that ends inside a cluster holding one of the pairs
+    fake = np.r_[ev_ref[:k], ev_ref[k - 1] + 1e-13]
+    with pytest.raises(AssertionError, match="end of the"):
+        check_against_values(g, ev_ref[:k], V_ref[:, :k], fake)

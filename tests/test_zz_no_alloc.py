@@ -41,19 +41,34 @@ def _noalloc(pkg, A, B, ones):
 
 @pytest.mark.parametrize("dt", [torch.float64, torch.float32])
 def test_noalloc_matches_lap_gram_twice(pkg, dt):
+    """Calls in a row with different shapes, the largest documented one
+    included (p + ones = 65, q = 64: every scratch slot up to the arrival
+    counter), each checked entry by entry against the FP64 host product
+    [1/n * 1 | A]^T B with a bound scaled by |A|^T |B| (a dropped or doubled
+    row tile, or a wrong column-mean row, exceeds it by orders of magnitude),
+    and against the handle-based lap_gram."""
     n = 50_000 + 37  # several tiles and a ragged tail
     gph = G.path_graph(n)  # lap_gram only needs the handle's row layout
     H = pkg.Graph(gph)
-    cases = [(12, 9, 1), (40, 20, 0)]  # two calls in a row, different shapes
+    rel = 1e-12 if dt == torch.float64 else 1e-5
+    cases = [(12, 9, 1), (40, 20, 0), (64, 64, 1), (30, 64, 0), (0, 5, 1)]
     for i, (p, q, ones) in enumerate(cases):
-        A = torch.from_numpy(G.random_block(n, p, 10 + i)).to(dt).cuda()
-        B = torch.from_numpy(G.random_block(n, q, 20 + i)).to(dt).cuda()
+        npdt = np.float64 if dt == torch.float64 else np.float32
+        A64 = G.random_block(n, p, 10 + i).astype(npdt).astype(np.float64)
+        B64 = G.random_block(n, q, 20 + i).astype(npdt).astype(np.float64)
+        A = torch.from_numpy(A64).to(dt).cuda() if p else None
+        B = torch.from_numpy(B64).to(dt).cuda()
         got = _noalloc(pkg, A, B, ones).cpu().numpy()
-        ref = H.gram(A, B, ones=bool(ones)).cpu().numpy()[0]
-        eps = np.finfo(np.float64 if dt == torch.float64 else np.float32).eps
-        tol = (64 if dt == torch.float64 else 64 * 32) * eps * n
+        ref = A64.T @ B64
+        bound = np.abs(A64).T @ np.abs(B64)
+        if ones:
+            ref = np.vstack([B64.mean(axis=0, keepdims=True), ref])
+            bound = np.vstack([np.abs(B64).mean(axis=0, keepdims=True), bound])
         assert got.shape == ref.shape
-        assert np.abs(got - ref).max() <= tol, np.abs(got - ref).max()
+        assert np.all(np.abs(got - ref) <= rel * bound), np.max(np.abs(got - ref) / bound)
+        if p:
+            lg = H.gram(A, B, ones=bool(ones)).cpu().numpy()[0]
+            assert np.all(np.abs(got - lg) <= 2 * rel * bound)
     H.close()
 
 
