@@ -53,6 +53,10 @@ def test_value_based_check_certifies_and_rejects():
     with pytest.raises(AssertionError, match="eigenvalue"):
         check_against_values(g, ev_ref[idx], V_ref[:, idx], ev_ref[:12])
     # a list that ends inside a cluster holding one of the pairs
+    # a list that ends inside a cluster holding one of the pairs: no
+    # per-cluster angle is certified, the k-subspace bound still is
     fake = np.r_[ev_ref[:k], ev_ref[k - 1] + 1e-13]
-    with pytest.raises(AssertionError, match="end of the"):
-        check_against_values(g, ev_ref[:k], V_ref[:, :k], fake)
+    out = check_against_values(g, ev_ref[:k], V_ref[:, :k], fake)
+    assert out["angle_bound"] is None
+    out = check_against_values(g, ev_ref[:k], V_ref[:, :k], ev_ref[:12])
+    assert out["subspace_bound"] < 1e-10
