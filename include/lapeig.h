@@ -164,14 +164,18 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
  * the handle's reduction and hub-chunk scratch is shared by them. */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
 
-/* Launch settings of the persistent kernels on this handle, used by the
- * step-level entry points and by solves whose opts leave them at 0:
- * max_ctas caps the grid (0 = every co-resident CTA; a smaller grid gives
- * each CTA more row tiles), device_timeout_ms bounds one CTA's wait at one
- * grid barrier (0 = 4000 ms; a wait that runs out makes the call return
- * LAP_ETIMEOUT and the handle's device state is restored).  Negative values
- * return LAP_EINVAL. */
-int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms);
+/* Launch settings of the correction solve and orthonormalisation on this
+ * handle, used by the step-level entry points and by solves whose opts leave
+ * them at 0: max_ctas caps the grid of the persistent kernels (0 = every
+ * co-resident CTA; a smaller grid gives each CTA more row tiles);
+ * device_timeout_ms bounds one CTA's wait at a grid barrier or for its bulk
+ * copies (0 = 4000 ms; a wait that runs out makes the call return
+ * LAP_ETIMEOUT and the handle's device state is restored); split_rows is the
+ * row count from which the correction solve runs as one launch per PCG phase
+ * with bulk-copy staging instead of one persistent launch (0 = 100,000;
+ * used when rows are at most 64 bytes and strides multiples of 16 bytes).
+ * Negative values return LAP_EINVAL. */
+int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms, int split_rows);
 
 /* Solve on a handle whose graphs are already on the device (the CSR is not
  * copied again).  evals: host [nseg * k] (graph s at s*k); evecs_dev: device
@@ -286,6 +290,54 @@ int lap_residual_norms(lap_graph* g, int dtype, const void* X, int ldx, const do
  * [e, X], as residuals of Ritz pairs of X are), T (device output, ldt = b). */
 int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const double* theta, const void* R,
                        int ldr, void* T, int ldt, int b, int iters, double delta, void* stream);
+
+/* ---------------------------------------------------------------- applications of the computed pairs
+ * Section 2 of the paper: the Fiedler pair (lambda_2, v_2) for graph
+ * bisection and the profile-reducing ordering, and the smallest pairs for
+ * approximations of the pseudo-inverse L^+ = sum_{i>=2} v_i v_i^T / lambda_i
+ * used by current-flow centralities.  Single-graph handles; device arrays are
+ * the caller's, FP64 unless stated; work on `stream`.  Entry points that return
+ * host scalars synchronise the stream. */
+
+/* Ordering by the Fiedler vector (the relaxed profile-reducing ordering of
+ * Section 2): perm (device int32 [n], nullable) receives the nodes sorted by
+ * their entry of v2 (device [n]), ties by node index; bandwidth
+ * max |pos(i) - pos(j)| and profile sum_r (r - min(r, min_j pos(j))) of A
+ * under that ordering and under the given one (host, nullable). */
+int lap_fiedler_order(lap_graph* g, const double* v2, int* perm, int64_t* bandwidth, int64_t* profile,
+                      int64_t* bandwidth0, int64_t* profile0, void* stream);
+
+/* Bisection (Section 2): side (device int32 [n]) = 0 for the n1 nodes first
+ * in the Fiedler ordering, 1 for the others (0 < n1 < n); cut (host) = the
+ * total weight of the edges between the sides, Eq. 1 at x_i = +-1/2; bound
+ * (host) = n1 n2 lambda2 / n, the minimum of the relaxed problem, which no
+ * bisection of these sizes cuts below. */
+int lap_fiedler_bisect(lap_graph* g, const double* v2, double lambda2, int64_t n1, int* side, double* cut,
+                       double* bound, void* stream);
+
+/* Y = P X for P built from k computed pairs (evals host [k], all > 0; V
+ * device row-major n x k, ld ldv, orthonormal and orthogonal to e):
+ * mode 0: P = T = sum_j v_j v_j^T / lambda_j (the partial sums of L^+);
+ * mode 1: P = S = (I - e e^T / n) / sigma + sum_j (1/lambda_j - 1/sigma) v_j v_j^T
+ * (the eigenvalues not computed replaced by sigma > 0, Section 2).
+ * X, Y device row-major n x b (b <= 64); 1 <= k <= 64. */
+int lap_pinv_apply(lap_graph* g, int k, const double* evals, const double* V, int ldv, int mode, double sigma,
+                   const double* X, int ldx, double* Y, int ldy, int b, void* stream);
+
+/* Current-flow closeness of every node with P as above: out[i] =
+ * 1 / sum_j R_ij, R_ij = P_ii + P_jj - 2 P_ij the effective resistance; as
+ * P e = 0 this is 1 / (n P_ii + tr P).  out device [n]. */
+int lap_cf_closeness(lap_graph* g, int k, const double* evals, const double* V, int ldv, int mode, double sigma,
+                     double* out, void* stream);
+
+/* Current-flow betweenness throughput with P as above, summed over npairs
+ * source-target pairs (host int64 [2 * npairs], s != t): for each pair the
+ * potentials are p = P (e_s - e_t) and node i other than s, t carries
+ * 1/2 sum_j A_ij |p_i - p_j|.  out device [n], not normalised (over all
+ * n (n - 1) / 2 pairs with P = L^+ it is the unnormalised current-flow
+ * betweenness). */
+int lap_cf_betweenness(lap_graph* g, int k, const double* evals, const double* V, int ldv, int mode, double sigma,
+                       int64_t npairs, const int64_t* pairs, double* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -111,7 +111,7 @@ _SIGNATURES = {
     "lap_graph_destroy": (None, [_P]),
     "lap_graph_info": (_I, [_P, _PI64, _PI, _PD, _PI, _PI]),
     "lap_graph_set_schedule": (_I, [_P, _I, _I]),
-    "lap_graph_set_launch": (_I, [_P, _I, _D]),
+    "lap_graph_set_launch": (_I, [_P, _I, _D, _I]),
     "lap_spmm": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gram": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
     "lap_gram_noalloc": (_I, [_I64, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
@@ -126,6 +126,11 @@ _SIGNATURES = {
     "lap_rayleigh_ritz": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "lap_residual_norms": (_I, [_P, _I, _P, _I, _P, _I, _P, _P]),
     "lap_pcg_correction": (_I, [_P, _I, _P, _I, _P, _P, _I, _P, _I, _I, _I, _D, _P]),
+    "lap_fiedler_order": (_I, [_P, _P, _P, _PI64, _PI64, _PI64, _PI64, _P]),
+    "lap_fiedler_bisect": (_I, [_P, _P, _D, _I64, _P, _PD, _PD, _P]),
+    "lap_pinv_apply": (_I, [_P, _I, _PD, _P, _I, _I, _D, _P, _I, _P, _I, _I, _P]),
+    "lap_cf_closeness": (_I, [_P, _I, _PD, _P, _I, _I, _D, _P, _P]),
+    "lap_cf_betweenness": (_I, [_P, _I, _PD, _P, _I, _I, _D, _I64, _PI64, _P, _P]),
 }
 
 
@@ -301,9 +306,10 @@ class Graph:
     def set_schedule(self, team=0, long_thresh=0):
         _check(lib().lap_graph_set_schedule(self.h, team, long_thresh), "lap_graph_set_schedule")
 
-    def set_launch(self, max_ctas=0, device_timeout_ms=0.0):
-        """CTA cap and grid-barrier wait limit of the persistent kernels."""
-        _check(lib().lap_graph_set_launch(self.h, max_ctas, device_timeout_ms), "lap_graph_set_launch")
+    def set_launch(self, max_ctas=0, device_timeout_ms=0.0, split_rows=0):
+        """CTA cap, device wait limit, and the row count from which the
+        correction solve runs as per-phase launches (lap_graph_set_launch)."""
+        _check(lib().lap_graph_set_launch(self.h, max_ctas, device_timeout_ms, split_rows), "lap_graph_set_launch")
 
     def eigs(self, k: int, tol: float = 1e-8, method: str = "jd", evecs=None, **opts):
         """Solve on the resident graph(s) (lap_eigs_graph).  evecs: optional
@@ -381,6 +387,73 @@ class Graph:
                                         ctypes.c_void_p(T.data_ptr()), b, b, iters, delta, _stream()),
                "lap_pcg_correction")
         return T
+
+
+def _evals_arg(evals):
+    e = np.ascontiguousarray(evals, dtype=np.float64)
+    return e, _ptr(e, ctypes.c_double)
+
+
+_MODES = {"T": 0, "S": 1}
+
+
+class Applications:
+    """The computed pairs put to use (Section 2): Fiedler ordering and
+    bisection, and the pseudo-inverse approximations with the current-flow
+    centralities, on a single-graph handle.  v2 and V are float64 CUDA
+    tensors (n, and n x k row-major)."""
+
+    def __init__(self, graph: "Graph"):
+        self.G = graph
+
+    def fiedler_order(self, v2):
+        import torch
+        perm = torch.empty(self.G.n, dtype=torch.int32, device=v2.device)
+        bw, pr, bw0, pr0 = (ctypes.c_int64() for _ in range(4))
+        _check(lib().lap_fiedler_order(self.G.h, ctypes.c_void_p(v2.data_ptr()), ctypes.c_void_p(perm.data_ptr()),
+                                       ctypes.byref(bw), ctypes.byref(pr), ctypes.byref(bw0), ctypes.byref(pr0),
+                                       _stream()), "lap_fiedler_order")
+        return perm, dict(bandwidth=bw.value, profile=pr.value, bandwidth0=bw0.value, profile0=pr0.value)
+
+    def fiedler_bisect(self, v2, lambda2: float, n1: int):
+        import torch
+        side = torch.empty(self.G.n, dtype=torch.int32, device=v2.device)
+        cut, bound = ctypes.c_double(), ctypes.c_double()
+        _check(lib().lap_fiedler_bisect(self.G.h, ctypes.c_void_p(v2.data_ptr()), float(lambda2), int(n1),
+                                        ctypes.c_void_p(side.data_ptr()), ctypes.byref(cut), ctypes.byref(bound),
+                                        _stream()), "lap_fiedler_bisect")
+        return side, cut.value, bound.value
+
+    def pinv_apply(self, evals, V, X, mode="T", sigma=0.0):
+        import torch
+        e, pe = _evals_arg(evals)
+        Y = torch.empty_like(X)
+        pv, ldv = _blk(V)
+        px, ldx = _blk(X)
+        py, ldy = _blk(Y)
+        _check(lib().lap_pinv_apply(self.G.h, e.size, pe, pv, ldv, _MODES[mode], float(sigma), px, ldx, py, ldy,
+                                    X.shape[1], _stream()), "lap_pinv_apply")
+        return Y
+
+    def closeness(self, evals, V, mode="T", sigma=0.0):
+        import torch
+        e, pe = _evals_arg(evals)
+        out = torch.empty(self.G.n, dtype=torch.float64, device=V.device)
+        pv, ldv = _blk(V)
+        _check(lib().lap_cf_closeness(self.G.h, e.size, pe, pv, ldv, _MODES[mode], float(sigma),
+                                      ctypes.c_void_p(out.data_ptr()), _stream()), "lap_cf_closeness")
+        return out
+
+    def betweenness(self, evals, V, pairs, mode="T", sigma=0.0):
+        import torch
+        e, pe = _evals_arg(evals)
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int64).reshape(-1, 2))
+        out = torch.empty(self.G.n, dtype=torch.float64, device=V.device)
+        pv, ldv = _blk(V)
+        _check(lib().lap_cf_betweenness(self.G.h, e.size, pe, pv, ldv, _MODES[mode], float(sigma), pr.shape[0],
+                                        _ptr(pr, ctypes.c_int64), ctypes.c_void_p(out.data_ptr()), _stream()),
+               "lap_cf_betweenness")
+        return out
 
 
 def lap_syev_batched(H):

@@ -256,10 +256,14 @@ int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   return graph_set_schedule(g, team, long_thresh);
 }
 
-int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms) {
-  if (!g || max_ctas < 0 || !(device_timeout_ms >= 0.0)) { set_error("bad arguments to lap_graph_set_launch"); return LAP_EINVAL; }
+int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms, int split_rows) {
+  if (!g || max_ctas < 0 || !(device_timeout_ms >= 0.0) || split_rows < 0) {
+    set_error("bad arguments to lap_graph_set_launch");
+    return LAP_EINVAL;
+  }
   g->max_ctas = max_ctas;
   g->timeout_ms = device_timeout_ms;
+  g->split_rows = split_rows;
   return LAP_OK;
 }
 
@@ -429,8 +433,10 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
   const int S = g->hg.nseg;
   const size_t es = dtype == LAP_F32 ? 4 : 8;
   const size_t n = (size_t)g->hg.n;
-  const int ldlx = (b + 3) / 4 * 4;
-  int rc = graph_scratch(g, 4 * n * b * es + n * ldlx * es + 512, sizeof(double) * S * 64 + 1024);
+  // L X at the work blocks' stride when its rows are 16-byte multiples (the
+  // per-phase form needs equal strides), else padded to 4 columns
+  const int ldlx = ((size_t)b * es) % 16 == 0 ? b : (b + 3) / 4 * 4;
+  int rc = graph_scratch(g, 5 * n * b * es + n * ldlx * es + 1024, sizeof(double) * S * 64 + 1024);
   if (rc) return rc;
   if (!g->pcg.acc1) {
     rc = g->pcg.init(S);
@@ -440,6 +446,7 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
   g->pcg.max_ctas = g->max_ctas;
   g->pcg.hub_cnt = g->d_hub_cnt;
   g->pcg.nlong = g->dg.nlong;
+  g->pcg.split_rows = g->split_rows;
   double* th = g->small;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaMemcpy2DAsync(th, 64 * sizeof(double), theta, b * sizeof(double), b * sizeof(double), S, cudaMemcpyDeviceToDevice,
@@ -450,8 +457,10 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     T* P = Z + n * b;
     T* AP = P + n * b;
     T* LX = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(AP + n * b) + 255) & ~(uintptr_t)255);
-    const FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, LX, ldlx, b, b, th, 64, nullptr, nullptr, delta, iters,
-                                   g->d_long_seg);
+    T* Xs = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(LX + n * ldlx) + 255) & ~(uintptr_t)255);
+    FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, LX, ldlx, b, b, th, 64, nullptr, nullptr, delta, iters,
+                             g->d_long_seg);
+    f.Xsv = Xs;
     if (pcg_fused<T>(g->dg, f, s, g->pcg.max_ctas) != 0) return check_cuda("lap_pcg_correction launch");
   });
   if (g->pcg.error_flag(s)) { set_error("grid barrier timed out"); return LAP_ETIMEOUT; }

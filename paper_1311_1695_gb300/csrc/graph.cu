@@ -400,6 +400,8 @@ FusedPcg PcgWork::args(const void* X, int ldx, const void* R, int ldr, void* Tt,
   f.done = done; f.res0 = res0; f.resn = resn; f.state_stride = (int64_t)nseg * 64; f.hub_seg = hub_seg;
   f.bar = gridbar();
   f.iters_out = reinterpret_cast<int*>(bar + 3);
+  f.stop = reinterpret_cast<int*>(bar + 4);
+  f.split_rows = split_rows;
   return f;
 }
 

@@ -27,6 +27,7 @@ struct PcgWork {
   size_t bytes = 0;         // the whole block (zero at rest)
   unsigned long long timeout_ns = kDefaultTimeoutNs;  // grid-barrier wait limit
   int max_ctas = 0;         // CTA cap of the persistent launches (0: all co-resident)
+  int split_rows = 0;       // rows from which the per-phase form is used (0: kSplitRows)
   int* hub_cnt = nullptr;   // the graph's hub arrival counters (zero at rest), reset with the rest
   int nlong = 0;
   int init(int nseg_);
@@ -86,6 +87,7 @@ struct lap_graph {
   lapeig::PcgWork pcg;          // persistent correction-solve state (lazy)
   int max_ctas = 0;             // persistent-kernel CTA cap (0: all co-resident)
   double timeout_ms = 0.0;      // grid-barrier wait limit (0: default)
+  int split_rows = 0;           // per-phase correction solve from this many rows (0: default)
 };
 
 namespace lapeig {

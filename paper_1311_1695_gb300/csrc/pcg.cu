@@ -551,8 +551,19 @@ double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
   return unit * (iters + 1);
 }
 
+bool pcg_uses_split(const DevGraph& g, const FusedPcg& f, int elem) {
+  const size_t rowb = (size_t)elem * f.ld;
+  return f.Xsv && f.stop && g.n >= (f.split_rows > 0 ? f.split_rows : kSplitRows) && f.ld >= f.b && rowb <= 64 &&
+         rowb % 16 == 0 && f.ldlx == f.ld;
+}
+
 template <typename T>
 int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
+  if (pcg_uses_split(g, f, (int)sizeof(T))) {
+    LAP_PROF("pcg_split", pcg_bytes(g, f.b, f.itmax, (int)sizeof(T)), s);
+    const int r = pcg_split<T>(g, f, s, max_ctas);
+    if (r <= 0) return r;
+  }
   LAP_PROF("pcg_fused", pcg_bytes(g, f.b, f.itmax, (int)sizeof(T)), s);
   if (f.b <= 8) return launch<T, 8>(g, f, s, max_ctas);
   if (f.b <= 16) return launch<T, 16>(g, f, s, max_ctas);

@@ -34,7 +34,14 @@ struct FusedPcg {
   GridBar bar;
   int early_exit = 0;   // single graph: stop when every column has converged
   int* iters_out = nullptr;  // receives the number of PCG steps done
+  // per-phase form (pcg_split.cu), used from split_rows rows on when the
+  // shapes allow it: scratch for X packed at stride ld, and its stop flag
+  const void* Xsv = nullptr;
+  int* stop = nullptr;
+  int split_rows = 0;   // 0: kSplitRows
 };
+
+constexpr int kSplitRows = 100000;
 
 // The expansion's CGS2 with Cholesky-QR of V[:, m0 : m0+q] against
 // [e, V[:, 0:m0]] (m0 <= 64, q <= 32) as one cooperative launch (ortho.cu);
@@ -46,9 +53,17 @@ template <typename T>
 int ortho_fused(const DevGraph& g, T* V, int ldv, int m0, int q, double drop1, double* acc, int* keep,
                 const int* seg_skip, const GridBar& bar, cudaStream_t s, int max_ctas);
 
-// Launch the whole correction solve; returns 0 or -1 (launch failure).
+// Launch the whole correction solve (the per-phase form for graphs of at
+// least split_rows rows when its shapes allow, else the persistent one);
+// returns 0 or -1 (launch failure).
 template <typename T>
 int pcg_fused(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas);
+// The per-phase form alone: 1 when the shapes do not allow it (nothing
+// launched), 0, or -1.
+template <typename T>
+int pcg_split(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas);
+// Whether pcg_fused takes the per-phase form for these arguments.
+bool pcg_uses_split(const DevGraph& g, const FusedPcg& f, int elem);
 // Algorithmic bytes of a solve of `iters` steps with elem-byte values.
 double pcg_bytes(const DevGraph& g, int b, int iters, int elem);
 

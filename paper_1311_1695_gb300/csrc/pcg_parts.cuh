@@ -206,12 +206,15 @@ __device__ __forceinline__ void stage_lx(T* lxs, const T* LX, int ldlx, int r0, 
 
 // Merge-path SpMM of one tile's ordinary nonzeros: accA[i][c] += sum over row
 // i of w * src[col][c].  The nonzeros are cut into SLOTS equal ranges, one per
-// row group; a group walks its range with kU independent gathers in flight and
+// row group; a group walks its range with U independent gathers in flight and
 // adds each finished (or cut) row into the shared row accumulator.
-template <typename T, int BMAX, int SLOTS>
+// scol, when set, holds the tile's column indices colidx[cbase ...] in
+// shared memory (one global round trip fewer per batch); RO: src is not
+// written during the launch, so the gathers may go through L1.
+template <typename T, int BMAX, int SLOTS, int U = kU, bool RO = false>
 __device__ __forceinline__ void walk_tile(const DevGraph& g, const T* __restrict__ w, const T* src, int lds,
                                           const int* s_rp, const int* s_erp, int nrows, T* accA, int grp, int c,
-                                          bool colok) {
+                                          bool colok, const int* scol = nullptr, int cbase = 0) {
   const int E0 = s_erp[0], E = s_erp[nrows] - E0;
   const int es = E0 + (int)((long long)E * grp / SLOTS);
   const int ee = E0 + (int)((long long)E * (grp + 1) / SLOTS);
@@ -225,11 +228,11 @@ __device__ __forceinline__ void walk_tile(const DevGraph& g, const T* __restrict
   int nx = s_erp[i + 1];
   int pb = s_rp[i] - s_erp[i];  // p = pb + e inside row i
   T a = T(0);
-  for (int e0 = es; e0 < ee; e0 += kU) {
-    int pu[kU], iu[kU];
+  for (int e0 = es; e0 < ee; e0 += U) {
+    int pu[U], iu[U];
     int ii = i;
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < U; ++u) {
       const int e = e0 + u;
       pu[u] = -1;
       iu[u] = ii;
@@ -244,21 +247,26 @@ __device__ __forceinline__ void walk_tile(const DevGraph& g, const T* __restrict
       }
     }
     // every slot loads (an exhausted slot repeats slot 0's nonzero, a lane
-    // past b reads column 0), so the kU column indices and then the kU
+    // past b reads column 0), so the U column indices and then the U
     // gathers issue back to back instead of one predicated chain each
-    int col[kU];
+    int col[U];
+    if (scol) {
 #pragma unroll
-    for (int u = 0; u < kU; ++u) col[u] = __ldg(g.colidx + (pu[u] >= 0 ? pu[u] : pu[0]));
+      for (int u = 0; u < U; ++u) col[u] = scol[(pu[u] >= 0 ? pu[u] : pu[0]) - cbase];
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) col[u] = __ldg(g.colidx + (pu[u] >= 0 ? pu[u] : pu[0]));
+    }
     const int cc = colok ? c : 0;
-    T v[kU];
+    T v[U];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) v[u] = __ldcg(src + (size_t)col[u] * lds + cc);
+    for (int u = 0; u < U; ++u) v[u] = RO ? __ldg(src + (size_t)col[u] * lds + cc) : __ldcg(src + (size_t)col[u] * lds + cc);
     if (w) {
 #pragma unroll
-      for (int u = 0; u < kU; ++u) v[u] *= __ldg(w + (pu[u] >= 0 ? pu[u] : pu[0]));
+      for (int u = 0; u < U; ++u) v[u] *= __ldg(w + (pu[u] >= 0 ? pu[u] : pu[0]));
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < U; ++u) {
       if (pu[u] >= 0) {
         if (iu[u] != i) {
           if (colok) atomicAdd(accA + i * BMAX + c, a);

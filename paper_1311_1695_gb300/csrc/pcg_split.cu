@@ -1,0 +1,775 @@
+// The correction solve of Algorithm 2 step 8 (Eq. 5, Section 3.2.1) for
+// large graphs: the same two-phase projected, Jacobi-preconditioned CG as
+// pcg.cu (same arithmetic, same accumulator and scalar protocol), but one
+// ordinary launch per phase instead of one persistent launch with grid
+// barriers, and the streamed row blocks of each row tile staged in shared
+// memory by bulk asynchronous copies.
+//
+// Why: on a graph of 10^6 rows the blocks of one PCG step (z~, X, L X, p,
+// q~, r, t) no longer fit in L2, and the persistent kernel, which loads its
+// rows through registers at two CTAs of 126 registers per SM, keeps too few
+// bytes in flight to use HBM (about an eighth of it).  Here one thread of a
+// CTA issues cp.async.bulk copies of the tile's rows of every streamed block
+// (contiguous: rows are row-major with a 16-byte multiple stride) into
+// shared memory, completing on an mbarrier; in phase M they are issued before
+// the merge-path SpMM walk of the tile and arrive while its gathers run.
+// The kernel boundary is the grid-wide barrier (a few microseconds, against
+// hundreds per phase at this size), and each phase gets its own register
+// budget.
+//
+// Launch sequence of one solve: pack (X into a zero-padded row stride),
+// init (L X, RES = -R, t = 0, z~ = RES / d, partial G2), then per step
+// M (beta, p', q~', partial G1) and B (alpha, t, r, z~, partial G2), and fin
+// (the final residual norms, step count, accumulators back to zero).  A
+// single-graph solve that meets its tolerance stops early: the M launch that
+// sees every column done raises a stop flag and the remaining launches
+// return at once.
+#include <algorithm>
+
+#include "common.cuh"
+#include "hub.cuh"
+#include "kernels.cuh"
+#include "pcg_fused.cuh"
+#include "pcg_parts.cuh"
+#include "prof.h"
+
+namespace lapeig {
+
+namespace {
+
+using namespace pcgp;
+
+// ---------------------------------------------------------------- bulk copies
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// The issuing thread arrives on the barrier announcing `bytes` of copies.
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// One bulk copy global -> shared of `bytes` (a multiple of 16; both
+// addresses 16-byte aligned), completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// The same with an L2 hint: evict-first for streamed blocks (each row is
+// used once per phase), so the gathered block stays in L2.
+__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                                unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned long long evict_first_policy() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, at most timeout_ns.  On time-out
+// the grid's error flag is raised and the wait is retried once more (the
+// copies still target this CTA's shared memory); returns false.
+__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, const GridBar& gb) {
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity)) {
+    if (global_ns() - t0 > gb.timeout_ns) {
+      atomicExch(gb.err, 1);
+      const unsigned long long t1 = global_ns();
+      while (!mbar_test(bar, parity) && global_ns() - t1 < gb.timeout_ns) {
+      }
+      return false;
+    }
+  }
+  return true;
+}
+
+// The launch-time view of a split solve: the persistent form's view plus
+// the stop flag and the packed X.
+template <typename T>
+struct SplitView {
+  View<T> v;
+  const T* Xs;   // X packed: row stride v.ld, columns [b, ld) zero
+  int* stop;     // raised by the M launch that ends a single-graph solve
+};
+
+// X (ldx) -> Xs (ld, zero-padded columns [b, ld)).
+template <typename T>
+__global__ void k_pack_x(int n, const T* __restrict__ X, int ldx, T* __restrict__ Xs, int ld, int b) {
+  const int64_t total = (int64_t)n * ld;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ld), c = (int)(e - (int64_t)r * ld);
+    Xs[e] = c < b ? X[(size_t)r * ldx + c] : T(0);
+  }
+}
+
+// Column indices of a tile staged in shared memory when its nonzeros (hub
+// rows included) number at most this; else the walk loads them from L2.
+constexpr int kColCap = 4096;
+// gathers in flight per row group in the walks of this form
+constexpr int kUSplit = 8;
+
+// Shared-memory layout of one split kernel (element offsets in T, every
+// region 16-byte aligned): red (flushes and staged totals), accA
+// (kTileRows x BMAX row accumulators), nstage staged blocks of
+// kTileRows x ld, then the tile's row pointers (ints) and the mbarrier.
+template <typename T, int BMAX, int BWL>
+struct SplitSmem {
+  static constexpr int red = (kWarps * (BMAX + 3) * BWL > (BMAX + 1) * BMAX + 2 * BMAX)
+                                 ? kWarps * (BMAX + 3) * BWL
+                                 : (BMAX + 1) * BMAX + 2 * BMAX;
+  static constexpr int red_al = (red + 3) / 4 * 4;
+  static constexpr int acc = kTileRows * BMAX;
+  // with_acc: the row accumulators of an SpMM walk and the tile's staged
+  // column indices (init, phase M)
+  static size_t bytes(int nstage, int ld, bool with_acc) {
+    const size_t t = sizeof(T) * ((size_t)red_al + (with_acc ? acc : 0) + (size_t)nstage * kTileRows * ld + kTileRows);
+    return (t + 15) / 16 * 16 + sizeof(int) * (2 * (kTileRows + 4) + (with_acc ? kColCap : 0)) + 16;
+  }
+};
+
+// Row helpers over a staged row of stride ld (a multiple of the vector
+// width, at most BMAX; columns [b, ld) are zero): y - G[0] - sum_i x_i G[i+1],
+// acc[0] += z and acc[1 + i] += x_i z, sum_i r_i G[i+1].
+template <typename T, int BMAX>
+__device__ __forceinline__ T project_ld(T y, const T* __restrict__ xr, const T (&Gc)[BMAX + 1], int ld) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  y -= Gc[0];
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    if (i < ld) {
+      const V v = *reinterpret_cast<const V*>(xr + i);
+      if constexpr (W == 4) {
+        y -= v.x * Gc[i + 1]; y -= v.y * Gc[i + 2]; y -= v.z * Gc[i + 3]; y -= v.w * Gc[i + 4];
+      } else {
+        y -= v.x * Gc[i + 1]; y -= v.y * Gc[i + 2];
+      }
+    }
+  }
+  return y;
+}
+
+template <typename T, int BMAX>
+__device__ __forceinline__ void gram_ld(T (&acc)[BMAX + 1], const T* __restrict__ xr, T z, int ld) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  acc[0] += z;
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    if (i < ld) {
+      const V v = *reinterpret_cast<const V*>(xr + i);
+      if constexpr (W == 4) {
+        acc[i + 1] += v.x * z; acc[i + 2] += v.y * z; acc[i + 3] += v.z * z; acc[i + 4] += v.w * z;
+      } else {
+        acc[i + 1] += v.x * z; acc[i + 2] += v.y * z;
+      }
+    }
+  }
+}
+
+template <typename T, int BMAX>
+__device__ __forceinline__ T dot_ld(const T* __restrict__ r, const T (&Gc)[BMAX + 1], int ld) {
+  using V = typename VecOf<T>::type;
+  constexpr int W = VecOf<T>::w;
+  T s = T(0);
+#pragma unroll
+  for (int i = 0; i < BMAX; i += W) {
+    if (i < ld) {
+      const V v = *reinterpret_cast<const V*>(r + i);
+      if constexpr (W == 4) {
+        s += v.x * Gc[i + 1]; s += v.y * Gc[i + 2]; s += v.z * Gc[i + 3]; s += v.w * Gc[i + 4];
+      } else {
+        s += v.x * Gc[i + 1]; s += v.y * Gc[i + 2];
+      }
+    }
+  }
+  return s;
+}
+
+// Per-CTA context of a split kernel: its shared-memory regions and the
+// mbarrier of its bulk copies (phase bit flips at every completed wait).
+template <typename T, int BMAX, int BWL>
+struct Ctx {
+  T* red;
+  T* accA;
+  T* stage;      // nstage blocks of kTileRows x ld (block i at stage + i * kTileRows * ld)
+  T* s_deg;      // [kTileRows] the tile's degrees
+  int* s_rp;     // [kTileRows + 1]
+  int* s_erp;    // [kTileRows + 1]
+  int* s_col;    // [kColCap] the tile's column indices (with_acc)
+  unsigned long long* bar;
+  unsigned phase;
+  unsigned long long policy;  // evict-first
+  __device__ void setup(unsigned char* smem, int nstage, int ld, bool with_acc) {
+    using L = SplitSmem<T, BMAX, BWL>;
+    const int na = with_acc ? L::acc : 0;
+    red = reinterpret_cast<T*>(smem);
+    accA = red + L::red_al;
+    stage = accA + na;
+    s_deg = stage + (size_t)nstage * kTileRows * ld;
+    const size_t tb = sizeof(T) * ((size_t)L::red_al + na + (size_t)nstage * kTileRows * ld + kTileRows);
+    s_rp = reinterpret_cast<int*>(smem + (tb + 15) / 16 * 16);
+    s_erp = s_rp + kTileRows + 4;
+    s_col = s_erp + kTileRows + 4;
+    bar = reinterpret_cast<unsigned long long*>(s_col + (with_acc ? kColCap : 0));
+    phase = 0;
+    policy = evict_first_policy();
+    if (threadIdx.x == 0) mbar_init(bar);
+    for (int e = threadIdx.x; e < na; e += kThreads) accA[e] = T(0);
+    __syncthreads();
+  }
+  __device__ T* blk(int i, int ld) { return stage + (size_t)i * kTileRows * ld; }
+  // thread 0: copy rows [r0, r1) of the nb blocks src[i] (row stride ld[i])
+  // into staged block i
+  // (blocks whose bit is set in keep are copied without the evict-first hint)
+  template <int NB>
+  __device__ void issue(const T* const (&src)[NB], const int (&ldb)[NB], int ld, int r0, int r1, unsigned keep = 0) {
+    if (threadIdx.x != 0) return;
+    unsigned total = 0;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) total += (unsigned)(sizeof(T) * (size_t)(r1 - r0) * ldb[i]);
+    mbar_expect(bar, total);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const unsigned bytes = (unsigned)(sizeof(T) * (size_t)(r1 - r0) * ldb[i]);
+      if (keep & (1u << i)) bulk_g2s(blk(i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar);
+      else bulk_g2s_stream(blk(i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar, policy);
+    }
+  }
+  // every thread: wait for the last issue; false when the wait ran out
+  __device__ bool wait(const GridBar& gb) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = mbar_wait(bar, phase, gb) ? 1 : 0;
+    phase ^= 1u;
+    __syncthreads();
+    return s_ok != 0;
+  }
+  // the tile's row pointers, effective row pointers and degrees
+  __device__ void rows(const DevGraph& g, const Tile& t, const T* deg) {
+    for (int i = threadIdx.x; i <= t.r1 - t.r0; i += kThreads) {
+      s_rp[i] = g.rowptr[t.r0 + i];
+      s_erp[i] = g.erp[t.r0 + i];
+      if (i < t.r1 - t.r0) s_deg[i] = deg[t.r0 + i];
+    }
+  }
+  // after rows() and a CTA barrier: the tile's column indices when they
+  // fit (returns them, else null; the same answer in every thread)
+  __device__ const int* cols(const DevGraph& g, int nrows) {
+    const int p0 = s_rp[0], cnt = s_rp[nrows] - p0;
+    if (cnt > kColCap) return nullptr;
+    for (int q = threadIdx.x; q < cnt; q += kThreads) s_col[q] = __ldg(g.colidx + p0 + q);
+    return s_col;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ const T* deg_of(const DevGraph& g) {
+  return reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
+}
+template <typename T>
+__device__ __forceinline__ const T* w_of(const DevGraph& g) {
+  return reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.w32 : (const void*)g.w64);
+}
+
+// accumulators of graph s, parity q
+template <typename T>
+__device__ __forceinline__ T* acc1_of(const View<T>& f, const DevGraph& g, int q, int s) {
+  return f.acc1 + ((size_t)q * g.nseg + s) * f.acc_stride;
+}
+template <typename T>
+__device__ __forceinline__ T* acc2_of(const View<T>& f, const DevGraph& g, int q, int s) {
+  return f.acc2 + ((size_t)q * g.nseg + s) * f.acc_stride;
+}
+
+// A graph's nout + 2b totals into red, one load per value for the CTA.
+template <typename T>
+__device__ __forceinline__ const T* stage_totals(T* red, const T* A, int cnt) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < cnt; e += kThreads) red[e] = __ldcg(A + e);
+  __syncthreads();
+  return red;
+}
+
+// Gc[i] = column c of the totals' row i (row 0, the ones row, scaled to the
+// graph's mean); zero for i > b and lanes past b.
+template <typename T, int BMAX>
+__device__ __forceinline__ void coeffs(T (&Gc)[BMAX + 1], const T* tot, int b, int c, bool colok, int nrows) {
+  const int cc = colok ? c : 0;
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) {
+    const T v = tot[(i <= b ? i : b) * b + cc];
+    Gc[i] = (colok && i <= b) ? v : T(0);
+  }
+  Gc[0] *= T(1) / (T)nrows;
+}
+
+// ---------------------------------------------------------------- init
+// LX = L X (the SpMM of X); RES = -R (active columns), t = 0, z~ = RES / d;
+// partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity 1.
+template <typename T, int BMAX, int BWL>
+__global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T> sv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const View<T>& f = sv.v;
+  Ctx<T, BMAX, BWL> cx;
+  const int ld = f.ld;
+  cx.setup(smem_raw, 1, ld, true);
+  constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
+  const int b = f.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, grp = warp * RW + lane / BWL;
+  const bool colok = c < b;
+  const T* __restrict__ deg = deg_of<T>(g);
+  const T* __restrict__ w = w_of<T>(g);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sv.stop = 0;
+  T acc[BMAX + 1];
+  T ex[2] = {T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
+  int cur = -1;
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (f.seg_skip && f.seg_skip[t.seg]) continue;
+    if (t.seg != cur) {
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
+      cur = t.seg;
+    }
+    const int nrows = t.r1 - t.r0;
+    __syncthreads();  // the previous tile's readers are done with the stage
+    {
+      const T* src[1] = {sv.Xs};
+      const int lds[1] = {ld};
+      cx.issue<1>(src, lds, ld, t.r0, t.r1);
+    }
+    cx.rows(g, t, deg);
+    __syncthreads();
+    const int* scol = cx.cols(g, nrows);
+    __syncthreads();
+    walk_tile<T, BMAX, SLOTS, kUSplit, true>(g, w, sv.Xs, ld, cx.s_rp, cx.s_erp, nrows, cx.accA, grp, c, colok, scol,
+                                             cx.s_rp[0]);
+    if (!cx.wait(f.bar)) return;  // also the CTA barrier after the walk
+    const T* xs = cx.blk(0, ld);
+    const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
+    if (c < f.ldlx) {
+      for (int il = grp; il < nrows; il += SLOTS) {
+        const int r = t.r0 + il;
+        const T dv = cx.s_deg[il];
+        const T* xr = xs + (size_t)il * ld;
+        if (cx.s_rp[il + 1] - cx.s_rp[il] <= g.long_thresh) {  // hub rows: by their chunks
+          const T a = cx.accA[il * BMAX + c];
+          cx.accA[il * BMAX + c] = T(0);
+          f.LX[(size_t)r * f.ldlx + c] = colok ? dv * xr[c] - a : T(0);
+        }
+        if (colok) {
+          const size_t o = (size_t)r * ld + c;
+          const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
+          const T z = res / dv;
+          f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
+          gram_ld<T, BMAX>(acc, xr, z, ld);
+          ex[0] += res * z;
+          ex[1] += res * res;
+        }
+      }
+    }
+  }
+  hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, sv.Xs, ld, cx.red, b, grp, c, colok,
+                         [&](const int4& cc, int, T a) {
+                           const int row = cc.x;
+                           if (lane < BWL && c < f.ldlx)
+                             f.LX[(size_t)row * f.ldlx + c] = colok ? deg[row] * sv.Xs[(size_t)row * ld + c] - a : T(0);
+                         });
+  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
+}
+
+// ---------------------------------------------------------------- phase M
+// beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
+// p' = P z~ + beta p and q~' = (L - theta) p' via
+//   (L - theta) P z~ = (L z~ - theta z~) + theta G2[0] - [0 | LX - theta X] G2;
+// partial G1 = [1|X]^T q~', p'.q~' into acc1 parity `par`.  Staged blocks:
+// z~, X, LX, p, q~ rows of the tile (issued before its SpMM walk).
+template <typename T, int BMAX, int BWL>
+__global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> sv, int it) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const View<T>& f = sv.v;
+  if (__ldcg(sv.stop)) return;
+  const int ld = f.ld, b = f.b;
+  const int par = it & 1, prv = par ^ 1;
+  const int nout = (b + 1) * b;
+  const int64_t ss = f.state_stride;
+  // single graph: stop once every column met delta after the previous step
+  // (every CTA derives the same decision from the same totals)
+  if (f.early_exit && it > 0) {
+    int mine = 1;
+    T rn = T(0);
+    if (threadIdx.x < b) {
+      rn = sqrt(__ldcg(acc2_of(f, g, prv, 0) + nout + b + threadIdx.x));
+      const int d0 = __ldcg(f.done + (size_t)prv * ss + threadIdx.x);
+      mine = d0 || !(rn > (T)f.delta * __ldcg(f.res0 + threadIdx.x)) || !isfinite(rn);
+    }
+    if (__syncthreads_and(mine)) {
+      if (blockIdx.x == 0) {
+        if (threadIdx.x < b) f.resn[threadIdx.x] = rn;
+        if (threadIdx.x == 0) {
+          *sv.stop = 1;
+          if (f.iters_out) *f.iters_out = it;
+        }
+      }
+      return;
+    }
+  }
+  Ctx<T, BMAX, BWL> cx;
+  cx.setup(smem_raw, 5, ld, true);
+  constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, grp = warp * RW + lane / BWL;
+  const bool colok = c < b;
+  const T* __restrict__ deg = deg_of<T>(g);
+  const T* __restrict__ w = w_of<T>(g);
+  const T* Xs = sv.Xs;
+  T acc[BMAX + 1];
+  T ex[2] = {T(0), T(0)};
+  T Gc[BMAX + 1];
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) acc[i] = Gc[i] = T(0);
+  // acc1 parity prv was last read in the previous step's phase B
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (t.idx_in_seg == 0 && !(f.seg_skip && f.seg_skip[t.seg]))
+      for (int e = threadIdx.x; e < f.acc_stride; e += kThreads) acc1_of(f, g, prv, t.seg)[e] = T(0);
+  }
+  auto beta_of = [&](int seg, T rho_new) -> T {
+    if (it == 0 || !colok) return T(0);
+    const size_t k = (size_t)seg * f.bstride + c;
+    const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
+    const int dn = __ldcg(f.done + (size_t)prv * ss + k);
+    return (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
+  };
+  int cur = -1, gseg = -1;
+  T thc = T(0), be = T(0);
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (f.seg_skip && f.seg_skip[t.seg]) continue;
+    if (t.seg != cur) {
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
+      cur = gseg = t.seg;
+      const T* tot = stage_totals(cx.red, acc2_of(f, g, prv, t.seg), nout + 2 * b);
+      thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
+      coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
+      be = beta_of(t.seg, colok ? tot[nout + c] : T(0));
+      if (t.idx_in_seg == 0 && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
+        const size_t k = (size_t)t.seg * f.bstride + c;
+        const T rho_new = tot[nout + c];
+        const T rn = sqrt(tot[nout + b + c]);
+        int dn;
+        if (it == 0) {
+          const int act = f.active == nullptr || f.active[k];
+          dn = (!act || rn == T(0) || rho_new == T(0) || !isfinite(rho_new)) ? 1 : 0;
+          f.res0[k] = rn;
+        } else {
+          dn = __ldcg(f.done + (size_t)prv * ss + k);
+          if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
+        }
+        f.rho[(size_t)par * ss + k] = rho_new;
+        f.done[(size_t)par * ss + k] = dn;
+        f.resn[k] = rn;
+      }
+    }
+    const int nrows = t.r1 - t.r0;
+    __syncthreads();  // the previous tile's epilogue is done with the stage and accA
+    {
+      const T* src[5] = {f.Z, Xs, f.LX, f.P, f.AP};
+      const int lds[5] = {ld, ld, ld, ld, ld};
+      cx.issue<5>(src, lds, ld, t.r0, t.r1, 1u);  // z~ (gathered too) without the evict-first hint
+    }
+    cx.rows(g, t, deg);
+    __syncthreads();
+    const int* scol = cx.cols(g, nrows);
+    __syncthreads();
+    // z~ is not written in this phase: gathers through L1
+    walk_tile<T, BMAX, SLOTS, kUSplit, true>(g, w, f.Z, ld, cx.s_rp, cx.s_erp, nrows, cx.accA, grp, c, colok, scol,
+                                             cx.s_rp[0]);
+    if (!cx.wait(f.bar)) return;
+    if (colok) {
+      const T* sz = cx.blk(0, ld);
+      const T* sx = cx.blk(1, ld);
+      const T* slx = cx.blk(2, ld);
+      const T* sp = cx.blk(3, ld);
+      const T* sq = cx.blk(4, ld);
+      for (int il = grp; il < nrows; il += SLOTS) {
+        if (cx.s_rp[il + 1] - cx.s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
+        const int r = t.r0 + il;
+        const T dv = cx.s_deg[il];
+        const size_t so = (size_t)il * ld;
+        const T zv = sz[so + c];
+        const T a = cx.accA[il * BMAX + c];
+        cx.accA[il * BMAX + c] = T(0);
+        const T pz = project_ld<T, BMAX>(zv, sx + so, Gc, ld);
+        const T sl = dot_ld<T, BMAX>(slx + so, Gc, ld);
+        T q = dv * zv - a - sl - thc * pz;
+        T p = pz;
+        if (be != T(0)) { q += be * sq[so + c]; p += be * sp[so + c]; }
+        const size_t o = (size_t)r * ld + c;
+        __stcs(f.P + o, p);
+        __stcs(f.AP + o, q);
+        gram_ld<T, BMAX>(acc, sx + so, q, ld);
+        ex[0] += p * q;
+      }
+    }
+  }
+  // hub rows: the completing warp forms p' and q~' of the row from its
+  // graph's totals and adds its share of G1 and p'.q~' (to the CTA's
+  // registers when the hub is in the CTA's current graph, else atomically)
+  hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, f.Z, ld, cx.red, b, grp, c, colok,
+                         [&](const int4& cc, int seg, T a) {
+    const int row = cc.x;
+    const bool own = colok && lane < BWL;  // group 0 holds the row
+    if (seg != gseg) {  // warp-uniform
+      const T* A = acc2_of(f, g, prv, seg);
+      const int c0 = colok ? c : 0;
+#pragma unroll
+      for (int i = 0; i <= BMAX; ++i) {
+        const T v = __ldcg(A + (i <= b ? i : b) * b + c0);
+        Gc[i] = (colok && i <= b) ? v : T(0);
+      }
+      Gc[0] *= T(1) / (T)seg_rows(g, seg);
+      be = beta_of(seg, colok ? __ldcg(A + nout + c) : T(0));
+      thc = colok ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
+      gseg = seg;
+    }
+    const T bs = be;
+    const T th = own ? thc : T(0);
+    const size_t o = (size_t)row * ld + c;
+    const T zr = own ? __ldcg(f.Z + o) : T(0);
+    const T xc = own ? Xs[(size_t)row * ld + c] : T(0);
+    const T lc = own ? __ldcg(f.LX + (size_t)row * f.ldlx + c) : T(0);
+    T sx = Gc[0], sl = T(0);
+#pragma unroll
+    for (int i = 0; i < BMAX; ++i) {
+      const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+      const T li = __shfl_sync(0xffffffffu, lc, i, BWL);
+      sx += xi * Gc[i + 1];
+      sl += li * Gc[i + 1];
+    }
+    const T pz = zr - sx;
+    T q = deg[row] * zr - a - sl - th * pz;
+    T p = pz;
+    if (own && bs != T(0)) { q += bs * __ldcg(f.AP + o); p += bs * __ldcg(f.P + o); }
+    if (!own) { q = T(0); p = T(0); }
+    if (own) { f.P[o] = p; f.AP[o] = q; }
+    if (seg == cur) {
+      gram_col<T, BMAX, BWL>(acc, xc, q, b);
+      ex[0] += p * q;
+    } else {
+      T* a1 = acc1_of(f, g, par, seg);
+      for (int i = 0; i < b; ++i) {
+        const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
+        if (own) atomicAdd(a1 + (size_t)(1 + i) * b + c, xi * q);
+      }
+      if (own) {
+        atomicAdd(a1 + c, q);
+        atomicAdd(a1 + nout + c, p * q);
+      }
+    }
+  });
+  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
+}
+
+// ---------------------------------------------------------------- phase B
+// alpha = rho / p.q~; q = q~ - [1|X] G1; t += alpha p; r -= alpha q;
+// z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity `par`.
+// Staged blocks: q~, r, t, p, X rows of the tile.
+template <typename T, int BMAX, int BWL>
+__global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> sv, int it) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const View<T>& f = sv.v;
+  if (__ldcg(sv.stop)) return;
+  const int ld = f.ld, b = f.b;
+  const int par = it & 1, prv = par ^ 1;
+  const int nout = (b + 1) * b;
+  const int64_t ss = f.state_stride;
+  Ctx<T, BMAX, BWL> cx;
+  cx.setup(smem_raw, 5, ld, false);
+  constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, grp = warp * RW + lane / BWL;
+  const bool colok = c < b;
+  const T* __restrict__ deg = deg_of<T>(g);
+  T acc[BMAX + 1];
+  T ex[2] = {T(0), T(0)};
+  T Gc[BMAX + 1];
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) acc[i] = Gc[i] = T(0);
+  // acc2 parity prv was last read in this step's phase M
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (t.idx_in_seg == 0 && !(f.seg_skip && f.seg_skip[t.seg]))
+      for (int e = threadIdx.x; e < f.acc_stride; e += kThreads) acc2_of(f, g, prv, t.seg)[e] = T(0);
+  }
+  int cur = -1;
+  T al = T(0);
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (f.seg_skip && f.seg_skip[t.seg]) continue;
+    if (t.seg != cur) {
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+      cur = t.seg;
+      const T* tot = stage_totals(cx.red, acc1_of(f, g, par, t.seg), nout + 2 * b);
+      coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
+      al = T(0);
+      if (colok) {
+        const size_t k = (size_t)t.seg * f.bstride + c;
+        const T pq = tot[nout + c];
+        const T rho = __ldcg(f.rho + (size_t)par * ss + k);
+        const int dn = __ldcg(f.done + (size_t)par * ss + k);
+        if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
+      }
+    }
+    const int nrows = t.r1 - t.r0;
+    __syncthreads();  // the previous tile's readers are done with the stage
+    {
+      const T* src[5] = {f.AP, f.RES, f.Tt, f.P, sv.Xs};
+      const int lds[5] = {ld, ld, ld, ld, ld};
+      cx.issue<5>(src, lds, ld, t.r0, t.r1);
+    }
+    cx.rows(g, t, deg);
+    if (!cx.wait(f.bar)) return;
+    if (colok) {
+      const T* sq = cx.blk(0, ld);
+      const T* sr = cx.blk(1, ld);
+      const T* st = cx.blk(2, ld);
+      const T* sp = cx.blk(3, ld);
+      const T* sx = cx.blk(4, ld);
+      for (int il = grp; il < nrows; il += SLOTS) {
+        const int r = t.r0 + il;
+        const size_t so = (size_t)il * ld;
+        const T q = project_ld<T, BMAX>(sq[so + c], sx + so, Gc, ld);
+        const T res = sr[so + c] - al * q;
+        const T z = res / cx.s_deg[il];
+        const size_t o = (size_t)r * ld + c;
+        __stcs(f.Tt + o, st[so + c] + al * sp[so + c]);
+        __stcs(f.RES + o, res);
+        f.Z[o] = z;  // gathered in the next phase M: normal priority
+        gram_ld<T, BMAX>(acc, sx + so, z, ld);
+        ex[0] += res * z;
+        ex[1] += res * res;
+      }
+    }
+  }
+  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+}
+
+// ---------------------------------------------------------------- fin
+// The residual norms after the last step (when the solve did not stop
+// early), the step count, and every accumulator back to zero.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_split_fin(DevGraph g, SplitView<T> sv, int itmax) {
+  const View<T>& f = sv.v;
+  const int b = f.b, nout = (b + 1) * b;
+  const bool stopped = __ldcg(sv.stop) != 0;
+  const int last = (itmax + 1) & 1;  // parity of the last phase B
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (t.idx_in_seg != 0 || (f.seg_skip && f.seg_skip[t.seg])) continue;
+    if (!stopped && threadIdx.x < b)
+      f.resn[(size_t)t.seg * f.bstride + threadIdx.x] = sqrt(__ldcg(acc2_of(f, g, last, t.seg) + nout + b + threadIdx.x));
+    __syncthreads();
+    for (int e = threadIdx.x; e < f.acc_stride; e += kThreads) {
+      acc1_of(f, g, 0, t.seg)[e] = T(0); acc1_of(f, g, 1, t.seg)[e] = T(0);
+      acc2_of(f, g, 0, t.seg)[e] = T(0); acc2_of(f, g, 1, t.seg)[e] = T(0);
+    }
+  }
+  if (!stopped && f.iters_out && blockIdx.x == 0 && threadIdx.x == 0) *f.iters_out = itmax;
+}
+
+template <typename T, int BMAX>
+int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
+  constexpr int BWL = BMAX <= 4 ? 4 : (BMAX > 16 ? 32 : BMAX);  // lanes per row, as in the persistent form
+  const int ld = f.ld;
+  View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
+             static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv),
+             static_cast<T*>(f.LXv), f.ldlx, f.ld, f.b,
+             f.theta, f.sth, f.active, f.bstride, f.seg_skip, f.delta, f.itmax, reinterpret_cast<T*>(f.acc1),
+             reinterpret_cast<T*>(f.acc2), f.acc_stride, reinterpret_cast<T*>(f.rho), f.done,
+             reinterpret_cast<T*>(f.res0), reinterpret_cast<T*>(f.resn), f.state_stride, f.hub_seg, f.bar,
+             f.early_exit && g.nseg == 1, f.iters_out, 0};
+  SplitView<T> sv{ff, static_cast<const T*>(f.Xsv), f.stop};
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  auto grid_of = [&](const void* kern, size_t smem) {
+    // the opt-in above 48 KB belongs to the current device: set at every launch
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    int grid = per_sm * nsm;
+    if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+    if (grid > g.ntiles) grid = g.ntiles;
+    return grid < 1 ? 1 : grid;
+  };
+  using L = SplitSmem<T, BMAX, BWL>;
+  auto ki = k_split_init<T, BMAX, BWL>;
+  auto km = k_split_m<T, BMAX, BWL>;
+  auto kb = k_split_b<T, BMAX, BWL>;
+  const size_t si = L::bytes(1, ld, true), sm = L::bytes(5, ld, true), sb = L::bytes(5, ld, false);
+  const int gi = grid_of(reinterpret_cast<const void*>(ki), si);
+  const int gm = grid_of(reinterpret_cast<const void*>(km), sm);
+  const int gb = grid_of(reinterpret_cast<const void*>(kb), sb);
+  const int64_t tot = (int64_t)g.n * ld;
+  const int pgrid = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)nsm * 8);
+  k_pack_x<T><<<pgrid > 0 ? pgrid : 1, 256, 0, s>>>(g.n, ff.X, f.ldx, const_cast<T*>(sv.Xs), ld, f.b);
+  ki<<<gi, kThreads, si, s>>>(g, sv);
+  for (int it = 0; it < f.itmax; ++it) {
+    km<<<gm, kThreads, sm, s>>>(g, sv, it);
+    kb<<<gb, kThreads, sb, s>>>(g, sv, it);
+  }
+  k_split_fin<T><<<std::max(1, std::min(g.ntiles, nsm * 4)), kThreads, 0, s>>>(g, sv, f.itmax);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+// Correction solve by per-phase launches with bulk-copy staging: returns 1
+// (and launches nothing) when the shapes do not allow it -- rows of more than
+// 64 bytes (FP32 beyond 16 columns, FP64 beyond 8), a row stride that is not
+// a multiple of 16 bytes, L X with another stride, an unaligned block, or no
+// scratch for the packed X -- else 0, or -1 on a launch failure.
+template <typename T>
+int pcg_split(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
+  const size_t rowb = sizeof(T) * (size_t)f.ld;
+  if (!f.Xsv || !f.stop || f.ld < f.b || rowb > 64 || rowb % 16 != 0 || f.ldlx != f.ld) return 1;
+  const void* ptrs[7] = {f.Xsv, f.Ttv, f.RESv, f.Zv, f.Pv, f.APv, f.LXv};
+  for (const void* p : ptrs)
+    if (!aligned16(p)) return 1;
+  if (f.b <= 4 && sizeof(T) == 4) return split_launch<T, 4>(g, f, s, max_ctas);
+  if (f.b <= 8) return split_launch<T, 8>(g, f, s, max_ctas);
+  return split_launch<T, 16>(g, f, s, max_ctas);
+}
+
+template int pcg_split<float>(const DevGraph&, const FusedPcg&, cudaStream_t, int);
+template int pcg_split<double>(const DevGraph&, const FusedPcg&, cudaStream_t, int);
+
+}  // namespace lapeig

@@ -108,9 +108,12 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
       bool c = true, fin = true;
       double ratio = 0.0;
       if (j < b) {
-        const double r = sqrt(fmax(0.0, rn2[(size_t)s * 64 + j]));
+        // ||r|| from ||r||^2: rounding below zero is 0, NaN stays NaN (fmax
+        // would turn it into 0, a converged column)
+        const double r2 = rn2[(size_t)s * 64 + j];
+        const double r = r2 >= 0.0 ? sqrt(r2) : (r2 < 0.0 ? 0.0 : r2);
         const double* th = theta + (size_t)s * mmax;
-        fin = isfinite(r);
+        fin = isfinite(r) && isfinite(th[j]);
         c = r <= tol_abs[s] && th[j] <= norm1[s];
         if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, j, r, tol_abs[s], ev_rtol);
         ratio = j < k ? r / tol_abs[s] : 0.0;

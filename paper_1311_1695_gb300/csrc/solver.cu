@@ -177,6 +177,7 @@ struct JD {
   TP* P;
   TP* AP;
   TP* LXb;  // L X of the correction solve
+  TP* Xs;   // X packed for the per-phase correction solve
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
@@ -229,7 +230,7 @@ struct JD {
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     add(2 * n * z.ldv * sizeof(TV));
     add(n * z.ldb * sizeof(TV));
-    for (int i = 0; i < 8; ++i) add(n * z.ldb * sizeof(TP));
+    for (int i = 0; i < 9; ++i) add(n * z.ldb * sizeof(TP));
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
@@ -252,6 +253,7 @@ struct JD {
     P = a.take<TP>(n * z.ldb);
     AP = a.take<TP>(n * z.ldb);
     LXb = a.take<TP>(n * z.ldb);
+    Xs = a.take<TP>(n * z.ldb);
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
     Y = a.take<double>(S * mm);
@@ -400,6 +402,7 @@ struct JD {
     FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, theta, z.mmax, active, seg_skip,
                           delta, itmax, G->d_long_seg);
     f.early_exit = 1;
+    f.Xsv = Xs;
     if (pcg_fused<TP>(g, f, st, pw->max_ctas) != 0) {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;
@@ -590,7 +593,10 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
     }
     jd.inner_its += s2.pcg_steps;
     jd.n_matvec += (int64_t)(s2.pcg_steps + 1) * nact;
-    if (prof_on()) prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));
+    if (prof_on()) {
+      prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));
+      prof_set_last_bytes("pcg_split", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));
+    }
   }
   for (int s = 0; s < S; ++s) jd.skip_h[s] = jd.state_h[s] != 0 ? 1 : 0;
   // make sure skip flags are cleared on the device for whatever comes next
@@ -722,6 +728,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   pw.max_ctas = o.max_ctas > 0 ? o.max_ctas : G->max_ctas;
   pw.hub_cnt = G->d_hub_cnt;
   pw.nlong = G->dg.nlong;
+  pw.split_rows = G->split_rows;
   struct PwGuard { PcgWork& p; ~PwGuard() { p.release(); } } pw_guard{pw};
   int outer = 0;
   const bool mixed = o.precision == LAP_PREC_MIXED;

@@ -184,3 +184,28 @@ def test_cuda_graph_replay_matches_eager(pkg, precision):
         assert info["status"] == 0, info
         ev_ref, V_ref = all_pairs(x)
         check_eigpairs(x, ev, V, ev_ref, V_ref, k=6)
+
+
+@pytest.mark.parametrize("precision,k", [("mixed", 10), ("fp64", 6)])
+def test_solve_with_per_phase_correction(pkg, precision, k):
+    """Whole solves whose correction solves run in the per-phase form (forced
+    on from the first row; b = k + 2 columns, rows of at most 64 bytes),
+    early exit included, against the dense definition."""
+    g = G.workload_graph("c1")
+    Gd = pkg.Graph(g)
+    Gd.set_launch(split_rows=1)
+    V = __import__("torch").zeros(g.n * k, dtype=__import__("torch").float64, device="cuda")
+    pkg.lap_profile_read()
+    pkg.lap_profile_enable(True)
+    ev, infos = Gd.eigs(k, 1e-8, evecs=V, precision=precision, cuda_graph=False)
+    names = set(pkg.lap_profile_read())
+    pkg.lap_profile_enable(False)
+    assert "pcg_split" in names and "pcg_fused" not in names, names
+    assert infos[0]["status"] == 0, infos[0]
+    ev_ref, V_ref = all_pairs(g)
+    check_eigpairs(g, ev[0], V.cpu().numpy().reshape(k, g.n).T, ev_ref, V_ref, k=k)
+    # and replayed as a captured CUDA graph
+    ev2, infos2 = Gd.eigs(k, 1e-8, evecs=V, precision=precision)
+    assert infos2[0]["status"] == 0
+    check_eigpairs(g, ev2[0], V.cpu().numpy().reshape(k, g.n).T, ev_ref, V_ref, k=k)
+    Gd.close()
