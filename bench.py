@@ -361,14 +361,15 @@ def bench_ours(args):
                 "share_of_kernel_time": round(v["ms"] / sum(x["ms"] for x in prof.values()), 4)}
 
     roofline = roof(*dom)
-    if dom[0] == "pcg_fused":
+    if dom[0] in ("pcg_fused", "pcg_split"):
         roofline["bytes_model"] = ("per matrix-vector product of the correction solve (its steps + the set-up's L X): "
                                    "row pointers and column indices once, 2 b n values (gathered block read, product "
                                    "written), 2 (b + 1) n (the projection reads Q = [e, X] twice), 7 b n (CG vector "
                                    "passes); Jacobi preconditioner from the stored degrees (0 bytes)")
-    for v in spmm_roof.values():
-        v["bytes_model"] = "row pointers and column indices once (+ weights), X read once, Y written once" 
+
     spmm_roof = {kname: roof(kname, v) for kname, v in spmm_items.items()}
+    for v in spmm_roof.values():
+        v["bytes_model"] = "row pointers and column indices once (+ weights), X read once, Y written once"
     kern_table = {kname: {"ms_per_step": round(v["ms"] / args.steps, 4), "launches_per_step": v["launches"] // args.steps}
                   for kname, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
 
