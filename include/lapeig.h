@@ -136,12 +136,17 @@ const char* lap_last_error(void);
 int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* weights, int k,
              double tol, int method, const lap_opts* opts, double* evals, double* evecs, lap_info* info);
 
-/* Many independent graphs in one lock-step solve: every kernel launch covers
- * all graphs (one block-diagonal SpMM, per-graph reductions, one eigensolver
- * CTA per graph).  Same k for all graphs.  Arrays of nb host pointers; evecs
- * and infos may be NULL. JD only. */
+/* Many independent graphs: arrays of nb host pointers (weights, evecs and
+ * infos may be NULL; an entry of weights may be NULL for unit weights), k
+ * host [nb] (graph s gets its k[s] smallest pairs, evals[s] [k[s]], evecs[s]
+ * [n[s] * k[s]] column-major).  method LAP_JD solves all graphs in one
+ * lock-step solve: every kernel launch covers all graphs (one block-diagonal
+ * SpMM, per-graph reductions, one eigensolver CTA per graph), the block
+ * sized for the largest k, each graph converged on its own k.  LAP_DACG and
+ * LAP_IRLM solve the graphs one after another.  Returns the first non-OK
+ * status of a graph (LAP_OK when every graph converged). */
 int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
-                     const double* const* weights, int k, double tol, const lap_opts* opts,
+                     const double* const* weights, const int* k, double tol, int method, const lap_opts* opts,
                      double* const* evals, double* const* evecs, lap_info* infos);
 
 /* ---------------------------------------------------------------- graph handle

@@ -99,8 +99,8 @@ _SIGNATURES = {
     "lap_last_error": (ctypes.c_char_p, []),
     "lap_eigs": (_I, [_I64, _PI64, _PI32, _PD, _I, _D, _I, ctypes.POINTER(lap_opts), _PD, _PD,
                       ctypes.POINTER(lap_info)]),
-    "lap_eigs_batched": (_I, [_I, _PI64, ctypes.POINTER(_PI64), ctypes.POINTER(_PI32), ctypes.POINTER(_PD), _I, _D,
-                              ctypes.POINTER(lap_opts), ctypes.POINTER(_PD), ctypes.POINTER(_PD),
+    "lap_eigs_batched": (_I, [_I, _PI64, ctypes.POINTER(_PI64), ctypes.POINTER(_PI32), ctypes.POINTER(_PD), _PI, _D,
+                              _I, ctypes.POINTER(lap_opts), ctypes.POINTER(_PD), ctypes.POINTER(_PD),
                               ctypes.POINTER(lap_info)]),
     "lap_eigs_graph": (_I, [_P, _I, _D, _I, ctypes.POINTER(lap_opts), _PD, _P, ctypes.POINTER(lap_info)]),
     "lap_profile_enable": (_I, [_I]),
@@ -215,21 +215,26 @@ def lap_eigs(g, k: int, tol: float = 1e-8, method: str = "jd", want_vectors: boo
     return evals, (None if evecs is None else evecs.T.copy()), info.as_dict()
 
 
-def lap_eigs_batched(graphs, k: int, tol: float = 1e-8, want_vectors: bool = True, **opts):
-    """Lock-step block JD over many graphs.  Returns lists (evals, evecs, infos)."""
+def lap_eigs_batched(graphs, k, tol: float = 1e-8, method: str = "jd", want_vectors: bool = True, **opts):
+    """Many graphs: lock-step block JD (or DACG / IRLM one graph after
+    another).  k: one count for all graphs or one per graph.  Returns lists
+    (evals, evecs, infos)."""
     nb = len(graphs)
     args = [_csr_args(g) for g in graphs]
+    ks = np.ascontiguousarray(np.broadcast_to(np.asarray(k, dtype=np.int32), (nb,)))
     ns = np.array([a[0] for a in args], dtype=np.int64)
     rps = (_PI64 * nb)(*[_ptr(a[1], ctypes.c_int64) for a in args])
     cis = (_PI32 * nb)(*[_ptr(a[2], ctypes.c_int32) for a in args])
     ws = (_PD * nb)(*[_ptr(a[3], ctypes.c_double) for a in args])
-    evals = [np.zeros(k) for _ in range(nb)]
-    evecs = [np.zeros((k, a[0])) for a in args] if want_vectors else None
+    evals = [np.zeros(int(kk)) for kk in ks]
+    evecs = [np.zeros((int(kk), a[0])) for kk, a in zip(ks, args)] if want_vectors else None
     ev_p = (_PD * nb)(*[_ptr(e, ctypes.c_double) for e in evals])
     vv_p = (_PD * nb)(*[_ptr(v, ctypes.c_double) for v in evecs]) if want_vectors else None
     infos = (lap_info * nb)()
     o, _keep = make_opts(**opts)
-    st = lib().lap_eigs_batched(nb, _ptr(ns, ctypes.c_int64), rps, cis, ws, k, tol, ctypes.byref(o), ev_p, vv_p, infos)
+    st = lib().lap_eigs_batched(nb, _ptr(ns, ctypes.c_int64), rps, cis, ws, ks.ctypes.data_as(_PI), tol,
+                                _METHODS[method] if isinstance(method, str) else int(method), ctypes.byref(o), ev_p,
+                                vv_p, infos)
     _check(st, "lap_eigs_batched", allow_partial=True)
     return evals, ([v.T.copy() for v in evecs] if want_vectors else None), [i.as_dict() for i in infos]
 

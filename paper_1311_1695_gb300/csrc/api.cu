@@ -50,9 +50,10 @@ int solve(lap_graph* g, int k, double tol, int method, const lap_opts& o, bool w
   }
 }
 
-// Prepend the null pair (0, e/sqrt(n)) when requested.
-void add_null(SolveOut& out, const std::vector<int>& nrows, int kk) {
+// Prepend the null pair (0, e/sqrt(n)) when requested; graph s has kk[s] pairs.
+void add_null(SolveOut& out, const std::vector<int>& nrows, const std::vector<int>& kks) {
   for (size_t s = 0; s < out.evals.size(); ++s) {
+    const int kk = kks[s];
     out.evals[s].insert(out.evals[s].begin(), 0.0);
     if (!out.evecs.empty()) {
       const int n = nrows[s];
@@ -112,40 +113,59 @@ const char* lap_strerror(int s) {
 const char* lap_last_error(void) { return lapeig::last_error(); }
 
 int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
-                     const double* const* weights, int k, double tol, const lap_opts* opts, double* const* evals,
-                     double* const* evecs, lap_info* infos) {
+                     const double* const* weights, const int* k, double tol, int method, const lap_opts* opts,
+                     double* const* evals, double* const* evecs, lap_info* infos) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (nb < 1 || !n || !rowptr || !colidx || !evals || k < 1 || !(tol > 0.0)) {
+  if (nb < 1 || !n || !rowptr || !colidx || !evals || !k || !(tol > 0.0) || method < LAP_JD || method > LAP_IRLM) {
     set_error("bad arguments to lap_eigs_batched");
     return LAP_EINVAL;
   }
   lap_opts o = merged(opts);
-  const int kk = o.include_null ? k - 1 : k;
-  std::vector<int> nrows(nb);
+  std::vector<int> nrows(nb), kk(nb);
+  int kmax = 0;
   for (int s = 0; s < nb; ++s) {
-    if (n[s] < 2 || kk < 1 || kk > n[s] - 1 || !evals[s]) { set_error("k out of range for a graph"); return LAP_EINVAL; }
+    kk[s] = o.include_null ? k[s] - 1 : k[s];
+    if (n[s] < 2 || kk[s] < 1 || kk[s] > n[s] - 1 || !evals[s]) { set_error("k out of range for a graph"); return LAP_EINVAL; }
     nrows[s] = (int)n[s];
+    kmax = std::max(kmax, kk[s]);
+  }
+  const bool want = evecs != nullptr;
+  if (method != LAP_JD) {
+    // DACG and IRLM solve one graph at a time
+    int rc_all = LAP_OK;
+    for (int s = 0; s < nb; ++s) {
+      lap_info in{};
+      const int rc = lap_eigs(n[s], rowptr[s], colidx[s], weights ? weights[s] : nullptr, k[s], tol, method, &o, evals[s],
+                              want ? evecs[s] : nullptr, &in);
+      if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+      if (infos) infos[s] = in;
+      if (rc != LAP_OK && rc_all == LAP_OK) rc_all = rc;
+    }
+    return rc_all;
   }
   lap_graph* g = nullptr;
   int rc = graph_build(nb, n, rowptr, colidx, weights, &g);
   if (rc) return rc;
   if (o.team) {
-    rc = apply_team(g, o, k);
+    rc = apply_team(g, o, kmax);
     if (rc) { graph_free(g); return rc; }
   }
   SolveOut out;
-  const bool want = evecs != nullptr;
-  rc = solve_jd(g, kk, tol, o, want, out);
+  rc = solve_jd(g, kmax, tol, o, want, out, kk.data());
   graph_free(g);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+  for (int s = 0; s < nb; ++s) {  // graph s keeps its first kk[s] pairs (columns are contiguous)
+    out.evals[s].resize(kk[s]);
+    if (want) out.evecs[s].resize((size_t)nrows[s] * kk[s]);
+  }
   if (o.include_null) add_null(out, nrows, kk);
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   bool all_ok = true;
   for (int s = 0; s < nb; ++s) all_ok = all_ok && out.info[s].status == LAP_OK;
   if (rc == LAP_ENOCONV && all_ok) rc = LAP_OK;
   for (int s = 0; s < nb; ++s) {
-    std::memcpy(evals[s], out.evals[s].data(), sizeof(double) * k);
-    if (want && evecs[s]) std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k);
+    std::memcpy(evals[s], out.evals[s].data(), sizeof(double) * k[s]);
+    if (want && evecs[s]) std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k[s]);
     if (infos) {
       infos[s] = out.info[s];
       infos[s].elapsed_ms = ms;
@@ -178,7 +198,7 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   rc = solve(g, kk, tol, method, o, evecs != nullptr, out);
   graph_free(g);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
-  if (o.include_null) add_null(out, std::vector<int>{(int)n}, kk);
+  if (o.include_null) add_null(out, std::vector<int>{(int)n}, std::vector<int>{kk});
   std::memcpy(evals, out.evals[0].data(), sizeof(double) * k);
   if (evecs) std::memcpy(evecs, out.evecs[0].data(), sizeof(double) * (size_t)n * k);
   if (info) {
@@ -213,7 +233,7 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
   out.dev_vecs = evecs_dev;
   int rc = solve(g, kk, tol, method, o, evecs_dev != nullptr, out);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
-  if (o.include_null) add_null(out, nrows, kk);
+  if (o.include_null) add_null(out, nrows, std::vector<int>(S, kk));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int s = 0; s < S; ++s) {
     std::memcpy(evals + (size_t)s * k, out.evals[s].data(), sizeof(double) * k);

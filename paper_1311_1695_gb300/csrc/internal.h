@@ -114,7 +114,10 @@ struct SolveOut {
 };
 
 // Block Jacobi-Davidson over all segments of the handle (lock-step).
-int solve_jd(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);
+// kseg (host [nseg], nullable): graph s needs only its first kseg[s] <= k
+// pairs to converge (the block is sized for k).
+int solve_jd(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out,
+             const int* kseg = nullptr);
 // Single-graph DACG and IRLM on the device kernels.
 int solve_dacg(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);
 int solve_irlm(lap_graph* g, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out);

@@ -91,9 +91,9 @@ __host__ __device__ inline bool ev_accurate(const double* th, int nrv, int j, do
 // One CTA; a warp per graph (lane j = column j, b <= 32), warp reductions,
 // then a fixed-order reduction over the warps.
 __global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
-                           const double* __restrict__ norm1, const double* __restrict__ tol_abs, int k, int b,
-                           int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
-                           const unsigned* bar, JdStatus* status, double* segw) {
+                           const double* __restrict__ norm1, const double* __restrict__ tol_abs, int kall,
+                           const int* __restrict__ kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state,
+                           int* active, int* skip, const unsigned* bar, JdStatus* status, double* segw) {
   constexpr int NW = 8;
   __shared__ double s_w[NW];
   __shared__ int s_c[NW], s_bad[NW], s_act[NW], s_open[NW];
@@ -103,6 +103,7 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
   for (int s = warp; s < nseg; s += NW) {
     int st = state[s];
     double ws = 0.0;
+    const int k = kseg ? kseg[s] : kall;  // the graph's wanted pairs
     if (st != 1) {
       const int j = lane;
       bool c = true, fin = true;
@@ -212,10 +213,10 @@ void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg
   k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, norm1, seg_skip);
 }
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
-              const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s) {
+              int k, const int* kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active,
+              int* skip, const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
-  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, b, nrv, ev_rtol, explicit_check, state,
+  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, kseg, b, nrv, ev_rtol, explicit_check, state,
                                active, skip, bar, status, segw);
 }
 

@@ -30,9 +30,10 @@ struct JdStatus {
 // segw[s]: graph s's worst ||r_j|| / tol_abs over j < k (0 once converged).
 // ev_rtol > 0 adds the eigenvalue-accuracy test (Kato-Temple estimate over
 // the nrv Ritz values of the basis, ev_accurate_host).
+// kseg (device [nseg], nullable): graph s wants kseg[s] <= k pairs.
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active, int* skip,
-              const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s);
+              int k, const int* kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active,
+              int* skip, const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s);
 // Pair j's Ritz value is within ev_rtol * max(|theta_j|, tol_abs) of an
 // eigenvalue by the Kato-Temple bound r^2 / delta, delta from the other
 // Ritz values th[0:nrv] (always true for ev_rtol <= 0).

@@ -198,6 +198,7 @@ struct JD {
   bool explicit_h = std::is_same<TV, double>::value;
   int injections = 0;
   double ev_rtol = 0.0;  // eigenvalue-accuracy test of an explicit check (0: off)
+  int* kseg_d = nullptr;  // per-graph wanted pairs (device [S]; null: z.k for all)
   int nrv = 0;           // Ritz values of the last Rayleigh-Ritz (theta[0:nrv])
   PcgWork* pw = nullptr;
   // device-side convergence state (one outer iteration replays as a graph)
@@ -360,7 +361,7 @@ struct JD {
     const int mk = rayleigh_ritz(m);
     nrv = m;
     residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
-    converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, z.b, m, explicit_check ? ev_rtol : 0.0,
+    converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, kseg_d, z.b, m, explicit_check ? ev_rtol : 0.0,
              explicit_check ? 1 : 0, state, active, seg_skip, pw->bar, status_d, segw, st);
     cudaMemcpyAsync(status_h, status_d, sizeof(JdStatus), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(state_h, state, sizeof(int) * z.nseg, cudaMemcpyDeviceToHost, st);
@@ -428,6 +429,7 @@ struct JD {
 struct Params {
   int k, b, mk, itmax, max_outer, verbose;
   double tol, delta, max_seconds, ev_rtol;
+  std::vector<int> kseg;  // pairs wanted per graph (<= k)
   std::chrono::steady_clock::time_point t0;
 };
 
@@ -493,7 +495,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
       for (int s = 0; s < S; ++s) {
         if (jd.state_h[s] == 2) {
           bool segc = true;
-          for (int j = 0; j < P.k; ++j) {
+          for (int j = 0; j < P.kseg[s]; ++j) {
             const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
             const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
             const bool c = r <= tol_abs[s] && th[j] <= jd.G->norm1[s] &&
@@ -619,6 +621,7 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
   out.evals.assign(S, {});
   out.info.assign(S, lap_info{});
   for (int s = 0; s < S; ++s) {
+    const int ks = P.kseg[s];
     out.evals[s].assign(jd.theta_h.begin() + (size_t)s * jd.z.mmax, jd.theta_h.begin() + (size_t)s * jd.z.mmax + P.k);
     lap_info& in = out.info[s];
     in.status = status;
@@ -626,7 +629,7 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     int nconv = 0;
     bool prefix = true;
     const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
-    for (int j = 0; j < P.k; ++j) {
+    for (int j = 0; j < ks; ++j) {
       const double ra = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
       const double r = ra / G->norm1[s];
       const bool real = th[j] <= G->norm1[s];
@@ -637,8 +640,8 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     in.n_converged = nconv;
     // per graph: a batch member whose k pairs all meet the test is converged
     // even when another member hit the cap
-    if (status == LAP_ENOCONV && nconv == P.k) in.status = LAP_OK;
-    if (status == LAP_OK && nconv < P.k) in.status = LAP_ENOCONV;
+    if (status == LAP_ENOCONV && nconv == ks) in.status = LAP_OK;
+    if (status == LAP_OK && nconv < ks) in.status = LAP_ENOCONV;
     in.outer_its = outer;
     in.inner_its = jd.inner_its;
     in.n_matvec = jd.n_matvec;
@@ -665,10 +668,13 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
 
 }  // namespace
 
-int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out) {
+int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs, SolveOut& out, const int* kseg) {
   Params P;
   P.t0 = std::chrono::steady_clock::now();
   P.k = k;
+  P.kseg.assign(G->hg.nseg, k);
+  if (kseg)
+    for (int s = 0; s < G->hg.nseg; ++s) P.kseg[s] = std::min(std::max(kseg[s], 1), k);
   // default block: k plus two guard columns (they are corrected but need not
   // converge; they keep a cluster that straddles k from being missed)
   P.b = o.block > 0 ? std::max(o.block, k) : std::min(k + 2, 32);
@@ -695,11 +701,16 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   for (int s = 0; s < S; ++s) tol_abs[s] = tol * G->norm1[s];
 
   Arena outa;
-  int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k +
+  int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k + sizeof(int) * S + 256 +
                      sizeof(double) * (size_t)z.n * (o.x0 ? std::min(std::max(o.k0, 0), 64) : 0) + 4096);
   if (rc) return rc;
   double* d_out = outa.take<double>((size_t)z.n * k);
   unsigned long long* d_best = outa.take<unsigned long long>(2 * (size_t)S * k);
+  int* kseg_d = nullptr;
+  if (kseg) {
+    kseg_d = outa.take<int>((size_t)S);
+    cudaMemcpyAsync(kseg_d, P.kseg.data(), sizeof(int) * S, cudaMemcpyHostToDevice, st);
+  }
 
   // optional warm start (single graph): host n x k0 column-major -> device row-major
   double* x0d = nullptr;
@@ -739,6 +750,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     JD<double, double> jd(G, z, st);
     jd.carve(a);
     jd.pw = &pw;
+    jd.kseg_d = kseg_d;
     jd.ev_rtol = P.ev_rtol;
     int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
@@ -755,6 +767,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   JD<float, float> j1(G, z, st);
   j1.carve(a1);
   j1.pw = &pw;
+  j1.kseg_d = kseg_d;
   int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
   std::vector<double> tol1(S);
   for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
@@ -770,6 +783,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   JD<double, float> j2(G, z, st);
   j2.carve(a2);
   j2.pw = &pw;
+  j2.kseg_d = kseg_d;
   j2.ev_rtol = P.ev_rtol;
   const int mk = std::min(m_out, z.mk);
   convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);

@@ -209,3 +209,19 @@ def test_solve_with_per_phase_correction(pkg, precision, k):
     assert infos2[0]["status"] == 0
     check_eigpairs(g, ev2[0], V.cpu().numpy().reshape(k, g.n).T, ev_ref, V_ref, k=k)
     Gd.close()
+
+
+@pytest.mark.parametrize("method", ["jd", "dacg", "irlm"])
+def test_batched_per_graph_k_and_method(pkg, method):
+    """lap_eigs_batched with a pair count per graph: JD solves them in one
+    lock-step solve (block sized for the largest k, each graph converged on
+    its own k), DACG and IRLM one graph after another."""
+    gs = [G.ba_graph(400, 2, 61), G.grid_graph(18, 25), G.chung_lu(1500, 2.4, 5.0, 62),
+          G.with_random_weights(G.ba_graph(700, 3, 63), 64)]
+    ks = [3, 7, 5, 2] if method == "jd" else [3, 2, 4, 2]
+    evs, Vs, infos = pkg.lap_eigs_batched(gs, ks, tol=1e-8, method=method, precision="mixed")
+    for g, k, ev, V, info in zip(gs, ks, evs, Vs, infos):
+        assert info["status"] == 0, info
+        assert ev.size == k and V.shape == (g.n, k)
+        ev_ref, V_ref = all_pairs(g)
+        check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)
