@@ -456,7 +456,7 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
   // L X at the work blocks' stride when its rows are 16-byte multiples (the
   // per-phase form needs equal strides), else padded to 4 columns
   const int ldlx = ((size_t)b * es) % 16 == 0 ? b : (b + 3) / 4 * 4;
-  int rc = graph_scratch(g, 5 * n * b * es + n * ldlx * es + 1024, sizeof(double) * S * 64 + 1024);
+  int rc = graph_scratch(g, 6 * n * b * es + n * ldlx * es + 1536, sizeof(double) * S * 64 + 1024);
   if (rc) return rc;
   if (!g->pcg.acc1) {
     rc = g->pcg.init(S);
@@ -478,9 +478,11 @@ int lap_pcg_correction(lap_graph* g, int dtype, const void* X, int ldx, const do
     T* AP = P + n * b;
     T* LX = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(AP + n * b) + 255) & ~(uintptr_t)255);
     T* Xs = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(LX + n * ldlx) + 255) & ~(uintptr_t)255);
+    T* LZ = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Xs + n * b) + 255) & ~(uintptr_t)255);
     FusedPcg f = g->pcg.args(X, ldx, R, ldr, Tout, RES, Z, P, AP, LX, ldlx, b, b, th, 64, nullptr, nullptr, delta, iters,
                              g->d_long_seg);
     f.Xsv = Xs;
+    f.LZv = LZ;
     if (pcg_fused<T>(g->dg, f, s, g->pcg.max_ctas) != 0) return check_cuda("lap_pcg_correction launch");
   });
   if (g->pcg.error_flag(s)) { set_error("grid barrier timed out"); return LAP_ETIMEOUT; }

@@ -63,6 +63,14 @@ struct DevGraph {
   const int2* hub_chunks;  // [nlong] {first chunk, number of chunks}
   int* hub_cnt;          // [nlong] arrival counters, zero at rest
   double* hub_part;      // [nchunk * kPartStride]
+  // the ordinary (non-hub) rows by decreasing degree (ties by row): the
+  // row-slot schedule of the vectorised SpMM, so that the rows a warp takes
+  // together have nearly the same length
+  const int* order;      // [norder]
+  int norder;
+  // set by a launcher for one launch: the SpMM kernels return at once when
+  // *skip_flag is nonzero (a correction solve that already stopped)
+  const int* skip_flag;
 };
 
 constexpr int kHubChunk = 128;

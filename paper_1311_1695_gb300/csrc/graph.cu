@@ -112,7 +112,7 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   cudaFree(g->d_sched);
   g->d_sched = nullptr;
   g->d_long = nullptr; g->d_long_seg = nullptr; g->d_chunks = nullptr; g->d_hub_chunks = nullptr;
-  g->d_hub_cnt = nullptr; g->d_hub_part = nullptr; g->d_erp = nullptr;
+  g->d_hub_cnt = nullptr; g->d_hub_part = nullptr; g->d_erp = nullptr; g->d_order = nullptr;
   std::vector<int> erp((size_t)n + 1, 0);
   for (int i = 0; i < n; ++i) {
     const int d = g->rowptr_h[i + 1] - g->rowptr_h[i];
@@ -129,7 +129,24 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
     hub_chunks[h] = make_int2((int)chunks.size(), (p1 - p0 + kHubChunk - 1) / kHubChunk);
     for (int p = p0; p < p1; p += kHubChunk) chunks.push_back(make_int4(r, p, std::min(p + kHubChunk, p1), (int)h));
   }
+  // ordinary rows by decreasing degree, ties by row (a counting sort)
+  std::vector<int> order;
+  {
+    const int lt = g->dg.long_thresh;
+    std::vector<int> cnt((size_t)lt + 2, 0);
+    for (int i = 0; i < n; ++i) {
+      const int d = g->rowptr_h[i + 1] - g->rowptr_h[i];
+      if (d <= lt) ++cnt[(size_t)(lt - d) + 1];
+    }
+    for (size_t v = 1; v < cnt.size(); ++v) cnt[v] += cnt[v - 1];
+    order.resize((size_t)cnt.back());
+    for (int i = 0; i < n; ++i) {
+      const int d = g->rowptr_h[i + 1] - g->rowptr_h[i];
+      if (d <= lt) order[(size_t)cnt[(size_t)(lt - d)]++] = i;
+    }
+  }
   Packer pk;  // hub counters start at zero (no source)
+  pk.add(&g->d_order, order.data(), order.size());
   pk.add(&g->d_long, hubs.data(), hubs.size());
   pk.add(&g->d_long_seg, hseg.data(), hseg.size());
   pk.add(&g->d_chunks, chunks.data(), chunks.size());
@@ -148,6 +165,8 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   g->dg.hub_cnt = g->d_hub_cnt;
   g->dg.hub_part = g->d_hub_part;
   g->dg.erp = g->d_erp;
+  g->dg.order = g->d_order;
+  g->dg.norder = (int)order.size();
   return LAP_OK;
 }
 

@@ -68,6 +68,7 @@ struct lap_graph {
   int* d_long = nullptr;
   int* d_long_seg = nullptr;   // segment of each hub row
   int* d_erp = nullptr;        // effective row pointer (hub rows empty)
+  int* d_order = nullptr;      // ordinary rows by decreasing degree
   int4* d_chunks = nullptr;    // hub chunks {row, p0, p1, hub}
   int2* d_hub_chunks = nullptr;
   int* d_hub_cnt = nullptr;

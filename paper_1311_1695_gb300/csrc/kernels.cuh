@@ -14,8 +14,9 @@ struct Reduce {
 };
 
 // ---- K1: Y = L X (degree fused), b columns
+// skip (device, nullable): the launch does nothing when *skip != 0.
 template <typename T>
-void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s);
+void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip = nullptr);
 
 // ---- Gram: G[s] = [1 | A]^T B per segment (ones adds a leading row of column
 // sums, divided by the segment's row count when ones_mean is set).  G is

@@ -37,6 +37,7 @@ struct FusedPcg {
   // per-phase form (pcg_split.cu), used from split_rows rows on when the
   // shapes allow it: scratch for X packed at stride ld, and its stop flag
   const void* Xsv = nullptr;
+  void* LZv = nullptr;  // n x ld scratch for L z~
   int* stop = nullptr;
   int split_rows = 0;   // 0: kSplitRows
 };

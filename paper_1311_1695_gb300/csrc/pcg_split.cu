@@ -8,22 +8,23 @@
 // Why: on a graph of 10^6 rows the blocks of one PCG step (z~, X, L X, p,
 // q~, r, t) no longer fit in L2, and the persistent kernel, which loads its
 // rows through registers at two CTAs of 126 registers per SM, keeps too few
-// bytes in flight to use HBM (about an eighth of it).  Here one thread of a
-// CTA issues cp.async.bulk copies of the tile's rows of every streamed block
+// bytes in flight to use HBM (about an eighth of it).  Here the SpMM of the
+// step is the library's vectorised SpMM (degree-sorted rows, 32 registers,
+// full occupancy, hub rows chunked) writing L z~ to a block, and the row-wise
+// work of each phase streams its rows: one thread of a CTA issues
+// cp.async.bulk copies of the tile's rows of every block it reads
 // (contiguous: rows are row-major with a 16-byte multiple stride) into
-// shared memory, completing on an mbarrier; in phase M they are issued before
-// the merge-path SpMM walk of the tile and arrive while its gathers run.
-// The kernel boundary is the grid-wide barrier (a few microseconds, against
-// hundreds per phase at this size), and each phase gets its own register
-// budget.
+// shared memory, completing on an mbarrier.  The kernel boundary is the
+// grid-wide barrier (a few microseconds, against a hundred or more per phase
+// at this size), and each phase gets its own register budget.
 //
 // Launch sequence of one solve: pack (X into a zero-padded row stride),
-// init (L X, RES = -R, t = 0, z~ = RES / d, partial G2), then per step
-// M (beta, p', q~', partial G1) and B (alpha, t, r, z~, partial G2), and fin
-// (the final residual norms, step count, accumulators back to zero).  A
-// single-graph solve that meets its tolerance stops early: the M launch that
-// sees every column done raises a stop flag and the remaining launches
-// return at once.
+// SpMM (L X), init (RES = -R, t = 0, z~ = RES / d, partial G2), then per step
+// SpMM (L z~), M (beta, p', q~', partial G1) and B (alpha, t, r, z~, partial
+// G2), and fin (the final residual norms, step count, accumulators back to
+// zero).  A single-graph solve that meets its tolerance stops early: the M
+// launch that sees every column done raises a stop flag and the remaining
+// launches (the SpMMs included) return at once.
 #include <algorithm>
 
 #include "common.cuh"
@@ -108,11 +109,12 @@ __device__ bool mbar_wait(unsigned long long* bar, unsigned parity, const GridBa
 }
 
 // The launch-time view of a split solve: the persistent form's view plus
-// the stop flag and the packed X.
+// the stop flag, the packed X and the block receiving L z~.
 template <typename T>
 struct SplitView {
   View<T> v;
   const T* Xs;   // X packed: row stride v.ld, columns [b, ld) zero
+  const T* LZ;   // L z~ of the current step (row stride v.ld)
   int* stop;     // raised by the M launch that ends a single-graph solve
 };
 
@@ -126,28 +128,18 @@ __global__ void k_pack_x(int n, const T* __restrict__ X, int ldx, T* __restrict_
   }
 }
 
-// Column indices of a tile staged in shared memory when its nonzeros (hub
-// rows included) number at most this; else the walk loads them from L2.
-constexpr int kColCap = 4096;
-// gathers in flight per row group in the walks of this form
-constexpr int kUSplit = 8;
-
-// Shared-memory layout of one split kernel (element offsets in T, every
-// region 16-byte aligned): red (flushes and staged totals), accA
-// (kTileRows x BMAX row accumulators), nstage staged blocks of
-// kTileRows x ld, then the tile's row pointers (ints) and the mbarrier.
+// Shared-memory layout of one split kernel (every region 16-byte aligned):
+// red (flushes and staged totals), nstage staged blocks of kTileRows x ld,
+// the tile's degrees, then the mbarrier.
 template <typename T, int BMAX, int BWL>
 struct SplitSmem {
   static constexpr int red = (kWarps * (BMAX + 3) * BWL > (BMAX + 1) * BMAX + 2 * BMAX)
                                  ? kWarps * (BMAX + 3) * BWL
                                  : (BMAX + 1) * BMAX + 2 * BMAX;
   static constexpr int red_al = (red + 3) / 4 * 4;
-  static constexpr int acc = kTileRows * BMAX;
-  // with_acc: the row accumulators of an SpMM walk and the tile's staged
-  // column indices (init, phase M)
-  static size_t bytes(int nstage, int ld, bool with_acc) {
-    const size_t t = sizeof(T) * ((size_t)red_al + (with_acc ? acc : 0) + (size_t)nstage * kTileRows * ld + kTileRows);
-    return (t + 15) / 16 * 16 + sizeof(int) * (2 * (kTileRows + 4) + (with_acc ? kColCap : 0)) + 16;
+  static size_t bytes(int nstage, int ld) {
+    const size_t t = sizeof(T) * ((size_t)red_al + (size_t)nstage * kTileRows * ld + kTileRows);
+    return (t + 15) / 16 * 16 + 16;
   }
 };
 
@@ -215,37 +207,27 @@ __device__ __forceinline__ T dot_ld(const T* __restrict__ r, const T (&Gc)[BMAX 
 template <typename T, int BMAX, int BWL>
 struct Ctx {
   T* red;
-  T* accA;
   T* stage;      // nstage blocks of kTileRows x ld (block i at stage + i * kTileRows * ld)
   T* s_deg;      // [kTileRows] the tile's degrees
-  int* s_rp;     // [kTileRows + 1]
-  int* s_erp;    // [kTileRows + 1]
-  int* s_col;    // [kColCap] the tile's column indices (with_acc)
   unsigned long long* bar;
   unsigned phase;
   unsigned long long policy;  // evict-first
-  __device__ void setup(unsigned char* smem, int nstage, int ld, bool with_acc) {
+  __device__ void setup(unsigned char* smem, int nstage, int ld) {
     using L = SplitSmem<T, BMAX, BWL>;
-    const int na = with_acc ? L::acc : 0;
     red = reinterpret_cast<T*>(smem);
-    accA = red + L::red_al;
-    stage = accA + na;
+    stage = red + L::red_al;
     s_deg = stage + (size_t)nstage * kTileRows * ld;
-    const size_t tb = sizeof(T) * ((size_t)L::red_al + na + (size_t)nstage * kTileRows * ld + kTileRows);
-    s_rp = reinterpret_cast<int*>(smem + (tb + 15) / 16 * 16);
-    s_erp = s_rp + kTileRows + 4;
-    s_col = s_erp + kTileRows + 4;
-    bar = reinterpret_cast<unsigned long long*>(s_col + (with_acc ? kColCap : 0));
+    const size_t tb = sizeof(T) * ((size_t)L::red_al + (size_t)nstage * kTileRows * ld + kTileRows);
+    bar = reinterpret_cast<unsigned long long*>(smem + (tb + 15) / 16 * 16);
     phase = 0;
     policy = evict_first_policy();
     if (threadIdx.x == 0) mbar_init(bar);
-    for (int e = threadIdx.x; e < na; e += kThreads) accA[e] = T(0);
     __syncthreads();
   }
   __device__ T* blk(int i, int ld) { return stage + (size_t)i * kTileRows * ld; }
-  // thread 0: copy rows [r0, r1) of the nb blocks src[i] (row stride ld[i])
-  // into staged block i
-  // (blocks whose bit is set in keep are copied without the evict-first hint)
+  // thread 0: copy rows [r0, r1) of the nb blocks src[i] (row stride ldb[i])
+  // into staged block i (blocks whose bit is set in keep are copied without
+  // the evict-first hint)
   template <int NB>
   __device__ void issue(const T* const (&src)[NB], const int (&ldb)[NB], int ld, int r0, int r1, unsigned keep = 0) {
     if (threadIdx.x != 0) return;
@@ -268,31 +250,15 @@ struct Ctx {
     __syncthreads();
     return s_ok != 0;
   }
-  // the tile's row pointers, effective row pointers and degrees
-  __device__ void rows(const DevGraph& g, const Tile& t, const T* deg) {
-    for (int i = threadIdx.x; i <= t.r1 - t.r0; i += kThreads) {
-      s_rp[i] = g.rowptr[t.r0 + i];
-      s_erp[i] = g.erp[t.r0 + i];
-      if (i < t.r1 - t.r0) s_deg[i] = deg[t.r0 + i];
-    }
-  }
-  // after rows() and a CTA barrier: the tile's column indices when they
-  // fit (returns them, else null; the same answer in every thread)
-  __device__ const int* cols(const DevGraph& g, int nrows) {
-    const int p0 = s_rp[0], cnt = s_rp[nrows] - p0;
-    if (cnt > kColCap) return nullptr;
-    for (int q = threadIdx.x; q < cnt; q += kThreads) s_col[q] = __ldg(g.colidx + p0 + q);
-    return s_col;
+  // the tile's degrees (read after the next wait)
+  __device__ void degrees(const Tile& t, const T* deg) {
+    for (int i = threadIdx.x; i < t.r1 - t.r0; i += kThreads) s_deg[i] = deg[t.r0 + i];
   }
 };
 
 template <typename T>
 __device__ __forceinline__ const T* deg_of(const DevGraph& g) {
   return reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.deg32 : (const void*)g.deg64);
-}
-template <typename T>
-__device__ __forceinline__ const T* w_of(const DevGraph& g) {
-  return reinterpret_cast<const T*>(sizeof(T) == 4 ? (const void*)g.w32 : (const void*)g.w64);
 }
 
 // accumulators of graph s, parity q
@@ -328,21 +294,21 @@ __device__ __forceinline__ void coeffs(T (&Gc)[BMAX + 1], const T* tot, int b, i
 }
 
 // ---------------------------------------------------------------- init
-// LX = L X (the SpMM of X); RES = -R (active columns), t = 0, z~ = RES / d;
-// partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity 1.
+// RES = -R (active columns), t = 0, z~ = RES / d, LX's padding columns zero;
+// partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity 1.  (L X itself comes
+// from the SpMM launched before.)  Staged block: X rows of the tile.
 template <typename T, int BMAX, int BWL>
 __global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T> sv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   Ctx<T, BMAX, BWL> cx;
   const int ld = f.ld;
-  cx.setup(smem_raw, 1, ld, true);
+  cx.setup(smem_raw, 1, ld);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
   const int b = f.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL, grp = warp * RW + lane / BWL;
   const bool colok = c < b;
   const T* __restrict__ deg = deg_of<T>(g);
-  const T* __restrict__ w = w_of<T>(g);
   if (blockIdx.x == 0 && threadIdx.x == 0) *sv.stop = 0;
   T acc[BMAX + 1];
   T ex[2] = {T(0), T(0)};
@@ -363,52 +329,37 @@ __global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T
       const int lds[1] = {ld};
       cx.issue<1>(src, lds, ld, t.r0, t.r1);
     }
-    cx.rows(g, t, deg);
-    __syncthreads();
-    const int* scol = cx.cols(g, nrows);
-    __syncthreads();
-    walk_tile<T, BMAX, SLOTS, kUSplit, true>(g, w, sv.Xs, ld, cx.s_rp, cx.s_erp, nrows, cx.accA, grp, c, colok, scol,
-                                             cx.s_rp[0]);
-    if (!cx.wait(f.bar)) return;  // also the CTA barrier after the walk
+    cx.degrees(t, deg);
+    if (!cx.wait(f.bar)) return;
     const T* xs = cx.blk(0, ld);
     const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-    if (c < f.ldlx) {
+    if (c < ld) {
       for (int il = grp; il < nrows; il += SLOTS) {
         const int r = t.r0 + il;
-        const T dv = cx.s_deg[il];
-        const T* xr = xs + (size_t)il * ld;
-        if (cx.s_rp[il + 1] - cx.s_rp[il] <= g.long_thresh) {  // hub rows: by their chunks
-          const T a = cx.accA[il * BMAX + c];
-          cx.accA[il * BMAX + c] = T(0);
-          f.LX[(size_t)r * f.ldlx + c] = colok ? dv * xr[c] - a : T(0);
+        if (!colok) {
+          f.LX[(size_t)r * f.ldlx + c] = T(0);
+          continue;
         }
-        if (colok) {
-          const size_t o = (size_t)r * ld + c;
-          const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
-          const T z = res / dv;
-          f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
-          gram_ld<T, BMAX>(acc, xr, z, ld);
-          ex[0] += res * z;
-          ex[1] += res * res;
-        }
+        const size_t o = (size_t)r * ld + c;
+        const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
+        const T z = res / cx.s_deg[il];
+        f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
+        gram_ld<T, BMAX>(acc, xs + (size_t)il * ld, z, ld);
+        ex[0] += res * z;
+        ex[1] += res * res;
       }
     }
   }
-  hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, sv.Xs, ld, cx.red, b, grp, c, colok,
-                         [&](const int4& cc, int, T a) {
-                           const int row = cc.x;
-                           if (lane < BWL && c < f.ldlx)
-                             f.LX[(size_t)row * f.ldlx + c] = colok ? deg[row] * sv.Xs[(size_t)row * ld + c] - a : T(0);
-                         });
   if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
 }
 
 // ---------------------------------------------------------------- phase M
 // beta = rho'/rho, column done when ||r|| <= delta ||r_0||;
 // p' = P z~ + beta p and q~' = (L - theta) p' via
-//   (L - theta) P z~ = (L z~ - theta z~) + theta G2[0] - [0 | LX - theta X] G2;
-// partial G1 = [1|X]^T q~', p'.q~' into acc1 parity `par`.  Staged blocks:
-// z~, X, LX, p, q~ rows of the tile (issued before its SpMM walk).
+//   (L - theta) P z~ = L z~ - [LX] g - theta (z~ - g0 - [X] g),  (g0, g) = G2,
+// with L z~ from the SpMM launched before (hub rows included); partial
+// G1 = [1|X]^T q~', p'.q~' into acc1 parity `par`.  Staged blocks: z~, X,
+// LX, p, q~, L z~ rows of the tile.
 template <typename T, int BMAX, int BWL>
 __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> sv, int it) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -440,14 +391,11 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
     }
   }
   Ctx<T, BMAX, BWL> cx;
-  cx.setup(smem_raw, 5, ld, true);
+  cx.setup(smem_raw, 6, ld);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL, grp = warp * RW + lane / BWL;
   const bool colok = c < b;
-  const T* __restrict__ deg = deg_of<T>(g);
-  const T* __restrict__ w = w_of<T>(g);
-  const T* Xs = sv.Xs;
   T acc[BMAX + 1];
   T ex[2] = {T(0), T(0)};
   T Gc[BMAX + 1];
@@ -459,28 +407,27 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
     if (t.idx_in_seg == 0 && !(f.seg_skip && f.seg_skip[t.seg]))
       for (int e = threadIdx.x; e < f.acc_stride; e += kThreads) acc1_of(f, g, prv, t.seg)[e] = T(0);
   }
-  auto beta_of = [&](int seg, T rho_new) -> T {
-    if (it == 0 || !colok) return T(0);
-    const size_t k = (size_t)seg * f.bstride + c;
-    const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
-    const int dn = __ldcg(f.done + (size_t)prv * ss + k);
-    return (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
-  };
-  int cur = -1, gseg = -1;
+  int cur = -1;
   T thc = T(0), be = T(0);
   for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
     const Tile t = g.tiles[ti];
     if (f.seg_skip && f.seg_skip[t.seg]) continue;
     if (t.seg != cur) {
       if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
-      cur = gseg = t.seg;
+      cur = t.seg;
       const T* tot = stage_totals(cx.red, acc2_of(f, g, prv, t.seg), nout + 2 * b);
       thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
       coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
-      be = beta_of(t.seg, colok ? tot[nout + c] : T(0));
+      be = T(0);
+      const T rho_new = colok ? tot[nout + c] : T(0);
+      if (it > 0 && colok) {  // beta = rho'/rho (0 for a column already done)
+        const size_t k = (size_t)t.seg * f.bstride + c;
+        const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
+        const int dn = __ldcg(f.done + (size_t)prv * ss + k);
+        be = (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
+      }
       if (t.idx_in_seg == 0 && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
         const size_t k = (size_t)t.seg * f.bstride + c;
-        const T rho_new = tot[nout + c];
         const T rn = sqrt(tot[nout + b + c]);
         int dn;
         if (it == 0) {
@@ -497,19 +444,12 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
       }
     }
     const int nrows = t.r1 - t.r0;
-    __syncthreads();  // the previous tile's epilogue is done with the stage and accA
+    __syncthreads();  // the previous tile's epilogue is done with the stage
     {
-      const T* src[5] = {f.Z, Xs, f.LX, f.P, f.AP};
-      const int lds[5] = {ld, ld, ld, ld, ld};
-      cx.issue<5>(src, lds, ld, t.r0, t.r1, 1u);  // z~ (gathered too) without the evict-first hint
+      const T* src[6] = {f.Z, sv.Xs, f.LX, f.P, f.AP, sv.LZ};
+      const int lds[6] = {ld, ld, ld, ld, ld, ld};
+      cx.issue<6>(src, lds, ld, t.r0, t.r1, 1u);  // z~ (gathered by the next SpMM too) without the evict-first hint
     }
-    cx.rows(g, t, deg);
-    __syncthreads();
-    const int* scol = cx.cols(g, nrows);
-    __syncthreads();
-    // z~ is not written in this phase: gathers through L1
-    walk_tile<T, BMAX, SLOTS, kUSplit, true>(g, w, f.Z, ld, cx.s_rp, cx.s_erp, nrows, cx.accA, grp, c, colok, scol,
-                                             cx.s_rp[0]);
     if (!cx.wait(f.bar)) return;
     if (colok) {
       const T* sz = cx.blk(0, ld);
@@ -517,17 +457,13 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
       const T* slx = cx.blk(2, ld);
       const T* sp = cx.blk(3, ld);
       const T* sq = cx.blk(4, ld);
+      const T* slz = cx.blk(5, ld);
       for (int il = grp; il < nrows; il += SLOTS) {
-        if (cx.s_rp[il + 1] - cx.s_rp[il] > g.long_thresh) continue;  // a hub: done by its chunks
         const int r = t.r0 + il;
-        const T dv = cx.s_deg[il];
         const size_t so = (size_t)il * ld;
-        const T zv = sz[so + c];
-        const T a = cx.accA[il * BMAX + c];
-        cx.accA[il * BMAX + c] = T(0);
-        const T pz = project_ld<T, BMAX>(zv, sx + so, Gc, ld);
+        const T pz = project_ld<T, BMAX>(sz[so + c], sx + so, Gc, ld);
         const T sl = dot_ld<T, BMAX>(slx + so, Gc, ld);
-        T q = dv * zv - a - sl - thc * pz;
+        T q = slz[so + c] - sl - thc * pz;
         T p = pz;
         if (be != T(0)) { q += be * sq[so + c]; p += be * sp[so + c]; }
         const size_t o = (size_t)r * ld + c;
@@ -538,61 +474,6 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
       }
     }
   }
-  // hub rows: the completing warp forms p' and q~' of the row from its
-  // graph's totals and adds its share of G1 and p'.q~' (to the CTA's
-  // registers when the hub is in the CTA's current graph, else atomically)
-  hub_pass<T, BMAX, BWL>(g, f.hub_seg, f.seg_skip, w, f.Z, ld, cx.red, b, grp, c, colok,
-                         [&](const int4& cc, int seg, T a) {
-    const int row = cc.x;
-    const bool own = colok && lane < BWL;  // group 0 holds the row
-    if (seg != gseg) {  // warp-uniform
-      const T* A = acc2_of(f, g, prv, seg);
-      const int c0 = colok ? c : 0;
-#pragma unroll
-      for (int i = 0; i <= BMAX; ++i) {
-        const T v = __ldcg(A + (i <= b ? i : b) * b + c0);
-        Gc[i] = (colok && i <= b) ? v : T(0);
-      }
-      Gc[0] *= T(1) / (T)seg_rows(g, seg);
-      be = beta_of(seg, colok ? __ldcg(A + nout + c) : T(0));
-      thc = colok ? (T)f.theta[(size_t)seg * f.sth + c] : T(0);
-      gseg = seg;
-    }
-    const T bs = be;
-    const T th = own ? thc : T(0);
-    const size_t o = (size_t)row * ld + c;
-    const T zr = own ? __ldcg(f.Z + o) : T(0);
-    const T xc = own ? Xs[(size_t)row * ld + c] : T(0);
-    const T lc = own ? __ldcg(f.LX + (size_t)row * f.ldlx + c) : T(0);
-    T sx = Gc[0], sl = T(0);
-#pragma unroll
-    for (int i = 0; i < BMAX; ++i) {
-      const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-      const T li = __shfl_sync(0xffffffffu, lc, i, BWL);
-      sx += xi * Gc[i + 1];
-      sl += li * Gc[i + 1];
-    }
-    const T pz = zr - sx;
-    T q = deg[row] * zr - a - sl - th * pz;
-    T p = pz;
-    if (own && bs != T(0)) { q += bs * __ldcg(f.AP + o); p += bs * __ldcg(f.P + o); }
-    if (!own) { q = T(0); p = T(0); }
-    if (own) { f.P[o] = p; f.AP[o] = q; }
-    if (seg == cur) {
-      gram_col<T, BMAX, BWL>(acc, xc, q, b);
-      ex[0] += p * q;
-    } else {
-      T* a1 = acc1_of(f, g, par, seg);
-      for (int i = 0; i < b; ++i) {
-        const T xi = __shfl_sync(0xffffffffu, xc, i, BWL);
-        if (own) atomicAdd(a1 + (size_t)(1 + i) * b + c, xi * q);
-      }
-      if (own) {
-        atomicAdd(a1 + c, q);
-        atomicAdd(a1 + nout + c, p * q);
-      }
-    }
-  });
   if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
 }
 
@@ -610,7 +491,7 @@ __global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> s
   const int nout = (b + 1) * b;
   const int64_t ss = f.state_stride;
   Ctx<T, BMAX, BWL> cx;
-  cx.setup(smem_raw, 5, ld, false);
+  cx.setup(smem_raw, 5, ld);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL, grp = warp * RW + lane / BWL;
@@ -653,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> s
       const int lds[5] = {ld, ld, ld, ld, ld};
       cx.issue<5>(src, lds, ld, t.r0, t.r1);
     }
-    cx.rows(g, t, deg);
+    cx.degrees(t, deg);
     if (!cx.wait(f.bar)) return;
     if (colok) {
       const T* sq = cx.blk(0, ld);
@@ -670,7 +551,7 @@ __global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> s
         const size_t o = (size_t)r * ld + c;
         __stcs(f.Tt + o, st[so + c] + al * sp[so + c]);
         __stcs(f.RES + o, res);
-        f.Z[o] = z;  // gathered in the next phase M: normal priority
+        f.Z[o] = z;  // gathered by the next SpMM: normal priority
         gram_ld<T, BMAX>(acc, sx + so, z, ld);
         ex[0] += res * z;
         ex[1] += res * res;
@@ -714,7 +595,9 @@ int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_c
              reinterpret_cast<T*>(f.acc2), f.acc_stride, reinterpret_cast<T*>(f.rho), f.done,
              reinterpret_cast<T*>(f.res0), reinterpret_cast<T*>(f.resn), f.state_stride, f.hub_seg, f.bar,
              f.early_exit && g.nseg == 1, f.iters_out, 0};
-  SplitView<T> sv{ff, static_cast<const T*>(f.Xsv), f.stop};
+  T* Xs = static_cast<T*>(const_cast<void*>(f.Xsv));
+  T* LZ = static_cast<T*>(f.LZv);
+  SplitView<T> sv{ff, Xs, LZ, f.stop};
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -732,15 +615,17 @@ int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_c
   auto ki = k_split_init<T, BMAX, BWL>;
   auto km = k_split_m<T, BMAX, BWL>;
   auto kb = k_split_b<T, BMAX, BWL>;
-  const size_t si = L::bytes(1, ld, true), sm = L::bytes(5, ld, true), sb = L::bytes(5, ld, false);
+  const size_t si = L::bytes(1, ld), sm = L::bytes(6, ld), sb = L::bytes(5, ld);
   const int gi = grid_of(reinterpret_cast<const void*>(ki), si);
   const int gm = grid_of(reinterpret_cast<const void*>(km), sm);
   const int gb = grid_of(reinterpret_cast<const void*>(kb), sb);
   const int64_t tot = (int64_t)g.n * ld;
   const int pgrid = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)nsm * 8);
-  k_pack_x<T><<<pgrid > 0 ? pgrid : 1, 256, 0, s>>>(g.n, ff.X, f.ldx, const_cast<T*>(sv.Xs), ld, f.b);
-  ki<<<gi, kThreads, si, s>>>(g, sv);
+  k_pack_x<T><<<pgrid > 0 ? pgrid : 1, 256, 0, s>>>(g.n, ff.X, f.ldx, Xs, ld, f.b);
+  ki<<<gi, kThreads, si, s>>>(g, sv);  // resets the stop flag first
+  spmm<T>(g, Xs, ld, ff.LX, f.ldlx, f.b, s, f.stop);
   for (int it = 0; it < f.itmax; ++it) {
+    spmm<T>(g, ff.Z, ld, LZ, ld, f.b, s, f.stop);  // returns at once after a stop
     km<<<gm, kThreads, sm, s>>>(g, sv, it);
     kb<<<gb, kThreads, sb, s>>>(g, sv, it);
   }
@@ -756,12 +641,12 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // (and launches nothing) when the shapes do not allow it -- rows of more than
 // 64 bytes (FP32 beyond 16 columns, FP64 beyond 8), a row stride that is not
 // a multiple of 16 bytes, L X with another stride, an unaligned block, or no
-// scratch for the packed X -- else 0, or -1 on a launch failure.
+// scratch for the packed X and L z~ -- else 0, or -1 on a launch failure.
 template <typename T>
 int pcg_split(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
   const size_t rowb = sizeof(T) * (size_t)f.ld;
-  if (!f.Xsv || !f.stop || f.ld < f.b || rowb > 64 || rowb % 16 != 0 || f.ldlx != f.ld) return 1;
-  const void* ptrs[7] = {f.Xsv, f.Ttv, f.RESv, f.Zv, f.Pv, f.APv, f.LXv};
+  if (!f.Xsv || !f.LZv || !f.stop || f.ld < f.b || rowb > 64 || rowb % 16 != 0 || f.ldlx != f.ld || !g.order) return 1;
+  const void* ptrs[8] = {f.Xsv, f.LZv, f.Ttv, f.RESv, f.Zv, f.Pv, f.APv, f.LXv};
   for (const void* p : ptrs)
     if (!aligned16(p)) return 1;
   if (f.b <= 4 && sizeof(T) == 4) return split_launch<T, 4>(g, f, s, max_ctas);

@@ -178,6 +178,7 @@ struct JD {
   TP* AP;
   TP* LXb;  // L X of the correction solve
   TP* Xs;   // X packed for the per-phase correction solve
+  TP* LZb;  // L z~ of the per-phase correction solve
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
@@ -231,7 +232,7 @@ struct JD {
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     add(2 * n * z.ldv * sizeof(TV));
     add(n * z.ldb * sizeof(TV));
-    for (int i = 0; i < 9; ++i) add(n * z.ldb * sizeof(TP));
+    for (int i = 0; i < 10; ++i) add(n * z.ldb * sizeof(TP));
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
@@ -255,6 +256,7 @@ struct JD {
     AP = a.take<TP>(n * z.ldb);
     LXb = a.take<TP>(n * z.ldb);
     Xs = a.take<TP>(n * z.ldb);
+    LZb = a.take<TP>(n * z.ldb);
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
     Y = a.take<double>(S * mm);
@@ -404,6 +406,7 @@ struct JD {
                           delta, itmax, G->d_long_seg);
     f.early_exit = 1;
     f.Xsv = Xs;
+    f.LZv = LZb;
     if (pcg_fused<TP>(g, f, st, pw->max_ctas) != 0) {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;

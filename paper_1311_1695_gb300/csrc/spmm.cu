@@ -66,6 +66,7 @@ __device__ __forceinline__ void gather_row(T (&acc)[BMAX], const T* __restrict__
 template <typename T, int BMAX, int TEAM, bool VEC>
 __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ X, int ldx,
                                               T* __restrict__ Y, int ldy, int b) {
+  if (g.skip_flag && *(volatile const int*)g.skip_flag) return;
   const T* __restrict__ w = weights_of<T>(g);
   T acc[BMAX];
 #pragma unroll
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(256) k_spmm(DevGraph g, const T* __restrict__ 
 template <typename T, int BWL>
 __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restrict__ X, int ldx,
                                                    T* __restrict__ Y, int ldy, int b) {
+  if (g.skip_flag && *(volatile const int*)g.skip_flag) return;
   const T* __restrict__ w = weights_of<T>(g);
   constexpr int RW = 32 / BWL;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,6 +180,101 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
   Y[(size_t)row * ldy + c] = degree_of<T>(g, row) * X[(size_t)row * ldx + c] - a;
 }
 
+// Vectorised rows (b <= 16, X and Y rows 16-byte aligned): NQ lanes own a
+// row, lane q the W columns [W q, W q + W) as one vector load per nonzero; a
+// warp takes RPW = 32 / NQ ordinary rows from the degree-sorted schedule, so
+// its rows have nearly the same length and no lane waits long for another,
+// and walks them with U independent gathers per lane.  Hub rows are chunked
+// over the first blocks as in k_spmm_cols (BWL lanes as columns).
+template <typename T, int NQ, int BWL>
+__global__ void __launch_bounds__(256) k_spmm_vec(DevGraph g, const T* __restrict__ X, int ldx,
+                                                  T* __restrict__ Y, int ldy, int b) {
+  if (g.skip_flag && *(volatile const int*)g.skip_flag) return;
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::w;
+  constexpr int RPW = 32 / NQ;
+  constexpr int U = 4;
+  const T* __restrict__ w = weights_of<T>(g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nhb = (g.nchunk + 7) / 8;
+  if ((int)blockIdx.x < nhb) {  // hub chunks, lanes as columns
+    constexpr int RW = 32 / BWL;
+    const int c = lane % BWL;
+    const bool colok = c < b;
+    const int ch = blockIdx.x * 8 + warp;
+    if (ch >= g.nchunk) return;  // whole warp
+    const int4 cc = g.chunks[ch];
+    T a = T(0);
+#pragma unroll 8
+    for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+      const int j = __ldg(g.colidx + p);
+      const T wv = w ? __ldg(w + p) : T(1);
+      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+    }
+#pragma unroll
+    for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (!hub_finish<T>(g, ch, cc, a, b)) return;
+    const int row = cc.x;
+    if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
+    return;
+  }
+  const int grp = lane / NQ, q = lane - grp * NQ;
+  const int slot = ((blockIdx.x - nhb) * 8 + warp) * RPW + grp;
+  if (grp >= RPW || slot >= g.norder) return;  // no shuffles below
+  const int row = __ldg(g.order + slot);
+  const int p0 = __ldg(g.rowptr + row), p1 = __ldg(g.rowptr + row + 1);
+  const V* __restrict__ Xv = reinterpret_cast<const V*>(X);
+  const int ldxv = ldx / W;
+  T acc[W];
+#pragma unroll
+  for (int e = 0; e < W; ++e) acc[e] = T(0);
+  auto add = [&](const V& v, T wv) {
+    if constexpr (W == 4) {
+      acc[0] += wv * v.x; acc[1] += wv * v.y; acc[2] += wv * v.z; acc[3] += wv * v.w;
+    } else {
+      acc[0] += wv * v.x; acc[1] += wv * v.y;
+    }
+  };
+  int p = p0;
+  for (; p + U <= p1; p += U) {
+    int col[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) col[u] = __ldg(g.colidx + p + u);
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = __ldg(Xv + (size_t)col[u] * ldxv + q);
+#pragma unroll
+    for (int u = 0; u < U; ++u) add(v[u], w ? __ldg(w + p + u) : T(1));
+  }
+  for (; p < p1; ++p) add(__ldg(Xv + (size_t)__ldg(g.colidx + p) * ldxv + q), w ? __ldg(w + p) : T(1));
+  const T d = degree_of<T>(g, row);
+  const V xr = Xv[(size_t)row * ldxv + q];
+  T out[W];
+  if constexpr (W == 4) {
+    out[0] = d * xr.x - acc[0]; out[1] = d * xr.y - acc[1]; out[2] = d * xr.z - acc[2]; out[3] = d * xr.w - acc[3];
+  } else {
+    out[0] = d * xr.x - acc[0]; out[1] = d * xr.y - acc[1];
+  }
+  const int c0 = W * q;
+  if (c0 + W <= b) {
+    V o;
+    if constexpr (W == 4) o = make_float4(out[0], out[1], out[2], out[3]);
+    else o = make_double2(out[0], out[1]);
+    reinterpret_cast<V*>(Y)[(size_t)row * (ldy / W) + q] = o;
+  } else {
+#pragma unroll
+    for (int e = 0; e < W; ++e)
+      if (c0 + e < b) Y[(size_t)row * ldy + c0 + e] = out[e];
+  }
+}
+
+template <typename T, int NQ, int BWL>
+static void launch_vec(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
+  constexpr int RPB = 8 * (32 / NQ);  // rows per block
+  const int blocks = (g.nchunk + 7) / 8 + (g.norder + RPB - 1) / RPB;
+  if (blocks > 0) k_spmm_vec<T, NQ, BWL><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+}
+
 template <typename T, int BWL>
 static void launch_cols(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
   constexpr int RPB = 8 * (32 / BWL);  // rows per block
@@ -220,8 +317,10 @@ template double spmm_bytes<float>(const DevGraph&, int);
 template double spmm_bytes<double>(const DevGraph&, int);
 
 template <typename T>
-void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
-  LAP_PROF(sizeof(T) == 4 ? "spmm_f32" : "spmm_f64", spmm_bytes<T>(g, b), s);
+void spmm(const DevGraph& g0, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip) {
+  LAP_PROF(sizeof(T) == 4 ? "spmm_f32" : "spmm_f64", spmm_bytes<T>(g0, b), s);
+  DevGraph g = g0;
+  g.skip_flag = skip;
   constexpr int W = Vec2<T>::w;
   for (int c0 = 0; c0 < b; c0 += 32) {
     const int bb = (b - c0) < 32 ? (b - c0) : 32;
@@ -230,6 +329,23 @@ void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStre
     const int bpad = (bb + W - 1) / W * W;
     const bool vec = bb > 1 && (reinterpret_cast<uintptr_t>(Xc) % 16 == 0) && (ldx % W == 0) &&
                      (c0 + bpad <= ldx);
+    const bool yvec = (reinterpret_cast<uintptr_t>(Yc) % 16 == 0) && (ldy % W == 0) && (c0 + bpad <= ldy);
+    if (vec && yvec && bb >= 3 && bb <= 16 && g.order) {
+      // vectorised rows on the degree-sorted schedule
+      const int nq = (bb + W - 1) / W;
+      if (W == 4) {
+        if (nq <= 1) launch_vec<T, 1, 4>(g, Xc, ldx, Yc, ldy, bb, s);
+        else if (nq <= 2) launch_vec<T, 2, 8>(g, Xc, ldx, Yc, ldy, bb, s);
+        else if (nq <= 3) launch_vec<T, 3, 16>(g, Xc, ldx, Yc, ldy, bb, s);
+        else launch_vec<T, 4, 16>(g, Xc, ldx, Yc, ldy, bb, s);
+      } else {
+        if (nq <= 2) launch_vec<T, 2, 4>(g, Xc, ldx, Yc, ldy, bb, s);
+        else if (nq <= 4) launch_vec<T, 4, 8>(g, Xc, ldx, Yc, ldy, bb, s);
+        else if (nq <= 6) launch_vec<T, 6, 16>(g, Xc, ldx, Yc, ldy, bb, s);
+        else launch_vec<T, 8, 16>(g, Xc, ldx, Yc, ldy, bb, s);
+      }
+      continue;
+    }
     if (bb == 1) launch_bmax<T, 1>(g, Xc, ldx, Yc, ldy, bb, false, s);
     else if (bb == 2) launch_bmax<T, 4>(g, Xc, ldx, Yc, ldy, bb, vec, s);
     else if (bb <= 4) launch_cols<T, 4>(g, Xc, ldx, Yc, ldy, bb, s);
@@ -239,8 +355,8 @@ void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStre
   }
 }
 
-template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t);
-template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t);
+template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t, const int*);
+template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t, const int*);
 
 }  // namespace lapeig
 
