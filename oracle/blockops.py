@@ -74,20 +74,22 @@ def residual_norms(g, X: np.ndarray, theta: np.ndarray) -> np.ndarray:
 
 
 def pcg_correction(g, theta: np.ndarray, R: np.ndarray, Q: np.ndarray, iters: int,
-                   null: bool = True):
-    """``iters`` steps of projected Jacobi-preconditioned CG, column by column,
-    on Pi (L - theta_j I) Pi t_j = -r_j with Pi = I - [e/sqrt(n), Q][.]^T,
-    starting from t_j = 0.  No early exit, so the iterates are defined exactly.
-    Returns T (n x b)."""
+                   null: bool = True, precond=None):
+    """``iters`` steps of projected preconditioned CG, column by column, on
+    Pi (L - theta_j I) Pi t_j = -r_j with Pi = I - [e/sqrt(n), Q][.]^T,
+    starting from t_j = 0, preconditioner Pi M Pi with M = D^{-1} (Jacobi) or
+    the callable ``precond`` (x -> M x).  No early exit, so the iterates are
+    defined exactly.  Returns T (n x b)."""
     lap = Laplacian(g)
     d = lap.d
+    apply = (lambda x: x / d) if precond is None else precond
     n, b = R.shape
     T = np.zeros((n, b))
     for j in range(b):
         th = theta[j]
         res = project(-R[:, j:j + 1], Q, null)[:, 0]
         t = np.zeros(n)
-        z = project((res / d)[:, None], Q, null)[:, 0]
+        z = project(apply(res)[:, None], Q, null)[:, 0]
         p = z.copy()
         rho = res @ z
         for _ in range(iters):
@@ -98,7 +100,7 @@ def pcg_correction(g, theta: np.ndarray, R: np.ndarray, Q: np.ndarray, iters: in
             alpha = rho / pq
             t = t + alpha * p
             res = res - alpha * q
-            z = project((res / d)[:, None], Q, null)[:, 0]
+            z = project(apply(res)[:, None], Q, null)[:, 0]
             rho_new = res @ z
             beta = rho_new / rho
             rho = rho_new

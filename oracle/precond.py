@@ -1,6 +1,15 @@
 """Preconditioners P ~ L^{-1} (Section 3, item 2; Section 3.1.1; Section 4).
 
 * ``jacobi``: P = D^{-1}, the diagonal of L inverted.
+* ``fsai``:   a factored sparse approximate inverse P = G^T G, the
+  "approximate inverse ... as a product of sparse matrices" the paper's
+  conclusion (Section 5) proposes for parallel machines.  G is lower
+  triangular with the pattern of tril(A), A = L + alpha diag(L) (L itself is
+  singular), row i from the small system A[P_i, P_i] y = e_i over its pattern
+  P_i = {j <= i : A_ij != 0}, g_i = y / sqrt(y_i); so (G A)_ij = 0 for
+  j in P_i, j != i, and (G A G^T)_ii = 1.  Reading: a row whose pattern holds
+  more than FSAI_CAP entries keeps only its diagonal (g_ii = 1/sqrt(a_ii)),
+  so the set-up stays local; alpha = 1e-3 as for IC(0).
 * ``ic0``:    incomplete Cholesky with no fill-in, K^{-1} = (F F^T)^{-1}
   (Section 4), computed on L + alpha diag(L).  L is singular (L e = 0), so the
   last pivot of an exact factorisation vanishes; the paper does not discuss
@@ -50,6 +59,36 @@ def ic0_factor(Lmat: sp.csr_matrix, alpha: float):
     return sp.csr_matrix((vi, (ri, ci)), shape=(n, n))
 
 
+FSAI_CAP = 32
+
+
+def fsai_factor(Lmat: sp.csr_matrix, alpha: float = 1e-3, cap: int = FSAI_CAP) -> sp.csr_matrix:
+    """G (lower triangular, CSR) of the factored approximate inverse G^T G of
+    A = L + alpha diag(L), row by row."""
+    n = Lmat.shape[0]
+    A = (Lmat + alpha * sp.diags(Lmat.diagonal())).tocsr()
+    A.sort_indices()
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        pat = [int(j) for j in A.indices[lo:hi] if j <= i]
+        if len(pat) > cap:
+            pat = [i]
+        m = len(pat)
+        sub = np.zeros((m, m))
+        for a, ja in enumerate(pat):
+            for c, jc in enumerate(pat):
+                sub[a, c] = A[ja, jc]
+        e = np.zeros(m)
+        e[pat.index(i)] = 1.0
+        y = np.linalg.solve(sub, e)
+        y /= np.sqrt(y[pat.index(i)])
+        rows += [i] * m
+        cols += pat
+        vals += list(y)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
 def make_preconditioner(lap, kind: str):
     if kind == "jacobi":
         dinv = 1.0 / lap.d
@@ -66,6 +105,10 @@ def make_preconditioner(lap, kind: str):
             y = spsolve_triangular(F, x, lower=True)
             return spsolve_triangular(Ft, y, lower=False)
         return apply
+    if kind == "fsai":
+        G = fsai_factor(lap.L)
+        Gt = G.T.tocsr()
+        return lambda x: Gt @ (G @ x)
     if kind == "none":
         return lambda x: x
     raise ValueError(kind)

@@ -285,8 +285,8 @@ def _cg_krylov_minimiser(A, M, rhs, j):
     return K @ np.linalg.solve(K.T @ A @ K, K.T @ rhs)
 
 
-@pytest.mark.parametrize("weighted", [False, True])
-def test_pcg_correction_iterates_are_cg_optimal(weighted):
+@pytest.mark.parametrize("weighted,kind", [(False, "jacobi"), (True, "jacobi"), (False, "fsai"), (True, "fsai")])
+def test_pcg_correction_iterates_are_cg_optimal(weighted, kind):
     """Algorithm 2 step 8 after j steps (not only at convergence): with Q =
     [e/sqrt(n), X] and theta below the spectrum of L on the complement of Q
     (the SPD case), the projected operator A = Pi (L - theta) Pi and the
@@ -309,9 +309,16 @@ def test_pcg_correction_iterates_are_cg_optimal(weighted):
     lam = np.linalg.eigvalsh(Z.T @ Lm @ Z)[0]
     theta = np.array([0.5 * lam, 0.1 * lam, 0.9 * lam])
     R = uniform_block(22, n, 3)
-    M = Pi @ np.diag(1.0 / lap.d) @ Pi
+    from oracle import precond as pc
+    if kind == "jacobi":
+        Mfull, fn = np.diag(1.0 / lap.d), None
+    else:
+        Gf = pc.fsai_factor(lap.L).toarray()
+        Mfull = Gf.T @ Gf
+        fn = pc.make_preconditioner(lap, "fsai")
+    M = Pi @ Mfull @ Pi
     for j in (1, 2, 3, 5, 8):
-        T = blockops.pcg_correction(g, theta, R, X, iters=j)
+        T = blockops.pcg_correction(g, theta, R, X, iters=j, precond=fn)
         for c in range(3):
             A = Pi @ (Lm - theta[c] * np.eye(n)) @ Pi
             ref = _cg_krylov_minimiser(A, M, -Pi @ R[:, c], j)
@@ -350,3 +357,54 @@ def test_canonical_signs_convention():
     assert np.array_equal(W[:, 2], -V[:, 2])
     assert np.array_equal(W[:, 3], -V[:, 3])
     assert np.array_equal(V[0], [0.1, 0.5, -0.5, 0.0])  # input untouched
+
+
+
+@pytest.mark.parametrize("cap", [32, 2])
+def test_fsai_factor_defining_conditions(cap):
+    """Factored approximate inverse (Section 5's product of sparse matrices):
+    G lower triangular on the pattern of tril(A) (rows over the cap keep
+    their diagonal), (G A)_ij = 0 for j < i in the row's pattern, and
+    (G A G^T)_ii = 1, A = L + alpha diag(L)."""
+    from oracle import precond as pc
+    import scipy.sparse as sp
+    g = G.with_random_weights(G.chung_lu(200, 2.3, 4.0, 3), 5)
+    lap = Laplacian(g)
+    alpha = 1e-3
+    Gm = pc.fsai_factor(lap.L, alpha, cap).toarray()
+    A = (lap.L + alpha * sp.diags(lap.L.diagonal())).toarray()
+    assert np.allclose(np.triu(Gm, 1), 0.0)
+    low = np.tril(A) != 0
+    capped = low.sum(axis=1) > cap
+    pat = low.copy()
+    pat[capped] = np.eye(g.n, dtype=bool)[capped]
+    assert np.array_equal(Gm != 0, pat)
+    GA = Gm @ A
+    off = pat & ~np.eye(g.n, dtype=bool)
+    assert np.abs(GA[off]).max() < 1e-12 * np.abs(A).max()
+    assert np.allclose(np.diag(Gm @ A @ Gm.T), 1.0, atol=1e-12)
+    if cap == 2:
+        assert capped.any()
+
+
+def test_fsai_with_a_full_pattern_is_the_exact_inverse():
+    """On a complete graph tril(A) is full: G is the inverse Cholesky factor
+    and G^T G = A^{-1} exactly."""
+    from oracle import precond as pc
+    import scipy.sparse as sp
+    g = G.complete_graph(9)
+    lap = Laplacian(g)
+    Gm = pc.fsai_factor(lap.L, 1e-3).toarray()
+    A = (lap.L + 1e-3 * sp.diags(lap.L.diagonal())).toarray()
+    assert np.allclose(Gm.T @ Gm, np.linalg.inv(A), atol=1e-10)
+
+
+@pytest.mark.parametrize("g", [G.ba_graph(300, 2, 21), G.chung_lu(600, 2.3, 4.0, 8)], ids=["ba300", "cl600"])
+def test_jd_with_fsai_reaches_the_same_pairs(g):
+    """The preconditioner changes the iteration counts, not the pairs.  (Like
+    any single-vector JD with locking, the oracle can skip an eigenvalue and
+    lock the next one first; ba(200, 2, 4) does so with this preconditioner,
+    which is why the GPU solver works on a block.)"""
+    ev_ref, _ = dense.smallest_eigpairs(g, 4)
+    ev, V, _ = jd.jd_smallest(g, 4, precond="fsai")
+    _check_pairs(g, ev, V, ev_ref, 1e-8)
