@@ -57,6 +57,7 @@ enum {
 typedef enum { LAP_JD = 0, LAP_DACG = 1, LAP_IRLM = 2 } lap_method;
 typedef enum { LAP_PREC_FP64 = 0, LAP_PREC_MIXED = 1 } lap_precision;
 typedef enum { LAP_F64 = 0, LAP_F32 = 1 } lap_dtype;
+typedef enum { LAP_PRECOND_JACOBI = 0, LAP_PRECOND_FSAI = 1 } lap_precond;
 
 /* Options.  Zero-initialise and set struct_size = sizeof(lap_opts) (or call
  * lap_opts_default); a zero field means "default". */
@@ -93,6 +94,12 @@ typedef struct {
   int max_ctas;       /* cap on the CTAs of the persistent kernels (0 = the
                          handle's setting, default all co-resident CTAs); fewer
                          CTAs give each more row tiles (tuning, sharing the GPU) */
+  int precond;        /* JD correction-solve preconditioner: LAP_PRECOND_JACOBI
+                         (default, D^{-1}) or LAP_PRECOND_FSAI (G^T G, see
+                         lap_graph_set_precond); applied where the per-phase
+                         correction solve runs (rows of at most 64 bytes: FP32
+                         b <= 16, FP64 b <= 8), else Jacobi */
+  double precond_alpha; /* FSAI: diagonal shift alpha of A = L + alpha diag(L) (0 = 1e-3) */
   double ev_rtol;     /* JD: a pair also needs its Ritz value within ev_rtol
                          relative of an eigenvalue by the Kato-Temple bound
                          ||r||^2 / delta (delta = distance to the nearest other
@@ -168,6 +175,19 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
  * Calls that run SpMM-type kernels on one handle must be stream-ordered:
  * the handle's reduction and hub-chunk scratch is shared by them. */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
+
+/* Preconditioner of the correction solve on this handle (Section 3 item 2,
+ * Section 3.2.1).  LAP_PRECOND_JACOBI: M = D^{-1}, nothing to set up.
+ * LAP_PRECOND_FSAI: the factored sparse approximate inverse M = G^T G, the
+ * preconditioner as a product of sparse matrices that the paper's conclusion
+ * (Section 5) proposes for parallel machines: G lower triangular with the
+ * pattern of tril(A), A = L + alpha diag(L) (alpha > 0; 0 = 1e-3), each row
+ * from a small SPD system on its pattern, so that (G A)_ij = 0 for j in the
+ * pattern, j != i, and (G A G^T)_ii = 1; rows with more than 32 entries in
+ * their pattern keep the diagonal only.  Computed on the host at this call
+ * (rows in parallel), applied on the device as two sparse products.  The
+ * correction solve then runs in its per-phase form. */
+int lap_graph_set_precond(lap_graph* g, int kind, double alpha);
 
 /* Launch settings of the correction solve and orthonormalisation on this
  * handle, used by the step-level entry points and by solves whose opts leave

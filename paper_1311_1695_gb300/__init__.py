@@ -26,6 +26,8 @@ LAP_ENUMERIC, LAP_ENOMEM, LAP_ETIMEOUT, LAP_ECUDA, LAP_EUNSORTED = -5, -6, -7, -
 LAP_JD, LAP_DACG, LAP_IRLM = 0, 1, 2
 LAP_PREC_FP64, LAP_PREC_MIXED = 0, 1
 LAP_F64, LAP_F32 = 0, 1
+LAP_PRECOND_JACOBI, LAP_PRECOND_FSAI = 0, 1
+_PRECONDS = {"jacobi": LAP_PRECOND_JACOBI, "fsai": LAP_PRECOND_FSAI}
 
 _METHODS = {"jd": LAP_JD, "dacg": LAP_DACG, "irlm": LAP_IRLM}
 _PRECISIONS = {"fp64": LAP_PREC_FP64, "mixed": LAP_PREC_MIXED}
@@ -60,6 +62,8 @@ class lap_opts(ctypes.Structure):
         ("cuda_graph", ctypes.c_int),
         ("device_timeout_ms", ctypes.c_double),
         ("max_ctas", ctypes.c_int),
+        ("precond", ctypes.c_int),
+        ("precond_alpha", ctypes.c_double),
         ("ev_rtol", ctypes.c_double),
     ]
 
@@ -112,6 +116,7 @@ _SIGNATURES = {
     "lap_graph_info": (_I, [_P, _PI64, _PI, _PD, _PI, _PI]),
     "lap_graph_set_schedule": (_I, [_P, _I, _I]),
     "lap_graph_set_launch": (_I, [_P, _I, _D, _I]),
+    "lap_graph_set_precond": (_I, [_P, _I, _D]),
     "lap_spmm": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gram": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
     "lap_gram_noalloc": (_I, [_I64, _I, _P, _I, _I, _P, _I, _I, _I, _P, _P]),
@@ -175,7 +180,8 @@ def _ptr(a, ct):
 
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
               include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
-              x0_dev=None, cuda_graph=True, device_timeout_ms=0.0, max_ctas=0, ev_rtol=0.0):
+              x0_dev=None, cuda_graph=True, device_timeout_ms=0.0, max_ctas=0, ev_rtol=0.0, precond="jacobi",
+              precond_alpha=0.0):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -187,6 +193,8 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.stream = stream
     o.cuda_graph = 0 if cuda_graph else -1
     o.device_timeout_ms, o.max_ctas, o.ev_rtol = device_timeout_ms, max_ctas, ev_rtol
+    o.precond = _PRECONDS[precond] if isinstance(precond, str) else int(precond)
+    o.precond_alpha = precond_alpha
     keep = None
     if x0_dev is not None:  # a row-major float64 CUDA tensor n x k0
         o.x0_dev = ctypes.c_void_p(x0_dev.data_ptr())
@@ -310,6 +318,11 @@ class Graph:
 
     def set_schedule(self, team=0, long_thresh=0):
         _check(lib().lap_graph_set_schedule(self.h, team, long_thresh), "lap_graph_set_schedule")
+
+    def set_precond(self, kind="fsai", alpha=0.0):
+        """Correction-solve preconditioner of the handle (lap_graph_set_precond)."""
+        _check(lib().lap_graph_set_precond(self.h, _PRECONDS[kind] if isinstance(kind, str) else int(kind), alpha),
+               "lap_graph_set_precond")
 
     def set_launch(self, max_ctas=0, device_timeout_ms=0.0, split_rows=0):
         """CTA cap, device wait limit, and the row count from which the

@@ -67,6 +67,13 @@ void add_null(SolveOut& out, const std::vector<int>& nrows, const std::vector<in
   }
 }
 
+// opts.precond: set the handle's preconditioner when the solve asks for
+// one it does not have
+int apply_precond(lap_graph* g, const lap_opts& o) {
+  if (o.precond == 0 || g->dg.precond == o.precond) return LAP_OK;
+  return graph_set_precond(g, o.precond, o.precond_alpha);
+}
+
 // opts.team: > 0 fixed lanes per row, -1 autotuned on the graph
 int apply_team(lap_graph* g, const lap_opts& o, int k) {
   if (o.team > 0) return graph_set_schedule(g, o.team, 0);
@@ -150,6 +157,8 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
     rc = apply_team(g, o, kmax);
     if (rc) { graph_free(g); return rc; }
   }
+  rc = apply_precond(g, o);
+  if (rc) { graph_free(g); return rc; }
   SolveOut out;
   rc = solve_jd(g, kmax, tol, o, want, out, kk.data());
   graph_free(g);
@@ -194,6 +203,8 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
     rc = apply_team(g, o, k);
     if (rc) { graph_free(g); return rc; }
   }
+  rc = apply_precond(g, o);
+  if (rc) { graph_free(g); return rc; }
   SolveOut out;
   rc = solve(g, kk, tol, method, o, evecs != nullptr, out);
   graph_free(g);
@@ -227,6 +238,10 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
   if (o.include_null && evecs_dev) { set_error("include_null needs host eigenvectors (use lap_eigs)"); return LAP_EINVAL; }
   if (o.team) {
     const int rc = apply_team(g, o, k);
+    if (rc) return rc;
+  }
+  {
+    const int rc = apply_precond(g, o);
     if (rc) return rc;
   }
   SolveOut out;

@@ -71,6 +71,13 @@ struct DevGraph {
   // set by a launcher for one launch: the SpMM kernels return at once when
   // *skip_flag is nonzero (a correction solve that already stopped)
   const int* skip_flag;
+  // preconditioner of the correction solve: 0 Jacobi (the degrees), 1 the
+  // factored approximate inverse G^T G (precond.cu), G and G^T in CSR
+  int precond;
+  const int *pg_rp, *pg_ci, *pt_rp, *pt_ci;
+  const double *pg_v64, *pt_v64;
+  const float *pg_v32, *pt_v32;
+  int pg_nnz;
 };
 
 constexpr int kHubChunk = 128;

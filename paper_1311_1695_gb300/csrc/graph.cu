@@ -299,6 +299,8 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 
   std::vector<float> w32(w64.begin(), w64.end());
   std::vector<float> deg32(deg.begin(), deg.end());
+  g->colidx_h = colcat;  // kept for set-ups that need the pattern (preconditioner)
+  g->w64_h = w64;
   Packer pk;
   pk.add(&g->d_rowptr, g->rowptr_h.data(), g->rowptr_h.size());
   pk.add(&g->d_colidx, colcat.data(), colcat.size());
@@ -347,6 +349,7 @@ void graph_free(lap_graph* g) {
   if (!g) return;
   cudaFree(g->d_block);  // every array of the graph
   cudaFree(g->d_sched);  // the hub schedule
+  cudaFree(g->d_prec);   // the preconditioner
   cudaFree(g->scratch); cudaFree(g->small);
   g->pcg.release();
   delete g;

@@ -77,6 +77,10 @@ struct lap_graph {
   std::vector<int> row0, tile_ptr;
   std::vector<double> norm1;
   std::vector<int> rowptr_h;   // int32 concatenated
+  std::vector<int> colidx_h;   // global column numbering
+  std::vector<double> w64_h;   // empty for unit weights
+  void* d_prec = nullptr;      // the preconditioner's arrays (precond.cu)
+  double prec_alpha = 0.0;
   std::vector<int> long_rows_h;
   double avg_degree = 0.0;
   int max_degree = 0;
@@ -98,6 +102,12 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
                 const double* const* weights, lap_graph** out);
 void graph_free(lap_graph* g);
 int graph_set_schedule(lap_graph* g, int team, int long_thresh);
+// Preconditioner of the correction solve (LAP_PRECOND_*), set up on the host.
+int graph_set_precond(lap_graph* g, int kind, double alpha);
+// Y = G X or G^T X of the factored approximate inverse (b <= 16, rows 16-byte aligned).
+template <typename T>
+void fsai_apply(const DevGraph& g, int transpose, const T* X, int ldx, T* Y, int ldy, int b, const int* skip,
+                cudaStream_t s);
 int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_out, cudaStream_t s);
 // Barrier wait limit in ns: the first positive of (opts, handle), else the default.
 unsigned long long timeout_ns_of(double opts_ms, double handle_ms);

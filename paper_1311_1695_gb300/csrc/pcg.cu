@@ -553,8 +553,9 @@ double pcg_bytes(const DevGraph& g, int b, int iters, int elem) {
 
 bool pcg_uses_split(const DevGraph& g, const FusedPcg& f, int elem) {
   const size_t rowb = (size_t)elem * f.ld;
-  return f.Xsv && f.LZv && f.stop && g.order && g.n >= (f.split_rows > 0 ? f.split_rows : kSplitRows) && f.ld >= f.b &&
-         rowb <= 64 && rowb % 16 == 0 && f.ldlx == f.ld;
+  // the approximate-inverse preconditioner exists only in the per-phase form
+  const bool want = g.precond != 0 || g.n >= (f.split_rows > 0 ? f.split_rows : kSplitRows);
+  return want && f.Xsv && f.LZv && f.stop && g.order && f.ld >= f.b && rowb <= 64 && rowb % 16 == 0 && f.ldlx == f.ld;
 }
 
 template <typename T>

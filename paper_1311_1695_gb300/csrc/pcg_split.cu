@@ -31,6 +31,7 @@
 #include "hub.cuh"
 #include "kernels.cuh"
 #include "pcg_fused.cuh"
+#include "internal.h"
 #include "pcg_parts.cuh"
 #include "prof.h"
 
@@ -298,7 +299,7 @@ __device__ __forceinline__ void coeffs(T (&Gc)[BMAX + 1], const T* tot, int b, i
 // partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity 1.  (L X itself comes
 // from the SpMM launched before.)  Staged block: X rows of the tile.
 template <typename T, int BMAX, int BWL>
-__global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T> sv) {
+__global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T> sv, int fsai) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   Ctx<T, BMAX, BWL> cx;
@@ -342,8 +343,10 @@ __global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T
         }
         const size_t o = (size_t)r * ld + c;
         const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
+        f.RES[o] = res; f.Tt[o] = T(0);
+        if (fsai) continue;  // z~ = G^T G r and its Gram follow in their own launches
         const T z = res / cx.s_deg[il];
-        f.RES[o] = res; f.Tt[o] = T(0); f.Z[o] = z;
+        f.Z[o] = z;
         gram_ld<T, BMAX>(acc, xs + (size_t)il * ld, z, ld);
         ex[0] += res * z;
         ex[1] += res * res;
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
 // z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity `par`.
 // Staged blocks: q~, r, t, p, X rows of the tile.
 template <typename T, int BMAX, int BWL>
-__global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> sv, int it) {
+__global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> sv, int it, int fsai) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   if (__ldcg(sv.stop)) return;
@@ -547,11 +550,67 @@ __global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> s
         const size_t so = (size_t)il * ld;
         const T q = project_ld<T, BMAX>(sq[so + c], sx + so, Gc, ld);
         const T res = sr[so + c] - al * q;
-        const T z = res / cx.s_deg[il];
         const size_t o = (size_t)r * ld + c;
         __stcs(f.Tt + o, st[so + c] + al * sp[so + c]);
+        if (fsai) {  // z~ = G^T G r and its Gram follow in their own launches
+          f.RES[o] = res;
+          continue;
+        }
+        const T z = res / cx.s_deg[il];
         __stcs(f.RES + o, res);
         f.Z[o] = z;  // gathered by the next SpMM: normal priority
+        gram_ld<T, BMAX>(acc, sx + so, z, ld);
+        ex[0] += res * z;
+        ex[1] += res * res;
+      }
+    }
+  }
+  if (cur >= 0 && !fsai) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+}
+
+// ---------------------------------------------------------------- the preconditioned residual's Gram
+// With the approximate inverse, z~ = G^T G r comes from two sparse products
+// after phase B; this launch adds partial G2 = [1|X]^T z~, r.z~, r.r into
+// acc2 parity `par`.  Staged blocks: z~, r, X rows of the tile.
+template <typename T, int BMAX, int BWL>
+__global__ void __launch_bounds__(kThreads) k_split_g2(DevGraph g, SplitView<T> sv, int par) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const View<T>& f = sv.v;
+  if (__ldcg(sv.stop)) return;
+  const int ld = f.ld, b = f.b;
+  Ctx<T, BMAX, BWL> cx;
+  cx.setup(smem_raw, 3, ld);
+  constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, grp = warp * RW + lane / BWL;
+  const bool colok = c < b;
+  T acc[BMAX + 1];
+  T ex[2] = {T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
+  int cur = -1;
+  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
+    const Tile t = g.tiles[ti];
+    if (f.seg_skip && f.seg_skip[t.seg]) continue;
+    if (t.seg != cur) {
+      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+      cur = t.seg;
+    }
+    const int nrows = t.r1 - t.r0;
+    __syncthreads();  // the previous tile's readers are done with the stage
+    {
+      const T* src[3] = {f.Z, f.RES, sv.Xs};
+      const int lds[3] = {ld, ld, ld};
+      cx.issue<3>(src, lds, ld, t.r0, t.r1, 1u);
+    }
+    if (!cx.wait(f.bar)) return;
+    if (colok) {
+      const T* sz = cx.blk(0, ld);
+      const T* sr = cx.blk(1, ld);
+      const T* sx = cx.blk(2, ld);
+      for (int il = grp; il < nrows; il += SLOTS) {
+        const size_t so = (size_t)il * ld;
+        const T z = sz[so + c], res = sr[so + c];
         gram_ld<T, BMAX>(acc, sx + so, z, ld);
         ex[0] += res * z;
         ex[1] += res * res;
@@ -615,19 +674,30 @@ int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_c
   auto ki = k_split_init<T, BMAX, BWL>;
   auto km = k_split_m<T, BMAX, BWL>;
   auto kb = k_split_b<T, BMAX, BWL>;
-  const size_t si = L::bytes(1, ld), sm = L::bytes(6, ld), sb = L::bytes(5, ld);
+  auto kg = k_split_g2<T, BMAX, BWL>;
+  const size_t si = L::bytes(1, ld), sm = L::bytes(6, ld), sb = L::bytes(5, ld), sg = L::bytes(3, ld);
   const int gi = grid_of(reinterpret_cast<const void*>(ki), si);
   const int gm = grid_of(reinterpret_cast<const void*>(km), sm);
   const int gb = grid_of(reinterpret_cast<const void*>(kb), sb);
+  const int fsai = g.precond == LAP_PRECOND_FSAI ? 1 : 0;
+  const int gg = fsai ? grid_of(reinterpret_cast<const void*>(kg), sg) : 1;
+  // z~ = G^T (G r): G r into the L z~ block (free until the next step's SpMM), then G^T
+  auto precondition = [&](int par) {
+    fsai_apply<T>(g, 0, ff.RES, ld, LZ, ld, f.b, f.stop, s);
+    fsai_apply<T>(g, 1, LZ, ld, ff.Z, ld, f.b, f.stop, s);
+    kg<<<gg, kThreads, sg, s>>>(g, sv, par);
+  };
   const int64_t tot = (int64_t)g.n * ld;
   const int pgrid = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)nsm * 8);
   k_pack_x<T><<<pgrid > 0 ? pgrid : 1, 256, 0, s>>>(g.n, ff.X, f.ldx, Xs, ld, f.b);
-  ki<<<gi, kThreads, si, s>>>(g, sv);  // resets the stop flag first
+  ki<<<gi, kThreads, si, s>>>(g, sv, fsai);  // resets the stop flag first
   spmm<T>(g, Xs, ld, ff.LX, f.ldlx, f.b, s, f.stop);
+  if (fsai) precondition(1);
   for (int it = 0; it < f.itmax; ++it) {
     spmm<T>(g, ff.Z, ld, LZ, ld, f.b, s, f.stop);  // returns at once after a stop
     km<<<gm, kThreads, sm, s>>>(g, sv, it);
-    kb<<<gb, kThreads, sb, s>>>(g, sv, it);
+    kb<<<gb, kThreads, sb, s>>>(g, sv, it, fsai);
+    if (fsai) precondition(it & 1);
   }
   k_split_fin<T><<<std::max(1, std::min(g.ntiles, nsm * 4)), kThreads, 0, s>>>(g, sv, f.itmax);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
