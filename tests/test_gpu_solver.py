@@ -225,3 +225,14 @@ def test_batched_per_graph_k_and_method(pkg, method):
         assert ev.size == k and V.shape == (g.n, k)
         ev_ref, V_ref = all_pairs(g)
         check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)
+
+
+@pytest.mark.parametrize("precision,k", [("mixed", 10), ("fp64", 6)])
+def test_solve_with_approximate_inverse(pkg, precision, k):
+    """Whole solves with the factored approximate-inverse preconditioner
+    (opts.precond): the same pairs as the dense definition."""
+    g = G.workload_graph("c1")
+    ev, V, info = pkg.lap_eigs(g, k, tol=1e-8, precision=precision, precond="fsai")
+    assert info["status"] == 0, info
+    ev_ref, V_ref = all_pairs(g)
+    check_eigpairs(g, ev, V, ev_ref, V_ref, k=k)

@@ -427,3 +427,32 @@ def test_pcg_per_phase_form_batched_with_hubs(pkg, dt):
         assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
         off += g.n
     Gd.close()
+
+
+@pytest.mark.parametrize("dt,b", [(torch.float32, 12), (torch.float32, 4), (torch.float64, 8)])
+def test_pcg_correction_with_approximate_inverse(pkg, dt, b):
+    """The correction solve with the factored approximate inverse G^T G
+    (two sparse products per step) against the oracle's fixed-step projected
+    PCG with the oracle's own FSAI factor."""
+    from oracle import precond as pc
+    g, U = _wide_graph()
+    Gd = pkg.Graph(g)
+    Gd.set_precond("fsai")
+    X, theta, R = _ritz_block(g, U, b, 90 + b)
+    npdt = np.float32 if dt == torch.float32 else np.float64
+    X, R = X.astype(npdt), R.astype(npdt)
+    if dt == torch.float32:
+        theta = np.full_like(theta, 0.5 * theta[0])  # SPD shift: FP32 follows FP64 to rounding
+    iters = 8
+    out = {}
+
+    def run():
+        out["T"] = Gd.pcg_correction(_dev(X, dt), torch.from_numpy(theta[None, :]).cuda(), _dev(R, dt), iters)
+    names = _kernel_names(pkg, run)
+    assert "precond_apply" in names and "pcg_split" in names, names
+    T = out["T"].cpu().double().numpy()
+    M = pc.make_preconditioner(Laplacian(g), "fsai")
+    ref = blockops.pcg_correction(g, theta, R.astype(np.float64), X.astype(np.float64), iters, precond=M)
+    err = (np.abs(T - ref).max(axis=0) / np.abs(ref).max(axis=0)).max()
+    assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
+    Gd.close()
