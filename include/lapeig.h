@@ -116,7 +116,9 @@ typedef struct {
   double max_rel_residual;/* max_j ||L v_j - lambda_j v_j||_2 / ||L||_1, FP64, explicit */
   double elapsed_ms;      /* wall time inside the call */
   int phase1_outer;       /* mixed precision: outer iterations done in FP32 */
-  int spmm_team;          /* SpMM lanes per row used */
+  int spmm_team;          /* lanes per row of the scalar SpMM kernels (blocks of 1-2 columns) */
+  int spmm_unroll;        /* gathers in flight per lane of the vectorised SpMM */
+  int hub_threshold;      /* rows longer than this are split into chunks over warps */
 } lap_info;
 
 void lap_opts_default(lap_opts* opts);
@@ -240,9 +242,13 @@ int lap_block_update(lap_graph* g, int dtype, void* Y, int ldy, int q, double be
                      int lda, int p, int ones, const double* S, int lds, int64_t ss, void* stream);
 
 /* Autotune the SpMM schedule of the handle: time the degree-fused SpMM on a
- * b-column block of dtype for lanes-per-row 4, 8, 16, 32 and several hub
- * thresholds with CUDA events, keep the fastest (returned in team/thresh,
- * nullable).  Allocates a scratch block for the trial. */
+ * b-column block of dtype with CUDA events for hub thresholds 32, 64, 128,
+ * 256 and none, and for 2, 4 or 8 gathers in flight per lane (the
+ * vectorised kernel, 3 <= b <= 16; returned in team) or 4, 8, 16, 32 lanes
+ * per row (the scalar kernels, b <= 2); keep the fastest (team and thresh
+ * nullable).  Allocates a scratch block for the trial.  lap_eigs_graph runs
+ * it once per handle at the first solve of a graph of 100,000 rows or more
+ * (and whenever opts.team = -1). */
 int lap_graph_autotune(lap_graph* g, int dtype, int b, int* team, int* thresh, void* stream);
 
 /* ---------------------------------------------------------------- step-level entry points

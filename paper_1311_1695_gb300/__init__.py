@@ -80,6 +80,8 @@ class lap_info(ctypes.Structure):
         ("elapsed_ms", ctypes.c_double),
         ("phase1_outer", ctypes.c_int),
         ("spmm_team", ctypes.c_int),
+        ("spmm_unroll", ctypes.c_int),
+        ("hub_threshold", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -318,6 +320,15 @@ class Graph:
 
     def set_schedule(self, team=0, long_thresh=0):
         _check(lib().lap_graph_set_schedule(self.h, team, long_thresh), "lap_graph_set_schedule")
+
+    def autotune(self, dtype="f32", b=12):
+        """Time the SpMM schedules on this handle and keep the fastest
+        (lap_graph_autotune); returns (gathers in flight or lanes per row,
+        hub threshold)."""
+        t, h = ctypes.c_int(), ctypes.c_int()
+        _check(lib().lap_graph_autotune(self.h, LAP_F32 if dtype == "f32" else LAP_F64, b, ctypes.byref(t),
+                                        ctypes.byref(h), _stream()), "lap_graph_autotune")
+        return t.value, h.value
 
     def set_precond(self, kind="fsai", alpha=0.0):
         """Correction-solve preconditioner of the handle (lap_graph_set_precond)."""

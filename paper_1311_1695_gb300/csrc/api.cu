@@ -236,8 +236,11 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
     if (kk < 1 || kk > nrows[s] - 1) { set_error("k out of range for a graph"); return LAP_EINVAL; }
   }
   if (o.include_null && evecs_dev) { set_error("include_null needs host eigenvectors (use lap_eigs)"); return LAP_EINVAL; }
-  if (o.team) {
-    const int rc = apply_team(g, o, k);
+  if (o.team || (!g->tuned && g->hg.n >= kSplitRows)) {
+    // a resident handle of a large graph is autotuned once, at its first solve
+    lap_opts ot = o;
+    if (!ot.team) ot.team = -1;
+    const int rc = apply_team(g, ot, k);
     if (rc) return rc;
   }
   {

@@ -50,7 +50,8 @@ struct DevGraph {
   const int* long_rows;  // hub rows: degree > long_thresh, longest first
   int nlong;
   int long_thresh;
-  int team;              // lanes per row in the SpMM (autotuned)
+  int team;              // lanes per row in the scalar SpMM kernels (autotuned)
+  int vec_u;             // gathers in flight per lane in the vectorised SpMM (autotuned)
   // Hub rows are split into chunks of at most kHubChunk nonzeros, one warp
   // per chunk.  A hub with several chunks combines them through hub_part
   // (per chunk: kMaxCols column sums + the weight sum) and an arrival

@@ -339,6 +339,7 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   // schedule heuristic (overridden by the autotuner or the caller)
   d.team = g->avg_degree <= 6.0 ? 4 : (g->avg_degree <= 24.0 ? 8 : (g->avg_degree <= 96.0 ? 16 : 32));
   d.long_thresh = 64;
+  d.vec_u = 4;
   rc = graph_set_schedule(g, 0, 0);
   if (rc) { graph_free(g); return rc; }
   *out = g;

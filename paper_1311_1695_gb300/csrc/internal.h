@@ -93,6 +93,7 @@ struct lap_graph {
   int max_ctas = 0;             // persistent-kernel CTA cap (0: all co-resident)
   double timeout_ms = 0.0;      // grid-barrier wait limit (0: default)
   int split_rows = 0;           // per-phase correction solve from this many rows (0: default)
+  int tuned = 0;                // the SpMM schedule was autotuned on this handle
 };
 
 namespace lapeig {

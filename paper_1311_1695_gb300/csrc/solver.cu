@@ -651,6 +651,8 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
     in.norm_L = G->norm1[s];
     in.max_rel_residual = worst;
     in.spmm_team = G->dg.team;
+    in.spmm_unroll = G->dg.vec_u;
+    in.hub_threshold = G->dg.long_thresh;
   }
   if (want_vecs && out.dev_vecs) {
     copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, out.dev_vecs, st);

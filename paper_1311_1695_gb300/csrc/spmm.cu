@@ -186,14 +186,13 @@ __global__ void __launch_bounds__(256) k_spmm_cols(DevGraph g, const T* __restri
 // its rows have nearly the same length and no lane waits long for another,
 // and walks them with U independent gathers per lane.  Hub rows are chunked
 // over the first blocks as in k_spmm_cols (BWL lanes as columns).
-template <typename T, int NQ, int BWL>
+template <typename T, int NQ, int BWL, int U>
 __global__ void __launch_bounds__(256) k_spmm_vec(DevGraph g, const T* __restrict__ X, int ldx,
                                                   T* __restrict__ Y, int ldy, int b) {
   if (g.skip_flag && *(volatile const int*)g.skip_flag) return;
   using V = typename Vec2<T>::type;
   constexpr int W = Vec2<T>::w;
   constexpr int RPW = 32 / NQ;
-  constexpr int U = 4;
   const T* __restrict__ w = weights_of<T>(g);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nhb = (g.nchunk + 7) / 8;
@@ -268,11 +267,15 @@ __global__ void __launch_bounds__(256) k_spmm_vec(DevGraph g, const T* __restric
   }
 }
 
+// g.vec_u: independent gathers per lane in flight (2, 4 or 8; the autotuner's choice)
 template <typename T, int NQ, int BWL>
 static void launch_vec(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
   constexpr int RPB = 8 * (32 / NQ);  // rows per block
   const int blocks = (g.nchunk + 7) / 8 + (g.norder + RPB - 1) / RPB;
-  if (blocks > 0) k_spmm_vec<T, NQ, BWL><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+  if (blocks <= 0) return;
+  if (g.vec_u <= 2) k_spmm_vec<T, NQ, BWL, 2><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+  else if (g.vec_u >= 8) k_spmm_vec<T, NQ, BWL, 8><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+  else k_spmm_vec<T, NQ, BWL, 4><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
 }
 
 template <typename T, int BWL>
@@ -381,13 +384,19 @@ int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_ou
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // candidates: the hub threshold, and lanes per row of the scalar kernels
+  // (b <= 2) or gathers in flight per lane of the vectorised one
+  const bool vec_path = b >= 3 && b <= 16;
   const int teams[4] = {4, 8, 16, 32};
-  const int threshs[4] = {32, 64, 128, 1 << 30};
+  const int unrolls[4] = {2, 4, 8, 8};
+  const int threshs[5] = {32, 64, 128, 256, 1 << 30};
+  const int nvar = vec_path ? 3 : 4;
   float best = 1e30f;
-  int bt = g->dg.team, bh = g->dg.long_thresh;
-  for (int ti = 0; ti < 4; ++ti) {
-    for (int hi = 0; hi < 4; ++hi) {
-      if (graph_set_schedule(g, teams[ti], threshs[hi]) != LAP_OK) continue;
+  int bt = g->dg.team, bh = g->dg.long_thresh, bu = g->dg.vec_u;
+  for (int ti = 0; ti < nvar; ++ti) {
+    for (int hi = 0; hi < 5; ++hi) {
+      if (graph_set_schedule(g, vec_path ? 0 : teams[ti], threshs[hi]) != LAP_OK) continue;
+      if (vec_path) g->dg.vec_u = unrolls[ti];
       auto run = [&]() {
         if (dtype == LAP_F32) spmm<float>(g->dg, (const float*)X, ld, (float*)Y, ld, b, s);
         else spmm<double>(g->dg, (const double*)X, ld, (double*)Y, ld, b, s);
@@ -399,14 +408,16 @@ int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_ou
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bt = teams[ti]; bh = threshs[hi]; }
+      if (ms < best) { best = ms; bt = vec_path ? g->dg.team : teams[ti]; bh = threshs[hi]; bu = g->dg.vec_u; }
     }
   }
+  g->dg.vec_u = bu;
+  g->tuned = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
   const int rc = graph_set_schedule(g, bt, bh);
-  if (team_out) *team_out = bt;
+  if (team_out) *team_out = vec_path ? bu : bt;
   if (thresh_out) *thresh_out = bh;
   if (cudaGetLastError() != cudaSuccess) { set_error("CUDA error in autotune"); return LAP_ECUDA; }
   return rc;

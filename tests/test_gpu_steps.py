@@ -456,3 +456,23 @@ def test_pcg_correction_with_approximate_inverse(pkg, dt, b):
     err = (np.abs(T - ref).max(axis=0) / np.abs(ref).max(axis=0)).max()
     assert err <= (1e-8 if dt == torch.float64 else 5e-3), err
     Gd.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float64])
+@pytest.mark.parametrize("b", [2, 12])
+def test_autotuned_schedule_matches_oracle(pkg, dt, b):
+    """The autotuner picks among its candidates and the SpMM it leaves in
+    place gives the oracle's L X (hub rows included)."""
+    g = GRAPHS["cl_hubs"]()
+    Gd = pkg.Graph(g)
+    u, h = Gd.autotune("f32" if dt == torch.float32 else "f64", b)
+    assert h in (32, 64, 128, 256, 1 << 30)
+    assert u in ((2, 4, 8) if b >= 3 else (4, 8, 16, 32))
+    X = G.random_block(g.n, b, 21).astype(np.float32 if dt == torch.float32 else np.float64)
+    Xd = _dev(X, dt)
+    Yd = torch.empty_like(Xd)
+    Gd.spmm(Xd, Yd)
+    ref = blockops.lap_spmm(g, X.astype(np.float64))
+    S, deg = _abs_bound(g, X.astype(np.float64))
+    assert np.all(np.abs(Yd.cpu().double().numpy() - ref) <= 2 * EPS[dt] * deg[:, None] * S + 1e-300)
+    Gd.close()
