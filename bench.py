@@ -439,7 +439,10 @@ def bench_ours(args):
                    "step_ms": [round(x, 3) for x in times]},
         "roofline": roofline, "spmm_roofline": spmm_roof, "kernels": kern_table,
         "gpu_launches": int(launches) * args.steps, "clocks": clk, "e2e": e2e, "cpu_baseline": base,
-        "compare": compare, "oracle_compare": ocmp, "schedule": tuned, "start": args.warm,
+        "compare": compare, "oracle_compare": ocmp,
+        "schedule": tuned or {"spmm_gathers_in_flight": inf.get("spmm_unroll"), "hub_threshold": inf.get("hub_threshold"),
+                              "autotuned": n >= 100000},
+        "start": args.warm,
     }
     G.close()
     if rank == 0:
