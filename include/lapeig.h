@@ -241,6 +241,28 @@ int lap_gnn_tanh(lap_graph* g, int mode, float* Z, int ldz, const float* H, int 
 int lap_block_update(lap_graph* g, int dtype, void* Y, int ldy, int q, double beta, double alpha, const void* A,
                      int lda, int p, int ones, const double* S, int lds, int64_t ss, void* stream);
 
+/* BF16 forms of the network's kernels (tensor cores; storage BF16, products
+ * accumulated in FP32).  Blocks are row-major over all rows of the handle;
+ * BF16 blocks are __nv_bfloat16 arrays.
+ *   lap_gnn_features_bf16 : the features of lap_gnn_features, stored in BF16.
+ *   lap_gnn_aggregate_bf16: Y = D^{-1} A X (transpose 0) or A D^{-1} X
+ *                           (transpose 1) on BF16 X, Y; w <= 32; FP32 sums.
+ *   lap_gnn_dense_bf16    : Y = act(A W + 1 b^T), A BF16 n x K (K = 32 or 64,
+ *                           lda even), W BF16 K x 32 row-major (columns past
+ *                           ncols zero), b FP32 [32] or NULL, act 1 = tanh;
+ *                           Y BF16 (out_bf16 = 1, ldy even) or FP32, the
+ *                           first ncols <= 32 columns written.
+ *   lap_gnn_wgrad_bf16    : Gw = A^T dZ over all rows (K x 32, device FP64,
+ *                           overwritten), A BF16 n x K, dZ FP32 n x 32 (ldz
+ *                           >= 32; rounded to BF16 for the product).
+ *   lap_gnn_tanh_back_bf16: dZ <- dZ (1 - H^2), dZ FP32, H BF16 (w <= 64). */
+int lap_gnn_features_bf16(lap_graph* g, uint64_t seed, int nfeat, void* F, int ldf, void* stream);
+int lap_gnn_aggregate_bf16(lap_graph* g, int transpose, const void* X, int ldx, void* Y, int ldy, int w, void* stream);
+int lap_gnn_dense_bf16(lap_graph* g, int K, const void* A, int lda, const void* W, const float* bias, void* Y, int ldy,
+                       int ncols, int act, int out_bf16, void* stream);
+int lap_gnn_wgrad_bf16(lap_graph* g, int K, const void* A, int lda, const float* dZ, int ldz, double* Gw, void* stream);
+int lap_gnn_tanh_back_bf16(lap_graph* g, float* dZ, int ldz, const void* H, int ldh, int w, void* stream);
+
 /* Autotune the SpMM schedule of the handle: time the degree-fused SpMM on a
  * b-column block of dtype with CUDA events for hub thresholds 32, 64, 128,
  * 256 and none, and for 2, 4 or 8 gathers in flight per lane (the

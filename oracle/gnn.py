@@ -82,16 +82,31 @@ def _mean_agg_T(g, H):
     return lap.A @ (H / lap.d[:, None])
 
 
-def forward(g, F, params):
-    H = F
+def round_bf16(x) -> np.ndarray:
+    """Nearest BFloat16 value (8-bit significand, ties to even) of each
+    entry, as FP64: the float32 bit pattern with its low 16 bits rounded
+    away (values and their FP32 rounding: the stored activations are FP32
+    sums rounded once)."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)) << np.uint64(16)
+    return r.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(x))
+
+
+def forward(g, F, params, store=None):
+    """store: None (FP64 throughout) or a rounding applied to every stored
+    activation -- the features, each aggregation hop, each layer's output --
+    as the BF16 inference and training kernels store them."""
+    keep = (lambda v: v) if store is None else store
+    H = keep(F)
     cache = []
     for l in range(LAYERS):
         W, U, b = params[3 * l: 3 * l + 3]
         MH = H
         for _ in range(HOPS):
-            MH = _mean_agg(g, MH)
+            MH = keep(_mean_agg(g, MH))
         Z = MH @ W + H @ U + b[None, :]
-        Hn = np.tanh(Z)
+        Hn = keep(np.tanh(Z))
         cache.append((H, MH, Hn))
         H = Hn
     X = H @ params[-1]

@@ -126,6 +126,11 @@ _SIGNATURES = {
     "lap_gnn_aggregate": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_gnn_tanh": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
     "lap_block_update": (_I, [_P, _I, _P, _I, _I, _D, _D, _P, _I, _I, _I, _P, _I, _I64, _P]),
+    "lap_gnn_features_bf16": (_I, [_P, ctypes.c_uint64, _I, _P, _I, _P]),
+    "lap_gnn_aggregate_bf16": (_I, [_P, _I, _P, _I, _P, _I, _I, _P]),
+    "lap_gnn_dense_bf16": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _I, _P]),
+    "lap_gnn_wgrad_bf16": (_I, [_P, _I, _P, _I, _P, _I, _P, _P]),
+    "lap_gnn_tanh_back_bf16": (_I, [_P, _P, _I, _P, _I, _I, _P]),
     "lap_graph_autotune": (_I, [_P, _I, _I, _PI, _PI, _P]),
     "lap_project": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _P]),
     "lap_cgs2": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _PI, _P]),

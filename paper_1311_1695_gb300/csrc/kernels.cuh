@@ -15,8 +15,11 @@ struct Reduce {
 
 // ---- K1: Y = L X (degree fused), b columns
 // skip (device, nullable): the launch does nothing when *skip != 0.
+// profile = false: not timed on its own (a part of a launch sequence that
+// the profiler times as one, such as the per-phase correction solve).
 template <typename T>
-void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip = nullptr);
+void spmm(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip = nullptr,
+          bool profile = true);
 
 // ---- Gram: G[s] = [1 | A]^T B per segment (ones adds a leading row of column
 // sums, divided by the segment's row count when ones_mean is set).  G is

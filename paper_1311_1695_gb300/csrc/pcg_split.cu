@@ -691,10 +691,10 @@ int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_c
   const int pgrid = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)nsm * 8);
   k_pack_x<T><<<pgrid > 0 ? pgrid : 1, 256, 0, s>>>(g.n, ff.X, f.ldx, Xs, ld, f.b);
   ki<<<gi, kThreads, si, s>>>(g, sv, fsai);  // resets the stop flag first
-  spmm<T>(g, Xs, ld, ff.LX, f.ldlx, f.b, s, f.stop);
+  spmm<T>(g, Xs, ld, ff.LX, f.ldlx, f.b, s, f.stop, false);
   if (fsai) precondition(1);
   for (int it = 0; it < f.itmax; ++it) {
-    spmm<T>(g, ff.Z, ld, LZ, ld, f.b, s, f.stop);  // returns at once after a stop
+    spmm<T>(g, ff.Z, ld, LZ, ld, f.b, s, f.stop, false);  // returns at once after a stop
     km<<<gm, kThreads, sm, s>>>(g, sv, it);
     kb<<<gb, kThreads, sb, s>>>(g, sv, it, fsai);
     if (fsai) precondition(it & 1);

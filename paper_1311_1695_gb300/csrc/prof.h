@@ -18,7 +18,9 @@ void prof_set_last_bytes(const char* name, double bytes);
 struct ProfScope {
   int slot;
   cudaStream_t s;
-  ProfScope(const char* name, double bytes, cudaStream_t st) : slot(prof_on() ? prof_begin(name, bytes, st) : -1), s(st) {}
+  // name nullptr: not timed (a launch inside a sequence timed as one)
+  ProfScope(const char* name, double bytes, cudaStream_t st)
+      : slot(name && prof_on() ? prof_begin(name, bytes, st) : -1), s(st) {}
   ~ProfScope() {
     if (slot >= 0) prof_end(slot, s);
   }

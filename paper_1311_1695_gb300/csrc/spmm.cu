@@ -320,8 +320,9 @@ template double spmm_bytes<float>(const DevGraph&, int);
 template double spmm_bytes<double>(const DevGraph&, int);
 
 template <typename T>
-void spmm(const DevGraph& g0, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip) {
-  LAP_PROF(sizeof(T) == 4 ? "spmm_f32" : "spmm_f64", spmm_bytes<T>(g0, b), s);
+void spmm(const DevGraph& g0, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s, const int* skip,
+          bool profile) {
+  LAP_PROF(profile ? (sizeof(T) == 4 ? "spmm_f32" : "spmm_f64") : nullptr, spmm_bytes<T>(g0, b), s);
   DevGraph g = g0;
   g.skip_flag = skip;
   constexpr int W = Vec2<T>::w;
@@ -358,8 +359,8 @@ void spmm(const DevGraph& g0, const T* X, int ldx, T* Y, int ldy, int b, cudaStr
   }
 }
 
-template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t, const int*);
-template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t, const int*);
+template void spmm<float>(const DevGraph&, const float*, int, float*, int, int, cudaStream_t, const int*, bool);
+template void spmm<double>(const DevGraph&, const double*, int, double*, int, int, cudaStream_t, const int*, bool);
 
 }  // namespace lapeig
 

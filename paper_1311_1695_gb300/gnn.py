@@ -2,15 +2,19 @@
 proposes the initial Jacobi-Davidson block, trained on eigenvectors the
 solver itself computed.  The paper has no learned component.
 
-Every forward and backward step runs in the library's kernels
-(lap_gnn_features / lap_gnn_aggregate / lap_gnn_tanh / lap_block_update /
-lap_gram); this module only lays out the device buffers and marshals the
-small parameter matrices.  Weights are kept as FP64 masters and rounded to
-BF16 for every use (the kernels compute with FP32 data and accumulate in FP32
-within a row, FP64 across rows).
+Every forward and backward step runs in the library's kernels; this module
+only lays out the device buffers and marshals the small parameter matrices.
+Storage and arithmetic: the node features, every aggregation hop and every
+layer's output are BF16 (lap_gnn_features_bf16, lap_gnn_aggregate_bf16);
+the dense layers [M^s H | H] [W; U] + b are BF16 tensor-core products with
+FP32 accumulation and the tanh fused (lap_gnn_dense_bf16); the weight
+gradients [M^s H | H]^T dZ are BF16 tensor-core products over the rows with
+FP32 accumulation within a CTA and FP64 across CTAs (lap_gnn_wgrad_bf16);
+the output X, the loss gradient dX and the back-propagated dH are FP32.
+Weights are FP64 masters rounded to BF16 for every use.
 
 Network, for a batch handle of graphs (each graph its own segment):
-    H_0 = F (features),  [M^s H_l | H_l] [W_l; U_l] + b_l -> tanh -> H_{l+1},
+    H_0 = F (features),  tanh([M^s H_l | H_l] [W_l; U_l] + b_l) -> H_{l+1},
     X = C H_3 W_out,     M = D^{-1} A,  s = HOPS,  C = per-graph centring.
 Loss per graph: 1 - tr(G^{-1} X^T U U^T X) / k with G = X^T X + eps tr(X^T X)/k I
 (U = solver eigenvectors); the k x k algebra of the loss runs on the host.
@@ -76,16 +80,17 @@ class Net:
         self.G, self.k = G, k
         n = G.n
         dev = "cuda"
-        f32 = torch.float32
-        # AH_l = [M H_l | H_l]; layer 0 holds the features in its right half
-        self.AH = [torch.zeros((n, 2 * NFEAT), dtype=f32, device=dev)] + \
-                  [torch.zeros((n, 2 * WIDTH), dtype=f32, device=dev) for _ in range(LAYERS)]
+        f32, b16 = torch.float32, torch.bfloat16
+        # AH_l = [M^s H_l | H_l] in BF16; layer 0 holds the features in its right half
+        self.AH = [torch.zeros((n, 2 * NFEAT), dtype=b16, device=dev)] + \
+                  [torch.zeros((n, 2 * WIDTH), dtype=b16, device=dev) for _ in range(LAYERS)]
+        self.tmp = [torch.zeros((n, WIDTH), dtype=b16, device=dev) for _ in range(2)]
         self.UX = torch.zeros((n, 2 * k), dtype=f32, device=dev)  # [U | X]
-        self.dX = torch.zeros((n, k), dtype=f32, device=dev)
+        self.dX = torch.zeros((n, WIDTH), dtype=f32, device=dev)  # k columns used, the rest zero
         self.dH = torch.zeros((n, WIDTH), dtype=f32, device=dev)
         self.T1 = torch.zeros((n, WIDTH), dtype=f32, device=dev)
         self.dHn = torch.zeros((n, WIDTH), dtype=f32, device=dev)
-        self.tmp = [torch.zeros((n, WIDTH), dtype=f32, device=dev) for _ in range(2)]
+        self.ftmp = [torch.zeros((n, WIDTH), dtype=f32, device=dev) for _ in range(2)]
         self.nseg = G.nseg
         self.rows = np.diff(G.row0)
 
@@ -110,15 +115,46 @@ class Net:
                               ctypes.c_void_p(B), ldb, q, ones, ctypes.c_void_p(Gm.data_ptr()), _stream()), "lap_gram")
         return Gm
 
-    def _aggregate(self, transpose, src, lds, dst, ldd, w):
-        """dst = M^s src (transpose = 0) or (M^T)^s src, s = HOPS."""
+    def _weights_bf16(self, mats, cols=WIDTH):
+        """Stacked BF16 weights (rows of the inputs, `cols` columns, zero padded)."""
+        import torch
+        W = np.concatenate([np.atleast_2d(m) for m in mats], axis=0)
+        Wp = np.zeros((W.shape[0], cols))
+        Wp[:, :W.shape[1]] = W
+        # the values are BF16 already (to_bf16): the conversion is exact
+        return torch.from_numpy(Wp).to(torch.float32).to(torch.bfloat16).cuda().contiguous()
+
+    def _aggregate16(self, src, lds, dst, ldd, w):
+        """dst = M^s src, every hop stored in BF16 (s = HOPS)."""
         cur, ldc = src, lds
         for h in range(HOPS):
             last = h == HOPS - 1
             out, ldo = (dst, ldd) if last else (self.tmp[h % 2].data_ptr(), WIDTH)
-            _check(lib().lap_gnn_aggregate(self.G.h, transpose, ctypes.c_void_p(cur), ldc, ctypes.c_void_p(out), ldo, w,
+            _check(lib().lap_gnn_aggregate_bf16(self.G.h, 0, ctypes.c_void_p(cur), ldc, ctypes.c_void_p(out), ldo, w,
+                                                _stream()), "lap_gnn_aggregate_bf16")
+            cur, ldc = out, ldo
+
+    def _aggregate_T32(self, src, lds, dst, ldd, w):
+        """dst = (M^T)^s src on FP32 blocks (back-propagation)."""
+        cur, ldc = src, lds
+        for h in range(HOPS):
+            last = h == HOPS - 1
+            out, ldo = (dst, ldd) if last else (self.ftmp[h % 2].data_ptr(), WIDTH)
+            _check(lib().lap_gnn_aggregate(self.G.h, 1, ctypes.c_void_p(cur), ldc, ctypes.c_void_p(out), ldo, w,
                                            _stream()), "lap_gnn_aggregate")
             cur, ldc = out, ldo
+
+    def _dense(self, K, A, lda, W, bias, Y, ldy, ncols, act, out_bf16):
+        _check(lib().lap_gnn_dense_bf16(self.G.h, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(W.data_ptr()),
+                                        None if bias is None else ctypes.c_void_p(bias.data_ptr()), ctypes.c_void_p(Y),
+                                        ldy, ncols, act, out_bf16, _stream()), "lap_gnn_dense_bf16")
+
+    def _wgrad(self, K, A, lda, dZ, ldz):
+        import torch
+        Gw = torch.zeros((K, WIDTH), dtype=torch.float64, device="cuda")
+        _check(lib().lap_gnn_wgrad_bf16(self.G.h, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(dZ), ldz,
+                                        ctypes.c_void_p(Gw.data_ptr()), _stream()), "lap_gnn_wgrad_bf16")
+        return Gw.cpu().numpy()
 
     def _centre(self, Y, ldy, q):
         """Subtract each graph's column means from Y (n x q, FP32)."""
@@ -128,28 +164,29 @@ class Net:
 
     # -- forward: returns X (view of UX[:, k:])
     def forward(self, params, seed: int):
+        import torch
         P = [to_bf16(p) for p in params]
         AH = self.AH
-        e4 = 4
-        # features into the right half of AH_0
-        _check(lib().lap_gnn_features(self.G.h, seed, NFEAT, ctypes.c_void_p(AH[0].data_ptr() + e4 * NFEAT),
-                                      2 * NFEAT, _stream()), "lap_gnn_features")
+        e2 = 2  # bytes per BF16 value
+        _check(lib().lap_gnn_features_bf16(self.G.h, seed, NFEAT, ctypes.c_void_p(AH[0].data_ptr() + e2 * NFEAT),
+                                           2 * NFEAT, _stream()), "lap_gnn_features_bf16")
         fin = NFEAT
+        self._dev_w = []
         for l in range(LAYERS):
             A = AH[l]
             # left half = M^s H_l
-            self._aggregate(0, A.data_ptr() + e4 * fin, 2 * fin, A.data_ptr(), 2 * fin, fin)
+            self._aggregate16(A.data_ptr() + e2 * fin, 2 * fin, A.data_ptr(), 2 * fin, fin)
             W, U, b = P[3 * l: 3 * l + 3]
-            S, lds, ss = self._S([b[None, :], W, U])
-            out = AH[l + 1]
-            Hn = out.data_ptr() + e4 * WIDTH
-            self._update(Hn, 2 * WIDTH, WIDTH, 0.0, A.data_ptr(), 2 * fin, 2 * fin, 1, S, lds, 0)
-            _check(lib().lap_gnn_tanh(self.G.h, 0, ctypes.c_void_p(Hn), 2 * WIDTH, None, 0, WIDTH, _stream()),
-                   "lap_gnn_tanh")
+            Wd = self._weights_bf16([W, U])
+            bd = torch.from_numpy(b).float().cuda()
+            self._dev_w.append((Wd, bd))
+            Hn = AH[l + 1].data_ptr() + e2 * WIDTH
+            self._dense(2 * fin, A.data_ptr(), 2 * fin, Wd, bd, Hn, 2 * WIDTH, WIDTH, 1, 1)
             fin = WIDTH
-        S, lds, ss = self._S([P[-1]])
-        X = self.UX.data_ptr() + e4 * self.k
-        self._update(X, 2 * self.k, self.k, 0.0, AH[LAYERS].data_ptr() + e4 * WIDTH, 2 * WIDTH, WIDTH, 0, S, lds, 0)
+        Wo = self._weights_bf16([P[-1]])
+        self._dev_w.append((Wo, None))
+        X = self.UX.data_ptr() + 4 * self.k
+        self._dense(WIDTH, AH[LAYERS].data_ptr() + e2 * WIDTH, 2 * WIDTH, Wo, None, X, 2 * self.k, self.k, 0, 0)
         self._centre(X, 2 * self.k, self.k)
         self._P = P
         return self.UX[:, self.k:]
@@ -178,37 +215,37 @@ class Net:
             S[s, k:] = (2.0 / k) * (A + (EPS_RIDGE / k) * np.trace(A) * np.eye(k)) / self.nseg
         import torch
         St = torch.from_numpy(S).cuda()
-        self._update(self.dX.data_ptr(), k, k, 0.0, UXp, 2 * k, 2 * k, 0, St, k, 2 * k * k)
+        self._update(self.dX.data_ptr(), WIDTH, k, 0.0, UXp, 2 * k, 2 * k, 0, St, k, 2 * k * k)
         return losses
 
     # -- backward: gradients (summed over the graphs of the batch), FP64 numpy
     def backward(self):
         P, k, AH = self._P, self.k, self.AH
-        e4 = 4
+        e2 = 2
         grads = [None] * len(P)
-        self._centre(self.dX.data_ptr(), k, k)  # the centring is its own adjoint
-        H3 = AH[LAYERS].data_ptr() + e4 * WIDTH
-        grads[-1] = self._gram(H3, 2 * WIDTH, WIDTH, self.dX.data_ptr(), k, k, 0).cpu().numpy().sum(axis=0)
+        self._centre(self.dX.data_ptr(), WIDTH, k)  # the centring is its own adjoint
+        H3 = AH[LAYERS].data_ptr() + e2 * WIDTH
+        grads[-1] = self._wgrad(WIDTH, H3, 2 * WIDTH, self.dX.data_ptr(), WIDTH)[:, :k]
         S, lds, _ = self._S([P[-1].T])
-        self._update(self.dH.data_ptr(), WIDTH, WIDTH, 0.0, self.dX.data_ptr(), k, k, 0, S, lds, 0)
+        self._update(self.dH.data_ptr(), WIDTH, WIDTH, 0.0, self.dX.data_ptr(), WIDTH, k, 0, S, lds, 0)
         fin_of = [NFEAT] + [WIDTH] * (LAYERS - 1)
         for l in reversed(range(LAYERS)):
             fin = fin_of[l]
-            Hn = AH[l + 1].data_ptr() + e4 * WIDTH
+            Hn = AH[l + 1].data_ptr() + e2 * WIDTH
             dZ = self.dH.data_ptr()
-            _check(lib().lap_gnn_tanh(self.G.h, 1, ctypes.c_void_p(dZ), WIDTH, ctypes.c_void_p(Hn), 2 * WIDTH,
-                                      WIDTH, _stream()), "lap_gnn_tanh")
-            Gm = self._gram(AH[l].data_ptr(), 2 * fin, 2 * fin, dZ, WIDTH, WIDTH, 1).cpu().numpy()
-            # the leading row is a per-graph mean: back to a sum
-            db = (Gm[:, 0, :] * self.rows[:, None]).sum(axis=0)
-            grads[3 * l] = Gm[:, 1:1 + fin, :].sum(axis=0)
-            grads[3 * l + 1] = Gm[:, 1 + fin:, :].sum(axis=0)
-            grads[3 * l + 2] = db
+            _check(lib().lap_gnn_tanh_back_bf16(self.G.h, ctypes.c_void_p(dZ), WIDTH, ctypes.c_void_p(Hn), 2 * WIDTH,
+                                                WIDTH, _stream()), "lap_gnn_tanh_back_bf16")
+            Gw = self._wgrad(2 * fin, AH[l].data_ptr(), 2 * fin, dZ, WIDTH)
+            grads[3 * l] = Gw[:fin]
+            grads[3 * l + 1] = Gw[fin:]
+            Gm = self._gram(None, 0, 0, dZ, WIDTH, WIDTH, 1).cpu().numpy()
+            # the ones row is a per-graph mean: back to a sum
+            grads[3 * l + 2] = (Gm[:, 0, :] * self.rows[:, None]).sum(axis=0)
             if l > 0:
                 W, U = P[3 * l], P[3 * l + 1]
                 S, lds, _ = self._S([W.T])
                 self._update(self.T1.data_ptr(), WIDTH, fin, 0.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
-                self._aggregate(1, self.T1.data_ptr(), WIDTH, self.dHn.data_ptr(), WIDTH, fin)
+                self._aggregate_T32(self.T1.data_ptr(), WIDTH, self.dHn.data_ptr(), WIDTH, fin)
                 S, lds, _ = self._S([U.T])
                 self._update(self.dHn.data_ptr(), WIDTH, fin, 1.0, dZ, WIDTH, WIDTH, 0, S, lds, 0)
                 self.dH, self.dHn = self.dHn, self.dH

@@ -87,3 +87,19 @@ def test_features_shape_and_range():
     assert F.shape == (30, gnn.NFEAT)
     assert np.all(F[:, 0] == 1.0) and F[:, 1].max() == 1.0
     assert np.abs(F[:, 2:]).max() < 1.0
+
+
+def test_bf16_rounding_against_known_values():
+    """The oracle's BF16 rounding: 8 significant bits, ties to even."""
+    from oracle.gnn import round_bf16
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 2.0 ** -9, 1.0 + 3 * 2.0 ** -9, -3.14159, 65504.0, 1e-40])
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 (the spacing at 1): ties to even
+    ref = np.array([1.0, 1.0, 1.0, 1.0 + 2.0 ** -7, -3.140625, 65536.0, 0.0])
+    got = round_bf16(x)
+    assert np.array_equal(got[:6], ref[:6])
+    assert abs(got[6]) < 1e-38  # a float32 subnormal keeps its top bits
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(1000) * 10.0 ** rng.integers(-5, 5, 1000)
+    r = round_bf16(v)
+    assert np.all(np.abs(r - v) <= 2.0 ** -8 * np.abs(v) * (1 + 1e-6))
+    assert np.array_equal(round_bf16(r), r)  # idempotent
