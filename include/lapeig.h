@@ -59,12 +59,21 @@ typedef enum { LAP_PREC_FP64 = 0, LAP_PREC_MIXED = 1 } lap_precision;
 typedef enum { LAP_F64 = 0, LAP_F32 = 1 } lap_dtype;
 typedef enum { LAP_PRECOND_JACOBI = 0, LAP_PRECOND_FSAI = 1 } lap_precond;
 
+/* Stop test of a pair (lap_opts.tol_mode). */
+typedef enum {
+  LAP_TOL_NORM1 = 0, /* ||L v_j - theta_j v_j||_2 <= tol ||L||_1 (default) */
+  LAP_TOL_THETA = 1  /* ||L v_j - theta_j v_j||_2 <= tol theta_j: the relative-residual exit
+                        test of the paper's experiments (Section 4); needs theta_j > 0,
+                        i.e. a connected graph without include_null */
+} lap_tol_mode;
+
 /* Options.  Zero-initialise and set struct_size = sizeof(lap_opts) (or call
  * lap_opts_default); a zero field means "default". */
 typedef struct {
   uint32_t struct_size;
   int block;          /* JD block width b >= k (default min(k + 2, 32), at most 32) */
-  int m_keep;         /* JD: Ritz vectors kept at each restart (default b + 2);
+  int m_keep;         /* JD: Ritz vectors kept at each restart (default max(b + 2, 20),
+                         less on graphs too small for it);
                          the paper's m_min (Section 3.2, Section 4) */
   int inner_maxit;    /* correction-solve PCG steps, ITMAX (default 20, Section 4) */
   double inner_tol;   /* relative PCG residual drop delta_PCG (default 1e-2, Section 4) */
@@ -104,6 +113,7 @@ typedef struct {
                          relative of an eigenvalue by the Kato-Temple bound
                          ||r||^2 / delta (delta = distance to the nearest other
                          Ritz value farther than ||r||); 0 = 1e-7, < 0 = off */
+  int tol_mode;       /* lap_tol_mode (default LAP_TOL_NORM1) */
 } lap_opts;
 
 typedef struct {

@@ -28,6 +28,8 @@ LAP_PREC_FP64, LAP_PREC_MIXED = 0, 1
 LAP_F64, LAP_F32 = 0, 1
 LAP_PRECOND_JACOBI, LAP_PRECOND_FSAI = 0, 1
 _PRECONDS = {"jacobi": LAP_PRECOND_JACOBI, "fsai": LAP_PRECOND_FSAI}
+LAP_TOL_NORM1, LAP_TOL_THETA = 0, 1
+_TOL_MODES = {"norm1": LAP_TOL_NORM1, "theta": LAP_TOL_THETA}
 
 _METHODS = {"jd": LAP_JD, "dacg": LAP_DACG, "irlm": LAP_IRLM}
 _PRECISIONS = {"fp64": LAP_PREC_FP64, "mixed": LAP_PREC_MIXED}
@@ -65,6 +67,7 @@ class lap_opts(ctypes.Structure):
         ("precond", ctypes.c_int),
         ("precond_alpha", ctypes.c_double),
         ("ev_rtol", ctypes.c_double),
+        ("tol_mode", ctypes.c_int),
     ]
 
 
@@ -188,7 +191,7 @@ def _ptr(a, ct):
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
               include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
               x0_dev=None, cuda_graph=True, device_timeout_ms=0.0, max_ctas=0, ev_rtol=0.0, precond="jacobi",
-              precond_alpha=0.0):
+              precond_alpha=0.0, tol_mode="norm1"):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -202,6 +205,7 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
     o.device_timeout_ms, o.max_ctas, o.ev_rtol = device_timeout_ms, max_ctas, ev_rtol
     o.precond = _PRECONDS[precond] if isinstance(precond, str) else int(precond)
     o.precond_alpha = precond_alpha
+    o.tol_mode = _TOL_MODES[tol_mode] if isinstance(tol_mode, str) else int(tol_mode)
     keep = None
     if x0_dev is not None:  # a row-major float64 CUDA tensor n x k0
         o.x0_dev = ctypes.c_void_p(x0_dev.data_ptr())

@@ -109,7 +109,7 @@ struct DevBuf {
 
 int finish_pairs(lap_graph* G, const double* U, int ldu, int k, std::vector<double> lam, double tol,
                  bool want_vecs, SolveOut& out, int status, int outer, int inner, int64_t nmv, cudaStream_t st,
-                 bool rayleigh = false) {
+                 bool rayleigh, double theta_rel) {
   const DevGraph& g = G->dg;
   const int n = g.n;
   // explicit residuals of the returned pairs (FP64)
@@ -153,7 +153,8 @@ int finish_pairs(lap_graph* G, const double* U, int ldu, int k, std::vector<doub
     const double v = r2[ord[i]];  // NaN: never converged
     const double r = (v >= 0.0 ? std::sqrt(v) : (v < 0.0 ? 0.0 : HUGE_VAL)) / G->norm1[0];
     worst = std::max(worst, r);
-    if (prefix && r <= tol) ++nconv; else prefix = false;
+    const double thr = theta_rel > 0.0 ? pair_threshold(64.0 * 0x1p-53, theta_rel / G->norm1[0], lam[ord[i]]) : tol;
+    if (prefix && r <= thr) ++nconv; else prefix = false;
   }
   lap_info& in = out.info[0];
   in.status = (status == LAP_OK && nconv < k) ? LAP_ENOCONV : status;
@@ -214,7 +215,10 @@ int solve_dacg(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
   double* tmp = sm + 256;   // 64
   double* scl = sm + 320;   // 64
   const int maxit = o.max_outer > 0 ? std::max(o.max_outer * 50, 2000) : 50000;
-  const double stop = tol * G->norm1[0];
+  // stop test: tol ||L||_1, or tol q (q the Rayleigh quotient) under the
+  // relative-residual test of Section 4
+  const double theta_rel = o.tol_mode == LAP_TOL_THETA ? tol : 0.0;
+  const double stop_abs = theta_rel > 0.0 ? 64.0 * 0x1p-53 * G->norm1[0] : tol * G->norm1[0];
   std::vector<double> lam;
   int its_total = 0;
   int64_t nmv = 0;
@@ -260,7 +264,7 @@ int solve_dacg(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
         cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("CUDA error in DACG"); return LAP_ECUDA; }
         if (!std::isfinite(h[2])) { set_error("NaN/Inf in DACG"); return LAP_ENUMERIC; }
-        if (std::sqrt(h[2]) <= 0.5 * stop) { conv = true; ++it; break; }
+        if (std::sqrt(h[2]) <= 0.5 * pair_threshold(stop_abs, theta_rel, h[0])) { conv = true; ++it; break; }
         const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         if (o.max_seconds > 0 && el > o.max_seconds) { status = LAP_ETIMEOUT; break; }
       }
@@ -282,7 +286,7 @@ int solve_dacg(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
       break;
     }
   }
-  return finish_pairs(G, U, ldu, k, lam, tol, want_vecs, out, status, its_total, 0, nmv, st);
+  return finish_pairs(G, U, ldu, k, lam, tol, want_vecs, out, status, its_total, 0, nmv, st, false, theta_rel);
 }
 
 // Shifted QR steps on the symmetric tridiagonal T (m x m, stored full in
@@ -492,7 +496,7 @@ int solve_irlm(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vec
       for (int i = 0; i < k; ++i) lam[i] = 1.0 / evh[m - 1 - i];
       Xr = Xb;
       const int fs = finish_pairs(G, Xb, ldk, k, lam, tol, want_vecs, out, est_ok ? LAP_OK : (timeout ? LAP_ETIMEOUT : LAP_ENOCONV),
-                                  solves, inner, nmv, st, true);
+                                  solves, inner, nmv, st, true, o.tol_mode == LAP_TOL_THETA ? tol : 0.0);
       if (fs < 0) return fs;
       status = fs;
       if (status == LAP_OK || timeout || restarts + 1 == max_restarts) break;

@@ -92,8 +92,9 @@ __host__ __device__ inline bool ev_accurate(const double* th, int nrv, int j, do
 // then a fixed-order reduction over the warps.
 __global__ void k_converge(int nseg, const double* __restrict__ rn2, const double* __restrict__ theta, int mmax,
                            const double* __restrict__ norm1, const double* __restrict__ tol_abs, int kall,
-                           const int* __restrict__ kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state,
-                           int* active, int* skip, const unsigned* bar, JdStatus* status, double* segw) {
+                           const int* __restrict__ kseg, int b, int nrv, double ev_rtol, double theta_rel,
+                           int explicit_check, int* state, int* active, int* skip, const unsigned* bar,
+                           JdStatus* status, double* segw) {
   constexpr int NW = 8;
   __shared__ double s_w[NW];
   __shared__ int s_c[NW], s_bad[NW], s_act[NW], s_open[NW];
@@ -115,9 +116,10 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
         const double r = r2 >= 0.0 ? sqrt(r2) : (r2 < 0.0 ? 0.0 : r2);
         const double* th = theta + (size_t)s * mmax;
         fin = isfinite(r) && isfinite(th[j]);
-        c = r <= tol_abs[s] && th[j] <= norm1[s];
-        if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, j, r, tol_abs[s], ev_rtol);
-        ratio = j < k ? r / tol_abs[s] : 0.0;
+        const double thr = pair_threshold(tol_abs[s], theta_rel, th[j]);
+        c = r <= thr && th[j] <= norm1[s];
+        if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, j, r, thr, ev_rtol);
+        ratio = j < k ? r / thr : 0.0;
         active[(size_t)s * 64 + j] = (j < k && c) ? 0 : 1;
       }
       const bool segc = __all_sync(0xffffffffu, j >= k || c);
@@ -213,11 +215,12 @@ void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg
   k_h_border<<<nseg, 256, 0, s>>>(H, ldh, sh, G, ldg, sg, mk, b, keep, sk, norm1, seg_skip);
 }
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, const int* kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active,
-              int* skip, const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s) {
+              int k, const int* kseg, int b, int nrv, double ev_rtol, double theta_rel, int explicit_check,
+              int* state, int* active, int* skip, const unsigned* bar, JdStatus* status, double* segw,
+              cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
-  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, kseg, b, nrv, ev_rtol, explicit_check, state,
-                               active, skip, bar, status, segw);
+  k_converge<<<1, 256, 0, s>>>(nseg, rn2, theta, mmax, norm1, tol_abs, k, kseg, b, nrv, ev_rtol, theta_rel,
+                               explicit_check, state, active, skip, bar, status, segw);
 }
 
 bool ev_accurate_host(const double* th, int nrv, int j, double r, double tol_abs, double ev_rtol) {

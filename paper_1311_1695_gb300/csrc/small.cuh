@@ -31,9 +31,18 @@ struct JdStatus {
 // ev_rtol > 0 adds the eigenvalue-accuracy test (Kato-Temple estimate over
 // the nrv Ritz values of the basis, ev_accurate_host).
 // kseg (device [nseg], nullable): graph s wants kseg[s] <= k pairs.
+// theta_rel > 0: pair j's threshold is max(theta_rel |theta_j|, tol_abs[s])
+// (the relative-residual exit test of Section 4, tol_abs[s] then a floor),
+// else tol_abs[s] (pair_threshold).
 void converge(int nseg, const double* rn2, const double* theta, int mmax, const double* norm1, const double* tol_abs,
-              int k, const int* kseg, int b, int nrv, double ev_rtol, int explicit_check, int* state, int* active,
-              int* skip, const unsigned* bar, JdStatus* status, double* segw, cudaStream_t s);
+              int k, const int* kseg, int b, int nrv, double ev_rtol, double theta_rel, int explicit_check,
+              int* state, int* active, int* skip, const unsigned* bar, JdStatus* status, double* segw,
+              cudaStream_t s);
+// Residual threshold of a pair with Ritz value theta: tol_abs, or under the
+// relative-residual test max(theta_rel |theta|, tol_abs).
+__host__ __device__ inline double pair_threshold(double tol_abs, double theta_rel, double theta) {
+  return theta_rel > 0.0 ? fmax(theta_rel * fabs(theta), tol_abs) : tol_abs;
+}
 // Pair j's Ritz value is within ev_rtol * max(|theta_j|, tol_abs) of an
 // eigenvalue by the Kato-Temple bound r^2 / delta, delta from the other
 // Ritz values th[0:nrv] (always true for ev_rtol <= 0).

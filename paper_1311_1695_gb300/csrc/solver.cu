@@ -199,6 +199,7 @@ struct JD {
   bool explicit_h = std::is_same<TV, double>::value;
   int injections = 0;
   double ev_rtol = 0.0;  // eigenvalue-accuracy test of an explicit check (0: off)
+  double theta_rel = 0.0;  // > 0: relative-residual stop test (pair_threshold)
   int* kseg_d = nullptr;  // per-graph wanted pairs (device [S]; null: z.k for all)
   int nrv = 0;           // Ritz values of the last Rayleigh-Ritz (theta[0:nrv])
   PcgWork* pw = nullptr;
@@ -364,7 +365,7 @@ struct JD {
     nrv = m;
     residual<TV>(g, red, V, z.ldv, W, z.ldv, theta, z.mmax, Rv, z.ldb, z.b, rn2, 64, seg_skip, st);
     converge(z.nseg, rn2, theta, z.mmax, G->d_norm1, tol_d, z.k, kseg_d, z.b, m, explicit_check ? ev_rtol : 0.0,
-             explicit_check ? 1 : 0, state, active, seg_skip, pw->bar, status_d, segw, st);
+             theta_rel, explicit_check ? 1 : 0, state, active, seg_skip, pw->bar, status_d, segw, st);
     cudaMemcpyAsync(status_h, status_d, sizeof(JdStatus), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(state_h, state, sizeof(int) * z.nseg, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(segw_h, segw, sizeof(double) * z.nseg, cudaMemcpyDeviceToHost, st);
@@ -432,6 +433,8 @@ struct JD {
 struct Params {
   int k, b, mk, itmax, max_outer, verbose;
   double tol, delta, max_seconds, ev_rtol;
+  double theta_rel = 0.0;  // relative-residual test: tol, else 0
+  double tol_floor = 0.0;  // the ||L||_1-relative threshold (tol, or a floor under the relative test)
   std::vector<int> kseg;  // pairs wanted per graph (<= k)
   std::chrono::steady_clock::time_point t0;
 };
@@ -501,8 +504,8 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
           for (int j = 0; j < P.kseg[s]; ++j) {
             const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
             const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
-            const bool c = r <= tol_abs[s] && th[j] <= jd.G->norm1[s] &&
-                           ev_accurate_host(th, jd.nrv, j, r, tol_abs[s], jd.ev_rtol);
+            const double thr = pair_threshold(tol_abs[s], jd.theta_rel, th[j]);
+            const bool c = r <= thr && th[j] <= jd.G->norm1[s] && ev_accurate_host(th, jd.nrv, j, r, thr, jd.ev_rtol);
             segc = segc && c;
             act[(size_t)s * 64 + j] = c ? 0 : 1;
           }
@@ -637,8 +640,9 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
       const double r = ra / G->norm1[s];
       const bool real = th[j] <= G->norm1[s];
       worst = std::max(worst, real ? r : 1.0);
-      const bool acc = ev_accurate_host(th, jd.nrv, j, ra, P.tol * G->norm1[s], P.ev_rtol);
-      if (prefix && real && r <= P.tol && acc) ++nconv; else prefix = false;
+      const double thr = pair_threshold(P.tol_floor * G->norm1[s], P.theta_rel, th[j]);
+      const bool acc = ev_accurate_host(th, jd.nrv, j, ra, thr, P.ev_rtol);
+      if (prefix && real && ra <= thr && acc) ++nconv; else prefix = false;
     }
     in.n_converged = nconv;
     // per graph: a batch member whose k pairs all meet the test is converged
@@ -684,7 +688,13 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   // converge; they keep a cluster that straddles k from being missed)
   P.b = o.block > 0 ? std::max(o.block, k) : std::min(k + 2, 32);
   if (P.b > 32) { set_error("JD block width must be <= 32"); return LAP_EINVAL; }
-  P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b) : P.b + 2;
+  // default restart size: at least 20 kept Ritz vectors (measured on the
+  // power-law workloads: fewer outer iterations, and no stalls on clusters
+  // of close eigenvalues, for a little more orthogonalisation per iteration),
+  // at least b + 2, at most what the smallest graph of the handle allows
+  int ns_min = 1 << 30;
+  for (int s = 0; s < G->hg.nseg; ++s) ns_min = std::min(ns_min, G->row0[s + 1] - G->row0[s]);
+  P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b) : std::max(P.b + 2, std::min(20, ns_min - 1 - P.b));
   P.mk = std::min(P.mk, 64 - P.b);
   P.itmax = o.inner_maxit > 0 ? o.inner_maxit : 20;
   P.delta = o.inner_tol > 0 ? o.inner_tol : 1e-2;
@@ -693,6 +703,10 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   P.max_seconds = o.max_seconds;
   P.verbose = o.verbose;
   P.ev_rtol = o.ev_rtol > 0.0 ? o.ev_rtol : (o.ev_rtol < 0.0 ? 0.0 : 1e-7);
+  // relative-residual test (Section 4): threshold tol theta_j, above a floor
+  // of FP64 rounding in L x
+  P.theta_rel = o.tol_mode == LAP_TOL_THETA ? tol : 0.0;
+  P.tol_floor = o.tol_mode == LAP_TOL_THETA ? 64.0 * 0x1p-53 : tol;
   const int S = G->hg.nseg;
   for (int s = 0; s < S; ++s) {
     const int ns = G->row0[s + 1] - G->row0[s];
@@ -703,7 +717,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   z.ldv = round_up(z.mmax, 4); z.ldb = round_up(z.b, 4);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(o.stream);
   std::vector<double> tol_abs(S);
-  for (int s = 0; s < S; ++s) tol_abs[s] = tol * G->norm1[s];
+  for (int s = 0; s < S; ++s) tol_abs[s] = P.tol_floor * G->norm1[s];
 
   Arena outa;
   int rc = outa.init(sizeof(double) * (size_t)z.n * k + 2 * sizeof(unsigned long long) * (size_t)S * k + sizeof(int) * S + 256 +
@@ -757,6 +771,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     jd.pw = &pw;
     jd.kseg_d = kseg_d;
     jd.ev_rtol = P.ev_rtol;
+    jd.theta_rel = P.theta_rel;
     int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
     const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30, o.cuda_graph >= 0);
@@ -773,9 +788,10 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   j1.carve(a1);
   j1.pw = &pw;
   j1.kseg_d = kseg_d;
+  j1.theta_rel = P.theta_rel;
   int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
   std::vector<double> tol1(S);
-  for (int s = 0; s < S; ++s) tol1[s] = std::max(tol, 2e-6) * G->norm1[s];
+  for (int s = 0; s < S; ++s) tol1[s] = std::max(P.tol_floor, 2e-6) * G->norm1[s];
   int m_out = m;
   Params P1 = P;
   int st1 = iterate(j1, m, P1, tol1, false, outer, m_out, 1e-10, 8, o.cuda_graph >= 0);
@@ -790,6 +806,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   j2.pw = &pw;
   j2.kseg_d = kseg_d;
   j2.ev_rtol = P.ev_rtol;
+  j2.theta_rel = P.theta_rel;
   const int mk = std::min(m_out, z.mk);
   convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);
   j2.n_matvec = j1.n_matvec;

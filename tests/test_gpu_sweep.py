@@ -1,0 +1,98 @@
+"""The paper's experiment grid (Section 4): the relative-residual exit test
+||L u - theta u|| <= delta theta, the three solvers at N_eig up to 50, and the
+sweep driver, checked against the oracle's dense definition."""
+import numpy as np
+import pytest
+
+import graphgen as G
+from oracle.laplacian import Laplacian
+from parity import all_pairs, check_eigpairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_1311_1695_gb300 as p
+    from paper_1311_1695_gb300 import build
+    build.build()
+    return p
+
+
+@pytest.fixture(scope="module")
+def c1():
+    g = G.workload_graph("c1")
+    return g, all_pairs(g)
+
+
+def _relative_residuals(g, ev, V):
+    lap = Laplacian(g)
+    R = lap.matvec(V) - V * ev[None, :]
+    return np.linalg.norm(R, axis=0) / np.abs(ev)
+
+
+@pytest.mark.parametrize("method,precision", [("jd", "fp64"), ("jd", "mixed"), ("dacg", "fp64"), ("irlm", "fp64")])
+@pytest.mark.parametrize("delta", [1e-3, 1e-6])
+def test_relative_residual_exit_test(pkg, c1, method, precision, delta):
+    """tol_mode="theta": every returned pair meets ||r_j|| <= delta theta_j,
+    recomputed here in FP64, and its eigenvalue is the definition's within
+    the residual's bound (Kato-Temple: r^2 / gap, with the smallest gap to
+    another eigenvalue, or r itself for a clustered value)."""
+    g, (ev_ref, V_ref) = c1
+    k = 5
+    ev, V, info = pkg.lap_eigs(g, k, tol=delta, method=method, precision=precision, tol_mode="theta")
+    assert info["status"] == 0, info
+    rel = _relative_residuals(g, ev, V)
+    assert rel.max() <= delta * (1 + 1e-6), rel
+    r = rel * np.abs(ev)
+    gaps = np.array([np.min(np.abs(np.delete(ev_ref, i) - ev_ref[i])) for i in range(k)])
+    bound = np.minimum(r, r * r / np.maximum(gaps - r, 1e-300)) + 1e-12 * np.abs(ev_ref[:k])
+    assert np.all(np.abs(ev - ev_ref[:k]) <= bound), (ev - ev_ref[:k], bound)
+    if delta == 1e-6:  # tight enough for the full parity check
+        check_eigpairs(g, ev, V, ev_ref, V_ref, tol=delta * ev.max() / Laplacian(g).norm1, k=k)
+
+
+def test_relative_test_is_stricter_for_small_eigenvalues(pkg, c1):
+    """On a graph whose ||L||_1 is large against lambda_2, the relative test at
+    the same tol needs more work than the ||L||_1-relative one."""
+    g, _ = c1
+    _, _, a = pkg.lap_eigs(g, 5, tol=1e-6, method="jd", tol_mode="norm1")
+    _, _, b = pkg.lap_eigs(g, 5, tol=1e-6, method="jd", tol_mode="theta")
+    assert a["status"] == 0 and b["status"] == 0
+    assert b["n_matvec"] > a["n_matvec"]
+
+
+@pytest.mark.parametrize("method", ["dacg", "irlm"])
+def test_fifty_pairs(pkg, c1, method):
+    """N_eig = 50, the paper's largest, with DACG and IRLM (ncv capped at 63)
+    against the dense definition."""
+    g, (ev_ref, V_ref) = c1
+    ev, V, info = pkg.lap_eigs(g, 50, tol=1e-8, method=method)
+    assert info["status"] == 0, info
+    check_eigpairs(g, ev, V, ev_ref, V_ref, k=50)
+
+
+def test_thirty_pairs_jd(pkg, c1):
+    """JD at its largest block (b = 32): 30 pairs against the definition."""
+    g, (ev_ref, V_ref) = c1
+    for precision in ("fp64", "mixed"):
+        ev, V, info = pkg.lap_eigs(g, 30, tol=1e-8, method="jd", precision=precision)
+        assert info["status"] == 0, (precision, info)
+        check_eigpairs(g, ev, V, ev_ref, V_ref, k=30)
+
+
+def test_sweep_records(pkg, c1):
+    """The sweep driver on the protein-sized graph: one record per cell, JD
+    beyond its block reported as not run, every run meeting its exit test."""
+    from paper_1311_1695_gb300 import sweep
+    g, (ev_ref, _) = c1
+    H = pkg.Graph([g])
+    recs = [sweep.run_one(H, k, 1e-3, m, warmup=False) for k in (1, 5) for m in sweep.METHODS]
+    recs.append(sweep.run_one(H, 50, 1e-3, "jd", warmup=False))
+    assert "skipped" in recs[-1]
+    for r in recs[:-1]:
+        assert r["status"] == 0, r
+        assert r["mvp"] > 0 and r["seconds"] > 0
+        assert abs(r["lambda_2"] - ev_ref[0]) <= 1e-3 * ev_ref[0]
+    txt = sweep.table(recs)
+    assert txt.count("\n") == 4  # header, rule, rows for N_eig 1, 5 and 50 at delta 1e-3
