@@ -72,8 +72,8 @@ typedef enum {
 typedef struct {
   uint32_t struct_size;
   int block;          /* JD block width b >= k (default min(k + 2, 32), at most 32) */
-  int m_keep;         /* JD: Ritz vectors kept at each restart (default max(b + 2, 20),
-                         less on graphs too small for it);
+  int m_keep;         /* JD: Ritz vectors kept at each restart (default max(b + 2, 20)
+                         rounded up to a multiple of 4, less on graphs too small for it);
                          the paper's m_min (Section 3.2, Section 4) */
   int inner_maxit;    /* correction-solve PCG steps, ITMAX (default 20, Section 4) */
   double inner_tol;   /* relative PCG residual drop delta_PCG (default 1e-2, Section 4) */

@@ -691,10 +691,13 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   // default restart size: at least 20 kept Ritz vectors (measured on the
   // power-law workloads: fewer outer iterations, and no stalls on clusters
   // of close eigenvalues, for a little more orthogonalisation per iteration),
-  // at least b + 2, at most what the smallest graph of the handle allows
+  // at least b + 2, a multiple of 4 (the new block then starts on a 16-byte
+  // boundary of every row, which the vectorised SpMM needs), at most what the
+  // smallest graph of the handle allows
   int ns_min = 1 << 30;
   for (int s = 0; s < G->hg.nseg; ++s) ns_min = std::min(ns_min, G->row0[s + 1] - G->row0[s]);
-  P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b) : std::max(P.b + 2, std::min(20, ns_min - 1 - P.b));
+  P.mk = o.m_keep > 0 ? std::max(o.m_keep, P.b)
+                      : std::max(P.b + 2, std::min(round_up(std::max(P.b + 2, 20), 4), ns_min - 1 - P.b));
   P.mk = std::min(P.mk, 64 - P.b);
   P.itmax = o.inner_maxit > 0 ? o.inner_maxit : 20;
   P.delta = o.inner_tol > 0 ? o.inner_tol : 1e-2;
