@@ -114,6 +114,13 @@ typedef struct {
                          ||r||^2 / delta (delta = distance to the nearest other
                          Ritz value farther than ||r||); 0 = 1e-7, < 0 = off */
   int tol_mode;       /* lap_tol_mode (default LAP_TOL_NORM1) */
+  int use_gnn;        /* 1: JD on one graph starts from the learned warm start
+                         (lap_gnn_warm_start with gnn_params, gnn_k and seed);
+                         without parameters, with x0/x0_dev set, for another
+                         method or a batch, or when the forward pass fails:
+                         the seeded random start */
+  int gnn_k;          /* columns of the network's output (1..32) */
+  const double* gnn_params; /* host, lap_gnn_param_count(gnn_k) values */
 } lap_opts;
 
 typedef struct {
@@ -250,6 +257,36 @@ int lap_gnn_aggregate(lap_graph* g, int transpose, const float* X, int ldx, floa
 int lap_gnn_tanh(lap_graph* g, int mode, float* Z, int ldz, const float* H, int ldh, int w, void* stream);
 int lap_block_update(lap_graph* g, int dtype, void* Y, int ldy, int q, double beta, double alpha, const void* A,
                      int lda, int p, int ones, const double* S, int lds, int64_t ss, void* stream);
+
+/* The learned warm start (no counterpart in the paper): the network's
+ * forward pass on graph handle g, X = C H_3 W_out (device FP64, row-major
+ * n x kg, row stride ldx >= kg), C removing each graph's column means.
+ * Network: H_0 = 16 seeded node features (lap_gnn_features_bf16),
+ * H_{l+1} = tanh([M^4 H_l | H_l] [W_l; U_l] + b_l) for l = 0, 1, 2 (width 32,
+ * M = D^{-1} A), every parameter rounded to BF16, activations BF16, FP32
+ * accumulation.  params (host FP64, nparams = lap_gnn_param_count(kg)
+ * values): per layer W_l (f_l x 32 row-major), U_l (f_l x 32), b_l (32),
+ * f_0 = 16, f_1 = f_2 = 32; then W_out (32 x kg).  Synchronises `stream`.
+ * Errors: LAP_EINVAL (sizes), LAP_ENOMEM, LAP_ECUDA. */
+int lap_gnn_warm_start(lap_graph* g, const double* params, int64_t nparams, int kg, uint64_t seed, double* X,
+                       int ldx, void* stream);
+int64_t lap_gnn_param_count(int kg);
+
+/* Training steps of the network that are not row products (device, FP64):
+ *   lap_gnn_loss : per graph s (one CTA each), from P_s = U^T X and
+ *                  Q_s = X^T X (k x k row-major, [nseg] consecutive), the
+ *                  subspace loss 1 - tr(G^{-1} P^T P)/k with the ridge
+ *                  G = Q + eps tr(Q)/k I into loss[s], and S_s (2k x k):
+ *                  dX = U S_u + X S_x is the loss's gradient averaged over
+ *                  the nseg graphs (S_u = -(2/k) P G^{-1} / nseg,
+ *                  S_x = (2/k)(A + (eps/k) tr(A) I) / nseg, A = G^{-1} P^T P G^{-1}).
+ *                  k <= 32.
+ *   lap_adam_step: Adam (bias-corrected first and second moments) on a flat
+ *                  vector of n parameters p with gradient g and moments m, v
+ *                  (device FP64), step number t >= 1. */
+int lap_gnn_loss(int nseg, int k, double eps, const double* P, const double* Q, double* loss, double* S, void* stream);
+int lap_adam_step(int64_t n, double* p, const double* g, double* m, double* v, int t, double lr, double b1, double b2,
+                  double eps, void* stream);
 
 /* BF16 forms of the network's kernels (tensor cores; storage BF16, products
  * accumulated in FP32).  Blocks are row-major over all rows of the handle;

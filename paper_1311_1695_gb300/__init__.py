@@ -68,6 +68,9 @@ class lap_opts(ctypes.Structure):
         ("precond_alpha", ctypes.c_double),
         ("ev_rtol", ctypes.c_double),
         ("tol_mode", ctypes.c_int),
+        ("use_gnn", ctypes.c_int),
+        ("gnn_k", ctypes.c_int),
+        ("gnn_params", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -134,6 +137,10 @@ _SIGNATURES = {
     "lap_gnn_dense_bf16": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _I, _P]),
     "lap_gnn_wgrad_bf16": (_I, [_P, _I, _P, _I, _P, _I, _P, _P]),
     "lap_gnn_tanh_back_bf16": (_I, [_P, _P, _I, _P, _I, _I, _P]),
+    "lap_gnn_warm_start": (_I, [_P, _PD, ctypes.c_int64, _I, ctypes.c_uint64, _P, _I, _P]),
+    "lap_gnn_param_count": (ctypes.c_int64, [_I]),
+    "lap_gnn_loss": (_I, [_I, _I, _D, _P, _P, _P, _P, _P]),
+    "lap_adam_step": (_I, [ctypes.c_int64, _P, _P, _P, _P, _I, _D, _D, _D, _D, _P]),
     "lap_graph_autotune": (_I, [_P, _I, _I, _PI, _PI, _P]),
     "lap_project": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _P]),
     "lap_cgs2": (_I, [_P, _I, _P, _I, _I, _P, _I, _I, _PI, _P]),
@@ -191,7 +198,7 @@ def _ptr(a, ct):
 def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000, ncv=0, precision="fp64",
               include_null=False, seed=0x5EED, x0=None, stream=None, max_seconds=0.0, team=0, verbose=False,
               x0_dev=None, cuda_graph=True, device_timeout_ms=0.0, max_ctas=0, ev_rtol=0.0, precond="jacobi",
-              precond_alpha=0.0, tol_mode="norm1"):
+              precond_alpha=0.0, tol_mode="norm1", use_gnn=False, gnn_params=None):
     o = lap_opts()
     lib().lap_opts_default(ctypes.byref(o))
     o.block, o.m_keep, o.inner_maxit, o.inner_tol = block, m_keep, inner_maxit, inner_tol
@@ -215,6 +222,16 @@ def make_opts(block=0, m_keep=0, inner_maxit=20, inner_tol=1e-2, max_outer=1000,
         keep = np.asfortranarray(x0, dtype=np.float64)
         o.x0 = keep.ctypes.data_as(_PD)
         o.k0 = keep.shape[1]
+    if use_gnn:
+        # the network's parameters, flattened in their order (gnn.param_shapes);
+        # default: the trained weights shipped with the package
+        if gnn_params is None:
+            from . import gnn as _gnn
+            gnn_params, _ = _gnn.load_params()
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in gnn_params]))
+        o.use_gnn, o.gnn_k = 1, int(np.asarray(gnn_params[-1]).shape[1])
+        o.gnn_params = flat.ctypes.data_as(_PD)
+        keep = (keep, flat)
     return o, keep
 
 

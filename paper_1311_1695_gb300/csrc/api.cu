@@ -69,6 +69,33 @@ void add_null(SolveOut& out, const std::vector<int>& nrows, const std::vector<in
 
 // opts.precond: set the handle's preconditioner when the solve asks for
 // one it does not have
+// The learned start (lap_opts.use_gnn): for a JD solve of one graph without
+// a start block of the caller's, the network's proposal (gnn_infer.cu)
+// becomes the start block; without parameters, or when the forward pass
+// fails, the solve starts from the seeded random block as usual.
+struct GnnStart {
+  double* x0 = nullptr;
+  ~GnnStart() { cudaFree(x0); }
+};
+void apply_gnn(lap_graph* g, lap_opts& o, int method, GnnStart& gs) {
+  if (!o.use_gnn || method != LAP_JD || g->hg.nseg != 1 || !o.gnn_params || o.gnn_k < 1 || o.gnn_k > 32 || o.x0 ||
+      o.x0_dev)
+    return;
+  if (cudaMalloc(&gs.x0, sizeof(double) * (size_t)g->hg.n * o.gnn_k) != cudaSuccess) {
+    cudaGetLastError();
+    gs.x0 = nullptr;
+    return;
+  }
+  if (gnn_warm_start(g, o.gnn_params, o.gnn_k, o.seed, gs.x0, o.gnn_k, reinterpret_cast<cudaStream_t>(o.stream)) !=
+      LAP_OK) {
+    cudaGetLastError();
+    return;
+  }
+  o.x0_dev = gs.x0;
+  o.ldx0 = o.gnn_k;
+  o.k0 = o.gnn_k;
+}
+
 int apply_precond(lap_graph* g, const lap_opts& o) {
   if (o.precond == 0 || g->dg.precond == o.precond) return LAP_OK;
   return graph_set_precond(g, o.precond, o.precond_alpha);
@@ -159,6 +186,8 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
   }
   rc = apply_precond(g, o);
   if (rc) { graph_free(g); return rc; }
+  GnnStart gs;
+  apply_gnn(g, o, method, gs);
   SolveOut out;
   rc = solve_jd(g, kmax, tol, o, want, out, kk.data());
   graph_free(g);
@@ -205,6 +234,8 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   }
   rc = apply_precond(g, o);
   if (rc) { graph_free(g); return rc; }
+  GnnStart gs;
+  apply_gnn(g, o, method, gs);
   SolveOut out;
   rc = solve(g, kk, tol, method, o, evecs != nullptr, out);
   graph_free(g);
@@ -247,6 +278,8 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
     const int rc = apply_precond(g, o);
     if (rc) return rc;
   }
+  GnnStart gs;
+  apply_gnn(g, o, method, gs);
   SolveOut out;
   out.dev_vecs = evecs_dev;
   int rc = solve(g, kk, tol, method, o, evecs_dev != nullptr, out);

@@ -115,6 +115,11 @@ unsigned long long timeout_ns_of(double opts_ms, double handle_ms);
 // Ensure the handle's step-level scratch holds at least `bytes` (device).
 int graph_scratch(lap_graph* g, size_t bytes, size_t small_bytes);
 
+// The warm-start network's forward pass on graph handle g (gnn_infer.cu):
+// X (device FP64, row-major n x kg, row stride ldx) from the parameter vector.
+int gnn_warm_start(lap_graph* g, const double* params, int kg, uint64_t seed, double* X, int ldx, cudaStream_t s);
+int64_t gnn_param_count(int kg);
+
 // Error string of the last failure on this thread.
 void set_error(const std::string& msg);
 

@@ -54,6 +54,34 @@ template <typename T>
 int ortho_fused(const DevGraph& g, T* V, int ldv, int m0, int q, double drop1, double* acc, int* keep,
                 const int* seg_skip, const GridBar& bar, cudaStream_t s, int max_ctas);
 
+// The same orthonormalisation as streaming sweeps for large graphs
+// (ortho_ts.cu): working storage per graph, accumulators zero at rest.
+struct OrthoTs {
+  double* acc; int64_t sacc;  // accumulators, sacc >= 66 * 32 doubles per graph
+  double* R; int64_t sr;      // q x q coefficients per graph
+  double* G; int64_t sg;      // (m0 + 1) x q coefficients per graph
+  double* S; int64_t ss;      // q x q Gram matrix per graph
+  int* keep1;                 // [nseg * 64] columns kept by pass 1 (then by both)
+  int* keep2;                 // [nseg * 64] columns kept by pass 2
+  const int* seg_skip;
+  GridBar bar;                // error flag and limit of the copy waits
+  int max_ctas;
+};
+// V (row stride ldv) 16-byte aligned with 16-byte-multiple rows, q <= 32, m0 + q <= 64.
+template <typename T>
+bool ortho_ts_ok(const void* V, int ldv, int m0, int q);
+// CGS2 + Cholesky-QR of V[:, m0 : m0+q] against [e, V[:, 0:m0]] in the
+// basis precision; keep1 = the columns both passes kept.  Returns 0, 1 (the
+// shapes do not allow it: nothing launched) or -1 (launch failure).
+template <typename T>
+int ortho_ts(const DevGraph& g, const OrthoTs& w, T* V, int ldv, int m0, int q, double drop1, cudaStream_t s);
+// The mixed-precision form: the correction block Tt (FP32, row stride ldt)
+// against V32 = V[:, 0:m0] in FP32 (row stride ld32) in FP32, then into
+// V[:, m0 : m0+q] (FP64) and one FP64 pass.  Tt is overwritten.
+int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int m0, int q, const float* V32,
+                   int ld32, float* Tt, int ldt, double drop1, cudaStream_t s);
+constexpr int kOrthoTsAcc = 66 * 32;
+
 // Launch the whole correction solve (the per-phase form for graphs of at
 // least split_rows rows when its shapes allow, else the persistent one);
 // returns 0 or -1 (launch failure).

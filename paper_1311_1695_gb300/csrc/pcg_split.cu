@@ -34,6 +34,7 @@
 #include "internal.h"
 #include "pcg_parts.cuh"
 #include "prof.h"
+#include "stage.cuh"
 
 namespace lapeig {
 
@@ -42,72 +43,12 @@ namespace {
 using namespace pcgp;
 
 // ---------------------------------------------------------------- bulk copies
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// The issuing thread arrives on the barrier announcing `bytes` of copies.
-__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// One bulk copy global -> shared of `bytes` (a multiple of 16; both
-// addresses 16-byte aligned), completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-// The same with an L2 hint: evict-first for streamed blocks (each row is
-// used once per phase), so the gathered block stays in L2.
-__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
-                                                unsigned long long policy) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
-      : "memory");
-}
-
-__device__ __forceinline__ unsigned long long evict_first_policy() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for phase `parity` of the barrier, at most timeout_ns.  On time-out
-// the grid's error flag is raised and the wait is retried once more (the
-// copies still target this CTA's shared memory); returns false.
-__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, const GridBar& gb) {
-  const unsigned long long t0 = global_ns();
-  while (!mbar_test(bar, parity)) {
-    if (global_ns() - t0 > gb.timeout_ns) {
-      atomicExch(gb.err, 1);
-      const unsigned long long t1 = global_ns();
-      while (!mbar_test(bar, parity) && global_ns() - t1 < gb.timeout_ns) {
-      }
-      return false;
-    }
-  }
-  return true;
-}
+using stg::bulk_g2s;
+using stg::bulk_g2s_stream;
+using stg::evict_first_policy;
+using stg::mbar_expect;
+using stg::mbar_init;
+using stg::mbar_wait;
 
 // The launch-time view of a split solve: the persistent form's view plus
 // the stop flag, the packed X and the block receiving L z~.
@@ -129,19 +70,25 @@ __global__ void k_pack_x(int n, const T* __restrict__ X, int ldx, T* __restrict_
   }
 }
 
+// Rows of one staged unit: each row tile is walked in units of at most
+// kChunk rows, double-buffered (the copies of the next unit are in flight
+// while the current one is computed), so two buffers take the shared memory
+// one whole tile took.
+constexpr int kChunk = kTileRows / 2;
+
 // Shared-memory layout of one split kernel (every region 16-byte aligned):
-// red (flushes and staged totals), nstage staged blocks of kTileRows x ld,
-// the tile's degrees, then the mbarrier.
+// red (flushes and staged totals), two buffers of nstage staged blocks of
+// kChunk x ld, the two units' degrees, then the two mbarriers.
 template <typename T, int BMAX, int BWL>
 struct SplitSmem {
   static constexpr int red = (kWarps * (BMAX + 3) * BWL > (BMAX + 1) * BMAX + 2 * BMAX)
                                  ? kWarps * (BMAX + 3) * BWL
                                  : (BMAX + 1) * BMAX + 2 * BMAX;
   static constexpr int red_al = (red + 3) / 4 * 4;
-  static size_t bytes(int nstage, int ld) {
-    const size_t t = sizeof(T) * ((size_t)red_al + (size_t)nstage * kTileRows * ld + kTileRows);
-    return (t + 15) / 16 * 16 + 16;
+  __host__ __device__ static size_t body(int nstage, int ld) {
+    return sizeof(T) * ((size_t)red_al + 2 * (size_t)nstage * kChunk * ld + 2 * kChunk);
   }
+  __host__ __device__ static size_t bytes(int nstage, int ld) { return (body(nstage, ld) + 15) / 16 * 16 + 32; }
 };
 
 // Row helpers over a staged row of stride ld (a multiple of the vector
@@ -203,59 +150,135 @@ __device__ __forceinline__ T dot_ld(const T* __restrict__ r, const T (&Gc)[BMAX 
   return s;
 }
 
-// Per-CTA context of a split kernel: its shared-memory regions and the
-// mbarrier of its bulk copies (phase bit flips at every completed wait).
+// Per-CTA context of a split kernel: its shared-memory regions and the two
+// mbarriers of its bulk copies (buffer u's phase bit flips at every
+// completed wait on it).
 template <typename T, int BMAX, int BWL>
 struct Ctx {
   T* red;
-  T* stage;      // nstage blocks of kTileRows x ld (block i at stage + i * kTileRows * ld)
-  T* s_deg;      // [kTileRows] the tile's degrees
-  unsigned long long* bar;
-  unsigned phase;
+  T* stage;      // 2 buffers x nst blocks of kChunk x ld
+  T* s_deg;      // 2 x kChunk reciprocal degrees
+  unsigned long long* bar;  // [2]
+  unsigned phase;           // bit u: the phase to wait for on buffer u
+  int nst;
   unsigned long long policy;  // evict-first
   __device__ void setup(unsigned char* smem, int nstage, int ld) {
     using L = SplitSmem<T, BMAX, BWL>;
+    nst = nstage;
     red = reinterpret_cast<T*>(smem);
     stage = red + L::red_al;
-    s_deg = stage + (size_t)nstage * kTileRows * ld;
-    const size_t tb = sizeof(T) * ((size_t)L::red_al + (size_t)nstage * kTileRows * ld + kTileRows);
-    bar = reinterpret_cast<unsigned long long*>(smem + (tb + 15) / 16 * 16);
+    s_deg = stage + 2 * (size_t)nstage * kChunk * ld;
+    bar = reinterpret_cast<unsigned long long*>(smem + (L::body(nstage, ld) + 15) / 16 * 16);
     phase = 0;
     policy = evict_first_policy();
-    if (threadIdx.x == 0) mbar_init(bar);
+    if (threadIdx.x == 0) {
+      mbar_init(bar);
+      mbar_init(bar + 1);
+    }
     __syncthreads();
   }
-  __device__ T* blk(int i, int ld) { return stage + (size_t)i * kTileRows * ld; }
-  // thread 0: copy rows [r0, r1) of the nb blocks src[i] (row stride ldb[i])
-  // into staged block i (blocks whose bit is set in keep are copied without
-  // the evict-first hint)
+  __device__ T* blk(int u, int i, int ld) { return stage + ((size_t)u * nst + i) * kChunk * ld; }
+  __device__ const T* deg(int u) const { return s_deg + u * kChunk; }
+  // thread 0: copy rows [r0, r1) (at most kChunk) of the nb blocks src[i]
+  // (row stride ldb[i]) into block i of buffer u (blocks whose bit is set in
+  // keep are copied without the evict-first hint)
   template <int NB>
-  __device__ void issue(const T* const (&src)[NB], const int (&ldb)[NB], int ld, int r0, int r1, unsigned keep = 0) {
+  __device__ void issue(int u, const T* const (&src)[NB], const int (&ldb)[NB], int ld, int r0, int r1,
+                        unsigned keep) {
     if (threadIdx.x != 0) return;
     unsigned total = 0;
 #pragma unroll
     for (int i = 0; i < NB; ++i) total += (unsigned)(sizeof(T) * (size_t)(r1 - r0) * ldb[i]);
-    mbar_expect(bar, total);
+    mbar_expect(bar + u, total);
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const unsigned bytes = (unsigned)(sizeof(T) * (size_t)(r1 - r0) * ldb[i]);
-      if (keep & (1u << i)) bulk_g2s(blk(i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar);
-      else bulk_g2s_stream(blk(i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar, policy);
+      if (keep & (1u << i)) bulk_g2s(blk(u, i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar + u);
+      else bulk_g2s_stream(blk(u, i, ld), src[i] + (size_t)r0 * ldb[i], bytes, bar + u, policy);
     }
   }
-  // every thread: wait for the last issue; false when the wait ran out
-  __device__ bool wait(const GridBar& gb) {
+  // every thread: wait for the copies into buffer u; false when the wait ran out
+  __device__ bool wait(int u, const GridBar& gb) {
     __shared__ int s_ok;
-    if (threadIdx.x == 0) s_ok = mbar_wait(bar, phase, gb) ? 1 : 0;
-    phase ^= 1u;
+    if (threadIdx.x == 0) s_ok = mbar_wait(bar + u, (phase >> u) & 1u, gb) ? 1 : 0;
+    phase ^= 1u << u;
     __syncthreads();
     return s_ok != 0;
   }
-  // the tile's degrees (read after the next wait)
-  __device__ void degrees(const Tile& t, const T* deg) {
-    for (int i = threadIdx.x; i < t.r1 - t.r0; i += kThreads) s_deg[i] = deg[t.r0 + i];
+  // the reciprocal degrees of rows [r0, r1) into buffer u's slot (read after
+  // its wait): one division per row instead of one per element of the row
+  __device__ void degrees(int u, int r0, int r1, const T* deg_g) {
+    for (int i = threadIdx.x; i < r1 - r0; i += kThreads) s_deg[u * kChunk + i] = T(1) / deg_g[r0 + i];
   }
 };
+
+// A CTA's units: its row tiles (tile blockIdx.x + j gridDim.x of the graphs
+// not skipped) in order, each cut into runs of at most kChunk rows.
+struct Unit {
+  int ti, r0, r1;
+  Tile t;
+  __device__ void load(const DevGraph& g, const int* skip) {
+    for (; ti < g.ntiles; ti += gridDim.x) {
+      t = g.tiles[ti];
+      if (!(skip && skip[t.seg])) break;
+    }
+    if (ti < g.ntiles) {
+      r0 = t.r0;
+      r1 = min(t.r1, r0 + kChunk);
+    }
+  }
+  __device__ bool valid(const DevGraph& g) const { return ti < g.ntiles; }
+  __device__ void next(const DevGraph& g, const int* skip) {
+    if (r1 < t.r1) {
+      r0 = r1;
+      r1 = min(t.r1, r0 + kChunk);
+    } else {
+      ti += gridDim.x;
+      load(g, skip);
+    }
+  }
+};
+
+// The double-buffered walk over a CTA's units: on_seg(tile) when the graph
+// changes (before its first unit is computed), body(tile, r0, nrows, u) with
+// the unit's NB blocks staged in buffer u (and its degrees when deg_g is
+// set), the next unit's copies in flight meanwhile.  Returns false when a
+// copy wait ran out (the grid's error flag is raised; the other buffer's
+// copies are waited for, with the same limit, before returning).
+template <int NB, typename T, int BMAX, int BWL, typename Seg, typename Body>
+__device__ bool walk_units(Ctx<T, BMAX, BWL>& cx, const DevGraph& g, const int* skip, const T* const (&src)[NB],
+                           const int (&ldb)[NB], int ld, unsigned keep, const T* deg_g, const GridBar& gb,
+                           Seg&& on_seg, Body&& body) {
+  Unit u;
+  u.ti = blockIdx.x;
+  u.load(g, skip);
+  if (!u.valid(g)) return true;
+  cx.template issue<NB>(0, src, ldb, ld, u.r0, u.r1, keep);
+  if (deg_g) cx.degrees(0, u.r0, u.r1, deg_g);
+  int seg = -1, buf = 0;
+  while (true) {
+    if (u.t.seg != seg) {
+      on_seg(u.t);
+      seg = u.t.seg;
+    }
+    Unit nx = u;
+    nx.next(g, skip);
+    const bool more = nx.valid(g);
+    __syncthreads();  // the body of the unit before is done with buffer buf ^ 1
+    if (more) {
+      cx.template issue<NB>(buf ^ 1, src, ldb, ld, nx.r0, nx.r1, keep);
+      if (deg_g) cx.degrees(buf ^ 1, nx.r0, nx.r1, deg_g);
+    }
+    if (!cx.wait(buf, gb)) {
+      if (more) cx.wait(buf ^ 1, gb);
+      return false;
+    }
+    body(u.t, u.r0, u.r1 - u.r0, buf);
+    if (!more) return true;
+    u = nx;
+    buf ^= 1;
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ const T* deg_of(const DevGraph& g) {
@@ -316,44 +339,38 @@ __global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T
 #pragma unroll
   for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
   int cur = -1;
-  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-    const Tile t = g.tiles[ti];
-    if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    if (t.seg != cur) {
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
-      cur = t.seg;
-    }
-    const int nrows = t.r1 - t.r0;
-    __syncthreads();  // the previous tile's readers are done with the stage
-    {
-      const T* src[1] = {sv.Xs};
-      const int lds[1] = {ld};
-      cx.issue<1>(src, lds, ld, t.r0, t.r1);
-    }
-    cx.degrees(t, deg);
-    if (!cx.wait(f.bar)) return;
-    const T* xs = cx.blk(0, ld);
-    const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
-    if (c < ld) {
-      for (int il = grp; il < nrows; il += SLOTS) {
-        const int r = t.r0 + il;
-        if (!colok) {
-          f.LX[(size_t)r * f.ldlx + c] = T(0);
-          continue;
+  const T* src[1] = {sv.Xs};
+  const int lds[1] = {ld};
+  const bool ok = walk_units<1>(
+      cx, g, f.seg_skip, src, lds, ld, 0u, deg, f.bar,
+      [&](const Tile& t) {
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
+        cur = t.seg;
+      },
+      [&](const Tile& t, int r0, int nrows, int u) {
+        const T* xs = cx.blk(u, 0, ld);
+        const T* sdinv = cx.deg(u);
+        const bool act = colok && (f.active == nullptr || f.active[(size_t)t.seg * f.bstride + c]);
+        if (c >= ld) return;
+        for (int il = grp; il < nrows; il += SLOTS) {
+          const int r = r0 + il;
+          if (!colok) {
+            f.LX[(size_t)r * f.ldlx + c] = T(0);
+            continue;
+          }
+          const size_t o = (size_t)r * ld + c;
+          const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
+          f.RES[o] = res;
+          f.Tt[o] = T(0);
+          if (fsai) continue;  // z~ = G^T G r and its Gram follow in their own launches
+          const T z = res * sdinv[il];
+          f.Z[o] = z;
+          gram_ld<T, BMAX>(acc, xs + (size_t)il * ld, z, ld);
+          ex[0] += res * z;
+          ex[1] += res * res;
         }
-        const size_t o = (size_t)r * ld + c;
-        const T res = act ? -f.R[(size_t)r * f.ldr + c] : T(0);
-        f.RES[o] = res; f.Tt[o] = T(0);
-        if (fsai) continue;  // z~ = G^T G r and its Gram follow in their own launches
-        const T z = res / cx.s_deg[il];
-        f.Z[o] = z;
-        gram_ld<T, BMAX>(acc, xs + (size_t)il * ld, z, ld);
-        ex[0] += res * z;
-        ex[1] += res * res;
-      }
-    }
-  }
-  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
+      });
+  if (ok && cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, 1, cur), b, 2, acc, ex, cx.red);
 }
 
 // ---------------------------------------------------------------- phase M
@@ -412,72 +429,69 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
   }
   int cur = -1;
   T thc = T(0), be = T(0);
-  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-    const Tile t = g.tiles[ti];
-    if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    if (t.seg != cur) {
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
-      cur = t.seg;
-      const T* tot = stage_totals(cx.red, acc2_of(f, g, prv, t.seg), nout + 2 * b);
-      thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
-      coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
-      be = T(0);
-      const T rho_new = colok ? tot[nout + c] : T(0);
-      if (it > 0 && colok) {  // beta = rho'/rho (0 for a column already done)
-        const size_t k = (size_t)t.seg * f.bstride + c;
-        const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
-        const int dn = __ldcg(f.done + (size_t)prv * ss + k);
-        be = (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
-      }
-      if (t.idx_in_seg == 0 && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
-        const size_t k = (size_t)t.seg * f.bstride + c;
-        const T rn = sqrt(tot[nout + b + c]);
-        int dn;
-        if (it == 0) {
-          const int act = f.active == nullptr || f.active[k];
-          dn = (!act || rn == T(0) || rho_new == T(0) || !isfinite(rho_new)) ? 1 : 0;
-          f.res0[k] = rn;
-        } else {
-          dn = __ldcg(f.done + (size_t)prv * ss + k);
-          if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
+  const T* src[6] = {f.Z, sv.Xs, f.LX, f.P, f.AP, sv.LZ};
+  const int lds[6] = {ld, ld, ld, ld, ld, ld};
+  const bool ok = walk_units<6>(
+      cx, g, f.seg_skip, src, lds, ld, 1u /* z~ (gathered by the next SpMM too) without the evict-first hint */,
+      static_cast<const T*>(nullptr), f.bar,
+      [&](const Tile& t) {
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
+        cur = t.seg;
+        const T* tot = stage_totals(cx.red, acc2_of(f, g, prv, t.seg), nout + 2 * b);
+        thc = colok ? (T)f.theta[(size_t)t.seg * f.sth + c] : T(0);
+        coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
+        be = T(0);
+        const T rho_new = colok ? tot[nout + c] : T(0);
+        if (it > 0 && colok) {  // beta = rho'/rho (0 for a column already done)
+          const size_t k = (size_t)t.seg * f.bstride + c;
+          const T rho = __ldcg(f.rho + (size_t)prv * ss + k);
+          const int dn = __ldcg(f.done + (size_t)prv * ss + k);
+          be = (!dn && rho != T(0) && isfinite(rho_new)) ? rho_new / rho : T(0);
         }
-        f.rho[(size_t)par * ss + k] = rho_new;
-        f.done[(size_t)par * ss + k] = dn;
-        f.resn[k] = rn;
-      }
-    }
-    const int nrows = t.r1 - t.r0;
-    __syncthreads();  // the previous tile's epilogue is done with the stage
-    {
-      const T* src[6] = {f.Z, sv.Xs, f.LX, f.P, f.AP, sv.LZ};
-      const int lds[6] = {ld, ld, ld, ld, ld, ld};
-      cx.issue<6>(src, lds, ld, t.r0, t.r1, 1u);  // z~ (gathered by the next SpMM too) without the evict-first hint
-    }
-    if (!cx.wait(f.bar)) return;
-    if (colok) {
-      const T* sz = cx.blk(0, ld);
-      const T* sx = cx.blk(1, ld);
-      const T* slx = cx.blk(2, ld);
-      const T* sp = cx.blk(3, ld);
-      const T* sq = cx.blk(4, ld);
-      const T* slz = cx.blk(5, ld);
-      for (int il = grp; il < nrows; il += SLOTS) {
-        const int r = t.r0 + il;
-        const size_t so = (size_t)il * ld;
-        const T pz = project_ld<T, BMAX>(sz[so + c], sx + so, Gc, ld);
-        const T sl = dot_ld<T, BMAX>(slx + so, Gc, ld);
-        T q = slz[so + c] - sl - thc * pz;
-        T p = pz;
-        if (be != T(0)) { q += be * sq[so + c]; p += be * sp[so + c]; }
-        const size_t o = (size_t)r * ld + c;
-        __stcs(f.P + o, p);
-        __stcs(f.AP + o, q);
-        gram_ld<T, BMAX>(acc, sx + so, q, ld);
-        ex[0] += p * q;
-      }
-    }
-  }
-  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
+        if (t.idx_in_seg == 0 && threadIdx.x < BWL && colok) {  // the graph's persistent scalars, parity par
+          const size_t k = (size_t)t.seg * f.bstride + c;
+          const T rn = sqrt(tot[nout + b + c]);
+          int dn;
+          if (it == 0) {
+            const int act = f.active == nullptr || f.active[k];
+            dn = (!act || rn == T(0) || rho_new == T(0) || !isfinite(rho_new)) ? 1 : 0;
+            f.res0[k] = rn;
+          } else {
+            dn = __ldcg(f.done + (size_t)prv * ss + k);
+            if (!(rn > (T)f.delta * __ldcg(f.res0 + k)) || !isfinite(rn)) dn = 1;
+          }
+          f.rho[(size_t)par * ss + k] = rho_new;
+          f.done[(size_t)par * ss + k] = dn;
+          f.resn[k] = rn;
+        }
+      },
+      [&](const Tile&, int r0, int nrows, int u) {
+        if (!colok) return;
+        const T* sz = cx.blk(u, 0, ld);
+        const T* sx = cx.blk(u, 1, ld);
+        const T* slx = cx.blk(u, 2, ld);
+        const T* sp = cx.blk(u, 3, ld);
+        const T* sq = cx.blk(u, 4, ld);
+        const T* slz = cx.blk(u, 5, ld);
+        T* const P = f.P + (size_t)r0 * ld;
+        T* const AP = f.AP + (size_t)r0 * ld;
+        for (int il = grp; il < nrows; il += SLOTS) {
+          const int so = il * ld;
+          const T pz = project_ld<T, BMAX>(sz[so + c], sx + so, Gc, ld);
+          const T sl = dot_ld<T, BMAX>(slx + so, Gc, ld);
+          T q = slz[so + c] - sl - thc * pz;
+          T p = pz;
+          if (be != T(0)) {
+            q += be * sq[so + c];
+            p += be * sp[so + c];
+          }
+          __stcs(P + so + c, p);
+          __stcs(AP + so + c, q);
+          gram_ld<T, BMAX>(acc, sx + so, q, ld);
+          ex[0] += p * q;
+        }
+      });
+  if (ok && cur >= 0) flush_cols<T, BMAX, BWL>(acc1_of(f, g, par, cur), b, 1, acc, ex, cx.red);
 }
 
 // ---------------------------------------------------------------- phase B
@@ -485,7 +499,7 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
 // z~ = r / d; partial G2 = [1|X]^T z~, r.z~, r.r into acc2 parity `par`.
 // Staged blocks: q~, r, t, p, X rows of the tile.
 template <typename T, int BMAX, int BWL>
-__global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> sv, int it, int fsai) {
+__global__ void __launch_bounds__(kThreads, 3) k_split_b(DevGraph g, SplitView<T> sv, int it, int fsai) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   if (__ldcg(sv.stop)) return;
@@ -513,59 +527,55 @@ __global__ void __launch_bounds__(kThreads) k_split_b(DevGraph g, SplitView<T> s
   }
   int cur = -1;
   T al = T(0);
-  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-    const Tile t = g.tiles[ti];
-    if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    if (t.seg != cur) {
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
-      cur = t.seg;
-      const T* tot = stage_totals(cx.red, acc1_of(f, g, par, t.seg), nout + 2 * b);
-      coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
-      al = T(0);
-      if (colok) {
-        const size_t k = (size_t)t.seg * f.bstride + c;
-        const T pq = tot[nout + c];
-        const T rho = __ldcg(f.rho + (size_t)par * ss + k);
-        const int dn = __ldcg(f.done + (size_t)par * ss + k);
-        if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
-      }
-    }
-    const int nrows = t.r1 - t.r0;
-    __syncthreads();  // the previous tile's readers are done with the stage
-    {
-      const T* src[5] = {f.AP, f.RES, f.Tt, f.P, sv.Xs};
-      const int lds[5] = {ld, ld, ld, ld, ld};
-      cx.issue<5>(src, lds, ld, t.r0, t.r1);
-    }
-    cx.degrees(t, deg);
-    if (!cx.wait(f.bar)) return;
-    if (colok) {
-      const T* sq = cx.blk(0, ld);
-      const T* sr = cx.blk(1, ld);
-      const T* st = cx.blk(2, ld);
-      const T* sp = cx.blk(3, ld);
-      const T* sx = cx.blk(4, ld);
-      for (int il = grp; il < nrows; il += SLOTS) {
-        const int r = t.r0 + il;
-        const size_t so = (size_t)il * ld;
-        const T q = project_ld<T, BMAX>(sq[so + c], sx + so, Gc, ld);
-        const T res = sr[so + c] - al * q;
-        const size_t o = (size_t)r * ld + c;
-        __stcs(f.Tt + o, st[so + c] + al * sp[so + c]);
-        if (fsai) {  // z~ = G^T G r and its Gram follow in their own launches
-          f.RES[o] = res;
-          continue;
+  const T* src[5] = {f.AP, f.RES, f.Tt, f.P, sv.Xs};
+  const int lds[5] = {ld, ld, ld, ld, ld};
+  const bool ok = walk_units<5>(
+      cx, g, f.seg_skip, src, lds, ld, 0u, deg, f.bar,
+      [&](const Tile& t) {
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+        cur = t.seg;
+        const T* tot = stage_totals(cx.red, acc1_of(f, g, par, t.seg), nout + 2 * b);
+        coeffs<T, BMAX>(Gc, tot, b, c, colok, seg_rows(g, t.seg));
+        al = T(0);
+        if (colok) {
+          const size_t k = (size_t)t.seg * f.bstride + c;
+          const T pq = tot[nout + c];
+          const T rho = __ldcg(f.rho + (size_t)par * ss + k);
+          const int dn = __ldcg(f.done + (size_t)par * ss + k);
+          if (!dn && pq != T(0) && isfinite(pq)) al = rho / pq;
         }
-        const T z = res / cx.s_deg[il];
-        __stcs(f.RES + o, res);
-        f.Z[o] = z;  // gathered by the next SpMM: normal priority
-        gram_ld<T, BMAX>(acc, sx + so, z, ld);
-        ex[0] += res * z;
-        ex[1] += res * res;
-      }
-    }
-  }
-  if (cur >= 0 && !fsai) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+      },
+      [&](const Tile&, int r0, int nrows, int u) {
+        if (!colok) return;
+        const T* sq = cx.blk(u, 0, ld);
+        const T* sr = cx.blk(u, 1, ld);
+        const T* st = cx.blk(u, 2, ld);
+        const T* sp = cx.blk(u, 3, ld);
+        const T* sx = cx.blk(u, 4, ld);
+        const T* sdinv = cx.deg(u);
+        // the unit's rows of the outputs (row stride ld)
+        T* const Tt = f.Tt + (size_t)r0 * ld;
+        T* const RES = f.RES + (size_t)r0 * ld;
+        T* const Z = f.Z + (size_t)r0 * ld;
+        for (int il = grp; il < nrows; il += SLOTS) {
+          const int so = il * ld;
+          const T q = project_ld<T, BMAX>(sq[so + c], sx + so, Gc, ld);
+          const T res = sr[so + c] - al * q;
+          const int o = so + c;
+          __stcs(Tt + o, st[so + c] + al * sp[so + c]);
+          if (fsai) {  // z~ = G^T G r and its Gram follow in their own launches
+            RES[o] = res;
+            continue;
+          }
+          const T z = res * sdinv[il];
+          __stcs(RES + o, res);
+          Z[o] = z;  // gathered by the next SpMM: normal priority
+          gram_ld<T, BMAX>(acc, sx + so, z, ld);
+          ex[0] += res * z;
+          ex[1] += res * res;
+        }
+      });
+  if (ok && cur >= 0 && !fsai) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
 }
 
 // ---------------------------------------------------------------- the preconditioned residual's Gram
@@ -589,35 +599,28 @@ __global__ void __launch_bounds__(kThreads) k_split_g2(DevGraph g, SplitView<T> 
 #pragma unroll
   for (int i = 0; i <= BMAX; ++i) acc[i] = T(0);
   int cur = -1;
-  for (int ti = blockIdx.x; ti < g.ntiles; ti += gridDim.x) {
-    const Tile t = g.tiles[ti];
-    if (f.seg_skip && f.seg_skip[t.seg]) continue;
-    if (t.seg != cur) {
-      if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
-      cur = t.seg;
-    }
-    const int nrows = t.r1 - t.r0;
-    __syncthreads();  // the previous tile's readers are done with the stage
-    {
-      const T* src[3] = {f.Z, f.RES, sv.Xs};
-      const int lds[3] = {ld, ld, ld};
-      cx.issue<3>(src, lds, ld, t.r0, t.r1, 1u);
-    }
-    if (!cx.wait(f.bar)) return;
-    if (colok) {
-      const T* sz = cx.blk(0, ld);
-      const T* sr = cx.blk(1, ld);
-      const T* sx = cx.blk(2, ld);
-      for (int il = grp; il < nrows; il += SLOTS) {
-        const size_t so = (size_t)il * ld;
-        const T z = sz[so + c], res = sr[so + c];
-        gram_ld<T, BMAX>(acc, sx + so, z, ld);
-        ex[0] += res * z;
-        ex[1] += res * res;
-      }
-    }
-  }
-  if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+  const T* src[3] = {f.Z, f.RES, sv.Xs};
+  const int lds[3] = {ld, ld, ld};
+  const bool ok = walk_units<3>(
+      cx, g, f.seg_skip, src, lds, ld, 1u, static_cast<const T*>(nullptr), f.bar,
+      [&](const Tile& t) {
+        if (cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
+        cur = t.seg;
+      },
+      [&](const Tile&, int, int nrows, int u) {
+        if (!colok) return;
+        const T* sz = cx.blk(u, 0, ld);
+        const T* sr = cx.blk(u, 1, ld);
+        const T* sx = cx.blk(u, 2, ld);
+        for (int il = grp; il < nrows; il += SLOTS) {
+          const size_t so = (size_t)il * ld;
+          const T z = sz[so + c], res = sr[so + c];
+          gram_ld<T, BMAX>(acc, sx + so, z, ld);
+          ex[0] += res * z;
+          ex[1] += res * res;
+        }
+      });
+  if (ok && cur >= 0) flush_cols<T, BMAX, BWL>(acc2_of(f, g, par, cur), b, 2, acc, ex, cx.red);
 }
 
 // ---------------------------------------------------------------- fin

@@ -76,6 +76,12 @@ Profiler& P() {
 
 bool prof_on() { return P().on; }
 
+namespace {
+thread_local int g_prof_depth = 0;
+}
+bool prof_enter() { return g_prof_depth++ > 0; }
+void prof_exit() { --g_prof_depth; }
+
 int prof_begin(const char* name, double bytes, cudaStream_t s) {
   Profiler& p = P();
   if (p.pending.size() > 200000) p.drain();

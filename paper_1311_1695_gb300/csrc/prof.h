@@ -15,14 +15,23 @@ void prof_end(int slot, cudaStream_t s);
 // kernel whose work is known only after it ran, e.g. a solve that stops early).
 void prof_set_last_bytes(const char* name, double bytes);
 
+// Scope nesting on the calling thread: prof_enter returns true when a scope
+// is already open (the launches of a sequence timed as one are not timed
+// again on their own).
+bool prof_enter();
+void prof_exit();
+
 struct ProfScope {
   int slot;
   cudaStream_t s;
-  // name nullptr: not timed (a launch inside a sequence timed as one)
-  ProfScope(const char* name, double bytes, cudaStream_t st)
-      : slot(name && prof_on() ? prof_begin(name, bytes, st) : -1), s(st) {}
+  // name nullptr, or a scope inside another: not timed
+  ProfScope(const char* name, double bytes, cudaStream_t st) : slot(-1), s(st) {
+    const bool nested = prof_enter();
+    if (!nested && name && prof_on()) slot = prof_begin(name, bytes, st);
+  }
   ~ProfScope() {
     if (slot >= 0) prof_end(slot, s);
+    prof_exit();
   }
 };
 

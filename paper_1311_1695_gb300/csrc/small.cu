@@ -32,6 +32,48 @@ __global__ void k_h_restart(double* H, int ldh, int64_t sh, int mmax, const doub
   }
 }
 
+// One CTA per graph: T = H Y[:, 0:mk] into shared memory (H read from
+// global, m x m), then Hn = Y^T T in registers, then H <- [Hn 0; 0 0].
+__global__ void k_h_rotate(double* H, int ldh, int64_t sh, int mmax, const double* __restrict__ Y, int ldy,
+                           int64_t sy, int m, int mk, const int* seg_skip) {
+  __shared__ double T[64 * 64];
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* h = H + (size_t)s * sh;
+  const double* y = Y + (size_t)s * sy;
+  for (int e = threadIdx.x; e < m * mk; e += blockDim.x) {
+    const int i = e / mk, j = e % mk;
+    double t = 0.0;
+    for (int l = 0; l < m; ++l) t += h[(size_t)i * ldh + l] * y[(size_t)l * ldy + j];
+    T[i * 64 + j] = t;
+  }
+  __syncthreads();
+  // the upper triangle (i <= j), written to both halves: exactly symmetric
+  constexpr int PER = 64 * 64 / 256;  // outputs per thread at most (blockDim 256)
+  double out[PER];
+  int cnt = 0;
+  for (int e = threadIdx.x; e < mk * mk && cnt < PER; e += blockDim.x, ++cnt) {
+    const int i = e / mk, j = e % mk;
+    double t = 0.0;
+    if (i <= j)
+      for (int l = 0; l < m; ++l) t += y[(size_t)l * ldy + i] * T[l * 64 + j];
+    out[cnt] = t;
+  }
+  __syncthreads();  // every read of H is done
+  for (int e = threadIdx.x; e < mmax * mmax; e += blockDim.x) {
+    const int i = e / mmax, j = e % mmax;
+    if (i >= mk || j >= mk) h[(size_t)i * ldh + j] = 0.0;
+  }
+  cnt = 0;
+  for (int e = threadIdx.x; e < mk * mk && cnt < PER; e += blockDim.x, ++cnt) {
+    const int i = e / mk, j = e % mk;
+    if (i <= j) {
+      h[(size_t)i * ldh + j] = out[cnt];
+      h[(size_t)j * ldh + i] = out[cnt];
+    }
+  }
+}
+
 // New border of H (Algorithm 2 step 4) from G = V[:, 0:mk+b]^T (L T):
 //   H[i, mk+j] = H[mk+j, i] = G[i, j]           i < mk
 //   H[mk+i, mk+j] = (G[mk+i, j] + G[mk+j, i]) / 2
@@ -208,6 +250,11 @@ void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double*
                const int* seg_skip, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
   k_h_restart<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, theta, st, mk, seg_skip);
+}
+void h_rotate(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* Y, int ldy, int64_t sy, int m, int mk,
+              const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
+  k_h_rotate<<<nseg, 256, 0, s>>>(H, ldh, sh, mmax, Y, ldy, sy, m, mk, seg_skip);
 }
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s) {

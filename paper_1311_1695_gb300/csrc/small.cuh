@@ -7,6 +7,13 @@ namespace lapeig {
 void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s);
 void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                const int* seg_skip, cudaStream_t s);
+// The restart's projected matrix of the rotated basis V Y[:, 0:mk] taken
+// from the small matrices: H[0:mk, 0:mk] <- Y^T H Y (FP64), the rest of H
+// (mmax x mmax) zero.  In exact arithmetic this is (V Y)^T L (V Y) for
+// H = V^T L V, and unlike diag(theta) it keeps what the small eigensolver's
+// rounding left off the diagonal.  m <= 64 rows of H and Y.
+void h_rotate(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* Y, int ldy, int64_t sy, int m, int mk,
+              const int* seg_skip, cudaStream_t s);
 void h_border(int nseg, double* H, int ldh, int64_t sh, const double* G, int ldg, int64_t sg, int mk, int b,
               const int* keep, int64_t sk, const double* norm1, const int* seg_skip, cudaStream_t s);
 void and_flags(int count, int* a, const int* b, cudaStream_t s);

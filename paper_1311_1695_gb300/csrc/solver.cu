@@ -179,6 +179,8 @@ struct JD {
   TP* LXb;  // L X of the correction solve
   TP* Xs;   // X packed for the per-phase correction solve
   TP* LZb;  // L z~ of the per-phase correction solve
+  float* V32 = nullptr;  // FP32 copy of the kept block V[:, 0:mk] (FP64 basis, large graphs)
+  int ld32 = 0;
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
@@ -190,12 +192,14 @@ struct JD {
   int inner_its = 0;
   int last_nact = 0;  // columns corrected by the last correction solve
   bool inject = false;  // next expansion adds random directions (stagnation)
-  // The restart recomputes the kept block of H as V^T W instead of taking
+  // The restart forms the kept block of H as Y^T H Y instead of taking
   // diag(theta) (always for an FP64 basis, else after stagnation): with a
   // near-degenerate cluster diag(theta) can carry a Ritz value that is off by
   // ~1e-7 (a value below the cluster's eigenvalue was seen), and its error
   // (rho(x) - theta) x lies in span(V), which the correction equation
-  // projects out, so only a fresh projected matrix removes it.
+  // projects out, so only the projected matrix of the rotated basis removes
+  // it.  (It equals (V Y)^T W Y in exact arithmetic, without the FP64 Gram
+  // product over all rows.)
   bool explicit_h = std::is_same<TV, double>::value;
   int injections = 0;
   double ev_rtol = 0.0;  // eigenvalue-accuracy test of an explicit check (0: off)
@@ -214,6 +218,10 @@ struct JD {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_m = 0;  // basis size after a replayed iteration
+
+  // FP64 basis with FP32 corrections: an FP32 copy of the kept block serves
+  // as the correction solve's X and as the first orthogonalisation pass's V0
+  static constexpr bool mixed_v32 = std::is_same<TV, double>::value && std::is_same<TP, float>::value;
 
   JD(lap_graph* G_, const Sizes& z_, cudaStream_t s) : G(G_), g(G_->dg), red(G_->red), z(z_), st(s) {}
   ~JD() {
@@ -234,6 +242,7 @@ struct JD {
     add(2 * n * z.ldv * sizeof(TV));
     add(n * z.ldb * sizeof(TV));
     for (int i = 0; i < 10; ++i) add(n * z.ldb * sizeof(TP));
+    if (mixed_v32) add(n * (size_t)round_up(z.mk, 4) * sizeof(float));
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
@@ -258,6 +267,10 @@ struct JD {
     LXb = a.take<TP>(n * z.ldb);
     Xs = a.take<TP>(n * z.ldb);
     LZb = a.take<TP>(n * z.ldb);
+    if (mixed_v32) {
+      ld32 = round_up(z.mk, 4);
+      V32 = a.take<float>(n * (size_t)ld32);
+    }
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
     Y = a.take<double>(S * mm);
@@ -289,7 +302,15 @@ struct JD {
   }
 
   // CGS2 of columns [m0, m0+q) of V against [e, V[:, 0:m0]]; keep1 = surviving columns.
+  // Large graphs take the streaming form (ortho_ts.cu), the others the
+  // persistent one; the step-level sequence below is the fallback.
+  bool large() const { return g.n >= (pw->split_rows > 0 ? pw->split_rows : kSplitRows); }
+  OrthoTs ortho_work() const {
+    return OrthoTs{oacc, kOrthoTsAcc, Rinv, 64 * 64, Gm, 65 * 64, Sm, 64 * 64, keep1, keep2, seg_skip, pw->gridbar(),
+                   pw->max_ctas};
+  }
   void ortho(int m0, int q, double drop1) {
+    if (large() && ortho_ts<TV>(g, ortho_work(), V, z.ldv, m0, q, drop1, st) == 0) return;
     if (ortho_fused<TV>(g, V, z.ldv, m0, q, drop1, oacc, keep1, seg_skip, pw->gridbar(), st, pw->max_ctas) == 0) return;
     TV* T = V + m0;
     // unit-normalise the columns
@@ -350,10 +371,18 @@ struct JD {
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
          seg_skip, sweeps, st, mk);
     update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
-    update<TV>(g, W, z.ldv, mk, 0.0, 1.0, W, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
-    h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
-    if (explicit_h)
-      gram<TV>(g, red, V, z.ldv, mk, W, z.ldv, mk, 0, 0, H, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
+    // W[:, 0:b] = L V[:, 0:b] by one SpMM of the Ritz block instead of the
+    // rotation W <- W Y of all m columns: the residuals read only these b
+    // columns and the next border only L T, and at b columns one SpMM moves
+    // fewer bytes (and, for an FP64 basis, far fewer FP64 operations) than a
+    // rotation of m columns into mk; the residuals are explicit as a bonus.
+    // The caller counts these b matrix-vector products.
+    spmm<TV>(g, V, z.ldv, W, z.ldv, z.b, st);
+    if (explicit_h)  // Y^T H Y: the rotated basis's projected matrix, from the small matrices
+      h_rotate(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax, m, mk,
+               seg_skip, st);
+    else
+      h_restart(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, z.mmax, theta, z.mmax, mk, seg_skip, st);
     return mk;
   }
 
@@ -398,9 +427,16 @@ struct JD {
     if constexpr (std::is_same<TV, TP>::value) {
       X = V; ldx = z.ldv; R = Rv; ldr = z.ldb;
     } else {
-      convert<TV, TP>(g, V, z.ldv, Xp, z.ldb, z.b, st);
+      const bool ts = mixed_v32 && large();
+      if (ts) {  // the whole kept block in FP32 (X = its first b columns)
+        convert<TV, float>(g, V, z.ldv, V32, ld32, mk, st);
+        X = reinterpret_cast<const TP*>(V32); ldx = ld32;
+      } else {
+        convert<TV, TP>(g, V, z.ldv, Xp, z.ldb, z.b, st);
+        X = Xp; ldx = z.ldb;
+      }
       convert<TV, TP>(g, Rv, z.ldb, Rp, z.ldb, z.b, st);
-      X = Xp; ldx = z.ldb; R = Rp; ldr = z.ldb;
+      R = Rp; ldr = z.ldb;
     }
     // single graph: the solve stops once every active column met delta
     FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, theta, z.mmax, active, seg_skip,
@@ -412,17 +448,38 @@ struct JD {
       set_error(std::string("correction-solve launch failed: ") + cudaGetErrorString(cudaGetLastError()));
       return -1;
     }
-    // T -> V[:, mk : mk+b]
-    convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
-    if (inject) {
-      // stagnation: the guard columns' slots (or the last slot) get random
-      // directions, so the search space keeps growing when corrections lie
-      // in span(V) and would be dropped
-      const int c0 = z.k < z.b ? z.k : z.b - 1;
-      random_block<TV>(g, V + mk + c0, z.ldv, z.b - c0, 0xA076'1D64'78BD'642Full ^ (uint64_t)(++injections), st);
-      inject = false;
+    // stagnation: the guard columns' slots (or the last slot) get random
+    // directions, so the search space keeps growing when corrections lie in
+    // span(V) and would be dropped
+    const int c0 = z.k < z.b ? z.k : z.b - 1;
+    const uint64_t iseed = 0xA076'1D64'78BD'642Full ^ (uint64_t)(injections + 1);
+    bool done = false;
+    if constexpr (mixed_v32) {
+      if (large()) {  // FP32 first pass on the correction block, then the FP64 pass (ortho_ts.cu)
+        if (inject) {
+          random_block<TP>(g, Tt + c0, z.ldb, z.b - c0, iseed, st);
+          ++injections;
+          inject = false;
+        }
+        const int rc = ortho_ts_mixed(g, ortho_work(), V, z.ldv, mk, z.b, V32, ld32, reinterpret_cast<float*>(Tt),
+                                      z.ldb, drop1, st);
+        if (rc < 0) {
+          set_error(std::string("orthonormalisation launch failed: ") + cudaGetErrorString(cudaGetLastError()));
+          return -1;
+        }
+        done = rc == 0;
+      }
     }
-    ortho(mk, z.b, drop1);
+    if (!done) {
+      // T -> V[:, mk : mk+b]
+      convert<TP, TV>(g, Tt, z.ldb, V + mk, z.ldv, z.b, st);
+      if (inject) {
+        random_block<TV>(g, V + mk + c0, z.ldv, z.b - c0, iseed, st);
+        ++injections;
+        inject = false;
+      }
+      ortho(mk, z.b, drop1);
+    }
     spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
     gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
     h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, G->d_norm1, seg_skip, st);
@@ -468,6 +525,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
   int rc = LAP_ENOCONV;
   ++outer;
   m = jd.tail(m, explicit_check);
+  jd.n_matvec += jd.z.b;  // the Rayleigh-Ritz step's L X
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("CUDA error in JD loop"); return LAP_ECUDA; }
   while (true) {
     const JdStatus stt = *jd.status_h;
@@ -600,7 +658,7 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
       return LAP_ETIMEOUT;
     }
     jd.inner_its += s2.pcg_steps;
-    jd.n_matvec += (int64_t)(s2.pcg_steps + 1) * nact;
+    jd.n_matvec += (int64_t)(s2.pcg_steps + 1) * nact + jd.z.b;  // + the Rayleigh-Ritz step's L X
     if (prof_on()) {
       prof_set_last_bytes("pcg_fused", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));
       prof_set_last_bytes("pcg_split", pcg_bytes(jd.g, jd.z.b, s2.pcg_steps, (int)sizeof(TP)));

@@ -17,7 +17,8 @@ Network, for a batch handle of graphs (each graph its own segment):
     H_0 = F (features),  tanh([M^s H_l | H_l] [W_l; U_l] + b_l) -> H_{l+1},
     X = C H_3 W_out,     M = D^{-1} A,  s = HOPS,  C = per-graph centring.
 Loss per graph: 1 - tr(G^{-1} X^T U U^T X) / k with G = X^T X + eps tr(X^T X)/k I
-(U = solver eigenvectors); the k x k algebra of the loss runs on the host.
+(U = solver eigenvectors); its k x k algebra (lap_gnn_loss) and the Adam update
+(lap_adam_step) run in the library too.
 """
 from __future__ import annotations
 
@@ -197,26 +198,20 @@ class Net:
 
     # -- loss per graph and dX
     def loss(self):
+        """Per-graph losses (numpy) and dX on the device; the k x k algebra runs
+        in the library (lap_gnn_loss)."""
+        import torch
         k = self.k
         UXp = self.UX.data_ptr()
-        UtX = self._gram(UXp, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).cpu().numpy()
-        XtX = self._gram(UXp + 4 * k, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).cpu().numpy()
-        losses = np.zeros(self.nseg)
-        S = np.zeros((self.nseg, 2 * k, k))
-        for s in range(self.nseg):
-            Gr = XtX[s] + EPS_RIDGE * (np.trace(XtX[s]) / k) * np.eye(k)
-            Gi = np.linalg.inv(Gr)
-            UX = UtX[s]
-            M = UX.T @ UX
-            losses[s] = 1.0 - np.trace(Gi @ M) / k
-            A = Gi @ M @ Gi
-            # dX = U S_u + X S_x; mean over graphs: scale by 1/nseg
-            S[s, :k] = -(2.0 / k) * UX @ Gi / self.nseg
-            S[s, k:] = (2.0 / k) * (A + (EPS_RIDGE / k) * np.trace(A) * np.eye(k)) / self.nseg
-        import torch
-        St = torch.from_numpy(S).cuda()
+        P = self._gram(UXp, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).contiguous()
+        Q = self._gram(UXp + 4 * k, 2 * k, k, UXp + 4 * k, 2 * k, k, 0).contiguous()
+        losses = torch.zeros(self.nseg, dtype=torch.float64, device="cuda")
+        St = torch.zeros((self.nseg, 2 * k, k), dtype=torch.float64, device="cuda")
+        _check(lib().lap_gnn_loss(self.nseg, k, EPS_RIDGE, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(Q.data_ptr()),
+                                  ctypes.c_void_p(losses.data_ptr()), ctypes.c_void_p(St.data_ptr()), _stream()),
+               "lap_gnn_loss")
         self._update(self.dX.data_ptr(), WIDTH, k, 0.0, UXp, 2 * k, 2 * k, 0, St, k, 2 * k * k)
-        return losses
+        return losses.cpu().numpy()
 
     # -- backward: gradients (summed over the graphs of the batch), FP64 numpy
     def backward(self):
@@ -253,21 +248,29 @@ class Net:
 
 
 class Adam:
+    """Adam over the parameter list; the update runs in the library
+    (lap_adam_step) on a flat device copy of the parameters and moments."""
+
     def __init__(self, params, lr=3e-3, b1=0.9, b2=0.999, eps=1e-8):
-        self.m = [np.zeros_like(p) for p in params]
-        self.v = [np.zeros_like(p) for p in params]
+        import torch
+        n = sum(p.size for p in params)
+        self.m = torch.zeros(n, dtype=torch.float64, device="cuda")
+        self.v = torch.zeros(n, dtype=torch.float64, device="cuda")
         self.t, self.lr, self.b1, self.b2, self.eps = 0, lr, b1, b2, eps
 
     def step(self, params, grads):
+        import torch
         self.t += 1
-        for p, g, m, v in zip(params, grads, self.m, self.v):
-            m *= self.b1
-            m += (1 - self.b1) * g
-            v *= self.b2
-            v += (1 - self.b2) * g * g
-            mh = m / (1 - self.b1 ** self.t)
-            vh = v / (1 - self.b2 ** self.t)
-            p -= self.lr * mh / (np.sqrt(vh) + self.eps)
+        p = torch.from_numpy(np.concatenate([x.ravel() for x in params])).cuda()
+        g = torch.from_numpy(np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in grads])).cuda()
+        _check(lib().lap_adam_step(p.numel(), ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                   ctypes.c_void_p(self.m.data_ptr()), ctypes.c_void_p(self.v.data_ptr()), self.t,
+                                   self.lr, self.b1, self.b2, self.eps, _stream()), "lap_adam_step")
+        flat = p.cpu().numpy()
+        o = 0
+        for x in params:
+            x[...] = flat[o:o + x.size].reshape(x.shape)
+            o += x.size
 
 
 def warm_start(G: Graph, params, seed: int = 0x5EED):
@@ -277,3 +280,15 @@ def warm_start(G: Graph, params, seed: int = 0x5EED):
     net = Net(G, k)
     X = net.forward(params, seed)
     return X.double().contiguous()
+
+
+def warm_start_native(G: Graph, params, seed: int = 0x5EED):
+    """The same proposal from the library's own forward pass
+    (lap_gnn_warm_start): float64 CUDA tensor n x k."""
+    import torch
+    k = int(params[-1].shape[1])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in params]))
+    X = torch.zeros((G.n, k), dtype=torch.float64, device="cuda")
+    _check(lib().lap_gnn_warm_start(G.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), flat.size, k, seed,
+                                    ctypes.c_void_p(X.data_ptr()), k, _stream()), "lap_gnn_warm_start")
+    return X
