@@ -413,25 +413,26 @@ def bench_ours(args):
         def one(H, **kw):
             H.eigs(k, 1e-8, evecs=evecs if H is G else None, stream=sp, **kw)
             flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
             _, infc = H.eigs(k, 1e-8, evecs=evecs if H is G else None, stream=sp, **kw)
-            e1.record(stream)
-            e1.synchronize()
-            return round(e0.elapsed_time(e1), 1), infc[0]
+            c1.record(stream)
+            c1.synchronize()
+            return round(c0.elapsed_time(c1), 1), infc[0]
 
         compare = {}
         if os.path.exists(gnn_mod.WEIGHTS):
             gp, _ = gnn_mod.load_params()
-            ms, ic = one(G, precision=args.precision, use_gnn=True, gnn_params=gp)
-            compare["learned_start"] = {"ms": ms, "outer_its": ic["outer_its"], "n_matvec": ic["n_matvec"],
+            c_ms, ic = one(G, precision=args.precision, use_gnn=True, gnn_params=gp)
+            compare["learned_start"] = {"ms": c_ms, "outer_its": ic["outer_its"], "n_matvec": ic["n_matvec"],
                                         "status": ic["status"]}
-        ms, ic = one(G, precision="fp64")
-        compare["fp64_jd"] = {"ms": ms, "outer_its": ic["outer_its"], "n_matvec": ic["n_matvec"], "status": ic["status"]}
+        c_ms, ic = one(G, precision="fp64")
+        compare["fp64_jd"] = {"ms": c_ms, "outer_its": ic["outer_its"], "n_matvec": ic["n_matvec"],
+                              "status": ic["status"]}
         g3 = graphgen.workload_graph("c3")
         H3 = pkg.Graph([g3])
-        ms, ic = one(H3, precision=args.precision)
-        compare["c3_mixed"] = {"ms": ms, "n": g3.n, "nnz": int(g3.nnz), "outer_its": ic["outer_its"],
+        c_ms, ic = one(H3, precision=args.precision)
+        compare["c3_mixed"] = {"ms": c_ms, "n": g3.n, "nnz": int(g3.nnz), "outer_its": ic["outer_its"],
                                "max_rel_residual": ic["max_rel_residual"], "status": ic["status"]}
         H3.close()
     base = None

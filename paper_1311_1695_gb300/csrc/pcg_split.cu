@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) k_split_init(DevGraph g, SplitView<T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   Ctx<T, BMAX, BWL> cx;
-  const int ld = f.ld;
+  constexpr int ld = BMAX;  // the row stride (the launch passes only blocks of exactly BMAX columns)
   cx.setup(smem_raw, 1, ld);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
   const int b = f.b, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   if (__ldcg(sv.stop)) return;
-  const int ld = f.ld, b = f.b;
+  constexpr int ld = BMAX;  // the row stride (the launch passes only blocks of exactly BMAX columns)
+  const int b = f.b;
   const int par = it & 1, prv = par ^ 1;
   const int nout = (b + 1) * b;
   const int64_t ss = f.state_stride;
@@ -503,7 +504,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_split_b(DevGraph g, SplitView<T
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   if (__ldcg(sv.stop)) return;
-  const int ld = f.ld, b = f.b;
+  constexpr int ld = BMAX;  // the row stride (the launch passes only blocks of exactly BMAX columns)
+  const int b = f.b;
   const int par = it & 1, prv = par ^ 1;
   const int nout = (b + 1) * b;
   const int64_t ss = f.state_stride;
@@ -587,7 +589,8 @@ __global__ void __launch_bounds__(kThreads) k_split_g2(DevGraph g, SplitView<T> 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const View<T>& f = sv.v;
   if (__ldcg(sv.stop)) return;
-  const int ld = f.ld, b = f.b;
+  constexpr int ld = BMAX;  // the row stride (the launch passes only blocks of exactly BMAX columns)
+  const int b = f.b;
   Ctx<T, BMAX, BWL> cx;
   cx.setup(smem_raw, 3, ld);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
@@ -648,7 +651,8 @@ __global__ void __launch_bounds__(kThreads) k_split_fin(DevGraph g, SplitView<T>
 
 template <typename T, int BMAX>
 int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas) {
-  constexpr int BWL = BMAX <= 4 ? 4 : (BMAX > 16 ? 32 : BMAX);  // lanes per row, as in the persistent form
+  // lanes per row: the power of two >= BMAX (idle lanes past b)
+  constexpr int BWL = BMAX <= 4 ? 4 : (BMAX <= 8 ? 8 : (BMAX <= 16 ? 16 : 32));
   const int ld = f.ld;
   View<T> ff{static_cast<const T*>(f.Xv), f.ldx, static_cast<const T*>(f.Rv), f.ldr, static_cast<T*>(f.Ttv),
              static_cast<T*>(f.RESv), static_cast<T*>(f.Zv), static_cast<T*>(f.Pv), static_cast<T*>(f.APv),
@@ -722,9 +726,23 @@ int pcg_split(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_ctas
   const void* ptrs[8] = {f.Xsv, f.LZv, f.Ttv, f.RESv, f.Zv, f.Pv, f.APv, f.LXv};
   for (const void* p : ptrs)
     if (!aligned16(p)) return 1;
-  if (f.b <= 4 && sizeof(T) == 4) return split_launch<T, 4>(g, f, s, max_ctas);
-  if (f.b <= 8) return split_launch<T, 8>(g, f, s, max_ctas);
-  return split_launch<T, 16>(g, f, s, max_ctas);
+  // one instantiation per row stride, so the row loops have compile-time
+  // trip counts (a run-time bound cost a quarter more instructions)
+  if constexpr (sizeof(T) == 4) {
+    switch (f.ld) {
+      case 4: return split_launch<T, 4>(g, f, s, max_ctas);
+      case 8: return split_launch<T, 8>(g, f, s, max_ctas);
+      case 12: return split_launch<T, 12>(g, f, s, max_ctas);
+      default: return split_launch<T, 16>(g, f, s, max_ctas);
+    }
+  } else {
+    switch (f.ld) {
+      case 2: return split_launch<T, 2>(g, f, s, max_ctas);
+      case 4: return split_launch<T, 4>(g, f, s, max_ctas);
+      case 6: return split_launch<T, 6>(g, f, s, max_ctas);
+      default: return split_launch<T, 8>(g, f, s, max_ctas);
+    }
+  }
 }
 
 template int pcg_split<float>(const DevGraph&, const FusedPcg&, cudaStream_t, int);
