@@ -348,7 +348,7 @@ def bench_ours(args):
         per_launch_ms = v["ms"] / v["launches"]
         ach = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": traffic_for(name, args.workload),
+                "frac": round(ach / hbm, 4), "traffic": traffic_for(name, args.workload, per_launch_bytes),
                 "bytes_per_launch": per_launch_bytes, "us_per_launch": round(per_launch_ms * 1e3, 3),
                 "launches_per_step": v["launches"] // max(1, args.steps), "peak_source": peak_src,
                 "share_of_kernel_time": round(v["ms"] / sum(x["ms"] for x in prof.values()), 4)}
@@ -481,9 +481,11 @@ def ctypes_int():
     return ctypes.c_int()
 
 
-def traffic_for(kernel: str, workload: str):
+def traffic_for(kernel: str, workload: str, bytes_per_launch: float):
     """DRAM bytes per launch from a committed ncu capture of this kernel and
-    workload, if the kernel source has not changed since (else null)."""
+    workload (profiles/traffic.json: measured DRAM bytes over the model's
+    algorithmic bytes on the captured launches, times this launch's model
+    bytes), if no source file of the kernel has changed since (else null)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -493,9 +495,12 @@ def traffic_for(kernel: str, workload: str):
         e = d.get(f"{kernel}@{workload}")
         if not e:
             return None
-        src = os.path.join(ROOT, "paper_1311_1695_gb300", "csrc", e["source"])
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return e["dram_bytes_per_launch"] if h == e["source_sha"] else None
+        h = hashlib.sha256()
+        for src in e["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_1311_1695_gb300", "csrc", src), "rb").read())
+        if h.hexdigest()[:16] != e["source_sha"]:
+            return None
+        return round(e["dram_over_model"] * bytes_per_launch)
     except Exception:
         return None
 

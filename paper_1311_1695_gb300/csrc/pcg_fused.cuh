@@ -80,6 +80,11 @@ int ortho_ts(const DevGraph& g, const OrthoTs& w, T* V, int ldv, int m0, int q, 
 // V[:, m0 : m0+q] (FP64) and one FP64 pass.  Tt is overwritten.
 int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int m0, int q, const float* V32,
                    int ld32, float* Tt, int ldt, double drop1, cudaStream_t s);
+// One FP64 pass over V[:, 0:q] (FP64, already orthonormal to FP32 accuracy,
+// T32 its FP32 original): the columns orthonormal to FP64 accuracy and
+// orthogonal to e; keep1 = the columns kept.  Returns 0, 1 or -1.
+int ortho_ts_refine(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int q, const float* T32, int ld32,
+                    cudaStream_t s);
 constexpr int kOrthoTsAcc = 66 * 32;
 
 // Launch the whole correction solve (the per-phase form for graphs of at

@@ -331,13 +331,21 @@ struct JD {
   // Start: V[:, 0:q] from `init` (or random), orthonormalised; W = L V; H = V^T W.
   // x0d (device, row-major n x ldx0, FP64): optional warm-start columns that
   // replace the first k0 random columns.
+  // init32: the FP32 block `init` was converted from, orthonormal to FP32
+  // accuracy (the phase change of mixed precision): one FP64 refinement pass
+  // replaces the full orthonormalisation on large graphs
   int start(const TV* init, int ldi, int q, uint64_t seed, double drop1, const double* x0d = nullptr, int ldx0 = 0,
-            int k0 = 0) {
+            int k0 = 0, const float* init32 = nullptr, int ld32i = 0) {
     if (init) convert<TV, TV>(g, init, ldi, V, z.ldv, q, st);
     else random_block<TV>(g, V, z.ldv, q, seed, st);
     if (!init && x0d && k0 > 0) convert<double, TV>(g, x0d, ldx0, V, z.ldv, k0 < q ? k0 : q, st);
     cudaMemsetAsync(seg_skip, 0, sizeof(int) * z.nseg * 64, st);
-    ortho(0, q, drop1);
+    bool refined = false;
+    if constexpr (std::is_same<TV, double>::value) {
+      if (init32 && large())
+        refined = ortho_ts_refine(g, ortho_work(), V, z.ldv, q, init32, ld32i, st) == 0;
+    }
+    if (!refined) ortho(0, q, drop1);
     // a start column dropped as dependent (a degenerate warm start, or one
     // parallel to e) is replaced by a fresh random column: the search space
     // must start with q independent directions
@@ -872,7 +880,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   convert<float, double>(G->dg, j1.V, z.ldv, j2.V, z.ldv, mk, st);
   j2.n_matvec = j1.n_matvec;
   j2.inner_its = j1.inner_its;
-  m = j2.start(j2.V, z.ldv, mk, 0, 1e-20);
+  m = j2.start(j2.V, z.ldv, mk, 0, 1e-20, nullptr, 0, 0, j1.V, z.ldv);
   int status = (st1 == LAP_ETIMEOUT) ? LAP_ETIMEOUT : iterate(j2, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30,
                                                                 o.cuda_graph >= 0);
   if (status < 0 && status != LAP_ETIMEOUT) return status;
