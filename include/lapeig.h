@@ -134,7 +134,8 @@ typedef struct {
   double elapsed_ms;      /* wall time inside the call */
   int phase1_outer;       /* mixed precision: outer iterations done in FP32 */
   int spmm_team;          /* lanes per row of the scalar SpMM kernels (blocks of 1-2 columns) */
-  int spmm_unroll;        /* gathers in flight per lane of the vectorised SpMM */
+  int spmm_unroll;        /* gathers in flight per lane of the vectorised SpMM (2, 4, 8), or
+                             100 + neighbours in flight of its lane-per-row form */
   int hub_threshold;      /* rows longer than this are split into chunks over warps */
 } lap_info;
 
@@ -194,6 +195,11 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
  * Calls that run SpMM-type kernels on one handle must be stream-ordered:
  * the handle's reduction and hub-chunk scratch is shared by them. */
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh);
+/* Override the vectorised SpMM's form (blocks of 3..16 columns, rows 16-byte
+ * aligned): 2, 4 or 8 gathers in flight per lane with several lanes per row,
+ * or 102 / 104 for a lane per row with 2 / 4 neighbours in flight (the
+ * values lap_graph_autotune chooses among).  LAP_EINVAL for other values. */
+int lap_graph_set_gathers(lap_graph* g, int gathers);
 
 /* Preconditioner of the correction solve on this handle (Section 3 item 2,
  * Section 3.2.1).  LAP_PRECOND_JACOBI: M = D^{-1}, nothing to set up.

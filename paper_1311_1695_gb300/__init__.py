@@ -137,6 +137,7 @@ _SIGNATURES = {
     "lap_gnn_dense_bf16": (_I, [_P, _I, _P, _I, _P, _P, _P, _I, _I, _I, _I, _P]),
     "lap_gnn_wgrad_bf16": (_I, [_P, _I, _P, _I, _P, _I, _P, _P]),
     "lap_gnn_tanh_back_bf16": (_I, [_P, _P, _I, _P, _I, _I, _P]),
+    "lap_graph_set_gathers": (_I, [_P, _I]),
     "lap_gnn_warm_start": (_I, [_P, _PD, ctypes.c_int64, _I, ctypes.c_uint64, _P, _I, _P]),
     "lap_gnn_param_count": (ctypes.c_int64, [_I]),
     "lap_gnn_loss": (_I, [_I, _I, _D, _P, _P, _P, _P, _P]),
@@ -360,6 +361,10 @@ class Graph:
         """Correction-solve preconditioner of the handle (lap_graph_set_precond)."""
         _check(lib().lap_graph_set_precond(self.h, _PRECONDS[kind] if isinstance(kind, str) else int(kind), alpha),
                "lap_graph_set_precond")
+
+    def set_gathers(self, gathers):
+        """Form of the vectorised SpMM (lap_graph_set_gathers): 2, 4, 8, 102 or 104."""
+        _check(lib().lap_graph_set_gathers(self.h, gathers), "lap_graph_set_gathers")
 
     def set_launch(self, max_ctas=0, device_timeout_ms=0.0, split_rows=0):
         """CTA cap, device wait limit, and the row count from which the

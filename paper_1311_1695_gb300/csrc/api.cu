@@ -327,6 +327,15 @@ int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   return graph_set_schedule(g, team, long_thresh);
 }
 
+int lap_graph_set_gathers(lap_graph* g, int gathers) {
+  if (!g || (gathers != 2 && gathers != 4 && gathers != 8 && gathers != 102 && gathers != 104)) {
+    set_error("bad arguments to lap_graph_set_gathers");
+    return LAP_EINVAL;
+  }
+  g->dg.vec_u = gathers;
+  return LAP_OK;
+}
+
 int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms, int split_rows) {
   if (!g || max_ctas < 0 || !(device_timeout_ms >= 0.0) || split_rows < 0) {
     set_error("bad arguments to lap_graph_set_launch");

@@ -35,6 +35,7 @@
 // in the FP64 Gram sweep) with the run-time shape as a predicate, and the
 // coefficient columns of the lane live in registers.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -87,6 +88,28 @@ struct SweepSmem {
   static constexpr size_t head = (sizeof(T) * (kRed + kCoef) + 15) / 16 * 16;
 };
 
+// n values of a staged row into registers by 16-byte loads; the vectors
+// that start at or past `valid` are zero (src 16-byte aligned, and the row
+// holds every vector that starts below `valid`)
+template <typename T, int N>
+__device__ __forceinline__ void load_row(T (&d)[N], const T* src, int valid) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int W = 16 / sizeof(T);
+  static_assert(N % W == 0, "whole vectors");
+#pragma unroll
+  for (int i = 0; i < N; i += W) {
+    if (i < valid) {
+      const V v = *reinterpret_cast<const V*>(src + i);
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int k = 0; k < W; ++k) d[i + k] = e[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) d[i + k] = T(0);
+    }
+  }
+}
+
 template <typename T, int BWL, int M0B, int MODE, bool HR, bool HG>
 __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -110,6 +133,11 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
   const int na = MODE == kGram ? m0 + 1 + q : (MODE == kFull ? a.mfull + 1 : 0);
   T accG[M0B];  // [1|V0]^T x (kFull: [1|V]^T t)
   T accS[BWL];  // x^T x
+  // a write-only sweep keeps its coefficient columns in registers (it has
+  // no accumulators); the Gram sweeps read them from shared memory
+  constexpr bool kRegC = MODE == kWrite;
+  T gcol[kRegC && HG ? M0B : 1];
+  T rcol[kRegC && HR ? BWL : 1];
 #pragma unroll
   for (int i = 0; i < M0B; ++i) accG[i] = T(0);
 #pragma unroll
@@ -151,6 +179,19 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
       [&](const Tile& t) {
         if (MODE != kWrite && cur >= 0) flush();
         cur = t.seg;
+        if constexpr (kRegC) {
+          if constexpr (HR) {
+            const double* Rg = a.R + (size_t)t.seg * a.sr;
+#pragma unroll
+            for (int j = 0; j < BWL; ++j) rcol[j] = (colok && j <= c) ? (T)Rg[j * q + c] : T(0);
+          }
+          if constexpr (HG) {
+            const double* Gg = a.G + (size_t)t.seg * a.sg;
+#pragma unroll
+            for (int i = 0; i < M0B; ++i) gcol[i] = (colok && i <= m0) ? (T)Gg[i * q + c] : T(0);
+          }
+          return;
+        }
         __syncthreads();  // the previous graph's rows are done with the coefficients
         if constexpr (HR) {  // R (upper triangular: rows j <= c), zero outside q x q
           const double* Rg = a.R + (size_t)t.seg * a.sr;
@@ -178,19 +219,25 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
           const T* tr = stt + (size_t)ir * ldt + toff;
           const T* vr = sq + (size_t)ir * a.ldq;
           const bool live = row && colok;
+          constexpr int W = 16 / sizeof(T);
+          constexpr int NV = (M0B - 1 + W - 1) / W * W;  // V row values held
+          T vrow[NV];
+          load_row<T, NV>(vrow, vr, MODE == kFull ? a.mfull : m0);
+          T trow[HR ? BWL : W];
+          if constexpr (HR) load_row<T, BWL>(trow, tr, q);
           T x = colok ? tr[c] : T(0);
           if constexpr (HR) {
             T s = T(0);
 #pragma unroll
             for (int j = 0; j < BWL; ++j)
-              if (j < q) s += tr[j] * Rs[j * BWL + c];
+              if (j < q) s += trow[j] * (kRegC ? rcol[kRegC ? j : 0] : Rs[j * BWL + c]);  // past q: padding
             x = s;
           }
           if constexpr (HG) {
-            T s = Gs[c];
+            T s = kRegC ? gcol[0] : Gs[c];
 #pragma unroll
             for (int i = 0; i < M0B - 1; ++i)
-              if (i < m0) s += vr[i] * Gs[(i + 1) * BWL + c];
+              if (i < m0) s += vrow[i] * (kRegC ? gcol[kRegC ? i + 1 : 0] : Gs[(i + 1) * BWL + c]);
             x -= s;
           }
           if (MODE != kFull && a.out && live) {
@@ -203,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
             accG[0] += y;
 #pragma unroll
             for (int i = 0; i < M0B - 1; ++i)
-              if (i < m0) accG[i + 1] += vr[i] * y;
+              if (i < m0) accG[i + 1] += vrow[i] * y;
 #pragma unroll
             for (int j = 0; j < BWL; ++j) {
               const T xj = __shfl_sync(0xffffffffu, y, gbase + j);
@@ -214,7 +261,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
             accG[0] += y;
 #pragma unroll
             for (int i = 0; i < M0B - 1; ++i)
-              if (i < a.mfull) accG[i + 1] += vr[i] * y;
+              if (i < a.mfull) accG[i + 1] += vrow[i] * y;
           }
         }
       });
@@ -331,7 +378,11 @@ void pyth_step(const DevGraph& g, const OrthoTs& w, int m0, int q, int scale, do
 // strides of 16-byte multiples; q <= 32, m0 + q <= 64.
 template <typename T>
 bool ortho_ts_ok(const void* V, int ldv, int m0, int q) {
-  return a16(V) && ((size_t)ldv * sizeof(T)) % 16 == 0 && q >= 1 && q <= 32 && m0 >= 0 && m0 + q <= 64;
+  // rows and the new block's first column on 16-byte boundaries, every
+  // 16-byte vector that starts inside V0 or t inside the row
+  const int w = 16 / (int)sizeof(T);
+  return a16(V) && ((size_t)ldv * sizeof(T)) % 16 == 0 && m0 % w == 0 && q >= 1 && q <= 32 && m0 >= 0 &&
+         m0 + q <= 64 && ldv >= m0 + (q + w - 1) / w * w;
 }
 
 template <typename T>

@@ -267,9 +267,120 @@ __global__ void __launch_bounds__(256) k_spmm_vec(DevGraph g, const T* __restric
   }
 }
 
-// g.vec_u: independent gathers per lane in flight (2, 4 or 8; the autotuner's choice)
+// Lane-per-row form of the vectorised SpMM: a lane takes a whole ordinary
+// row (all its NQ vectors of W columns), 32 rows of similar degree per warp
+// (the degree-sorted schedule), U neighbours' rows in flight, each one NQ
+// vector loads; hub rows as in k_spmm_vec (the first blocks take the
+// chunks).  Against k_spmm_vec's NQ lanes per row it loads each column
+// index once instead of NQ times and keeps NQ times more gathers in flight
+// per warp, at the price of column-index loads scattered over 32 rows.
+template <typename T, int NQ, int BWL, int U>
+__global__ void __launch_bounds__(256) k_spmm_lane(DevGraph g, const T* __restrict__ X, int ldx,
+                                                   T* __restrict__ Y, int ldy, int b) {
+  if (g.skip_flag && *(volatile const int*)g.skip_flag) return;
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::w;
+  const T* __restrict__ w = weights_of<T>(g);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nhb = (g.nchunk + 7) / 8;
+  if ((int)blockIdx.x < nhb) {  // hub chunks, lanes as columns
+    constexpr int RW = 32 / BWL;
+    const int c = lane % BWL;
+    const bool colok = c < b;
+    const int ch = blockIdx.x * 8 + warp;
+    if (ch >= g.nchunk) return;  // whole warp
+    const int4 cc = g.chunks[ch];
+    T a = T(0);
+#pragma unroll 8
+    for (int p = cc.y + lane / BWL; p < cc.z; p += RW) {
+      const int j = __ldg(g.colidx + p);
+      const T wv = w ? __ldg(w + p) : T(1);
+      if (colok) a += wv * __ldg(X + (size_t)j * ldx + c);
+    }
+#pragma unroll
+    for (int o = BWL; o < 32; o <<= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (!hub_finish<T>(g, ch, cc, a, b)) return;
+    const int row = cc.x;
+    if (lane < b) Y[(size_t)row * ldy + lane] = degree_of<T>(g, row) * X[(size_t)row * ldx + lane] - a;
+    return;
+  }
+  const int slot = (blockIdx.x - nhb) * 256 + threadIdx.x;
+  if (slot >= g.norder) return;  // no shuffles below
+  const int row = __ldg(g.order + slot);
+  const int p0 = __ldg(g.rowptr + row), p1 = __ldg(g.rowptr + row + 1);
+  const V* __restrict__ Xv = reinterpret_cast<const V*>(X);
+  const int ldxv = ldx / W;
+  T acc[NQ][W];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k)
+#pragma unroll
+    for (int e = 0; e < W; ++e) acc[k][e] = T(0);
+  auto add = [&](const V (&v)[NQ], T wv) {
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      if constexpr (W == 4) {
+        acc[k][0] += wv * v[k].x; acc[k][1] += wv * v[k].y; acc[k][2] += wv * v[k].z; acc[k][3] += wv * v[k].w;
+      } else {
+        acc[k][0] += wv * v[k].x; acc[k][1] += wv * v[k].y;
+      }
+    }
+  };
+  int p = p0;
+  for (; p + U <= p1; p += U) {
+    int col[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) col[u] = __ldg(g.colidx + p + u);
+    V v[U][NQ];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) v[u][k] = __ldg(Xv + (size_t)col[u] * ldxv + k);
+#pragma unroll
+    for (int u = 0; u < U; ++u) add(v[u], w ? __ldg(w + p + u) : T(1));
+  }
+  for (; p < p1; ++p) {
+    const int j = __ldg(g.colidx + p);
+    V v[NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) v[k] = __ldg(Xv + (size_t)j * ldxv + k);
+    add(v, w ? __ldg(w + p) : T(1));
+  }
+  const T d = degree_of<T>(g, row);
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const V xr = Xv[(size_t)row * ldxv + k];
+    T out[W];
+    if constexpr (W == 4) {
+      out[0] = d * xr.x - acc[k][0]; out[1] = d * xr.y - acc[k][1];
+      out[2] = d * xr.z - acc[k][2]; out[3] = d * xr.w - acc[k][3];
+    } else {
+      out[0] = d * xr.x - acc[k][0]; out[1] = d * xr.y - acc[k][1];
+    }
+    const int c0 = W * k;
+    if (c0 + W <= b) {
+      V o;
+      if constexpr (W == 4) o = make_float4(out[0], out[1], out[2], out[3]);
+      else o = make_double2(out[0], out[1]);
+      reinterpret_cast<V*>(Y)[(size_t)row * (ldy / W) + k] = o;
+    } else {
+#pragma unroll
+      for (int e = 0; e < W; ++e)
+        if (c0 + e < b) Y[(size_t)row * ldy + c0 + e] = out[e];
+    }
+  }
+}
+
+// g.vec_u: independent gathers per lane in flight (2, 4 or 8), or 100 + neighbours in
+// flight of the lane-per-row form (102, 104); the autotuner's choice
 template <typename T, int NQ, int BWL>
 static void launch_vec(const DevGraph& g, const T* X, int ldx, T* Y, int ldy, int b, cudaStream_t s) {
+  if (g.vec_u > 100) {  // lane per row, vec_u - 100 neighbours in flight
+    const int blocks = (g.nchunk + 7) / 8 + (g.norder + 255) / 256;
+    if (blocks <= 0) return;
+    if (g.vec_u >= 104) k_spmm_lane<T, NQ, BWL, 4><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+    else k_spmm_lane<T, NQ, BWL, 2><<<blocks, 256, 0, s>>>(g, X, ldx, Y, ldy, b);
+    return;
+  }
   constexpr int RPB = 8 * (32 / NQ);  // rows per block
   const int blocks = (g.nchunk + 7) / 8 + (g.norder + RPB - 1) / RPB;
   if (blocks <= 0) return;
@@ -388,10 +499,12 @@ int graph_autotune(lap_graph* g, int dtype, int b, int* team_out, int* thresh_ou
   // candidates: the hub threshold, and lanes per row of the scalar kernels
   // (b <= 2) or gathers in flight per lane of the vectorised one
   const bool vec_path = b >= 3 && b <= 16;
-  const int teams[4] = {4, 8, 16, 32};
-  const int unrolls[4] = {2, 4, 8, 8};
+  const int teams[5] = {4, 8, 16, 32, 32};
+  // vectorised kernel: gathers in flight per lane (2, 4, 8), or lane per row
+  // with 2 or 4 neighbours in flight (102, 104)
+  const int unrolls[5] = {2, 4, 8, 102, 104};
   const int threshs[5] = {32, 64, 128, 256, 1 << 30};
-  const int nvar = vec_path ? 3 : 4;
+  const int nvar = vec_path ? 5 : 4;
   float best = 1e30f;
   int bt = g->dg.team, bh = g->dg.long_thresh, bu = g->dg.vec_u;
   for (int ti = 0; ti < nvar; ++ti) {

@@ -467,8 +467,27 @@ def test_autotuned_schedule_matches_oracle(pkg, dt, b):
     Gd = pkg.Graph(g)
     u, h = Gd.autotune("f32" if dt == torch.float32 else "f64", b)
     assert h in (32, 64, 128, 256, 1 << 30)
-    assert u in ((2, 4, 8) if b >= 3 else (4, 8, 16, 32))
+    assert u in ((2, 4, 8, 102, 104) if b >= 3 else (4, 8, 16, 32))
     X = G.random_block(g.n, b, 21).astype(np.float32 if dt == torch.float32 else np.float64)
+    Xd = _dev(X, dt)
+    Yd = torch.empty_like(Xd)
+    Gd.spmm(Xd, Yd)
+    ref = blockops.lap_spmm(g, X.astype(np.float64))
+    S, deg = _abs_bound(g, X.astype(np.float64))
+    assert np.all(np.abs(Yd.cpu().double().numpy() - ref) <= 2 * EPS[dt] * deg[:, None] * S + 1e-300)
+    Gd.close()
+
+
+@pytest.mark.parametrize("gathers", [2, 4, 8, 102, 104])
+@pytest.mark.parametrize("dt,b", [(torch.float32, 12), (torch.float32, 5), (torch.float64, 6)])
+def test_every_vectorised_form_matches_oracle(pkg, gathers, dt, b):
+    """Each form of the vectorised SpMM the autotuner chooses among (lanes
+    per row with 2/4/8 gathers in flight, or a lane per row with 2/4
+    neighbours in flight) gives the oracle's L X, hub rows included."""
+    g = GRAPHS["cl_hubs"]()
+    Gd = pkg.Graph(g)
+    Gd.set_gathers(gathers)
+    X = G.random_block(g.n, b, 23).astype(np.float32 if dt == torch.float32 else np.float64)
     Xd = _dev(X, dt)
     Yd = torch.empty_like(Xd)
     Gd.spmm(Xd, Yd)
