@@ -350,12 +350,11 @@ template <typename T, int MODE, bool HR, bool HG>
 int sweep_m(const DevGraph& g, const SweepArgs& a, cudaStream_t s, int max_ctas) {
   const int rows = MODE == kFull ? a.mfull + 1 : a.m0 + 1;
   const bool small = rows <= 24;
-  const bool mid = rows <= 34;
+  if (rows > 34) return 1;  // ortho_ts_ok keeps shapes within 34 rows
   auto pick = [&](auto bwl) -> int {
     constexpr int B = decltype(bwl)::value;
     if (small) return launch_sweep<T, B, 24, MODE, HR, HG>(g, a, s, max_ctas);
-    if (mid) return launch_sweep<T, B, 34, MODE, HR, HG>(g, a, s, max_ctas);
-    return launch_sweep<T, B, 66, MODE, HR, HG>(g, a, s, max_ctas);
+    return launch_sweep<T, B, 34, MODE, HR, HG>(g, a, s, max_ctas);
   };
   if (a.q <= 8) return pick(std::integral_constant<int, 8>{});
   if (a.q <= 16) return pick(std::integral_constant<int, 16>{});
@@ -380,9 +379,11 @@ template <typename T>
 bool ortho_ts_ok(const void* V, int ldv, int m0, int q) {
   // rows and the new block's first column on 16-byte boundaries, every
   // 16-byte vector that starts inside V0 or t inside the row
+  // the sweeps keep at most 34 coefficient or accumulator rows per lane
+  // (m0 + q + 1 in the FP64 Gram sweep); wider shapes take the persistent form
   const int w = 16 / (int)sizeof(T);
   return a16(V) && ((size_t)ldv * sizeof(T)) % 16 == 0 && m0 % w == 0 && q >= 1 && q <= 32 && m0 >= 0 &&
-         m0 + q <= 64 && ldv >= m0 + (q + w - 1) / w * w;
+         m0 + q + 1 <= 34 && ldv >= m0 + (q + w - 1) / w * w;
 }
 
 template <typename T>

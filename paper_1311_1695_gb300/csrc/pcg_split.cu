@@ -75,6 +75,8 @@ __global__ void k_pack_x(int n, const T* __restrict__ X, int ldx, T* __restrict_
 // while the current one is computed), so two buffers take the shared memory
 // one whole tile took.
 constexpr int kChunk = kTileRows / 2;
+// phase M stages six blocks: with 96-row units three CTAs fit an SM
+constexpr int kChunkM = 96;
 
 // Shared-memory layout of one split kernel (every region 16-byte aligned):
 // red (flushes and staged totals), two buffers of nstage staged blocks of
@@ -85,10 +87,12 @@ struct SplitSmem {
                                  ? kWarps * (BMAX + 3) * BWL
                                  : (BMAX + 1) * BMAX + 2 * BMAX;
   static constexpr int red_al = (red + 3) / 4 * 4;
-  __host__ __device__ static size_t body(int nstage, int ld) {
-    return sizeof(T) * ((size_t)red_al + 2 * (size_t)nstage * kChunk * ld + 2 * kChunk);
+  __host__ __device__ static size_t body(int nstage, int ld, int ch = kChunk) {
+    return sizeof(T) * ((size_t)red_al + 2 * (size_t)nstage * ch * ld + 2 * ch);
   }
-  __host__ __device__ static size_t bytes(int nstage, int ld) { return (body(nstage, ld) + 15) / 16 * 16 + 32; }
+  __host__ __device__ static size_t bytes(int nstage, int ld, int ch = kChunk) {
+    return (body(nstage, ld, ch) + 15) / 16 * 16 + 32;
+  }
 };
 
 // Row helpers over a staged row of stride ld (a multiple of the vector
@@ -156,19 +160,21 @@ __device__ __forceinline__ T dot_ld(const T* __restrict__ r, const T (&Gc)[BMAX 
 template <typename T, int BMAX, int BWL>
 struct Ctx {
   T* red;
-  T* stage;      // 2 buffers x nst blocks of kChunk x ld
-  T* s_deg;      // 2 x kChunk reciprocal degrees
+  T* stage;      // 2 buffers x nst blocks of ch x ld
+  T* s_deg;      // 2 x ch reciprocal degrees
+  int ch;        // rows of a unit
   unsigned long long* bar;  // [2]
   unsigned phase;           // bit u: the phase to wait for on buffer u
   int nst;
   unsigned long long policy;  // evict-first
-  __device__ void setup(unsigned char* smem, int nstage, int ld) {
+  __device__ void setup(unsigned char* smem, int nstage, int ld, int rows = kChunk) {
+    ch = rows;
     using L = SplitSmem<T, BMAX, BWL>;
     nst = nstage;
     red = reinterpret_cast<T*>(smem);
     stage = red + L::red_al;
-    s_deg = stage + 2 * (size_t)nstage * kChunk * ld;
-    bar = reinterpret_cast<unsigned long long*>(smem + (L::body(nstage, ld) + 15) / 16 * 16);
+    s_deg = stage + 2 * (size_t)nstage * ch * ld;
+    bar = reinterpret_cast<unsigned long long*>(smem + (L::body(nstage, ld, ch) + 15) / 16 * 16);
     phase = 0;
     policy = evict_first_policy();
     if (threadIdx.x == 0) {
@@ -177,8 +183,8 @@ struct Ctx {
     }
     __syncthreads();
   }
-  __device__ T* blk(int u, int i, int ld) { return stage + ((size_t)u * nst + i) * kChunk * ld; }
-  __device__ const T* deg(int u) const { return s_deg + u * kChunk; }
+  __device__ T* blk(int u, int i, int ld) { return stage + ((size_t)u * nst + i) * ch * ld; }
+  __device__ const T* deg(int u) const { return s_deg + u * ch; }
   // thread 0: copy rows [r0, r1) (at most kChunk) of the nb blocks src[i]
   // (row stride ldb[i]) into block i of buffer u (blocks whose bit is set in
   // keep are copied without the evict-first hint)
@@ -208,34 +214,7 @@ struct Ctx {
   // the reciprocal degrees of rows [r0, r1) into buffer u's slot (read after
   // its wait): one division per row instead of one per element of the row
   __device__ void degrees(int u, int r0, int r1, const T* deg_g) {
-    for (int i = threadIdx.x; i < r1 - r0; i += kThreads) s_deg[u * kChunk + i] = T(1) / deg_g[r0 + i];
-  }
-};
-
-// A CTA's units: its row tiles (tile blockIdx.x + j gridDim.x of the graphs
-// not skipped) in order, each cut into runs of at most kChunk rows.
-struct Unit {
-  int ti, r0, r1;
-  Tile t;
-  __device__ void load(const DevGraph& g, const int* skip) {
-    for (; ti < g.ntiles; ti += gridDim.x) {
-      t = g.tiles[ti];
-      if (!(skip && skip[t.seg])) break;
-    }
-    if (ti < g.ntiles) {
-      r0 = t.r0;
-      r1 = min(t.r1, r0 + kChunk);
-    }
-  }
-  __device__ bool valid(const DevGraph& g) const { return ti < g.ntiles; }
-  __device__ void next(const DevGraph& g, const int* skip) {
-    if (r1 < t.r1) {
-      r0 = r1;
-      r1 = min(t.r1, r0 + kChunk);
-    } else {
-      ti += gridDim.x;
-      load(g, skip);
-    }
+    for (int i = threadIdx.x; i < r1 - r0; i += kThreads) s_deg[u * ch + i] = T(1) / deg_g[r0 + i];
   }
 };
 
@@ -249,9 +228,9 @@ template <int NB, typename T, int BMAX, int BWL, typename Seg, typename Body>
 __device__ bool walk_units(Ctx<T, BMAX, BWL>& cx, const DevGraph& g, const int* skip, const T* const (&src)[NB],
                            const int (&ldb)[NB], int ld, unsigned keep, const T* deg_g, const GridBar& gb,
                            Seg&& on_seg, Body&& body) {
-  Unit u;
+  stg::Unit u;
   u.ti = blockIdx.x;
-  u.load(g, skip);
+  u.load(g, skip, cx.ch);
   if (!u.valid(g)) return true;
   cx.template issue<NB>(0, src, ldb, ld, u.r0, u.r1, keep);
   if (deg_g) cx.degrees(0, u.r0, u.r1, deg_g);
@@ -261,8 +240,8 @@ __device__ bool walk_units(Ctx<T, BMAX, BWL>& cx, const DevGraph& g, const int* 
       on_seg(u.t);
       seg = u.t.seg;
     }
-    Unit nx = u;
-    nx.next(g, skip);
+    stg::Unit nx = u;
+    nx.next(g, skip, cx.ch);
     const bool more = nx.valid(g);
     __syncthreads();  // the body of the unit before is done with buffer buf ^ 1
     if (more) {
@@ -412,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) k_split_m(DevGraph g, SplitView<T> s
     }
   }
   Ctx<T, BMAX, BWL> cx;
-  cx.setup(smem_raw, 6, ld);
+  cx.setup(smem_raw, 6, ld, kChunkM);
   constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int c = lane % BWL, grp = warp * RW + lane / BWL;
@@ -571,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_split_b(DevGraph g, SplitView<T
           }
           const T z = res * sdinv[il];
           __stcs(RES + o, res);
-          Z[o] = z;  // gathered by the next SpMM: normal priority
+          Z[o] = z;  // gathered by the next SpMM: normal priority (an evict-last hint measured no better)
           gram_ld<T, BMAX>(acc, sx + so, z, ld);
           ex[0] += res * z;
           ex[1] += res * res;
@@ -682,7 +661,7 @@ int split_launch(const DevGraph& g, const FusedPcg& f, cudaStream_t s, int max_c
   auto km = k_split_m<T, BMAX, BWL>;
   auto kb = k_split_b<T, BMAX, BWL>;
   auto kg = k_split_g2<T, BMAX, BWL>;
-  const size_t si = L::bytes(1, ld), sm = L::bytes(6, ld), sb = L::bytes(5, ld), sg = L::bytes(3, ld);
+  const size_t si = L::bytes(1, ld), sm = L::bytes(6, ld, kChunkM), sb = L::bytes(5, ld), sg = L::bytes(3, ld);
   const int gi = grid_of(reinterpret_cast<const void*>(ki), si);
   const int gm = grid_of(reinterpret_cast<const void*>(km), sm);
   const int gb = grid_of(reinterpret_cast<const void*>(kb), sb);
