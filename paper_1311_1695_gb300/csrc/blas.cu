@@ -268,6 +268,50 @@ __global__ void __launch_bounds__(kThreads) k_residual(DevGraph g, Reduce red, c
   }
 }
 
+// The same for blocks of at most 32 columns: a row group of BWL lanes
+// takes a row (lane c: column c), 32 / BWL rows per warp pass, and the
+// squares are summed in T within a tile (FP64 only across tiles: an FP32
+// block pays no FP64 conversion per element).
+template <typename T, int BWL>
+__global__ void __launch_bounds__(kThreads) k_residual_rows(DevGraph g, Reduce red, const T* __restrict__ X, int ldx,
+                                                            const T* __restrict__ LX, int ldlx,
+                                                            const double* __restrict__ theta, int64_t sth, T* R,
+                                                            int ldr, int q, double* norms2, int64_t so,
+                                                            const int* __restrict__ seg_skip) {
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  constexpr int RW = 32 / BWL;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, sub = lane / BWL;
+  const bool colok = c < q;
+  const T th = colok ? (T)theta[(size_t)t.seg * sth + c] : T(0);
+  T acc = T(0);
+  for (int r = t.r0 + warp * RW + sub; r < t.r1; r += (kThreads / 32) * RW) {
+    if (colok) {
+      const T v = LX[(size_t)r * ldlx + c] - th * X[(size_t)r * ldx + c];
+      if (R) R[(size_t)r * ldr + c] = v;
+      acc += v * v;
+    }
+  }
+#pragma unroll
+  for (int o = BWL; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red_s[kThreads / 32][32];
+  if (sub == 0) red_s[warp][c] = (double)acc;
+  __syncthreads();
+  __shared__ double colsum[32];
+  if (threadIdx.x < 32) {
+    double s2 = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) s2 += threadIdx.x < BWL ? red_s[w][threadIdx.x] : 0.0;
+    colsum[threadIdx.x] = s2;
+  }
+  __syncthreads();
+  double none[1] = {0.0};
+  if (commit<1>(red, t.seg, seg_tiles(g, t.seg), none, 0, colsum, q)) {
+    for (int cc = threadIdx.x; cc < q; cc += kThreads) norms2[(size_t)t.seg * so + cc] = total(red, t.seg, cc);
+    release(red, t.seg, q);
+  }
+}
+
 // ------------------------------------------------------------------ random start, convert
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
@@ -786,7 +830,11 @@ template <typename T>
 void residual(const DevGraph& g, const Reduce& red, const T* X, int ldx, const T* LX, int ldlx, const double* theta,
               int64_t sth, T* R, int ldr, int q, double* norms2, int64_t so, const int* seg_skip, cudaStream_t s) {
   LAP_PROF("residual", (double)sizeof(T) * g.n * (R ? 3 : 2) * q, s);
-  k_residual<T><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+  if (q <= 4) k_residual_rows<T, 4><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+  else if (q <= 8) k_residual_rows<T, 8><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+  else if (q <= 16) k_residual_rows<T, 16><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+  else if (q <= 32) k_residual_rows<T, 32><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
+  else k_residual<T><<<g.ntiles, kThreads, 0, s>>>(g, red, X, ldx, LX, ldlx, theta, sth, R, ldr, q, norms2, so, seg_skip);
 }
 
 void chol_inv(int nseg, int q, const double* S, int64_t ss, double drop, int absolute, double* Rinv, int64_t sr,

@@ -73,6 +73,7 @@ struct SweepArgs {
   const double* G;  // per graph (stride sg) (m0 + 1) x q, row 0 the mean coefficient, or null
   int64_t sg;
   int mfull;        // kFull: columns of block 0 in the product
+  int no_t;         // kWrite without t: x = -[1|V0] G (a rotation of V0)
   double* acc;      // per graph (stride sacc), zero at rest: rows of q values
   int64_t sacc;
   const int* seg_skip;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
           load_row<T, NV>(vrow, vr, MODE == kFull ? a.mfull : m0);
           T trow[HR ? BWL : W];
           if constexpr (HR) load_row<T, BWL>(trow, tr, q);
-          T x = colok ? tr[c] : T(0);
+          T x = (colok && !a.no_t) ? tr[c] : T(0);
           if constexpr (HR) {
             T s = T(0);
 #pragma unroll
@@ -326,6 +327,109 @@ __global__ void k_pyth_post(int m0, int q, int corr, double* R, int64_t sr, doub
   for (int e = threadIdx.x; e < q * q; e += blockDim.x) Rg[e] = Rn[e] - ((corr && e / q == e % q) ? 1.0 : 0.0);
 }
 
+// After sweep A (totals: rows 0..m0 = [1|V0]^T t, rows m0+1.. = t^T t):
+// D = diag(t^T t)^-1/2 (0 for a zero or non-finite norm), R = diag(D),
+// G = [1|V0]^T t D with row 0 divided by the graph's rows (the mean);
+// accumulators back to zero.
+__global__ void k_coef_a(int m0, int q, double* acc, int64_t sacc, double* R, int64_t sr, double* G, int64_t sg,
+                         const int* __restrict__ row0, const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* A = acc + (size_t)s * sacc;
+  __shared__ double d[32];
+  if (threadIdx.x < q) {
+    const double p = A[(size_t)(m0 + 1 + threadIdx.x) * q + threadIdx.x];
+    d[threadIdx.x] = (p > 0.0 && isfinite(p)) ? 1.0 / sqrt(p) : 0.0;
+  }
+  __syncthreads();
+  const double inv_n = 1.0 / (double)(row0[s + 1] - row0[s]);
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) R[(size_t)s * sr + e] = (e / q == e % q) ? d[e / q] : 0.0;
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x) {
+    const double v = A[e] * d[e % q];
+    G[(size_t)s * sg + e] = e < q ? v * inv_n : v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < (m0 + 1 + q) * q; e += blockDim.x) A[e] = 0.0;
+}
+
+// After sweep B (totals of x = (t - Q c1) D: rows 0..m0 = [1|V0]^T x, rows
+// m0+1.. = x^T x): S = x^T x, the exact Gram matrix of the projected block;
+// G = [1|V0]^T x (row 0 the column sums) or zero (zero_g); accumulators back
+// to zero.
+__global__ void k_cholqr_pre(int m0, int q, int zero_g, double* acc, int64_t sacc, double* S, int64_t ss, double* G,
+                             int64_t sg, const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* A = acc + (size_t)s * sacc;
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) S[(size_t)s * ss + e] = A[(size_t)(m0 + 1) * q + e];
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x) G[(size_t)s * sg + e] = zero_g ? 0.0 : A[e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < (m0 + 1 + q) * q; e += blockDim.x) A[e] = 0.0;
+}
+
+// With R1^-1 (R, from chol_inv of x^T x): x1 = x R1^-1 has orthonormal
+// columns; its coefficients on Q are c2 = [colsum(x1)/sqrt(n); V0^T x1] =
+// G R1^-1 (row 0 scaled), and the second pass's Gram matrix is
+// S = I - c2^T c2 (nothing cancels: x1 is orthogonal to Q to working
+// precision).  G <- G R1^-1 (row 0 still a column sum).
+__global__ void k_cholqr_mid(int m0, int q, const double* R, int64_t sr, double* G, int64_t sg, double* S, int64_t ss,
+                             const int* __restrict__ row0, const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  const double* Rg = R + (size_t)s * sr;
+  double* Gg = G + (size_t)s * sg;
+  __shared__ double C[65 * 32];
+  const double inv_sqrt_n = 1.0 / sqrt((double)(row0[s + 1] - row0[s]));
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x) {
+    const int i = e / q, c = e - i * q;
+    double v = 0.0;
+    for (int j = 0; j <= c; ++j) v += Gg[(size_t)i * q + j] * Rg[(size_t)j * q + c];
+    C[e] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    const int j = e / q, c = e - j * q;
+    double v = (j == c) ? 1.0 : 0.0;
+    v -= C[j] * C[c] * inv_sqrt_n * inv_sqrt_n;
+    for (int i = 1; i <= m0; ++i) v -= C[i * q + j] * C[i * q + c];
+    S[(size_t)s * ss + e] = v;
+  }
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x) Gg[e] = C[e];
+}
+
+// Final coefficients x'' = x R - [1|V0] G of the second pass, from R1^-1 (R)
+// and R2^-1 (R2): R <- R1^-1 R2^-1, G <- G R2^-1 with row 0 divided by the
+// graph's rows (the mean).
+__global__ void k_cholqr_post(int m0, int q, double* R, int64_t sr, const double* R2, int64_t sr2, double* G,
+                              int64_t sg, const int* __restrict__ row0, const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  double* Rg = R + (size_t)s * sr;
+  const double* R2g = R2 + (size_t)s * sr2;
+  double* Gg = G + (size_t)s * sg;
+  __shared__ double Rn[32 * 32];
+  constexpr int kMaxOut = 65 * 32 / 256 + 1;
+  double out[kMaxOut];
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+    const int j = e / q, c = e - j * q;
+    double v = 0.0;
+    for (int l = j; l <= c; ++l) v += Rg[(size_t)j * q + l] * R2g[(size_t)l * q + c];
+    Rn[e] = v;
+  }
+  const double inv_n = 1.0 / (double)(row0[s + 1] - row0[s]);
+  int n = 0;
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x, ++n) {
+    const int i = e / q, c = e - i * q;
+    double v = 0.0;
+    for (int j = 0; j <= c; ++j) v += Gg[(size_t)i * q + j] * R2g[(size_t)j * q + c];
+    out[n] = i == 0 ? v * inv_n : v;
+  }
+  __syncthreads();
+  n = 0;
+  for (int e = threadIdx.x; e < (m0 + 1) * q; e += blockDim.x, ++n) Gg[e] = out[n];
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) Rg[e] = Rn[e];
+}
+
 // ---------------------------------------------------------------- launches
 template <typename T, int BWL, int M0B, int MODE, bool HR, bool HG>
 int launch_sweep(const DevGraph& g, const SweepArgs& a, cudaStream_t s, int max_ctas) {
@@ -397,14 +501,18 @@ int ortho_ts(const DevGraph& g, const OrthoTs& w, T* V, int ldv, int m0, int q, 
   a.ldo = ldv;
   a.R = w.R; a.sr = w.sr; a.G = w.G; a.sg = w.sg;
   int rc = 0;
-  // A: G1 and P1 of the raw block
+  // A: G1 = [1|V0]^T t and the column norms
   rc |= sweep_m<T, kGram, false, false>(g, a, s, w.max_ctas);
-  pyth_step(g, w, m0, q, 1, drop1, w.keep1, f32, 0, s);
-  // B: x = (t - Q c1) D R1^-1 written, G2 and P2
+  k_coef_a<<<g.nseg, 256, 0, s>>>(m0, q, w.acc, w.sacc, w.R, w.sr, w.G, w.sg, g.row0, w.seg_skip);
+  // B: x = (t - Q c1) D written; [1|V0]^T x and x^T x
   a.out = V + m0;
   rc |= sweep_m<T, kGram, true, true>(g, a, s, w.max_ctas);
-  pyth_step(g, w, m0, q, 0, 0.25, w.keep2, f32, 0, s);
-  // C: x <- (x - Q c2) R2^-1
+  k_cholqr_pre<<<g.nseg, 256, 0, s>>>(m0, q, 0, w.acc, w.sacc, w.S, w.ss, w.G, w.sg, w.seg_skip);
+  chol_inv(g.nseg, q, w.S, w.ss, drop1, 1, w.R, w.sr, w.keep1, w.seg_skip, s, f32);
+  k_cholqr_mid<<<g.nseg, 256, 0, s>>>(m0, q, w.R, w.sr, w.G, w.sg, w.S, w.ss, g.row0, w.seg_skip);
+  chol_inv(g.nseg, q, w.S, w.ss, 0.25, 1, w.R2, w.sr, w.keep2, w.seg_skip, s, f32);
+  k_cholqr_post<<<g.nseg, 256, 0, s>>>(m0, q, w.R, w.sr, w.R2, w.sr, w.G, w.sg, g.row0, w.seg_skip);
+  // C: x <- (x R1^-1 - Q c2) R2^-1
   rc |= sweep_m<T, kWrite, true, true>(g, a, s, w.max_ctas);
   and_flags(g.nseg * 64, w.keep1, w.keep2, s);
   return rc ? -1 : 0;
@@ -421,10 +529,14 @@ int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int 
   a.acc = w.acc; a.sacc = w.sacc; a.seg_skip = w.seg_skip; a.bar = w.bar;
   a.R = w.R; a.sr = w.sr; a.G = w.G; a.sg = w.sg;
   int rc = 0;
-  // FP32 pass on the correction block: G1, P1; t <- (t - Q c1) D R1^-1
+  // FP32 pass on the correction block: G1 and the norms; x = (t - Q c1) D
+  // written with its Gram matrix; t <- x R1^-1
   rc |= sweep_m<float, kGram, false, false>(g, a, s, w.max_ctas);
-  pyth_step(g, w, m0, q, 1, drop1, w.keep1, true, 0, s);
+  k_coef_a<<<g.nseg, 256, 0, s>>>(m0, q, w.acc, w.sacc, w.R, w.sr, w.G, w.sg, g.row0, w.seg_skip);
   a.out = Tt; a.ldo = ldt;
+  rc |= sweep_m<float, kGram, true, true>(g, a, s, w.max_ctas);
+  k_cholqr_pre<<<g.nseg, 256, 0, s>>>(m0, q, 1, w.acc, w.sacc, w.S, w.ss, w.G, w.sg, w.seg_skip);
+  chol_inv(g.nseg, q, w.S, w.ss, drop1, 1, w.R, w.sr, w.keep1, w.seg_skip, s, true);
   rc |= sweep_m<float, kWrite, true, true>(g, a, s, w.max_ctas);
   // into the FP64 basis
   convert<float, double>(g, Tt, ldt, V + m0, ldv, q, s);
@@ -457,6 +569,31 @@ int ortho_ts_refine(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int
   a.out = V; a.ldo = ldv; a.out64 = 1;
   rc |= sweep_m<float, kWrite, true, true>(g, a, s, w.max_ctas);
   return rc ? -1 : 0;
+}
+
+// G for a rotation: row 0 (the ones column) zero, rows 1..m the negated Y
+// (m x mk, row stride ldy, graph stride sy), so that -[1|V] G = V Y.
+__global__ void k_rot_coef(int m, int mk, const double* __restrict__ Y, int ldy, int64_t sy, double* G, int64_t sg,
+                           const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (seg_skip && seg_skip[s]) return;
+  for (int e = threadIdx.x; e < (m + 1) * mk; e += blockDim.x) {
+    const int i = e / mk, c = e - i * mk;
+    G[(size_t)s * sg + e] = i == 0 ? 0.0 : -Y[(size_t)s * sy + (size_t)(i - 1) * ldy + c];
+  }
+}
+
+int rotate_ts(const DevGraph& g, const OrthoTs& w, float* V, int ldv, int m, int mk, const double* Y, int ldy,
+              int64_t sy, cudaStream_t s) {
+  LAP_PROF("update", 4.0 * (double)g.n * (m + mk), s);
+  if (!a16(V) || ((size_t)ldv * sizeof(float)) % 16 != 0 || m + 1 > 34 || mk < 1 || mk > 32 || ldv < (m + 3) / 4 * 4)
+    return 1;
+  k_rot_coef<<<g.nseg, 256, 0, s>>>(m, mk, Y, ldy, sy, w.G, w.sg, w.seg_skip);
+  SweepArgs a{};
+  a.Qb = V; a.ldq = ldv; a.m0 = m; a.Tb = nullptr; a.toff = 0; a.q = mk; a.no_t = 1;
+  a.out = V; a.ldo = ldv; a.G = w.G; a.sg = w.sg;
+  a.acc = w.acc; a.sacc = w.sacc; a.seg_skip = w.seg_skip; a.bar = w.bar;
+  return sweep_m<float, kWrite, false, true>(g, a, s, w.max_ctas) ? -1 : 0;
 }
 
 template bool ortho_ts_ok<float>(const void*, int, int, int);

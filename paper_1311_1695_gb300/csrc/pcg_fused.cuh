@@ -61,6 +61,7 @@ struct OrthoTs {
   double* R; int64_t sr;      // q x q coefficients per graph
   double* G; int64_t sg;      // (m0 + 1) x q coefficients per graph
   double* S; int64_t ss;      // q x q Gram matrix per graph
+  double* R2;                 // q x q per graph (stride sr): the second pass's R^-1
   int* keep1;                 // [nseg * 64] columns kept by pass 1 (then by both)
   int* keep2;                 // [nseg * 64] columns kept by pass 2
   const int* seg_skip;
@@ -85,6 +86,11 @@ int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int 
 // orthogonal to e; keep1 = the columns kept.  Returns 0, 1 or -1.
 int ortho_ts_refine(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int q, const float* T32, int ld32,
                     cudaStream_t s);
+// V[:, 0:mk] <- V[:, 0:m] Y (FP32 basis; Y per graph m x mk, FP64, row stride
+// ldy, graph stride sy) as one streaming sweep, in place.  Returns 0, 1 (shapes
+// not supported: nothing launched) or -1.
+int rotate_ts(const DevGraph& g, const OrthoTs& w, float* V, int ldv, int m, int mk, const double* Y, int ldy,
+              int64_t sy, cudaStream_t s);
 constexpr int kOrthoTsAcc = 66 * 32;
 
 // Launch the whole correction solve (the per-phase form for graphs of at

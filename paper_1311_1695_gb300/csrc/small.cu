@@ -242,6 +242,20 @@ __global__ void k_copy_out(const Tile* tiles, const T* X, int ldx, int k, const 
 
 }  // namespace
 
+__global__ void k_guard_shifts(int nseg, const double* __restrict__ theta, int64_t st, int b, int kall,
+                               const int* __restrict__ kseg, double* shift, const int* __restrict__ seg_skip) {
+  const int s = blockIdx.x;
+  if (s >= nseg || (seg_skip && seg_skip[s])) return;
+  const int k = kseg ? kseg[s] : kall;
+  for (int c = threadIdx.x; c < b; c += blockDim.x)
+    shift[(size_t)s * 64 + c] = (c == b - 1 && b - 1 >= k) ? 0.0 : theta[(size_t)s * st + c];
+}
+void guard_shifts(int nseg, const double* theta, int64_t st, int b, int kall, const int* kseg, double* shift,
+                  const int* seg_skip, cudaStream_t s) {
+  LAP_PROF("small", 0.0, s);
+  k_guard_shifts<<<nseg, 64, 0, s>>>(nseg, theta, st, b, kall, kseg, shift, seg_skip);
+}
+
 void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);
   k_inv_sqrt<<<(count + 255) / 256, 256, 0, s>>>(count, in, out, floor_v);

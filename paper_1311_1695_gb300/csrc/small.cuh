@@ -5,6 +5,15 @@
 namespace lapeig {
 
 void inv_sqrt(int count, const double* in, double* out, double floor_v, cudaStream_t s);
+// Shifts of the correction equations: shift[s * 64 + c] = theta[s * st + c]
+// for c < b - 1 and 0 for the last column c = b - 1 when it is a guard
+// column (b - 1 >= the graph's wanted pairs): that column's correction
+// solves the projected (L - 0) t = -r, an inverse-iteration step on the
+// complement of [e, X] that draws in an eigenvalue below the Ritz block's
+// (one the start space missed), where a shift at its own Ritz value would
+// only refine the guard.
+void guard_shifts(int nseg, const double* theta, int64_t st, int b, int kall, const int* kseg, double* shift,
+                  const int* seg_skip, cudaStream_t s);
 void h_restart(int nseg, double* H, int ldh, int64_t sh, int mmax, const double* theta, int64_t st, int mk,
                const int* seg_skip, cudaStream_t s);
 // The restart's projected matrix of the rotated basis V Y[:, 0:mk] taken

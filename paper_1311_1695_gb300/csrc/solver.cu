@@ -183,6 +183,8 @@ struct JD {
   int ld32 = 0;
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
+  double* R2b;  // second R^-1 of the streaming orthonormalisation
+  double* shifts;  // [S][64] shifts of the correction equations
   int *keep1, *keep2, *active, *seg_skip, *sweeps;
   double* oacc;  // accumulators of the fused orthonormalisation
   // host mirrors
@@ -246,6 +248,8 @@ struct JD {
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
+    add(S * 64 * 64 * 8);
+    add(S * 64 * 8);
     for (int i = 0; i < 5; ++i) add(S * 64 * 4);
     add(S * 4); add(S * 8); add(sizeof(JdStatus)); add(S * 8);
     add(ortho_acc_doubles((int)S) * 8);
@@ -279,6 +283,8 @@ struct JD {
     Gm = a.take<double>(S * 65 * 64);
     Sm = a.take<double>(S * 64 * 64);
     Rinv = a.take<double>(S * 64 * 64);
+    R2b = a.take<double>(S * 64 * 64);
+    shifts = a.take<double>(S * 64);
     scale = a.take<double>(S * 64);
     tmp = a.take<double>(S * 64);
     keep1 = a.take<int>(S * 64);
@@ -306,7 +312,7 @@ struct JD {
   // persistent one; the step-level sequence below is the fallback.
   bool large() const { return g.n >= (pw->split_rows > 0 ? pw->split_rows : kSplitRows); }
   OrthoTs ortho_work() const {
-    return OrthoTs{oacc, kOrthoTsAcc, Rinv, 64 * 64, Gm, 65 * 64, Sm, 64 * 64, keep1, keep2, seg_skip, pw->gridbar(),
+    return OrthoTs{oacc, kOrthoTsAcc, Rinv, 64 * 64, Gm, 65 * 64, Sm, 64 * 64, R2b, keep1, keep2, seg_skip, pw->gridbar(),
                    pw->max_ctas};
   }
   void ortho(int m0, int q, double drop1) {
@@ -378,7 +384,13 @@ struct JD {
     const int mk = std::min(m, z.mk);
     syev(z.nseg, m, H, z.mmax, (int64_t)z.mmax * z.mmax, theta, z.mmax, Y, z.mmax, (int64_t)z.mmax * z.mmax,
          seg_skip, sweeps, st, mk);
-    update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
+    bool rotated = false;
+    if constexpr (std::is_same<TV, float>::value) {  // large graphs: one streaming sweep (ortho_ts.cu)
+      if (large())
+        rotated = rotate_ts(g, ortho_work(), V, z.ldv, m, mk, Y, z.mmax, (int64_t)z.mmax * z.mmax, st) == 0;
+    }
+    if (!rotated)
+      update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     // W[:, 0:b] = L V[:, 0:b] by one SpMM of the Ritz block instead of the
     // rotation W <- W Y of all m columns: the residuals read only these b
     // columns and the next border only L T, and at b columns one SpMM moves
@@ -447,7 +459,9 @@ struct JD {
       R = Rp; ldr = z.ldb;
     }
     // single graph: the solve stops once every active column met delta
-    FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, theta, z.mmax, active, seg_skip,
+    // the last guard column's correction targets the bottom of the spectrum (guard_shifts)
+    guard_shifts(z.nseg, theta, z.mmax, z.b, z.k, kseg_d, shifts, seg_skip, st);
+    FusedPcg f = pw->args(X, ldx, R, ldr, Tt, RES, Zb, P, AP, LXb, z.ldb, z.ldb, z.b, shifts, 64, active, seg_skip,
                           delta, itmax, G->d_long_seg);
     f.early_exit = 1;
     f.Xsv = Xs;
@@ -841,7 +855,7 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
     jd.kseg_d = kseg_d;
     jd.ev_rtol = P.ev_rtol;
     jd.theta_rel = P.theta_rel;
-    int m = jd.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
+    int m = jd.start(nullptr, 0, z.mk, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-20, x0d, ldx0, k0);
     int m_out = m;
     const int status = iterate(jd, m, P, tol_abs, true, outer, m_out, 1e-20, 1 << 30, o.cuda_graph >= 0);
     if (status < 0 && status != LAP_ETIMEOUT) return status;
@@ -858,7 +872,11 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   j1.pw = &pw;
   j1.kseg_d = kseg_d;
   j1.theta_rel = P.theta_rel;
-  int m = j1.start(nullptr, 0, z.b, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
+  // the first basis holds m_keep start columns, not only the b of the block:
+  // a wider random start is far less likely to miss the direction of a
+  // well-separated smallest eigenvalue, which the shift-targeted corrections
+  // would not bring back
+  int m = j1.start(nullptr, 0, z.mk, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
   std::vector<double> tol1(S);
   for (int s = 0; s < S; ++s) tol1[s] = std::max(P.tol_floor, 2e-6) * G->norm1[s];
   int m_out = m;
