@@ -541,6 +541,55 @@ __device__ __forceinline__ void small_gemm(int ni, int nj, int nl, const double*
   }
 }
 
+// Eigen-decomposition of a small symmetric c x c matrix B (row-major, in
+// place) by cyclic Jacobi in FP64, one thread: U (identity on entry)
+// accumulates the rotations, lam receives the eigenvalues in ascending order
+// with U's columns permuted to match.  Rotation of a pair (p, q): tau =
+// (b_qq - b_pp) / (2 b_pq), t = sign(tau) / (|tau| + sqrt(1 + tau^2)) (the
+// smaller root), c = 1 / sqrt(1 + t^2), s = t c.
+__device__ void small_jacobi(double* B, double* U, int c, double* lam) {
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < c; ++p)
+      for (int q = 0; q < c; ++q) (p == q ? dia : off) += B[p * c + q] * B[p * c + q];
+    if (!(off > 1e-34 * dia)) break;
+    for (int p = 0; p < c - 1; ++p)
+      for (int q = p + 1; q < c; ++q) {
+        const double bpq = B[p * c + q];
+        if (bpq == 0.0) continue;
+        const double tau = (B[q * c + q] - B[p * c + p]) / (2.0 * bpq);
+        const double t = fabs(tau) > 1e150 ? 0.5 / tau : (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < c; ++k) {  // columns p, q of B
+          const double bp = B[k * c + p], bq = B[k * c + q];
+          B[k * c + p] = cs * bp - sn * bq;
+          B[k * c + q] = sn * bp + cs * bq;
+        }
+        for (int k = 0; k < c; ++k) {  // rows p, q of B
+          const double bp = B[p * c + k], bq = B[q * c + k];
+          B[p * c + k] = cs * bp - sn * bq;
+          B[q * c + k] = sn * bp + cs * bq;
+        }
+        for (int k = 0; k < c; ++k) {  // columns p, q of U
+          const double up = U[k * c + p], uq = U[k * c + q];
+          U[k * c + p] = cs * up - sn * uq;
+          U[k * c + q] = sn * up + cs * uq;
+        }
+      }
+  }
+  // ascending order: selection sort of the diagonal, U's columns alike
+  for (int i = 0; i < c; ++i) {
+    int best = i;
+    for (int j = i + 1; j < c; ++j)
+      if (B[j * c + j] < B[best * c + best]) best = j;
+    if (best != i) {
+      const double t = B[i * c + i]; B[i * c + i] = B[best * c + best]; B[best * c + best] = t;
+      for (int k = 0; k < c; ++k) { const double u = U[k * c + i]; U[k * c + i] = U[k * c + best]; U[k * c + best] = u; }
+    }
+    lam[i] = B[i * c + i];
+  }
+}
+
 // Symmetric eigensolver for m <= 64, FP64 result, one CTA per matrix.
 // GB300 issues FP32 about 58x faster than FP64, so the sweeps run in FP32 on
 // fl32(H) (jacobi2s: eigenvectors to about 1e-7), and FP64 finishes:
@@ -700,6 +749,8 @@ __global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__
   __syncthreads();
   for (int j = tid; j < m; j += NT) lam[j] = lam_s[j];
   __syncthreads();
+  __shared__ int s_link[64];  // s_link[i]: refined columns i and i + 1 share a cluster
+  for (int i = tid; i < 64; i += NT) s_link[i] = 0;
   if (nr > 0) {
     double* Z = W;               // m x LR (overwrites the FP32 arrays)
     double* S = Z + m * LR;
@@ -727,6 +778,8 @@ __global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__
       if (i != j) {
         const double num = S[i * LR + j] + lam[j] * R[i * LR + j], gap = lam[j] - lam[i];
         if (fabs(num) < 1e-3 * fabs(gap)) ev_ = num / gap;  // strict: equal Ritz values (gap 0) are a cluster, not 0/0
+        else if (i < nr)
+          for (int l = min(i, j); l < max(i, j); ++l) s_link[l] = 1;  // every writer stores 1
       }
       S[i * LR + j] = ev_;
     }
@@ -764,6 +817,51 @@ __global__ void __launch_bounds__(1024) k_syev(int m, const double* __restrict__
     }
     for (int e = tid; e < m * nr; e += NT) X[(e / nr) * LM + (e % nr)] = Xn[(e / nr) * LR + (e % nr)];
     __syncthreads();
+    // Clusters: a run [a, e] of refined columns linked above spans their
+    // invariant subspace to FP64 accuracy but is mixed inside it at the FP32
+    // level (angle ~ eps32 ||H|| / gap), which leaves the Ritz vectors of
+    // close eigenvalues with residuals ~ gap * angle that no correction
+    // removes.  Resolve each run of at most kClus columns exactly:
+    // B = X_C^T H X_C in FP64, cyclic Jacobi on B (one thread, c <= kClus),
+    // X_C <- X_C U, the cluster's values from diag(U^T B U), ascending.
+    constexpr int kClus = 8;
+    for (int a = 0; a < nr;) {
+      int e = a;
+      while (e + 1 < nr && s_link[e]) ++e;
+      const int c = e - a + 1;
+      if (c >= 2 && c <= kClus) {
+        double* Zc = Z;              // m x c: H X_C
+        double* Bc = R;              // c x c
+        double* Uc = R + kClus * kClus;
+        for (int q = tid; q < m * c; q += NT) {
+          const int r = q / c, jj = q - r * c;
+          double t = 0.0;
+          for (int i = 0; i < m; ++i) t = fma(Hs[r * LM + i], X[i * LM + a + jj], t);
+          Zc[q] = t;
+        }
+        __syncthreads();
+        for (int q = tid; q < c * c; q += NT) {
+          const int ii = q / c, jj = q - ii * c;
+          double t = 0.0;
+          for (int r = 0; r < m; ++r) t = fma(X[r * LM + a + ii], Zc[r * c + jj], t);
+          Bc[q] = t;
+          Uc[q] = ii == jj ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (tid == 0) small_jacobi(Bc, Uc, c, lam + a);
+        __syncthreads();
+        for (int q = tid; q < m * c; q += NT) {  // X_C U into Zc, then back
+          const int r = q / c, jj = q - r * c;
+          double t = 0.0;
+          for (int i = 0; i < c; ++i) t = fma(X[r * LM + a + i], Uc[i * c + jj], t);
+          Zc[q] = t;
+        }
+        __syncthreads();
+        for (int q = tid; q < m * c; q += NT) X[(q / c) * LM + a + (q % c)] = Zc[q];
+        __syncthreads();
+      }
+      a = e + 1;
+    }
   }
   for (int j = tid; j < m; j += NT) ev[j] = lam[j];
   for (int e = tid; e < m * m; e += NT) {

@@ -113,21 +113,47 @@ __global__ void k_and(int count, int* a, const int* b) {
 }
 
 // Eigenvalue accuracy of Ritz pair j (Kato-Temple): a Ritz value theta_j
-// with residual norm r lies within r^2 / delta of an eigenvalue, delta the
-// distance from theta_j to the rest of the spectrum, here estimated by the
-// nearest other Ritz value of the basis that is farther than r (closer ones
-// are the same eigenvalue within the residual).  Accurate when that bound is
-// at most ev_rtol * max(|theta_j|, tol_abs).  Shared by the device
-// bookkeeping and the host's explicit check.
-__host__ __device__ inline bool ev_accurate(const double* th, int nrv, int j, double r, double tol_abs,
-                                            double ev_rtol) {
+// with residual norm r_j lies within r_j^2 / delta of an eigenvalue, delta
+// the distance from theta_j to the rest of the spectrum, here estimated by
+// the nearest other Ritz value of the basis that is farther than r_j (closer
+// ones are the same eigenvalue within the residual).  For a Ritz value with
+// a close neighbour that bound is weak, so clusters are tried too: for a
+// run J = [lo, hi] of consecutive Ritz values around j, grown towards the
+// nearer neighbour, the quadratic residual bound of a Ritz cluster puts
+// every theta_i of J within ||R_J||_2^2 / delta_J of an eigenvalue, with
+// ||R_J||_2^2 <= sum_{i in J} r_i^2 and delta_J the distance from
+// [theta_lo, theta_hi] to the nearest Ritz value outside J.  Only columns
+// with a residual (i < nr) join a cluster.  Accurate when one of the bounds
+// is at most ev_rtol * max(|theta_j|, tol_abs).  Shared by the device
+// bookkeeping and the host's explicit check; rn2 holds squared norms
+// (rounding below zero counts as 0, NaN fails every test).
+__host__ __device__ inline bool ev_accurate(const double* th, int nrv, const double* rn2, int nr, int j,
+                                            double tol_abs, double ev_rtol) {
+  constexpr int kMaxCluster = 8;
+  const double lim = ev_rtol * fmax(fabs(th[j]), tol_abs);
+  const double r2j = rn2[j] > 0.0 ? rn2[j] : (rn2[j] <= 0.0 ? 0.0 : rn2[j]);
+  const double r = sqrt(r2j);
   double delta = HUGE_VAL;
   for (int i = 0; i < nrv; ++i) {
     const double d = fabs(th[i] - th[j]);
     if (i != j && d > r && d < delta) delta = d;
   }
-  const double scale = fmax(fabs(th[j]), tol_abs);
-  return r * r <= ev_rtol * scale * delta;
+  if (r2j <= lim * delta) return true;
+  int lo = j, hi = j;
+  double sum2 = r2j;
+  for (int size = 2; size <= kMaxCluster; ++size) {
+    const double gl = lo > 0 ? th[lo] - th[lo - 1] : HUGE_VAL;
+    const double gh = hi + 1 < nrv ? th[hi + 1] - th[hi] : HUGE_VAL;
+    const bool can_l = lo > 0 && lo - 1 < nr, can_h = hi + 1 < nr && hi + 1 < nrv;
+    if (!can_l && !can_h) break;
+    const int add = (can_l && (!can_h || gl <= gh)) ? --lo : ++hi;
+    const double r2a = rn2[add] > 0.0 ? rn2[add] : (rn2[add] <= 0.0 ? 0.0 : rn2[add]);
+    sum2 += r2a;
+    const double dl = lo > 0 ? th[lo] - th[lo - 1] : HUGE_VAL;
+    const double dh = hi + 1 < nrv ? th[hi + 1] - th[hi] : HUGE_VAL;
+    if (sum2 <= lim * fmin(dl, dh)) return true;
+  }
+  return false;
 }
 
 // One CTA; a warp per graph (lane j = column j, b <= 32), warp reductions,
@@ -160,7 +186,7 @@ __global__ void k_converge(int nseg, const double* __restrict__ rn2, const doubl
         fin = isfinite(r) && isfinite(th[j]);
         const double thr = pair_threshold(tol_abs[s], theta_rel, th[j]);
         c = r <= thr && th[j] <= norm1[s];
-        if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, j, r, thr, ev_rtol);
+        if (c && ev_rtol > 0.0) c = ev_accurate(th, nrv, rn2 + (size_t)s * 64, b, j, thr, ev_rtol);
         ratio = j < k ? r / thr : 0.0;
         active[(size_t)s * 64 + j] = (j < k && c) ? 0 : 1;
       }
@@ -284,8 +310,8 @@ void converge(int nseg, const double* rn2, const double* theta, int mmax, const 
                                explicit_check, state, active, skip, bar, status, segw);
 }
 
-bool ev_accurate_host(const double* th, int nrv, int j, double r, double tol_abs, double ev_rtol) {
-  return ev_rtol <= 0.0 || ev_accurate(th, nrv, j, r, tol_abs, ev_rtol);
+bool ev_accurate_host(const double* th, int nrv, const double* rn2, int nr, int j, double tol_abs, double ev_rtol) {
+  return ev_rtol <= 0.0 || ev_accurate(th, nrv, rn2, nr, j, tol_abs, ev_rtol);
 }
 void and_flags(int count, int* a, const int* b, cudaStream_t s) {
   LAP_PROF("small", 0.0, s);

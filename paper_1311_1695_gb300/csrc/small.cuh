@@ -60,9 +60,10 @@ __host__ __device__ inline double pair_threshold(double tol_abs, double theta_re
   return theta_rel > 0.0 ? fmax(theta_rel * fabs(theta), tol_abs) : tol_abs;
 }
 // Pair j's Ritz value is within ev_rtol * max(|theta_j|, tol_abs) of an
-// eigenvalue by the Kato-Temple bound r^2 / delta, delta from the other
-// Ritz values th[0:nrv] (always true for ev_rtol <= 0).
-bool ev_accurate_host(const double* th, int nrv, int j, double r, double tol_abs, double ev_rtol);
+// eigenvalue by the Kato-Temple bound r_j^2 / delta or the quadratic bound
+// of a cluster of neighbouring Ritz values, gaps from the other Ritz values
+// th[0:nrv], squared residual norms rn2[0:nr] (always true for ev_rtol <= 0).
+bool ev_accurate_host(const double* th, int nrv, const double* rn2, int nr, int j, double tol_abs, double ev_rtol);
 // best: device scratch of 2 * nseg * k 64-bit words.
 template <typename T>
 void copy_out(const DevGraph& g, const T* X, int ldx, int k, unsigned long long* best, double* out, cudaStream_t s);

@@ -585,7 +585,8 @@ int iterate(JD<TV, TP>& jd, int m, const Params& P, const std::vector<double>& t
             const double r = res_norm(jd.rn2_h[(size_t)s * 64 + j]);
             const double* th = jd.theta_h.data() + (size_t)s * jd.z.mmax;
             const double thr = pair_threshold(tol_abs[s], jd.theta_rel, th[j]);
-            const bool c = r <= thr && th[j] <= jd.G->norm1[s] && ev_accurate_host(th, jd.nrv, j, r, thr, jd.ev_rtol);
+            const bool c = r <= thr && th[j] <= jd.G->norm1[s] &&
+                             ev_accurate_host(th, jd.nrv, jd.rn2_h.data() + (size_t)s * 64, jd.z.b, j, thr, jd.ev_rtol);
             segc = segc && c;
             act[(size_t)s * 64 + j] = c ? 0 : 1;
           }
@@ -721,7 +722,7 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
       const bool real = th[j] <= G->norm1[s];
       worst = std::max(worst, real ? r : 1.0);
       const double thr = pair_threshold(P.tol_floor * G->norm1[s], P.theta_rel, th[j]);
-      const bool acc = ev_accurate_host(th, jd.nrv, j, ra, thr, P.ev_rtol);
+      const bool acc = ev_accurate_host(th, jd.nrv, jd.rn2_h.data() + (size_t)s * 64, jd.z.b, j, thr, P.ev_rtol);
       if (prefix && real && ra <= thr && acc) ++nconv; else prefix = false;
     }
     in.n_converged = nconv;
