@@ -46,7 +46,7 @@ WORKLOAD_TEXT = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5", choices=list(WORKLOAD_TEXT))
@@ -456,7 +456,9 @@ def bench_ours(args):
                    "k": k, "tol": 1e-8, "precision": args.precision, "method": "block Jacobi-Davidson",
                    "l2": "flushed before each step (256 MiB write)",
                    "parallelism": (f"graphs sharded by nnz x{world}" if args.workload == "c4" else f"replicas x{world}"),
-                   "outer_iteration": "eager" if args.no_graph else "CUDA graph replay"},
+                   "outer_iteration": "eager" if args.no_graph else "CUDA graph replay",
+                   "node_order": ("solver copy by decreasing degree" if len(graphs) == 1 and n >= 100000
+                                  else "as numbered")},
         "result": {"outer_its": inf["outer_its"], "phase1_outer": inf["phase1_outer"], "n_matvec": inf["n_matvec"],
                    "max_rel_residual": max(i_["max_rel_residual"] for i_ in infos_all),
                    "lambda_2": float(ev[0][0]), "lambda_k+1": float(ev[0][k - 1]),

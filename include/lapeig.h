@@ -58,6 +58,8 @@ typedef enum { LAP_JD = 0, LAP_DACG = 1, LAP_IRLM = 2 } lap_method;
 typedef enum { LAP_PREC_FP64 = 0, LAP_PREC_MIXED = 1 } lap_precision;
 typedef enum { LAP_F64 = 0, LAP_F32 = 1 } lap_dtype;
 typedef enum { LAP_PRECOND_JACOBI = 0, LAP_PRECOND_FSAI = 1 } lap_precond;
+/* Node order of the solves on a handle (lap_graph_set_reorder). */
+typedef enum { LAP_REORDER_AUTO = -1, LAP_REORDER_NONE = 0, LAP_REORDER_DEGREE = 1 } lap_reorder;
 
 /* Stop test of a pair (lap_opts.tol_mode). */
 typedef enum {
@@ -226,6 +228,21 @@ int lap_graph_set_precond(lap_graph* g, int kind, double alpha);
  * used when rows are at most 64 bytes and strides multiples of 16 bytes).
  * Negative values return LAP_EINVAL. */
 int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms, int split_rows);
+
+/* Node order of the solves on this handle (lap_eigs_graph; the eigenpairs of
+ * L do not depend on it: P L P^T has eigenvectors P v).  LAP_REORDER_DEGREE:
+ * the handle keeps a second device copy of its graphs with each graph's
+ * nodes numbered by decreasing degree (ties by original number), built at
+ * the first solve that needs it, and solves on that copy: the correction
+ * solve's SpMM then streams the rows of its degree-sorted schedule and finds
+ * the hubs' rows together in L2.  Start blocks (x0, x0_dev) are permuted in
+ * and eigenvectors permuted back, so results are in the caller's numbering;
+ * the schedule of the copy is autotuned at its first solve like any large
+ * handle's.  LAP_REORDER_NONE: solve on the graph as numbered.
+ * LAP_REORDER_AUTO (default): degree order for a single graph of at least
+ * 100,000 nodes.  The step-level entry points always use the graph as
+ * numbered.  Other values return LAP_EINVAL. */
+int lap_graph_set_reorder(lap_graph* g, int mode);
 
 /* Solve on a handle whose graphs are already on the device (the CSR is not
  * copied again).  evals: host [nseg * k] (graph s at s*k); evecs_dev: device

@@ -28,6 +28,8 @@ LAP_PREC_FP64, LAP_PREC_MIXED = 0, 1
 LAP_F64, LAP_F32 = 0, 1
 LAP_PRECOND_JACOBI, LAP_PRECOND_FSAI = 0, 1
 _PRECONDS = {"jacobi": LAP_PRECOND_JACOBI, "fsai": LAP_PRECOND_FSAI}
+LAP_REORDER_AUTO, LAP_REORDER_NONE, LAP_REORDER_DEGREE = -1, 0, 1
+_REORDERS = {"auto": LAP_REORDER_AUTO, "none": LAP_REORDER_NONE, "degree": LAP_REORDER_DEGREE}
 LAP_TOL_NORM1, LAP_TOL_THETA = 0, 1
 _TOL_MODES = {"norm1": LAP_TOL_NORM1, "theta": LAP_TOL_THETA}
 
@@ -138,6 +140,7 @@ _SIGNATURES = {
     "lap_gnn_wgrad_bf16": (_I, [_P, _I, _P, _I, _P, _I, _P, _P]),
     "lap_gnn_tanh_back_bf16": (_I, [_P, _P, _I, _P, _I, _I, _P]),
     "lap_graph_set_gathers": (_I, [_P, _I]),
+    "lap_graph_set_reorder": (_I, [_P, _I]),
     "lap_gnn_warm_start": (_I, [_P, _PD, ctypes.c_int64, _I, ctypes.c_uint64, _P, _I, _P]),
     "lap_gnn_param_count": (ctypes.c_int64, [_I]),
     "lap_gnn_loss": (_I, [_I, _I, _D, _P, _P, _P, _P, _P]),
@@ -365,6 +368,11 @@ class Graph:
     def set_gathers(self, gathers):
         """Form of the vectorised SpMM (lap_graph_set_gathers): 2, 4, 8, 102 or 104."""
         _check(lib().lap_graph_set_gathers(self.h, gathers), "lap_graph_set_gathers")
+
+    def set_reorder(self, mode="auto"):
+        """Node order of the solves (lap_graph_set_reorder): "auto", "none" or "degree"."""
+        _check(lib().lap_graph_set_reorder(self.h, _REORDERS[mode] if isinstance(mode, str) else int(mode)),
+               "lap_graph_set_reorder")
 
     def set_launch(self, max_ctas=0, device_timeout_ms=0.0, split_rows=0):
         """CTA cap, device wait limit, and the row count from which the

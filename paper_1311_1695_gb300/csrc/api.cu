@@ -73,6 +73,16 @@ void add_null(SolveOut& out, const std::vector<int>& nrows, const std::vector<in
 // a start block of the caller's, the network's proposal (gnn_infer.cu)
 // becomes the start block; without parameters, or when the forward pass
 // fails, the solve starts from the seeded random block as usual.
+// A device allocation released at scope exit.
+struct DevMem {
+  void* p = nullptr;
+  ~DevMem() { cudaFree(p); }
+  bool alloc(size_t bytes) {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); p = nullptr; return false; }
+    return true;
+  }
+};
+
 struct GnnStart {
   double* x0 = nullptr;
   ~GnnStart() { cudaFree(x0); }
@@ -250,23 +260,31 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   return rc;
 }
 
-int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* opts, double* evals, double* evecs_dev,
+int lap_eigs_graph(lap_graph* g0, int k, double tol, int method, const lap_opts* opts, double* evals, double* evecs_dev,
                    lap_info* infos) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (!g || !evals || k < 1 || !(tol > 0.0) || method < LAP_JD || method > LAP_IRLM ||
-      (method != LAP_JD && g->hg.nseg > 1)) {
+  if (!g0 || !evals || k < 1 || !(tol > 0.0) || method < LAP_JD || method > LAP_IRLM ||
+      (method != LAP_JD && g0->hg.nseg > 1)) {
     set_error("bad arguments to lap_eigs_graph");
     return LAP_EINVAL;
   }
   lap_opts o = merged(opts);
   const int kk = o.include_null ? k - 1 : k;
-  const int S = g->hg.nseg;
+  const int S = g0->hg.nseg;
   std::vector<int> nrows(S);
   for (int s = 0; s < S; ++s) {
-    nrows[s] = g->row0[s + 1] - g->row0[s];
+    nrows[s] = g0->row0[s + 1] - g0->row0[s];
     if (kk < 1 || kk > nrows[s] - 1) { set_error("k out of range for a graph"); return LAP_EINVAL; }
   }
   if (o.include_null && evecs_dev) { set_error("include_null needs host eigenvectors (use lap_eigs)"); return LAP_EINVAL; }
+  // the solves run on the handle's degree-ordered twin when its node order asks for one
+  lap_graph* g = g0;
+  {
+    const int rc = graph_solve_handle(g0, &g);
+    if (rc) return rc;
+  }
+  const bool twin = g != g0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(o.stream);
   if (o.team || (!g->tuned && g->hg.n >= kSplitRows)) {
     // a resident handle of a large graph is autotuned once, at its first solve
     lap_opts ot = o;
@@ -278,12 +296,45 @@ int lap_eigs_graph(lap_graph* g, int k, double tol, int method, const lap_opts* 
     const int rc = apply_precond(g, o);
     if (rc) return rc;
   }
+  // a caller's start block into the twin's order
+  DevMem x0p;
+  std::vector<double> x0h;
+  if (twin && method == LAP_JD && S == 1 && o.k0 > 0 && (o.x0_dev || o.x0)) {
+    const int n = g->hg.n;
+    if (o.x0_dev) {
+      const int ld = o.ldx0 > 0 ? o.ldx0 : o.k0;
+      if (!x0p.alloc(sizeof(double) * (size_t)n * ld)) { set_error("device allocation failed (start block)"); return LAP_ENOMEM; }
+      if (twin_permute_rows(g, o.x0_dev, ld, static_cast<double*>(x0p.p), ld, o.k0, st)) {
+        set_error("CUDA error permuting the start block");
+        return LAP_ECUDA;
+      }
+      o.x0_dev = static_cast<double*>(x0p.p);
+      o.ldx0 = ld;
+    } else {
+      x0h.resize((size_t)n * o.k0);
+      for (int c = 0; c < o.k0; ++c)
+        for (int i = 0; i < n; ++i) x0h[(size_t)c * n + g->perm_of_parent[(size_t)i]] = o.x0[(size_t)c * n + i];
+      o.x0 = x0h.data();
+    }
+  }
   GnnStart gs;
   apply_gnn(g, o, method, gs);
   SolveOut out;
-  out.dev_vecs = evecs_dev;
+  DevMem vt;
+  if (twin && evecs_dev) {
+    if (!vt.alloc(sizeof(double) * (size_t)g->hg.n * kk)) { set_error("device allocation failed (eigenvectors)"); return LAP_ENOMEM; }
+    out.dev_vecs = static_cast<double*>(vt.p);
+  } else {
+    out.dev_vecs = evecs_dev;
+  }
   int rc = solve(g, kk, tol, method, o, evecs_dev != nullptr, out);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
+  if (twin && evecs_dev) {
+    if (twin_unpermute_blocks(g, kk, out.dev_vecs, evecs_dev, st) != LAP_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+      set_error("CUDA error returning the eigenvectors");
+      return LAP_ECUDA;
+    }
+  }
   if (o.include_null) add_null(out, nrows, std::vector<int>(S, kk));
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   for (int s = 0; s < S; ++s) {
@@ -324,7 +375,12 @@ int lap_graph_info(const lap_graph* g, int64_t* n_total, int* nseg, double* norm
 
 int lap_graph_set_schedule(lap_graph* g, int team, int long_thresh) {
   if (!g) { set_error("NULL handle"); return LAP_EINVAL; }
-  return graph_set_schedule(g, team, long_thresh);
+  int rc = graph_set_schedule(g, team, long_thresh);
+  if (rc) return rc;
+  if (team) g->user_team = team;
+  if (long_thresh > 0) g->user_thresh = long_thresh;
+  if (g->twin) rc = graph_set_schedule(g->twin, team, long_thresh);
+  return rc;
 }
 
 int lap_graph_set_gathers(lap_graph* g, int gathers) {
@@ -333,6 +389,8 @@ int lap_graph_set_gathers(lap_graph* g, int gathers) {
     return LAP_EINVAL;
   }
   g->dg.vec_u = gathers;
+  g->user_gathers = gathers;
+  if (g->twin) g->twin->dg.vec_u = gathers;
   return LAP_OK;
 }
 
@@ -341,9 +399,12 @@ int lap_graph_set_launch(lap_graph* g, int max_ctas, double device_timeout_ms, i
     set_error("bad arguments to lap_graph_set_launch");
     return LAP_EINVAL;
   }
-  g->max_ctas = max_ctas;
-  g->timeout_ms = device_timeout_ms;
-  g->split_rows = split_rows;
+  for (lap_graph* h : {g, g->twin}) {
+    if (!h) continue;
+    h->max_ctas = max_ctas;
+    h->timeout_ms = device_timeout_ms;
+    h->split_rows = split_rows;
+  }
   return LAP_OK;
 }
 

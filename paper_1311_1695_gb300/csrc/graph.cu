@@ -171,15 +171,17 @@ int graph_set_schedule(lap_graph* g, int team, int long_thresh) {
 }
 
 int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
-                const double* const* weights, lap_graph** out) {
+                const double* const* weights, lap_graph** out, bool check) {
   *out = nullptr;
   if (nb < 1 || !n || !rowptr || !colidx) { set_error("bad batch arguments"); return LAP_EINVAL; }
   int64_t ntot = 0, nnztot = 0;
   bool weighted = false;
   for (int s = 0; s < nb; ++s) {
     if (!rowptr[s]) { set_error("NULL rowptr"); return LAP_EINVAL; }
-    const int rc = validate(n[s], rowptr[s], colidx[s], weights ? weights[s] : nullptr);
-    if (rc) return rc;
+    if (check) {  // (a handle's own relabelled copy is valid by construction)
+      const int rc = validate(n[s], rowptr[s], colidx[s], weights ? weights[s] : nullptr);
+      if (rc) return rc;
+    }
     ntot += n[s];
     nnztot += rowptr[s][n[s]];
     if (weights && weights[s]) weighted = true;
@@ -352,7 +354,9 @@ void graph_free(lap_graph* g) {
   cudaFree(g->d_sched);  // the hub schedule
   cudaFree(g->d_prec);   // the preconditioner
   cudaFree(g->scratch); cudaFree(g->small);
+  cudaFree(g->d_perm_of_parent);
   g->pcg.release();
+  graph_free(g->twin);
   delete g;
 }
 

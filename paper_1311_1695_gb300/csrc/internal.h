@@ -94,13 +94,30 @@ struct lap_graph {
   double timeout_ms = 0.0;      // grid-barrier wait limit (0: default)
   int split_rows = 0;           // per-phase correction solve from this many rows (0: default)
   int tuned = 0;                // the SpMM schedule was autotuned on this handle
+  // the caller's explicit settings (lap_graph_set_schedule / _set_gathers), for the twin
+  int user_team = 0, user_thresh = 0, user_gathers = 0;
+  // node order of the solves (reorder.cu): lap_reorder mode, the degree-ordered
+  // copy the solves run on, and (on that copy) the parent's row -> own row map
+  int reorder = LAP_REORDER_AUTO;
+  lap_graph* twin = nullptr;
+  int* d_perm_of_parent = nullptr;
+  std::vector<int> perm_of_parent;
 };
 
 namespace lapeig {
 
 // Validate and upload a batch of host CSR graphs.  Returns LAP_* status.
 int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const int32_t* const* colidx,
-                const double* const* weights, lap_graph** out);
+                const double* const* weights, lap_graph** out, bool check = true);
+// Node order of the solves (reorder.cu).  graph_solve_handle: the handle the
+// solvers run on (g, or its degree-ordered twin, built on first use);
+// twin_permute_rows: start block rows into the twin's order (row-major);
+// twin_unpermute_blocks: eigenvector blocks back to the original order.
+bool reorder_wanted(const lap_graph* g);
+int graph_solve_handle(lap_graph* g, lap_graph** out);
+void graph_drop_twin(lap_graph* g);
+int twin_permute_rows(const lap_graph* tw, const double* in, int ldin, double* out, int ldout, int cols, cudaStream_t s);
+int twin_unpermute_blocks(const lap_graph* tw, int k, const double* in, double* out, cudaStream_t s);
 void graph_free(lap_graph* g);
 int graph_set_schedule(lap_graph* g, int team, int long_thresh);
 // Preconditioner of the correction solve (LAP_PRECOND_*), set up on the host.

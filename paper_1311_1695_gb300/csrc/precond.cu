@@ -263,5 +263,7 @@ template void fsai_apply<double>(const DevGraph&, int, const double*, int, doubl
 
 extern "C" int lap_graph_set_precond(lap_graph* g, int kind, double alpha) {
   if (!g) { lapeig::set_error("NULL handle"); return LAP_EINVAL; }
-  return lapeig::graph_set_precond(g, kind, alpha);
+  int rc = lapeig::graph_set_precond(g, kind, alpha);
+  if (rc == LAP_OK && g->twin) rc = lapeig::graph_set_precond(g->twin, kind, alpha);
+  return rc;
 }
