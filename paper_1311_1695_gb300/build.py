@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblapeig.so")
 
-SOURCES = ["spmm.cu", "blas.cu", "small.cu", "graph.cu", "solver.cu", "methods.cu", "api.cu", "gnn.cu", "prof.cu", "pcg.cu", "noalloc.cu", "ortho.cu", "pcg_split.cu", "apps.cu", "precond.cu", "gnn_mma.cu", "ortho_ts.cu", "gnn_infer.cu", "gnn_train.cu", "reorder.cu"]
+SOURCES = ["spmm.cu", "blas.cu", "small.cu", "graph.cu", "solver.cu", "methods.cu", "api.cu", "gnn.cu", "prof.cu", "pcg.cu", "noalloc.cu", "ortho.cu", "pcg_split.cu", "apps.cu", "precond.cu", "gnn_mma.cu", "ortho_ts.cu", "gnn_infer.cu", "gnn_train.cu", "reorder.cu", "df64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

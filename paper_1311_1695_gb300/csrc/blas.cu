@@ -14,6 +14,7 @@
 // (they are zero at rest).  FP32 data is summed in FP32 within a 32-row chunk
 // and in FP64 across chunks and tiles.
 #include "common.cuh"
+#include "df64.cuh"
 #include "kernels.cuh"
 #include "prof.h"
 
@@ -139,6 +140,66 @@ __global__ void __launch_bounds__(kThreads) k_gram(DevGraph g, Reduce red, const
         const int i = oi[u], j = oj[u];
         G[(size_t)t.seg * sg + (size_t)i * ldg + j] = (i < ones && ones_mean) ? v[u] * inv_n : v[u];
       }
+    }
+    release(red, t.seg, nout);
+  }
+}
+
+// ------------------------------------------------------------------ Gram, double-float
+// G[s] = A^T B for FP64 blocks of at most 32 columns each, accumulated in
+// double-float arithmetic (df64.cuh) within a tile, in FP64 across tiles.
+constexpr int kDfCols = 32;
+__global__ void __launch_bounds__(kThreads) k_gram_df64(DevGraph g, Reduce red, const double* __restrict__ A,
+                                                        int lda, int p, const double* __restrict__ B, int ldb,
+                                                        int q, double* __restrict__ G, int ldg, int64_t sg,
+                                                        const int* __restrict__ seg_skip) {
+  constexpr int NO = kDfCols * kDfCols / kThreads;
+  const Tile t = g.tiles[blockIdx.x];
+  if (seg_skip && seg_skip[t.seg]) return;
+  __shared__ float Ah[kChunk * kDfCols], Al[kChunk * kDfCols], Bh[kChunk * kDfCols], Bl[kChunk * kDfCols];
+  const int nout = p * q;
+  float H[NO], L[NO];
+  int oi[NO], oj[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int o = threadIdx.x + kThreads * u;
+    H[u] = L[u] = 0.f;
+    oi[u] = o < nout ? o / q : -1;
+    oj[u] = o < nout ? o - (o / q) * q : 0;
+  }
+  for (int c0 = t.r0; c0 < t.r1; c0 += kChunk) {
+    const int nr = min(kChunk, t.r1 - c0);
+    for (int e = threadIdx.x; e < nr * p; e += kThreads) {
+      const int r = e / p, c = e - r * p;
+      split64(A[(size_t)(c0 + r) * lda + c], Ah[e], Al[e]);
+    }
+    for (int e = threadIdx.x; e < nr * q; e += kThreads) {
+      const int r = e / q, c = e - r * q;
+      split64(B[(size_t)(c0 + r) * ldb + c], Bh[e], Bl[e]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int i = oi[u], j = oj[u];
+      if (i >= 0)
+        for (int r = 0; r < nr; ++r) mac64(H[u], L[u], Ah[r * p + i], Al[r * p + i], Bh[r * q + j], Bl[r * q + j]);
+    }
+    __syncthreads();
+  }
+  double accd[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) accd[u] = join64(H[u], L[u]);
+  if (commit<NO>(red, t.seg, seg_tiles(g, t.seg), accd, nout, nullptr, 0)) {
+    double v[NO];  // every total loaded before any is stored
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int o = threadIdx.x + kThreads * u;
+      v[u] = o < nout ? total(red, t.seg, o) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int o = threadIdx.x + kThreads * u;
+      if (o < nout) G[(size_t)t.seg * sg + (size_t)oi[u] * ldg + oj[u]] = v[u];
     }
     release(red, t.seg, nout);
   }
@@ -889,6 +950,14 @@ void gram(const DevGraph& g, const Reduce& red, const T* A, int lda, int p, cons
   else if (nout <= 4 * kThreads) launch_gram<T, 4>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
   else if (nout <= 8 * kThreads) launch_gram<T, 8>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
   else launch_gram<T, 17>(g, red, A, lda, p, B, ldb, q, ones, ones_mean, G, ldg, sg, seg_skip, s);
+}
+
+int gram_df64(const DevGraph& g, const Reduce& red, const double* A, int lda, int p, const double* B, int ldb, int q,
+              double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s) {
+  if (p < 1 || p > kDfCols || q < 1 || q > kDfCols) return 1;
+  LAP_PROF("gram", 8.0 * g.n * (p + q), s);
+  k_gram_df64<<<g.ntiles, kThreads, 0, s>>>(g, red, A, lda, p, B, ldb, q, G, ldg, sg, seg_skip);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <typename T>

@@ -34,6 +34,17 @@ template <typename T>
 void update(const DevGraph& g, T* Y, int ldy, int q, double beta, double alpha, const T* A, int lda,
             int p, int ones, const double* S, int lds, int64_t ss, const int* seg_skip, cudaStream_t s);
 
+// ---- Rotation V[:, 0:mk] = V[:, 0:m] Y_s (in place) in double-float
+// arithmetic (df64.cu), m, mk <= 32; returns 1 for other shapes (nothing
+// launched), -1 on a launch error.
+int rotate_df64(const DevGraph& g, double* V, int ldv, int m, int mk, const double* Y, int ldy, int64_t sy,
+                const int* seg_skip, cudaStream_t s);
+
+// ---- Gram G[s] = A^T B of FP64 blocks (p, q <= 32) in double-float
+// arithmetic within a tile (blas.cu); returns 1 for other shapes.
+int gram_df64(const DevGraph& g, const Reduce& red, const double* A, int lda, int p, const double* B, int ldb, int q,
+              double* G, int ldg, int64_t sg, const int* seg_skip, cudaStream_t s);
+
 // ---- Column dots: out[s*so + c] = sum_rows A[:, c] B[:, c], c < q
 template <typename T>
 void coldots(const DevGraph& g, const Reduce& red, const T* A, int lda, const T* B, int ldb, int q,

@@ -389,6 +389,11 @@ struct JD {
       if (large())
         rotated = rotate_ts(g, ortho_work(), V, z.ldv, m, mk, Y, z.mmax, (int64_t)z.mmax * z.mmax, st) == 0;
     }
+    if constexpr (std::is_same<TV, double>::value && std::is_same<TP, float>::value) {
+      // the mixed solve's FP64 basis: double-float rotation (FP64 issues at
+      // 1/58 of the FP32 rate on GB300)
+      rotated = rotate_df64(g, V, z.ldv, m, mk, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st) == 0;
+    }
     if (!rotated)
       update<TV>(g, V, z.ldv, mk, 0.0, 1.0, V, z.ldv, m, 0, Y, z.mmax, (int64_t)z.mmax * z.mmax, seg_skip, st);
     // W[:, 0:b] = L V[:, 0:b] by one SpMM of the Ritz block instead of the
@@ -503,7 +508,11 @@ struct JD {
       ortho(mk, z.b, drop1);
     }
     spmm<TV>(g, V + mk, z.ldv, W + mk, z.ldv, z.b, st);
-    gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
+    bool bordered = false;
+    if constexpr (std::is_same<TV, double>::value && std::is_same<TP, float>::value)  // double-float, as the rotation
+      bordered = gram_df64(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, Gm, z.b, 65 * 64, seg_skip, st) == 0;
+    if (!bordered)
+      gram<TV>(g, red, V, z.ldv, mk + z.b, W + mk, z.ldv, z.b, 0, 0, Gm, z.b, 65 * 64, seg_skip, st);
     h_border(z.nseg, H, z.mmax, (int64_t)z.mmax * z.mmax, Gm, z.b, 65 * 64, mk, z.b, keep1, 64, G->d_norm1, seg_skip, st);
     return mk + z.b;
   }
@@ -878,8 +887,12 @@ int solve_jd(lap_graph* G, int k, double tol, const lap_opts& o, bool want_vecs,
   // well-separated smallest eigenvalue, which the shift-targeted corrections
   // would not bring back
   int m = j1.start(nullptr, 0, z.mk, o.seed ^ 0x9E3779B97F4A7C15ull, 1e-10, x0d, ldx0, k0);
+  // phase 1 runs to 5e-7 ||L||_1, within a decade of the FP32 floor
+  // (eps32 ||L||): an FP32 outer iteration costs about two thirds of a
+  // mixed one (measured on the power-law benchmark graphs: 2e-6 left two
+  // more iterations to the second phase)
   std::vector<double> tol1(S);
-  for (int s = 0; s < S; ++s) tol1[s] = std::max(P.tol_floor, 2e-6) * G->norm1[s];
+  for (int s = 0; s < S; ++s) tol1[s] = std::max(P.tol_floor, 5e-7) * G->norm1[s];
   int m_out = m;
   Params P1 = P;
   int st1 = iterate(j1, m, P1, tol1, false, outer, m_out, 1e-10, 8, o.cuda_graph >= 0);
