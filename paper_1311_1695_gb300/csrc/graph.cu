@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "internal.h"
 
@@ -50,6 +51,25 @@ struct Packer {
   }
 };
 
+// Rows [0, n) cut into at most `threads` ranges of about equal nonzero
+// count (rowptr quantiles); f(r0, r1, t) runs on each, the calling thread
+// taking range 0.  One range (one thread) below ~64k nonzeros.
+template <typename F>
+void for_row_ranges(int64_t n, const int64_t* rowptr, F&& f) {
+  const int64_t nnz = rowptr[n];
+  const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)hw, nnz / 65536));
+  std::vector<int64_t> cut((size_t)nt + 1, n);
+  cut[0] = 0;
+  for (int t = 1; t < nt; ++t)
+    cut[(size_t)t] = std::lower_bound(rowptr, rowptr + n + 1, nnz * t / nt) - rowptr;
+  for (int t = 1; t <= nt; ++t) cut[(size_t)t] = std::max(cut[(size_t)t], cut[(size_t)t - 1]);
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back([&, t] { f(cut[(size_t)t], cut[(size_t)t + 1], t); });
+  f(cut[0], cut[1], 0);
+  for (auto& x : th) x.join();
+}
+
 int validate(int64_t n, const int64_t* rowptr, const int32_t* colidx, const double* w) {
   if (n < 1 || !rowptr || (!colidx && rowptr[n] > 0)) {
     set_error("n < 1 or NULL CSR array");
@@ -60,34 +80,60 @@ int validate(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
     if (rowptr[i + 1] < rowptr[i]) { set_error("rowptr not monotone"); return LAP_EINVAL; }
   const int64_t nnz = rowptr[n];
   if (nnz >= (int64_t(1) << 31) || n >= (int64_t(1) << 31)) { set_error("graph too large for int32 indices"); return LAP_EINVAL; }
-  for (int64_t i = 0; i < n; ++i) {
-    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int64_t j = colidx[p];
-      if (j < 0 || j >= n) { set_error("column index out of range"); return LAP_EINVAL; }
-      if (j == i) { set_error("diagonal entry (self-loop) in adjacency"); return LAP_ESELFLOOP; }
-      if (p > rowptr[i] && colidx[p - 1] >= j) { set_error("column indices not strictly increasing"); return LAP_EUNSORTED; }
-      if (w && !(std::isfinite(w[p]) && w[p] > 0.0)) { set_error("weight not finite and positive"); return LAP_EWEIGHT; }
+  // per-row checks, in parallel; the failure reported is the first in row
+  // order (each range keeps its first, the ranges are in row order)
+  struct Fail { int64_t row = -1; int code = LAP_OK; const char* msg = nullptr; };
+  const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
+  std::vector<Fail> fails(hw);
+  for_row_ranges(n, rowptr, [&](int64_t r0, int64_t r1, int t) {
+    for (int64_t i = r0; i < r1; ++i) {
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        const int64_t j = colidx[p];
+        const char* msg = nullptr;
+        int code = LAP_OK;
+        if (j < 0 || j >= n) { msg = "column index out of range"; code = LAP_EINVAL; }
+        else if (j == i) { msg = "diagonal entry (self-loop) in adjacency"; code = LAP_ESELFLOOP; }
+        else if (p > rowptr[i] && colidx[p - 1] >= j) { msg = "column indices not strictly increasing"; code = LAP_EUNSORTED; }
+        else if (w && !(std::isfinite(w[p]) && w[p] > 0.0)) { msg = "weight not finite and positive"; code = LAP_EWEIGHT; }
+        if (code != LAP_OK) { fails[(size_t)t] = Fail{i, code, msg}; return; }
+      }
     }
-  }
-  // symmetry: (i, j, w) needs (j, i, w).  The transpose by a counting sort
-  // (rows visited in order, so each transposed row comes out sorted) must
-  // equal the matrix itself: sequential passes instead of a binary search
-  // per nonzero in another row.
-  std::vector<int64_t> next(rowptr, rowptr + n);
-  std::vector<int32_t> tcol((size_t)nnz);
-  std::vector<double> tw(w ? (size_t)nnz : 0);
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-      const int64_t j = colidx[p];
-      const int64_t q = next[j]++;
-      if (q >= rowptr[j + 1]) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
-      tcol[q] = (int32_t)i;
-      if (w) tw[q] = w[p];
+  });
+  for (const Fail& f : fails)
+    if (f.code != LAP_OK) { set_error(f.msg); return f.code; }
+  // symmetry: (i, j, w) needs (j, i, w).  With sorted rows and no duplicate
+  // column, a binary search for i in row j per nonzero decides it: the map
+  // (i, j) -> (j, i) then sends the pattern into itself injectively, so onto.
+  std::vector<int> bad(hw, 0);  // 1: pattern, 2: values
+  // (the lookups are random rows: they go in batches whose row-pointer loads
+  // and first column loads are all issued before any search depends on them)
+  for_row_ranges(n, rowptr, [&](int64_t r0, int64_t r1, int t) {
+    constexpr int kB = 16;
+    int64_t rows[kB], js[kB], ps[kB], lo[kB], hi[kB];
+    int64_t i = r0;
+    const int64_t pend = rowptr[r1];
+    for (int64_t p0 = rowptr[r0]; p0 < pend; p0 += kB) {
+      const int nb = (int)std::min<int64_t>(kB, pend - p0);
+      for (int k = 0; k < nb; ++k) {  // the row of each nonzero
+        while (rowptr[i + 1] <= p0 + k) ++i;
+        rows[k] = i;
+        ps[k] = p0 + k;
+        js[k] = colidx[p0 + k];
+      }
+      for (int k = 0; k < nb; ++k) { lo[k] = rowptr[js[k]]; hi[k] = rowptr[js[k] + 1]; }
+      for (int k = 0; k < nb; ++k) __builtin_prefetch(colidx + lo[k]);
+      for (int k = 0; k < nb; ++k) {
+        const int32_t* b1 = colidx + hi[k];
+        const int32_t* q = std::lower_bound(colidx + lo[k], b1, (int32_t)rows[k]);
+        if (q == b1 || *q != rows[k]) { bad[(size_t)t] = 1; return; }
+        if (w && w[q - colidx] != w[ps[k]]) { bad[(size_t)t] = 2; return; }
+      }
     }
-  for (int64_t q = 0; q < nnz; ++q) {
-    if (tcol[q] != colidx[q]) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
-    if (w && tw[q] != w[q]) { set_error("adjacency values not symmetric"); return LAP_ENOTSYM; }
-  }
+  });
+  int worst = 0;
+  for (int v : bad) worst = worst == 1 ? 1 : (v == 1 ? 1 : std::max(worst, v));
+  if (worst == 1) { set_error("adjacency pattern not symmetric"); return LAP_ENOTSYM; }
+  if (worst == 2) { set_error("adjacency values not symmetric"); return LAP_ENOTSYM; }
   return LAP_OK;
 }
 
@@ -202,23 +248,39 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
   g->norm1.assign(nb, 0.0);
   int64_t r = 0, p = 0;
   int maxdeg = 0;
+  const unsigned hw = std::max(1u, std::min(std::thread::hardware_concurrency(), 32u));
   for (int s = 0; s < nb; ++s) {
     g->row0[s] = (int)r;
     const int64_t* rp = rowptr[s];
     const double* ws = weights ? weights[s] : nullptr;
-    double dmax = 0.0;
-    for (int64_t i = 0; i < n[s]; ++i, ++r) {
-      double d = 0.0;
-      for (int64_t q = rp[i]; q < rp[i + 1]; ++q, ++p) {
-        colcat[p] = (int)(colidx[s][q] + g->row0[s]);
-        const double wv = ws ? ws[q] : 1.0;
-        if (weighted) w64[p] = wv;
-        d += wv;
+    const int64_t rb = r, pb = p;  // the graph's first row and nonzero in the concatenation
+    std::vector<double> dmax_t(hw, 0.0);
+    std::vector<int> maxdeg_t(hw, 0);
+    for_row_ranges(n[s], rp, [&](int64_t i0, int64_t i1, int t) {
+      double dm = 0.0;
+      int md = 0;
+      for (int64_t i = i0; i < i1; ++i) {
+        double d = 0.0;
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+          colcat[(size_t)(pb + q)] = (int)(colidx[s][q] + rb);
+          const double wv = ws ? ws[q] : 1.0;
+          if (weighted) w64[(size_t)(pb + q)] = wv;
+          d += wv;
+        }
+        g->rowptr_h[(size_t)(rb + i + 1)] = (int)(pb + rp[i + 1]);
+        deg[(size_t)(rb + i)] = d;
+        dm = std::max(dm, d);
+        md = std::max(md, (int)(rp[i + 1] - rp[i]));
       }
-      g->rowptr_h[r + 1] = (int)p;
-      deg[r] = d;
-      dmax = std::max(dmax, d);
-      maxdeg = std::max(maxdeg, (int)(rp[i + 1] - rp[i]));
+      dmax_t[(size_t)t] = dm;
+      maxdeg_t[(size_t)t] = md;
+    });
+    r += n[s];
+    p += rp[n[s]];
+    double dmax = 0.0;
+    for (unsigned t = 0; t < hw; ++t) {
+      dmax = std::max(dmax, dmax_t[t]);
+      maxdeg = std::max(maxdeg, maxdeg_t[t]);
     }
     g->norm1[s] = 2.0 * dmax;
   }
@@ -301,11 +363,11 @@ int graph_build(int nb, const int64_t* n, const int64_t* const* rowptr, const in
 
   std::vector<float> w32(w64.begin(), w64.end());
   std::vector<float> deg32(deg.begin(), deg.end());
-  g->colidx_h = colcat;  // kept for set-ups that need the pattern (preconditioner)
+  g->colidx_h = std::move(colcat);  // kept for set-ups that need the pattern (preconditioner)
   g->w64_h = w64;
   Packer pk;
   pk.add(&g->d_rowptr, g->rowptr_h.data(), g->rowptr_h.size());
-  pk.add(&g->d_colidx, colcat.data(), colcat.size());
+  pk.add(&g->d_colidx, g->colidx_h.data(), g->colidx_h.size());
   if (weighted) {
     pk.add(&g->d_w64, w64.data(), w64.size());
     pk.add(&g->d_w32, w32.data(), w32.size());

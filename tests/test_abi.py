@@ -73,7 +73,7 @@ def test_rejects_asymmetric(lib):
 
 
 def test_rejects_asymmetric_values_and_counts(lib):
-    """The symmetry check (a counting-sort transpose compared with the matrix):
+    """The symmetry check (a binary search for (j, i) per nonzero (i, j)):
     equal patterns with unequal weights, and a row with an extra one-way edge
     whose row counts still add up, are both rejected; a symmetric weighted
     graph passes the host checks."""
@@ -93,6 +93,34 @@ def test_rejects_asymmetric_values_and_counts(lib):
     rp2 = rp.copy()
     rp2[4:] -= 1
     assert _call(G.CSRGraph(6, rp2, ci[keep], None)) == pkg.LAP_ENOTSYM
+
+
+def test_validation_of_large_graphs_split_over_threads(lib):
+    """Graphs large enough for the host checks to run on several threads
+    (row ranges of equal nonzero count): a fault in any range is found, and
+    when several rows are faulty the first one in row order decides the
+    status."""
+    g = G.with_random_weights(G.grid_graph(300, 300), 5)  # 358,800 nonzeros
+    n, rp = g.n, g.rowptr
+    late = rp[n - 10]  # a nonzero in the last range
+    # one-way weight change near the end
+    w = g.weights.copy()
+    w[late] *= 3.0
+    assert _call(G.CSRGraph(n, rp, g.colidx, w)) == pkg.LAP_ENOTSYM
+    # a missing reverse entry in the middle: drop (i, j), keep (j, i)
+    mid = n // 2
+    keep = np.ones(g.colidx.size, bool)
+    keep[rp[mid]] = False
+    rp2 = rp.copy()
+    rp2[mid + 1:] -= 1
+    assert _call(G.CSRGraph(n, rp2, g.colidx[keep], w[keep])) == pkg.LAP_ENOTSYM
+    # an unsorted row late and a non-positive weight early: the earlier row decides
+    ci = g.colidx.copy()
+    ci[late], ci[late + 1] = ci[late + 1], ci[late]
+    w2 = g.weights.copy()
+    w2[rp[100]] = 0.0
+    assert _call(G.CSRGraph(n, rp, ci, w2)) == pkg.LAP_EWEIGHT
+    assert _call(G.CSRGraph(n, rp, ci, g.weights)) == pkg.LAP_EUNSORTED
 
 
 def test_rejects_bad_weight(lib):
