@@ -252,7 +252,7 @@ def lap_eigs(g, k: int, tol: float = 1e-8, method: str = "jd", want_vectors: boo
                         _METHODS[method] if isinstance(method, str) else int(method), ctypes.byref(o),
                         _ptr(evals, ctypes.c_double), _ptr(evecs, ctypes.c_double), ctypes.byref(info))
     _check(st, "lap_eigs", allow_partial=True)
-    return evals, (None if evecs is None else evecs.T.copy()), info.as_dict()
+    return evals, (None if evecs is None else evecs.T), info.as_dict()  # n x k (a column-major view)
 
 
 def lap_eigs_batched(graphs, k, tol: float = 1e-8, method: str = "jd", want_vectors: bool = True, **opts):
@@ -276,7 +276,7 @@ def lap_eigs_batched(graphs, k, tol: float = 1e-8, method: str = "jd", want_vect
                                 _METHODS[method] if isinstance(method, str) else int(method), ctypes.byref(o), ev_p,
                                 vv_p, infos)
     _check(st, "lap_eigs_batched", allow_partial=True)
-    return evals, ([v.T.copy() for v in evecs] if want_vectors else None), [i.as_dict() for i in infos]
+    return evals, ([v.T for v in evecs] if want_vectors else None), [i.as_dict() for i in infos]  # column-major views
 
 
 # ---------------------------------------------------------------- device-level API

@@ -199,12 +199,13 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
   GnnStart gs;
   apply_gnn(g, o, method, gs);
   SolveOut out;
+  if (want && !o.include_null) out.host_vecs = evecs;  // straight into the caller's arrays
   rc = solve_jd(g, kmax, tol, o, want, out, kk.data());
   graph_free(g);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
   for (int s = 0; s < nb; ++s) {  // graph s keeps its first kk[s] pairs (columns are contiguous)
     out.evals[s].resize(kk[s]);
-    if (want) out.evecs[s].resize((size_t)nrows[s] * kk[s]);
+    if (want && !out.evecs.empty()) out.evecs[s].resize((size_t)nrows[s] * kk[s]);
   }
   if (o.include_null) add_null(out, nrows, kk);
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -213,7 +214,8 @@ int lap_eigs_batched(int nb, const int64_t* n, const int64_t* const* rowptr, con
   if (rc == LAP_ENOCONV && all_ok) rc = LAP_OK;
   for (int s = 0; s < nb; ++s) {
     std::memcpy(evals[s], out.evals[s].data(), sizeof(double) * k[s]);
-    if (want && evecs[s]) std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k[s]);
+    if (want && evecs[s] && !out.evecs.empty())
+      std::memcpy(evecs[s], out.evecs[s].data(), sizeof(double) * (size_t)n[s] * k[s]);
     if (infos) {
       infos[s] = out.info[s];
       infos[s].elapsed_ms = ms;
@@ -247,12 +249,14 @@ int lap_eigs(int64_t n, const int64_t* rowptr, const int32_t* colidx, const doub
   GnnStart gs;
   apply_gnn(g, o, method, gs);
   SolveOut out;
+  double* hv[1] = {evecs};
+  if (evecs && !o.include_null) out.host_vecs = hv;  // JD copies straight into the caller's array
   rc = solve(g, kk, tol, method, o, evecs != nullptr, out);
   graph_free(g);
   if (rc < 0 && rc != LAP_ETIMEOUT) return rc;
   if (o.include_null) add_null(out, std::vector<int>{(int)n}, std::vector<int>{kk});
   std::memcpy(evals, out.evals[0].data(), sizeof(double) * k);
-  if (evecs) std::memcpy(evecs, out.evecs[0].data(), sizeof(double) * (size_t)n * k);
+  if (evecs && !out.evecs.empty()) std::memcpy(evecs, out.evecs[0].data(), sizeof(double) * (size_t)n * k);
   if (info) {
     *info = out.info[0];
     info->elapsed_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

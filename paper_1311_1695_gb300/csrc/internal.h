@@ -145,6 +145,9 @@ struct SolveOut {
   std::vector<std::vector<double>> evecs;   // per segment [n_s * k] column-major (may stay empty)
   std::vector<lap_info> info;               // per segment
   double* dev_vecs = nullptr;               // if set: eigenvectors stay on the device here
+  // if set (JD, host eigenvectors): graph s's first kseg[s] columns go straight
+  // into host_vecs[s] (n_s x kseg[s] column-major) and evecs stays empty
+  double* const* host_vecs = nullptr;
 };
 
 // Block Jacobi-Davidson over all segments of the handle (lock-step).

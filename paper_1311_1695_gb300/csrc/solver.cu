@@ -751,6 +751,15 @@ void finish(JD<TV, TP>& jd, const Params& P, int status, int outer, lap_graph* G
   if (want_vecs && out.dev_vecs) {
     copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, out.dev_vecs, st);
     cudaStreamSynchronize(st);
+  } else if (want_vecs && out.host_vecs) {  // into the caller's arrays, no staging copy
+    copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, d_out, st);
+    for (int s = 0; s < S; ++s) {
+      const int ns = G->row0[s + 1] - G->row0[s];
+      if (out.host_vecs[s])
+        cudaMemcpyAsync(out.host_vecs[s], d_out + (size_t)G->row0[s] * P.k, sizeof(double) * ns * P.kseg[s],
+                        cudaMemcpyDeviceToHost, st);
+    }
+    cudaStreamSynchronize(st);
   } else if (want_vecs) {
     copy_out<TV>(G->dg, jd.V, jd.z.ldv, P.k, d_best, d_out, st);
     out.evecs.assign(S, {});
