@@ -43,6 +43,7 @@
 #include "pcg_fused.cuh"
 #include "prof.h"
 #include "small.cuh"
+#include "df64.cuh"
 #include "stage.cuh"
 
 namespace lapeig {
@@ -267,6 +268,129 @@ __global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
         }
       });
   if (MODE != kWrite && ok && cur >= 0) flush();
+}
+
+// ---------------------------------------------------------------- FP64 pass from FP32 inputs
+// [1 | V0 | t]^T t of the mixed solve's FP64 pass (rows 0..mfull of the
+// accumulators, q columns), with the FP64 kept basis given as its FP32 split
+// V0 = Vh + Vl (hi and remainder, split64) and t exactly FP32: a product
+// vh t is exact as the FP32 pair (p, fma(vh, t, -p)), the remainder's
+// product vl t (2^-24 of the term) needs FP32 only, and the sums run in
+// double-float arithmetic (df64.cuh): FP32 issue cost instead of one FP64
+// product per term.  Staged blocks: Vh, Vl (row stride ldq), t (ldt).
+template <int BWL, int M0B>
+__global__ void __launch_bounds__(kThreads) k_full32(DevGraph g, SweepArgs a, const float* __restrict__ Vl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kRed = M0B * BWL;
+  double* red = reinterpret_cast<double*>(smem_raw);
+  constexpr size_t head = (sizeof(double) * kRed + 15) / 16 * 16;
+  stg::Stager<float> sg;
+  {
+    const int widths[3] = {a.ldq, a.ldq, a.ldt};
+    sg.setup(smem_raw + head, 3, widths);
+  }
+  constexpr int RW = 32 / BWL, SLOTS = kWarps * RW;
+  const int m0 = a.m0, q = a.q, mfull = a.m0 + a.q;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane % BWL, sub = lane / BWL;
+  const bool colok = c < q;
+  float H[M0B], L[M0B];
+#pragma unroll
+  for (int i = 0; i < M0B; ++i) H[i] = L[i] = 0.f;
+  int cur = -1;
+  auto flush = [&]() {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kRed; e += kThreads) red[e] = 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < M0B; ++i) {
+      if (i <= mfull) {  // uniform across the CTA
+        double v = join64(H[i], L[i]);
+#pragma unroll
+        for (int o = BWL; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (sub == 0 && colok) atomicAdd(red + i * BWL + c, v);
+      }
+      H[i] = L[i] = 0.f;
+    }
+    __syncthreads();
+    double* A = a.acc + (size_t)cur * a.sacc;
+    for (int e = threadIdx.x; e < (mfull + 1) * q; e += kThreads) {
+      const int i = e / q, cc = e - i * q;
+      const double v = red[i * BWL + cc];
+      if (v != 0.0) atomicAdd(A + e, v);
+    }
+  };
+  const float* src[3] = {static_cast<const float*>(a.Qb), Vl, static_cast<const float*>(a.Tb)};
+  const bool ok = stg::walk<float>(
+      sg, g, a.seg_skip, src, 0u, a.bar,
+      [&](const Tile& t) {
+        if (cur >= 0) flush();
+        cur = t.seg;
+      },
+      [&](const Tile&, int, int nrows, int u) {
+        const float* sh = sg.blk(u, 0);
+        const float* sl = sg.blk(u, 1);
+        const float* stt = sg.blk(u, 2);
+        for (int base = warp * RW; base < nrows; base += SLOTS) {
+          const int il = base + sub;
+          const bool row = il < nrows;
+          const int ir = row ? il : nrows - 1;  // rows past the end read a valid row, add nothing
+          const float* vh = sh + (size_t)ir * a.ldq;
+          const float* vl = sl + (size_t)ir * a.ldq;
+          const float* tr = stt + (size_t)ir * a.ldt;
+          const float y = (row && colok) ? tr[c] : 0.f;
+          mac64(H[0], L[0], 1.f, 0.f, y, 0.f);
+#pragma unroll
+          for (int i = 0; i < M0B - 1; ++i) {
+            if (i < m0) mac64(H[i + 1], L[i + 1], vh[i], vl[i], y, 0.f);
+            else if (i < mfull) mac64(H[i + 1], L[i + 1], tr[i - m0], 0.f, y, 0.f);
+          }
+        }
+      });
+  if (ok && cur >= 0) flush();
+}
+
+// V[:, 0:m] (FP64) -> Vh + Vl (FP32 split, split64), row stride ld.
+__global__ void k_split_block(DevGraph g, const double* __restrict__ V, int ldv, float* __restrict__ Vh,
+                              float* __restrict__ Vl, int ld, int m) {
+  const int64_t total = (int64_t)g.n * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / m), i = (int)(e - (int64_t)r * m);
+    float h, l;
+    split64(V[(size_t)r * ldv + i], h, l);
+    Vh[(size_t)r * ld + i] = h;
+    Vl[(size_t)r * ld + i] = l;
+  }
+}
+
+template <int BWL, int M0B>
+int launch_full32(const DevGraph& g, const SweepArgs& a, const float* Vl, cudaStream_t s, int max_ctas) {
+  const int widths[3] = {a.ldq, a.ldq, a.ldt};
+  const size_t smem = (sizeof(double) * M0B * BWL + 15) / 16 * 16 + stg::Stager<float>::bytes(3, widths);
+  auto kern = k_full32<BWL, M0B>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return -1;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  int grid = std::max(1, per_sm) * nsm;
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+  if (grid > g.ntiles) grid = g.ntiles;
+  kern<<<std::max(grid, 1), kThreads, smem, s>>>(g, a, Vl);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int full32_m(const DevGraph& g, const SweepArgs& a, const float* Vl, cudaStream_t s, int max_ctas) {
+  const int rows = a.m0 + a.q + 1;
+  if (rows > 34) return 1;
+  auto pick = [&](auto bwl) -> int {
+    constexpr int B = decltype(bwl)::value;
+    if (rows <= 24) return launch_full32<B, 24>(g, a, Vl, s, max_ctas);
+    return launch_full32<B, 34>(g, a, Vl, s, max_ctas);
+  };
+  if (a.q <= 8) return pick(std::integral_constant<int, 8>{});
+  if (a.q <= 16) return pick(std::integral_constant<int, 16>{});
+  return pick(std::integral_constant<int, 32>{});
 }
 
 // ---------------------------------------------------------------- small steps
@@ -518,11 +642,18 @@ int ortho_ts(const DevGraph& g, const OrthoTs& w, T* V, int ldv, int m0, int q, 
   return rc ? -1 : 0;
 }
 
+void split_block(const DevGraph& g, const double* V, int ldv, float* Vh, float* Vl, int ld, int m, cudaStream_t s) {
+  LAP_PROF("convert", 16.0 * g.n * m, s);
+  const int64_t total = (int64_t)g.n * m;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+  k_split_block<<<grid, 256, 0, s>>>(g, V, ldv, Vh, Vl, ld, m);
+}
+
 int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int m0, int q, const float* V32,
-                   int ld32, float* Tt, int ldt, double drop1, cudaStream_t s) {
+                   int ld32, float* Tt, int ldt, double drop1, cudaStream_t s, const float* V32lo) {
   LAP_PROF("ortho", 0.0, s);
   if (!ortho_ts_ok<double>(V, ldv, m0, q) || !ortho_ts_ok<float>(V32, ld32, 0, q) ||
-      !ortho_ts_ok<float>(Tt, ldt, 0, q) || ld32 < m0 || ldt < q)
+      !ortho_ts_ok<float>(Tt, ldt, 0, q) || ld32 < m0 || ldt < q || (V32lo && !a16(V32lo)))
     return 1;
   SweepArgs a{};
   a.Qb = V32; a.ldq = ld32; a.m0 = m0; a.Tb = Tt; a.ldt = ldt; a.toff = 0; a.q = q;
@@ -544,7 +675,14 @@ int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int 
   SweepArgs b{};
   b.Qb = V; b.ldq = ldv; b.m0 = m0; b.Tb = nullptr; b.toff = m0; b.q = q; b.mfull = m0 + q;
   b.acc = w.acc; b.sacc = w.sacc; b.seg_skip = w.seg_skip; b.bar = w.bar;
-  rc |= sweep_m<double, kFull, false, false>(g, b, s, w.max_ctas);
+  if (V32lo) {  // the same products from the FP32 split of V0 and the FP32 t
+    SweepArgs c{};
+    c.Qb = V32; c.ldq = ld32; c.m0 = m0; c.Tb = Tt; c.ldt = ldt; c.q = q;
+    c.acc = w.acc; c.sacc = w.sacc; c.seg_skip = w.seg_skip; c.bar = w.bar;
+    rc |= full32_m(g, c, V32lo, s, w.max_ctas);
+  } else {
+    rc |= sweep_m<double, kFull, false, false>(g, b, s, w.max_ctas);
+  }
   pyth_step(g, w, m0, q, 0, 0.25, w.keep2, false, 1, s);
   a.out = V + m0; a.ldo = ldv; a.out64 = 1;
   rc |= sweep_m<float, kWrite, true, true>(g, a, s, w.max_ctas);

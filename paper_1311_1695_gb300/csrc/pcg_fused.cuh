@@ -78,9 +78,15 @@ template <typename T>
 int ortho_ts(const DevGraph& g, const OrthoTs& w, T* V, int ldv, int m0, int q, double drop1, cudaStream_t s);
 // The mixed-precision form: the correction block Tt (FP32, row stride ldt)
 // against V32 = V[:, 0:m0] in FP32 (row stride ld32) in FP32, then into
-// V[:, m0 : m0+q] (FP64) and one FP64 pass.  Tt is overwritten.
+// V[:, m0 : m0+q] (FP64) and one FP64 pass.  Tt is overwritten.  With
+// V32lo (the remainders of split_block, stride ld32), V32 holding the high
+// parts, the FP64 pass's Gram products come from the FP32 blocks in
+// double-float arithmetic instead of FP64 products.
 int ortho_ts_mixed(const DevGraph& g, const OrthoTs& w, double* V, int ldv, int m0, int q, const float* V32,
-                   int ld32, float* Tt, int ldt, double drop1, cudaStream_t s);
+                   int ld32, float* Tt, int ldt, double drop1, cudaStream_t s, const float* V32lo = nullptr);
+// V[:, 0:m] (FP64, row stride ldv) -> Vh + Vl (FP32 high parts and
+// remainders, df64.cuh split64, row stride ld).
+void split_block(const DevGraph& g, const double* V, int ldv, float* Vh, float* Vl, int ld, int m, cudaStream_t s);
 // One FP64 pass over V[:, 0:q] (FP64, already orthonormal to FP32 accuracy,
 // T32 its FP32 original): the columns orthonormal to FP64 accuracy and
 // orthogonal to e; keep1 = the columns kept.  Returns 0, 1 or -1.

@@ -179,7 +179,8 @@ struct JD {
   TP* LXb;  // L X of the correction solve
   TP* Xs;   // X packed for the per-phase correction solve
   TP* LZb;  // L z~ of the per-phase correction solve
-  float* V32 = nullptr;  // FP32 copy of the kept block V[:, 0:mk] (FP64 basis, large graphs)
+  float* V32 = nullptr;    // FP32 high parts of the kept block V[:, 0:mk] (FP64 basis, large graphs)
+  float* V32lo = nullptr;  // and their FP32 remainders (split_block)
   int ld32 = 0;
   // small FP64 per segment
   double *H, *Y, *theta, *rn2, *Gm, *Sm, *Rinv, *scale, *tmp;
@@ -244,7 +245,7 @@ struct JD {
     add(2 * n * z.ldv * sizeof(TV));
     add(n * z.ldb * sizeof(TV));
     for (int i = 0; i < 10; ++i) add(n * z.ldb * sizeof(TP));
-    if (mixed_v32) add(n * (size_t)round_up(z.mk, 4) * sizeof(float));
+    if (mixed_v32) add(2 * n * (size_t)round_up(z.mk, 4) * sizeof(float));
     const size_t mm = (size_t)z.mmax * z.mmax;
     add(S * mm * 8); add(S * mm * 8); add(S * z.mmax * 8); add(S * 64 * 8);
     add(S * 65 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 64 * 8); add(S * 64 * 8); add(S * 64 * 8);
@@ -274,6 +275,7 @@ struct JD {
     if (mixed_v32) {
       ld32 = round_up(z.mk, 4);
       V32 = a.take<float>(n * (size_t)ld32);
+      V32lo = a.take<float>(n * (size_t)ld32);
     }
     const size_t mm = (size_t)z.mmax * z.mmax;
     H = a.take<double>(S * mm);
@@ -453,8 +455,8 @@ struct JD {
       X = V; ldx = z.ldv; R = Rv; ldr = z.ldb;
     } else {
       const bool ts = mixed_v32 && large();
-      if (ts) {  // the whole kept block in FP32 (X = its first b columns)
-        convert<TV, float>(g, V, z.ldv, V32, ld32, mk, st);
+      if (ts) {  // the whole kept block split into FP32 high parts and remainders (X = the first b high parts)
+        split_block(g, reinterpret_cast<const double*>(V), z.ldv, V32, V32lo, ld32, mk, st);
         X = reinterpret_cast<const TP*>(V32); ldx = ld32;
       } else {
         convert<TV, TP>(g, V, z.ldv, Xp, z.ldb, z.b, st);
@@ -489,7 +491,7 @@ struct JD {
           inject = false;
         }
         const int rc = ortho_ts_mixed(g, ortho_work(), V, z.ldv, mk, z.b, V32, ld32, reinterpret_cast<float*>(Tt),
-                                      z.ldb, drop1, st);
+                                      z.ldb, drop1, st, V32lo);
         if (rc < 0) {
           set_error(std::string("orthonormalisation launch failed: ") + cudaGetErrorString(cudaGetLastError()));
           return -1;
