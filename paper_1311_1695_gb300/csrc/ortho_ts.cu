@@ -113,7 +113,7 @@ __device__ __forceinline__ void load_row(T (&d)[N], const T* src, int valid) {
 }
 
 template <typename T, int BWL, int M0B, int MODE, bool HR, bool HG>
-__global__ void __launch_bounds__(kThreads) k_sweep(DevGraph g, SweepArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) k_sweep(DevGraph g, SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using SM = SweepSmem<T, BWL, M0B>;
   T* red = reinterpret_cast<T*>(smem_raw);
