@@ -65,7 +65,15 @@ void for_row_ranges(int64_t n, const int64_t* rowptr, F&& f) {
     cut[(size_t)t] = std::lower_bound(rowptr, rowptr + n + 1, nnz * t / nt) - rowptr;
   for (int t = 1; t <= nt; ++t) cut[(size_t)t] = std::max(cut[(size_t)t], cut[(size_t)t - 1]);
   std::vector<std::thread> th;
-  for (int t = 1; t < nt; ++t) th.emplace_back([&, t] { f(cut[(size_t)t], cut[(size_t)t + 1], t); });
+  int started = 1;  // ranges 1 .. started-1 have a thread
+  try {
+    for (int t = 1; t < nt; ++t) {
+      th.emplace_back([&, t] { f(cut[(size_t)t], cut[(size_t)t + 1], t); });
+      started = t + 1;
+    }
+  } catch (...) {  // no thread could be created: the caller's thread takes the rest
+  }
+  for (int t = started; t < nt; ++t) f(cut[(size_t)t], cut[(size_t)t + 1], t);
   f(cut[0], cut[1], 0);
   for (auto& x : th) x.join();
 }
